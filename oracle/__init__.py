@@ -1,0 +1,153 @@
+"""CPU oracle for the single-pulse search hot path (ASTROFLOW, arXiv 2511.02328).
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+cpu_baseline / reference leg of bench.py may import this package.  It shares
+no code with the CUDA library and never calls it.
+
+The heavy loops live in oracle.c (plain C, fp64, OpenMP over DM rows); this
+module loads it with ctypes and adds numpy-friendly wrappers.  The pure-Python
+brute force for tiny inputs is in oracle.brute, the candidate clustering and
+matching rule in oracle.nms, the cut-out and CNN oracles in oracle.cutout and
+oracle.cnn.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from .build import build_oracle
+
+_lib = None
+
+
+class OracleCand(ctypes.Structure):
+    _fields_ = [("dm_idx", ctypes.c_int32), ("t", ctypes.c_int32),
+                ("width", ctypes.c_int32), ("snr", ctypes.c_double)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build_oracle()
+        L = ctypes.CDLL(path)
+        L.oracle_chan_freq.restype = ctypes.c_double
+        L.oracle_chan_freq.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        L.oracle_ref_freq.restype = ctypes.c_double
+        L.oracle_ref_freq.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.oracle_delay_table.restype = ctypes.c_int
+        L.oracle_delay_table.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+        L.oracle_dmax.restype = ctypes.c_int32
+        L.oracle_dmax.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+        L.oracle_dedisperse.restype = None
+        L.oracle_dedisperse.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                        ctypes.c_int, ctypes.c_int64, ctypes.c_void_p]
+        L.oracle_rowstats.restype = None
+        L.oracle_rowstats.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                      ctypes.c_void_p]
+        L.oracle_row_sigma.restype = ctypes.c_double
+        L.oracle_row_sigma.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
+        L.oracle_boxcar_snr.restype = None
+        L.oracle_boxcar_snr.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                        ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+        L.oracle_peaks.restype = ctypes.c_int64
+        L.oracle_peaks.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                                   ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64]
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def chan_freqs(nchan, f_lo, f_hi):
+    """Channel-centre frequencies in MHz (reading: centres), via the C oracle."""
+    L = lib()
+    return np.array([L.oracle_chan_freq(c, nchan, f_lo, f_hi) for c in range(nchan)])
+
+
+def delay_table(nchan, f_lo, f_hi, tsamp, dms):
+    """int32 [ndm][nchan] integer delays, Eq. (coarse_delay) (Sec. 2.3)."""
+    dms = np.ascontiguousarray(dms, dtype=np.float64)
+    D = np.empty((dms.size, nchan), dtype=np.int32)
+    rc = lib().oracle_delay_table(nchan, f_lo, f_hi, tsamp, _ptr(dms), dms.size, _ptr(D))
+    if rc != 0:
+        raise ValueError("oracle_delay_table failed (%d)" % rc)
+    return D
+
+
+def dedisperse(X, D, nout=None):
+    """Brute-force plane Y[d][t] = sum_c X[c][t + D[d][c]] (Sec. 2.3), int32."""
+    X = np.ascontiguousarray(X, dtype=np.uint8)
+    D = np.ascontiguousarray(D, dtype=np.int32)
+    nchan, nsamp = X.shape
+    ndm = D.shape[0]
+    if D.shape[1] != nchan:
+        raise ValueError("delay table / data channel mismatch")
+    if nout is None:
+        nout = nsamp - int(D.max())
+    if nout <= 0 or int(D.max()) + nout > nsamp or int(D.min()) < 0:
+        raise ValueError("nout out of range")
+    Y = np.empty((ndm, nout), dtype=np.int32)
+    lib().oracle_dedisperse(_ptr(X), nchan, nsamp, _ptr(D), ndm, nout, _ptr(Y))
+    return Y
+
+
+def rowstats(Y):
+    Y = np.ascontiguousarray(Y, dtype=np.int32)
+    ndm, nout = Y.shape
+    S = np.empty(ndm, dtype=np.int64)
+    Q = np.empty(ndm, dtype=np.int64)
+    lib().oracle_rowstats(_ptr(Y), ndm, nout, _ptr(S), _ptr(Q))
+    return S, Q
+
+
+def row_sigma(S, Q, nout):
+    return lib().oracle_row_sigma(int(S), int(Q), int(nout))
+
+
+def boxcar_snr(Y, widths):
+    """(best_snr float64 [ndm][nout], best_w int32 index [ndm][nout])."""
+    Y = np.ascontiguousarray(Y, dtype=np.int32)
+    widths = np.ascontiguousarray(widths, dtype=np.int32)
+    if widths.size == 0 or np.any(np.diff(widths) <= 0) or widths[0] < 1:
+        raise ValueError("widths must be strictly ascending and >= 1")
+    ndm, nout = Y.shape
+    snr = np.empty((ndm, nout), dtype=np.float64)
+    bw = np.empty((ndm, nout), dtype=np.int32)
+    lib().oracle_boxcar_snr(_ptr(Y), ndm, nout, _ptr(widths), widths.size, _ptr(snr), _ptr(bw))
+    return snr, bw
+
+
+def peaks(best_snr, best_w, widths, thresh, cap=1 << 22):
+    """List of (dm_idx, t, width, snr) in (d, t) order, and the total count."""
+    best_snr = np.ascontiguousarray(best_snr, dtype=np.float64)
+    best_w = np.ascontiguousarray(best_w, dtype=np.int32)
+    widths = np.ascontiguousarray(widths, dtype=np.int32)
+    ndm, nout = best_snr.shape
+    out = (OracleCand * cap)()
+    n = lib().oracle_peaks(_ptr(best_snr), _ptr(best_w), ndm, nout, _ptr(widths), float(thresh),
+                           ctypes.cast(out, ctypes.c_void_p), cap)
+    res = [(out[i].dm_idx, out[i].t, out[i].width, out[i].snr) for i in range(min(n, cap))]
+    return res, int(n)
+
+
+def search(X, D, widths, thresh):
+    """Whole plain search on the CPU: plane, S/N, candidates."""
+    Y = dedisperse(X, D)
+    snr, bw = boxcar_snr(Y, widths)
+    cands, n = peaks(snr, bw, widths, thresh)
+    return Y, snr, bw, cands
+
+
+def injection_offsets(nchan, f_lo, f_hi, tsamp, dm, t0):
+    """Per-channel start sample of a pulse that arrives at f_ref at sample t0
+    with dispersion measure dm: t0 + D_inj[c], where D_inj uses the same
+    rounding as Eq. (coarse_delay).  Used to build injected test inputs."""
+    D = delay_table(nchan, f_lo, f_hi, tsamp, [dm])[0]
+    return (np.int64(t0) + D.astype(np.int64))
+
+
+def threads():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
