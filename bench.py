@@ -1,0 +1,338 @@
+"""Benchmark of the single-pulse search hot path on one GB300 (or N replicas).
+
+Workload (the full-band plain search): 4096 channels 1000-1500 MHz, tsamp
+49.152 us, 2^18 uint8 samples of N(128,12) noise with 20 injected dispersed
+pulses (DM 50-1000, width 0.2-10 ms, S/N 6-30), DM trials 0..1000 step 1,
+boxcar widths 1..256 (powers of two), threshold S/N 8.
+
+A step is one pass of the device path: dedispersion -> row sums -> boxcar S/N
+-> candidate compaction, on inputs already resident in HBM (`value`).  The
+e2e figure runs the same search through the host-buffer entry point af_search
+(pinned host input copied in, candidates copied out and clustered on the host).
+
+metric: DM-trial x channel x output-sample additions per second (the brute-force
+work ndm*nchan*nout), plus the real-time factor R = nout*tsamp / kernel time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 launch with torch.distributed.run; every rank searches its own beam
+(same workload shape, different seed): weak scaling, no data-path collective.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DM-trial·chan·samples/s, realtime factor, p99 chunk latency at equal recall"
+UNIT = "DM-trial·chan·samples/s"
+WORKLOAD = ("plain search, full band: 4096 ch 1000-1500 MHz, tsamp 49.152 us, 2^18 samples uint8 "
+            "N(128,12) + 20 injected pulses DM 50-1000 width 0.2-10 ms S/N 6-30; DMs 0-1000 step 1; "
+            "boxcar 1..256 (powers of two); threshold 8")
+NCHAN, F_LO, F_HI, TSAMP, NSAMP = 4096, 1000.0, 1500.0, 49.152e-6, 1 << 18
+DMS = np.arange(0.0, 1001.0, 1.0)
+WIDTHS = [1, 2, 4, 8, 16, 32, 64, 128, 256]
+THRESH = 8.0
+CAP = 1 << 20
+SM_MAX_MHZ_FALLBACK = 2070.0
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def make_input(seed, delays_fn):
+    """Noise + 20 pulses; the pulses' per-channel start samples come from
+    delays_fn(dm_list) -> int [n][nchan] (the library's plan on the GPU arm)."""
+    from paper_2511_02328_gb300 import synth
+    pp = synth.pulse_params(20, seed + 1000, (50.0, 1000.0), (0.2e-3, 10e-3), (6.0, 30.0),
+                            (0.5, (NSAMP - 50000) * TSAMP - 0.5), 0.45, TSAMP)
+    D = delays_fn([p["dm"] for p in pp])
+    pulses = [synth.Pulse(p["t0"] + D[i].astype(np.int64), p["width"],
+                          synth.pulse_amplitude(p["snr"], NCHAN, p["width"])) for i, p in enumerate(pp)]
+    return synth.filterbank(NCHAN, NSAMP, seed=seed, pulses=pulses), pp
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.rows = []
+        self.proc = None
+        self.active = False
+        self.lock = threading.Lock()
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            with self.lock:
+                if self.active:
+                    self.rows.append([x.strip() for x in line.split(",")])
+
+    def mark(self, on):
+        with self.lock:
+            self.active = on
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except Exception:
+                continue
+            for n, v in zip(names, r[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != n:
+        raise SystemExit("--gpus %d but WORLD_SIZE=%d" % (n, world))
+    return rank, world, local
+
+
+def cpu_oracle_sample(x, D, rows, nout):
+    """Time the oracle (as it stands) on a bounded sample: the listed DM rows of
+    the same workload, dedispersion + S/N + candidates."""
+    import oracle
+    t0 = time.perf_counter()
+    Y = oracle.dedisperse(x, D[rows], nout=nout)
+    snr, bw = oracle.boxcar_snr(Y, WIDTHS)
+    oracle.peaks(snr, bw, WIDTHS, THRESH)
+    dt = time.perf_counter() - t0
+    work = len(rows) * NCHAN * nout
+    return work / dt, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    cores = oracle.threads()
+    x, _ = make_input(12345, lambda dms: oracle.delay_table(NCHAN, F_LO, F_HI, TSAMP, dms))
+    D = oracle.delay_table(NCHAN, F_LO, F_HI, TSAMP, DMS)
+    nout = NSAMP - int(D.max())
+    rows_per_step = 8
+    rng = np.random.default_rng(5)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(x, D, rng.choice(len(DMS), 2, replace=False), nout)
+    times = []
+    for _ in range(args.steps):
+        rows = np.sort(rng.choice(len(DMS), rows_per_step, replace=False))
+        _, dt = cpu_oracle_sample(x, D, rows, nout)
+        times.append(dt)
+    total = sum(times)
+    value = args.steps * rows_per_step * NCHAN * nout / total
+    sample = "%d random DM rows of 1001 per step (full nout=%d, all 4096 channels): dedispersion + S/N + peaks" % (
+        rows_per_step, nout)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="afgb", choices=["afgb", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2511_02328_gb300 import _lib
+    from paper_2511_02328_gb300.search import Plan
+
+    plan = Plan(NCHAN, F_LO, F_HI, TSAMP, DMS)
+    nout = plan.nout(NSAMP)
+    x_host, pulses = make_input(1 + 7919 * rank, lambda dms: Plan(NCHAN, F_LO, F_HI, TSAMP, dms).delays())
+    dev = torch.device("cuda", local)
+    x = torch.from_numpy(x_host).to(dev)
+    plane = torch.empty((plan.ndm, nout), dtype=torch.int32, device=dev)
+    stats = torch.empty((plan.ndm, 2), dtype=torch.int64, device=dev)
+    snr = torch.empty((plan.ndm, nout), dtype=torch.float32, device=dev)
+    bw = torch.empty((plan.ndm, nout), dtype=torch.uint8, device=dev)
+    cands = torch.empty((CAP, 24), dtype=torch.uint8, device=dev)
+    count = torch.empty(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+    H = plan.handle
+    launches_per_step = 5   # dedisperse, rowstats, rowconst, boxcar, candidates
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+
+    def step(i=None):
+        if i is not None:
+            ev[i][0].record(stream)
+        _lib.af_dedisperse(H, x.data_ptr(), NSAMP, plane.data_ptr(), 0, sp)
+        if i is not None:
+            ev[i][1].record(stream)
+        _lib.af_rowstats(H, plane.data_ptr(), nout, stats.data_ptr(), sp)
+        _lib.af_boxcar_snr(H, plane.data_ptr(), nout, stats.data_ptr(), WIDTHS, snr.data_ptr(), bw.data_ptr(), sp)
+        _lib.af_candidates(H, snr.data_ptr(), bw.data_ptr(), nout, WIDTHS, THRESH, 0, cands.data_ptr(), CAP,
+                           count.data_ptr(), sp)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    gpu_id = local
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    clocks.mark(True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        step(i)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clocks.mark(False)
+    if dist is not None:
+        dist.barrier()
+    ms_total = t_start.elapsed_time(t_end)
+    ms_dedisp = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    ncand = int(count.item())
+    if dist is not None:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+
+    # ---- e2e through the host-buffer entry point (pinned input, copies timed)
+    x_pin = torch.from_numpy(x_host).pin_memory()
+    _lib.af_search_reserve(H, NSAMP, CAP)
+    out = np.empty(CAP, dtype=_lib.CAND_DTYPE)
+    for _ in range(2):
+        _lib.af_search(H, x_pin.data_ptr(), NSAMP, WIDTHS, THRESH, CAP, sp, out=out)
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    nc = 0
+    for _ in range(args.e2e_steps):
+        c, nc = _lib.af_search(H, x_pin.data_ptr(), NSAMP, WIDTHS, THRESH, CAP, sp, out=out)
+        plan.cluster(c)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    clocks.stop()
+
+    work = float(plan.ndm) * NCHAN * nout
+    ms_step = ms_total / args.steps
+    value = world * work / (ms_step * 1e-3)
+    pk = peaks()
+    sm_max = float(pk.get("sm_max_mhz", SM_MAX_MHZ_FALLBACK))
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = nsm * 128 * sm_max * 1e6 / 1e12          # T int32 lane-ops/s
+    achieved = work / (ms_dedisp * 1e-3) / 1e12        # T adds/s
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+    alg_bytes = NCHAN * NSAMP + plan.ndm * nout * 4
+    hbm_ach = alg_bytes / (ms_dedisp * 1e-3) / 1e9
+    clk = clocks.summary()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        D = plan.delays()
+        rows = np.array([0, 250, 500, 750, 1000, 123, 377, 888])
+        v, dt = cpu_oracle_sample(x_host, D, rows, nout)
+        cpu = {"value": v, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+               "sample": "8 DM rows of 1001 (full nout=%d, 4096 channels): dedispersion + S/N + peaks, %.1f s"
+                         % (nout, dt)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nchan": NCHAN, "nsamp": NSAMP, "ndm": plan.ndm, "nout": nout,
+                       "widths": WIDTHS, "threshold": THRESH, "parallelism": "replicas (one beam per GPU)",
+                       "l2": "inputs larger than L2 (1.07 GB input, 0.86 GB plane per step)"},
+            "realtime_factor": nout * TSAMP / (ms_dedisp * 1e-3),
+            "realtime_factor_step": nout * TSAMP / (ms_step * 1e-3),
+            "dedisp_ms": ms_dedisp,
+            "candidates": ncand,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                         "frac": achieved / alu_peak, "traffic": None,
+                         "peak_basis": "%d SMs x 128 int32 lanes x %.0f MHz (derived, of max clock)" % (nsm, sm_max),
+                         "hbm": {"achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak,
+                                 "basis": "of measured"}},
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * work / e2e_s, "unit": UNIT, "h2d_bytes_per_step": NCHAN * NSAMP,
+                    "d2h_bytes_per_step": 4 + 24 * min(nc, CAP)},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * afgb.h -- C ABI of the GB300 (sm_103a) single-pulse search library.
+ *
+ * The library implements the hot path of the single-pulse search of
+ * ASTROFLOW (arXiv 2511.02328): exact brute-force incoherent dedispersion of
+ * 8-bit filterbank data into an int32 DM-time plane (Sec. 2.3), boxcar
+ * matched filtering with S/N normalisation (step (iii) of the workflow in
+ * Sec. 1) and thresholding into a candidate list (Sec. 2), with the
+ * true-positive clustering rule of Sec. 4.2.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an int status: AF_OK (0) or one of the AF_E* codes.
+ *    af_last_error() returns a thread-local message for the last failure.
+ *  - Pointers named d_* are DEVICE pointers owned by the caller (for example
+ *    torch tensors); pointers named h_* or host_* are host pointers owned by
+ *    the caller.  The library never frees caller memory.
+ *  - Handles (af_plan_t, af_batch_t, af_stream_t, af_model_t) are owned by
+ *    the library and freed by the matching *_destroy call.
+ *  - Calls that take `void* stream` (a cudaStream_t; NULL = legacy default
+ *    stream) only ENQUEUE work on that stream and return at once; results are
+ *    valid after the stream is synchronised.  Argument errors are reported
+ *    synchronously, before anything is enqueued.
+ *  - No call that launches work allocates device memory.  Scratch lives in the
+ *    plan (sized at af_plan time) or in a reservation made by an explicit
+ *    *_reserve call.
+ *  - Filterbank data are uint8, channel-major: x[c * nsamp + t].
+ *  - A plan is not thread-safe: calls on the same plan must not overlap in
+ *    host threads, and work enqueued on different streams with the same plan
+ *    shares the plan's scratch (serialise such streams).
+ */
+#ifndef AFGB_H
+#define AFGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define AF_OK        0
+#define AF_EINVAL    1  /* invalid argument (sizes, pointers, ordering)      */
+#define AF_ENOMEM    2  /* device or host allocation failed                  */
+#define AF_ENOBUFS   3  /* request exceeds a reservation or an HBM budget     */
+#define AF_ECUDA     4  /* a CUDA runtime call failed; see af_last_error()   */
+#define AF_ETIMEOUT  5  /* a bounded device or host wait ran out             */
+#define AF_EOVERFLOW 6  /* more candidates than capacity; count is the total */
+#define AF_EAGAIN    7  /* nothing ready yet (polling calls)                 */
+
+#define AF_MAX_WIDTHS 32 /* maximum number of boxcar widths per call         */
+#define AF_NO_WIDTH 0xFF /* best-width index where no width fits (tail)      */
+
+typedef struct af_plan_s* af_plan_t;
+
+/* Per-DM-row sums of the plane: sum = sum_t Y[d][t], sumsq = sum_t Y[d][t]^2
+ * over the row's nout samples (exact 64-bit integers). */
+typedef struct {
+    int64_t sum;
+    int64_t sumsq;
+} af_rowstats_t;
+
+/* One candidate: DM row, output time index t of the window's leading edge
+ * (arrival time at f_ref, the top of the band), boxcar width in samples,
+ * S/N, and abs_sample = sample0 + t (sample0 is given by the caller, e.g. the
+ * first sample of a streamed chunk).  TOA in seconds = abs_sample * tsamp. */
+typedef struct {
+    int32_t dm_idx;
+    int32_t t;
+    int32_t width;
+    float snr;
+    int64_t abs_sample;
+} af_cand_t;
+
+/* Thread-local message describing the last failing call ("" if none). */
+const char* af_last_error(void);
+
+/* Library version string. */
+const char* af_version(void);
+
+/* ---- plan: channel frequencies and the integer delay table ------------- *
+ * Builds the delay table of Eq. (coarse_delay), Sec. 2.3, for an explicit DM
+ * list:
+ *     D[d][c] = round( K_DM * dm_list[d] / tsamp * (1/f_c^2 - 1/f_ref^2) )
+ * with K_DM = 4.148808e3 s MHz^2 pc^-1 cm^3 (Eq. KDM; the paper prints the
+ * unit as ms, the value is in seconds with f in MHz), f_c the CENTRE of
+ * channel c, f_c = f_lo + (c + 0.5) * (f_hi - f_lo) / nchan, f_ref =
+ * max(f_lo, f_hi) (top of the band), round = half away from zero, evaluated
+ * in IEEE double as a = (K*dm)/tsamp, b = 1/(fc*fc) - 1/(fr*fr), D = llround(a*b)
+ * with no fused multiply-add.
+ *  nchan   number of channels (1 .. 65536)
+ *  f_lo    band edge on channel 0's side, MHz (> 0)
+ *  f_hi    band edge on channel nchan-1's side, MHz (> 0, != f_lo); f_hi < f_lo
+ *          means channel 0 is the highest frequency
+ *  tsamp   sampling interval, seconds (> 0)
+ *  dm_list host array of ndm trial DMs, pc cm^-3, each >= 0 and finite; any
+ *          order (rows of the plane follow this order)
+ *  ndm     1 .. 1<<20
+ * The plan copies everything it needs, uploads the table to the current
+ * device and allocates its scratch there (AF_ENOMEM / AF_ECUDA on failure).
+ * AF_EINVAL if an argument is out of range or a delay exceeds int32. */
+int af_plan(af_plan_t* out, int nchan, double f_lo, double f_hi, double tsamp,
+            const double* dm_list, int ndm);
+
+/* Frees the plan and everything it allocated (NULL is accepted). */
+int af_plan_destroy(af_plan_t plan);
+
+/* Copies the delay table to host_out ([ndm][nchan] int32, may be NULL) and
+ * the largest delay Dmax to *dmax (may be NULL). */
+int af_plan_delays(af_plan_t plan, int32_t* host_out, int32_t* dmax);
+
+/* Plan dimensions (any output pointer may be NULL). */
+int af_plan_info(af_plan_t plan, int* nchan, int* ndm, int32_t* dmax, double* tsamp);
+
+/* Output length for nsamp input samples: nout = nsamp - Dmax (reading of the
+ * paper's truncation by the DM delay, Sec. 3).  AF_EINVAL if nout <= 0. */
+int af_plan_nout(af_plan_t plan, int64_t nsamp, int64_t* nout);
+
+/* ---- dedispersion: Sec. 2.3, the brute-force sum over channels ---------- *
+ *     Y[d][t] = sum_{c} X[c][t + D[d][c]],   0 <= t < nout = nsamp - Dmax
+ * exact in int32 (requires 255 * nchan < 2^31).
+ *  d_in     uint8 [nchan][nsamp] (channel-major), base 16-byte aligned
+ *  nsamp    samples per channel (row pitch of d_in), > Dmax
+ *  d_plane  int32 [ndm][nout] output (row pitch nout)
+ *  d_stats  optional af_rowstats_t [ndm] output (may be NULL)
+ * Enqueued on `stream`. */
+int af_dedisperse(af_plan_t plan, const uint8_t* d_in, int64_t nsamp,
+                  int32_t* d_plane, af_rowstats_t* d_stats, void* stream);
+
+/* Row sums of a plane [ndm][nout] into d_stats [ndm] (see af_rowstats_t). */
+int af_rowstats(af_plan_t plan, const int32_t* d_plane, int64_t nout,
+                af_rowstats_t* d_stats, void* stream);
+
+/* ---- boxcar matched filter and S/N (step (iii), Sec. 1) ----------------- *
+ * For every row d and time t, over the widths w in `widths` whose window
+ * t .. t+w-1 fits in the row:
+ *     B_w = sum_{k=t}^{t+w-1} Y[d][k]
+ *     snr_w = (nout*B_w - w*S_d) / (nout * sigma_d * sqrt(w))
+ * with S_d = row sum and sigma_d the population standard deviation of the
+ * row (sigma_d = 0 gives snr 0).  Writes the largest snr_w (ties to the
+ * smaller width) and its index into `widths`; where no width fits,
+ * -INFINITY and AF_NO_WIDTH.
+ *  d_plane     int32 [ndm][nout]
+ *  d_stats     row sums from af_dedisperse/af_rowstats, or NULL: then the
+ *              library computes them into the plan's scratch first
+ *  widths      HOST array of nw strictly ascending widths, 1 <= w <= nout,
+ *              nw <= AF_MAX_WIDTHS, and w * 255 * nchan < 2^32
+ *  d_best_snr  float [ndm][nout] output
+ *  d_best_w    uint8 [ndm][nout] output (may be NULL)
+ * Uses the plan's scratch (per-row normalisation constants). */
+int af_boxcar_snr(af_plan_t plan, const int32_t* d_plane, int64_t nout,
+                  const af_rowstats_t* d_stats, const int32_t* widths, int nw,
+                  float* d_best_snr, uint8_t* d_best_w, void* stream);
+
+/* ---- thresholding and compaction into a candidate list (Sec. 2) -------- *
+ * (d,t) is a candidate iff best_snr[d][t] >= thresh and, with w the best
+ * width at (d,t), best_snr[d][t] > best_snr[d][u] for t-w <= u < t and
+ * best_snr[d][t] >= best_snr[d][u] for t < u <= t+w (a local maximum along
+ * time; ties go to the earliest t).  Candidates are appended to d_out in no
+ * particular order; *d_count receives the TOTAL number found (it may exceed
+ * cap; only cap records are written).  d_count is overwritten, not added to.
+ *  d_best_snr, d_best_w  outputs of af_boxcar_snr ([ndm][nout])
+ *  widths, nw            the same host width list
+ *  sample0               added to t to form abs_sample
+ *  d_out                 af_cand_t [cap] output; d_count int32 [1] output */
+int af_candidates(af_plan_t plan, const float* d_best_snr, const uint8_t* d_best_w,
+                  int64_t nout, const int32_t* widths, int nw, float thresh,
+                  int64_t sample0, af_cand_t* d_out, int32_t cap, int32_t* d_count,
+                  void* stream);
+
+/* ---- host-side clustering (true-positive rule of Sec. 4.2) -------------- *
+ * Sorts h_cands (in place) by (dm_idx, t), then keeps candidates greedily in
+ * order of (snr desc, dm_idx asc, t asc), dropping any within
+ * |dDM| < dm_tol AND |dTOA| < toa_tol (seconds) of one already kept.  DM
+ * values come from the plan's DM list and TOA = abs_sample * tsamp.  Writes
+ * the kept candidates to h_out (capacity n) in keep order and their number
+ * to *n_out. */
+int af_cluster(af_plan_t plan, af_cand_t* h_cands, int32_t n, double dm_tol,
+               double toa_tol, af_cand_t* h_out, int32_t* n_out);
+
+/* ---- whole search from HOST buffers ------------------------------------- *
+ * Copies h_in (uint8 [nchan][nsamp], ideally pinned) to the device, runs
+ * af_dedisperse -> af_boxcar_snr -> af_candidates on `stream` in the plan's
+ * reserved workspace, copies the candidates back, sorts them by (dm_idx, t)
+ * and returns after the stream has been synchronised.  *h_count = total
+ * found; AF_EOVERFLOW (with the first cap candidates in h_out) if it exceeds
+ * cap.  Requires af_search_reserve(plan, >= nsamp, >= cap) first (AF_ENOBUFS
+ * otherwise). */
+int af_search_reserve(af_plan_t plan, int64_t max_nsamp, int32_t cap);
+int af_search(af_plan_t plan, const uint8_t* h_in, int64_t nsamp,
+              const int32_t* widths, int nw, float thresh,
+              af_cand_t* h_out, int32_t cap, int32_t* h_count, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AFGB_H */

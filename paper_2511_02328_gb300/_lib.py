@@ -1,0 +1,187 @@
+"""ctypes binding of libafgb.so (include/afgb.h), argument marshalling only.
+
+Every function here has the name of the C entry point it wraps, takes plain
+integers (device pointers as ints, e.g. tensor.data_ptr()) or numpy arrays
+for host buffers, raises AFError on a non-zero status and returns the
+outputs.  No computation happens in Python.  Importing this module on a
+machine without the built library raises at once: there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libafgb.so")
+
+AF_OK, AF_EINVAL, AF_ENOMEM, AF_ENOBUFS, AF_ECUDA, AF_ETIMEOUT, AF_EOVERFLOW, AF_EAGAIN = range(8)
+AF_MAX_WIDTHS = 32
+AF_NO_WIDTH = 0xFF
+_NAMES = {0: "AF_OK", 1: "AF_EINVAL", 2: "AF_ENOMEM", 3: "AF_ENOBUFS", 4: "AF_ECUDA", 5: "AF_ETIMEOUT",
+          6: "AF_EOVERFLOW", 7: "AF_EAGAIN"}
+
+
+class AFError(RuntimeError):
+    def __init__(self, code, fn, msg):
+        super().__init__("%s failed: %s: %s" % (fn, _NAMES.get(code, code), msg))
+        self.code = code
+
+
+class RowStats(ctypes.Structure):
+    _fields_ = [("sum", ctypes.c_int64), ("sumsq", ctypes.c_int64)]
+
+
+class Cand(ctypes.Structure):
+    _fields_ = [("dm_idx", ctypes.c_int32), ("t", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("snr", ctypes.c_float), ("abs_sample", ctypes.c_int64)]
+
+
+CAND_DTYPE = np.dtype([("dm_idx", np.int32), ("t", np.int32), ("width", np.int32), ("snr", np.float32),
+                       ("abs_sample", np.int64)])
+assert CAND_DTYPE.itemsize == ctypes.sizeof(Cand) == 24
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+_F = ctypes.c_float
+
+# name -> argtypes (all return int unless listed in _RESTYPE)
+SIGNATURES = {
+    "af_last_error": [],
+    "af_version": [],
+    "af_plan": [_P, _I, _D, _D, _D, _P, _I],
+    "af_plan_destroy": [_P],
+    "af_plan_delays": [_P, _P, _P],
+    "af_plan_info": [_P, _P, _P, _P, _P],
+    "af_plan_nout": [_P, _I64, _P],
+    "af_dedisperse": [_P, _P, _I64, _P, _P, _P],
+    "af_rowstats": [_P, _P, _I64, _P, _P],
+    "af_boxcar_snr": [_P, _P, _I64, _P, _P, _I, _P, _P, _P],
+    "af_candidates": [_P, _P, _P, _I64, _P, _I, _F, _I64, _P, _I32, _P, _P],
+    "af_cluster": [_P, _P, _I32, _D, _D, _P, _P],
+    "af_search_reserve": [_P, _I64, _I32],
+    "af_search": [_P, _P, _I64, _P, _I, _F, _P, _I32, _P, _P],
+}
+_RESTYPE = {"af_last_error": ctypes.c_char_p, "af_version": ctypes.c_char_p}
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libafgb.so is not built: run paper_2511_02328_gb300.build.build() "
+                              "(or __graft_entry__.build()) first")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = _RESTYPE.get(name, ctypes.c_int)
+        _lib = L
+    return _lib
+
+
+def _check(rc, fn, allow=()):
+    if rc != AF_OK and rc not in allow:
+        raise AFError(rc, fn, lib().af_last_error().decode())
+    return rc
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(_P)
+
+
+def af_last_error():
+    return lib().af_last_error().decode()
+
+
+def af_version():
+    return lib().af_version().decode()
+
+
+def af_plan(nchan, f_lo, f_hi, tsamp, dm_list):
+    dms, pd = _host(dm_list, np.float64)
+    h = _P()
+    _check(lib().af_plan(ctypes.byref(h), int(nchan), float(f_lo), float(f_hi), float(tsamp), pd, int(dms.size)),
+           "af_plan")
+    return h.value
+
+
+def af_plan_destroy(plan):
+    _check(lib().af_plan_destroy(plan), "af_plan_destroy")
+
+
+def af_plan_info(plan):
+    nchan, ndm, dmax, tsamp = _I(), _I(), _I32(), _D()
+    _check(lib().af_plan_info(plan, ctypes.byref(nchan), ctypes.byref(ndm), ctypes.byref(dmax),
+                              ctypes.byref(tsamp)), "af_plan_info")
+    return nchan.value, ndm.value, dmax.value, tsamp.value
+
+
+def af_plan_delays(plan):
+    nchan, ndm, _, _ = af_plan_info(plan)
+    out = np.empty((ndm, nchan), dtype=np.int32)
+    dmax = _I32()
+    _check(lib().af_plan_delays(plan, out.ctypes.data_as(_P), ctypes.byref(dmax)), "af_plan_delays")
+    return out, dmax.value
+
+
+def af_plan_nout(plan, nsamp):
+    n = _I64()
+    _check(lib().af_plan_nout(plan, int(nsamp), ctypes.byref(n)), "af_plan_nout")
+    return n.value
+
+
+def af_dedisperse(plan, d_in, nsamp, d_plane, d_stats=0, stream=0):
+    _check(lib().af_dedisperse(plan, d_in, int(nsamp), d_plane, d_stats or None, stream or None), "af_dedisperse")
+
+
+def af_rowstats(plan, d_plane, nout, d_stats, stream=0):
+    _check(lib().af_rowstats(plan, d_plane, int(nout), d_stats, stream or None), "af_rowstats")
+
+
+def af_boxcar_snr(plan, d_plane, nout, d_stats, widths, d_best_snr, d_best_w=0, stream=0):
+    w, pw = _host(widths, np.int32)
+    _check(lib().af_boxcar_snr(plan, d_plane, int(nout), d_stats or None, pw, int(w.size), d_best_snr,
+                               d_best_w or None, stream or None), "af_boxcar_snr")
+
+
+def af_candidates(plan, d_best_snr, d_best_w, nout, widths, thresh, sample0, d_out, cap, d_count, stream=0):
+    w, pw = _host(widths, np.int32)
+    _check(lib().af_candidates(plan, d_best_snr, d_best_w, int(nout), pw, int(w.size), float(thresh),
+                               int(sample0), d_out or None, int(cap), d_count, stream or None), "af_candidates")
+
+
+def af_cluster(plan, cands, dm_tol=20.0, toa_tol=0.2):
+    """cands: numpy array of CAND_DTYPE (sorted in place by (dm_idx, t))."""
+    c = np.ascontiguousarray(cands, dtype=CAND_DTYPE)
+    out = np.empty_like(c)
+    n = _I32()
+    _check(lib().af_cluster(plan, c.ctypes.data_as(_P), int(c.size), float(dm_tol), float(toa_tol),
+                            out.ctypes.data_as(_P), ctypes.byref(n)), "af_cluster")
+    return out[: n.value]
+
+
+def af_search_reserve(plan, max_nsamp, cap):
+    _check(lib().af_search_reserve(plan, int(max_nsamp), int(cap)), "af_search_reserve")
+
+
+def af_search(plan, h_in, nsamp, widths, thresh, cap, stream=0, out=None):
+    """h_in: host pointer (int) or a C-contiguous uint8 numpy array [nchan][nsamp].
+    Returns (candidates sorted by (dm_idx, t), total count)."""
+    w, pw = _host(widths, np.int32)
+    if isinstance(h_in, np.ndarray):
+        keep = np.ascontiguousarray(h_in, dtype=np.uint8)
+        ptr = keep.ctypes.data
+    else:
+        ptr = int(h_in)
+    if out is None:
+        out = np.empty(max(int(cap), 1), dtype=CAND_DTYPE)
+    n = _I32()
+    _check(lib().af_search(plan, ptr, int(nsamp), pw, int(w.size), float(thresh), out.ctypes.data_as(_P),
+                           int(cap), ctypes.byref(n), stream or None), "af_search", allow=(AF_EOVERFLOW,))
+    return out[: min(n.value, int(cap))], n.value

@@ -1,0 +1,84 @@
+// internal.h -- shared declarations of the afgb library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "afgb.h"
+
+// ---------------------------------------------------------------- errors
+int af_set_error(int code, const char* fmt, ...);
+int af_cuda_check(cudaError_t e, const char* what);
+#define AF_CUDA(call)                                                  \
+    do {                                                               \
+        cudaError_t _e = (call);                                       \
+        if (_e != cudaSuccess) return af_cuda_check(_e, #call);        \
+    } while (0)
+
+// ---------------------------------------------------------------- widths
+// Boxcar widths passed to kernels by value.
+struct af_widths_t {
+    int32_t w[AF_MAX_WIDTHS];
+    int32_t n;
+};
+
+// Per-row, per-width S/N constants:  snr = float(B - q) * k - c  with
+// q = floor(w*S/nout), k = 1/(sigma*sqrt(w)), c = ((w*S - q*nout)/nout) * k.
+struct af_rowconst_t {
+    int64_t q;
+    float k;
+    float c;
+};
+
+// ---------------------------------------------------------------- plan
+struct af_plan_s {
+    int nchan = 0;
+    int ndm = 0;
+    double f_lo = 0, f_hi = 0, tsamp = 0;
+    int32_t dmax = 0;
+    int device = 0;
+    std::vector<double> dms;
+    std::vector<int32_t> delays;           // [ndm][nchan]
+    int num_sms = 0;
+
+    // device copies and scratch (owned)
+    int32_t* d_delays = nullptr;           // [ndm][nchan]
+    int32_t* d_delays_cm = nullptr;        // [nchan][ndm_pad] channel-major copy
+    int ndm_pad = 0;
+    int32_t* d_dmin_blk = nullptr;         // per (dm block, channel) minimum delay
+    int32_t* d_dspan_blk = nullptr;        // per dm block: max over channels of (max-min) delay
+    int dm_block = 0;                      // DM block size the two tables above use
+    int n_dm_blocks = 0;
+    af_rowstats_t* d_stats = nullptr;      // [ndm] scratch
+    af_rowconst_t* d_rowconst = nullptr;   // [ndm][AF_MAX_WIDTHS] scratch
+
+    // reserved workspace of af_search
+    int64_t ws_nsamp = 0;
+    int32_t ws_cap = 0;
+    uint8_t* ws_in = nullptr;
+    int32_t* ws_plane = nullptr;
+    float* ws_snr = nullptr;
+    uint8_t* ws_bw = nullptr;
+    af_cand_t* ws_cands = nullptr;
+    int32_t* ws_count = nullptr;
+};
+
+int af_check_plan(af_plan_t p);
+int af_check_widths(af_plan_t p, const int32_t* widths, int nw, int64_t nout, af_widths_t* out);
+
+// ---------------------------------------------------------------- launchers
+// All launchers enqueue on `s` and return AF_OK or AF_ECUDA (launch error).
+int af_launch_dedisperse(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout,
+                         int32_t* d_plane, cudaStream_t s);
+int af_launch_rowstats(const int32_t* d_plane, int ndm, int64_t nout, af_rowstats_t* d_stats,
+                       cudaStream_t s);
+int af_launch_boxcar(const int32_t* d_plane, int ndm, int64_t nout, const af_rowstats_t* d_stats,
+                     const af_widths_t& w, af_rowconst_t* d_rowconst, float* d_best_snr,
+                     uint8_t* d_best_w, cudaStream_t s);
+int af_launch_candidates(const float* d_best_snr, const uint8_t* d_best_w, int ndm, int64_t nout,
+                         const af_widths_t& w, float thresh, int64_t sample0, af_cand_t* d_out,
+                         int32_t cap, int32_t* d_count, cudaStream_t s);
+int af_prepare_dedisp_tables(af_plan_t p);

@@ -1,0 +1,379 @@
+// plan.cpp -- host side of the afgb C ABI: errors, the delay-table plan
+// (Eq. coarse_delay, Sec. 2.3), argument checking, candidate clustering
+// (Sec. 4.2) and the host-buffer search.
+//
+// Compiled with -ffp-contract=off so that the delay arithmetic is the plain
+// IEEE double sequence stated in afgb.h on every host (x86_64 and aarch64).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+static thread_local std::string g_last_error;
+
+int af_set_error(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int af_cuda_check(cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return AF_OK;
+    return af_set_error(e == cudaErrorMemoryAllocation ? AF_ENOMEM : AF_ECUDA, "%s: %s (%s)", what,
+                        cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+extern "C" const char* af_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* af_version(void) { return "afgb 0.1 (sm_103a)"; }
+
+int af_check_plan(af_plan_t p)
+{
+    if (!p) return af_set_error(AF_EINVAL, "null plan");
+    return AF_OK;
+}
+
+// Dispersion constant, Eq. (KDM): seconds when frequencies are in MHz.
+static const double kKDM = 4.148808e3;
+
+static void free_search_ws(af_plan_t p)
+{
+    cudaFree(p->ws_in);
+    cudaFree(p->ws_plane);
+    cudaFree(p->ws_snr);
+    cudaFree(p->ws_bw);
+    cudaFree(p->ws_cands);
+    cudaFree(p->ws_count);
+    p->ws_in = nullptr;
+    p->ws_plane = nullptr;
+    p->ws_snr = nullptr;
+    p->ws_bw = nullptr;
+    p->ws_cands = nullptr;
+    p->ws_count = nullptr;
+    p->ws_nsamp = 0;
+    p->ws_cap = 0;
+}
+
+static void free_plan(af_plan_t p)
+{
+    if (!p) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != p->device) cudaSetDevice(p->device);
+    cudaFree(p->d_delays);
+    cudaFree(p->d_delays_cm);
+    cudaFree(p->d_dmin_blk);
+    cudaFree(p->d_dspan_blk);
+    cudaFree(p->d_stats);
+    cudaFree(p->d_rowconst);
+    free_search_ws(p);
+    if (cur != p->device) cudaSetDevice(cur);
+    delete p;
+}
+
+extern "C" int af_plan(af_plan_t* out, int nchan, double f_lo, double f_hi, double tsamp,
+                       const double* dm_list, int ndm)
+{
+    if (!out) return af_set_error(AF_EINVAL, "af_plan: out is NULL");
+    *out = nullptr;
+    if (nchan < 1 || nchan > 65536) return af_set_error(AF_EINVAL, "af_plan: nchan %d out of range", nchan);
+    if (ndm < 1 || ndm > (1 << 20)) return af_set_error(AF_EINVAL, "af_plan: ndm %d out of range", ndm);
+    if (!dm_list) return af_set_error(AF_EINVAL, "af_plan: dm_list is NULL");
+    if (!(f_lo > 0.0) || !(f_hi > 0.0) || f_lo == f_hi || !isfinite(f_lo) || !isfinite(f_hi))
+        return af_set_error(AF_EINVAL, "af_plan: bad band edges %g %g", f_lo, f_hi);
+    if (!(tsamp > 0.0) || !isfinite(tsamp)) return af_set_error(AF_EINVAL, "af_plan: bad tsamp %g", tsamp);
+    for (int d = 0; d < ndm; d++)
+        if (!(dm_list[d] >= 0.0) || !isfinite(dm_list[d]))
+            return af_set_error(AF_EINVAL, "af_plan: dm_list[%d] = %g is not a finite value >= 0", d, dm_list[d]);
+
+    af_plan_s* p = new (std::nothrow) af_plan_s();
+    if (!p) return af_set_error(AF_ENOMEM, "af_plan: host allocation failed");
+    p->nchan = nchan;
+    p->ndm = ndm;
+    p->f_lo = f_lo;
+    p->f_hi = f_hi;
+    p->tsamp = tsamp;
+    p->dms.assign(dm_list, dm_list + ndm);
+    try {
+        p->delays.resize((size_t)ndm * nchan);
+    } catch (...) {
+        delete p;
+        return af_set_error(AF_ENOMEM, "af_plan: host allocation of the delay table failed");
+    }
+
+    // Eq. (coarse_delay): D = round(K*DM/tsamp * (1/fc^2 - 1/fref^2)),
+    // channel centres, f_ref = top band edge, round half away from zero.
+    const double fr = f_lo > f_hi ? f_lo : f_hi;
+    const double df = (f_hi - f_lo) / (double)nchan;
+    std::vector<double> bterm(nchan);
+    for (int c = 0; c < nchan; c++) {
+        double fc = f_lo + ((double)c + 0.5) * df;
+        bterm[c] = 1.0 / (fc * fc) - 1.0 / (fr * fr);
+    }
+    int32_t dmax = 0;
+    for (int d = 0; d < ndm; d++) {
+        double a = (kKDM * dm_list[d]) / tsamp;
+        for (int c = 0; c < nchan; c++) {
+            double x = a * bterm[c];
+            if (!(x < 2147483647.0)) {
+                delete p;
+                return af_set_error(AF_EINVAL, "af_plan: delay of dm %g channel %d exceeds int32", dm_list[d], c);
+            }
+            int32_t D = (int32_t)llround(x);
+            p->delays[(size_t)d * nchan + c] = D;
+            dmax = D > dmax ? D : dmax;
+        }
+    }
+    p->dmax = dmax;
+
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return af_cuda_check(e, "af_plan: cudaGetDevice");
+    }
+    cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    size_t tbytes = (size_t)ndm * nchan * sizeof(int32_t);
+    int rc = AF_OK;
+    if ((e = cudaMalloc(&p->d_delays, tbytes)) != cudaSuccess ||
+        (e = cudaMemcpy(p->d_delays, p->delays.data(), tbytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_stats, (size_t)ndm * sizeof(af_rowstats_t))) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_rowconst, (size_t)ndm * AF_MAX_WIDTHS * sizeof(af_rowconst_t))) != cudaSuccess) {
+        rc = af_cuda_check(e, "af_plan: device allocation/upload");
+    }
+    if (rc == AF_OK) rc = af_prepare_dedisp_tables(p);
+    if (rc != AF_OK) {
+        free_plan(p);
+        return rc;
+    }
+    *out = p;
+    return AF_OK;
+}
+
+extern "C" int af_plan_destroy(af_plan_t plan)
+{
+    free_plan(plan);
+    return AF_OK;
+}
+
+extern "C" int af_plan_delays(af_plan_t p, int32_t* host_out, int32_t* dmax)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    if (host_out) memcpy(host_out, p->delays.data(), p->delays.size() * sizeof(int32_t));
+    if (dmax) *dmax = p->dmax;
+    return AF_OK;
+}
+
+extern "C" int af_plan_info(af_plan_t p, int* nchan, int* ndm, int32_t* dmax, double* tsamp)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    if (nchan) *nchan = p->nchan;
+    if (ndm) *ndm = p->ndm;
+    if (dmax) *dmax = p->dmax;
+    if (tsamp) *tsamp = p->tsamp;
+    return AF_OK;
+}
+
+extern "C" int af_plan_nout(af_plan_t p, int64_t nsamp, int64_t* nout)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    if (!nout) return af_set_error(AF_EINVAL, "af_plan_nout: nout is NULL");
+    int64_t n = nsamp - (int64_t)p->dmax;
+    if (n <= 0)
+        return af_set_error(AF_EINVAL, "af_plan_nout: nsamp %lld <= Dmax %d", (long long)nsamp, p->dmax);
+    *nout = n;
+    return AF_OK;
+}
+
+int af_check_widths(af_plan_t p, const int32_t* widths, int nw, int64_t nout, af_widths_t* out)
+{
+    if (!widths) return af_set_error(AF_EINVAL, "widths is NULL");
+    if (nw < 1 || nw > AF_MAX_WIDTHS) return af_set_error(AF_EINVAL, "nw %d not in 1..%d", nw, AF_MAX_WIDTHS);
+    memset(out, 0, sizeof *out);
+    for (int i = 0; i < nw; i++) {
+        if (widths[i] < 1 || (i > 0 && widths[i] <= widths[i - 1]))
+            return af_set_error(AF_EINVAL, "widths must be strictly ascending and >= 1");
+        if ((int64_t)widths[i] > nout)
+            return af_set_error(AF_EINVAL, "width %d exceeds nout %lld", widths[i], (long long)nout);
+        if ((double)widths[i] * 255.0 * (double)p->nchan >= 4294967296.0)
+            return af_set_error(AF_EINVAL, "width %d too large for exact 32-bit window sums", widths[i]);
+        if (widths[i] > 8192) return af_set_error(AF_EINVAL, "width %d > 8192 not supported", widths[i]);
+        out->w[i] = widths[i];
+    }
+    out->n = nw;
+    return AF_OK;
+}
+
+static int check_nout(af_plan_t p, int64_t nsamp, int64_t* nout)
+{
+    int64_t n = nsamp - (int64_t)p->dmax;
+    if (n <= 0)
+        return af_set_error(AF_EINVAL, "nsamp %lld must exceed Dmax %d", (long long)nsamp, p->dmax);
+    if (n > INT32_MAX) return af_set_error(AF_EINVAL, "nout %lld too large", (long long)n);
+    *nout = n;
+    return AF_OK;
+}
+
+extern "C" int af_dedisperse(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int32_t* d_plane,
+                             af_rowstats_t* d_stats, void* stream)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    if (!d_in || !d_plane) return af_set_error(AF_EINVAL, "af_dedisperse: NULL buffer");
+    if (((uintptr_t)d_in & 15) != 0) return af_set_error(AF_EINVAL, "af_dedisperse: d_in not 16-byte aligned");
+    if (255.0 * p->nchan >= 2147483648.0) return af_set_error(AF_EINVAL, "af_dedisperse: too many channels");
+    int64_t nout;
+    if (int rc = check_nout(p, nsamp, &nout)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (int rc = af_launch_dedisperse(p, d_in, nsamp, nout, d_plane, s)) return rc;
+    if (d_stats)
+        if (int rc = af_launch_rowstats(d_plane, p->ndm, nout, d_stats, s)) return rc;
+    return AF_OK;
+}
+
+extern "C" int af_rowstats(af_plan_t p, const int32_t* d_plane, int64_t nout, af_rowstats_t* d_stats,
+                           void* stream)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    if (!d_plane || !d_stats) return af_set_error(AF_EINVAL, "af_rowstats: NULL buffer");
+    if (nout < 1 || nout > INT32_MAX) return af_set_error(AF_EINVAL, "af_rowstats: bad nout");
+    return af_launch_rowstats(d_plane, p->ndm, nout, d_stats, (cudaStream_t)stream);
+}
+
+extern "C" int af_boxcar_snr(af_plan_t p, const int32_t* d_plane, int64_t nout, const af_rowstats_t* d_stats,
+                             const int32_t* widths, int nw, float* d_best_snr, uint8_t* d_best_w, void* stream)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    if (!d_plane || !d_best_snr) return af_set_error(AF_EINVAL, "af_boxcar_snr: NULL buffer");
+    if (nout < 1 || nout > INT32_MAX) return af_set_error(AF_EINVAL, "af_boxcar_snr: bad nout");
+    af_widths_t w;
+    if (int rc = af_check_widths(p, widths, nw, nout, &w)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!d_stats) {
+        if (int rc = af_launch_rowstats(d_plane, p->ndm, nout, p->d_stats, s)) return rc;
+        d_stats = p->d_stats;
+    }
+    return af_launch_boxcar(d_plane, p->ndm, nout, d_stats, w, p->d_rowconst, d_best_snr, d_best_w, s);
+}
+
+extern "C" int af_candidates(af_plan_t p, const float* d_best_snr, const uint8_t* d_best_w, int64_t nout,
+                             const int32_t* widths, int nw, float thresh, int64_t sample0, af_cand_t* d_out,
+                             int32_t cap, int32_t* d_count, void* stream)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    if (!d_best_snr || !d_best_w || !d_count || (cap > 0 && !d_out))
+        return af_set_error(AF_EINVAL, "af_candidates: NULL buffer");
+    if (cap < 0) return af_set_error(AF_EINVAL, "af_candidates: negative cap");
+    if (nout < 1 || nout > INT32_MAX) return af_set_error(AF_EINVAL, "af_candidates: bad nout");
+    if (!isfinite(thresh)) return af_set_error(AF_EINVAL, "af_candidates: threshold not finite");
+    af_widths_t w;
+    if (int rc = af_check_widths(p, widths, nw, nout, &w)) return rc;
+    return af_launch_candidates(d_best_snr, d_best_w, p->ndm, nout, w, thresh, sample0, d_out, cap, d_count,
+                                (cudaStream_t)stream);
+}
+
+static bool cand_less_dt(const af_cand_t& a, const af_cand_t& b)
+{
+    if (a.dm_idx != b.dm_idx) return a.dm_idx < b.dm_idx;
+    if (a.abs_sample != b.abs_sample) return a.abs_sample < b.abs_sample;
+    return a.width < b.width;
+}
+
+extern "C" int af_cluster(af_plan_t p, af_cand_t* h_cands, int32_t n, double dm_tol, double toa_tol,
+                          af_cand_t* h_out, int32_t* n_out)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    if (n < 0 || (n > 0 && (!h_cands || !h_out)) || !n_out) return af_set_error(AF_EINVAL, "af_cluster: bad args");
+    for (int32_t i = 0; i < n; i++)
+        if (h_cands[i].dm_idx < 0 || h_cands[i].dm_idx >= p->ndm)
+            return af_set_error(AF_EINVAL, "af_cluster: dm_idx out of range");
+    std::sort(h_cands, h_cands + n, cand_less_dt);
+    std::vector<int32_t> order(n);
+    for (int32_t i = 0; i < n; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        if (h_cands[a].snr != h_cands[b].snr) return h_cands[a].snr > h_cands[b].snr;
+        return cand_less_dt(h_cands[a], h_cands[b]);
+    });
+    int32_t k = 0;
+    for (int32_t i = 0; i < n; i++) {
+        const af_cand_t& c = h_cands[order[i]];
+        double dm = p->dms[c.dm_idx], toa = (double)c.abs_sample * p->tsamp;
+        bool keep = true;
+        for (int32_t j = 0; j < k && keep; j++) {
+            if (fabs(p->dms[h_out[j].dm_idx] - dm) < dm_tol && fabs((double)h_out[j].abs_sample * p->tsamp - toa) < toa_tol)
+                keep = false;
+        }
+        if (keep) h_out[k++] = c;
+    }
+    *n_out = k;
+    return AF_OK;
+}
+
+extern "C" int af_search_reserve(af_plan_t p, int64_t max_nsamp, int32_t cap)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    int64_t nout;
+    if (int rc = check_nout(p, max_nsamp, &nout)) return rc;
+    if (cap < 1) return af_set_error(AF_EINVAL, "af_search_reserve: cap must be >= 1");
+    if (max_nsamp <= p->ws_nsamp && cap <= p->ws_cap) return AF_OK;
+    free_search_ws(p);
+    size_t nin = (size_t)p->nchan * (size_t)max_nsamp, npl = (size_t)p->ndm * (size_t)nout;
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->ws_in, nin)) != cudaSuccess || (e = cudaMalloc(&p->ws_plane, npl * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&p->ws_snr, npl * 4)) != cudaSuccess || (e = cudaMalloc(&p->ws_bw, npl)) != cudaSuccess ||
+        (e = cudaMalloc(&p->ws_cands, (size_t)cap * sizeof(af_cand_t))) != cudaSuccess ||
+        (e = cudaMalloc(&p->ws_count, 16)) != cudaSuccess) {
+        free_search_ws(p);
+        return af_cuda_check(e, "af_search_reserve");
+    }
+    p->ws_nsamp = max_nsamp;
+    p->ws_cap = cap;
+    return AF_OK;
+}
+
+extern "C" int af_search(af_plan_t p, const uint8_t* h_in, int64_t nsamp, const int32_t* widths, int nw,
+                         float thresh, af_cand_t* h_out, int32_t cap, int32_t* h_count, void* stream)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    if (!h_in || !h_count || (cap > 0 && !h_out)) return af_set_error(AF_EINVAL, "af_search: NULL buffer");
+    int64_t nout;
+    if (int rc = check_nout(p, nsamp, &nout)) return rc;
+    if (nsamp > p->ws_nsamp || cap > p->ws_cap)
+        return af_set_error(AF_ENOBUFS, "af_search: call af_search_reserve(nsamp >= %lld, cap >= %d) first",
+                            (long long)nsamp, cap);
+    af_widths_t w;
+    if (int rc = af_check_widths(p, widths, nw, nout, &w)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    AF_CUDA(cudaMemcpyAsync(p->ws_in, h_in, (size_t)p->nchan * nsamp, cudaMemcpyHostToDevice, s));
+    if (int rc = af_launch_dedisperse(p, p->ws_in, nsamp, nout, p->ws_plane, s)) return rc;
+    if (int rc = af_launch_rowstats(p->ws_plane, p->ndm, nout, p->d_stats, s)) return rc;
+    if (int rc = af_launch_boxcar(p->ws_plane, p->ndm, nout, p->d_stats, w, p->d_rowconst, p->ws_snr, p->ws_bw, s))
+        return rc;
+    if (int rc = af_launch_candidates(p->ws_snr, p->ws_bw, p->ndm, nout, w, thresh, 0, p->ws_cands, cap,
+                                      p->ws_count, s))
+        return rc;
+    int32_t total = 0;
+    AF_CUDA(cudaMemcpyAsync(&total, p->ws_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AF_CUDA(cudaStreamSynchronize(s));
+    int32_t ncopy = total < cap ? total : cap;
+    if (ncopy > 0) {
+        AF_CUDA(cudaMemcpyAsync(h_out, p->ws_cands, (size_t)ncopy * sizeof(af_cand_t), cudaMemcpyDeviceToHost, s));
+        AF_CUDA(cudaStreamSynchronize(s));
+        std::sort(h_out, h_out + ncopy, cand_less_dt);
+    }
+    *h_count = total;
+    if (total > cap) return af_set_error(AF_EOVERFLOW, "af_search: %d candidates, capacity %d", total, cap);
+    return AF_OK;
+}
