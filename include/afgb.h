@@ -50,6 +50,7 @@ extern "C" {
 
 #define AF_MAX_WIDTHS 32 /* maximum number of boxcar widths per call         */
 #define AF_NO_WIDTH 0xFF /* best-width index where no width fits (tail)      */
+#define AF_NOALLOC_MAX_ROWS 4096 /* row limit of af_boxcar_snr_noalloc       */
 
 typedef struct af_plan_s* af_plan_t;
 
@@ -151,6 +152,25 @@ int af_rowstats(af_plan_t plan, const int32_t* d_plane, int64_t nout,
 int af_boxcar_snr(af_plan_t plan, const int32_t* d_plane, int64_t nout,
                   const af_rowstats_t* d_stats, const int32_t* widths, int nw,
                   float* d_best_snr, uint8_t* d_best_w, void* stream);
+
+/* ---- boxcar S/N without any device allocation --------------------------- *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc (for example a real-time receiver thread, where an
+ * allocation would synchronise the device and stall the stream, or an
+ * application whose own memory pool already holds all device memory) and so
+ * cannot create a plan.  It computes exactly what af_boxcar_snr computes with
+ * d_stats = NULL, for a plane of ndm rows of nout samples summed over nchan
+ * 8-bit channels (nchan bounds the window sums: w * 255 * nchan < 2^32).
+ * Its scratch is a static device array inside the library, sized for
+ * ndm <= AF_NOALLOC_MAX_ROWS (about 2.1 MiB, held on every GPU that loads the
+ * library until the process exits); larger ndm returns AF_EINVAL.
+ * It allocates nothing.  The first call on each device looks up the array's
+ * address (make it before any stream capture).  All calls share the array:
+ * calls whose work overlaps on the GPU race and must be serialised.
+ * Arguments and outputs are as for af_boxcar_snr; widths is a host array. */
+int af_boxcar_snr_noalloc(const int32_t* d_plane, int ndm, int64_t nout, int nchan,
+                          const int32_t* widths, int nw, float* d_best_snr,
+                          uint8_t* d_best_w, void* stream);
 
 /* ---- thresholding and compaction into a candidate list (Sec. 2) -------- *
  * (d,t) is a candidate iff best_snr[d][t] >= thresh and, with w the best

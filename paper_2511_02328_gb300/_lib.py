@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libafgb.so")
 AF_OK, AF_EINVAL, AF_ENOMEM, AF_ENOBUFS, AF_ECUDA, AF_ETIMEOUT, AF_EOVERFLOW, AF_EAGAIN = range(8)
 AF_MAX_WIDTHS = 32
 AF_NO_WIDTH = 0xFF
+AF_NOALLOC_MAX_ROWS = 4096
 _NAMES = {0: "AF_OK", 1: "AF_EINVAL", 2: "AF_ENOMEM", 3: "AF_ENOBUFS", 4: "AF_ECUDA", 5: "AF_ETIMEOUT",
           6: "AF_EOVERFLOW", 7: "AF_EAGAIN"}
 
@@ -59,6 +60,7 @@ SIGNATURES = {
     "af_dedisperse": [_P, _P, _I64, _P, _P, _P],
     "af_rowstats": [_P, _P, _I64, _P, _P],
     "af_boxcar_snr": [_P, _P, _I64, _P, _P, _I, _P, _P, _P],
+    "af_boxcar_snr_noalloc": [_P, _I, _I64, _I, _P, _I, _P, _P, _P],
     "af_candidates": [_P, _P, _P, _I64, _P, _I, _F, _I64, _P, _I32, _P, _P],
     "af_cluster": [_P, _P, _I32, _D, _D, _P, _P],
     "af_search_reserve": [_P, _I64, _I32],
@@ -148,6 +150,12 @@ def af_boxcar_snr(plan, d_plane, nout, d_stats, widths, d_best_snr, d_best_w=0, 
     w, pw = _host(widths, np.int32)
     _check(lib().af_boxcar_snr(plan, d_plane, int(nout), d_stats or None, pw, int(w.size), d_best_snr,
                                d_best_w or None, stream or None), "af_boxcar_snr")
+
+
+def af_boxcar_snr_noalloc(d_plane, ndm, nout, nchan, widths, d_best_snr, d_best_w=0, stream=0):
+    w, pw = _host(widths, np.int32)
+    _check(lib().af_boxcar_snr_noalloc(d_plane, int(ndm), int(nout), int(nchan), pw, int(w.size), d_best_snr,
+                                       d_best_w or None, stream or None), "af_boxcar_snr_noalloc")
 
 
 def af_candidates(plan, d_best_snr, d_best_w, nout, widths, thresh, sample0, d_out, cap, d_count, stream=0):
