@@ -113,6 +113,12 @@ int af_plan_delays(af_plan_t plan, int32_t* host_out, int32_t* dmax);
 /* Plan dimensions (any output pointer may be NULL). */
 int af_plan_info(af_plan_t plan, int* nchan, int* ndm, int32_t* dmax, double* tsamp);
 
+/* Reads and clears the plan's device error flag, which a kernel of this plan
+ * sets when one of its bounded waits (for an asynchronous copy) ran out and it
+ * abandoned its work; returns AF_ETIMEOUT if the flag was set, else AF_OK.
+ * Blocks until all work on the device has finished. */
+int af_plan_check(af_plan_t plan);
+
 /* Output length for nsamp input samples: nout = nsamp - Dmax (reading of the
  * paper's truncation by the DM delay, Sec. 3).  AF_EINVAL if nout <= 0. */
 int af_plan_nout(af_plan_t plan, int64_t nsamp, int64_t* nout);

@@ -57,6 +57,7 @@ SIGNATURES = {
     "af_plan_delays": [_P, _P, _P],
     "af_plan_info": [_P, _P, _P, _P, _P],
     "af_plan_nout": [_P, _I64, _P],
+    "af_plan_check": [_P],
     "af_dedisperse": [_P, _P, _I64, _P, _P, _P],
     "af_rowstats": [_P, _P, _I64, _P, _P],
     "af_boxcar_snr": [_P, _P, _I64, _P, _P, _I, _P, _P, _P],
@@ -130,6 +131,10 @@ def af_plan_delays(plan):
     dmax = _I32()
     _check(lib().af_plan_delays(plan, out.ctypes.data_as(_P), ctypes.byref(dmax)), "af_plan_delays")
     return out, dmax.value
+
+
+def af_plan_check(plan):
+    _check(lib().af_plan_check(plan), "af_plan_check")
 
 
 def af_plan_nout(plan, nsamp):

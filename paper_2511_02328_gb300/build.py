@@ -41,8 +41,8 @@ def _up_to_date():
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def _compile(src, extra):
-    obj = os.path.join(OBJ, os.path.basename(src) + ".o")
+def _compile(src, extra, objdir=OBJ):
+    obj = os.path.join(objdir, os.path.basename(src) + ".o")
     cmd = [NVCC] + ARCH + COMMON + extra + ["-c", src, "-o", obj]
     if src.endswith(".cpp"):
         cmd = [NVCC] + COMMON + extra + ["-x", "c++", "-c", src, "-o", obj]
@@ -52,28 +52,31 @@ def _compile(src, extra):
     return obj, r.stderr
 
 
-def build(force=False, verbose=False, extra=()):
-    """Compile every CUDA/C++ source of the library and link libafgb.so."""
-    if not force and _up_to_date():
+def build(force=False, verbose=False, extra=(), out=None, objdir=None):
+    """Compile every CUDA/C++ source of the library and link libafgb.so
+    (or `out`, with objects in `objdir`, for a build with extra flags)."""
+    lib = out or LIB
+    objdir = objdir or OBJ
+    if not force and out is None and _up_to_date():
         return LIB
-    os.makedirs(OBJ, exist_ok=True)
+    os.makedirs(objdir, exist_ok=True)
     extra = list(extra)
     if verbose:
         extra += ["-Xptxas", "-v"]
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        res = list(ex.map(lambda s: _compile(s, extra), srcs))
+        res = list(ex.map(lambda s: _compile(s, extra, objdir), srcs))
     if verbose:
         for _, err in res:
             if err:
                 sys.stderr.write(err)
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = lib + ".%d.tmp" % os.getpid()
     cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in res]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed: %s\n%s\n%s" % (" ".join(cmd), r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -46,12 +46,17 @@ struct af_plan_s {
 
     // device copies and scratch (owned)
     int32_t* d_delays = nullptr;           // [ndm][nchan]
-    int32_t* d_delays_cm = nullptr;        // [nchan][ndm_pad] channel-major copy
+    // tile dedispersion kernel: DMs sorted ascending, padded to whole blocks
+    int32_t* d_dsort = nullptr;            // [ndm_pad][nchan] delays in sorted DM order
+    int32_t* d_perm = nullptr;             // [ndm_pad] plane row of each sorted DM (-1: padding)
+    int32_t* d_dmin_blk = nullptr;         // [n_dm_blocks][nchan] smallest delay per block and channel
+    int* d_err = nullptr;                  // device error flag (bounded waits that ran out)
     int ndm_pad = 0;
-    int32_t* d_dmin_blk = nullptr;         // per (dm block, channel) minimum delay
-    int32_t* d_dspan_blk = nullptr;        // per dm block: max over channels of (max-min) delay
-    int dm_block = 0;                      // DM block size the two tables above use
+    int dm_block = 0;                      // DM rows per block of the tile kernel
     int n_dm_blocks = 0;
+    int tile_rw = 0;                       // bytes per staged channel window
+    bool tile_ok = false;                  // the window fits in shared memory
+    bool force_simple = false;             // use the fallback kernel (AFGB_DEDISP_KERNEL=simple)
     af_rowstats_t* d_stats = nullptr;      // [ndm] scratch
     af_rowconst_t* d_rowconst = nullptr;   // [ndm][AF_MAX_WIDTHS] scratch
 
@@ -72,7 +77,7 @@ int af_check_widths(af_plan_t p, const int32_t* widths, int nw, int64_t nout, af
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `s` and return AF_OK or AF_ECUDA (launch error).
 int af_launch_dedisperse(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout,
-                         int32_t* d_plane, cudaStream_t s);
+                         int32_t* d_plane, af_rowstats_t* d_stats, cudaStream_t s);
 int af_launch_rowstats(const int32_t* d_plane, int ndm, int64_t nout, af_rowstats_t* d_stats,
                        cudaStream_t s);
 int af_launch_boxcar(const int32_t* d_plane, int ndm, int64_t nout, const af_rowstats_t* d_stats,

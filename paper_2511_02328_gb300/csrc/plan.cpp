@@ -8,6 +8,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -75,9 +76,10 @@ static void free_plan(af_plan_t p)
     cudaGetDevice(&cur);
     if (cur != p->device) cudaSetDevice(p->device);
     cudaFree(p->d_delays);
-    cudaFree(p->d_delays_cm);
+    cudaFree(p->d_dsort);
+    cudaFree(p->d_perm);
     cudaFree(p->d_dmin_blk);
-    cudaFree(p->d_dspan_blk);
+    cudaFree(p->d_err);
     cudaFree(p->d_stats);
     cudaFree(p->d_rowconst);
     free_search_ws(p);
@@ -146,6 +148,7 @@ extern "C" int af_plan(af_plan_t* out, int nchan, double f_lo, double f_hi, doub
         return af_cuda_check(e, "af_plan: cudaGetDevice");
     }
     cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (const char* k = getenv("AFGB_DEDISP_KERNEL")) p->force_simple = strcmp(k, "simple") == 0;
     size_t tbytes = (size_t)ndm * nchan * sizeof(int32_t);
     int rc = AF_OK;
     if ((e = cudaMalloc(&p->d_delays, tbytes)) != cudaSuccess ||
@@ -184,6 +187,19 @@ extern "C" int af_plan_info(af_plan_t p, int* nchan, int* ndm, int32_t* dmax, do
     if (ndm) *ndm = p->ndm;
     if (dmax) *dmax = p->dmax;
     if (tsamp) *tsamp = p->tsamp;
+    return AF_OK;
+}
+
+extern "C" int af_plan_check(af_plan_t p)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    int flag = 0;
+    AF_CUDA(cudaDeviceSynchronize());
+    AF_CUDA(cudaMemcpy(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        AF_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
+        return af_set_error(AF_ETIMEOUT, "a kernel's bounded wait for an asynchronous copy ran out");
+    }
     return AF_OK;
 }
 
@@ -237,10 +253,7 @@ extern "C" int af_dedisperse(af_plan_t p, const uint8_t* d_in, int64_t nsamp, in
     int64_t nout;
     if (int rc = check_nout(p, nsamp, &nout)) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    if (int rc = af_launch_dedisperse(p, d_in, nsamp, nout, d_plane, s)) return rc;
-    if (d_stats)
-        if (int rc = af_launch_rowstats(d_plane, p->ndm, nout, d_stats, s)) return rc;
-    return AF_OK;
+    return af_launch_dedisperse(p, d_in, nsamp, nout, d_plane, d_stats, s);
 }
 
 extern "C" int af_rowstats(af_plan_t p, const int32_t* d_plane, int64_t nout, af_rowstats_t* d_stats,
@@ -357,8 +370,7 @@ extern "C" int af_search(af_plan_t p, const uint8_t* h_in, int64_t nsamp, const 
     if (int rc = af_check_widths(p, widths, nw, nout, &w)) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     AF_CUDA(cudaMemcpyAsync(p->ws_in, h_in, (size_t)p->nchan * nsamp, cudaMemcpyHostToDevice, s));
-    if (int rc = af_launch_dedisperse(p, p->ws_in, nsamp, nout, p->ws_plane, s)) return rc;
-    if (int rc = af_launch_rowstats(p->ws_plane, p->ndm, nout, p->d_stats, s)) return rc;
+    if (int rc = af_launch_dedisperse(p, p->ws_in, nsamp, nout, p->ws_plane, p->d_stats, s)) return rc;
     if (int rc = af_launch_boxcar(p->ws_plane, p->ndm, nout, p->d_stats, w, p->d_rowconst, p->ws_snr, p->ws_bw, s))
         return rc;
     if (int rc = af_launch_candidates(p->ws_snr, p->ws_bw, p->ndm, nout, w, thresh, 0, p->ws_cands, cap,
@@ -367,6 +379,13 @@ extern "C" int af_search(af_plan_t p, const uint8_t* h_in, int64_t nsamp, const 
     int32_t total = 0;
     AF_CUDA(cudaMemcpyAsync(&total, p->ws_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     AF_CUDA(cudaStreamSynchronize(s));
+    int flag = 0;
+    AF_CUDA(cudaMemcpyAsync(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AF_CUDA(cudaStreamSynchronize(s));
+    if (flag) {
+        AF_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int), s));
+        return af_set_error(AF_ETIMEOUT, "af_search: a kernel's bounded wait for an asynchronous copy ran out");
+    }
     int32_t ncopy = total < cap ? total : cap;
     if (ncopy > 0) {
         AF_CUDA(cudaMemcpyAsync(h_out, p->ws_cands, (size_t)ncopy * sizeof(af_cand_t), cudaMemcpyDeviceToHost, s));

@@ -255,3 +255,48 @@ def test_c2_sampled_rows():
     ref_snr, ref_bw = oracle.boxcar_snr(Yr, cfg["widths"])
     _snr_close(snr[rows].cpu().numpy(), ref_snr)
     p.close()
+
+
+def test_fallback_kernel_for_wide_delay_spread():
+    """A DM grid so coarse that a block's delay spread does not fit the
+    shared-memory window runs on the fallback kernel; still bit-exact."""
+    from paper_2511_02328_gb300.search import Plan
+    nchan, tsamp = 64, 1e-4
+    dms = [0.0, 3000.0, 6000.0]
+    D = oracle.delay_table(nchan, 1000.0, 1500.0, tsamp, dms)
+    nsamp = int(D.max()) + 3000
+    x = np.random.default_rng(4).integers(0, 256, (nchan, nsamp), dtype=np.uint8)
+    p = Plan(nchan, 1000.0, 1500.0, tsamp, dms)
+    plane = p.dedisperse(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(plane.cpu().numpy(), oracle.dedisperse(x, D))
+    p.close()
+
+
+def test_simple_kernel_forced_matches(c1_data, monkeypatch):
+    """The fallback kernel selected explicitly gives the same plane."""
+    from paper_2511_02328_gb300.search import Plan
+    x, D, Y, _, _ = c1_data
+    monkeypatch.setenv("AFGB_DEDISP_KERNEL", "simple")
+    p = _plan(C1)
+    stats = torch.empty((p.ndm, 2), dtype=torch.int64, device="cuda")
+    plane = p.dedisperse(torch.from_numpy(x).cuda(), stats=stats)
+    torch.cuda.synchronize()
+    assert np.array_equal(plane.cpu().numpy(), Y)
+    S, Q = oracle.rowstats(Y)
+    assert np.array_equal(stats.cpu().numpy()[:, 0], S)
+    p.close()
+
+
+def test_repeated_calls_and_streams(c1_data):
+    """Same plan, two streams used one after the other, repeated calls: identical planes."""
+    x, D, Y, _, _ = c1_data
+    p = _plan(C1)
+    xd = torch.from_numpy(x).cuda()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    a = p.dedisperse(xd, stream=s1)
+    s1.synchronize()
+    b = p.dedisperse(xd, stream=s2)
+    s2.synchronize()
+    assert np.array_equal(a.cpu().numpy(), Y) and np.array_equal(b.cpu().numpy(), Y)
+    p.close()
