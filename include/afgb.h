@@ -217,6 +217,60 @@ int af_search(af_plan_t plan, const uint8_t* h_in, int64_t nsamp,
               const int32_t* widths, int nw, float thresh,
               af_cand_t* h_out, int32_t cap, int32_t* h_count, void* stream);
 
+/* ---- many beams in one persistent launch, replayed as a CUDA graph ------ *
+ * The paper runs several antenna streams on one GPU (Sec. 4.3); here each
+ * beam is an independent search (its own band, sampling, DM list, length,
+ * widths and threshold) and all beams' dedispersion runs as ONE persistent
+ * kernel that takes (beam, DM block, time tile) items from a work counter,
+ * followed by every beam's boxcar S/N and candidate compaction.  Results are
+ * identical to af_dedisperse / af_boxcar_snr / af_candidates on each beam
+ * alone. */
+typedef struct af_batch_s* af_batch_t;
+
+typedef struct {
+    int nchan;              /* channels of this beam                          */
+    double f_lo, f_hi;      /* band edges as for af_plan                      */
+    double tsamp;           /* sampling interval, s                           */
+    const double* dm_list;  /* host, ndm trial DMs (copied)                   */
+    int ndm;
+    const uint8_t* d_in;    /* DEVICE uint8 [nchan][nsamp], 16-byte aligned,
+                               caller-owned; read at every af_batch_run      */
+    int64_t nsamp;
+    const int32_t* widths;  /* host, nw strictly ascending widths (copied)    */
+    int nw;
+    float thresh;           /* S/N threshold of the candidate step            */
+    int32_t cap;            /* candidate capacity of this beam                */
+} af_beam_desc_t;
+
+/* Builds the batch: one plan per beam, each beam's plane / S/N / candidate
+ * buffers on the current device (AF_ENOBUFS if they need more than
+ * hbm_budget bytes; 0 = no budget), and picks the tile shape of the
+ * dedispersion kernel by timing every compiled shape on these beams (the
+ * beams' inputs must be valid device memory; their contents do not matter).
+ * With the environment variable AFGB_AUTOTUNE_CACHE naming a file, the
+ * choice is cached there as JSON keyed by GPU name and beam shapes. */
+int af_batch_build(af_batch_t* out, const af_beam_desc_t* beams, int nbeams, size_t hbm_budget);
+
+/* Enqueues the whole batch on `stream`: the first call captures a CUDA graph,
+ * later calls replay it (the beams' input pointers are fixed at build). */
+int af_batch_run(af_batch_t batch, void* stream);
+
+/* After the run's stream has been synchronised: copies up to cap of beam's
+ * candidates (sorted by dm_idx, t) to h_out and the total to *h_count;
+ * AF_EOVERFLOW if the total exceeds cap or the beam's capacity; AF_ETIMEOUT
+ * if a kernel's bounded wait ran out. */
+int af_batch_candidates(af_batch_t batch, int beam, af_cand_t* h_out, int32_t cap, int32_t* h_count);
+
+/* Device buffers of one beam (owned by the batch; any pointer may be NULL). */
+int af_batch_buffers(af_batch_t batch, int beam, int32_t** d_plane, float** d_snr, uint8_t** d_best_w,
+                     int64_t* nout);
+
+/* The tile shape chosen by the autotuner: DM rows per block, 128-output
+ * groups per lane, its measured time (ms, 0 if read from the cache). */
+int af_batch_shape(af_batch_t batch, int* nw, int* m, float* tuned_ms, int* from_cache);
+
+int af_batch_destroy(af_batch_t batch);
+
 #ifdef __cplusplus
 }
 #endif

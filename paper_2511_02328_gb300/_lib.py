@@ -66,6 +66,12 @@ SIGNATURES = {
     "af_cluster": [_P, _P, _I32, _D, _D, _P, _P],
     "af_search_reserve": [_P, _I64, _I32],
     "af_search": [_P, _P, _I64, _P, _I, _F, _P, _I32, _P, _P],
+    "af_batch_build": [_P, _P, _I, ctypes.c_size_t],
+    "af_batch_run": [_P, _P],
+    "af_batch_candidates": [_P, _I, _P, _I32, _P],
+    "af_batch_buffers": [_P, _I, _P, _P, _P, _P],
+    "af_batch_shape": [_P, _P, _P, _P, _P],
+    "af_batch_destroy": [_P],
 }
 _RESTYPE = {"af_last_error": ctypes.c_char_p, "af_version": ctypes.c_char_p}
 
@@ -198,3 +204,56 @@ def af_search(plan, h_in, nsamp, widths, thresh, cap, stream=0, out=None):
     _check(lib().af_search(plan, ptr, int(nsamp), pw, int(w.size), float(thresh), out.ctypes.data_as(_P),
                            int(cap), ctypes.byref(n), stream or None), "af_search", allow=(AF_EOVERFLOW,))
     return out[: min(n.value, int(cap))], n.value
+
+
+class BeamDesc(ctypes.Structure):
+    _fields_ = [("nchan", ctypes.c_int), ("f_lo", ctypes.c_double), ("f_hi", ctypes.c_double),
+                ("tsamp", ctypes.c_double), ("dm_list", ctypes.c_void_p), ("ndm", ctypes.c_int),
+                ("d_in", ctypes.c_void_p), ("nsamp", ctypes.c_int64), ("widths", ctypes.c_void_p),
+                ("nw", ctypes.c_int), ("thresh", ctypes.c_float), ("cap", ctypes.c_int32)]
+
+
+def af_batch_build(beams, hbm_budget=0):
+    """beams: list of dicts with keys nchan, f_lo, f_hi, tsamp, dm_list, d_in (device ptr),
+    nsamp, widths, thresh, cap.  Returns the batch handle."""
+    keep = []
+    arr = (BeamDesc * len(beams))()
+    for i, b in enumerate(beams):
+        dms, pd = _host(b["dm_list"], np.float64)
+        w, pw = _host(b["widths"], np.int32)
+        keep += [dms, w]
+        arr[i] = BeamDesc(int(b["nchan"]), float(b["f_lo"]), float(b["f_hi"]), float(b["tsamp"]), pd, int(dms.size),
+                          int(b["d_in"]), int(b["nsamp"]), pw, int(w.size), float(b["thresh"]), int(b["cap"]))
+    h = _P()
+    _check(lib().af_batch_build(ctypes.byref(h), arr, len(beams), int(hbm_budget)), "af_batch_build")
+    return h.value
+
+
+def af_batch_run(batch, stream=0):
+    _check(lib().af_batch_run(batch, stream or None), "af_batch_run")
+
+
+def af_batch_candidates(batch, beam, cap):
+    out = np.empty(max(int(cap), 1), dtype=CAND_DTYPE)
+    n = _I32()
+    _check(lib().af_batch_candidates(batch, int(beam), out.ctypes.data_as(_P), int(cap), ctypes.byref(n)),
+           "af_batch_candidates", allow=(AF_EOVERFLOW,))
+    return out[: min(n.value, int(cap))], n.value
+
+
+def af_batch_buffers(batch, beam):
+    pl, sn, bw, no = _P(), _P(), _P(), _I64()
+    _check(lib().af_batch_buffers(batch, int(beam), ctypes.byref(pl), ctypes.byref(sn), ctypes.byref(bw),
+                                  ctypes.byref(no)), "af_batch_buffers")
+    return pl.value, sn.value, bw.value, no.value
+
+
+def af_batch_shape(batch):
+    nw, m, ms, fc = _I(), _I(), _F(), _I()
+    _check(lib().af_batch_shape(batch, ctypes.byref(nw), ctypes.byref(m), ctypes.byref(ms), ctypes.byref(fc)),
+           "af_batch_shape")
+    return nw.value, m.value, ms.value, bool(fc.value)
+
+
+def af_batch_destroy(batch):
+    _check(lib().af_batch_destroy(batch), "af_batch_destroy")

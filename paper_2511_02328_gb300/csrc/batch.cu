@@ -1,0 +1,466 @@
+// batch.cu -- many beams of uneven shape in one persistent dedispersion
+// launch, replayed as a CUDA graph, with the block shape picked by timing.
+//
+// af_batch_build makes one plan per beam, allocates every beam's plane, S/N
+// and candidate buffers (within an HBM budget), then autotunes: for each
+// compiled tile shape (DM rows per block x outputs per lane) it builds the
+// beams' tile tables and times the persistent kernel on the batch itself;
+// the fastest shape is kept and cached in a JSON file (AFGB_AUTOTUNE_CACHE)
+// keyed by the GPU name and the beams' shapes.  af_batch_run replays a graph
+// of: counter and row-sum resets, the persistent dedispersion kernel over all
+// (beam, DM block, time tile) items, then per beam the boxcar S/N and the
+// candidate compaction.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "tile.cuh"
+
+namespace {
+
+typedef cudaError_t (*persistent_fn)(int grid, size_t smem, cudaStream_t s, const aftile::TileArgs* jobs,
+                                     const long long* first, int njobs, long long total, unsigned long long* counter);
+typedef cudaError_t (*attr_fn)(size_t smem);
+
+template <int NW, int M>
+cudaError_t launch_persistent(int grid, size_t smem, cudaStream_t s, const aftile::TileArgs* jobs,
+                              const long long* first, int njobs, long long total, unsigned long long* counter)
+{
+    aftile::k_tile_persistent<NW, M><<<grid, (NW + 1) * 32, smem, s>>>(jobs, first, njobs, total, counter);
+    return cudaGetLastError();
+}
+
+template <int NW, int M>
+cudaError_t set_attr(size_t smem)
+{
+    return cudaFuncSetAttribute(aftile::k_tile_persistent<NW, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+}
+
+struct Shape {
+    int nw, m;
+    persistent_fn launch;
+    attr_fn attr;
+};
+
+// Compiled block shapes the autotuner chooses from.
+const Shape kShapes[] = {
+    {11, 8, launch_persistent<11, 8>, set_attr<11, 8>},
+    {7, 8, launch_persistent<7, 8>, set_attr<7, 8>},
+    {15, 6, launch_persistent<15, 6>, set_attr<15, 6>},
+};
+constexpr int kNShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+struct Beam {
+    af_plan_t plan = nullptr;
+    const uint8_t* d_in = nullptr;
+    int64_t nsamp = 0, nout = 0;
+    af_widths_t widths;
+    float thresh = 0;
+    int32_t cap = 0;
+    int32_t* d_plane = nullptr;
+    af_rowstats_t* d_stats = nullptr;
+    float* d_snr = nullptr;
+    uint8_t* d_bw = nullptr;
+    af_cand_t* d_cands = nullptr;
+    int32_t* d_count = nullptr;
+    af_tile_tables tables;
+};
+
+}  // namespace
+
+struct af_batch_s {
+    int device = 0;
+    std::vector<Beam> beams;
+    std::vector<int> order;              // job order (largest channel count first)
+    int shape = 0;                       // index into kShapes
+    float tuned_ms = 0.0f;
+    bool from_cache = false;
+    aftile::TileArgs* d_jobs = nullptr;
+    long long* d_first = nullptr;
+    unsigned long long* d_counter = nullptr;
+    int* d_err = nullptr;
+    long long total = 0;
+    int grid = 0;
+    size_t smem = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+};
+
+static void free_batch(af_batch_t b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (Beam& x : b->beams) {
+        cudaFree(x.d_plane);
+        cudaFree(x.d_stats);
+        cudaFree(x.d_snr);
+        cudaFree(x.d_bw);
+        cudaFree(x.d_cands);
+        cudaFree(x.d_count);
+        af_tile_tables_free(&x.tables);
+        af_plan_destroy(x.plan);
+    }
+    cudaFree(b->d_jobs);
+    cudaFree(b->d_first);
+    cudaFree(b->d_counter);
+    cudaFree(b->d_err);
+    delete b;
+}
+
+// Builds the per-beam tile tables for shape si and uploads the job list.
+static int setup_shape(af_batch_t b, int si)
+{
+    const Shape& sh = kShapes[si];
+    int maxrw = 0;
+    for (Beam& x : b->beams) {
+        af_plan_t p = x.plan;
+        if (int rc = af_tile_tables_build(p->delays.data(), p->dms.data(), p->ndm, p->nchan, sh.nw, sh.m, b->device,
+                                          &x.tables))
+            return rc;
+        if (!x.tables.fits) return af_set_error(AF_EINVAL, "batch: a beam's delay spread does not fit shape %dx%d", sh.nw, sh.m);
+        maxrw = std::max(maxrw, x.tables.rw);
+    }
+    std::vector<aftile::TileArgs> jobs;
+    std::vector<long long> first(1, 0);
+    for (int k : b->order) {
+        const Beam& x = b->beams[k];
+        aftile::TileArgs a;
+        a.X = x.d_in;
+        a.nsamp = x.nsamp;
+        a.total = (int64_t)x.plan->nchan * x.nsamp;
+        a.nchan = x.plan->nchan;
+        a.nchunks = (x.plan->nchan + aftile::CC - 1) / aftile::CC;
+        a.dsort = x.tables.d_dsort;
+        a.perm = x.tables.d_perm;
+        a.dminblk = x.tables.d_dminblk;
+        a.nout = x.nout;
+        a.rw = x.tables.rw;
+        a.tiles = (unsigned)((x.nout + aftile::tte_of(sh.m) - 1) / aftile::tte_of(sh.m));
+        a.nblk = (unsigned)x.tables.nblk;
+        a.Y = x.d_plane;
+        a.stats = x.d_stats;
+        a.err = b->d_err;
+        jobs.push_back(a);
+        first.push_back(first.back() + (long long)a.tiles * a.nblk);
+    }
+    b->total = first.back();
+    b->smem = af_tile_smem(sh.nw, maxrw);
+    cudaFree(b->d_jobs);
+    cudaFree(b->d_first);
+    b->d_jobs = nullptr;
+    b->d_first = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&b->d_jobs, jobs.size() * sizeof(aftile::TileArgs))) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_jobs, jobs.data(), jobs.size() * sizeof(aftile::TileArgs), cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaMalloc(&b->d_first, first.size() * sizeof(long long))) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_first, first.data(), first.size() * sizeof(long long), cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = sh.attr(b->smem)) != cudaSuccess)
+        return af_cuda_check(e, "batch: job upload");
+    b->shape = si;
+    return AF_OK;
+}
+
+static int enqueue_dedisp(af_batch_t b, cudaStream_t s)
+{
+    const Shape& sh = kShapes[b->shape];
+    AF_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s));
+    for (Beam& x : b->beams)
+        AF_CUDA(cudaMemsetAsync(x.d_stats, 0, (size_t)x.plan->ndm * sizeof(af_rowstats_t), s));
+    AF_CUDA(sh.launch(b->grid, b->smem, s, b->d_jobs, b->d_first, (int)b->beams.size(), b->total, b->d_counter));
+    return AF_OK;
+}
+
+static int enqueue_all(af_batch_t b, cudaStream_t s)
+{
+    if (int rc = enqueue_dedisp(b, s)) return rc;
+    for (Beam& x : b->beams) {
+        if (int rc = af_launch_boxcar(x.d_plane, x.plan->ndm, x.nout, x.d_stats, x.widths, x.plan->d_rowconst,
+                                      x.d_snr, x.d_bw, s))
+            return rc;
+        if (int rc = af_launch_candidates(x.d_snr, x.d_bw, x.plan->ndm, x.nout, x.widths, x.thresh, 0, x.d_cands,
+                                          x.cap, x.d_count, s))
+            return rc;
+    }
+    return AF_OK;
+}
+
+// ---------------------------------------------------------------- autotune cache
+static std::string shape_sig(af_batch_t b)
+{
+    // channel count, DM list extent and sample count fix a beam's work shape
+    std::string k;
+    char buf[160];
+    for (const Beam& x : b->beams) {
+        const af_plan_s* p = x.plan;
+        snprintf(buf, sizeof buf, "|%d:%d:%lld:%d:%.6g:%.6g", p->nchan, p->ndm, (long long)x.nsamp, p->dmax,
+                 p->dms.front(), p->dms.back());
+        k += buf;
+    }
+    return k;
+}
+
+static bool cache_lookup(const std::string& path, const std::string& key, int* nw, int* m)
+{
+    FILE* f = fopen(path.c_str(), "r");
+    if (!f) return false;
+    std::string txt;
+    char buf[4096];
+    size_t n;
+    while ((n = fread(buf, 1, sizeof buf, f)) > 0) txt.append(buf, n);
+    fclose(f);
+    const std::string q = "\"" + key + "\"";
+    size_t pos = txt.find(q);
+    if (pos == std::string::npos) return false;
+    size_t a = txt.find("\"nw\":", pos), c = txt.find("\"m\":", pos);
+    if (a == std::string::npos || c == std::string::npos) return false;
+    *nw = atoi(txt.c_str() + a + 5);
+    *m = atoi(txt.c_str() + c + 4);
+    return true;
+}
+
+static void cache_store(const std::string& path, const std::string& key, int nw, int m, float ms)
+{
+    std::string txt;
+    if (FILE* f = fopen(path.c_str(), "r")) {
+        char buf[4096];
+        size_t n;
+        while ((n = fread(buf, 1, sizeof buf, f)) > 0) txt.append(buf, n);
+        fclose(f);
+    }
+    // keep the object's existing entries, append the new one
+    size_t end = txt.rfind('}');
+    char entry[256];
+    snprintf(entry, sizeof entry, "{\"nw\": %d, \"m\": %d, \"ms\": %.4f}", nw, m, ms);
+    std::string item = "\"" + key + "\": " + entry;
+    if (end == std::string::npos || txt.find('{') == std::string::npos) {
+        txt = "{\n  " + item + "\n}\n";
+    } else {
+        bool empty = txt.find('"') == std::string::npos;
+        txt = txt.substr(0, end) + (empty ? "  " : ",\n  ") + item + "\n}\n";
+    }
+    std::string tmp = path + ".tmp";
+    if (FILE* f = fopen(tmp.c_str(), "w")) {
+        fwrite(txt.data(), 1, txt.size(), f);
+        fclose(f);
+        rename(tmp.c_str(), path.c_str());
+    }
+}
+
+static int autotune(af_batch_t b)
+{
+    const char* path = getenv("AFGB_AUTOTUNE_CACHE");
+    const std::string key = [&] {
+        cudaDeviceProp prop;
+        cudaGetDeviceProperties(&prop, b->device);
+        return std::string(prop.name) + shape_sig(b);
+    }();
+    if (path) {
+        int nw = 0, m = 0;
+        if (cache_lookup(path, key, &nw, &m))
+            for (int si = 0; si < kNShapes; si++)
+                if (kShapes[si].nw == nw && kShapes[si].m == m) {
+                    if (int rc = setup_shape(b, si)) return rc;
+                    b->from_cache = true;
+                    return AF_OK;
+                }
+    }
+    cudaStream_t s;
+    AF_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = -1;
+    float best_ms = 0.0f;
+    int rc = AF_OK;
+    for (int si = 0; si < kNShapes && rc == AF_OK; si++) {
+        int r = setup_shape(b, si);
+        if (r == AF_EINVAL) continue;  // this shape's window does not fit: skip it
+        if (r) {
+            rc = r;
+            break;
+        }
+        float ms = 0.0f;
+        for (int rep = 0; rep < 3 && rc == AF_OK; rep++) {
+            cudaEventRecord(e0, s);
+            rc = enqueue_dedisp(b, s);
+            cudaEventRecord(e1, s);
+            cudaError_t ce = cudaStreamSynchronize(s);
+            if (ce != cudaSuccess) rc = af_cuda_check(ce, "autotune");
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) ms += t / 2.0f;  // first run warms up
+        }
+        if (rc == AF_OK && (best < 0 || ms < best_ms)) {
+            best = si;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    if (rc) return rc;
+    if (best < 0) return af_set_error(AF_EINVAL, "batch: no compiled tile shape fits these beams");
+    if (int r = setup_shape(b, best)) return r;
+    b->tuned_ms = best_ms;
+    if (path) cache_store(path, key, kShapes[best].nw, kShapes[best].m, best_ms);
+    return AF_OK;
+}
+
+extern "C" int af_batch_build(af_batch_t* out, const af_beam_desc_t* beams, int nbeams, size_t hbm_budget)
+{
+    if (!out || !beams || nbeams < 1 || nbeams > 4096) return af_set_error(AF_EINVAL, "af_batch_build: bad arguments");
+    *out = nullptr;
+    af_batch_s* b = new (std::nothrow) af_batch_s();
+    if (!b) return af_set_error(AF_ENOMEM, "af_batch_build: host allocation failed");
+    cudaGetDevice(&b->device);
+    b->beams.resize(nbeams);
+    size_t bytes = 0;
+    int rc = AF_OK;
+    for (int i = 0; i < nbeams && rc == AF_OK; i++) {
+        const af_beam_desc_t& d = beams[i];
+        Beam& x = b->beams[i];
+        if (!d.d_in || ((uintptr_t)d.d_in & 15)) {
+            rc = af_set_error(AF_EINVAL, "af_batch_build: beam %d input NULL or not 16-byte aligned", i);
+            break;
+        }
+        if ((rc = af_plan(&x.plan, d.nchan, d.f_lo, d.f_hi, d.tsamp, d.dm_list, d.ndm))) break;
+        x.d_in = d.d_in;
+        x.nsamp = d.nsamp;
+        if ((rc = af_plan_nout(x.plan, d.nsamp, &x.nout))) break;
+        if ((rc = af_check_widths(x.plan, d.widths, d.nw, x.nout, &x.widths))) break;
+        if (d.cap < 1 || !isfinite(d.thresh)) {
+            rc = af_set_error(AF_EINVAL, "af_batch_build: beam %d capacity or threshold", i);
+            break;
+        }
+        x.thresh = d.thresh;
+        x.cap = d.cap;
+        const size_t npl = (size_t)d.ndm * (size_t)x.nout;
+        bytes += npl * 9 + (size_t)d.ndm * sizeof(af_rowstats_t) + (size_t)d.cap * sizeof(af_cand_t) +
+                 (size_t)d.ndm * d.nchan * 8;
+        if (hbm_budget && bytes > hbm_budget) {
+            rc = af_set_error(AF_ENOBUFS, "af_batch_build: %zu bytes needed by %d beams exceed the budget of %zu",
+                              bytes, i + 1, hbm_budget);
+            break;
+        }
+        cudaError_t e;
+        if ((e = cudaMalloc(&x.d_plane, npl * 4)) != cudaSuccess || (e = cudaMalloc(&x.d_snr, npl * 4)) != cudaSuccess ||
+            (e = cudaMalloc(&x.d_bw, npl)) != cudaSuccess ||
+            (e = cudaMalloc(&x.d_stats, (size_t)d.ndm * sizeof(af_rowstats_t))) != cudaSuccess ||
+            (e = cudaMalloc(&x.d_cands, (size_t)d.cap * sizeof(af_cand_t))) != cudaSuccess ||
+            (e = cudaMalloc(&x.d_count, 16)) != cudaSuccess)
+            rc = af_cuda_check(e, "af_batch_build: beam buffers");
+    }
+    if (rc == AF_OK) {
+        cudaError_t e;
+        if ((e = cudaMalloc(&b->d_counter, sizeof(unsigned long long))) != cudaSuccess ||
+            (e = cudaMalloc(&b->d_err, sizeof(int))) != cudaSuccess || (e = cudaMemset(b->d_err, 0, sizeof(int))) != cudaSuccess)
+            rc = af_cuda_check(e, "af_batch_build: counters");
+    }
+    if (rc == AF_OK) {
+        b->order.resize(nbeams);
+        std::iota(b->order.begin(), b->order.end(), 0);
+        std::stable_sort(b->order.begin(), b->order.end(),
+                         [&](int p, int q) { return b->beams[p].plan->nchan > b->beams[q].plan->nchan; });
+        int nsm = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
+        b->grid = nsm;  // one resident block per SM (shared memory and registers allow one)
+        rc = autotune(b);
+    }
+    if (rc != AF_OK) {
+        free_batch(b);
+        return rc;
+    }
+    *out = b;
+    return AF_OK;
+}
+
+extern "C" int af_batch_run(af_batch_t b, void* stream)
+{
+    if (!b) return af_set_error(AF_EINVAL, "af_batch_run: NULL batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!b->exec) {
+        // capture once on a private stream, then replay on the caller's
+        cudaStream_t cs;
+        AF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        int rc = e == cudaSuccess ? enqueue_all(b, cs) : af_cuda_check(e, "af_batch_run: begin capture");
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        cudaStreamDestroy(cs);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e2 != cudaSuccess) return af_cuda_check(e2, "af_batch_run: end capture");
+        b->graph = g;
+        AF_CUDA(cudaGraphInstantiate(&b->exec, g, 0));
+    }
+    AF_CUDA(cudaGraphLaunch(b->exec, s));
+    return AF_OK;
+}
+
+extern "C" int af_batch_candidates(af_batch_t b, int beam, af_cand_t* h_out, int32_t cap, int32_t* h_count)
+{
+    if (!b || beam < 0 || beam >= (int)b->beams.size() || !h_count || (cap > 0 && !h_out))
+        return af_set_error(AF_EINVAL, "af_batch_candidates: bad arguments");
+    Beam& x = b->beams[beam];
+    int32_t total = 0;
+    AF_CUDA(cudaMemcpy(&total, x.d_count, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    int flag = 0;
+    AF_CUDA(cudaMemcpy(&flag, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        cudaMemset(b->d_err, 0, sizeof(int));
+        return af_set_error(AF_ETIMEOUT, "af_batch: a kernel's bounded wait for an asynchronous copy ran out");
+    }
+    int32_t n = std::min(std::min(total, cap), x.cap);
+    if (n > 0) {
+        AF_CUDA(cudaMemcpy(h_out, x.d_cands, (size_t)n * sizeof(af_cand_t), cudaMemcpyDeviceToHost));
+        std::sort(h_out, h_out + n, [](const af_cand_t& p, const af_cand_t& q) {
+            return p.dm_idx != q.dm_idx ? p.dm_idx < q.dm_idx : p.t < q.t;
+        });
+    }
+    *h_count = total;
+    if (total > std::min(cap, x.cap)) return af_set_error(AF_EOVERFLOW, "af_batch_candidates: %d found", total);
+    return AF_OK;
+}
+
+extern "C" int af_batch_buffers(af_batch_t b, int beam, int32_t** d_plane, float** d_snr, uint8_t** d_bw,
+                                int64_t* nout)
+{
+    if (!b || beam < 0 || beam >= (int)b->beams.size()) return af_set_error(AF_EINVAL, "af_batch_buffers: bad beam");
+    Beam& x = b->beams[beam];
+    if (d_plane) *d_plane = x.d_plane;
+    if (d_snr) *d_snr = x.d_snr;
+    if (d_bw) *d_bw = x.d_bw;
+    if (nout) *nout = x.nout;
+    return AF_OK;
+}
+
+extern "C" int af_batch_shape(af_batch_t b, int* nw, int* m, float* tuned_ms, int* from_cache)
+{
+    if (!b) return af_set_error(AF_EINVAL, "af_batch_shape: NULL batch");
+    if (nw) *nw = kShapes[b->shape].nw;
+    if (m) *m = kShapes[b->shape].m;
+    if (tuned_ms) *tuned_ms = b->tuned_ms;
+    if (from_cache) *from_cache = b->from_cache ? 1 : 0;
+    return AF_OK;
+}
+
+extern "C" int af_batch_destroy(af_batch_t b)
+{
+    free_batch(b);
+    return AF_OK;
+}

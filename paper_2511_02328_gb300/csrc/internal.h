@@ -33,6 +33,22 @@ struct af_rowconst_t {
     float c;
 };
 
+// ---------------------------------------------------------------- tile tables
+// Device tables of the tile dedispersion kernel for one delay table and block
+// shape (nw DM rows per block, m 128-output groups per lane).
+struct af_tile_tables {
+    int nw = 0, m = 0;
+    int32_t* d_dsort = nullptr;    // [ndm_pad][nchan] delays in ascending-DM order
+    int32_t* d_perm = nullptr;     // [ndm_pad] plane row of each sorted DM (-1: padding)
+    int32_t* d_dminblk = nullptr;  // [nblk][nchan] smallest delay per block and channel
+    int ndm_pad = 0, nblk = 0, spread = 0, rw = 0;
+    bool fits = false;             // the channel window fits in shared memory
+};
+int af_tile_tables_build(const int32_t* delays, const double* dms, int ndm, int nchan, int nw, int m, int device,
+                         af_tile_tables* t);
+void af_tile_tables_free(af_tile_tables* t);
+size_t af_tile_smem(int nw, int rw);
+
 // ---------------------------------------------------------------- plan
 struct af_plan_s {
     int nchan = 0;
@@ -46,16 +62,8 @@ struct af_plan_s {
 
     // device copies and scratch (owned)
     int32_t* d_delays = nullptr;           // [ndm][nchan]
-    // tile dedispersion kernel: DMs sorted ascending, padded to whole blocks
-    int32_t* d_dsort = nullptr;            // [ndm_pad][nchan] delays in sorted DM order
-    int32_t* d_perm = nullptr;             // [ndm_pad] plane row of each sorted DM (-1: padding)
-    int32_t* d_dmin_blk = nullptr;         // [n_dm_blocks][nchan] smallest delay per block and channel
+    af_tile_tables tile;                   // tables of the tile dedispersion kernel
     int* d_err = nullptr;                  // device error flag (bounded waits that ran out)
-    int ndm_pad = 0;
-    int dm_block = 0;                      // DM rows per block of the tile kernel
-    int n_dm_blocks = 0;
-    int tile_rw = 0;                       // bytes per staged channel window
-    bool tile_ok = false;                  // the window fits in shared memory
     bool force_simple = false;             // use the fallback kernel (AFGB_DEDISP_KERNEL=simple)
     af_rowstats_t* d_stats = nullptr;      // [ndm] scratch
     af_rowconst_t* d_rowconst = nullptr;   // [ndm][AF_MAX_WIDTHS] scratch

@@ -76,9 +76,7 @@ static void free_plan(af_plan_t p)
     cudaGetDevice(&cur);
     if (cur != p->device) cudaSetDevice(p->device);
     cudaFree(p->d_delays);
-    cudaFree(p->d_dsort);
-    cudaFree(p->d_perm);
-    cudaFree(p->d_dmin_blk);
+    af_tile_tables_free(&p->tile);
     cudaFree(p->d_err);
     cudaFree(p->d_stats);
     cudaFree(p->d_rowconst);

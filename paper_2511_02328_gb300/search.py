@@ -13,6 +13,18 @@ def _stream(stream):
     return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
 
 
+class _CudaArray:
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"data": (int(ptr), False), "shape": tuple(int(v) for v in shape),
+                                         "typestr": typestr, "version": 3, "strides": None}
+
+
+def device_view(ptr, shape, dtype):
+    """A torch tensor viewing library-owned device memory (no copy)."""
+    typestr = {torch.int32: "<i4", torch.float32: "<f4", torch.uint8: "|u1", torch.int64: "<i8"}[dtype]
+    return torch.as_tensor(_CudaArray(ptr, shape, typestr), device="cuda")
+
+
 class Plan:
     """Delay-table plan (Eq. coarse_delay, Sec. 2.3) on the current device."""
 
