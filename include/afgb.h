@@ -271,6 +271,91 @@ int af_batch_shape(af_batch_t batch, int* nw, int* m, float* tuned_ms, int* from
 
 int af_batch_destroy(af_batch_t batch);
 
+/* ---- streaming search with continuous batching --------------------------- *
+ * Every beam is a continuous stream, searched in windows of `window` samples
+ * that start every hop = window - Dmax samples: consecutive windows overlap
+ * by the largest delay, so their outputs (hop samples each) tile the stream
+ * exactly (the paper's time blocking with a halo of the maximum shift, Eq. L1
+ * of Sec. 2.3, applied across chunks).  The overlap of each beam stays on the
+ * device.  Requests are admitted into slots whose number the HBM budget sets;
+ * a dispatcher thread runs every admitted window together (one persistent
+ * dedispersion launch, then each window's S/N and candidates), so requests
+ * that arrive while others run join the next launch. */
+typedef struct af_stream_s* af_stream_t;
+
+typedef struct {
+    int nbeams;             /* independent streams                              */
+    int nchan;              /* all beams share band, sampling and DM list       */
+    double f_lo, f_hi, tsamp;
+    const double* dm_list;  /* host, copied */
+    int ndm;
+    int64_t window;         /* samples per searched window (> Dmax)             */
+    const int32_t* widths;  /* host, copied */
+    int nw;
+    float thresh;
+    int32_t cap;            /* candidates kept per window                       */
+    size_t hbm_budget;      /* bytes for slots + beam state; 0 = no limit       */
+    int max_slots;          /* upper bound on slots (0 = 4)                     */
+    int timeout_ms;         /* af_stream_push: longest wait for a free slot;
+                               0 = return AF_EAGAIN at once                     */
+} af_stream_cfg_t;
+
+typedef struct {
+    int beam;
+    int64_t seq;            /* chunk number of the beam (0, 1, 2, ...)          */
+    int64_t sample0;        /* stream sample of output t = 0 (= seq * hop)      */
+    int32_t slot;           /* pass to af_stream_release                        */
+    int32_t count;          /* candidates in `cands` (<= cap)                   */
+    int32_t total;          /* candidates found                                  */
+    const af_cand_t* cands; /* host, sorted by (dm_idx, t); valid until release */
+    double latency_ms;      /* push call -> candidates in host memory           */
+    int status;             /* AF_OK, AF_EOVERFLOW (total > cap), AF_ETIMEOUT   */
+} af_stream_result_t;
+
+typedef struct {
+    int64_t windows;        /* windows completed and polled                     */
+    int64_t launches;       /* persistent dedispersion launches                 */
+    int max_inflight;       /* most windows admitted at once                    */
+    int slots;
+    double p50_ms, p99_ms, max_ms;  /* chunk-to-candidate latency               */
+    double wall_s;          /* first push to last completion                    */
+    double work;            /* ndm * nchan * hop per window, summed             */
+    double rate;            /* work / wall_s                                    */
+} af_stream_stats_t;
+
+/* Opens the engine on the current device and starts its dispatcher thread.
+ * AF_ENOBUFS if the budget cannot hold one slot plus every beam's overlap. */
+int af_stream_open(af_stream_t* out, const af_stream_cfg_t* cfg);
+
+/* Submits the next chunk of a beam: h_data is host uint8 [nchan][nsamp]
+ * (pinned memory copies fastest), nsamp = window for the beam's first chunk
+ * (seq 0) and hop afterwards, seq = the beam's next chunk number (AF_EINVAL
+ * for a dropped, repeated or mis-sized chunk).  Waits up to timeout_ms for a
+ * free slot (AF_EAGAIN / AF_ETIMEOUT).  Returns once the data is on the
+ * device; the search itself runs asynchronously. */
+int af_stream_push(af_stream_t s, int beam, const uint8_t* h_data, int64_t nsamp, int64_t seq);
+
+/* Takes the next completed window (AF_EAGAIN if none within timeout_ms).
+ * The slot stays held, with its candidates and device buffers valid, until
+ * af_stream_release. */
+int af_stream_poll(af_stream_t s, af_stream_result_t* out, int timeout_ms);
+int af_stream_release(af_stream_t s, int32_t slot);
+
+/* Device plane [ndm][hop] and best S/N of a held slot. */
+int af_stream_result_plane(af_stream_t s, int32_t slot, int32_t** d_plane, float** d_snr, int64_t* nout);
+
+int af_stream_info(af_stream_t s, int64_t* hop, int64_t* dmax, int* nslots);
+int af_stream_stats(af_stream_t s, af_stream_stats_t* st);
+
+/* Per-beam state for checkpoint / resume: the overlap (uint8 [nchan][Dmax]),
+ * the next chunk number and the next window's first stream sample.  A beam
+ * restored into a fresh engine continues exactly as if it had never stopped. */
+int af_stream_snapshot(af_stream_t s, int beam, uint8_t* h_overlap, int64_t* next_seq, int64_t* next_sample);
+int af_stream_restore(af_stream_t s, int beam, const uint8_t* h_overlap, int64_t next_seq, int64_t next_sample);
+
+/* Waits for all work, stops the dispatcher and frees everything. */
+int af_stream_close(af_stream_t s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -72,6 +72,16 @@ SIGNATURES = {
     "af_batch_buffers": [_P, _I, _P, _P, _P, _P],
     "af_batch_shape": [_P, _P, _P, _P, _P],
     "af_batch_destroy": [_P],
+    "af_stream_open": [_P, _P],
+    "af_stream_push": [_P, _I, _P, _I64, _I64],
+    "af_stream_poll": [_P, _P, _I],
+    "af_stream_release": [_P, _I32],
+    "af_stream_result_plane": [_P, _I32, _P, _P, _P],
+    "af_stream_info": [_P, _P, _P, _P],
+    "af_stream_stats": [_P, _P],
+    "af_stream_snapshot": [_P, _I, _P, _P, _P],
+    "af_stream_restore": [_P, _I, _P, _I64, _I64],
+    "af_stream_close": [_P],
 }
 _RESTYPE = {"af_last_error": ctypes.c_char_p, "af_version": ctypes.c_char_p}
 
@@ -257,3 +267,96 @@ def af_batch_shape(batch):
 
 def af_batch_destroy(batch):
     _check(lib().af_batch_destroy(batch), "af_batch_destroy")
+
+
+class StreamCfg(ctypes.Structure):
+    _fields_ = [("nbeams", _I), ("nchan", _I), ("f_lo", _D), ("f_hi", _D), ("tsamp", _D), ("dm_list", _P),
+                ("ndm", _I), ("window", _I64), ("widths", _P), ("nw", _I), ("thresh", _F), ("cap", _I32),
+                ("hbm_budget", ctypes.c_size_t), ("max_slots", _I), ("timeout_ms", _I)]
+
+
+class StreamResult(ctypes.Structure):
+    _fields_ = [("beam", _I), ("seq", _I64), ("sample0", _I64), ("slot", _I32), ("count", _I32), ("total", _I32),
+                ("cands", _P), ("latency_ms", _D), ("status", _I)]
+
+
+class StreamStats(ctypes.Structure):
+    _fields_ = [("windows", _I64), ("launches", _I64), ("max_inflight", _I), ("slots", _I), ("p50_ms", _D),
+                ("p99_ms", _D), ("max_ms", _D), ("wall_s", _D), ("work", _D), ("rate", _D)]
+
+
+def af_stream_open(nbeams, nchan, f_lo, f_hi, tsamp, dm_list, window, widths, thresh, cap, hbm_budget=0,
+                   max_slots=0, timeout_ms=60000):
+    dms, pd = _host(dm_list, np.float64)
+    w, pw = _host(widths, np.int32)
+    cfg = StreamCfg(int(nbeams), int(nchan), float(f_lo), float(f_hi), float(tsamp), pd, int(dms.size), int(window),
+                    pw, int(w.size), float(thresh), int(cap), int(hbm_budget), int(max_slots), int(timeout_ms))
+    h = _P()
+    _check(lib().af_stream_open(ctypes.byref(h), ctypes.byref(cfg)), "af_stream_open")
+    return h.value
+
+
+def af_stream_push(stream, beam, h_data, seq):
+    """h_data: C-contiguous uint8 [nchan][nsamp] numpy array (or (ptr, nsamp))."""
+    if isinstance(h_data, np.ndarray):
+        a = np.ascontiguousarray(h_data, dtype=np.uint8)
+        ptr, nsamp = a.ctypes.data, a.shape[1]
+    else:
+        ptr, nsamp = h_data
+    return _check(lib().af_stream_push(stream, int(beam), ptr, int(nsamp), int(seq)), "af_stream_push")
+
+
+def af_stream_poll(stream, timeout_ms=60000):
+    """Returns a dict (beam, seq, sample0, slot, cands, total, latency_ms, status) or None."""
+    r = StreamResult()
+    rc = lib().af_stream_poll(stream, ctypes.byref(r), int(timeout_ms))
+    if rc == AF_EAGAIN:
+        return None
+    _check(rc, "af_stream_poll")
+    cands = np.empty(0, dtype=CAND_DTYPE)
+    if r.count > 0:
+        buf = (ctypes.c_char * (r.count * CAND_DTYPE.itemsize)).from_address(r.cands)
+        cands = np.frombuffer(buf, dtype=CAND_DTYPE).copy()
+    return dict(beam=r.beam, seq=r.seq, sample0=r.sample0, slot=r.slot, cands=cands, total=r.total,
+                latency_ms=r.latency_ms, status=r.status)
+
+
+def af_stream_release(stream, slot):
+    _check(lib().af_stream_release(stream, int(slot)), "af_stream_release")
+
+
+def af_stream_result_plane(stream, slot):
+    pl, sn, no = _P(), _P(), _I64()
+    _check(lib().af_stream_result_plane(stream, int(slot), ctypes.byref(pl), ctypes.byref(sn), ctypes.byref(no)),
+           "af_stream_result_plane")
+    return pl.value, sn.value, no.value
+
+
+def af_stream_info(stream):
+    hop, dmax, ns = _I64(), _I64(), _I()
+    _check(lib().af_stream_info(stream, ctypes.byref(hop), ctypes.byref(dmax), ctypes.byref(ns)), "af_stream_info")
+    return hop.value, dmax.value, ns.value
+
+
+def af_stream_stats(stream):
+    st = StreamStats()
+    _check(lib().af_stream_stats(stream, ctypes.byref(st)), "af_stream_stats")
+    return {k: getattr(st, k) for k, _ in StreamStats._fields_}
+
+
+def af_stream_snapshot(stream, beam, nchan, dmax):
+    ov = np.empty((nchan, max(dmax, 0)), dtype=np.uint8)
+    ns, nx = _I64(), _I64()
+    _check(lib().af_stream_snapshot(stream, int(beam), ov.ctypes.data_as(_P), ctypes.byref(ns), ctypes.byref(nx)),
+           "af_stream_snapshot")
+    return ov, ns.value, nx.value
+
+
+def af_stream_restore(stream, beam, overlap, next_seq, next_sample):
+    ov = np.ascontiguousarray(overlap, dtype=np.uint8)
+    _check(lib().af_stream_restore(stream, int(beam), ov.ctypes.data_as(_P), int(next_seq), int(next_sample)),
+           "af_stream_restore")
+
+
+def af_stream_close(stream):
+    _check(lib().af_stream_close(stream), "af_stream_close")
