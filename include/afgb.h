@@ -327,13 +327,15 @@ typedef struct {
  * AF_ENOBUFS if the budget cannot hold one slot plus every beam's overlap. */
 int af_stream_open(af_stream_t* out, const af_stream_cfg_t* cfg);
 
-/* Submits the next chunk of a beam: h_data is host uint8 [nchan][nsamp]
- * (pinned memory copies fastest), nsamp = window for the beam's first chunk
+/* Submits the next chunk of a beam: h_data is host uint8 [nchan] rows of
+ * nsamp samples, `pitch` bytes apart (0 = nsamp; pinned memory copies
+ * fastest), nsamp = window for the beam's first chunk
  * (seq 0) and hop afterwards, seq = the beam's next chunk number (AF_EINVAL
  * for a dropped, repeated or mis-sized chunk).  Waits up to timeout_ms for a
  * free slot (AF_EAGAIN / AF_ETIMEOUT).  Returns once the data is on the
  * device; the search itself runs asynchronously. */
-int af_stream_push(af_stream_t s, int beam, const uint8_t* h_data, int64_t nsamp, int64_t seq);
+int af_stream_push(af_stream_t s, int beam, const uint8_t* h_data, int64_t nsamp, int64_t pitch,
+                   int64_t seq);
 
 /* Takes the next completed window (AF_EAGAIN if none within timeout_ms).
  * The slot stays held, with its candidates and device buffers valid, until

@@ -73,7 +73,7 @@ SIGNATURES = {
     "af_batch_shape": [_P, _P, _P, _P, _P],
     "af_batch_destroy": [_P],
     "af_stream_open": [_P, _P],
-    "af_stream_push": [_P, _I, _P, _I64, _I64],
+    "af_stream_push": [_P, _I, _P, _I64, _I64, _I64],
     "af_stream_poll": [_P, _P, _I],
     "af_stream_release": [_P, _I32],
     "af_stream_result_plane": [_P, _I32, _P, _P, _P],
@@ -297,13 +297,17 @@ def af_stream_open(nbeams, nchan, f_lo, f_hi, tsamp, dm_list, window, widths, th
 
 
 def af_stream_push(stream, beam, h_data, seq):
-    """h_data: C-contiguous uint8 [nchan][nsamp] numpy array (or (ptr, nsamp))."""
+    """h_data: uint8 [nchan][nsamp] numpy array whose rows are contiguous (a
+    column slice of a larger C-contiguous array is passed with its pitch),
+    or a tuple (ptr, nsamp, pitch)."""
     if isinstance(h_data, np.ndarray):
-        a = np.ascontiguousarray(h_data, dtype=np.uint8)
-        ptr, nsamp = a.ctypes.data, a.shape[1]
+        a = h_data
+        if a.dtype != np.uint8 or a.ndim != 2 or a.strides[1] != 1:
+            a = np.ascontiguousarray(a, dtype=np.uint8)
+        ptr, nsamp, pitch = a.ctypes.data, a.shape[1], a.strides[0]
     else:
-        ptr, nsamp = h_data
-    return _check(lib().af_stream_push(stream, int(beam), ptr, int(nsamp), int(seq)), "af_stream_push")
+        ptr, nsamp, pitch = h_data
+    return _check(lib().af_stream_push(stream, int(beam), ptr, int(nsamp), int(pitch), int(seq)), "af_stream_push")
 
 
 def af_stream_poll(stream, timeout_ms=60000):

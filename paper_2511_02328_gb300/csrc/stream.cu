@@ -354,9 +354,12 @@ extern "C" int af_stream_open(af_stream_t* out, const af_stream_cfg_t* cfg)
     return AF_OK;
 }
 
-extern "C" int af_stream_push(af_stream_t s, int beam, const uint8_t* h_data, int64_t nsamp, int64_t seq)
+extern "C" int af_stream_push(af_stream_t s, int beam, const uint8_t* h_data, int64_t nsamp, int64_t pitch,
+                               int64_t seq)
 {
     if (!s || !h_data || beam < 0 || beam >= s->nbeams) return af_set_error(AF_EINVAL, "af_stream_push: bad arguments");
+    if (pitch == 0) pitch = nsamp;
+    if (pitch < nsamp) return af_set_error(AF_EINVAL, "af_stream_push: pitch %lld < nsamp %lld", (long long)pitch, (long long)nsamp);
     const Clock::time_point t_arrive = Clock::now();
     int k = -1;
     int64_t sample0 = 0;
@@ -414,13 +417,13 @@ extern "C" int af_stream_push(af_stream_t s, int beam, const uint8_t* h_data, in
     int rc = AF_OK;
     cudaError_t e;
     if (first) {
-        e = cudaMemcpyAsync(sl.d_in, h_data, (size_t)s->nchan * W, cudaMemcpyHostToDevice, st);
+        e = cudaMemcpy2DAsync(sl.d_in, W, h_data, (size_t)pitch, W, s->nchan, cudaMemcpyHostToDevice, st);
     } else {
         e = cudaStreamWaitEvent(st, b.overlap_ready, 0);
         if (e == cudaSuccess && D > 0)
             e = cudaMemcpy2DAsync(sl.d_in, W, b.d_overlap, D, D, s->nchan, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess)
-            e = cudaMemcpy2DAsync(sl.d_in + D, W, h_data, H, H, s->nchan, cudaMemcpyHostToDevice, st);
+            e = cudaMemcpy2DAsync(sl.d_in + D, W, h_data, (size_t)pitch, H, s->nchan, cudaMemcpyHostToDevice, st);
     }
     // the next window of this beam starts with this window's last Dmax samples
     if (e == cudaSuccess && D > 0)

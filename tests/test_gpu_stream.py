@@ -46,9 +46,10 @@ def _stream_data(seed):
 
 
 def _chunk(x, k, hop):
+    # column slices of the stream: passed to the engine with their row pitch
     if k == 0:
-        return np.ascontiguousarray(x[:, :WINDOW])
-    return np.ascontiguousarray(x[:, WINDOW + (k - 1) * hop: WINDOW + k * hop])
+        return x[:, :WINDOW]
+    return x[:, WINDOW + (k - 1) * hop: WINDOW + k * hop]
 
 
 def _open(nbeams, **kw):
