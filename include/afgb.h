@@ -358,6 +358,71 @@ int af_stream_restore(af_stream_t s, int beam, const uint8_t* h_overlap, int64_t
 /* Waits for all work, stops the dispatcher and frees everything. */
 int af_stream_close(af_stream_t s);
 
+/* ---- candidate classifier ----------------------------------------------- *
+ * The paper detects pulses with a YOLOv11n network on DM-time images
+ * (Sec. 2.5); its weights and data sets are not available, so the library
+ * carries a small CNN instead, trained on the GPU by the library's own kernels
+ * (BF16 tensor-core GEMMs, FP32 accumulation):
+ * input NHWC bf16 [n][64][64][2] (channel 0 DM-time, 1 frequency-time cut-out),
+ * three blocks conv3x3 (+bias) -> ReLU -> 2x2 max pool (2 -> 16 -> 32 -> 64
+ * channels), global average pool, fully connected 64 -> 2, softmax; label /
+ * class 1 = pulse.  bf16 values travel as uint16_t.  Parameters are fp32, flat:
+ * w0 [16][3][3][2], b0 [16], w1 [32][3][3][16], b1 [32], w2 [64][3][3][32],
+ * b2 [64], fw [2][64], fb [2] (23570 values). */
+typedef struct af_model_s* af_model_t;
+
+/* Two 64 x 64 cut-outs per candidate (adapting the gridding and min-max
+ * normalisation of Sec. 2.4): time bins of b = max(1, width/2) samples, bin j
+ * covering [t - 32b + jb, t - 32b + (j+1)b) (samples outside [0, nout) count 0);
+ * DM-time [i][j] = bin sum of plane row dm_idx - 32 + i (zero outside the
+ * plane); frequency-time [g][j] = bin sum over channel group g (nchan/64
+ * channels) of X[c][s + D[dm_idx][c]]; each normalised as
+ * float(v - min) / (float(max - min) + 1e-6f) and rounded to bf16.
+ *  d_in [nchan][nsamp] uint8, d_plane [ndm][nout] int32 (nout = nsamp - Dmax),
+ *  d_cands [n] device, d_out bf16 [n][64][64][2].  nchan must be a multiple of 64. */
+int af_cutouts(af_plan_t plan, const uint8_t* d_in, int64_t nsamp, const int32_t* d_plane, int64_t nout,
+               const af_cand_t* d_cands, int32_t n, uint16_t* d_out, void* stream);
+
+/* The classifier's tensor-core GEMM (bf16 operands, fp32 accumulation), for
+ * tests and tools:  C[m][n] (op)= sum_k A(m,k) B(k,n)  with
+ *  layout 0: A [M][K], B given as [N][K];   1: A [M][K], B [K][N];
+ *         2: A given as [K][M], B [K][N];   3: A given as [K][M], B as [N][K]
+ *  epi    0: C = acc;  1: C = max(acc + bias[n], 0);  2: C += acc (atomic, fp32)
+ * lda / ldb = row pitch of the stored arrays in elements (multiples of 8),
+ * ldc of C (fp32 [M][ldc]); operands 16-byte aligned; splits > 1 splits K
+ * across blocks (epi 2 only). */
+int af_nn_gemm(int layout, int epi, const uint16_t* d_a, int lda, const uint16_t* d_b, int ldb, int M, int N, int K,
+               int splits, float* d_c, int ldc, const float* d_bias, void* stream);
+
+/* Allocates parameters, Adam state and the workspace of batches up to
+ * max_batch on the current device; He-normal initial weights from `seed`. */
+int af_model_create(af_model_t* out, int max_batch, uint64_t seed);
+int af_model_destroy(af_model_t model);
+int af_model_nparams(af_model_t model, int64_t* n);
+/* Host fp32 parameter / gradient vectors in the flat order above (synchronous). */
+int af_model_set_params(af_model_t model, const float* h_params, int64_t n);
+int af_model_get_params(af_model_t model, float* h_params, int64_t n);
+int af_model_get_grads(af_model_t model, float* h_grads, int64_t n);
+/* Checkpoint: JSON header line + raw little-endian fp32 parameters and Adam moments. */
+int af_model_save(af_model_t model, const char* path);
+int af_model_load(af_model_t model, const char* path);
+
+/* Forward pass: d_x bf16 [n][64][64][2] (n <= max_batch, 16-byte aligned);
+ * d_logits fp32 [n][2] and d_prob fp32 [n] = P(pulse) (either may be NULL). */
+int af_model_forward(af_model_t model, const uint16_t* d_x, int32_t n, float* d_logits, float* d_prob,
+                     void* stream);
+/* Forward + backward of the mean softmax cross-entropy for labels d_y int32 [n]
+ * (0/1); gradients stay in the model (af_model_get_grads); d_loss fp32 [1]. */
+int af_model_backward(af_model_t model, const uint16_t* d_x, const int32_t* d_y, int32_t n, float* d_loss,
+                      void* stream);
+/* af_model_backward followed by one Adam step (beta1 0.9, beta2 0.999, eps 1e-8). */
+int af_train_step(af_model_t model, const uint16_t* d_x, const int32_t* d_y, int32_t n, float lr, float* d_loss,
+                  void* stream);
+/* Cut-outs of n candidates (any n; processed max_batch at a time) and the
+ * network's P(pulse) for each, into d_prob fp32 [n]. */
+int af_classify(af_model_t model, af_plan_t plan, const uint8_t* d_in, int64_t nsamp, const int32_t* d_plane,
+                int64_t nout, const af_cand_t* d_cands, int32_t n, float* d_prob, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,6 +82,20 @@ SIGNATURES = {
     "af_stream_snapshot": [_P, _I, _P, _P, _P],
     "af_stream_restore": [_P, _I, _P, _I64, _I64],
     "af_stream_close": [_P],
+    "af_nn_gemm": [_I, _I, _P, _I, _P, _I, _I, _I, _I, _I, _P, _I, _P, _P],
+    "af_cutouts": [_P, _P, _I64, _P, _I64, _P, _I32, _P, _P],
+    "af_model_create": [_P, _I, ctypes.c_uint64],
+    "af_model_destroy": [_P],
+    "af_model_nparams": [_P, _P],
+    "af_model_set_params": [_P, _P, _I64],
+    "af_model_get_params": [_P, _P, _I64],
+    "af_model_get_grads": [_P, _P, _I64],
+    "af_model_save": [_P, ctypes.c_char_p],
+    "af_model_load": [_P, ctypes.c_char_p],
+    "af_model_forward": [_P, _P, _I32, _P, _P, _P],
+    "af_model_backward": [_P, _P, _P, _I32, _P, _P],
+    "af_train_step": [_P, _P, _P, _I32, _F, _P, _P],
+    "af_classify": [_P, _P, _P, _I64, _P, _I64, _P, _I32, _P, _P],
 }
 _RESTYPE = {"af_last_error": ctypes.c_char_p, "af_version": ctypes.c_char_p}
 
@@ -364,3 +378,75 @@ def af_stream_restore(stream, beam, overlap, next_seq, next_sample):
 
 def af_stream_close(stream):
     _check(lib().af_stream_close(stream), "af_stream_close")
+
+
+NPARAMS = 23570
+
+
+def af_nn_gemm(layout, epi, d_a, lda, d_b, ldb, M, N, K, splits, d_c, ldc, d_bias=0, stream=0):
+    _check(lib().af_nn_gemm(int(layout), int(epi), d_a, int(lda), d_b, int(ldb), int(M), int(N), int(K), int(splits),
+                            d_c, int(ldc), d_bias or None, stream or None), "af_nn_gemm")
+
+
+def af_cutouts(plan, d_in, nsamp, d_plane, nout, d_cands, n, d_out, stream=0):
+    _check(lib().af_cutouts(plan, d_in, int(nsamp), d_plane, int(nout), d_cands or None, int(n), d_out or None,
+                            stream or None), "af_cutouts")
+
+
+def af_model_create(max_batch, seed=0):
+    h = _P()
+    _check(lib().af_model_create(ctypes.byref(h), int(max_batch), int(seed)), "af_model_create")
+    return h.value
+
+
+def af_model_destroy(model):
+    _check(lib().af_model_destroy(model), "af_model_destroy")
+
+
+def af_model_nparams(model):
+    n = _I64()
+    _check(lib().af_model_nparams(model, ctypes.byref(n)), "af_model_nparams")
+    return n.value
+
+
+def af_model_set_params(model, params):
+    p, pp = _host(params, np.float32)
+    _check(lib().af_model_set_params(model, pp, int(p.size)), "af_model_set_params")
+
+
+def af_model_get_params(model):
+    out = np.empty(af_model_nparams(model), dtype=np.float32)
+    _check(lib().af_model_get_params(model, out.ctypes.data_as(_P), int(out.size)), "af_model_get_params")
+    return out
+
+
+def af_model_get_grads(model):
+    out = np.empty(af_model_nparams(model), dtype=np.float32)
+    _check(lib().af_model_get_grads(model, out.ctypes.data_as(_P), int(out.size)), "af_model_get_grads")
+    return out
+
+
+def af_model_save(model, path):
+    _check(lib().af_model_save(model, str(path).encode()), "af_model_save")
+
+
+def af_model_load(model, path):
+    _check(lib().af_model_load(model, str(path).encode()), "af_model_load")
+
+
+def af_model_forward(model, d_x, n, d_logits=0, d_prob=0, stream=0):
+    _check(lib().af_model_forward(model, d_x, int(n), d_logits or None, d_prob or None, stream or None),
+           "af_model_forward")
+
+
+def af_model_backward(model, d_x, d_y, n, d_loss=0, stream=0):
+    _check(lib().af_model_backward(model, d_x, d_y, int(n), d_loss or None, stream or None), "af_model_backward")
+
+
+def af_train_step(model, d_x, d_y, n, lr, d_loss=0, stream=0):
+    _check(lib().af_train_step(model, d_x, d_y, int(n), float(lr), d_loss or None, stream or None), "af_train_step")
+
+
+def af_classify(model, plan, d_in, nsamp, d_plane, nout, d_cands, n, d_prob, stream=0):
+    _check(lib().af_classify(model, plan, d_in, int(nsamp), d_plane, int(nout), d_cands or None, int(n), d_prob,
+                             stream or None), "af_classify")
