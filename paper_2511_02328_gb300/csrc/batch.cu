@@ -42,8 +42,8 @@ cudaError_t launch_persistent(int grid, size_t smem, cudaStream_t s, const aftil
 template <int NW, int M>
 cudaError_t set_attr(size_t smem)
 {
-    return cudaFuncSetAttribute(aftile::k_tile_persistent<NW, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
+    return af_ensure_smem((const void*)aftile::k_tile_persistent<NW, M>, smem) == AF_OK ? cudaSuccess
+                                                                                         : cudaErrorInvalidValue;
 }
 
 struct Shape {
@@ -176,6 +176,7 @@ static int setup_shape(af_batch_t b, int si)
 static int enqueue_dedisp(af_batch_t b, cudaStream_t s)
 {
     const Shape& sh = kShapes[b->shape];
+    AF_CUDA(sh.attr(b->smem));
     AF_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s));
     for (Beam& x : b->beams)
         AF_CUDA(cudaMemsetAsync(x.d_stats, 0, (size_t)x.plan->ndm * sizeof(af_rowstats_t), s));

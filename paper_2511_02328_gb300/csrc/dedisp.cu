@@ -12,6 +12,8 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -103,6 +105,21 @@ k_rowstats(const int32_t* __restrict__ Y, int64_t nout, af_rowstats_t* __restric
 
 }  // namespace
 
+int af_ensure_smem(const void* kernel, size_t bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> set;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& cur = set[std::make_pair(dev, kernel)];
+    if (bytes <= cur) return AF_OK;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return af_cuda_check(e, "kernel shared memory attribute");
+    cur = bytes;
+    return AF_OK;
+}
+
 // Tile-kernel tables for one delay table and block shape: DMs sorted
 // ascending (ties keep list order), padded to a multiple of nw by repeating
 // the last one; the smallest delay of each block per channel; the window.
@@ -174,11 +191,8 @@ int af_prepare_dedisp_tables(af_plan_t p)
     cudaError_t e;
     if ((e = cudaMalloc(&p->d_err, sizeof(int))) != cudaSuccess || (e = cudaMemset(p->d_err, 0, sizeof(int))) != cudaSuccess)
         return af_cuda_check(e, "af_plan: error flag");
-    if (p->tile.fits) {
-        e = cudaFuncSetAttribute(aftile::k_tile<kDefaultNW, kDefaultM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)af_tile_smem(kDefaultNW, p->tile.rw));
-        if (e != cudaSuccess) return af_cuda_check(e, "af_plan: tile kernel shared memory");
-    }
+    if (p->tile.fits)
+        return af_ensure_smem((const void*)aftile::k_tile<kDefaultNW, kDefaultM>, af_tile_smem(kDefaultNW, p->tile.rw));
     return AF_OK;
 }
 
@@ -214,6 +228,9 @@ int af_launch_dedisperse(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_
         a.err = p->d_err;
         const unsigned long long nb = (unsigned long long)a.tiles * a.nblk;
         if (nb > 0x7fffffffULL) return af_set_error(AF_EINVAL, "dedisperse: problem too large for one grid");
+        if (int rc = af_ensure_smem((const void*)aftile::k_tile<kDefaultNW, kDefaultM>,
+                                    af_tile_smem(kDefaultNW, a.rw)))
+            return rc;
         aftile::k_tile<kDefaultNW, kDefaultM>
             <<<(unsigned)nb, (kDefaultNW + 1) * 32, af_tile_smem(kDefaultNW, a.rw), s>>>(a);
         return af_cuda_check(cudaGetLastError(), "dedisperse launch");

@@ -44,6 +44,10 @@ struct af_tile_tables {
     int ndm_pad = 0, nblk = 0, spread = 0, rw = 0;
     bool fits = false;             // the channel window fits in shared memory
 };
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` (the
+// attribute belongs to the kernel, not to a plan: it only ever grows).
+int af_ensure_smem(const void* kernel, size_t bytes);
+
 int af_tile_tables_build(const int32_t* delays, const double* dms, int ndm, int nchan, int nw, int m, int device,
                          af_tile_tables* t);
 void af_tile_tables_free(af_tile_tables* t);

@@ -149,10 +149,7 @@ int af_launch_boxcar(const int32_t* d_plane, int ndm, int64_t nout, const af_row
     if (nblk > 0x7fffffffULL) return af_set_error(AF_EINVAL, "boxcar: problem too large for one grid");
     const size_t smem = (size_t)(kBOut + w.w[w.n - 1] + 1) * sizeof(uint32_t);
     if (smem > 48 * 1024)
-        if (int rc = af_cuda_check(cudaFuncSetAttribute(k_boxcar, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                        (int)smem),
-                                   "boxcar smem attribute"))
-            return rc;
+        if (int rc = af_ensure_smem((const void*)k_boxcar, smem)) return rc;
     k_boxcar<<<(unsigned)nblk, kBT, smem, s>>>(d_plane, nout, tiles, w, d_rowconst, d_best_snr, d_best_w);
     return af_cuda_check(cudaGetLastError(), "boxcar launch");
 }

@@ -167,6 +167,7 @@ static int dispatch(af_stream_s* s, const std::vector<int>& batch)
     for (int k : batch) AF_CUDA(cudaStreamWaitEvent(d, s->slots[k].input_ready, 0));
     AF_CUDA(cudaMemsetAsync(s->d_counter, 0, sizeof(unsigned long long), d));
     for (int k : batch) AF_CUDA(cudaMemsetAsync(s->slots[k].d_stats, 0, (size_t)s->ndm * sizeof(af_rowstats_t), d));
+    if (int rc = af_ensure_smem((const void*)aftile::k_tile_persistent<kNW, kM>, s->smem)) return rc;
     aftile::k_tile_persistent<kNW, kM><<<s->grid, (kNW + 1) * 32, s->smem, d>>>(
         s->d_jobs[r], s->d_first[r], (int)batch.size(), first[batch.size()], s->d_counter);
     AF_CUDA(cudaGetLastError());
@@ -340,8 +341,8 @@ extern "C" int af_stream_open(af_stream_t* out, const af_stream_cfg_t* cfg)
         e = cudaStreamCreateWithFlags(&s->dstream, cudaStreamNonBlocking);
     if (e == cudaSuccess) {
         s->smem = af_tile_smem(kNW, p->tile.rw);
-        e = cudaFuncSetAttribute(aftile::k_tile_persistent<kNW, kM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)s->smem);
+        if (af_ensure_smem((const void*)aftile::k_tile_persistent<kNW, kM>, s->smem) != AF_OK)
+            e = cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) {
         rc = af_cuda_check(e, "af_stream_open: allocation");

@@ -110,3 +110,37 @@ def pulse_params(n, seed, dm_range, width_range_s, snr_range, t_range_s, min_sep
         res.append(dict(dm=dm, width=max(1, int(round(w_s / tsamp))), snr=snr,
                         t0=int(round(t0 / tsamp))))
     return res
+
+
+def filterbank_torch(nchan, nsamp, seed, pulses=(), rfi=None, device="cuda", mean=NOISE_MEAN, sigma=NOISE_SIGMA):
+    """The same recipe as filterbank(), drawn with a seeded torch generator on
+    the GPU (for large training sets); returns a uint8 tensor [nchan][nsamp]."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    x = torch.randn((nchan, nsamp), generator=g, device=device, dtype=torch.float32)
+    x.mul_(sigma).add_(mean)
+    if rfi is not None:
+        for c in rfi.narrow_channels:
+            x[c] = (x[c] - mean) * float(np.sqrt(rfi.narrow_var)) + mean + rfi.narrow_mean * sigma
+    rows = torch.arange(nchan, device=device)
+    for p in pulses:
+        offs = torch.as_tensor(np.asarray(p.offsets, dtype=np.int64), device=device)
+        cols = offs[:, None] + torch.arange(p.width, device=device)[None, :]
+        ok = (cols >= 0) & (cols < nsamp)
+        r = rows[:, None].expand_as(cols)[ok]
+        amp = torch.as_tensor(np.broadcast_to(np.asarray(p.amp, dtype=np.float32), (nchan,)).copy(), device=device)
+        x.index_put_((r, cols[ok]), amp[r], accumulate=True)
+    if rfi is not None:
+        for (t0, ln, amp) in rfi.bursts:
+            lo, hi = max(0, int(t0)), min(nsamp, int(t0) + int(ln))
+            if lo < hi:
+                x[:, lo:hi] += float(amp)
+        for (ch0, t0, ln, drift, amp) in rfi.tones:
+            k = torch.arange(int(ln), device=device, dtype=torch.float32)
+            c = torch.round(ch0 + drift * k).long()
+            t = int(t0) + k.long()
+            ok = (c >= 0) & (c < nchan) & (t >= 0) & (t < nsamp)
+            x.index_put_((c[ok], t[ok]), torch.full((int(ok.sum()),), float(amp), device=device), accumulate=True)
+    x.round_().clamp_(0, 255)
+    return x.to(torch.uint8)

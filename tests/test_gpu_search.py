@@ -300,3 +300,17 @@ def test_repeated_calls_and_streams(c1_data):
     s2.synchronize()
     assert np.array_equal(a.cpu().numpy(), Y) and np.array_equal(b.cpu().numpy(), Y)
     p.close()
+
+
+def test_plans_with_different_windows_coexist(c1_data):
+    """A plan created later with a smaller shared-memory window must not break
+    an earlier plan that needs a larger one (the limit belongs to the kernel)."""
+    from paper_2511_02328_gb300.search import Plan
+    x, D, Y, _, _ = c1_data
+    big = _plan(C1)                                           # 501 DMs, wide window
+    small = Plan(C1["nchan"], C1["f_lo"], C1["f_hi"], C1["tsamp"], [0.0, 0.5])
+    plane = big.dedisperse(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(plane.cpu().numpy(), Y)
+    small.close()
+    big.close()
