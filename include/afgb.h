@@ -53,6 +53,7 @@ extern "C" {
 #define AF_NOALLOC_MAX_ROWS 4096 /* row limit of af_boxcar_snr_noalloc       */
 
 typedef struct af_plan_s* af_plan_t;
+typedef struct af_model_s* af_model_t;  /* the candidate classifier, see below */
 
 /* Per-DM-row sums of the plane: sum = sum_t Y[d][t], sumsq = sum_t Y[d][t]^2
  * over the row's nout samples (exact 64-bit integers). */
@@ -343,6 +344,16 @@ int af_stream_push(af_stream_t s, int beam, const uint8_t* h_data, int64_t nsamp
 int af_stream_poll(af_stream_t s, af_stream_result_t* out, int timeout_ms);
 int af_stream_release(af_stream_t s, int32_t slot);
 
+/* Inline classification of a held window: cut-outs of the n host candidates
+ * (n <= the engine's cap; typically the cluster representatives of the
+ * window's candidates) from the window's device input and plane, and the
+ * classifier's P(pulse) for each into h_prob[n].  Synchronous.  Calls on the
+ * same engine must not overlap. */
+int af_stream_classify(af_stream_t s, int32_t slot, af_model_t model, const af_cand_t* h_cands, int32_t n,
+                       float* h_prob);
+/* The true-positive clustering of Sec. 4.2 (as af_cluster) with the engine's DM list and sampling. */
+int af_stream_cluster(af_stream_t s, af_cand_t* h_cands, int32_t n, af_cand_t* h_out, int32_t* n_out);
+
 /* Device plane [ndm][hop] and best S/N of a held slot. */
 int af_stream_result_plane(af_stream_t s, int32_t slot, int32_t** d_plane, float** d_snr, int64_t* nout);
 
@@ -369,8 +380,6 @@ int af_stream_close(af_stream_t s);
  * class 1 = pulse.  bf16 values travel as uint16_t.  Parameters are fp32, flat:
  * w0 [16][3][3][2], b0 [16], w1 [32][3][3][16], b1 [32], w2 [64][3][3][32],
  * b2 [64], fw [2][64], fb [2] (23570 values). */
-typedef struct af_model_s* af_model_t;
-
 /* Two 64 x 64 cut-outs per candidate (adapting the gridding and min-max
  * normalisation of Sec. 2.4): time bins of b = max(1, width/2) samples, bin j
  * covering [t - 32b + jb, t - 32b + (j+1)b) (samples outside [0, nout) count 0);

@@ -82,6 +82,8 @@ SIGNATURES = {
     "af_stream_snapshot": [_P, _I, _P, _P, _P],
     "af_stream_restore": [_P, _I, _P, _I64, _I64],
     "af_stream_close": [_P],
+    "af_stream_classify": [_P, _I32, _P, _P, _I32, _P],
+    "af_stream_cluster": [_P, _P, _I32, _P, _P],
     "af_nn_gemm": [_I, _I, _P, _I, _P, _I, _I, _I, _I, _I, _P, _I, _P, _P],
     "af_cutouts": [_P, _P, _I64, _P, _I64, _P, _I32, _P, _P],
     "af_model_create": [_P, _I, ctypes.c_uint64],
@@ -374,6 +376,24 @@ def af_stream_restore(stream, beam, overlap, next_seq, next_sample):
     ov = np.ascontiguousarray(overlap, dtype=np.uint8)
     _check(lib().af_stream_restore(stream, int(beam), ov.ctypes.data_as(_P), int(next_seq), int(next_sample)),
            "af_stream_restore")
+
+
+def af_stream_classify(stream, slot, model, cands):
+    """cands: CAND_DTYPE array (host).  Returns P(pulse) per candidate."""
+    c = np.ascontiguousarray(cands, dtype=CAND_DTYPE)
+    prob = np.empty(max(c.size, 1), dtype=np.float32)
+    _check(lib().af_stream_classify(stream, int(slot), model, c.ctypes.data_as(_P), int(c.size),
+                                    prob.ctypes.data_as(_P)), "af_stream_classify")
+    return prob[: c.size]
+
+
+def af_stream_cluster(stream, cands):
+    c = np.ascontiguousarray(cands, dtype=CAND_DTYPE).copy()
+    out = np.empty(max(c.size, 1), dtype=CAND_DTYPE)
+    n = _I32()
+    _check(lib().af_stream_cluster(stream, c.ctypes.data_as(_P), int(c.size), out.ctypes.data_as(_P),
+                                   ctypes.byref(n)), "af_stream_cluster")
+    return out[: n.value]
 
 
 def af_stream_close(stream):

@@ -107,6 +107,10 @@ struct af_stream_s {
     int grid = 0;
     size_t smem = 0;
     int max_batch = 0;
+    // inline classification of held windows
+    cudaStream_t cstream = nullptr;
+    af_cand_t* d_ccands = nullptr;
+    float* d_cprob = nullptr;
 
     // statistics
     std::vector<double> lat_ms;
@@ -254,6 +258,9 @@ static void free_stream(af_stream_s* s)
     }
     cudaFree(s->d_counter);
     cudaFree(s->d_err);
+    cudaFree(s->d_ccands);
+    cudaFree(s->d_cprob);
+    if (s->cstream) cudaStreamDestroy(s->cstream);
     if (s->dstream) cudaStreamDestroy(s->dstream);
     af_plan_destroy(s->plan);
     delete s;
@@ -337,7 +344,10 @@ extern "C" int af_stream_open(af_stream_t* out, const af_stream_cfg_t* cfg)
             break;
     }
     if (e == cudaSuccess && (e = cudaMalloc(&s->d_counter, 16)) == cudaSuccess &&
-        (e = cudaMalloc(&s->d_err, 16)) == cudaSuccess && (e = cudaMemset(s->d_err, 0, 16)) == cudaSuccess)
+        (e = cudaMalloc(&s->d_err, 16)) == cudaSuccess && (e = cudaMemset(s->d_err, 0, 16)) == cudaSuccess &&
+        (e = cudaMalloc(&s->d_ccands, (size_t)s->cap * sizeof(af_cand_t))) == cudaSuccess &&
+        (e = cudaMalloc(&s->d_cprob, (size_t)s->cap * sizeof(float))) == cudaSuccess &&
+        (e = cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking)) == cudaSuccess)
         e = cudaStreamCreateWithFlags(&s->dstream, cudaStreamNonBlocking);
     if (e == cudaSuccess) {
         s->smem = af_tile_smem(kNW, p->tile.rw);
@@ -513,6 +523,33 @@ extern "C" int af_stream_result_plane(af_stream_t s, int32_t slot, int32_t** d_p
     if (d_snr) *d_snr = s->slots[slot].d_snr;
     if (nout) *nout = s->hop;
     return AF_OK;
+}
+
+extern "C" int af_stream_classify(af_stream_t s, int32_t slot, af_model_t model, const af_cand_t* h_cands, int32_t n,
+                                  float* h_prob)
+{
+    if (!s || !model || slot < 0 || slot >= (int)s->slots.size() || n < 0 || n > s->cap ||
+        (n > 0 && (!h_cands || !h_prob)))
+        return af_set_error(AF_EINVAL, "af_stream_classify: bad arguments (n must be <= the engine's cap)");
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->slots[slot].state != HELD) return af_set_error(AF_EINVAL, "af_stream_classify: slot %d not held", slot);
+    }
+    if (n == 0) return AF_OK;
+    Slot& sl = s->slots[slot];
+    cudaStream_t cs = s->cstream;
+    AF_CUDA(cudaMemcpyAsync(s->d_ccands, h_cands, (size_t)n * sizeof(af_cand_t), cudaMemcpyHostToDevice, cs));
+    if (int rc = af_classify(model, s->plan, sl.d_in, s->window, sl.d_plane, s->hop, s->d_ccands, n, s->d_cprob, cs))
+        return rc;
+    AF_CUDA(cudaMemcpyAsync(h_prob, s->d_cprob, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, cs));
+    AF_CUDA(cudaStreamSynchronize(cs));
+    return AF_OK;
+}
+
+extern "C" int af_stream_cluster(af_stream_t s, af_cand_t* h_cands, int32_t n, af_cand_t* h_out, int32_t* n_out)
+{
+    if (!s) return af_set_error(AF_EINVAL, "af_stream_cluster: NULL stream");
+    return af_cluster(s->plan, h_cands, n, 20.0, 0.2, h_out, n_out);
 }
 
 extern "C" int af_stream_info(af_stream_t s, int64_t* hop, int64_t* dmax, int* nslots)

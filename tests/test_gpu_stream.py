@@ -208,3 +208,31 @@ def test_snapshot_restore_continues_exactly():
     for k in range(3, NWIN):
         assert np.array_equal(got[(0, k)][1], ref[(0, k)][1])
         assert np.array_equal(got[(0, k)][0]["cands"], ref[(0, k)][0]["cands"])
+
+
+def test_inline_classification_matches_classify():
+    """af_stream_classify on a held window equals af_classify on the same window
+    searched alone (same cut-outs, same network)."""
+    from paper_2511_02328_gb300 import _lib
+    from paper_2511_02328_gb300.search import Plan
+    x, hop = _stream_data(6)
+    s = _open(1)
+    m = _lib.af_model_create(8, 2)
+    _lib.af_stream_push(s, 0, _chunk(x, 0, hop), 0)
+    r = _lib.af_stream_poll(s, 60000)
+    reps = _lib.af_stream_cluster(s, r["cands"])
+    assert len(reps) >= 1
+    prob = _lib.af_stream_classify(s, r["slot"], m, reps)
+    _lib.af_stream_release(s, r["slot"])
+    _lib.af_stream_close(s)
+    p = Plan(NCHAN, F_LO, F_HI, TSAMP, DMS)
+    win = torch.from_numpy(np.ascontiguousarray(x[:, :WINDOW])).cuda()
+    plane = p.dedisperse(win)
+    cd = torch.from_numpy(np.ascontiguousarray(reps).view(np.uint8).reshape(len(reps), 24)).cuda()
+    ref = torch.empty(len(reps), dtype=torch.float32, device="cuda")
+    _lib.af_classify(m, p.handle, win.data_ptr(), WINDOW, plane.data_ptr(), plane.shape[1], cd.data_ptr(),
+                     len(reps), ref.data_ptr())
+    torch.cuda.synchronize()
+    assert np.array_equal(prob, ref.cpu().numpy())
+    _lib.af_model_destroy(m)
+    p.close()
