@@ -177,8 +177,9 @@ def run_reference(args):
 
 
 STREAM_WORKLOAD = ("streaming: 19 beams, 4096 ch x 49.152 us uint8, windows of 2^18 samples overlapping by the "
-                   "DM-2000 delay, DMs 0-2000 step 1, boxcar 1..256, threshold 8; chunks arrive at the real-time rate, "
-                   "beams staggered evenly over one hop")
+                   "DM-2000 delay, DMs 0-2000 step 1, boxcar 1..256, threshold 8; a pulse (DM 100-1900, S/N 12-30) "
+                   "every 40k samples and zero-DM bursts; chunks arrive at the real-time rate, beams staggered evenly "
+                   "over one hop; every cluster representative classified inline")
 
 
 def run_stream(args, dev, clocks):
@@ -197,10 +198,23 @@ def run_stream(args, dev, clocks):
     rounds = max(2, args.stream_rounds)
     stagger = 16384
     pool_len = (nbeams - 1) * stagger + window + (rounds - 1) * hop
-    g = torch.Generator(device=dev)
-    g.manual_seed(99)
-    pool_d = torch.randn((NCHAN, pool_len), generator=g, device=dev).mul_(12.0).add_(128.0).round_().clamp_(0, 255)
-    pool = pool_d.to(torch.uint8).cpu().pin_memory().numpy()
+    # seeded pool with a dispersed pulse every ~40k samples and zero-DM bursts (RFI)
+    from paper_2511_02328_gb300 import synth
+    from paper_2511_02328_gb300.search import Plan
+    rng = np.random.default_rng(99)
+    t0s = np.arange(20000, pool_len - 100000, 40000)
+    pdms = rng.uniform(100.0, 1900.0, len(t0s))
+    pplan = Plan(NCHAN, F_LO, F_HI, TSAMP, pdms)
+    pD = pplan.delays().astype(np.int64)
+    pplan.close()
+    pulses = []
+    for i, t0 in enumerate(t0s):
+        w = int(rng.integers(20, 100))
+        pulses.append(synth.Pulse(int(t0) + pD[i], w, synth.pulse_amplitude(rng.uniform(12, 30), NCHAN, w)))
+    bursts = [(int(t), int(rng.integers(1, 20)), synth.pulse_amplitude(30.0, NCHAN, 10))
+              for t in rng.integers(0, pool_len, 8)]
+    pool_d = synth.filterbank_torch(NCHAN, pool_len, 99, pulses=pulses, rfi=synth.RFI(bursts=bursts), device=dev)
+    pool = pool_d.cpu().pin_memory().numpy()
     del pool_d
     torch.cuda.empty_cache()
     hop_s = hop * TSAMP
