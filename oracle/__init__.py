@@ -53,6 +53,19 @@ def lib():
         L.oracle_peaks.restype = ctypes.c_int64
         L.oracle_peaks.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
                                    ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64]
+        L.oracle_subband_first.restype = ctypes.c_int
+        L.oracle_subband_first.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+        L.oracle_subband_freq.restype = ctypes.c_double
+        L.oracle_subband_freq.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int]
+        L.oracle_subband_residuals.restype = ctypes.c_int
+        L.oracle_subband_residuals.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, ctypes.c_void_p]
+        L.oracle_subband_dedisperse.restype = ctypes.c_int
+        L.oracle_subband_dedisperse.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                                ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                                ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p]
         _lib = L
     return _lib
 
@@ -147,6 +160,79 @@ def injection_offsets(nchan, f_lo, f_hi, tsamp, dm, t0):
     rounding as Eq. (coarse_delay).  Used to build injected test inputs."""
     D = delay_table(nchan, f_lo, f_hi, tsamp, [dm])[0]
     return (np.int64(t0) + D.astype(np.int64))
+
+
+FS_MEDIAN = 0   # representative frequency: median of the channel centres
+FS_INVSQ = 1    # representative frequency: 1/F^2 = mean of 1/f_c^2
+
+
+def subband_first(nchan, nsub):
+    """Partition of the channels into nsub contiguous subbands (Sec. 2.3):
+    int32 [nsub+1], subband s = channels [first[s], first[s+1])."""
+    first = np.empty(nsub + 1, dtype=np.int32)
+    if lib().oracle_subband_first(nchan, nsub, _ptr(first)) != 0:
+        raise ValueError("bad subband partition %d / %d" % (nchan, nsub))
+    return first
+
+
+def subband_freqs(nchan, f_lo, f_hi, nsub, mode):
+    """Representative frequency F_s of every subband (Sec. 2.3)."""
+    first = subband_first(nchan, nsub)
+    F = np.array([lib().oracle_subband_freq(nchan, f_lo, f_hi, int(first[s]), int(first[s + 1]), mode)
+                  for s in range(nsub)])
+    if np.any(F <= 0):
+        raise ValueError("bad subband frequency mode %r" % (mode,))
+    return F
+
+
+def subband_tables(nchan, f_lo, f_hi, tsamp, dms, n0, nsub, mode):
+    """Tables of two-stage subband dedispersion (Sec. 2.3): the partition,
+    F_s, the coarse DMs dm[j*N0] and their delays (Eq. coarse_delay), the
+    residual shifts R [ndm][nsub] (Eq. residual)."""
+    dms = np.ascontiguousarray(dms, dtype=np.float64)
+    ndm = dms.size
+    R = np.empty((ndm, nsub), dtype=np.int32)
+    rc = lib().oracle_subband_residuals(nchan, f_lo, f_hi, tsamp, _ptr(dms), ndm, n0, nsub, mode, _ptr(R))
+    if rc != 0:
+        raise ValueError("oracle_subband_residuals failed (%d)" % rc)
+    coarse = dms[::n0].copy()
+    return dict(first=subband_first(nchan, nsub), F=subband_freqs(nchan, f_lo, f_hi, nsub, mode),
+                coarse_dms=coarse, Dc=delay_table(nchan, f_lo, f_hi, tsamp, coarse), R=R, n0=int(n0),
+                nsub=int(nsub), ndm=int(ndm), nchan=int(nchan))
+
+
+def subband_effective_delays(tab):
+    """Per-channel delay that the two stages apply for fine DM m:
+    Deff[m][c] = D[j(m)][c] + R[m][s(c)] (stage 2 of Eq. stage2 inserted into
+    Eq. stage1).  Reading: the plane of the two stages is the brute-force sum
+    with this table, and nout = nsamp - max(Deff)."""
+    first, Dc, R, n0 = tab["first"], tab["Dc"], tab["R"], tab["n0"]
+    ndm, nchan = tab["ndm"], tab["nchan"]
+    sub_of = np.repeat(np.arange(tab["nsub"]), np.diff(first))
+    j = np.arange(ndm) // n0
+    return (Dc[j, :].astype(np.int64) + R[:, sub_of].astype(np.int64)).astype(np.int32)
+
+
+def subband_dedisperse(X, tab, nout=None):
+    """Two-stage subband plane, Eqs. (stage1), (stage2) (Sec. 2.3), int32."""
+    X = np.ascontiguousarray(X, dtype=np.uint8)
+    nchan, nsamp = X.shape
+    if nchan != tab["nchan"]:
+        raise ValueError("table / data channel mismatch")
+    if nout is None:
+        nout = nsamp - int(subband_effective_delays(tab).max())
+    if nout <= 0:
+        raise ValueError("nout out of range")
+    ndm = tab["ndm"]
+    Y = np.empty((ndm, nout), dtype=np.int32)
+    Dc = np.ascontiguousarray(tab["Dc"], dtype=np.int32)
+    R = np.ascontiguousarray(tab["R"], dtype=np.int32)
+    first = np.ascontiguousarray(tab["first"], dtype=np.int32)
+    rc = lib().oracle_subband_dedisperse(_ptr(X), nchan, nsamp, _ptr(Dc), Dc.shape[0], _ptr(first), tab["nsub"],
+                                         _ptr(R), ndm, tab["n0"], nout, _ptr(Y))
+    if rc != 0:
+        raise ValueError("oracle_subband_dedisperse failed (%d)" % rc)
+    return Y
 
 
 def threads():

@@ -73,3 +73,35 @@ def peaks(snr, bw, widths, thresh):
             if all(row[t] > v for v in left) and all(row[t] >= v for v in right):
                 res.append((d, t, w, row[t]))
     return res
+
+
+def exact_shift(ddm, inv_f2, fr, tsamp):
+    """round(K*dDM/tsamp*(inv_f2 - 1/fr^2)) in exact rational arithmetic, half
+    away from zero: Eq. (residual) with 1/F_s^2 given directly (a Fraction)."""
+    x = K_DM * Fraction(ddm) / Fraction(tsamp) * (inv_f2 - 1 / Fraction(fr) ** 2)
+    n = math.floor(abs(x) + Fraction(1, 2))
+    return n if x >= 0 else -n, x
+
+
+def subband_dedisperse(X, Dc, first, R, n0, nout):
+    """Eqs. (stage1) and (stage2) by direct loops: for fine DM m in coarse
+    group j = m // n0, Y[m][v] = sum over subbands s of I(j, s, v + R[m][s]),
+    I(j, s, u) = sum over channels c of s of X[c][u + Dc[j][c]], with X taken
+    as zero outside the data."""
+    nsamp = len(X[0])
+    nsub = len(first) - 1
+    Y = []
+    for m in range(len(R)):
+        j = m // n0
+        row = []
+        for v in range(nout):
+            total = 0
+            for s in range(nsub):
+                u = v + R[m][s]
+                for c in range(first[s], first[s + 1]):
+                    t = u + Dc[j][c]
+                    if 0 <= t < nsamp:
+                        total += int(X[c][t])
+            row.append(total)
+        Y.append(row)
+    return Y

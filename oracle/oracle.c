@@ -228,3 +228,167 @@ int64_t oracle_peaks(const double* best_snr, const int32_t* best_w, int ndm, int
     }
     return n;
 }
+
+/* ======================================================================
+ * Two-stage subband dedispersion (Sec. 2.3, Eqs. stage1, residual, stage2).
+ * ====================================================================== */
+
+/* Subband partition.  Reading (the paper only says the channels are
+ * partitioned into subbands): nsub contiguous groups of as-equal-as-possible
+ * size, subband s = channels [floor(s*nchan/nsub), floor((s+1)*nchan/nsub)).
+ * first[] has nsub+1 entries.  Returns 0, or -1 on invalid arguments.       */
+int oracle_subband_first(int nchan, int nsub, int32_t* first)
+{
+    if (nchan <= 0 || nsub <= 0 || nsub > nchan)
+        return -1;
+    for (int s = 0; s <= nsub; s++)
+        first[s] = (int32_t)(((int64_t)s * nchan) / nsub);
+    return 0;
+}
+
+static int cmp_double(const void* a, const void* b)
+{
+    double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+/* Representative frequency F_s of the channels [c0, c1) (Sec. 2.3: "the
+ * median or a 1/f^2-weighted center").  Readings:
+ *   mode 0: median of the channel-centre frequencies (mean of the two middle
+ *           values when the count is even);
+ *   mode 1: the frequency whose 1/F^2 equals the mean of 1/f_c^2 over the
+ *           subband, F = (mean 1/f_c^2)^(-1/2)  (the centre of the quantity
+ *           the delay is linear in).
+ * Returns a negative value on invalid arguments.                            */
+double oracle_subband_freq(int nchan, double f_lo, double f_hi, int c0, int c1, int mode)
+{
+    int n = c1 - c0;
+    if (n <= 0 || c0 < 0 || c1 > nchan)
+        return -1.0;
+    if (mode == 0) {
+        double* f = (double*)malloc(sizeof(double) * n);
+        if (!f)
+            return -1.0;
+        for (int i = 0; i < n; i++)
+            f[i] = oracle_chan_freq(c0 + i, nchan, f_lo, f_hi);
+        qsort(f, n, sizeof(double), cmp_double);
+        double med = (n % 2) ? f[n / 2] : 0.5 * (f[n / 2 - 1] + f[n / 2]);
+        free(f);
+        return med;
+    }
+    if (mode == 1) {
+        double acc = 0.0;
+        for (int c = c0; c < c1; c++) {
+            double fc = oracle_chan_freq(c, nchan, f_lo, f_hi);
+            acc += 1.0 / (fc * fc);
+        }
+        return 1.0 / sqrt(acc / (double)n);
+    }
+    return -1.0;
+}
+
+/* Residual shift table, Eq. (residual).  The fine DM list dm[0..ndm) is
+ * grouped N0 at a time: j(m) = floor(m/N0), coarse DM_j = dm[j*N0] (for an
+ * evenly spaced list this is DM_low + j*N0*dDM, the paper's coarse grid), and
+ *     R[m][s] = round( K*(dm[m] - DM_j(m))/t_samp * (1/F_s^2 - 1/f_ref^2) )
+ * with the rounding and operation order of Eq. (coarse_delay) (llround of
+ * a*b, a = K*dDM/tsamp, b = 1/(F*F) - 1/(fr*fr)).  Reading: the list must be
+ * non-decreasing, so every residual DM and shift is >= 0.
+ * Returns 0, -1 on invalid arguments, -2 on int32 overflow.                 */
+int oracle_subband_residuals(int nchan, double f_lo, double f_hi, double tsamp, const double* dm, int ndm,
+                             int n0, int nsub, int mode, int32_t* R)
+{
+    if (nchan <= 0 || ndm <= 0 || n0 <= 0 || nsub <= 0 || nsub > nchan || !(tsamp > 0.0))
+        return -1;
+    for (int m = 1; m < ndm; m++)
+        if (!(dm[m] >= dm[m - 1]))
+            return -1;
+    int32_t* first = (int32_t*)malloc(sizeof(int32_t) * (nsub + 1));
+    if (!first)
+        return -1;
+    oracle_subband_first(nchan, nsub, first);
+    double fr = oracle_ref_freq(f_lo, f_hi);
+    int rc = 0;
+    for (int s = 0; s < nsub && rc == 0; s++) {
+        double F = oracle_subband_freq(nchan, f_lo, f_hi, first[s], first[s + 1], mode);
+        if (!(F > 0.0)) {
+            rc = -1;
+            break;
+        }
+        double b = 1.0 / (F * F) - 1.0 / (fr * fr);
+        for (int m = 0; m < ndm; m++) {
+            double ddm = dm[m] - dm[(m / n0) * n0];
+            double a = (ORACLE_K_DM * ddm) / tsamp;
+            double x = a * b;
+            if (!(x < 2147483647.0)) {
+                rc = -2;
+                break;
+            }
+            R[(int64_t)m * nsub + s] = (int32_t)llround(x);
+        }
+    }
+    free(first);
+    return rc;
+}
+
+/* Two-stage subband dedispersion, Eqs. (stage1) and (stage2), Sec. 2.3.
+ *   Dc     int32 [ncoarse][nchan]: delays of the coarse DMs, Eq. (coarse_delay)
+ *   first  int32 [nsub+1]: the partition;  R int32 [ndm][nsub]: Eq. (residual)
+ * Stage 1, for every coarse DM j and subband s (X is zero outside the data):
+ *     I(j,s,u) = sum_{c in C_s} X(c, u + D[j][c]),  0 <= u < nout + max_{m in j, s} R[m][s]
+ * Stage 2, for every fine DM m (j = floor(m/N0)):
+ *     Y(m,v) = sum_s I(j, s, v + R[m][s]),  0 <= v < nout.
+ * Reading: no time blocking (the paper's block length L only bounds memory;
+ * with nout = nsamp - max_{m,c}(D[j(m)][c] + R[m][s(c)]) every block gives
+ * the same values), so the whole time axis is one block.  The caller passes
+ * nout.  Stage 1 is evaluated per coarse DM (I of one j at a time).         */
+int oracle_subband_dedisperse(const uint8_t* X, int nchan, int64_t nsamp, const int32_t* Dc, int ncoarse,
+                              const int32_t* first, int nsub, const int32_t* R, int ndm, int n0, int64_t nout,
+                              int32_t* Y)
+{
+    if (n0 <= 0 || ncoarse != (ndm + n0 - 1) / n0 || nout <= 0)
+        return -1;
+    for (int j = 0; j < ncoarse; j++) {
+        int m_lo = j * n0, m_hi = (j + 1) * n0 < ndm ? (j + 1) * n0 : ndm;
+        int32_t rmax = 0;
+        for (int m = m_lo; m < m_hi; m++)
+            for (int s = 0; s < nsub; s++)
+                if (R[(int64_t)m * nsub + s] > rmax) rmax = R[(int64_t)m * nsub + s];
+        int64_t li = nout + rmax;
+        int32_t* I = (int32_t*)calloc((size_t)nsub * li, sizeof(int32_t));
+        if (!I)
+            return -2;
+        /* Stage 1 */
+        #pragma omp parallel for schedule(dynamic, 1)
+        for (int s = 0; s < nsub; s++) {
+            int32_t* Is = I + (int64_t)s * li;
+            for (int c = first[s]; c < first[s + 1]; c++) {
+                int64_t d = Dc[(int64_t)j * nchan + c];
+                const uint8_t* x = X + (int64_t)c * nsamp;
+                for (int64_t u = 0; u < li; u++) {
+                    int64_t t = u + d;
+                    if (t >= 0 && t < nsamp)
+                        Is[u] += (int32_t)x[t];
+                }
+            }
+        }
+        /* Stage 2 */
+        #pragma omp parallel for schedule(dynamic, 1)
+        for (int m = m_lo; m < m_hi; m++) {
+            int32_t* y = Y + (int64_t)m * nout;
+            for (int64_t v = 0; v < nout; v++)
+                y[v] = 0;
+            for (int s = 0; s < nsub; s++) {
+                const int32_t* Is = I + (int64_t)s * li;
+                int64_t r = R[(int64_t)m * nsub + s];
+                for (int64_t v = 0; v < nout; v++) {
+                    int64_t u = v + r;
+                    if (u >= 0 && u < li)
+                        y[v] += Is[u];
+                }
+            }
+        }
+        free(I);
+    }
+    return 0;
+}
