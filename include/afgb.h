@@ -124,6 +124,47 @@ int af_plan_check(af_plan_t plan);
  * paper's truncation by the DM delay, Sec. 3).  AF_EINVAL if nout <= 0. */
 int af_plan_nout(af_plan_t plan, int64_t nsamp, int64_t* nout);
 
+/* ---- subband plan: two-stage subband dedispersion, Sec. 2.3 ------------ *
+ * The paper's own dedispersion scheme (Eqs. stage1, residual, stage2).  The
+ * channels are split into nsub contiguous subbands, subband s = channels
+ * [floor(s*nchan/nsub), floor((s+1)*nchan/nsub)), each with a representative
+ * frequency F_s; the fine DM list is grouped n0 at a time, j(m) = m / n0, with
+ * coarse DM_j = dm_list[j*n0] (DM_low + j*n0*dDM for an evenly spaced list):
+ *   stage 1  I(j,s,u) = sum_{c in s} X[c][u + D[j][c]]   D: Eq. (coarse_delay) at DM_j
+ *   stage 2  Y[m][v]  = sum_s I(j(m), s, v + R[m][s])
+ *   R[m][s] = round(K*(dm_list[m] - DM_j(m))/tsamp * (1/F_s^2 - 1/f_ref^2))   Eq. (residual)
+ * with the channel centres, f_ref and rounding of af_plan.  The plane is the
+ * brute-force sum with the EFFECTIVE delay table
+ *     Deff[m][c] = D[j(m)][c] + R[m][s(c)],
+ * so af_plan_delays returns Deff, Dmax = max Deff, nout = nsamp - Dmax, and
+ * af_dedisperse, af_boxcar_snr, af_candidates, af_search, af_cutouts and
+ * af_classify accept the plan like any other.  Compared with the exact
+ * brute-force plane of dm_list the pulse is smeared by about
+ * 2*K*dDM*df_s/F_s^3 (Eq. sb_smear).
+ *  n0        fine DMs per coarse DM, 1 .. 32 (n0 = 1: the brute-force plane)
+ *  nsub      1 .. nchan subbands
+ *  fs_mode   AF_FS_MEDIAN: F_s = median of the subband's channel centres
+ *            (mean of the two middle ones for an even count);
+ *            AF_FS_INVSQ: 1/F_s^2 = mean of 1/f_c^2 over the subband
+ *  block_len the time block L of the paper's blocking (Eq. L1): af_dedisperse
+ *            runs stage 1 and stage 2 once per L outputs, and the plan holds a
+ *            stage-1 scratch of ncoarse*nsub*(L + max R) elements (uint16 when
+ *            every subband has at most 257 channels, else uint32); 0 chooses the
+ *            largest multiple of 4096 up to 2^18 that keeps it within 1 GiB.
+ *  dm_list   non-decreasing, each >= 0 (AF_EINVAL otherwise)
+ * Other arguments and errors as af_plan. */
+#define AF_FS_MEDIAN 0
+#define AF_FS_INVSQ  1
+int af_plan_subband(af_plan_t* out, int nchan, double f_lo, double f_hi, double tsamp,
+                    const double* dm_list, int ndm, int n0, int nsub, int fs_mode, int64_t block_len);
+
+/* Tables of a subband plan (AF_EINVAL for a plain plan); every output may be
+ * NULL: n0, nsub, ncoarse = ceil(ndm/n0), first int32 [nsub+1], fs double
+ * [nsub] (MHz), coarse_delays int32 [ncoarse][nchan], residuals int32
+ * [ndm][nsub], block_len = L in use. */
+int af_plan_subband_info(af_plan_t plan, int* n0, int* nsub, int* ncoarse, int32_t* first, double* fs,
+                         int32_t* coarse_delays, int32_t* residuals, int64_t* block_len);
+
 /* ---- dedispersion: Sec. 2.3, the brute-force sum over channels ---------- *
  *     Y[d][t] = sum_{c} X[c][t + D[d][c]],   0 <= t < nout = nsamp - Dmax
  * exact in int32 (requires 255 * nchan < 2^31).

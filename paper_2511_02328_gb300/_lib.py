@@ -53,6 +53,8 @@ SIGNATURES = {
     "af_last_error": [],
     "af_version": [],
     "af_plan": [_P, _I, _D, _D, _D, _P, _I],
+    "af_plan_subband": [_P, _I, _D, _D, _D, _P, _I, _I, _I, _I, _I64],
+    "af_plan_subband_info": [_P, _P, _P, _P, _P, _P, _P, _P, _P],
     "af_plan_destroy": [_P],
     "af_plan_delays": [_P, _P, _P],
     "af_plan_info": [_P, _P, _P, _P, _P],
@@ -144,6 +146,35 @@ def af_plan(nchan, f_lo, f_hi, tsamp, dm_list):
     _check(lib().af_plan(ctypes.byref(h), int(nchan), float(f_lo), float(f_hi), float(tsamp), pd, int(dms.size)),
            "af_plan")
     return h.value
+
+
+AF_FS_MEDIAN = 0
+AF_FS_INVSQ = 1
+
+
+def af_plan_subband(nchan, f_lo, f_hi, tsamp, dm_list, n0, nsub, fs_mode=AF_FS_INVSQ, block_len=0):
+    dms, pd = _host(dm_list, np.float64)
+    h = _P()
+    _check(lib().af_plan_subband(ctypes.byref(h), int(nchan), float(f_lo), float(f_hi), float(tsamp), pd,
+                                 int(dms.size), int(n0), int(nsub), int(fs_mode), int(block_len)),
+           "af_plan_subband")
+    return h.value
+
+
+def af_plan_subband_info(plan):
+    """dict(n0, nsub, ncoarse, first, F, Dc, R, block_len) of a subband plan."""
+    nchan, ndm, _, _ = af_plan_info(plan)
+    n0, nsub, ncoarse, L = _I(), _I(), _I(), _I64()
+    _check(lib().af_plan_subband_info(plan, ctypes.byref(n0), ctypes.byref(nsub), ctypes.byref(ncoarse), None,
+                                      None, None, None, ctypes.byref(L)), "af_plan_subband_info")
+    first = np.empty(nsub.value + 1, dtype=np.int32)
+    F = np.empty(nsub.value, dtype=np.float64)
+    Dc = np.empty((ncoarse.value, nchan), dtype=np.int32)
+    R = np.empty((ndm, nsub.value), dtype=np.int32)
+    _check(lib().af_plan_subband_info(plan, None, None, None, first.ctypes.data_as(_P), F.ctypes.data_as(_P),
+                                      Dc.ctypes.data_as(_P), R.ctypes.data_as(_P), None), "af_plan_subband_info")
+    return dict(n0=n0.value, nsub=nsub.value, ncoarse=ncoarse.value, first=first, F=F, Dc=Dc, R=R,
+                block_len=L.value)
 
 
 def af_plan_destroy(plan):

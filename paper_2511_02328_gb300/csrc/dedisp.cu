@@ -205,6 +205,10 @@ size_t af_tile_smem(int nw, int rw)
 int af_launch_dedisperse(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,
                          af_rowstats_t* d_stats, cudaStream_t s)
 {
+    // subband plans: the two stages, unless forced onto (or left to) the
+    // brute-force kernels, which compute the same plane from the effective delays
+    if (p->sb_nsub > 0 && p->sb.tile.fits && !p->force_simple && !p->force_brute)
+        return af_launch_subband(p, d_in, nsamp, nout, d_plane, d_stats, s);
     if (p->tile.fits && !p->force_simple) {
         if (d_stats)
             if (int rc = af_cuda_check(cudaMemsetAsync(d_stats, 0, (size_t)p->ndm * sizeof(af_rowstats_t), s),

@@ -53,6 +53,22 @@ int af_tile_tables_build(const int32_t* delays, const double* dms, int ndm, int 
 void af_tile_tables_free(af_tile_tables* t);
 size_t af_tile_smem(int nw, int rw);
 
+// ---------------------------------------------------------------- subband
+// Device side of a two-stage subband plan (Sec. 2.3): stage-1 tile tables
+// over the coarse DMs (staggered delays), the stagger and partition tables,
+// the residual shifts and the stage-1 scratch I [ncoarse][nsub][ipitch].
+struct af_sb_device {
+    af_tile_tables tile;           // stage-1 tables (rows = coarse DMs)
+    int32_t* d_stag = nullptr;     // [ndm_pad][nsub]
+    int32_t* d_first = nullptr;    // [nsub+1]
+    int32_t* d_r = nullptr;        // [ndm][nsub] residual shifts
+    void* d_I = nullptr;           // stage-1 scratch
+    bool i16 = false;              // I holds uint16 (every subband <= 257 channels)
+    int64_t ipitch = 0;            // elements per I row
+    int32_t maxstag = 0;           // largest stagger
+    int cps = 0;                   // 32-channel chunks per subband
+};
+
 // ---------------------------------------------------------------- plan
 struct af_plan_s {
     int nchan = 0;
@@ -69,6 +85,20 @@ struct af_plan_s {
     af_tile_tables tile;                   // tables of the tile dedispersion kernel
     int* d_err = nullptr;                  // device error flag (bounded waits that ran out)
     bool force_simple = false;             // use the fallback kernel (AFGB_DEDISP_KERNEL=simple)
+    bool force_brute = false;              // subband plans: brute-force tile kernel on the
+                                           // effective delays (AFGB_DEDISP_KERNEL=brute)
+
+    // two-stage subband dedispersion (sb_nsub > 0); `delays` then holds the
+    // effective table D[j(m)][c] + R[m][s(c)]
+    int sb_n0 = 0, sb_nsub = 0, sb_ncoarse = 0, sb_mode = 0;
+    int64_t sb_L = 0;                      // stage-2 outputs per time block
+    int32_t sb_rmax = 0;                   // largest residual shift
+    std::vector<int32_t> sb_first;         // [nsub+1]
+    std::vector<double> sb_F;              // [nsub] representative frequencies
+    std::vector<double> sb_cdms;           // [ncoarse] coarse DMs
+    std::vector<int32_t> sb_dc;            // [ncoarse][nchan] coarse delays
+    std::vector<int32_t> sb_r;             // [ndm][nsub] residual shifts
+    af_sb_device sb;
     af_rowstats_t* d_stats = nullptr;      // [ndm] scratch
     af_rowconst_t* d_rowconst = nullptr;   // [ndm][AF_MAX_WIDTHS] scratch
 
@@ -99,3 +129,9 @@ int af_launch_candidates(const float* d_best_snr, const uint8_t* d_best_w, int n
                          const af_widths_t& w, float thresh, int64_t sample0, af_cand_t* d_out,
                          int32_t cap, int32_t* d_count, cudaStream_t s);
 int af_prepare_dedisp_tables(af_plan_t p);
+// Subband plans: builds the device tables and the scratch (af_plan_subband);
+// frees them (plan destruction); launches stage 1 + stage 2 per time block.
+int af_sb_prepare(af_plan_t p);
+void af_sb_free(af_plan_t p);
+int af_launch_subband(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,
+                      af_rowstats_t* d_stats, cudaStream_t s);

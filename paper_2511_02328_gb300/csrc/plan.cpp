@@ -77,6 +77,7 @@ static void free_plan(af_plan_t p)
     if (cur != p->device) cudaSetDevice(p->device);
     cudaFree(p->d_delays);
     af_tile_tables_free(&p->tile);
+    af_sb_free(p);
     cudaFree(p->d_err);
     cudaFree(p->d_stats);
     cudaFree(p->d_rowconst);
@@ -85,82 +86,235 @@ static void free_plan(af_plan_t p)
     delete p;
 }
 
-extern "C" int af_plan(af_plan_t* out, int nchan, double f_lo, double f_hi, double tsamp,
-                       const double* dm_list, int ndm)
+static int check_plan_args(const char* who, int nchan, double f_lo, double f_hi, double tsamp,
+                           const double* dm_list, int ndm)
 {
-    if (!out) return af_set_error(AF_EINVAL, "af_plan: out is NULL");
-    *out = nullptr;
-    if (nchan < 1 || nchan > 65536) return af_set_error(AF_EINVAL, "af_plan: nchan %d out of range", nchan);
-    if (ndm < 1 || ndm > (1 << 20)) return af_set_error(AF_EINVAL, "af_plan: ndm %d out of range", ndm);
-    if (!dm_list) return af_set_error(AF_EINVAL, "af_plan: dm_list is NULL");
+    if (nchan < 1 || nchan > 65536) return af_set_error(AF_EINVAL, "%s: nchan %d out of range", who, nchan);
+    if (ndm < 1 || ndm > (1 << 20)) return af_set_error(AF_EINVAL, "%s: ndm %d out of range", who, ndm);
+    if (!dm_list) return af_set_error(AF_EINVAL, "%s: dm_list is NULL", who);
     if (!(f_lo > 0.0) || !(f_hi > 0.0) || f_lo == f_hi || !isfinite(f_lo) || !isfinite(f_hi))
-        return af_set_error(AF_EINVAL, "af_plan: bad band edges %g %g", f_lo, f_hi);
-    if (!(tsamp > 0.0) || !isfinite(tsamp)) return af_set_error(AF_EINVAL, "af_plan: bad tsamp %g", tsamp);
+        return af_set_error(AF_EINVAL, "%s: bad band edges %g %g", who, f_lo, f_hi);
+    if (!(tsamp > 0.0) || !isfinite(tsamp)) return af_set_error(AF_EINVAL, "%s: bad tsamp %g", who, tsamp);
     for (int d = 0; d < ndm; d++)
         if (!(dm_list[d] >= 0.0) || !isfinite(dm_list[d]))
-            return af_set_error(AF_EINVAL, "af_plan: dm_list[%d] = %g is not a finite value >= 0", d, dm_list[d]);
+            return af_set_error(AF_EINVAL, "%s: dm_list[%d] = %g is not a finite value >= 0", who, d, dm_list[d]);
+    return AF_OK;
+}
 
+// Channel-centre frequency and reference frequency (top band edge).
+static double chan_freq(int c, int nchan, double f_lo, double f_hi)
+{
+    const double df = (f_hi - f_lo) / (double)nchan;
+    return f_lo + ((double)c + 0.5) * df;
+}
+
+// Eq. (coarse_delay) for a list of DMs: D = round(K*DM/tsamp * (1/fc^2 - 1/fref^2)),
+// channel centres, f_ref = top band edge, round half away from zero.
+static int delay_rows(const char* who, int nchan, double f_lo, double f_hi, double tsamp, const double* dms,
+                      int n, int32_t* out, int32_t* dmax)
+{
+    const double fr = f_lo > f_hi ? f_lo : f_hi;
+    std::vector<double> bterm(nchan);
+    for (int c = 0; c < nchan; c++) {
+        const double fc = chan_freq(c, nchan, f_lo, f_hi);
+        bterm[c] = 1.0 / (fc * fc) - 1.0 / (fr * fr);
+    }
+    int32_t mx = 0;
+    for (int d = 0; d < n; d++) {
+        const double a = (kKDM * dms[d]) / tsamp;
+        for (int c = 0; c < nchan; c++) {
+            const double x = a * bterm[c];
+            if (!(x < 2147483647.0))
+                return af_set_error(AF_EINVAL, "%s: delay of dm %g channel %d exceeds int32", who, dms[d], c);
+            const int32_t D = (int32_t)llround(x);
+            out[(size_t)d * nchan + c] = D;
+            mx = D > mx ? D : mx;
+        }
+    }
+    if (dmax) *dmax = mx;
+    return AF_OK;
+}
+
+static af_plan_s* new_plan(int nchan, double f_lo, double f_hi, double tsamp, const double* dm_list, int ndm)
+{
     af_plan_s* p = new (std::nothrow) af_plan_s();
-    if (!p) return af_set_error(AF_ENOMEM, "af_plan: host allocation failed");
+    if (!p) return nullptr;
     p->nchan = nchan;
     p->ndm = ndm;
     p->f_lo = f_lo;
     p->f_hi = f_hi;
     p->tsamp = tsamp;
-    p->dms.assign(dm_list, dm_list + ndm);
     try {
+        p->dms.assign(dm_list, dm_list + ndm);
         p->delays.resize((size_t)ndm * nchan);
     } catch (...) {
         delete p;
-        return af_set_error(AF_ENOMEM, "af_plan: host allocation of the delay table failed");
+        return nullptr;
     }
+    return p;
+}
 
-    // Eq. (coarse_delay): D = round(K*DM/tsamp * (1/fc^2 - 1/fref^2)),
-    // channel centres, f_ref = top band edge, round half away from zero.
-    const double fr = f_lo > f_hi ? f_lo : f_hi;
-    const double df = (f_hi - f_lo) / (double)nchan;
-    std::vector<double> bterm(nchan);
-    for (int c = 0; c < nchan; c++) {
-        double fc = f_lo + ((double)c + 0.5) * df;
-        bterm[c] = 1.0 / (fc * fc) - 1.0 / (fr * fr);
-    }
-    int32_t dmax = 0;
-    for (int d = 0; d < ndm; d++) {
-        double a = (kKDM * dm_list[d]) / tsamp;
-        for (int c = 0; c < nchan; c++) {
-            double x = a * bterm[c];
-            if (!(x < 2147483647.0)) {
-                delete p;
-                return af_set_error(AF_EINVAL, "af_plan: delay of dm %g channel %d exceeds int32", dm_list[d], c);
-            }
-            int32_t D = (int32_t)llround(x);
-            p->delays[(size_t)d * nchan + c] = D;
-            dmax = D > dmax ? D : dmax;
-        }
-    }
-    p->dmax = dmax;
-
+// Device side common to every plan: table upload, scratch, tile tables.
+// Frees the plan on failure.
+static int plan_finish(af_plan_s* p, const char* who)
+{
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) {
         delete p;
-        return af_cuda_check(e, "af_plan: cudaGetDevice");
+        return af_cuda_check(e, who);
     }
     cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
-    if (const char* k = getenv("AFGB_DEDISP_KERNEL")) p->force_simple = strcmp(k, "simple") == 0;
-    size_t tbytes = (size_t)ndm * nchan * sizeof(int32_t);
+    if (const char* k = getenv("AFGB_DEDISP_KERNEL")) {
+        p->force_simple = strcmp(k, "simple") == 0;
+        p->force_brute = strcmp(k, "brute") == 0;
+    }
+    const size_t tbytes = (size_t)p->ndm * p->nchan * sizeof(int32_t);
     int rc = AF_OK;
     if ((e = cudaMalloc(&p->d_delays, tbytes)) != cudaSuccess ||
         (e = cudaMemcpy(p->d_delays, p->delays.data(), tbytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMalloc(&p->d_stats, (size_t)ndm * sizeof(af_rowstats_t))) != cudaSuccess ||
-        (e = cudaMalloc(&p->d_rowconst, (size_t)ndm * AF_MAX_WIDTHS * sizeof(af_rowconst_t))) != cudaSuccess) {
-        rc = af_cuda_check(e, "af_plan: device allocation/upload");
+        (e = cudaMalloc(&p->d_stats, (size_t)p->ndm * sizeof(af_rowstats_t))) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_rowconst, (size_t)p->ndm * AF_MAX_WIDTHS * sizeof(af_rowconst_t))) != cudaSuccess) {
+        rc = af_cuda_check(e, "plan: device allocation/upload");
     }
     if (rc == AF_OK) rc = af_prepare_dedisp_tables(p);
-    if (rc != AF_OK) {
-        free_plan(p);
+    if (rc == AF_OK && p->sb_nsub > 0) rc = af_sb_prepare(p);
+    if (rc != AF_OK) free_plan(p);
+    return rc;
+}
+
+extern "C" int af_plan(af_plan_t* out, int nchan, double f_lo, double f_hi, double tsamp,
+                       const double* dm_list, int ndm)
+{
+    if (!out) return af_set_error(AF_EINVAL, "af_plan: out is NULL");
+    *out = nullptr;
+    if (int rc = check_plan_args("af_plan", nchan, f_lo, f_hi, tsamp, dm_list, ndm)) return rc;
+    af_plan_s* p = new_plan(nchan, f_lo, f_hi, tsamp, dm_list, ndm);
+    if (!p) return af_set_error(AF_ENOMEM, "af_plan: host allocation failed");
+    if (int rc = delay_rows("af_plan", nchan, f_lo, f_hi, tsamp, dm_list, ndm, p->delays.data(), &p->dmax)) {
+        delete p;
         return rc;
     }
+    if (int rc = plan_finish(p, "af_plan")) return rc;
     *out = p;
+    return AF_OK;
+}
+
+// Representative frequency of channels [c0, c1), Sec. 2.3: the median of the
+// channel centres (mean of the two middle ones for an even count), or the
+// frequency whose 1/F^2 is the mean of 1/f_c^2.
+static double subband_freq(int nchan, double f_lo, double f_hi, int c0, int c1, int mode)
+{
+    const int n = c1 - c0;
+    if (mode == AF_FS_MEDIAN) {
+        std::vector<double> f(n);
+        for (int i = 0; i < n; i++) f[i] = chan_freq(c0 + i, nchan, f_lo, f_hi);
+        std::sort(f.begin(), f.end());
+        return (n % 2) ? f[n / 2] : 0.5 * (f[n / 2 - 1] + f[n / 2]);
+    }
+    double acc = 0.0;
+    for (int c = c0; c < c1; c++) {
+        const double fc = chan_freq(c, nchan, f_lo, f_hi);
+        acc += 1.0 / (fc * fc);
+    }
+    return 1.0 / sqrt(acc / (double)n);
+}
+
+extern "C" int af_plan_subband(af_plan_t* out, int nchan, double f_lo, double f_hi, double tsamp,
+                               const double* dm_list, int ndm, int n0, int nsub, int fs_mode, int64_t block_len)
+{
+    static const char* who = "af_plan_subband";
+    if (!out) return af_set_error(AF_EINVAL, "%s: out is NULL", who);
+    *out = nullptr;
+    if (int rc = check_plan_args(who, nchan, f_lo, f_hi, tsamp, dm_list, ndm)) return rc;
+    if (n0 < 1 || n0 > 32) return af_set_error(AF_EINVAL, "%s: n0 %d not in 1..32", who, n0);
+    if (nsub < 1 || nsub > nchan) return af_set_error(AF_EINVAL, "%s: nsub %d not in 1..nchan", who, nsub);
+    if (fs_mode != AF_FS_MEDIAN && fs_mode != AF_FS_INVSQ)
+        return af_set_error(AF_EINVAL, "%s: unknown fs_mode %d", who, fs_mode);
+    if (block_len < 0 || block_len > ((int64_t)1 << 30))
+        return af_set_error(AF_EINVAL, "%s: block_len %lld out of range", who, (long long)block_len);
+    for (int m = 1; m < ndm; m++)
+        if (!(dm_list[m] >= dm_list[m - 1]))
+            return af_set_error(AF_EINVAL, "%s: dm_list must be non-decreasing (entry %d)", who, m);
+    af_plan_s* p = new_plan(nchan, f_lo, f_hi, tsamp, dm_list, ndm);
+    if (!p) return af_set_error(AF_ENOMEM, "%s: host allocation failed", who);
+    p->sb_n0 = n0;
+    p->sb_nsub = nsub;
+    p->sb_mode = fs_mode;
+    p->sb_ncoarse = (ndm + n0 - 1) / n0;
+    try {
+        // partition: subband s = channels [floor(s*nchan/nsub), floor((s+1)*nchan/nsub))
+        p->sb_first.resize(nsub + 1);
+        for (int s = 0; s <= nsub; s++) p->sb_first[s] = (int32_t)(((int64_t)s * nchan) / nsub);
+        p->sb_F.resize(nsub);
+        for (int s = 0; s < nsub; s++)
+            p->sb_F[s] = subband_freq(nchan, f_lo, f_hi, p->sb_first[s], p->sb_first[s + 1], fs_mode);
+        // coarse DMs dm_list[j*n0] and their delays, Eq. (coarse_delay)
+        p->sb_cdms.resize(p->sb_ncoarse);
+        for (int j = 0; j < p->sb_ncoarse; j++) p->sb_cdms[j] = dm_list[j * n0];
+        p->sb_dc.resize((size_t)p->sb_ncoarse * nchan);
+        p->sb_r.resize((size_t)ndm * nsub);
+    } catch (...) {
+        delete p;
+        return af_set_error(AF_ENOMEM, "%s: host allocation failed", who);
+    }
+    if (int rc = delay_rows(who, nchan, f_lo, f_hi, tsamp, p->sb_cdms.data(), p->sb_ncoarse, p->sb_dc.data(),
+                            nullptr)) {
+        delete p;
+        return rc;
+    }
+    // residual shifts, Eq. (residual): R = round(K*dDM/tsamp * (1/F_s^2 - 1/fref^2))
+    const double fr = f_lo > f_hi ? f_lo : f_hi;
+    int32_t rmax = 0;
+    for (int s = 0; s < nsub; s++) {
+        const double F = p->sb_F[s];
+        const double b = 1.0 / (F * F) - 1.0 / (fr * fr);
+        for (int m = 0; m < ndm; m++) {
+            const double ddm = dm_list[m] - dm_list[(m / n0) * n0];
+            const double a = (kKDM * ddm) / tsamp;
+            const double x = a * b;
+            if (!(x < 2147483647.0)) {
+                delete p;
+                return af_set_error(AF_EINVAL, "%s: residual shift of dm %g exceeds int32", who, dm_list[m]);
+            }
+            const int32_t r = (int32_t)llround(x);
+            p->sb_r[(size_t)m * nsub + s] = r;
+            rmax = r > rmax ? r : rmax;
+        }
+    }
+    p->sb_rmax = rmax;
+    // effective delay table Deff[m][c] = D[j(m)][c] + R[m][s(c)]
+    int32_t dmax = 0;
+    for (int s = 0; s < nsub; s++)
+        for (int c = p->sb_first[s]; c < p->sb_first[s + 1]; c++)
+            for (int m = 0; m < ndm; m++) {
+                const int64_t v = (int64_t)p->sb_dc[(size_t)(m / n0) * nchan + c] + p->sb_r[(size_t)m * nsub + s];
+                if (v > INT32_MAX) {
+                    delete p;
+                    return af_set_error(AF_EINVAL, "%s: effective delay exceeds int32", who);
+                }
+                p->delays[(size_t)m * nchan + c] = (int32_t)v;
+                dmax = (int32_t)v > dmax ? (int32_t)v : dmax;
+            }
+    p->dmax = dmax;
+    p->sb_L = block_len;
+    if (int rc = plan_finish(p, who)) return rc;
+    *out = p;
+    return AF_OK;
+}
+
+extern "C" int af_plan_subband_info(af_plan_t p, int* n0, int* nsub, int* ncoarse, int32_t* first, double* fs,
+                                    int32_t* coarse_delays, int32_t* residuals, int64_t* block_len)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    if (p->sb_nsub == 0) return af_set_error(AF_EINVAL, "af_plan_subband_info: not a subband plan");
+    if (n0) *n0 = p->sb_n0;
+    if (nsub) *nsub = p->sb_nsub;
+    if (ncoarse) *ncoarse = p->sb_ncoarse;
+    if (first) memcpy(first, p->sb_first.data(), p->sb_first.size() * sizeof(int32_t));
+    if (fs) memcpy(fs, p->sb_F.data(), p->sb_F.size() * sizeof(double));
+    if (coarse_delays) memcpy(coarse_delays, p->sb_dc.data(), p->sb_dc.size() * sizeof(int32_t));
+    if (residuals) memcpy(residuals, p->sb_r.data(), p->sb_r.size() * sizeof(int32_t));
+    if (block_len) *block_len = p->sb_L;
     return AF_OK;
 }
 

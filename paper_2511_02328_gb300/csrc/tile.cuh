@@ -24,6 +24,16 @@
 //     E += w & 0x00FF00FF            (bytes 0 and 2; one LOP3)
 //     O += prmt(w, 0, 0x4341)        (bytes 1 and 3; one PRMT)
 // two channels per IADD3.
+//
+// Subband mode (SUB = true; stage 1 of the two-stage subband dedispersion,
+// Eq. stage1): the rows are coarse DMs, the channels are taken subband after
+// subband (cps chunks of 32 per subband, short chunks padded), and at the end
+// of every subband the warp folds and stores its partial sums
+//     I(j, s, u) = sum_{c in s} X[c][u + D[j][c]]
+// as one row of a scratch array.  The table delays are the coarse delays
+// minus a per-(row, subband) stagger stag[j][s] = D[j][c_top(s)] - min over
+// the block's rows of the same, so the delay spread inside a block is only
+// the within-subband dispersion; the warp's output u is then t - stag[j][s].
 #pragma once
 
 #include <cuda_runtime.h>
@@ -59,6 +69,16 @@ struct TileArgs {
     int32_t* Y;
     af_rowstats_t* stats;   // may be NULL
     int* err;
+    // subband mode only
+    int cps;                // chunks per subband
+    int nsub;
+    const int32_t* sbfirst; // [nsub+1] first channel of each subband
+    const int32_t* stag;    // [ndm_pad][nsub] stagger of each row and subband
+    void* I;                // [nrows][nsub][ipitch] uint16 or uint32 partial sums
+    int i16;                // I holds uint16
+    int64_t ipitch;         // elements per I row
+    int64_t li;             // valid outputs per I row in this launch
+    int64_t tbase;          // time of tile 0 (the time block's first output)
 };
 
 __host__ __device__ constexpr int tte_of(int M) { return 128 * M - 4; }
@@ -80,7 +100,7 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return m;
 }
 
-template <int NW, int M>
+template <int NW, int M, bool SUB = false>
 struct Tile {
     static constexpr int NT = (NW + 1) * 32;  // + one producer warp
     static constexpr int TTE = tte_of(M);
@@ -91,10 +111,30 @@ struct Tile {
         int dl[NW];
     };
 
+    // Channel of producer lane `lane` in chunk kk, and whether it exists.
+    static __device__ __forceinline__ int chan_of(const TileArgs& a, int kk, int lane, bool& valid)
+    {
+        if constexpr (SUB) {
+            const int s = kk / a.cps;
+            if (kk >= a.nchunks) {
+                valid = false;
+                return 0;
+            }
+            const int c = __ldg(a.sbfirst + s) + (kk - s * a.cps) * CC + lane;
+            valid = c < __ldg(a.sbfirst + s + 1);
+            return c;
+        } else {
+            const int c = kk * CC + lane;
+            valid = kk < a.nchunks && c < a.nchan;
+            return c;
+        }
+    }
+
     static __device__ __forceinline__ void load_chunk(const TileArgs& a, ChunkIn& in, int kk, int jb, int lane)
     {
-        const int c = kk * CC + lane;
-        if (kk < a.nchunks && c < a.nchan) {
+        bool valid;
+        const int c = chan_of(a, kk, lane, valid);
+        if (valid) {
             in.dmin = __ldg(a.dminblk + (int64_t)jb * a.nchan + c);
 #pragma unroll
             for (int w = 0; w < NW; w++) in.dl[w] = __ldg(a.dsort + (int64_t)(jb * NW + w) * a.nchan + c);
@@ -112,13 +152,14 @@ struct Tile {
                                                          uint32_t full_bar, const ChunkIn& in, int kk, int st,
                                                          int64_t t0, int lane)
     {
-        const int c = kk * CC + lane;
-        const bool valid = c < a.nchan;
+        bool valid;
+        const int c = chan_of(a, kk, lane, valid);
         int64_t start = 0;
         uint32_t bulk = 0, tail = 0;
         if (valid) {
             start = ((int64_t)c * a.nsamp + t0 + in.dmin) & ~(int64_t)15;
-            const int64_t want = min((int64_t)a.rw, a.total - start);
+            int64_t want = min((int64_t)a.rw, a.total - start);
+            if constexpr (SUB) want = max((int64_t)0, want);  // staggered tiles may start past the data
             bulk = (uint32_t)(want & ~(int64_t)15);
             tail = (uint32_t)(want - bulk);
         }
@@ -214,6 +255,37 @@ struct Tile {
         }
     }
 
+    // Subband mode: writes this warp's sums of subband s as I(row, s, u) with
+    // u = t0 - tbase + pos - stag[drow][s], for 0 <= u < li, and clears them.
+    static __device__ __forceinline__ void store_subband(const TileArgs& a, int drow, int s, int64_t t0,
+                                                         uint32_t (&Wd)[M][4], int lane)
+    {
+        const int orow = __ldg(a.perm + drow);
+        if (orow >= 0) {
+            const int64_t ub = t0 - a.tbase - (int64_t)__ldg(a.stag + (int64_t)drow * a.nsub + s);
+            const int64_t rowoff = ((int64_t)orow * a.nsub + s) * a.ipitch;
+#pragma unroll
+            for (int m = 0; m < M; m++) {
+                const int pos0 = 4 * (lane + 32 * m);
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const int pos = pos0 + k;
+                    const int64_t u = ub + pos;
+                    if (pos < TTE && u >= 0 && u < a.li) {
+                        if (a.i16)
+                            reinterpret_cast<uint16_t*>(a.I)[rowoff + u] = (uint16_t)Wd[m][k];
+                        else
+                            reinterpret_cast<uint32_t*>(a.I)[rowoff + u] = Wd[m][k];
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < M; m++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) Wd[m][k] = 0u;
+    }
+
     // The whole block computes tile (jb, t0) of job a.  Every thread returns.
     static __device__ __forceinline__ void run(const TileArgs& a, unsigned jb, int64_t t0, uint8_t* smem)
     {
@@ -265,6 +337,7 @@ struct Tile {
             for (int k = 0; k < 4; k++) Wd[m][k] = 0u;
         }
         const uint32_t lane4 = (uint32_t)lane * 4u;
+        int sb = 0, sq = 0;  // subband mode: current subband and chunk within it
         for (int kk = 0; kk < a.nchunks; kk++) {
             const int st = kk % NSTAGE;
             if (!afptx::mbar_wait_bounded(full0 + 8 * st, (uint32_t)(kk / NSTAGE) & 1u, WAIT_LIMIT)) {
@@ -312,8 +385,21 @@ struct Tile {
             }
             __syncwarp();
             if (lane == 0) afptx::mbar_arrive(empty0 + 8 * st);  // this warp is done with stage st
-            if ((kk % FLUSH_CHUNKS) == FLUSH_CHUNKS - 1 || kk == a.nchunks - 1) fold(E, O, Wd, lane);
+            if constexpr (SUB) {
+                const bool last = sq == a.cps - 1;
+                if ((sq % FLUSH_CHUNKS) == FLUSH_CHUNKS - 1 || last) fold(E, O, Wd, lane);
+                if (last) {
+                    store_subband(a, drow, sb, t0, Wd, lane);
+                    sq = 0;
+                    sb++;
+                } else {
+                    sq++;
+                }
+            } else {
+                if ((kk % FLUSH_CHUNKS) == FLUSH_CHUNKS - 1 || kk == a.nchunks - 1) fold(E, O, Wd, lane);
+            }
         }
+        if constexpr (SUB) return;
 
         // ---- outputs and fused row sums
         const int orow = a.perm[drow];
@@ -357,6 +443,17 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) k_tile(const TileArgs a)
     const unsigned jb = blockIdx.x % a.nblk;
     const int64_t t0 = (int64_t)(blockIdx.x / a.nblk) * Tile<NW, M>::TTE;
     Tile<NW, M>::run(a, jb, t0, smem);
+}
+
+// Stage 1 of the subband dedispersion: grid = tiles x row blocks, tile 0
+// starting at a.tbase.
+template <int NW, int M>
+__global__ void __launch_bounds__((NW + 1) * 32, 1) k_tile_sb(const TileArgs a)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const unsigned jb = blockIdx.x % a.nblk;
+    const int64_t t0 = a.tbase + (int64_t)(blockIdx.x / a.nblk) * Tile<NW, M, true>::TTE;
+    Tile<NW, M, true>::run(a, jb, t0, smem);
 }
 
 // Persistent multi-job kernel: each block takes work items (job, DM block,

@@ -28,10 +28,20 @@ def device_view(ptr, shape, dtype):
 class Plan:
     """Delay-table plan (Eq. coarse_delay, Sec. 2.3) on the current device."""
 
-    def __init__(self, nchan, f_lo, f_hi, tsamp, dm_list):
+    def __init__(self, nchan, f_lo, f_hi, tsamp, dm_list, subband=None):
+        """subband=None: brute-force plan; subband=dict(n0=, nsub=, fs_mode=, block_len=):
+        two-stage subband plan (Sec. 2.3, af_plan_subband)."""
         self.dm_list = np.ascontiguousarray(dm_list, dtype=np.float64)
-        self.handle = _lib.af_plan(nchan, f_lo, f_hi, tsamp, self.dm_list)
+        if subband is None:
+            self.handle = _lib.af_plan(nchan, f_lo, f_hi, tsamp, self.dm_list)
+        else:
+            self.handle = _lib.af_plan_subband(nchan, f_lo, f_hi, tsamp, self.dm_list, subband["n0"],
+                                               subband["nsub"], subband.get("fs_mode", _lib.AF_FS_INVSQ),
+                                               subband.get("block_len", 0))
         self.nchan, self.ndm, self.dmax, self.tsamp = _lib.af_plan_info(self.handle)
+
+    def subband_info(self):
+        return _lib.af_plan_subband_info(self.handle)
 
     def close(self):
         if self.handle:
