@@ -66,6 +66,9 @@ def lib():
         L.oracle_subband_dedisperse.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
                                                 ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                                 ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p]
+        L.oracle_downsample_sqlaw.restype = ctypes.c_int
+        L.oracle_downsample_sqlaw.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_void_p]
         _lib = L
     return _lib
 
@@ -233,6 +236,16 @@ def subband_dedisperse(X, tab, nout=None):
     if rc != 0:
         raise ValueError("oracle_subband_dedisperse failed (%d)" % rc)
     return Y
+
+
+def downsample_sqlaw(X, D, vmax=255):
+    """Square-law downsampling by D (Sec. 2.2), uint8 [nchan][ceil(nsamp/D)]."""
+    X = np.ascontiguousarray(X, dtype=np.uint8)
+    nchan, nsamp = X.shape
+    out = np.empty((nchan, (nsamp + D - 1) // D), dtype=np.uint8)
+    if lib().oracle_downsample_sqlaw(_ptr(X), nchan, nsamp, int(D), int(vmax), _ptr(out)) != 0:
+        raise ValueError("oracle_downsample_sqlaw: bad arguments")
+    return out
 
 
 def threads():

@@ -392,3 +392,54 @@ int oracle_subband_dedisperse(const uint8_t* X, int nchan, int64_t nsamp, const 
     }
     return 0;
 }
+
+/* ======================================================================
+ * Square-law time downsampling (Sec. 2.2, "Downsampling and Subband
+ * Combination").
+ * ====================================================================== */
+
+/* For each channel and each bin k of D consecutive samples (the last bin
+ * holds the remaining nsamp - (nout-1)*D samples, nout = ceil(nsamp/D), the
+ * paper's N_t = ceil(N_t/D)), with S the sum of the bin's N samples:
+ *     out = min( V * sqrt(S) / sqrt(N*V), V ) = min( sqrt(V*S/N), V ).
+ * Reading (the paper does not say how the value becomes an integer of the
+ * chosen bit width): round to nearest, halves up, evaluated exactly in integer
+ * arithmetic: round(sqrt(q)) = floor((isqrt(floor(4q)) + 1) / 2) for q >= 0,
+ * with 4q = 4*V*S/N.  V = vmax (255 for 8-bit data).
+ * X uint8 [nchan][nsamp]; out uint8 [nchan][ceil(nsamp/D)].
+ * Returns 0, or -1 on invalid arguments.                                     */
+static uint64_t isqrt_u64(uint64_t x)
+{
+    uint64_t r = 0, bit = (uint64_t)1 << 62;
+    while (bit > x) bit >>= 2;
+    while (bit) {
+        if (x >= r + bit) {
+            x -= r + bit;
+            r = (r >> 1) + bit;
+        } else {
+            r >>= 1;
+        }
+        bit >>= 2;
+    }
+    return r;
+}
+
+int oracle_downsample_sqlaw(const uint8_t* X, int nchan, int64_t nsamp, int D, int vmax, uint8_t* out)
+{
+    if (nchan <= 0 || nsamp <= 0 || D <= 0 || vmax <= 0 || vmax > 255)
+        return -1;
+    int64_t nout = (nsamp + D - 1) / D;
+    for (int c = 0; c < nchan; c++) {
+        const uint8_t* x = X + (int64_t)c * nsamp;
+        for (int64_t k = 0; k < nout; k++) {
+            int64_t t0 = k * D, t1 = t0 + D < nsamp ? t0 + D : nsamp;
+            uint64_t S = 0, N = (uint64_t)(t1 - t0);
+            for (int64_t t = t0; t < t1; t++)
+                S += x[t];
+            uint64_t r = isqrt_u64((4u * (uint64_t)vmax * S) / N);
+            uint64_t v = (r + 1) / 2;
+            out[(int64_t)c * nout + k] = (uint8_t)(v < (uint64_t)vmax ? v : (uint64_t)vmax);
+        }
+    }
+    return 0;
+}
