@@ -69,6 +69,15 @@ def lib():
         L.oracle_downsample_sqlaw.restype = ctypes.c_int
         L.oracle_downsample_sqlaw.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
                                               ctypes.c_int, ctypes.c_void_p]
+        L.oracle_zerodm.restype = ctypes.c_int
+        L.oracle_zerodm.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p]
+        L.oracle_row_robust.restype = None
+        L.oracle_row_robust.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                        ctypes.c_void_p]
+        L.oracle_boxcar_snr_norm.restype = None
+        L.oracle_boxcar_snr_norm.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                             ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p]
         _lib = L
     return _lib
 
@@ -246,6 +255,48 @@ def downsample_sqlaw(X, D, vmax=255):
     if lib().oracle_downsample_sqlaw(_ptr(X), nchan, nsamp, int(D), int(vmax), _ptr(out)) != 0:
         raise ValueError("oracle_downsample_sqlaw: bad arguments")
     return out
+
+
+MAD_TO_SIGMA = 1.482602218505602   # sigma / MAD for a normal distribution
+
+
+def zerodm(X):
+    """Zero-DM filter (reading: channel mean rounded half up, re-centred at 128, clipped)."""
+    X = np.ascontiguousarray(X, dtype=np.uint8)
+    out = np.empty_like(X)
+    if lib().oracle_zerodm(_ptr(X), X.shape[0], X.shape[1], _ptr(out)) != 0:
+        raise ValueError("oracle_zerodm: bad arguments")
+    return out
+
+
+def row_robust(Y):
+    """(median, MAD) of every plane row: lower medians, int64."""
+    Y = np.ascontiguousarray(Y, dtype=np.int32)
+    ndm, nout = Y.shape
+    med = np.empty(ndm, dtype=np.int64)
+    mad = np.empty(ndm, dtype=np.int64)
+    lib().oracle_row_robust(_ptr(Y), ndm, nout, _ptr(med), _ptr(mad))
+    return med, mad
+
+
+def boxcar_snr_norm(Y, widths, mu, sigma):
+    """Boxcar S/N with explicit per-row location and scale."""
+    Y = np.ascontiguousarray(Y, dtype=np.int32)
+    widths = np.ascontiguousarray(widths, dtype=np.int32)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    ndm, nout = Y.shape
+    snr = np.empty((ndm, nout), dtype=np.float64)
+    bw = np.empty((ndm, nout), dtype=np.int32)
+    lib().oracle_boxcar_snr_norm(_ptr(Y), ndm, nout, _ptr(widths), widths.size, _ptr(mu), _ptr(sigma), _ptr(snr),
+                                 _ptr(bw))
+    return snr, bw
+
+
+def boxcar_snr_robust(Y, widths):
+    """Robust S/N: location = median, scale = 1.4826 * MAD of each row."""
+    med, mad = row_robust(Y)
+    return boxcar_snr_norm(Y, widths, med.astype(np.float64), MAD_TO_SIGMA * mad.astype(np.float64))
 
 
 def threads():

@@ -443,3 +443,101 @@ int oracle_downsample_sqlaw(const uint8_t* X, int nchan, int64_t nsamp, int D, i
     }
     return 0;
 }
+
+/* ======================================================================
+ * Zero-DM filter and robust (median/MAD) S/N normalisation (Sec. 2.1 RFI
+ * mitigation; Sec. 4.4 names zero-DM filtering as the remedy for impulsive
+ * broadband RFI).
+ * ====================================================================== */
+
+/* Zero-DM filter: the mean over channels at each time sample (the DM = 0
+ * time series divided by nchan) is removed from every channel.  Readings (the
+ * paper gives no formula): the mean is rounded to nearest, halves up, exactly,
+ *     q[t] = floor((2 * sum_c X[c][t] + nchan) / (2 * nchan)),
+ * and the 8-bit result is re-centred on mid-scale and clipped:
+ *     X'[c][t] = min(255, max(0, X[c][t] - q[t] + 128)).
+ * X and out uint8 [nchan][nsamp] (out may equal X).  Returns 0 or -1.       */
+int oracle_zerodm(const uint8_t* X, int nchan, int64_t nsamp, uint8_t* out)
+{
+    if (nchan <= 0 || nsamp <= 0)
+        return -1;
+    int64_t* q = (int64_t*)malloc(sizeof(int64_t) * nsamp);
+    if (!q)
+        return -1;
+    for (int64_t t = 0; t < nsamp; t++) {
+        int64_t s = 0;
+        for (int c = 0; c < nchan; c++)
+            s += X[(int64_t)c * nsamp + t];
+        q[t] = (2 * s + nchan) / (2 * (int64_t)nchan);
+    }
+    for (int c = 0; c < nchan; c++)
+        for (int64_t t = 0; t < nsamp; t++) {
+            int64_t v = (int64_t)X[(int64_t)c * nsamp + t] - q[t] + 128;
+            out[(int64_t)c * nsamp + t] = (uint8_t)(v < 0 ? 0 : v > 255 ? 255 : v);
+        }
+    free(q);
+    return 0;
+}
+
+static int cmp_i64(const void* a, const void* b)
+{
+    int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+    return (x > y) - (x < y);
+}
+
+/* Robust location and scale of each plane row (reading of the robust S/N
+ * normalisation):  med_d = the lower median of the row (element (nout-1)/2 of
+ * the sorted row), mad_d = the lower median of |Y[d][t] - med_d|.  Both are
+ * integers.  The S/N scale is sigma_d = 1.482602218505602 * mad_d (the MAD of
+ * a normal distribution is sigma / 1.4826...).                              */
+void oracle_row_robust(const int32_t* Y, int ndm, int64_t nout, int64_t* med, int64_t* mad)
+{
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int d = 0; d < ndm; d++) {
+        int64_t* v = (int64_t*)malloc(sizeof(int64_t) * nout);
+        const int32_t* y = Y + (int64_t)d * nout;
+        for (int64_t t = 0; t < nout; t++)
+            v[t] = y[t];
+        qsort(v, nout, sizeof(int64_t), cmp_i64);
+        int64_t m = v[(nout - 1) / 2];
+        for (int64_t t = 0; t < nout; t++)
+            v[t] = y[t] >= m ? y[t] - m : m - y[t];
+        qsort(v, nout, sizeof(int64_t), cmp_i64);
+        med[d] = m;
+        mad[d] = v[(nout - 1) / 2];
+        free(v);
+    }
+}
+
+/* Boxcar S/N with an explicit location mu_d and scale sigma_d per row:
+ *     snr_w = (B_w - w*mu_d) / (sigma_d * sqrt(w))
+ * with the window, validity and tie rules of oracle_boxcar_snr; sigma_d = 0
+ * gives snr 0.  (mu = S/nout and sigma = the population deviation give
+ * oracle_boxcar_snr; mu = med and sigma = 1.4826*mad the robust S/N.)      */
+void oracle_boxcar_snr_norm(const int32_t* Y, int ndm, int64_t nout, const int32_t* widths, int nw,
+                            const double* mu, const double* sigma, double* best_snr, int32_t* best_w)
+{
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int d = 0; d < ndm; d++) {
+        const int32_t* y = Y + (int64_t)d * nout;
+        for (int64_t t = 0; t < nout; t++) {
+            double best = -INFINITY;
+            int32_t bi = -1;
+            for (int i = 0; i < nw; i++) {
+                int64_t w = widths[i];
+                if (t + w > nout)
+                    continue;
+                int64_t B = 0;
+                for (int64_t k = t; k < t + w; k++)
+                    B += y[k];
+                double snr = sigma[d] > 0.0 ? ((double)B - (double)w * mu[d]) / (sigma[d] * sqrt((double)w)) : 0.0;
+                if (snr > best) {
+                    best = snr;
+                    bi = i;
+                }
+            }
+            best_snr[(int64_t)d * nout + t] = best;
+            best_w[(int64_t)d * nout + t] = bi;
+        }
+    }
+}
