@@ -124,6 +124,47 @@ int af_plan_check(af_plan_t plan);
  * paper's truncation by the DM delay, Sec. 3).  AF_EINVAL if nout <= 0. */
 int af_plan_nout(af_plan_t plan, int64_t nsamp, int64_t* nout);
 
+/* ---- channel-range plan: the multi-band search, Sec. 2.2 ---------------- *
+ * A plan for the channels [c0, c1) of a band of nchan channels between f_lo
+ * and f_hi.  Channel centres and f_ref are those of the WHOLE band, so its
+ * delay table is columns [c0, c1) of the whole band's table and its
+ * candidates' TOAs refer to the whole band's top edge.  Its input is the
+ * [c1 - c0][nsamp] block of rows starting at channel c0 (d_in + c0 * nsamp of
+ * the whole band's array; af_dedisperse requires that address to be 16-byte
+ * aligned).  The paper's F+L+H search (its configurations A2/A3: F = 1000-1500,
+ * L = 1000-1250, H = 1250-1500 MHz) is three such plans, [0, nchan),
+ * [0, nchan/2) and [nchan/2, nchan), searched separately; the union of their
+ * candidates (same dm_list and tsamp, so the same dm_idx and abs_sample units)
+ * is merged by af_cluster.  The planes add up: Y_F = Y_L + Y_H on the first
+ * nout_F outputs.  Other arguments and errors as af_plan; AF_EINVAL unless
+ * 0 <= c0 < c1 <= nchan. */
+int af_plan_channels(af_plan_t* out, int nchan, double f_lo, double f_hi, double tsamp,
+                     const double* dm_list, int ndm, int c0, int c1);
+
+/* ---- square-law time downsampling, Sec. 2.2 ------------------------------ *
+ * For every channel and bin k of D consecutive samples (the last bin holds the
+ * remaining nsamp - (nout-1)*D; nout = ceil(nsamp/D)), with S the bin's sum and
+ * N its sample count:
+ *     out = min( V * sqrt(S) / sqrt(N * V), V ) = min( sqrt(V*S/N), V ),  V = 255,
+ * rounded to nearest with halves up, exactly: floor((isqrt(floor(4*V*S/N)) + 1) / 2).
+ *  d_in   uint8 [nchan][nsamp] (channel-major)
+ *  D      1 .. 32768
+ *  d_out  uint8 [nchan][ceil(nsamp/D)] (caller-owned)
+ * The output is searched with a plan whose tsamp is D * tsamp (the paper's
+ * t_samp on the downsampled grid, Eq. coarse_delay).  Enqueued on `stream`. */
+int af_downsample(const uint8_t* d_in, int nchan, int64_t nsamp, int D, uint8_t* d_out, void* stream);
+
+/* ---- zero-DM filter, Sec. 2.1 ------------------------------------------- *
+ * Removes the DM = 0 time series (the paper's zero-DM filter, named among its
+ * RFI steps in Sec. 2.1 and as the remedy for impulsive broadband RFI in
+ * Sec. 4.4; the formula is a reading): for every time sample t, with the mean
+ * over channels rounded half up, q[t] = floor((2 * sum_c X[c][t] + nchan) / (2 * nchan)),
+ *     out[c][t] = min(255, max(0, X[c][t] - q[t] + 128)),
+ * i.e. re-centred on mid-scale so that the result stays 8-bit.
+ *  d_in, d_out uint8 [nchan][nsamp] (d_out == d_in filters in place), nchan <= 65536.
+ * Enqueued on `stream`. */
+int af_zerodm(const uint8_t* d_in, int nchan, int64_t nsamp, uint8_t* d_out, void* stream);
+
 /* ---- subband plan: two-stage subband dedispersion, Sec. 2.3 ------------ *
  * The paper's own dedispersion scheme (Eqs. stage1, residual, stage2).  The
  * channels are split into nsub contiguous subbands, subband s = channels
@@ -200,6 +241,28 @@ int af_rowstats(af_plan_t plan, const int32_t* d_plane, int64_t nout,
 int af_boxcar_snr(af_plan_t plan, const int32_t* d_plane, int64_t nout,
                   const af_rowstats_t* d_stats, const int32_t* widths, int nw,
                   float* d_best_snr, uint8_t* d_best_w, void* stream);
+
+/* ---- robust S/N normalisation (median / MAD) ----------------------------- *
+ * The robust alternative to the mean / standard deviation of af_boxcar_snr
+ * (the paper lists robust RFI statistics among the steps either side of the
+ * dedispersion, Sec. 2.1; the formula here is a reading).  Per row d:
+ *     median = lower median of Y[d][0..nout) (element (nout-1)/2 of the sorted row)
+ *     mad    = lower median of |Y[d][t] - median|          (both exact integers)
+ *     snr_w  = (B_w - w*median) / (1.482602218505602 * mad * sqrt(w))   (mad = 0: snr 0)
+ * with the windows, validity, ties and best-width output of af_boxcar_snr. */
+typedef struct {
+    int64_t median;
+    int64_t mad;
+} af_robust_t;
+
+/* Median and MAD of every row of d_plane [ndm][nout] into d_robust [ndm]. */
+int af_rowstats_robust(af_plan_t plan, const int32_t* d_plane, int64_t nout, af_robust_t* d_robust,
+                       void* stream);
+
+/* Robust boxcar S/N; d_robust may be NULL (then computed into the plan's
+ * scratch first).  Other arguments and outputs as af_boxcar_snr. */
+int af_boxcar_snr_robust(af_plan_t plan, const int32_t* d_plane, int64_t nout, const af_robust_t* d_robust,
+                         const int32_t* widths, int nw, float* d_best_snr, uint8_t* d_best_w, void* stream);
 
 /* ---- boxcar S/N without any device allocation --------------------------- *
  * The paper has no counterpart: this entry point exists for callers that

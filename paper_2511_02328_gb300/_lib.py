@@ -55,6 +55,11 @@ SIGNATURES = {
     "af_plan": [_P, _I, _D, _D, _D, _P, _I],
     "af_plan_subband": [_P, _I, _D, _D, _D, _P, _I, _I, _I, _I, _I64],
     "af_plan_subband_info": [_P, _P, _P, _P, _P, _P, _P, _P, _P],
+    "af_plan_channels": [_P, _I, _D, _D, _D, _P, _I, _I, _I],
+    "af_downsample": [_P, _I, _I64, _I, _P, _P],
+    "af_zerodm": [_P, _I, _I64, _P, _P],
+    "af_rowstats_robust": [_P, _P, _I64, _P, _P],
+    "af_boxcar_snr_robust": [_P, _P, _I64, _P, _P, _I, _P, _P, _P],
     "af_plan_destroy": [_P],
     "af_plan_delays": [_P, _P, _P],
     "af_plan_info": [_P, _P, _P, _P, _P],
@@ -146,6 +151,32 @@ def af_plan(nchan, f_lo, f_hi, tsamp, dm_list):
     _check(lib().af_plan(ctypes.byref(h), int(nchan), float(f_lo), float(f_hi), float(tsamp), pd, int(dms.size)),
            "af_plan")
     return h.value
+
+
+def af_plan_channels(nchan, f_lo, f_hi, tsamp, dm_list, c0, c1):
+    dms, pd = _host(dm_list, np.float64)
+    h = _P()
+    _check(lib().af_plan_channels(ctypes.byref(h), int(nchan), float(f_lo), float(f_hi), float(tsamp), pd,
+                                  int(dms.size), int(c0), int(c1)), "af_plan_channels")
+    return h.value
+
+
+def af_downsample(d_in, nchan, nsamp, D, d_out, stream=0):
+    _check(lib().af_downsample(d_in, int(nchan), int(nsamp), int(D), d_out, stream or None), "af_downsample")
+
+
+def af_zerodm(d_in, nchan, nsamp, d_out, stream=0):
+    _check(lib().af_zerodm(d_in, int(nchan), int(nsamp), d_out, stream or None), "af_zerodm")
+
+
+def af_rowstats_robust(plan, d_plane, nout, d_robust, stream=0):
+    _check(lib().af_rowstats_robust(plan, d_plane, int(nout), d_robust, stream or None), "af_rowstats_robust")
+
+
+def af_boxcar_snr_robust(plan, d_plane, nout, d_robust, widths, d_best_snr, d_best_w=0, stream=0):
+    w, pw = _host(widths, np.int32)
+    _check(lib().af_boxcar_snr_robust(plan, d_plane, int(nout), d_robust or None, pw, int(w.size), d_best_snr,
+                                      d_best_w or None, stream or None), "af_boxcar_snr_robust")
 
 
 AF_FS_MEDIAN = 0

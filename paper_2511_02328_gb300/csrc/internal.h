@@ -129,6 +129,10 @@ int af_launch_candidates(const float* d_best_snr, const uint8_t* d_best_w, int n
                          const af_widths_t& w, float thresh, int64_t sample0, af_cand_t* d_out,
                          int32_t cap, int32_t* d_count, cudaStream_t s);
 int af_prepare_dedisp_tables(af_plan_t p);
+int af_launch_row_robust(const int32_t* d_plane, int ndm, int64_t nout, af_robust_t* d_robust, cudaStream_t s);
+int af_launch_boxcar_robust(const int32_t* d_plane, int ndm, int64_t nout, const af_robust_t* d_robust,
+                            const af_widths_t& w, af_rowconst_t* d_rowconst, float* d_best_snr, uint8_t* d_best_w,
+                            cudaStream_t s);
 // Subband plans: builds the device tables and the scratch (af_plan_subband);
 // frees them (plan destruction); launches stage 1 + stage 2 per time block.
 int af_sb_prepare(af_plan_t p);

@@ -110,13 +110,15 @@ static double chan_freq(int c, int nchan, double f_lo, double f_hi)
 
 // Eq. (coarse_delay) for a list of DMs: D = round(K*DM/tsamp * (1/fc^2 - 1/fref^2)),
 // channel centres, f_ref = top band edge, round half away from zero.
+// The table covers channels [c0, c0 + nchan) of a band of ntot channels.
 static int delay_rows(const char* who, int nchan, double f_lo, double f_hi, double tsamp, const double* dms,
-                      int n, int32_t* out, int32_t* dmax)
+                      int n, int32_t* out, int32_t* dmax, int c0 = 0, int ntot = 0)
 {
+    if (ntot == 0) ntot = nchan;
     const double fr = f_lo > f_hi ? f_lo : f_hi;
     std::vector<double> bterm(nchan);
     for (int c = 0; c < nchan; c++) {
-        const double fc = chan_freq(c, nchan, f_lo, f_hi);
+        const double fc = chan_freq(c0 + c, ntot, f_lo, f_hi);
         bterm[c] = 1.0 / (fc * fc) - 1.0 / (fr * fr);
     }
     int32_t mx = 0;
@@ -195,6 +197,27 @@ extern "C" int af_plan(af_plan_t* out, int nchan, double f_lo, double f_hi, doub
         return rc;
     }
     if (int rc = plan_finish(p, "af_plan")) return rc;
+    *out = p;
+    return AF_OK;
+}
+
+extern "C" int af_plan_channels(af_plan_t* out, int nchan, double f_lo, double f_hi, double tsamp,
+                                const double* dm_list, int ndm, int c0, int c1)
+{
+    static const char* who = "af_plan_channels";
+    if (!out) return af_set_error(AF_EINVAL, "%s: out is NULL", who);
+    *out = nullptr;
+    if (int rc = check_plan_args(who, nchan, f_lo, f_hi, tsamp, dm_list, ndm)) return rc;
+    if (c0 < 0 || c1 > nchan || c1 <= c0)
+        return af_set_error(AF_EINVAL, "%s: channel range [%d, %d) not inside [0, %d)", who, c0, c1, nchan);
+    const int n = c1 - c0;
+    af_plan_s* p = new_plan(n, f_lo, f_hi, tsamp, dm_list, ndm);
+    if (!p) return af_set_error(AF_ENOMEM, "%s: host allocation failed", who);
+    if (int rc = delay_rows(who, n, f_lo, f_hi, tsamp, dm_list, ndm, p->delays.data(), &p->dmax, c0, nchan)) {
+        delete p;
+        return rc;
+    }
+    if (int rc = plan_finish(p, who)) return rc;
     *out = p;
     return AF_OK;
 }
@@ -431,6 +454,34 @@ extern "C" int af_boxcar_snr(af_plan_t p, const int32_t* d_plane, int64_t nout, 
         d_stats = p->d_stats;
     }
     return af_launch_boxcar(d_plane, p->ndm, nout, d_stats, w, p->d_rowconst, d_best_snr, d_best_w, s);
+}
+
+extern "C" int af_rowstats_robust(af_plan_t p, const int32_t* d_plane, int64_t nout, af_robust_t* d_robust,
+                                  void* stream)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    if (!d_plane || !d_robust) return af_set_error(AF_EINVAL, "af_rowstats_robust: NULL buffer");
+    if (nout < 1 || nout > INT32_MAX) return af_set_error(AF_EINVAL, "af_rowstats_robust: bad nout");
+    return af_launch_row_robust(d_plane, p->ndm, nout, d_robust, (cudaStream_t)stream);
+}
+
+extern "C" int af_boxcar_snr_robust(af_plan_t p, const int32_t* d_plane, int64_t nout, const af_robust_t* d_robust,
+                                    const int32_t* widths, int nw, float* d_best_snr, uint8_t* d_best_w,
+                                    void* stream)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    if (!d_plane || !d_best_snr) return af_set_error(AF_EINVAL, "af_boxcar_snr_robust: NULL buffer");
+    if (nout < 1 || nout > INT32_MAX) return af_set_error(AF_EINVAL, "af_boxcar_snr_robust: bad nout");
+    af_widths_t w;
+    if (int rc = af_check_widths(p, widths, nw, nout, &w)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!d_robust) {
+        // the plan's row-sum scratch has the same size and alignment
+        af_robust_t* scratch = reinterpret_cast<af_robust_t*>(p->d_stats);
+        if (int rc = af_launch_row_robust(d_plane, p->ndm, nout, scratch, s)) return rc;
+        d_robust = scratch;
+    }
+    return af_launch_boxcar_robust(d_plane, p->ndm, nout, d_robust, w, p->d_rowconst, d_best_snr, d_best_w, s);
 }
 
 extern "C" int af_candidates(af_plan_t p, const float* d_best_snr, const uint8_t* d_best_w, int64_t nout,

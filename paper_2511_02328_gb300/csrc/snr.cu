@@ -12,6 +12,7 @@
 // prefix sums taken modulo 2^32, which are exact as long as every window sum
 // is below 2^32 (checked on the host: w * 255 * nchan < 2^32).
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <math.h>
 #include <stdint.h>
 
@@ -135,15 +136,134 @@ k_boxcar(const int32_t* __restrict__ Y, int64_t nout, unsigned tiles, af_widths_
     }
 }
 
-}  // namespace
+// ---------------------------------------------------------------- robust S/N
+// Per-row median and MAD (lower medians, exact) by radix selection: one block
+// per row; each pass histograms the remaining value range into at most 2048
+// bins in shared memory and keeps the bin holding the wanted rank, so a range
+// of R values takes ceil(log2(R) / 11) passes (two for 20-bit rows).
+constexpr int kRT = 512;
+constexpr int kRB = 2048;
 
-int af_launch_boxcar(const int32_t* d_plane, int ndm, int64_t nout, const af_rowstats_t* d_stats,
-                     const af_widths_t& w, af_rowconst_t* d_rowconst, float* d_best_snr, uint8_t* d_best_w,
-                     cudaStream_t s)
+template <int MODE>  // 0: u = v - base;  1: u = |v - base|
+__device__ __forceinline__ uint32_t robust_key(int32_t v, int32_t base)
 {
-    const int nrc = ndm * w.n;
-    k_rowconst<<<(nrc + 255) / 256, 256, 0, s>>>(d_stats, ndm, nout, w, d_rowconst);
-    if (int rc = af_cuda_check(cudaGetLastError(), "rowconst launch")) return rc;
+    if (MODE == 0) return (uint32_t)(v - base);
+    return v >= base ? (uint32_t)(v - base) : (uint32_t)(base - v);
+}
+
+// rank-th smallest key among the row's values (0-based), keys in [0, range].
+template <int MODE>
+__device__ uint32_t robust_select(const int32_t* __restrict__ y, int64_t n, int32_t base, uint32_t range,
+                                  int64_t rank, uint32_t* hist, long long* sel)
+{
+    uint32_t start = 0;
+    uint64_t width = (uint64_t)range + 1;
+    const int tid = threadIdx.x, lane = tid & 31;
+    while (width > 1) {
+        const int bits = 64 - __clzll((long long)(width - 1));
+        const int s = bits > 11 ? bits - 11 : 0;
+        for (int i = tid; i < kRB; i += kRT) hist[i] = 0u;
+        __syncthreads();
+        for (int64_t t = tid; t < n; t += kRT) {
+            const uint32_t u = robust_key<MODE>(__ldg(y + t), base);
+            if (u >= start && (uint64_t)(u - start) < width) atomicAdd(&hist[(u - start) >> s], 1u);
+        }
+        __syncthreads();
+        if (tid < 32) {
+            // lane l owns bins [64 l, 64 l + 64): find the bin where the count passes rank
+            uint32_t own = 0;
+            for (int i = 0; i < 64; i++) own += hist[lane * 64 + i];
+            uint32_t incl = own;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const uint32_t excl = incl - own;
+            if ((int64_t)excl <= rank && rank < (int64_t)incl) {
+                int64_t cum = excl;
+                for (int i = 0; i < 64; i++) {
+                    const uint32_t h = hist[lane * 64 + i];
+                    if (rank < cum + (int64_t)h) {
+                        sel[0] = lane * 64 + i;
+                        sel[1] = cum;
+                        break;
+                    }
+                    cum += h;
+                }
+            }
+        }
+        __syncthreads();
+        const uint32_t b = (uint32_t)sel[0];
+        rank -= sel[1];
+        start += b << s;
+        const uint64_t left = width - ((uint64_t)b << s);
+        width = left < ((uint64_t)1 << s) ? left : ((uint64_t)1 << s);
+        __syncthreads();
+    }
+    return start;
+}
+
+__global__ void __launch_bounds__(kRT) k_row_robust(const int32_t* __restrict__ Y, int64_t nout,
+                                                    af_robust_t* __restrict__ out)
+{
+    __shared__ uint32_t hist[kRB];
+    __shared__ long long sel[2];
+    __shared__ int32_t smin[kRT / 32], smax[kRT / 32];
+    const int d = blockIdx.x;
+    const int32_t* y = Y + (int64_t)d * nout;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int32_t lo = INT32_MAX, hi = INT32_MIN;
+    for (int64_t t = tid; t < nout; t += kRT) {
+        const int32_t v = __ldg(y + t);
+        lo = min(lo, v);
+        hi = max(hi, v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+        smin[warp] = lo;
+        smax[warp] = hi;
+    }
+    __syncthreads();
+    lo = smin[0];
+    hi = smax[0];
+    for (int i = 1; i < kRT / 32; i++) {
+        lo = min(lo, smin[i]);
+        hi = max(hi, smax[i]);
+    }
+    const int64_t k = (nout - 1) / 2;
+    const int32_t med = lo + (int32_t)robust_select<0>(y, nout, lo, (uint32_t)(hi - lo), k, hist, sel);
+    const uint32_t r2 = (uint32_t)max(hi - med, med - lo);
+    const uint32_t mad = robust_select<1>(y, nout, med, r2, k, hist, sel);
+    if (tid == 0) {
+        out[d].median = med;
+        out[d].mad = mad;
+    }
+}
+
+// Robust S/N constants: snr = (B - w*med) * k, k = 1/(1.482602218505602 * mad * sqrt(w)).
+__global__ void k_rowconst_robust(const af_robust_t* __restrict__ r, int ndm, af_widths_t w,
+                                  af_rowconst_t* __restrict__ rc)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ndm * w.n) return;
+    const int d = i / w.n, wi = i % w.n;
+    const int64_t W = w.w[wi];
+    const double sigma = 1.482602218505602 * (double)r[d].mad;
+    af_rowconst_t o;
+    o.q = W * r[d].median;
+    o.k = sigma > 0.0 ? (float)(1.0 / (sigma * sqrt((double)W))) : 0.0f;
+    o.c = 0.0f;
+    rc[(int64_t)d * AF_MAX_WIDTHS + wi] = o;
+}
+
+int launch_boxcar_tiles(const int32_t* d_plane, int ndm, int64_t nout, const af_widths_t& w,
+                        const af_rowconst_t* d_rowconst, float* d_best_snr, uint8_t* d_best_w, cudaStream_t s)
+{
     const unsigned tiles = (unsigned)((nout + kBOut - 1) / kBOut);
     const unsigned long long nblk = (unsigned long long)tiles * (unsigned long long)ndm;
     if (nblk > 0x7fffffffULL) return af_set_error(AF_EINVAL, "boxcar: problem too large for one grid");
@@ -152,4 +272,32 @@ int af_launch_boxcar(const int32_t* d_plane, int ndm, int64_t nout, const af_row
         if (int rc = af_ensure_smem((const void*)k_boxcar, smem)) return rc;
     k_boxcar<<<(unsigned)nblk, kBT, smem, s>>>(d_plane, nout, tiles, w, d_rowconst, d_best_snr, d_best_w);
     return af_cuda_check(cudaGetLastError(), "boxcar launch");
+}
+
+}  // namespace
+
+int af_launch_row_robust(const int32_t* d_plane, int ndm, int64_t nout, af_robust_t* d_robust, cudaStream_t s)
+{
+    k_row_robust<<<ndm, kRT, 0, s>>>(d_plane, nout, d_robust);
+    return af_cuda_check(cudaGetLastError(), "robust row statistics launch");
+}
+
+int af_launch_boxcar_robust(const int32_t* d_plane, int ndm, int64_t nout, const af_robust_t* d_robust,
+                            const af_widths_t& w, af_rowconst_t* d_rowconst, float* d_best_snr, uint8_t* d_best_w,
+                            cudaStream_t s)
+{
+    const int nrc = ndm * w.n;
+    k_rowconst_robust<<<(nrc + 255) / 256, 256, 0, s>>>(d_robust, ndm, w, d_rowconst);
+    if (int rc = af_cuda_check(cudaGetLastError(), "robust rowconst launch")) return rc;
+    return launch_boxcar_tiles(d_plane, ndm, nout, w, d_rowconst, d_best_snr, d_best_w, s);
+}
+
+int af_launch_boxcar(const int32_t* d_plane, int ndm, int64_t nout, const af_rowstats_t* d_stats,
+                     const af_widths_t& w, af_rowconst_t* d_rowconst, float* d_best_snr, uint8_t* d_best_w,
+                     cudaStream_t s)
+{
+    const int nrc = ndm * w.n;
+    k_rowconst<<<(nrc + 255) / 256, 256, 0, s>>>(d_stats, ndm, nout, w, d_rowconst);
+    if (int rc = af_cuda_check(cudaGetLastError(), "rowconst launch")) return rc;
+    return launch_boxcar_tiles(d_plane, ndm, nout, w, d_rowconst, d_best_snr, d_best_w, s);
 }

@@ -155,7 +155,6 @@ k_sb_stage2(const T* __restrict__ I, int64_t ipitch, int nsub, int n0, int ndm, 
 
 template <typename T, int NM>
 struct Stage2 {
-    static constexpr int TV = kS2Threads * (64 / NM);
     static const void* fn() { return (const void*)k_sb_stage2<T, NM>; }
     static void launch(unsigned grid, size_t smem, cudaStream_t s, const T* I, int64_t ipitch, int nsub, int n0,
                        int ndm, const int32_t* R, int rw, int sc, int64_t v0, int64_t lcur, int64_t nout,

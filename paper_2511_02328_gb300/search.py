@@ -28,11 +28,16 @@ def device_view(ptr, shape, dtype):
 class Plan:
     """Delay-table plan (Eq. coarse_delay, Sec. 2.3) on the current device."""
 
-    def __init__(self, nchan, f_lo, f_hi, tsamp, dm_list, subband=None):
+    def __init__(self, nchan, f_lo, f_hi, tsamp, dm_list, subband=None, channels=None):
         """subband=None: brute-force plan; subband=dict(n0=, nsub=, fs_mode=, block_len=):
-        two-stage subband plan (Sec. 2.3, af_plan_subband)."""
+        two-stage subband plan (Sec. 2.3, af_plan_subband); channels=(c0, c1): plan for
+        that channel range of the band (af_plan_channels, the multi-band search)."""
         self.dm_list = np.ascontiguousarray(dm_list, dtype=np.float64)
-        if subband is None:
+        self.c0 = 0
+        if channels is not None:
+            self.c0 = int(channels[0])
+            self.handle = _lib.af_plan_channels(nchan, f_lo, f_hi, tsamp, self.dm_list, channels[0], channels[1])
+        elif subband is None:
             self.handle = _lib.af_plan(nchan, f_lo, f_hi, tsamp, self.dm_list)
         else:
             self.handle = _lib.af_plan_subband(nchan, f_lo, f_hi, tsamp, self.dm_list, subband["n0"],
