@@ -309,6 +309,98 @@ def run_prep(args, dev, x, plane, snr, bw, ms_brute, stream):
     return res
 
 
+def run_batch(args, dev, stream):
+    """The multi-beam batch (pattern 2): 19 beams of uneven channel count, DM
+    range and length (workloads.multibeam: 10.7 GB of input, 1.07e13
+    DM-trial·chan·samples), each with 5 injected pulses, searched in one
+    persistent dedispersion launch + per-beam S/N and candidates, replayed as
+    a CUDA graph with the autotuned tile shape; compared with the same beams
+    searched one plan after another on the same stream (per-beam launches)."""
+    import torch
+    from paper_2511_02328_gb300 import _lib, synth, workloads
+    from paper_2511_02328_gb300.search import Plan
+
+    def dmax_of(nchan, f_lo, f_hi, tsamp, dm):
+        q = Plan(nchan, f_lo, f_hi, tsamp, [dm])
+        d = q.dmax
+        q.close()
+        return d
+
+    beams = workloads.multibeam(19, dmax_of)
+    xs, descs, work = [], [], 0.0
+    for b, bm in enumerate(beams):
+        q = Plan(bm["nchan"], bm["f_lo"], bm["f_hi"], bm["tsamp"], bm["dm_list"])
+        nout = q.nout(bm["nsamp"])
+        work += float(q.ndm) * bm["nchan"] * nout
+        pp = synth.pulse_params(5, 5000 + b, (0.1 * bm["dm_list"][-1], 0.9 * bm["dm_list"][-1]), (0.5e-3, 5e-3),
+                                (8.0, 20.0), (0.2, nout * bm["tsamp"] - 0.2), 0.1, bm["tsamp"])
+        D = Plan(bm["nchan"], bm["f_lo"], bm["f_hi"], bm["tsamp"], [p_["dm"] for p_ in pp]).delays()
+        pulses = [synth.Pulse(p_["t0"] + D[i].astype(np.int64), p_["width"],
+                              synth.pulse_amplitude(p_["snr"], bm["nchan"], p_["width"])) for i, p_ in enumerate(pp)]
+        x = synth.filterbank_torch(bm["nchan"], bm["nsamp"], seed=6000 + b, pulses=pulses, device=dev)
+        xs.append(x)
+        descs.append(dict(nchan=bm["nchan"], f_lo=bm["f_lo"], f_hi=bm["f_hi"], tsamp=bm["tsamp"],
+                          dm_list=bm["dm_list"], d_in=x.data_ptr(), nsamp=bm["nsamp"], widths=bm["widths"],
+                          thresh=bm["thresh"], cap=1 << 16))
+        q.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch = _lib.af_batch_build(descs)
+    build_s = time.perf_counter() - t0
+    nw, m, tuned_ms, cached = _lib.af_batch_shape(batch)
+    sp = stream.cuda_stream
+    steps = max(1, min(args.steps, 5))
+
+    def timed(fn, n):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n):
+            fn()
+        b_.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b_) / n
+
+    ms_batch = timed(lambda: _lib.af_batch_run(batch, sp), steps)
+    ncand = sum(_lib.af_batch_candidates(batch, i, 1 << 16)[1] for i in range(len(beams)))
+
+    # the same searches one plan at a time, writing into the batch's buffers
+    plans, bufs = [], []
+    for i, bm in enumerate(beams):
+        plans.append(Plan(bm["nchan"], bm["f_lo"], bm["f_hi"], bm["tsamp"], bm["dm_list"]))
+        bufs.append(_lib.af_batch_buffers(batch, i))
+    cnt = torch.empty(1, dtype=torch.int32, device=dev)
+    cands = torch.empty((1 << 16, 24), dtype=torch.uint8, device=dev)
+
+    def one_by_one():
+        for q, bm, (pl, sn, bw_, nout), x in zip(plans, beams, bufs, xs):
+            _lib.af_dedisperse(q.handle, x.data_ptr(), bm["nsamp"], pl, 0, sp)
+            _lib.af_boxcar_snr(q.handle, pl, nout, 0, bm["widths"], sn, bw_, sp)
+            _lib.af_candidates(q.handle, sn, bw_, nout, bm["widths"], bm["thresh"], 0, cands.data_ptr(), 1 << 16,
+                               cnt.data_ptr(), sp)
+
+    ms_sep = timed(one_by_one, steps)
+    for q in plans:
+        q.close()
+    _lib.af_batch_destroy(batch)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks().get("sm_max_mhz", SM_MAX_MHZ_FALLBACK))
+    alu_peak = nsm * 128 * sm_max * 1e6
+    return {
+        "workload": "19 beams: nchan 1024/2048/4096, tsamp 49.152 us x 4096/nchan, DM max 500-2000 step 0.5-2, "
+                    "2^16-2^19 samples (>= 2 Dmax), widths 1..256, threshold 8, 5 pulses per beam",
+        "input_gb": sum(x.numel() for x in xs) / 1e9, "work": work, "ms_per_batch": ms_batch,
+        "rate": work / (ms_batch * 1e-3), "unit": UNIT, "ms_one_plan_at_a_time": ms_sep,
+        "speedup_vs_one_plan_at_a_time": ms_sep / ms_batch, "tile_shape": [nw, m], "autotune_ms": tuned_ms,
+        "autotune_cached": bool(cached), "build_s": build_s, "candidates": int(ncand), "steps": steps,
+        "alu_frac_whole_batch": work / (ms_batch * 1e-3) / alu_peak,
+        "note": "ms_per_batch covers dedispersion of all beams in one persistent launch plus every beam's S/N and "
+                "candidates (CUDA graph replay); alu_frac is the batch's adds over 152 x 128 x max clock",
+    }
+
+
 def run_stream(args, dev, clocks):
     """Real-time paced multi-beam stream through the engine: returns latency
     percentiles and throughput.  Data: one seeded noise pool on pinned host
@@ -407,6 +499,7 @@ def main():
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--no-subband", action="store_true")
     ap.add_argument("--no-prep", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--stream-rounds", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -505,6 +598,11 @@ def main():
         e2e_s = float(t.item())
     clocks.stop()
 
+    batch_res = None
+    if not args.no_batch:
+        batch_res = run_batch(args, dev, stream)
+        torch.cuda.empty_cache()
+
     prep_res = None
     if not args.no_prep:
         prep_res = run_prep(args, dev, x, plane, snr, bw, ms_dedisp, stream)
@@ -570,6 +668,7 @@ def main():
             "stream": stream_res,
             "subband": sub_res,
             "prep": prep_res,
+            "batch": batch_res,
         }
         print(json.dumps(line))
     plan.close()

@@ -23,6 +23,7 @@ int af_cuda_check(cudaError_t e, const char* what);
 struct af_widths_t {
     int32_t w[AF_MAX_WIDTHS];
     int32_t n;
+    int32_t small;  // every window sum (hence B - q) is below 2^31: 32-bit difference
 };
 
 // Per-row, per-width S/N constants:  snr = float(B - q) * k - c  with

@@ -405,6 +405,7 @@ int af_check_widths(af_plan_t p, const int32_t* widths, int nw, int64_t nout, af
         out->w[i] = widths[i];
     }
     out->n = nw;
+    out->small = (double)widths[nw - 1] * 255.0 * (double)p->nchan < 2147483648.0 ? 1 : 0;
     return AF_OK;
 }
 

@@ -31,20 +31,39 @@ __global__ void __launch_bounds__(kDsThreads)
 k_downsample(const uint8_t* __restrict__ X, int64_t nsamp, int D, int64_t nout, int tb, unsigned runs,
              uint8_t* __restrict__ out)
 {
-    __shared__ uint8_t sx[kDsSpan];
+    __shared__ __align__(16) uint8_t sx[kDsSpan];
     const int c = (int)(blockIdx.x / runs);
     const int64_t k0 = (int64_t)(blockIdx.x % runs) * tb;
     const int64_t t0 = k0 * D;
     const int64_t span = min((int64_t)tb * D, nsamp - t0);
     const uint8_t* x = X + (int64_t)c * nsamp + t0;
-    for (int64_t i = threadIdx.x; i < span; i += kDsThreads) sx[i] = __ldg(x + i);
+    int64_t done = 0;
+    if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+        // all of a thread's 16-byte loads are issued before the first shared store
+        constexpr int NB = kDsSpan / 16 / kDsThreads;
+        const int n16 = (int)(span >> 4);
+        uint4 v[NB];
+#pragma unroll
+        for (int u = 0; u < NB; u++)
+            if ((int)threadIdx.x + u * kDsThreads < n16)
+                v[u] = __ldg(reinterpret_cast<const uint4*>(x) + threadIdx.x + u * kDsThreads);
+#pragma unroll
+        for (int u = 0; u < NB; u++)
+            if ((int)threadIdx.x + u * kDsThreads < n16) reinterpret_cast<uint4*>(sx)[threadIdx.x + u * kDsThreads] = v[u];
+        done = (int64_t)n16 << 4;
+    }
+    for (int64_t i = done + threadIdx.x; i < span; i += kDsThreads) sx[i] = __ldg(x + i);
     __syncthreads();
     for (int k = threadIdx.x; k < tb && k0 + k < nout; k += kDsThreads) {
         const int64_t a = (int64_t)k * D, b = min(a + D, span);
         uint32_t S = 0;
-        for (int64_t i = a; i < b; i++) S += sx[i];
+        int64_t i = a;
+        if ((D & 3) == 0)  // whole 32-bit words: one dp4a per 4 samples
+            for (; i + 4 <= b; i += 4) S = __dp4a(*reinterpret_cast<const uint32_t*>(sx + i), 0x01010101u, S);
+        for (; i < b; i++) S += sx[i];
         const uint32_t N = (uint32_t)(b - a);
-        const uint32_t q = (uint32_t)((4ull * 255ull * S) / N);  // <= 4 * 255 * 255
+        // floor(4 V S / N) <= 4 * 255 * 255; 32-bit when 4 V S < 2^32 (N <= 16448)
+        const uint32_t q = N <= 16448u ? (1020u * S) / N : (uint32_t)((1020ull * S) / N);
         const uint32_t v = (isqrt_small(q) + 1) / 2;
         out[(int64_t)c * nout + k0 + k] = (uint8_t)min(v, 255u);
     }
@@ -68,57 +87,104 @@ extern "C" int af_downsample(const uint8_t* d_in, int nchan, int64_t nsamp, int 
 
 // ---------------------------------------------------------------- zero-DM
 // Zero-DM filter: q[t] = round_half_up(sum_c X[c][t] / nchan), out = clip(X - q + 128).
-// Each thread owns 4 consecutive samples of every channel: it sums the column
-// block over all channels, then rewrites it (in place is safe: no thread reads
-// another thread's samples).  Word loads when the rows are 4-byte aligned.
+// Fast path (rows 16-byte aligned, nsamp % 16 == 0): a block owns a tile of
+// 512 samples; its 8 warps split the channels, lane l holding samples
+// [16 l, 16 l + 16) of the tile as one 16-byte load per channel.
+//   pass 1: per-warp channel sums in 16-bit lanes (bytes 0,2 / 1,3 of each
+//           word, folded into 32-bit sums every 256 channels), reduced across
+//           warps in shared memory into q[512];
+//   pass 2: every warp re-reads its channels and writes clip(x - q + 128).
+// In place is safe: a block reads every channel of its tile before writing.
+// Other shapes: one thread per 4 samples of every channel, byte accesses.
 namespace {
 
-constexpr int kZT = 128;
+constexpr int kZW = 8;            // warps per block (channel split)
+constexpr int kZTile = 512;       // samples per block
+constexpr int kZT = 128;          // generic kernel: threads per block
+
+__global__ void __launch_bounds__(kZW * 32)
+k_zerodm16(const uint8_t* X, int nchan, int64_t nsamp, uint8_t* out)
+{
+    __shared__ uint32_t part[kZW][kZTile];
+    __shared__ int32_t q[kZTile];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t t0 = (int64_t)blockIdx.x * kZTile + 16 * lane;
+    const int c0 = (int)((int64_t)nchan * warp / kZW), c1 = (int)((int64_t)nchan * (warp + 1) / kZW);
+    uint32_t sum[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) sum[i] = 0u;
+    for (int cb = c0; cb < c1; cb += 256) {
+        const int ce = min(c1, cb + 256);
+        uint32_t E[4] = {0u, 0u, 0u, 0u}, O[4] = {0u, 0u, 0u, 0u};
+#pragma unroll 4
+        for (int c = cb; c < ce; c++) {
+            const uint4 v = *reinterpret_cast<const uint4*>(X + (int64_t)c * nsamp + t0);
+            const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                E[j] += wv[j] & 0x00FF00FFu;
+                O[j] += __byte_perm(wv[j], 0u, 0x4341);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            sum[4 * j + 0] += E[j] & 0xFFFFu;
+            sum[4 * j + 1] += O[j] & 0xFFFFu;
+            sum[4 * j + 2] += E[j] >> 16;
+            sum[4 * j + 3] += O[j] >> 16;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 16; i++) part[warp][16 * lane + i] = sum[i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < kZTile; i += kZW * 32) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < kZW; w++) s += part[w][i];
+        q[i] = (int32_t)((2u * s + (uint32_t)nchan) / (2u * (uint32_t)nchan)) - 128;
+    }
+    __syncthreads();
+    int32_t qq[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) qq[i] = q[16 * lane + i];
+#pragma unroll 4
+    for (int c = c0; c < c1; c++) {
+        const int64_t o = (int64_t)c * nsamp + t0;
+        const uint4 v = *reinterpret_cast<const uint4*>(X + o);  // plain load: X may alias out
+        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+        uint32_t r[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            uint32_t acc = 0;
+#pragma unroll
+            for (int b = 0; b < 4; b++) {
+                const int x = (int)((wv[j] >> (8 * b)) & 0xFFu) - qq[4 * j + b];
+                acc |= (uint32_t)min(255, max(0, x)) << (8 * b);
+            }
+            r[j] = acc;
+        }
+        *reinterpret_cast<uint4*>(out + o) = make_uint4(r[0], r[1], r[2], r[3]);
+    }
+}
 
 __global__ void __launch_bounds__(kZT)
-k_zerodm(const uint8_t* X, int nchan, int64_t nsamp, uint8_t* out, int aligned)
+k_zerodm(const uint8_t* X, int nchan, int64_t nsamp, uint8_t* out)
 {
     const int64_t t = ((int64_t)blockIdx.x * kZT + threadIdx.x) * 4;
     if (t >= nsamp) return;
     const int n = (int)min((int64_t)4, nsamp - t);
     uint32_t s[4] = {0u, 0u, 0u, 0u};
-    if (aligned && n == 4) {
-#pragma unroll 8
-        for (int c = 0; c < nchan; c++) {
-            const uint32_t w = *reinterpret_cast<const uint32_t*>(X + (int64_t)c * nsamp + t);
-            s[0] += w & 0xFFu;
-            s[1] += (w >> 8) & 0xFFu;
-            s[2] += (w >> 16) & 0xFFu;
-            s[3] += w >> 24;
-        }
-    } else {
-        for (int c = 0; c < nchan; c++)
-            for (int i = 0; i < n; i++) s[i] += X[(int64_t)c * nsamp + t + i];
-    }
+    for (int c = 0; c < nchan; c++)
+        for (int i = 0; i < n; i++) s[i] += X[(int64_t)c * nsamp + t + i];
     int q[4];
 #pragma unroll
     for (int i = 0; i < 4; i++) q[i] = (int)((2u * s[i] + (uint32_t)nchan) / (2u * (uint32_t)nchan)) - 128;
-    if (aligned && n == 4) {
-#pragma unroll 8
-        for (int c = 0; c < nchan; c++) {
-            const int64_t o = (int64_t)c * nsamp + t;
-            const uint32_t w = *reinterpret_cast<const uint32_t*>(X + o);
-            uint32_t r = 0;
-#pragma unroll
-            for (int i = 0; i < 4; i++) {
-                const int v = (int)((w >> (8 * i)) & 0xFFu) - q[i];
-                r |= (uint32_t)min(255, max(0, v)) << (8 * i);
-            }
-            *reinterpret_cast<uint32_t*>(out + o) = r;
+    for (int c = 0; c < nchan; c++)
+        for (int i = 0; i < n; i++) {
+            const int64_t o = (int64_t)c * nsamp + t + i;
+            const int v = (int)X[o] - q[i];
+            out[o] = (uint8_t)min(255, max(0, v));
         }
-    } else {
-        for (int c = 0; c < nchan; c++)
-            for (int i = 0; i < n; i++) {
-                const int64_t o = (int64_t)c * nsamp + t + i;
-                const int v = (int)X[o] - q[i];
-                out[o] = (uint8_t)min(255, max(0, v));
-            }
-    }
 }
 
 }  // namespace
@@ -127,9 +193,17 @@ extern "C" int af_zerodm(const uint8_t* d_in, int nchan, int64_t nsamp, uint8_t*
 {
     if (!d_in || !d_out) return af_set_error(AF_EINVAL, "af_zerodm: NULL buffer");
     if (nchan < 1 || nchan > 65536 || nsamp < 1) return af_set_error(AF_EINVAL, "af_zerodm: bad shape");
-    const int64_t blocks = (nsamp + 4 * kZT - 1) / (4 * kZT);
-    if (blocks > 0x7fffffff) return af_set_error(AF_EINVAL, "af_zerodm: input too large");
-    const int aligned = (nsamp % 4 == 0) && ((uintptr_t)d_in % 4 == 0) && ((uintptr_t)d_out % 4 == 0);
-    k_zerodm<<<(unsigned)blocks, kZT, 0, (cudaStream_t)stream>>>(d_in, nchan, nsamp, d_out, aligned);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool fast = nsamp % kZTile == 0 && ((uintptr_t)d_in % 16 == 0) && ((uintptr_t)d_out % 16 == 0) &&
+                      nchan >= kZW;
+    if (fast) {
+        const int64_t blocks = nsamp / kZTile;
+        if (blocks > 0x7fffffff) return af_set_error(AF_EINVAL, "af_zerodm: input too large");
+        k_zerodm16<<<(unsigned)blocks, kZW * 32, 0, s>>>(d_in, nchan, nsamp, d_out);
+    } else {
+        const int64_t blocks = (nsamp + 4 * kZT - 1) / (4 * kZT);
+        if (blocks > 0x7fffffff) return af_set_error(AF_EINVAL, "af_zerodm: input too large");
+        k_zerodm<<<(unsigned)blocks, kZT, 0, s>>>(d_in, nchan, nsamp, d_out);
+    }
     return af_cuda_check(cudaGetLastError(), "af_zerodm launch");
 }

@@ -58,82 +58,178 @@ __global__ void k_rowconst(const af_rowstats_t* __restrict__ st, int ndm, int64_
 }
 
 constexpr int kBT = 256;             // threads per block
-constexpr int kBOut = 2048;          // outputs per block (8 per thread)
-constexpr int kPer = kBOut / kBT;
+constexpr int kPer = 16;             // outputs per thread
+constexpr int kBOut = kBT * kPer;    // outputs per block
 
-// Block = one tile of one row.  Loads Y[t0 .. t0+kBOut+wmax-1) into shared
-// memory, scans it into 32-bit prefix sums P[j] = sum_{k<j} Y[t0+k] (mod 2^32),
-// then every output evaluates all widths from two prefix values each.
-__global__ void __launch_bounds__(kBT)
+// Block = one tile of kBOut outputs of one row.
+//  1. Y[t0 .. t0 + L), L = kBOut + wmax - 1 (clipped at nout), is loaded into
+//     shared memory with coalesced (16-byte when aligned) loads, all issued
+//     before any is used.
+//  2. Prefix sums P[j] = sum_{k<j} Y[t0+k] (mod 2^32) in one pass: thread i
+//     scans its own segment of C consecutive values (C odd, so a warp's
+//     segment accesses fall in distinct banks), the segment totals are scanned
+//     across the block, and each thread adds its offset.
+//  3. Output t0 + lt (lt = tid + kBT*i) evaluates every width from P[lt] and
+//     P[lt + w]: B = P[lt+w] - P[lt], snr = (B - q) * k - c.
+// With SMALL (every window sum < 2^31) the difference B - q is formed and
+// converted in 32 bits.
+template <bool SMALL>
+__global__ void __launch_bounds__(kBT, 3)
 k_boxcar(const int32_t* __restrict__ Y, int64_t nout, unsigned tiles, af_widths_t w,
          const af_rowconst_t* __restrict__ rc, float* __restrict__ snr, uint8_t* __restrict__ bw)
 {
-    extern __shared__ uint32_t sP[];
+    extern __shared__ uint32_t sP[];  // 3 words of padding, then P[0 .. kBT*C]
     __shared__ int64_t sq[AF_MAX_WIDTHS];
     __shared__ float sk[AF_MAX_WIDTHS], sc[AF_MAX_WIDTHS];
+    __shared__ int sw[AF_MAX_WIDTHS];
     __shared__ uint32_t swarp[kBT / 32];
+    uint32_t* P = sP + 3;             // P[1 + j] holds Y[t0 + j]: 16-byte aligned for j % 4 == 0
 
     const int d = (int)(blockIdx.x / tiles);
     const int64_t t0 = (int64_t)(blockIdx.x % tiles) * kBOut;
     const int nw = w.n;
     const int wmax = w.w[nw - 1];
-    const int64_t lend = min(nout, t0 + kBOut + wmax - 1);
-    const int L = (int)(lend - t0);
-    const int32_t* y = Y + (int64_t)d * nout + t0;
+    const int L = (int)(min(nout, t0 + kBOut + wmax - 1) - t0);
+    const int64_t base = (int64_t)d * nout + t0;
+    const int32_t* y = Y + base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    if (threadIdx.x < nw) {
-        const af_rowconst_t c = rc[(int64_t)d * AF_MAX_WIDTHS + threadIdx.x];
-        sq[threadIdx.x] = c.q;
-        sk[threadIdx.x] = c.k;
-        sc[threadIdx.x] = c.c;
+    if (tid < nw) {
+        const af_rowconst_t c = rc[(int64_t)d * AF_MAX_WIDTHS + tid];
+        sq[tid] = c.q;
+        sk[tid] = c.k;
+        sc[tid] = c.c;
+        sw[tid] = w.w[tid];
     }
-    if (threadIdx.x == 0) sP[0] = 0u;
-
-    // inclusive scan in chunks of kBT elements: sP[j+1] = sum_{k<=j} y[k]
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t carry = 0;
-    for (int base = 0; base < L; base += kBT) {
-        const int j = base + threadIdx.x;
-        uint32_t v = j < L ? (uint32_t)__ldg(y + j) : 0u;
+    // 1. load Y into P[1 .. L]
+    int done = 0;
+    if ((reinterpret_cast<uintptr_t>(y) & 15) == 0) {
+        // every load of the tile is issued before the first shared store
+        constexpr int NB = (kBOut + 1024) / 4 / kBT;  // 16-byte loads per thread (L <= kBOut + 1023)
+        const int L4 = L >> 2;
+        const int4* y4 = reinterpret_cast<const int4*>(y);
+        int4 v[NB];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t n = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += n;
+        for (int u = 0; u < NB; u++)
+            if (tid + u * kBT < L4) v[u] = __ldg(y4 + tid + u * kBT);
+#pragma unroll
+        for (int u = 0; u < NB; u++)
+            if (tid + u * kBT < L4) reinterpret_cast<int4*>(P + 1)[tid + u * kBT] = v[u];
+        for (int j = tid + NB * kBT; j < L4; j += kBT) reinterpret_cast<int4*>(P + 1)[j] = __ldg(y4 + j);
+        done = 4 * L4;
+    }
+    for (int j = done + tid; j < L; j += kBT) P[j + 1] = (uint32_t)__ldg(y + j);
+    const int C = ((L + kBT - 1) / kBT) | 1;
+    for (int j = L + 1 + tid; j <= kBT * C; j += kBT) P[j] = 0u;  // pad the last segments
+    if (tid == 0) P[0] = 0u;
+    __syncthreads();
+
+    // 2. prefix sums: the segment of thread tid is P[1 + tid*C .. 1 + (tid+1)*C)
+    uint32_t* seg = P + 1 + tid * C;
+    uint32_t run = 0;
+    for (int k = 0; k < C; k++) {
+        run += seg[k];
+        seg[k] = run;
+    }
+    uint32_t incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) swarp[warp] = incl;
+    __syncthreads();
+    uint32_t off = incl - run;
+    for (int k = 0; k < warp; k++) off += swarp[k];
+    for (int k = 0; k < C; k++) seg[k] += off;
+    __syncthreads();
+
+    // 3. S/N of every width, best width.  Tiles whose every window ends
+    //    inside the row take the unchecked path: widths outer, the thread's
+    //    kPer outputs inner (independent chains).
+    if (t0 + kBOut + wmax - 1 <= nout) {
+        uint32_t p0[kPer];
+        float best[kPer];
+        int bi[kPer];
+#pragma unroll
+        for (int i = 0; i < kPer; i++) {
+            p0[i] = P[i * kBT + tid];
+            best[i] = -INFINITY;
+            bi[i] = AF_NO_WIDTH;
         }
-        if (lane == 31) swarp[warp] = v;
-        __syncthreads();
-        uint32_t off = carry;
-        for (int k = 0; k < warp; k++) off += swarp[k];
-        if (j < L) sP[j + 1] = v + off;
-        uint32_t tot = 0;
+        for (int k = 0; k < nw; k++) {
+            const int ww = sw[k];
+            const float kk = sk[k], cc = -sc[k];
+            const int64_t qq = sq[k];
 #pragma unroll
-        for (int k = 0; k < kBT / 32; k++) tot += swarp[k];
-        carry += tot;
-        __syncthreads();
+            for (int i = 0; i < kPer; i++) {
+                const uint32_t B = P[i * kBT + tid + ww] - p0[i];
+                float x;
+                if (SMALL)
+                    x = (float)((int32_t)B - (int32_t)qq);
+                else
+                    x = (float)((int64_t)B - qq);
+                const float v = fmaf(x, kk, cc);
+                if (v > best[i]) {
+                    best[i] = v;
+                    bi[i] = k;
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kPer; i++) {
+            const int64_t o = base + i * kBT + tid;
+            snr[o] = best[i];
+            if (bw) bw[o] = (uint8_t)bi[i];
+        }
+        return;
     }
-
 #pragma unroll 1
     for (int i = 0; i < kPer; i++) {
-        const int lt = i * kBT + threadIdx.x;
+        const int lt = i * kBT + tid;
         const int64_t t = t0 + lt;
         if (t >= nout) break;
-        const uint32_t p0 = sP[lt];
+        const uint32_t p0 = P[lt];
         float best = -INFINITY;
         int bi = AF_NO_WIDTH;
         for (int k = 0; k < nw; k++) {
-            const int ww = w.w[k];
+            const int ww = sw[k];
             if (t + ww > nout) break;
-            const uint32_t B = sP[lt + ww] - p0;
-            const float v = fmaf((float)((int64_t)B - sq[k]), sk[k], -sc[k]);
+            const uint32_t B = P[lt + ww] - p0;
+            float x;
+            if (SMALL)
+                x = (float)((int32_t)B - (int32_t)sq[k]);
+            else
+                x = (float)((int64_t)B - sq[k]);
+            const float v = fmaf(x, sk[k], -sc[k]);
             if (v > best) {
                 best = v;
                 bi = k;
             }
         }
-        const int64_t o = (int64_t)d * nout + t;
+        const int64_t o = base + lt;
         snr[o] = best;
         if (bw) bw[o] = (uint8_t)bi;
     }
+}
+
+int launch_boxcar_tiles(const int32_t* d_plane, int ndm, int64_t nout, const af_widths_t& w,
+                        const af_rowconst_t* d_rowconst, float* d_best_snr, uint8_t* d_best_w, cudaStream_t s)
+{
+    const unsigned tiles = (unsigned)((nout + kBOut - 1) / kBOut);
+    const unsigned long long nblk = (unsigned long long)tiles * (unsigned long long)ndm;
+    if (nblk > 0x7fffffffULL) return af_set_error(AF_EINVAL, "boxcar: problem too large for one grid");
+    const int L = kBOut + w.w[w.n - 1] - 1;
+    const int C = ((L + kBT - 1) / kBT) | 1;
+    const size_t smem = (size_t)(kBT * C + 4) * sizeof(uint32_t);
+    const void* fn = w.small ? (const void*)k_boxcar<true> : (const void*)k_boxcar<false>;
+    if (smem > 48 * 1024)
+        if (int rc = af_ensure_smem(fn, smem)) return rc;
+    if (w.small)
+        k_boxcar<true><<<(unsigned)nblk, kBT, smem, s>>>(d_plane, nout, tiles, w, d_rowconst, d_best_snr, d_best_w);
+    else
+        k_boxcar<false><<<(unsigned)nblk, kBT, smem, s>>>(d_plane, nout, tiles, w, d_rowconst, d_best_snr, d_best_w);
+    return af_cuda_check(cudaGetLastError(), "boxcar launch");
 }
 
 // ---------------------------------------------------------------- robust S/N
@@ -143,6 +239,7 @@ k_boxcar(const int32_t* __restrict__ Y, int64_t nout, unsigned tiles, af_widths_
 // of R values takes ceil(log2(R) / 11) passes (two for 20-bit rows).
 constexpr int kRT = 512;
 constexpr int kRB = 2048;
+constexpr int kRU = 8;   // loads per thread per iteration
 
 template <int MODE>  // 0: u = v - base;  1: u = |v - base|
 __device__ __forceinline__ uint32_t robust_key(int32_t v, int32_t base)
@@ -164,14 +261,21 @@ __device__ uint32_t robust_select(const int32_t* __restrict__ y, int64_t n, int3
         const int s = bits > 11 ? bits - 11 : 0;
         for (int i = tid; i < kRB; i += kRT) hist[i] = 0u;
         __syncthreads();
-        for (int64_t t = tid; t < n; t += kRT) {
-            const uint32_t u = robust_key<MODE>(__ldg(y + t), base);
-            if (u >= start && (uint64_t)(u - start) < width) atomicAdd(&hist[(u - start) >> s], 1u);
+        for (int64_t t = tid; t < n; t += (int64_t)kRT * kRU) {
+            int32_t v[kRU];  // kRU independent loads in flight per thread
+#pragma unroll
+            for (int u = 0; u < kRU; u++) v[u] = t + u * kRT < n ? __ldg(y + t + u * kRT) : 0;
+#pragma unroll
+            for (int u = 0; u < kRU; u++) {
+                const uint32_t k = robust_key<MODE>(v[u], base);
+                if (t + u * kRT < n && k >= start && (uint64_t)(k - start) < width) atomicAdd(&hist[(k - start) >> s], 1u);
+            }
         }
         __syncthreads();
         if (tid < 32) {
             // lane l owns bins [64 l, 64 l + 64): find the bin where the count passes rank
             uint32_t own = 0;
+#pragma unroll 8
             for (int i = 0; i < 64; i++) own += hist[lane * 64 + i];
             uint32_t incl = own;
 #pragma unroll
@@ -182,6 +286,7 @@ __device__ uint32_t robust_select(const int32_t* __restrict__ y, int64_t n, int3
             const uint32_t excl = incl - own;
             if ((int64_t)excl <= rank && rank < (int64_t)incl) {
                 int64_t cum = excl;
+#pragma unroll 1
                 for (int i = 0; i < 64; i++) {
                     const uint32_t h = hist[lane * 64 + i];
                     if (rank < cum + (int64_t)h) {
@@ -204,7 +309,7 @@ __device__ uint32_t robust_select(const int32_t* __restrict__ y, int64_t n, int3
     return start;
 }
 
-__global__ void __launch_bounds__(kRT) k_row_robust(const int32_t* __restrict__ Y, int64_t nout,
+__global__ void __launch_bounds__(kRT, 2) k_row_robust(const int32_t* __restrict__ Y, int64_t nout,
                                                     af_robust_t* __restrict__ out)
 {
     __shared__ uint32_t hist[kRB];
@@ -214,10 +319,15 @@ __global__ void __launch_bounds__(kRT) k_row_robust(const int32_t* __restrict__ 
     const int32_t* y = Y + (int64_t)d * nout;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int32_t lo = INT32_MAX, hi = INT32_MIN;
-    for (int64_t t = tid; t < nout; t += kRT) {
-        const int32_t v = __ldg(y + t);
-        lo = min(lo, v);
-        hi = max(hi, v);
+    for (int64_t t = tid; t < nout; t += (int64_t)kRT * kRU) {
+        int32_t v[kRU];
+#pragma unroll
+        for (int u = 0; u < kRU; u++) v[u] = t + u * kRT < nout ? __ldg(y + t + u * kRT) : __ldg(y + t);
+#pragma unroll
+        for (int u = 0; u < kRU; u++) {
+            lo = min(lo, v[u]);
+            hi = max(hi, v[u]);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -259,19 +369,6 @@ __global__ void k_rowconst_robust(const af_robust_t* __restrict__ r, int ndm, af
     o.k = sigma > 0.0 ? (float)(1.0 / (sigma * sqrt((double)W))) : 0.0f;
     o.c = 0.0f;
     rc[(int64_t)d * AF_MAX_WIDTHS + wi] = o;
-}
-
-int launch_boxcar_tiles(const int32_t* d_plane, int ndm, int64_t nout, const af_widths_t& w,
-                        const af_rowconst_t* d_rowconst, float* d_best_snr, uint8_t* d_best_w, cudaStream_t s)
-{
-    const unsigned tiles = (unsigned)((nout + kBOut - 1) / kBOut);
-    const unsigned long long nblk = (unsigned long long)tiles * (unsigned long long)ndm;
-    if (nblk > 0x7fffffffULL) return af_set_error(AF_EINVAL, "boxcar: problem too large for one grid");
-    const size_t smem = (size_t)(kBOut + w.w[w.n - 1] + 1) * sizeof(uint32_t);
-    if (smem > 48 * 1024)
-        if (int rc = af_ensure_smem((const void*)k_boxcar, smem)) return rc;
-    k_boxcar<<<(unsigned)nblk, kBT, smem, s>>>(d_plane, nout, tiles, w, d_rowconst, d_best_snr, d_best_w);
-    return af_cuda_check(cudaGetLastError(), "boxcar launch");
 }
 
 }  // namespace

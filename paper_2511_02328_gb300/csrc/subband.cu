@@ -40,18 +40,20 @@ constexpr int kS2BufBytes = 24576;       // target bytes per stage-2 buffer
 constexpr int64_t kScratchBudget = (int64_t)1 << 30;  // default stage-1 scratch
 constexpr int64_t kMaxDefaultL = (int64_t)1 << 18;
 constexpr uint32_t kS2WaitLimit = 1u << 24;
+constexpr int kS2RBytes = 16384;          // residual-shift table kept in shared memory up to this size
 
 template <typename T, int NM>
 __global__ void __launch_bounds__(kS2Threads)
 k_sb_stage2(const T* __restrict__ I, int64_t ipitch, int nsub, int n0, int ndm, const int32_t* __restrict__ R,
             int rw, int sc, int64_t v0, int64_t lcur, int64_t nout, unsigned vtiles, int32_t* __restrict__ Y,
-            af_rowstats_t* __restrict__ stats, int* err)
+            af_rowstats_t* __restrict__ stats, int* err, int rsmem)
 {
     constexpr int P = 64 / NM;
     constexpr int TV = kS2Threads * P;
     extern __shared__ __align__(16) uint8_t smem[];
     T* buf = reinterpret_cast<T*>(smem);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)2 * sc * rw * sizeof(T));
+    int32_t* sR = reinterpret_cast<int32_t*>(bars + 2);  // [NM][nsub] residual shifts of the group
     const uint32_t bar0 = afptx::smem_addr(bars);
     const int tid = threadIdx.x;
     const int j = (int)(blockIdx.x / vtiles);
@@ -66,6 +68,9 @@ k_sb_stage2(const T* __restrict__ I, int64_t ipitch, int nsub, int n0, int ndm, 
         afptx::mbar_init(bar0 + 8, 1);
         afptx::fence_mbar_init();
     }
+    if (rsmem)
+        for (int i = tid; i < nm * nsub; i += kS2Threads) sR[i] = __ldg(R + (int64_t)m0 * nsub + i);
+    const int32_t* Rg = rsmem ? sR : R + (int64_t)m0 * nsub;  // shared, or global for very many subbands
     __syncthreads();
 
     // chunk k = subbands [k*sc, k*sc + ns) into buffer k & 1
@@ -100,11 +105,11 @@ k_sb_stage2(const T* __restrict__ I, int64_t ipitch, int nsub, int n0, int ndm, 
         const int s0 = k * sc, ns = min(sc, nsub - s0);
         for (int i = 0; i < ns; i++) {
             const T* row = b + (size_t)i * rw;
-            const int32_t* Rs = R + (int64_t)m0 * nsub + s0 + i;
+            const int32_t* Rs = Rg + s0 + i;
 #pragma unroll
             for (int m = 0; m < NM; m++) {
                 if (m < nm) {
-                    const int r = __ldg(Rs + (int64_t)m * nsub);
+                    const int r = Rs[m * nsub];
 #pragma unroll
                     for (int p = 0; p < P; p++) acc[m][p] += (int)row[r + kS2Threads * p];
                 }
@@ -160,8 +165,9 @@ struct Stage2 {
                        int ndm, const int32_t* R, int rw, int sc, int64_t v0, int64_t lcur, int64_t nout,
                        unsigned vtiles, int32_t* Y, af_rowstats_t* stats, int* err)
     {
+        const int rsmem = (size_t)NM * nsub * 4 <= (size_t)kS2RBytes;
         k_sb_stage2<T, NM><<<grid, kS2Threads, smem, s>>>(I, ipitch, nsub, n0, ndm, R, rw, sc, v0, lcur, nout, vtiles,
-                                                          Y, stats, err);
+                                                          Y, stats, err, rsmem);
     }
 };
 
@@ -174,7 +180,8 @@ void s2_geometry(af_plan_t p, int* rw, int* sc, size_t* smem)
     const size_t es = p->sb.i16 ? 2 : 4;
     *rw = (tv_of(p->sb_n0) + p->sb_rmax + 7) & ~7;
     *sc = std::max(1, std::min(p->sb_nsub, (int)(kS2BufBytes / ((size_t)*rw * es))));
-    *smem = 2 * (size_t)(*sc) * (size_t)(*rw) * es + 16;
+    const size_t rbytes = (size_t)nm_class(p->sb_n0) * p->sb_nsub * 4;
+    *smem = 2 * (size_t)(*sc) * (size_t)(*rw) * es + 16 + (rbytes <= (size_t)kS2RBytes ? rbytes : 0);
 }
 
 template <typename T>

@@ -37,3 +37,56 @@ def multibeam(nbeams=19, max_delay_fn=None):
         beams.append(dict(nchan=nchan, f_lo=1000.0, f_hi=1500.0, tsamp=tsamp, dm_list=dms, nsamp=nsamp,
                           widths=[1, 2, 4, 8, 16, 32, 64, 128, 256], thresh=8.0))
     return beams
+
+
+def _run(argv=None):
+    """Runs one step of a workload `repeat` times on cuda:0 (inputs resident on
+    the device) -- the command the kernel profiles are taken with:
+        python -m paper_2511_02328_gb300.workloads search|subband|prep [--nsamp N] [--repeat R]
+    search:  brute-force dedispersion (row sums fused) + boxcar S/N + candidates
+    subband: two-stage subband dedispersion (n0 = 8, 64 subbands)
+    prep:    zero-DM filter, square-law downsampling by 8, median/MAD + robust S/N
+    on the 4096-channel full-band shape with nsamp samples (default 2^18)."""
+    import argparse
+    import torch
+    from . import _lib, synth
+    from .search import Plan
+    ap = argparse.ArgumentParser(prog="python -m paper_2511_02328_gb300.workloads")
+    ap.add_argument("step", choices=["search", "subband", "prep"])
+    ap.add_argument("--nsamp", type=int, default=1 << 18)
+    ap.add_argument("--repeat", type=int, default=3)
+    a = ap.parse_args(argv)
+    w = plain_full_band()
+    nch, nsamp = w["nchan"], a.nsamp
+    x = synth.filterbank_torch(nch, nsamp, seed=1, device="cuda")
+    sub = dict(n0=8, nsub=64, fs_mode=_lib.AF_FS_INVSQ, block_len=nsamp) if a.step == "subband" else None
+    p = Plan(nch, w["f_lo"], w["f_hi"], w["tsamp"], w["dm_list"], subband=sub)
+    nout = p.nout(nsamp)
+    plane = torch.empty((p.ndm, nout), dtype=torch.int32, device="cuda")
+    stats = torch.empty((p.ndm, 2), dtype=torch.int64, device="cuda")
+    if a.step != "subband":
+        snr = torch.empty((p.ndm, nout), dtype=torch.float32, device="cuda")
+        bw = torch.empty((p.ndm, nout), dtype=torch.uint8, device="cuda")
+    if a.step == "prep":
+        y = torch.empty_like(x)
+        ds = torch.empty((nch, (nsamp + 7) // 8), dtype=torch.uint8, device="cuda")
+        p.dedisperse(x, plane=plane, stats=stats)
+    for _ in range(a.repeat):
+        if a.step == "search":
+            p.dedisperse(x, plane=plane, stats=stats)
+            p.boxcar_snr(plane, w["widths"], stats=stats, snr=snr, bw=bw)
+            p.candidates(snr, bw, w["widths"], 8.0)
+        elif a.step == "subband":
+            p.dedisperse(x, plane=plane, stats=stats)
+        else:
+            _lib.af_zerodm(x.data_ptr(), nch, nsamp, y.data_ptr())
+            _lib.af_downsample(x.data_ptr(), nch, nsamp, 8, ds.data_ptr())
+            _lib.af_boxcar_snr_robust(p.handle, plane.data_ptr(), nout, 0, w["widths"], snr.data_ptr(), bw.data_ptr())
+    torch.cuda.synchronize()
+    _lib.af_plan_check(p.handle)
+    print("ok", a.step, nsamp, a.repeat)
+    p.close()
+
+
+if __name__ == "__main__":
+    _run()

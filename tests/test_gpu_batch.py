@@ -143,3 +143,48 @@ def test_hbm_budget_rejected():
     with pytest.raises(_lib.AFError) as e:
         _build(xs_dev, budget=1 << 20)
     assert e.value.code == _lib.AF_ENOBUFS
+
+
+def test_full_multibeam_batch_sampled_rows():
+    # The full 19-beam workload of the bench (10.7 GB of input, nchan 1024-4096,
+    # DM up to 2000, 2^16-2^19 samples) in one batch: two sampled rows of every
+    # beam are bit-exact with the oracle, their S/N within tolerance, and the
+    # batch's candidate counts equal the per-plan path's on two beams.
+    from paper_2511_02328_gb300 import _lib, workloads
+    from paper_2511_02328_gb300.search import Plan, device_view
+
+    def dmax_of(nchan, f_lo, f_hi, tsamp, dm):
+        return int(oracle.delay_table(nchan, f_lo, f_hi, tsamp, [dm]).max())
+
+    beams = workloads.multibeam(19, dmax_of)
+    xs, descs = [], []
+    for b, bm in enumerate(beams):
+        xs.append(synth.filterbank_torch(bm["nchan"], bm["nsamp"], seed=700 + b, device="cuda"))
+        descs.append(dict(nchan=bm["nchan"], f_lo=bm["f_lo"], f_hi=bm["f_hi"], tsamp=bm["tsamp"],
+                          dm_list=bm["dm_list"], d_in=xs[-1].data_ptr(), nsamp=bm["nsamp"], widths=bm["widths"],
+                          thresh=bm["thresh"], cap=1 << 16))
+    batch = _lib.af_batch_build(descs)
+    _lib.af_batch_run(batch, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    for i, bm in enumerate(beams):
+        pl, sn, _, nout = _lib.af_batch_buffers(batch, i)
+        ndm = len(bm["dm_list"])
+        rows = [0, ndm - 1] if i % 2 else [ndm // 3, (2 * ndm) // 3]
+        plane = device_view(pl, (ndm, nout), torch.int32)
+        snr = device_view(sn, (ndm, nout), torch.float32)
+        x = xs[i].cpu().numpy()
+        D = oracle.delay_table(bm["nchan"], bm["f_lo"], bm["f_hi"], bm["tsamp"], bm["dm_list"])
+        Y = oracle.dedisperse(x, D[rows], nout)
+        assert np.array_equal(plane[rows].cpu().numpy(), Y), i
+        ref, _ = oracle.boxcar_snr(Y, bm["widths"])
+        got = snr[rows].cpu().numpy().astype(np.float64)
+        fin = np.isfinite(ref)
+        assert np.array_equal(np.isfinite(got), fin)
+        assert float((np.abs(got[fin] - ref[fin]) / np.maximum(1.0, np.abs(ref[fin]))).max()) <= TOL, i
+        if i in (0, 11):
+            _, n = _lib.af_batch_candidates(batch, i, 1 << 16)
+            p = Plan(bm["nchan"], bm["f_lo"], bm["f_hi"], bm["tsamp"], bm["dm_list"])
+            _, nref = p.search_host(x, bm["widths"], bm["thresh"], cap=1 << 16)
+            assert n == nref, i
+            p.close()
+    _lib.af_batch_destroy(batch)

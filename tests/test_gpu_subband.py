@@ -59,6 +59,9 @@ CASES = [
     (520, 20000, 1000.0, 1500.0, 98.304e-6, np.arange(0.0, 100.0, 1.0), 7, 2, 1, 0),
     (4096, 20000, 1000.0, 1500.0, 49.152e-6, np.arange(0.0, 40.0, 1.0), 8, 64, 1, 0),
     (100, 9000, 1000.0, 1500.0, 98.304e-6, np.arange(0.0, 70.0, 0.5), 1, 10, 0, 0),
+    # residual-shift tables too large for shared memory (stage 2 reads them from global memory)
+    (1200, 9000, 1000.0, 1500.0, 98.304e-6, np.arange(0.0, 40.0, 1.0), 8, 600, 1, 0),
+    (1024, 9000, 1500.0, 1000.0, 98.304e-6, np.arange(0.0, 30.0, 1.0), 6, 1024, 0, 0),
 ]
 IDS = ["%dch-n0%d-sub%d" % (c[0], c[6], c[7]) for c in CASES]
 
