@@ -401,6 +401,68 @@ def run_batch(args, dev, stream):
     }
 
 
+CNN_FWD_FLOP = 2 * (64 * 64 * 16 * 2 * 9 + 32 * 32 * 32 * 16 * 9 + 16 * 16 * 64 * 32 * 9 + 64 * 2)
+
+
+def run_classifier(args, dev, x, plan, stream):
+    """The candidate classifier (pattern 4) on the benchmark input: cut-outs of
+    256 candidates + CNN forward (af_classify), forward alone, and one training
+    step (forward + backward + Adam) on a batch of 256; achieved TFLOP/s of the
+    convolutions against the measured bf16 peak."""
+    import torch
+    from paper_2511_02328_gb300 import _lib
+    sp = stream.cuda_stream
+    n = 256
+    nout = plan.nout(NSAMP)
+    plane = torch.empty((plan.ndm, nout), dtype=torch.int32, device=dev)
+    plan.dedisperse(x, plane=plane, stream=stream)
+    rng = np.random.default_rng(4)
+    c = np.zeros(n, dtype=_lib.CAND_DTYPE)
+    c["dm_idx"] = rng.integers(0, plan.ndm, n)
+    c["t"] = rng.integers(0, nout, n)
+    c["width"] = 2 ** rng.integers(0, 9, n)
+    c["abs_sample"] = c["t"]
+    cands = torch.from_numpy(c.view(np.uint8).reshape(n, 24)).to(dev)
+    xin = torch.empty((n, 64, 64, 2), dtype=torch.bfloat16, device=dev)
+    y = torch.from_numpy(rng.integers(0, 2, n).astype(np.int32)).to(dev)
+    prob = torch.empty(n, dtype=torch.float32, device=dev)
+    loss = torch.empty(1, dtype=torch.float32, device=dev)
+    model = _lib.af_model_create(n, 7)
+    _lib.af_cutouts(plan.handle, x.data_ptr(), NSAMP, plane.data_ptr(), nout, cands.data_ptr(), n, xin.data_ptr(), sp)
+
+    def timed(fn, k):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    k = max(3, args.steps)
+    ms_classify = timed(lambda: _lib.af_classify(model, plan.handle, x.data_ptr(), NSAMP, plane.data_ptr(), nout,
+                                                 cands.data_ptr(), n, prob.data_ptr(), sp), k)
+    ms_fwd = timed(lambda: _lib.af_model_forward(model, xin.data_ptr(), n, 0, prob.data_ptr(), sp), k)
+    ms_train = timed(lambda: _lib.af_train_step(model, xin.data_ptr(), y.data_ptr(), n, 1e-3, loss.data_ptr(), sp), k)
+    _lib.af_model_destroy(model)
+    pk = peaks()
+    peak = float(pk.get("bf16_tflops_sustained", 1700.0))
+    fwd_tf = n * CNN_FWD_FLOP / (ms_fwd * 1e-3) / 1e12
+    train_tf = 3 * n * CNN_FWD_FLOP / (ms_train * 1e-3) / 1e12
+    return {
+        "batch": n, "flop_per_sample_forward": CNN_FWD_FLOP,
+        "ms_classify": ms_classify, "candidates_per_s": n / (ms_classify * 1e-3),
+        "ms_forward": ms_fwd, "forward_tflops": fwd_tf, "ms_train_step": ms_train, "train_tflops": train_tf,
+        "peak_tflops": peak, "forward_frac": fwd_tf / peak, "train_frac": train_tf / peak,
+        "note": "convolutions as implicit GEMMs on mma.sync bf16 tensor cores (fp32 accumulate); a training step "
+                "counts 3x the forward FLOP; peak = measured bf16 sustained (cuBLAS); af_classify includes the "
+                "cut-out kernel",
+    }
+
+
 def run_stream(args, dev, clocks):
     """Real-time paced multi-beam stream through the engine: returns latency
     percentiles and throughput.  Data: one seeded noise pool on pinned host
@@ -500,6 +562,7 @@ def main():
     ap.add_argument("--no-subband", action="store_true")
     ap.add_argument("--no-prep", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-classifier", action="store_true")
     ap.add_argument("--stream-rounds", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -598,6 +661,10 @@ def main():
         e2e_s = float(t.item())
     clocks.stop()
 
+    cls_res = None
+    if not args.no_classifier:
+        cls_res = run_classifier(args, dev, x, plan, stream)
+
     batch_res = None
     if not args.no_batch:
         batch_res = run_batch(args, dev, stream)
@@ -669,6 +736,7 @@ def main():
             "subband": sub_res,
             "prep": prep_res,
             "batch": batch_res,
+            "classifier": cls_res,
         }
         print(json.dumps(line))
     plan.close()

@@ -2,7 +2,8 @@
 // square-law time downsampling and the zero-DM filter.
 //
 //   out[c][k] = min( sqrt(V * S / N), V ),  S = sum of bin k (N samples), V = 255,
-//   rounded half up, exactly: floor((isqrt(floor(4 V S / N)) + 1) / 2).
+//   rounded half up, exactly: floor((isqrt(floor(4 V S / N)) + 1) / 2), evaluated
+//   as max r with r^2 N <= 4 V S from a float estimate and two integer tests.
 //
 // One block per (channel, run of TB bins): the block's input span is read
 // with coalesced loads into shared memory, then every thread sums its bins
@@ -17,14 +18,16 @@ namespace {
 constexpr int kDsThreads = 256;
 constexpr int kDsSpan = 32768;  // bytes of input per block (shared memory)
 
-// isqrt(q) for q < 2^24: the float square root (correctly rounded) is within
-// one of the integer root; the two integer tests settle it exactly.
-__device__ __forceinline__ uint32_t isqrt_small(uint32_t q)
+// The rounded square root floor((isqrt(floor(T / N)) + 1) / 2), T = 4 V S, without
+// an integer division: isqrt(floor(T / N)) = max r with r^2 N <= T.  A float
+// estimate (rcpN = 1/N) is within one of r; two exact integer tests settle it.
+__device__ __forceinline__ uint32_t sqlaw_value(uint64_t T, uint32_t N, float rcpN)
 {
-    uint32_t r = (uint32_t)sqrtf((float)q);
-    if (r * r > q) r--;
-    if ((r + 1) * (r + 1) <= q) r++;
-    return r;
+    uint32_t r = (uint32_t)sqrtf((float)T * rcpN);
+    if ((uint64_t)r * r * N > T) r--;
+    if ((uint64_t)(r + 1) * (r + 1) * N <= T) r++;
+    const uint32_t v = (r + 1) / 2;
+    return v < 255u ? v : 255u;
 }
 
 __global__ void __launch_bounds__(kDsThreads)
@@ -54,18 +57,18 @@ k_downsample(const uint8_t* __restrict__ X, int64_t nsamp, int D, int64_t nout, 
     }
     for (int64_t i = done + threadIdx.x; i < span; i += kDsThreads) sx[i] = __ldg(x + i);
     __syncthreads();
+    const float rcpD = 1.0f / (float)D;
+    const int sp = (int)span;  // <= kDsSpan: 32-bit indices from here on
     for (int k = threadIdx.x; k < tb && k0 + k < nout; k += kDsThreads) {
-        const int64_t a = (int64_t)k * D, b = min(a + D, span);
+        const int a = k * D, b = min(a + D, sp);
         uint32_t S = 0;
-        int64_t i = a;
+        int i = a;
         if ((D & 3) == 0)  // whole 32-bit words: one dp4a per 4 samples
             for (; i + 4 <= b; i += 4) S = __dp4a(*reinterpret_cast<const uint32_t*>(sx + i), 0x01010101u, S);
         for (; i < b; i++) S += sx[i];
         const uint32_t N = (uint32_t)(b - a);
-        // floor(4 V S / N) <= 4 * 255 * 255; 32-bit when 4 V S < 2^32 (N <= 16448)
-        const uint32_t q = N <= 16448u ? (1020u * S) / N : (uint32_t)((1020ull * S) / N);
-        const uint32_t v = (isqrt_small(q) + 1) / 2;
-        out[(int64_t)c * nout + k0 + k] = (uint8_t)min(v, 255u);
+        const float rcpN = N == (uint32_t)D ? rcpD : 1.0f / (float)N;  // only the last bin is short
+        out[(int64_t)c * nout + k0 + k] = (uint8_t)sqlaw_value(4ull * 255ull * S, N, rcpN);
     }
 }
 
@@ -98,7 +101,7 @@ extern "C" int af_downsample(const uint8_t* d_in, int nchan, int64_t nsamp, int 
 // Other shapes: one thread per 4 samples of every channel, byte accesses.
 namespace {
 
-constexpr int kZW = 8;            // warps per block (channel split)
+constexpr int kZW = 16;           // warps per block (channel split)
 constexpr int kZTile = 512;       // samples per block
 constexpr int kZT = 128;          // generic kernel: threads per block
 
