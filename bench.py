@@ -131,6 +131,26 @@ def dist_setup(n):
     return rank, world, local
 
 
+def beam_seed(rank):
+    """Input seed of a replica: every rank searches its own beam."""
+    return 1 + 7919 * rank
+
+
+def max_over_ranks(v, dist, dev):
+    """The slowest rank's time (replicas: the job ends when the last one does)."""
+    if dist is None:
+        return float(v)
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world, work_per_rank, seconds):
+    """Whole-job rate of N replicas: the units all ranks processed over the slowest time."""
+    return world * work_per_rank / seconds
+
+
 def cpu_oracle_sample(x, D, rows, nout):
     """Time the oracle (as it stands) on a bounded sample: the listed DM rows of
     the same workload, dedispersion + S/N + candidates."""
@@ -585,7 +605,7 @@ def main():
 
     plan = Plan(NCHAN, F_LO, F_HI, TSAMP, DMS)
     nout = plan.nout(NSAMP)
-    x_host, pulses = make_input(1 + 7919 * rank, lambda dms: Plan(NCHAN, F_LO, F_HI, TSAMP, dms).delays())
+    x_host, pulses = make_input(beam_seed(rank), lambda dms: Plan(NCHAN, F_LO, F_HI, TSAMP, dms).delays())
     dev = torch.device("cuda", local)
     x = torch.from_numpy(x_host).to(dev)
     plane = torch.empty((plan.ndm, nout), dtype=torch.int32, device=dev)
@@ -636,10 +656,7 @@ def main():
     ms_total = t_start.elapsed_time(t_end)
     ms_dedisp = float(np.mean([a.elapsed_time(b) for a, b in ev]))
     ncand = int(count.item())
-    if dist is not None:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, dist, dev)
 
     # ---- e2e through the host-buffer entry point (pinned input, copies timed)
     x_pin = torch.from_numpy(x_host).pin_memory()
@@ -655,10 +672,20 @@ def main():
         c, nc = _lib.af_search(H, x_pin.data_ptr(), NSAMP, WIDTHS, THRESH, CAP, sp, out=out)
         plan.cluster(c)
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    # the input copy alone (pinned host -> device), for the e2e breakdown
+    h2d = torch.empty_like(x)
+    for _ in range(2):
+        h2d.copy_(x_pin, non_blocking=True)
+    torch.cuda.synchronize()
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record()
+    for _ in range(5):
+        h2d.copy_(x_pin, non_blocking=True)
+    eb.record()
+    torch.cuda.synchronize()
+    h2d_ms = ea.elapsed_time(eb) / 5
+    del h2d
+    e2e_s = max_over_ranks(e2e_s, dist, dev)
     clocks.stop()
 
     cls_res = None
@@ -688,7 +715,7 @@ def main():
 
     work = float(plan.ndm) * NCHAN * nout
     ms_step = ms_total / args.steps
-    value = world * work / (ms_step * 1e-3)
+    value = aggregate_rate(world, work, ms_step * 1e-3)
     pk = peaks()
     sm_max = float(pk.get("sm_max_mhz", SM_MAX_MHZ_FALLBACK))
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -727,7 +754,8 @@ def main():
                          "hbm": {"achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak,
                                  "basis": "of measured"}},
             "cpu_baseline": cpu,
-            "e2e": {"value": world * work / e2e_s, "unit": UNIT, "h2d_bytes_per_step": NCHAN * NSAMP,
+            "e2e": {"value": aggregate_rate(world, work, e2e_s), "unit": UNIT, "ms": e2e_s * 1e3, "h2d_ms": h2d_ms,
+                    "h2d_gbs": NCHAN * NSAMP / (h2d_ms * 1e-3) / 1e9, "h2d_bytes_per_step": NCHAN * NSAMP,
                     "d2h_bytes_per_step": 4 + 24 * min(nc, CAP)},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,

@@ -202,6 +202,40 @@ size_t af_tile_smem(int nw, int rw)
            2 * aftile::NSTAGE * 8;
 }
 
+int af_dedisp_tile_outputs() { return aftile::tte_of(kDefaultM); }
+
+bool af_dedisp_uses_tiles(af_plan_t p) { return p->tile.fits && !p->force_simple && p->sb_nsub == 0; }
+
+int af_launch_dedisperse_tiles(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,
+                               af_rowstats_t* d_stats, cudaStream_t s, unsigned tile_begin, unsigned tile_end)
+{
+    aftile::TileArgs a;
+    a.X = d_in;
+    a.nsamp = nsamp;
+    a.total = (int64_t)p->nchan * nsamp;
+    a.nchan = p->nchan;
+    a.nchunks = (p->nchan + aftile::CC - 1) / aftile::CC;
+    a.dsort = p->tile.d_dsort;
+    a.perm = p->tile.d_perm;
+    a.dminblk = p->tile.d_dminblk;
+    a.nout = nout;
+    a.rw = p->tile.rw;
+    a.tiles = tile_end - tile_begin;
+    a.nblk = (unsigned)p->tile.nblk;
+    a.Y = d_plane;
+    a.stats = d_stats;
+    a.err = p->d_err;
+    a.tbase = (int64_t)tile_begin * aftile::tte_of(kDefaultM);
+    const unsigned long long nb = (unsigned long long)a.tiles * a.nblk;
+    if (nb == 0) return AF_OK;
+    if (nb > 0x7fffffffULL) return af_set_error(AF_EINVAL, "dedisperse: problem too large for one grid");
+    if (int rc = af_ensure_smem((const void*)aftile::k_tile<kDefaultNW, kDefaultM>, af_tile_smem(kDefaultNW, a.rw)))
+        return rc;
+    aftile::k_tile<kDefaultNW, kDefaultM>
+        <<<(unsigned)nb, (kDefaultNW + 1) * 32, af_tile_smem(kDefaultNW, a.rw), s>>>(a);
+    return af_cuda_check(cudaGetLastError(), "dedisperse launch");
+}
+
 int af_launch_dedisperse(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,
                          af_rowstats_t* d_stats, cudaStream_t s)
 {
@@ -214,30 +248,8 @@ int af_launch_dedisperse(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_
             if (int rc = af_cuda_check(cudaMemsetAsync(d_stats, 0, (size_t)p->ndm * sizeof(af_rowstats_t), s),
                                        "dedisperse stats reset"))
                 return rc;
-        aftile::TileArgs a;
-        a.X = d_in;
-        a.nsamp = nsamp;
-        a.total = (int64_t)p->nchan * nsamp;
-        a.nchan = p->nchan;
-        a.nchunks = (p->nchan + aftile::CC - 1) / aftile::CC;
-        a.dsort = p->tile.d_dsort;
-        a.perm = p->tile.d_perm;
-        a.dminblk = p->tile.d_dminblk;
-        a.nout = nout;
-        a.rw = p->tile.rw;
-        a.tiles = (unsigned)((nout + aftile::tte_of(kDefaultM) - 1) / aftile::tte_of(kDefaultM));
-        a.nblk = (unsigned)p->tile.nblk;
-        a.Y = d_plane;
-        a.stats = d_stats;
-        a.err = p->d_err;
-        const unsigned long long nb = (unsigned long long)a.tiles * a.nblk;
-        if (nb > 0x7fffffffULL) return af_set_error(AF_EINVAL, "dedisperse: problem too large for one grid");
-        if (int rc = af_ensure_smem((const void*)aftile::k_tile<kDefaultNW, kDefaultM>,
-                                    af_tile_smem(kDefaultNW, a.rw)))
-            return rc;
-        aftile::k_tile<kDefaultNW, kDefaultM>
-            <<<(unsigned)nb, (kDefaultNW + 1) * 32, af_tile_smem(kDefaultNW, a.rw), s>>>(a);
-        return af_cuda_check(cudaGetLastError(), "dedisperse launch");
+        const unsigned tiles = (unsigned)((nout + aftile::tte_of(kDefaultM) - 1) / aftile::tte_of(kDefaultM));
+        return af_launch_dedisperse_tiles(p, d_in, nsamp, nout, d_plane, d_stats, s, 0, tiles);
     }
     const unsigned tiles = (unsigned)((nout + kThreads - 1) / kThreads);
     const unsigned long long nblk = (unsigned long long)tiles * (unsigned long long)((p->ndm + kDB - 1) / kDB);

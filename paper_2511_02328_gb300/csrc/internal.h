@@ -112,6 +112,8 @@ struct af_plan_s {
     uint8_t* ws_bw = nullptr;
     af_cand_t* ws_cands = nullptr;
     int32_t* ws_count = nullptr;
+    cudaStream_t ws_copy = nullptr;        // input copies of af_search, overlapped with dedispersion
+    cudaEvent_t ws_ev[4] = {};             // one per copied time segment
 };
 
 int af_check_plan(af_plan_t p);
@@ -123,6 +125,13 @@ int af_launch_dedisperse(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_
                          int32_t* d_plane, af_rowstats_t* d_stats, cudaStream_t s);
 int af_launch_rowstats(const int32_t* d_plane, int ndm, int64_t nout, af_rowstats_t* d_stats,
                        cudaStream_t s);
+// Brute-force tile kernel on output tiles [tile_begin, tile_end) only (row sums
+// accumulate; the caller clears them once), its tile length, and whether a plan
+// uses it.
+int af_launch_dedisperse_tiles(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,
+                               af_rowstats_t* d_stats, cudaStream_t s, unsigned tile_begin, unsigned tile_end);
+int af_dedisp_tile_outputs();
+bool af_dedisp_uses_tiles(af_plan_t p);
 int af_launch_boxcar(const int32_t* d_plane, int ndm, int64_t nout, const af_rowstats_t* d_stats,
                      const af_widths_t& w, af_rowconst_t* d_rowconst, float* d_best_snr,
                      uint8_t* d_best_w, cudaStream_t s);

@@ -59,6 +59,10 @@ static void free_search_ws(af_plan_t p)
     cudaFree(p->ws_bw);
     cudaFree(p->ws_cands);
     cudaFree(p->ws_count);
+    if (p->ws_copy) cudaStreamDestroy(p->ws_copy);
+    for (cudaEvent_t& e : p->ws_ev)
+        if (e) cudaEventDestroy(e), e = nullptr;
+    p->ws_copy = nullptr;
     p->ws_in = nullptr;
     p->ws_plane = nullptr;
     p->ws_snr = nullptr;
@@ -551,10 +555,16 @@ extern "C" int af_search_reserve(af_plan_t p, int64_t max_nsamp, int32_t cap)
     if ((e = cudaMalloc(&p->ws_in, nin)) != cudaSuccess || (e = cudaMalloc(&p->ws_plane, npl * 4)) != cudaSuccess ||
         (e = cudaMalloc(&p->ws_snr, npl * 4)) != cudaSuccess || (e = cudaMalloc(&p->ws_bw, npl)) != cudaSuccess ||
         (e = cudaMalloc(&p->ws_cands, (size_t)cap * sizeof(af_cand_t))) != cudaSuccess ||
-        (e = cudaMalloc(&p->ws_count, 16)) != cudaSuccess) {
+        (e = cudaMalloc(&p->ws_count, 16)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&p->ws_copy, cudaStreamNonBlocking)) != cudaSuccess) {
         free_search_ws(p);
         return af_cuda_check(e, "af_search_reserve");
     }
+    for (cudaEvent_t& ev : p->ws_ev)
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+            free_search_ws(p);
+            return af_cuda_check(e, "af_search_reserve: events");
+        }
     p->ws_nsamp = max_nsamp;
     p->ws_cap = cap;
     return AF_OK;
@@ -573,8 +583,34 @@ extern "C" int af_search(af_plan_t p, const uint8_t* h_in, int64_t nsamp, const 
     af_widths_t w;
     if (int rc = af_check_widths(p, widths, nw, nout, &w)) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    AF_CUDA(cudaMemcpyAsync(p->ws_in, h_in, (size_t)p->nchan * nsamp, cudaMemcpyHostToDevice, s));
-    if (int rc = af_launch_dedisperse(p, p->ws_in, nsamp, nout, p->ws_plane, p->d_stats, s)) return rc;
+    if (af_dedisp_uses_tiles(p)) {
+        // The input arrives in time segments on the copy stream; each segment's
+        // output tiles are dedispersed as soon as their columns (and the Dmax
+        // halo after them) are in, overlapping the rest of the copy.
+        const int64_t tte = af_dedisp_tile_outputs();
+        const unsigned tiles = (unsigned)((nout + tte - 1) / tte);
+        const unsigned K = tiles < 4u ? tiles : 4u;
+        AF_CUDA(cudaEventRecord(p->ws_ev[0], s));  // copies follow the caller's earlier work on s
+        AF_CUDA(cudaStreamWaitEvent(p->ws_copy, p->ws_ev[0], 0));
+        AF_CUDA(cudaMemsetAsync(p->d_stats, 0, (size_t)p->ndm * sizeof(af_rowstats_t), s));
+        int64_t col = 0;
+        for (unsigned k = 0; k < K; k++) {
+            const unsigned tb = tiles * k / K, te = tiles * (k + 1) / K;
+            const int64_t need = k + 1 == K ? nsamp : std::min<int64_t>(nsamp, (int64_t)te * tte + p->dmax);
+            if (need > col) {
+                AF_CUDA(cudaMemcpy2DAsync(p->ws_in + col, (size_t)nsamp, h_in + col, (size_t)nsamp, (size_t)(need - col),
+                                          (size_t)p->nchan, cudaMemcpyHostToDevice, p->ws_copy));
+                col = need;
+            }
+            AF_CUDA(cudaEventRecord(p->ws_ev[k], p->ws_copy));
+            AF_CUDA(cudaStreamWaitEvent(s, p->ws_ev[k], 0));
+            if (int rc = af_launch_dedisperse_tiles(p, p->ws_in, nsamp, nout, p->ws_plane, p->d_stats, s, tb, te))
+                return rc;
+        }
+    } else {
+        AF_CUDA(cudaMemcpyAsync(p->ws_in, h_in, (size_t)p->nchan * nsamp, cudaMemcpyHostToDevice, s));
+        if (int rc = af_launch_dedisperse(p, p->ws_in, nsamp, nout, p->ws_plane, p->d_stats, s)) return rc;
+    }
     if (int rc = af_launch_boxcar(p->ws_plane, p->ndm, nout, p->d_stats, w, p->d_rowconst, p->ws_snr, p->ws_bw, s))
         return rc;
     if (int rc = af_launch_candidates(p->ws_snr, p->ws_bw, p->ndm, nout, w, thresh, 0, p->ws_cands, cap,

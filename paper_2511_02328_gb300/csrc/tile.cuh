@@ -433,15 +433,15 @@ struct Tile {
     }
 };
 
-// Grid = tiles x DM blocks of one job.  Consecutive blocks take all DM blocks
-// of one time tile, so the input window of a time tile stays resident in L2
-// while every DM block reads it.
+// Grid = tiles x DM blocks of one job, tile 0 starting at output a.tbase.
+// Consecutive blocks take all DM blocks of one time tile, so the input window
+// of a time tile stays resident in L2 while every DM block reads it.
 template <int NW, int M>
 __global__ void __launch_bounds__((NW + 1) * 32, 1) k_tile(const TileArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const unsigned jb = blockIdx.x % a.nblk;
-    const int64_t t0 = (int64_t)(blockIdx.x / a.nblk) * Tile<NW, M>::TTE;
+    const int64_t t0 = a.tbase + (int64_t)(blockIdx.x / a.nblk) * Tile<NW, M>::TTE;
     Tile<NW, M>::run(a, jb, t0, smem);
 }
 
