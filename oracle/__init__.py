@@ -8,7 +8,7 @@ The heavy loops live in oracle.c (plain C, fp64, OpenMP over DM rows); this
 module loads it with ctypes and adds numpy-friendly wrappers.  The pure-Python
 brute force for tiny inputs is in oracle.brute, the candidate clustering and
 matching rule in oracle.nms, the cut-out and CNN oracles in oracle.cutout and
-oracle.cnn.
+oracle.cnn, the DM-time slice gridding in oracle.grid.
 """
 import ctypes
 import os
