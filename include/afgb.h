@@ -283,6 +283,27 @@ int af_boxcar_snr_noalloc(const int32_t* d_plane, int ndm, int64_t nout, int nch
                           const int32_t* widths, int nw, float* d_best_snr,
                           uint8_t* d_best_w, void* stream);
 
+/* ---- DM-time slice gridding for an image detector, Sec. 2.4 -------------- *
+ * The plane's time axis is cut into S = ceil(nout / ns) slices of ns columns
+ * (the last one shorter; the paper's n_s = ceil(T_slice / t_samp)) and each
+ * slice (ndm x w) is resampled to an M x M image (the paper uses M = 512):
+ *  - both dimensions shrink (ndm > M and w > M): the exact pixel-area mean,
+ *    U(i,j) = W(i,j) / (ndm w), W = sum_r sum_c ovr(i,r) ovc(j,c) X[r][c],
+ *    ovr(i,r) = |[i ndm, (i+1) ndm) & [r M, (r+1) M)| (ovc likewise);
+ *  - otherwise Lanczos-4 (separable; source x = (i + 0.5) n / M - 0.5, taps
+ *    floor(x) - 3 .. floor(x) + 4 weighted by sinc(t) sinc(t/4), normalised,
+ *    border replicated), evaluated in double;
+ * then normalised per slice to 8 bits:
+ *    Y = floor(255 (U - u_min) / (u_max - u_min + eps) + 1/2),  eps = 1e-6
+ * on the Lanczos path; on the area path exactly from the integer sums W,
+ * without eps (0 for a constant slice).  The paper's pseudo-colour map
+ * (a fixed 256-entry table applied to Y) is left to the caller.
+ *  d_plane int32 [ndm][nout]; d_out uint8 [S][M][M]; d_work int64 [S][2]
+ *  caller-owned scratch; M in 2..4096.  AF_EINVAL if ndm * ns * 2^31 >= 2^63.
+ * Enqueued on `stream`. */
+int af_grid(const int32_t* d_plane, int ndm, int64_t nout, int64_t ns, int M, uint8_t* d_out, int64_t* d_work,
+            void* stream);
+
 /* ---- thresholding and compaction into a candidate list (Sec. 2) -------- *
  * (d,t) is a candidate iff best_snr[d][t] >= thresh and, with w the best
  * width at (d,t), best_snr[d][t] > best_snr[d][u] for t-w <= u < t and

@@ -19,9 +19,11 @@ Readings (the paper names OpenCV's interpolations and gives no formulas):
   * Lanczos-4: separable, source coordinate x = (i + 0.5) h / M - 0.5, taps
     floor(x) - 3 .. floor(x) + 4 with weights L(x - k), L(t) = sinc(t) sinc(t/4),
     normalised to sum 1, indices clamped to the image (replicated border);
-  * eps only guards a constant slice: Y = floor(255 (U - u_min) / (u_max - u_min) + 1/2)
-    (round half up), and Y = 0 where u_max = u_min; on the area path the ratio is
-    taken exactly from W.
+  * Y = floor(255 (U - u_min) / (u_max - u_min + eps) + 1/2) (round half up)
+    with eps = 1e-6 on the Lanczos path, where U is a floating-point sum and a
+    constant slice would otherwise normalise its rounding noise; on the area
+    path U = W / (h w) is exact and the ratio is taken from the integers W
+    without eps (Y = 0 for a constant slice).
 """
 import math
 
@@ -47,10 +49,16 @@ def overlap_matrix(n, M):
 
 
 def area_weights(X, M):
-    """Exact W = Rw X Cw^T (int64) of the pixel-area mean; U = W / (h w)."""
+    """Exact W = Rw X Cw^T (int64) of the pixel-area mean; U = W / (h w).
+    The overlap matrices are sparse (a few entries per row), so the two
+    integer products are taken with scipy's sparse matrix product."""
+    from scipy import sparse
     X = np.asarray(X, dtype=np.int64)
     h, w = X.shape
-    return overlap_matrix(h, M) @ X @ overlap_matrix(w, M).T
+    Rw = sparse.csr_matrix(overlap_matrix(h, M))
+    CwT = sparse.csr_matrix(overlap_matrix(w, M).T)
+    XC = (sparse.csr_matrix(X) @ CwT).toarray().astype(np.int64)
+    return (Rw @ XC).astype(np.int64)
 
 
 def lanczos4_matrix(n, M):
@@ -66,12 +74,15 @@ def lanczos4_matrix(n, M):
     return A
 
 
-def to_gray(num, den_lo_hi):
-    """Y = floor(255 (v - lo) / (hi - lo) + 1/2), 0 where hi == lo."""
+EPS = 1e-6
+
+
+def to_gray(num, den_lo_hi, eps=EPS):
+    """Y = floor(255 (v - lo) / (hi - lo + eps) + 1/2) (0 where hi == lo and eps == 0)."""
     v, lo, hi = num, den_lo_hi[0], den_lo_hi[1]
-    if hi == lo:
+    if hi == lo and eps == 0:
         return np.zeros(v.shape, dtype=np.uint8)
-    return np.floor(255.0 * (v - lo) / (hi - lo) + 0.5).astype(np.uint8)
+    return np.floor(255.0 * (v - lo) / (hi - lo + eps) + 0.5).astype(np.uint8)
 
 
 def gray_exact(W):

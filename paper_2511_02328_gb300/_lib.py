@@ -60,6 +60,7 @@ SIGNATURES = {
     "af_zerodm": [_P, _I, _I64, _P, _P],
     "af_rowstats_robust": [_P, _P, _I64, _P, _P],
     "af_boxcar_snr_robust": [_P, _P, _I64, _P, _P, _I, _P, _P, _P],
+    "af_grid": [_P, _I, _I64, _I64, _I, _P, _P, _P],
     "af_plan_destroy": [_P],
     "af_plan_delays": [_P, _P, _P],
     "af_plan_info": [_P, _P, _P, _P, _P],
@@ -177,6 +178,10 @@ def af_boxcar_snr_robust(plan, d_plane, nout, d_robust, widths, d_best_snr, d_be
     w, pw = _host(widths, np.int32)
     _check(lib().af_boxcar_snr_robust(plan, d_plane, int(nout), d_robust or None, pw, int(w.size), d_best_snr,
                                       d_best_w or None, stream or None), "af_boxcar_snr_robust")
+
+
+def af_grid(d_plane, ndm, nout, ns, M, d_out, d_work, stream=0):
+    _check(lib().af_grid(d_plane, int(ndm), int(nout), int(ns), int(M), d_out, d_work, stream or None), "af_grid")
 
 
 AF_FS_MEDIAN = 0

@@ -79,7 +79,10 @@ def test_gray_levels():
     lo, hi = W.min(), W.max()
     f = 255.0 * (W - lo) / (hi - lo)
     ok = np.abs(f - np.floor(f) - 0.5) > 1e-6
-    assert np.array_equal(grid.gray_exact(W)[ok], grid.to_gray(W.astype(np.float64), (lo, hi))[ok])
+    assert np.array_equal(grid.gray_exact(W)[ok], grid.to_gray(W.astype(np.float64), (lo, hi), eps=0)[ok])
+    # the Lanczos path keeps eps: a slice that is constant up to rounding maps to 0
+    U = np.full((8, 8), 42.0) + np.random.default_rng(5).normal(0, 1e-12, (8, 8))
+    assert np.all(grid.to_gray(U, (U.min(), U.max())) == 0)
 
 
 def test_path_selection():
