@@ -216,14 +216,16 @@ def match_pulses(cands, pulses, dms):
     return np.array(out)
 
 
-def run_subband(args, dev, x, x_host, pulses, brute, ms_brute, stream):
+def run_subband(args, dev, x, x_host, pulses, brute, ms_brute, stream, n0=None, nsub=None):
     """Two-stage subband dedispersion (Sec. 2.3) of the same input: device time
     of af_dedisperse, the equivalent brute-force rate, and the S/N kept on the
     injected pulses against the brute-force plane (same boxcar and threshold)."""
     import torch
     from paper_2511_02328_gb300 import _lib
     from paper_2511_02328_gb300.search import Plan
-    sbp = Plan(NCHAN, F_LO, F_HI, TSAMP, DMS, subband=dict(n0=SB_N0, nsub=SB_NSUB, fs_mode=_lib.AF_FS_INVSQ,
+    n0 = SB_N0 if n0 is None else n0
+    nsub = SB_NSUB if nsub is None else nsub
+    sbp = Plan(NCHAN, F_LO, F_HI, TSAMP, DMS, subband=dict(n0=n0, nsub=nsub, fs_mode=_lib.AF_FS_INVSQ,
                                                            block_len=NSAMP))
     info = sbp.subband_info()
     nout = sbp.nout(NSAMP)
@@ -253,10 +255,11 @@ def run_subband(args, dev, x, x_host, pulses, brute, ms_brute, stream):
     ratio = found["subband"][both] / found["brute"][both]
     work = float(sbp.ndm) * NCHAN * nout
     stage1 = float(info["ncoarse"]) * NCHAN * (nout + int(info["R"].max()))
-    stage2 = float(sbp.ndm) * SB_NSUB * nout
+    stage2 = float(sbp.ndm) * nsub * nout
     res = {
         "workload": "the same input, two-stage subband dedispersion: n0=%d fine DMs per coarse DM, %d subbands of "
-                    "%d channels, 1/f^2-weighted centres, one time block" % (SB_N0, SB_NSUB, NCHAN // SB_NSUB),
+                    "%d channels, 1/f^2-weighted centres, one time block" % (n0, nsub, NCHAN // nsub),
+        "n0": n0, "nsub": nsub,
         "ms": ms, "effective_rate": work / (ms * 1e-3), "unit": UNIT, "speedup_vs_brute": ms_brute / ms,
         "block_len": info["block_len"],
         "realtime_factor": nout * TSAMP / (ms * 1e-3), "launches": launches,
@@ -591,6 +594,7 @@ def main():
     ap.add_argument("--no-prep", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-classifier", action="store_true")
+    ap.add_argument("--subband-sweep", default="", help="extra subband settings, e.g. 4x64,16x64,8x32 (n0 x nsub)")
     ap.add_argument("--stream-rounds", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -714,6 +718,14 @@ def main():
         del snr, bw
         torch.cuda.empty_cache()
         sub_res = run_subband(args, dev, x, x_host, pulses, plan, ms_dedisp, stream)
+        if args.subband_sweep:
+            sweep = []
+            for item in args.subband_sweep.split(","):
+                a_, b_ = item.split("x")
+                r_ = run_subband(args, dev, x, x_host, pulses, plan, ms_dedisp, stream, int(a_), int(b_))
+                sweep.append({k: r_[k] for k in ("n0", "nsub", "ms", "speedup_vs_brute", "snr_ratio_vs_brute",
+                                                  "pulses_found")})
+            sub_res["sweep"] = sweep
 
     stream_res = None
     if not args.no_stream:

@@ -2,6 +2,8 @@
 // backward and Adam, built from the kernels of nn.cu (the paper's detector is
 // YOLOv11n on DM-time images, Sec. 2.5; this small CNN replaces it).
 //
+// Inference (no labels) runs the fused kernel of nn_fused.cu; the layered
+// kernels below keep the activations that the backward pass needs.
 // Network: input NHWC bf16 [n][64][64][2]; three blocks conv3x3 (+bias) ->
 // ReLU -> 2x2 max pool with 2 -> 16 -> 32 -> 64 channels; global average pool;
 // fully connected 64 -> 2; softmax cross-entropy (label 1 = pulse).
@@ -224,6 +226,12 @@ extern "C" int af_model_get_grads(af_model_t m, float* h, int64_t n)
 
 static int forward(af_model_t m, const __nv_bfloat16* x, int n, const int32_t* y, float* prob, cudaStream_t s)
 {
+    if (!y) {  // inference: one fused kernel, activations never leave shared memory
+        const float* P = m->d_params;
+        return nn_forward_fused(x, n, P + m->L[0].woff, P + m->L[0].boff, P + m->L[1].woff, P + m->L[1].boff,
+                                P + m->L[2].woff, P + m->L[2].boff, P + m->fw_off, P + m->fb_off, m->d_logits, prob,
+                                s);
+    }
     const __nv_bfloat16* a = x;
     for (int l = 0; l < NL; l++) {
         const Layer& L = m->L[l];

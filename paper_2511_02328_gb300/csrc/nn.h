@@ -28,3 +28,9 @@ int nn_unpack_dw(const float* dw, int cout, int k9, int kp, float* g, cudaStream
 int nn_f32_to_bf16(const float* x, int64_t n, __nv_bfloat16* y, cudaStream_t s);
 int nn_cutouts(const uint8_t* X, int64_t nsamp, int nchan, const int32_t* D, int ndm, const int32_t* plane,
                int64_t nout, const af_cand_t* cands, int n, __nv_bfloat16* out, cudaStream_t s);
+// Inference in one kernel (nn_fused.cu): logits [n][2] and P(pulse) [n] of
+// bf16 inputs [n][64][64][2]; weights from the fp32 master parameters.
+size_t nn_forward_fused_smem();
+int nn_forward_fused(const __nv_bfloat16* x, int n, const float* w0, const float* b0, const float* w1,
+                     const float* b1, const float* w2, const float* b2, const float* fw, const float* fb,
+                     float* logits, float* prob, cudaStream_t s);
