@@ -740,6 +740,7 @@ def main():
     sm_max = float(pk.get("sm_max_mhz", SM_MAX_MHZ_FALLBACK))
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = nsm * 128 * sm_max * 1e6 / 1e12          # T int32 lane-ops/s
+    add_rate, pattern_rate = _lib.af_diag_int_rates()  # measured on this device (probe kernels)
     achieved = work / (ms_dedisp * 1e-3) / 1e12        # T adds/s
     hbm_peak = float(pk.get("hbm_gbs", 6800.0))
     alg_bytes = NCHAN * NSAMP + plan.ndm * nout * 4
@@ -771,6 +772,9 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                          "frac": achieved / alu_peak, "traffic": None,
                          "peak_basis": "%d SMs x 128 int32 lanes x %.0f MHz (derived, of max clock)" % (nsm, sm_max),
+                         "measured_int32_add_peak": add_rate / 1e12, "frac_of_measured_add_peak": achieved * 1e12 / add_rate,
+                         "measured_inner_pattern_peak": pattern_rate / 1e12,
+                         "frac_of_measured_pattern_peak": achieved * 1e12 / pattern_rate,
                          "hbm": {"achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak,
                                  "basis": "of measured"}},
             "cpu_baseline": cpu,

@@ -494,6 +494,19 @@ int af_stream_restore(af_stream_t s, int beam, const uint8_t* h_overlap, int64_t
 /* Waits for all work, stops the dispatcher and frees everything. */
 int af_stream_close(af_stream_t s);
 
+/* ---- diagnostic: measured integer issue rates ---------------------------- *
+ * Not a step of the paper's method: the denominator of the dedispersion
+ * roofline, measured on the current device.  Runs two short probe kernels
+ * (one block of 1024 threads per SM, a few milliseconds, synchronous) and
+ * returns, in thread-operations per second,
+ *   add_per_s           32-bit 2-input additions (8 independent chains per thread)
+ *   pattern_adds_per_s  sample additions of the dedispersion inner step: two
+ *                       32-bit shared loads (4 uint8 samples each), widening
+ *                       into 16-bit lanes (and-mask, byte permute) and the
+ *                       paired adds, i.e. 8 sample additions per step.
+ * Allocates nothing (a static device array receives the probes' results). */
+int af_diag_int_rates(double* add_per_s, double* pattern_adds_per_s);
+
 /* ---- candidate classifier ----------------------------------------------- *
  * The paper detects pulses with a YOLOv11n network on DM-time images
  * (Sec. 2.5); its weights and data sets are not available, so the library

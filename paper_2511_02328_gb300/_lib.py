@@ -61,6 +61,7 @@ SIGNATURES = {
     "af_rowstats_robust": [_P, _P, _I64, _P, _P],
     "af_boxcar_snr_robust": [_P, _P, _I64, _P, _P, _I, _P, _P, _P],
     "af_grid": [_P, _I, _I64, _I64, _I, _P, _P, _P],
+    "af_diag_int_rates": [_P, _P],
     "af_plan_destroy": [_P],
     "af_plan_delays": [_P, _P, _P],
     "af_plan_info": [_P, _P, _P, _P, _P],
@@ -182,6 +183,13 @@ def af_boxcar_snr_robust(plan, d_plane, nout, d_robust, widths, d_best_snr, d_be
 
 def af_grid(d_plane, ndm, nout, ns, M, d_out, d_work, stream=0):
     _check(lib().af_grid(d_plane, int(ndm), int(nout), int(ns), int(M), d_out, d_work, stream or None), "af_grid")
+
+
+def af_diag_int_rates():
+    """(int32 2-input adds per second, dedispersion-pattern sample adds per second)."""
+    a, b = _D(), _D()
+    _check(lib().af_diag_int_rates(ctypes.byref(a), ctypes.byref(b)), "af_diag_int_rates")
+    return a.value, b.value
 
 
 AF_FS_MEDIAN = 0

@@ -1,0 +1,102 @@
+// diag.cu -- measured integer issue rates of the device, the denominator of
+// the dedispersion roofline (no counterpart in the paper).
+//
+// Two probe kernels, one block of 1024 threads per SM (120 KB of dynamic
+// shared memory keeps it to one), a fixed number of iterations each:
+//   ADD:     8 independent chains of 2-input 32-bit additions per thread;
+//   PATTERN: the tile kernel's inner step -- two 32-bit shared loads (two
+//            channels, 4 samples each), widening into 16-bit lanes
+//            (w & 0x00FF00FF, prmt(w, 0x4341)) and the paired adds -- counted
+//            as 8 sample additions per iteration.
+// Results go to a static device array (no allocation); every shared address is
+// inside the block's own array.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int kDT = 1024;
+constexpr int kDIters = 4096;
+constexpr int kDMaxBlocks = 1024;
+constexpr int kDSmem = 120 * 1024;
+
+__device__ uint32_t g_diag_sink[kDMaxBlocks];
+
+template <int OP>
+__global__ void __launch_bounds__(kDT, 1) k_diag(uint32_t seed, uint32_t mask)
+{
+    extern __shared__ uint32_t sm[];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kDSmem / 4; i += kDT) sm[i] = (uint32_t)i * 2654435761u + seed;
+    __syncthreads();
+    uint32_t a0 = tid ^ seed, a1 = a0 * 3u, a2 = a0 * 5u, a3 = a0 * 7u, a4 = a0 * 11u, a5 = a0 * 13u, a6 = a0 * 17u,
+             a7 = a0 * 19u;
+    // per warp a 2 KB slice; offsets below stay under (31 * 2048 + mask + 128) bytes < kDSmem
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm) + (tid >> 5) * 2048u + (tid & 31) * 4u;
+#pragma unroll 2
+    for (int it = 0; it < kDIters; it++) {
+        if (OP == 0) {
+            asm volatile("add.u32 %0, %0, %1;" : "+r"(a0) : "r"(a1));
+            asm volatile("add.u32 %0, %0, %1;" : "+r"(a1) : "r"(a2));
+            asm volatile("add.u32 %0, %0, %1;" : "+r"(a2) : "r"(a3));
+            asm volatile("add.u32 %0, %0, %1;" : "+r"(a3) : "r"(a4));
+            asm volatile("add.u32 %0, %0, %1;" : "+r"(a4) : "r"(a5));
+            asm volatile("add.u32 %0, %0, %1;" : "+r"(a5) : "r"(a6));
+            asm volatile("add.u32 %0, %0, %1;" : "+r"(a6) : "r"(a7));
+            asm volatile("add.u32 %0, %0, %1;" : "+r"(a7) : "r"(a0));
+        } else {
+            // two independent accumulator pairs, one per parity of the iteration
+            uint32_t w1, w2;
+            const uint32_t off = ((uint32_t)it * 128u) & mask;
+            asm volatile("ld.shared.u32 %0, [%1];" : "=r"(w1) : "r"(sbase + off));
+            asm volatile("ld.shared.u32 %0, [%1];" : "=r"(w2) : "r"(sbase + ((off + 4096u) & mask)));
+            if (it & 1) {
+                a0 += (w1 & 0x00FF00FFu) + (w2 & 0x00FF00FFu);
+                a1 += __byte_perm(w1, 0u, 0x4341) + __byte_perm(w2, 0u, 0x4341);
+            } else {
+                a2 += (w1 & 0x00FF00FFu) + (w2 & 0x00FF00FFu);
+                a3 += __byte_perm(w1, 0u, 0x4341) + __byte_perm(w2, 0u, 0x4341);
+            }
+        }
+    }
+    if (tid == 0) g_diag_sink[blockIdx.x] = a0 ^ a1 ^ a2 ^ a3 ^ a4 ^ a5 ^ a6 ^ a7;
+}
+
+template <int OP>
+int time_probe(int nblk, float* ms)
+{
+    if (int rc = af_ensure_smem((const void*)k_diag<OP>, kDSmem)) return rc;
+    k_diag<OP><<<nblk, kDT, kDSmem>>>(12345u, 0x7fffu);
+    cudaEvent_t a, b;
+    AF_CUDA(cudaEventCreate(&a));
+    AF_CUDA(cudaEventCreate(&b));
+    cudaEventRecord(a);
+    k_diag<OP><<<nblk, kDT, kDSmem>>>(777u, 0x7fffu);
+    cudaEventRecord(b);
+    cudaError_t e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return af_cuda_check(e, "af_diag_int_rates probe");
+}
+
+}  // namespace
+
+extern "C" int af_diag_int_rates(double* add_per_s, double* pattern_adds_per_s)
+{
+    if (!add_per_s || !pattern_adds_per_s) return af_set_error(AF_EINVAL, "af_diag_int_rates: NULL output");
+    int dev = 0, nsm = 0;
+    AF_CUDA(cudaGetDevice(&dev));
+    AF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int nblk = nsm < kDMaxBlocks ? nsm : kDMaxBlocks;
+    float ms0 = 0.f, ms1 = 0.f;
+    if (int rc = time_probe<0>(nblk, &ms0)) return rc;
+    if (int rc = time_probe<1>(nblk, &ms1)) return rc;
+    const double threads = (double)nblk * kDT * kDIters;
+    *add_per_s = threads * 8.0 / (ms0 * 1e-3);
+    *pattern_adds_per_s = threads * 8.0 / (ms1 * 1e-3);
+    return AF_OK;
+}

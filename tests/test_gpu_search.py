@@ -314,3 +314,15 @@ def test_plans_with_different_windows_coexist(c1_data):
     assert np.array_equal(plane.cpu().numpy(), Y)
     small.close()
     big.close()
+
+
+def test_diag_int_rates_plausible():
+    # the measured integer rates that the bench's roofline reports: positive,
+    # below the nominal 128 lanes x 2.07 GHz per SM, and the dedispersion step
+    # no faster than plain additions
+    from paper_2511_02328_gb300 import _lib
+    add, pattern = _lib.af_diag_int_rates()
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    nominal = nsm * 128 * 2.07e9
+    assert 0.1 * nominal < add <= 1.05 * nominal
+    assert 0.05 * nominal < pattern <= 1.05 * add
