@@ -203,6 +203,11 @@ STREAM_WORKLOAD = ("streaming: 19 beams, 4096 ch x 49.152 us uint8, windows of 2
 
 
 SB_N0, SB_NSUB = 8, 64
+# DRAM read + write bytes of one k_tile<11,8> launch on this workload, from an ncu capture of the same
+# kernel (dram__bytes_read.sum + dram__bytes_write.sum); reset to None whenever the kernel changes
+TILE_TRAFFIC_BYTES = 1.34e10
+TILE_TRAFFIC_BASIS = ("ncu dram__bytes read+write of k_tile<11,8> at 2^17 samples (5.23 GB, 83 output tiles), "
+                      "scaled by the output tiles to this 2^18-sample launch (212 tiles)")
 
 
 def match_pulses(cands, pulses, dms):
@@ -770,7 +775,8 @@ def main():
             "dedisp_ms": ms_dedisp,
             "candidates": ncand,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                         "frac": achieved / alu_peak, "traffic": None,
+                         "frac": achieved / alu_peak, "traffic": TILE_TRAFFIC_BYTES,
+                         "traffic_basis": TILE_TRAFFIC_BASIS,
                          "peak_basis": "%d SMs x 128 int32 lanes x %.0f MHz (derived, of max clock)" % (nsm, sm_max),
                          "measured_int32_add_peak": add_rate / 1e12, "frac_of_measured_add_peak": achieved * 1e12 / add_rate,
                          "measured_inner_pattern_peak": pattern_rate / 1e12,

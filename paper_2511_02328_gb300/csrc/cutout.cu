@@ -21,7 +21,7 @@
 
 namespace {
 
-constexpr int S = 64, T = 256, NWARP = T / 32;
+constexpr int S = 64, T = 512, NWARP = T / 32;
 constexpr int CH = 128;  // window positions per chunk (4 per lane)
 constexpr int kDelaysInShared = 8192;  // channels whose delay row is staged in shared memory
 
@@ -50,7 +50,7 @@ __device__ __forceinline__ void block_minmax(long long& lo, long long& hi)
 
 // Adds the window positions of this warp's chunk [p0, p0 + CH) held in pos[]
 // to the lane's two bins 2*lane, 2*lane + 1 (bin j = positions [j b, (j+1) b)).
-__device__ __forceinline__ void bin_chunk(const long long* pos, int p0, int b, int lane, long long& b0,
+__device__ __forceinline__ void bin_chunk(const int32_t* pos, int p0, int b, int lane, long long& b0,
                                           long long& b1)
 {
 #pragma unroll
@@ -74,14 +74,14 @@ __device__ __forceinline__ void bin_chunk(const long long* pos, int p0, int b, i
 // 4l .. 4l+3 of the chunk (consecutive lanes: consecutive bytes or words),
 // summing over the row's channels in registers, then folding the chunk into
 // its two bins through a per-warp shared array.
-__global__ void __launch_bounds__(T) k_cutout(const uint8_t* __restrict__ X, int64_t nsamp, int nchan,
+__global__ void __launch_bounds__(T, 1) k_cutout(const uint8_t* __restrict__ X, int64_t nsamp, int nchan,
                                               const int32_t* __restrict__ D, int ndm,
                                               const int32_t* __restrict__ plane, int64_t nout,
                                               const af_cand_t* __restrict__ cands, __nv_bfloat16* __restrict__ out)
 {
-    __shared__ long long pos[NWARP][CH];
+    __shared__ int32_t pos[NWARP][CH];  // a chunk's column sums (plane values, or <= 255 * 1024)
     __shared__ int32_t sD[kDelaysInShared];  // the candidate's delay row (when it fits)
-    constexpr int RPW = 2 * S / NWARP;  // image rows per warp (8 DM-time + 8 frequency-time)
+    constexpr int RPW = 2 * S / NWARP;  // image rows per warp (half DM-time, half frequency-time)
     const af_cand_t cd = cands[blockIdx.x];
     const int d = cd.dm_idx;
     __nv_bfloat16* o = out + (int64_t)blockIdx.x * S * S * 2;
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(T) k_cutout(const uint8_t* __restrict__ X, int
     const int64_t start = (int64_t)cd.t - 32 * (int64_t)b;
     const int span = S * b;
     const int gsz = nchan / S;
-    long long* wp = pos[warp];
+    int32_t* wp = pos[warp];
     const bool dsh = nchan <= kDelaysInShared;
     if (dsh)
         for (int c = threadIdx.x; c < nchan; c += T) sD[c] = __ldg(D + (int64_t)d * nchan + c);
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(T) k_cutout(const uint8_t* __restrict__ X, int
                 bool ok[4];
 #pragma unroll
                 for (int q = 0; q < 4; q++) ok[q] = p0 + 4 * lane + q < span && s0 + q >= 0 && s0 + q < nout;
-                long long a[4] = {0, 0, 0, 0};
+                int32_t a[4] = {0, 0, 0, 0};
                 if (ft) {
                     uint32_t u[4] = {0u, 0u, 0u, 0u};
 #pragma unroll 8
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(T) k_cutout(const uint8_t* __restrict__ X, int
                             if (ok[q]) u[q] += __ldg(X + base + q);
                     }
 #pragma unroll
-                    for (int q = 0; q < 4; q++) a[q] = u[q];
+                    for (int q = 0; q < 4; q++) a[q] = (int32_t)u[q];
                 } else {
                     const int32_t* yr = plane + (int64_t)pr * nout;
 #pragma unroll
