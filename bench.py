@@ -499,6 +499,75 @@ def run_classifier(args, dev, x, plan, stream):
     }
 
 
+# The paper's GPU benchmarks (Sec. 3): 8-bit synthetic data, 40 us, 1000-1500 MHz, DM 0-1024; the kernel times
+# it prints for an RTX 4090 at the ends of each sweep (dedisp = the brute-force comparison code, ASTROFLOW = its
+# approximate subband kernel), in seconds.
+PAPER_SEC3 = {
+    "channels": {"span_s": 22.0, "ndm": 1500, "sweep": [512, 1024, 2048, 4096, 8192],
+                 "rtx4090_dedisp_s": {512: 1.03, 8192: 8.72}, "rtx4090_astroflow_s": {512: 0.11, 8192: 0.96}},
+    "dm_trials": {"span_s": 20.0, "nchan": 2048, "sweep": [512, 1024, 2048, 4096, 8192],
+                  "rtx4090_dedisp_s": {543: 1.21, 8298: 9.21}, "rtx4090_astroflow_s": {512: 0.091, 8192: 1.295}},
+}
+
+
+def run_paper_sec3(args, dev, stream):
+    """Our exact brute-force dedispersion and our two-stage subband dedispersion (n0 = 8, 64 subbands of 7.8 MHz) on
+    the configurations of the paper's Sec. 3 benchmarks; kernel time (CUDA events, mean of 3 after a warm-up)
+    and R = span / time."""
+    import torch
+    from paper_2511_02328_gb300 import _lib, synth
+    from paper_2511_02328_gb300.search import Plan
+    sp = stream.cuda_stream
+    tsamp = 40e-6
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(3):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 3
+
+    def one(nchan, ndm, span_s, seed):
+        dms = np.linspace(0.0, 1024.0, ndm)
+        bp = Plan(nchan, F_LO, F_HI, tsamp, dms)
+        nout = int(round(span_s / tsamp))
+        nsamp = nout + bp.dmax
+        sb = Plan(nchan, F_LO, F_HI, tsamp, dms, subband=dict(n0=8, nsub=min(64, nchan),
+                                                               fs_mode=_lib.AF_FS_INVSQ, block_len=1 << 17))
+        x = synth.filterbank_torch(nchan, nsamp, seed=seed, device=dev)
+        plane = torch.empty((ndm, nout), dtype=torch.int32, device=dev)
+        ms_b = timed(lambda: _lib.af_dedisperse(bp.handle, x.data_ptr(), nsamp, plane.data_ptr(), 0, sp))
+        nout_s = sb.nout(nsamp)
+        ms_s = timed(lambda: _lib.af_dedisperse(sb.handle, x.data_ptr(), nsamp, plane.data_ptr(), 0, sp))
+        _lib.af_plan_check(bp.handle)
+        _lib.af_plan_check(sb.handle)
+        kb = bp.kernel()
+        out = {"nchan": nchan, "ndm": ndm, "nout": nout, "brute_kernel": f'{kb["path"]}/ring {kb["ring"]}',
+               "brute_ms": ms_b, "brute_R": span_s / (ms_b * 1e-3),
+               "brute_rate": float(ndm) * nchan * nout / (ms_b * 1e-3), "subband_ms": ms_s,
+               "subband_R": nout_s * tsamp / (ms_s * 1e-3)}
+        del x, plane
+        bp.close()
+        sb.close()
+        torch.cuda.empty_cache()
+        return out
+
+    res = {}
+    c = PAPER_SEC3["channels"]
+    res["channels"] = [one(n, c["ndm"], c["span_s"], 900 + i) for i, n in enumerate(c["sweep"])]
+    d = PAPER_SEC3["dm_trials"]
+    res["dm_trials"] = [one(d["nchan"], n, d["span_s"], 950 + i) for i, n in enumerate(d["sweep"])]
+    res["paper_rtx4090_s"] = {k: {"dedisp": v["rtx4090_dedisp_s"], "astroflow": v["rtx4090_astroflow_s"]}
+                              for k, v in PAPER_SEC3.items()}
+    res["note"] = ("brute = the exact plane; subband = n0 8, 64 subbands, 1/f^2 centres (approximate, like the "
+                   "paper's own kernel); kernel time only, inputs resident, as the paper's R")
+    return res
+
+
 def run_stream(args, dev, clocks):
     """Real-time paced multi-beam stream through the engine: returns latency
     percentiles and throughput.  Data: one seeded noise pool on pinned host
@@ -600,6 +669,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-classifier", action="store_true")
     ap.add_argument("--subband-sweep", default="", help="extra subband settings, e.g. 4x64,16x64,8x32 (n0 x nsub)")
+    ap.add_argument("--paper-sec3", action="store_true", help="also time the paper's Sec. 3 benchmark configurations")
     ap.add_argument("--stream-rounds", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -705,6 +775,14 @@ def main():
     e2e_s = max_over_ranks(e2e_s, dist, dev)
     clocks.stop()
 
+    sec3_res = None
+    if args.paper_sec3:
+        del snr, bw
+        torch.cuda.empty_cache()
+        sec3_res = run_paper_sec3(args, dev, stream)
+        snr = torch.empty((plan.ndm, nout), dtype=torch.float32, device=dev)
+        bw = torch.empty((plan.ndm, nout), dtype=torch.uint8, device=dev)
+
     cls_res = None
     if not args.no_classifier:
         cls_res = run_classifier(args, dev, x, plan, stream)
@@ -795,6 +873,7 @@ def main():
             "prep": prep_res,
             "batch": batch_res,
             "classifier": cls_res,
+            "paper_sec3": sec3_res,
         }
         print(json.dumps(line))
     plan.close()

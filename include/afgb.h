@@ -114,6 +114,20 @@ int af_plan_delays(af_plan_t plan, int32_t* host_out, int32_t* dmax);
 /* Plan dimensions (any output pointer may be NULL). */
 int af_plan_info(af_plan_t plan, int* nchan, int* ndm, int32_t* dmax, double* tsamp);
 
+/* Which kernel af_dedisperse runs for this plan (any output may be NULL):
+ *  path    AF_PATH_SIMPLE (one thread per output, every delay read from the
+ *          table), AF_PATH_TILE (the shared-memory tile kernel) or
+ *          AF_PATH_SUBBAND (the two stages of Sec. 2.3);
+ *  ring    depth of the tile kernel's shared-memory ring (4; 3 or 2 when a
+ *          coarse DM grid widens each channel's window), 0 on the simple path;
+ *  spread  largest delay difference between DMs of one block of the tile
+ *          kernel, in samples (what sets the window width).
+ * Read-only; no device work.  Not a step of the paper's method. */
+#define AF_PATH_SIMPLE 0
+#define AF_PATH_TILE 1
+#define AF_PATH_SUBBAND 2
+int af_plan_kernel(af_plan_t plan, int* path, int* ring, int32_t* spread);
+
 /* Reads and clears the plan's device error flag, which a kernel of this plan
  * sets when one of its bounded waits (for an asynchronous copy) ran out and it
  * abandoned its work; returns AF_ETIMEOUT if the flag was set, else AF_OK.

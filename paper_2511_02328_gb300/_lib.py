@@ -67,6 +67,7 @@ SIGNATURES = {
     "af_plan_info": [_P, _P, _P, _P, _P],
     "af_plan_nout": [_P, _I64, _P],
     "af_plan_check": [_P],
+    "af_plan_kernel": [_P, _P, _P, _P],
     "af_dedisperse": [_P, _P, _I64, _P, _P, _P],
     "af_rowstats": [_P, _P, _I64, _P, _P],
     "af_boxcar_snr": [_P, _P, _I64, _P, _P, _I, _P, _P, _P],
@@ -230,6 +231,17 @@ def af_plan_info(plan):
     _check(lib().af_plan_info(plan, ctypes.byref(nchan), ctypes.byref(ndm), ctypes.byref(dmax),
                               ctypes.byref(tsamp)), "af_plan_info")
     return nchan.value, ndm.value, dmax.value, tsamp.value
+
+
+PATH_SIMPLE, PATH_TILE, PATH_SUBBAND = 0, 1, 2
+
+
+def af_plan_kernel(plan):
+    """(path, ring, spread) of the kernel that dedisperses this plan."""
+    path, ring, spread = _I(), _I(), _I32()
+    _check(lib().af_plan_kernel(plan, ctypes.byref(path), ctypes.byref(ring), ctypes.byref(spread)),
+           "af_plan_kernel")
+    return path.value, ring.value, spread.value
 
 
 def af_plan_delays(plan):

@@ -159,6 +159,9 @@ int af_tile_tables_build(const int32_t* delays, const double* dms, int ndm, int 
     t->spread = spread;
     t->rw = spread < (1 << 20) ? aftile::window_bytes(spread, m) : (1 << 20);
     t->fits = spread < (1 << 20) && af_tile_smem(nw, t->rw) <= (size_t)optin;
+    t->ns1 = 0;
+    for (int ns = 4; ns >= 2 && t->ns1 == 0; ns--)
+        if (spread < (1 << 20) && af_tile_smem(nw, t->rw, ns) <= (size_t)optin) t->ns1 = ns;
     cudaError_t e;
     if ((e = cudaMalloc(&t->d_dsort, dsort.size() * 4)) != cudaSuccess ||
         (e = cudaMemcpy(t->d_dsort, dsort.data(), dsort.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -181,6 +184,15 @@ void af_tile_tables_free(af_tile_tables* t)
     t->d_perm = nullptr;
     t->d_dminblk = nullptr;
     t->fits = false;
+    t->ns1 = 0;
+}
+
+// The single-plan tile kernel for a ring depth (4, or 3 / 2 for wide windows).
+static const void* single_kernel(int ns)
+{
+    return ns == 4 ? (const void*)aftile::k_tile<kDefaultNW, kDefaultM, 4>
+         : ns == 3 ? (const void*)aftile::k_tile<kDefaultNW, kDefaultM, 3>
+                   : (const void*)aftile::k_tile<kDefaultNW, kDefaultM, 2>;
 }
 
 int af_prepare_dedisp_tables(af_plan_t p)
@@ -191,20 +203,18 @@ int af_prepare_dedisp_tables(af_plan_t p)
     cudaError_t e;
     if ((e = cudaMalloc(&p->d_err, sizeof(int))) != cudaSuccess || (e = cudaMemset(p->d_err, 0, sizeof(int))) != cudaSuccess)
         return af_cuda_check(e, "af_plan: error flag");
-    if (p->tile.fits)
-        return af_ensure_smem((const void*)aftile::k_tile<kDefaultNW, kDefaultM>, af_tile_smem(kDefaultNW, p->tile.rw));
+    if (p->tile.ns1 > 0) return af_ensure_smem(single_kernel(p->tile.ns1), af_tile_smem(kDefaultNW, p->tile.rw, p->tile.ns1));
     return AF_OK;
 }
 
-size_t af_tile_smem(int nw, int rw)
+size_t af_tile_smem(int nw, int rw, int ns)
 {
-    return (size_t)aftile::NSTAGE * aftile::CC * rw + (size_t)aftile::NSTAGE * nw * aftile::TABW * sizeof(int) +
-           2 * aftile::NSTAGE * 8;
+    return (size_t)ns * aftile::CC * rw + (size_t)ns * nw * aftile::TABW * sizeof(int) + 2 * (size_t)ns * 8;
 }
 
 int af_dedisp_tile_outputs() { return aftile::tte_of(kDefaultM); }
 
-bool af_dedisp_uses_tiles(af_plan_t p) { return p->tile.fits && !p->force_simple && p->sb_nsub == 0; }
+bool af_dedisp_uses_tiles(af_plan_t p) { return p->tile.ns1 > 0 && !p->force_simple && p->sb_nsub == 0; }
 
 int af_launch_dedisperse_tiles(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,
                                af_rowstats_t* d_stats, cudaStream_t s, unsigned tile_begin, unsigned tile_end)
@@ -229,10 +239,15 @@ int af_launch_dedisperse_tiles(af_plan_t p, const uint8_t* d_in, int64_t nsamp, 
     const unsigned long long nb = (unsigned long long)a.tiles * a.nblk;
     if (nb == 0) return AF_OK;
     if (nb > 0x7fffffffULL) return af_set_error(AF_EINVAL, "dedisperse: problem too large for one grid");
-    if (int rc = af_ensure_smem((const void*)aftile::k_tile<kDefaultNW, kDefaultM>, af_tile_smem(kDefaultNW, a.rw)))
-        return rc;
-    aftile::k_tile<kDefaultNW, kDefaultM>
-        <<<(unsigned)nb, (kDefaultNW + 1) * 32, af_tile_smem(kDefaultNW, a.rw), s>>>(a);
+    const int ns = p->tile.ns1;
+    const size_t smem = af_tile_smem(kDefaultNW, a.rw, ns);
+    if (int rc = af_ensure_smem(single_kernel(ns), smem)) return rc;
+    if (ns == 4)
+        aftile::k_tile<kDefaultNW, kDefaultM, 4><<<(unsigned)nb, (kDefaultNW + 1) * 32, smem, s>>>(a);
+    else if (ns == 3)
+        aftile::k_tile<kDefaultNW, kDefaultM, 3><<<(unsigned)nb, (kDefaultNW + 1) * 32, smem, s>>>(a);
+    else
+        aftile::k_tile<kDefaultNW, kDefaultM, 2><<<(unsigned)nb, (kDefaultNW + 1) * 32, smem, s>>>(a);
     return af_cuda_check(cudaGetLastError(), "dedisperse launch");
 }
 
@@ -243,7 +258,7 @@ int af_launch_dedisperse(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_
     // brute-force kernels, which compute the same plane from the effective delays
     if (p->sb_nsub > 0 && p->sb.tile.fits && !p->force_simple && !p->force_brute)
         return af_launch_subband(p, d_in, nsamp, nout, d_plane, d_stats, s);
-    if (p->tile.fits && !p->force_simple) {
+    if (p->tile.ns1 > 0 && !p->force_simple) {
         if (d_stats)
             if (int rc = af_cuda_check(cudaMemsetAsync(d_stats, 0, (size_t)p->ndm * sizeof(af_rowstats_t), s),
                                        "dedisperse stats reset"))
@@ -258,6 +273,24 @@ int af_launch_dedisperse(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_
                                                         tiles);
     if (int rc = af_cuda_check(cudaGetLastError(), "dedisperse launch")) return rc;
     if (d_stats) return af_launch_rowstats(d_plane, p->ndm, nout, d_stats, s);
+    return AF_OK;
+}
+
+extern "C" int af_plan_kernel(af_plan_t p, int* path, int* ring, int32_t* spread)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    int pa = AF_PATH_SIMPLE, rg = 0, sp = p->tile.spread;
+    if (p->sb_nsub > 0 && p->sb.tile.fits && !p->force_simple && !p->force_brute) {
+        pa = AF_PATH_SUBBAND;
+        rg = aftile::NSTAGE;
+        sp = p->sb.tile.spread;
+    } else if (p->tile.ns1 > 0 && !p->force_simple) {
+        pa = AF_PATH_TILE;
+        rg = p->tile.ns1;
+    }
+    if (path) *path = pa;
+    if (ring) *ring = rg;
+    if (spread) *spread = sp;
     return AF_OK;
 }
 

@@ -43,7 +43,9 @@ struct af_tile_tables {
     int32_t* d_perm = nullptr;     // [ndm_pad] plane row of each sorted DM (-1: padding)
     int32_t* d_dminblk = nullptr;  // [nblk][nchan] smallest delay per block and channel
     int ndm_pad = 0, nblk = 0, spread = 0, rw = 0;
-    bool fits = false;             // the channel window fits in shared memory
+    bool fits = false;             // the channel window fits in shared memory with the 4-deep ring
+    int ns1 = 0;                   // ring depth of the single-plan kernel: 4, else 3 or 2 (coarse DM
+                                   // grids), 0 if none fits
 };
 // Raises a kernel's dynamic shared-memory limit to at least `bytes` (the
 // attribute belongs to the kernel, not to a plan: it only ever grows).
@@ -52,7 +54,7 @@ int af_ensure_smem(const void* kernel, size_t bytes);
 int af_tile_tables_build(const int32_t* delays, const double* dms, int ndm, int nchan, int nw, int m, int device,
                          af_tile_tables* t);
 void af_tile_tables_free(af_tile_tables* t);
-size_t af_tile_smem(int nw, int rw);
+size_t af_tile_smem(int nw, int rw, int ns = 4);
 
 // ---------------------------------------------------------------- subband
 // Device side of a two-stage subband plan (Sec. 2.3): stage-1 tile tables

@@ -7,7 +7,8 @@
 // One tile = NW DM rows (one consumer warp each; DMs taken in ascending order
 // so a block's delays per channel span the least) x TTE = 128*M - 4 outputs.
 // A producer warp streams the channels through shared memory CC = 32 at a
-// time in an NSTAGE-deep ring (full/empty mbarriers): for every channel one
+// time in an NS-deep ring (full/empty mbarriers; NS = 4, or 3 / 2 when a
+// coarse DM grid widens the windows): for every channel one
 // bulk async copy (cp.async.bulk) brings the byte window
 // [t0 + Dmin_c, t0 + Dmax_c + 128*M) of that channel, 16-byte aligned, and
 // the producer writes each consumer warp's offset table for the chunk.
@@ -45,7 +46,7 @@
 namespace aftile {
 
 constexpr int CC = 32;                 // channels per stage (one per producer lane)
-constexpr int NSTAGE = 4;              // depth of the shared-memory ring
+constexpr int NSTAGE = 4;              // default depth of the shared-memory ring
 constexpr int TABW = 48;               // ints per (stage, warp) table: 4 starts, 4 counts,
                                        // 40 offsets (at most 35 used; the slack absorbs
                                        // one-pair-ahead reads)
@@ -87,10 +88,10 @@ __host__ __device__ constexpr int tte_of(int M) { return 128 * M - 4; }
 // 128*M bytes read per warp, rounded to 16).
 __host__ __device__ inline int window_bytes(int spread, int M) { return (15 + spread + 128 * M + 15) & ~15; }
 
-template <int NW>
+template <int NW, int NS = NSTAGE>
 __host__ __device__ inline size_t smem_bytes(int rw)
 {
-    return (size_t)NSTAGE * CC * rw + (size_t)NSTAGE * NW * TABW * sizeof(int) + 2 * NSTAGE * 8;
+    return (size_t)NS * CC * rw + (size_t)NS * NW * TABW * sizeof(int) + 2 * NS * 8;
 }
 
 __device__ __forceinline__ unsigned lanemask_lt()
@@ -100,7 +101,7 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return m;
 }
 
-template <int NW, int M, bool SUB = false>
+template <int NW, int M, bool SUB = false, int NS = NSTAGE>
 struct Tile {
     static constexpr int NT = (NW + 1) * 32;  // + one producer warp
     static constexpr int TTE = tte_of(M);
@@ -290,12 +291,12 @@ struct Tile {
     static __device__ __forceinline__ void run(const TileArgs& a, unsigned jb, int64_t t0, uint8_t* smem)
     {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        int* tab = (int*)(smem + (size_t)NSTAGE * CC * a.rw);
-        uint64_t* bars = (uint64_t*)(tab + NSTAGE * NW * TABW);
-        const uint32_t full0 = afptx::smem_addr(bars), empty0 = full0 + 8 * NSTAGE;
+        int* tab = (int*)(smem + (size_t)NS * CC * a.rw);
+        uint64_t* bars = (uint64_t*)(tab + NS * NW * TABW);
+        const uint32_t full0 = afptx::smem_addr(bars), empty0 = full0 + 8 * NS;
 
         if (threadIdx.x == 0) {
-            for (int s = 0; s < NSTAGE; s++) {
+            for (int s = 0; s < NS; s++) {
                 afptx::mbar_init(full0 + 8 * s, 1);
                 afptx::mbar_init(empty0 + 8 * s, NW);
             }
@@ -310,10 +311,10 @@ struct Tile {
             load_chunk(a, cur, 0, (int)jb, lane);
             int kk = 0;
             for (; kk < a.nchunks; kk++) {
-                const int st = kk % NSTAGE;
+                const int st = kk % NS;
                 load_chunk(a, nxt, kk + 1, (int)jb, lane);
-                if (kk >= NSTAGE &&
-                    !afptx::mbar_wait_bounded(empty0 + 8 * st, (uint32_t)(kk / NSTAGE - 1) & 1u, WAIT_LIMIT)) {
+                if (kk >= NS &&
+                    !afptx::mbar_wait_bounded(empty0 + 8 * st, (uint32_t)(kk / NS - 1) & 1u, WAIT_LIMIT)) {
                     if (lane == 0) atomicExch(a.err, 1);
                     break;
                 }
@@ -321,8 +322,8 @@ struct Tile {
                 cur = nxt;
             }
             // leave no copy in flight behind (the consumers normally wait for all of them)
-            for (int k2 = max(0, kk - NSTAGE); k2 < kk; k2++)
-                afptx::mbar_wait_bounded(full0 + 8 * (k2 % NSTAGE), (uint32_t)(k2 / NSTAGE) & 1u, WAIT_LIMIT);
+            for (int k2 = max(0, kk - NS); k2 < kk; k2++)
+                afptx::mbar_wait_bounded(full0 + 8 * (k2 % NS), (uint32_t)(k2 / NS) & 1u, WAIT_LIMIT);
             return;
         }
 
@@ -339,8 +340,8 @@ struct Tile {
         const uint32_t lane4 = (uint32_t)lane * 4u;
         int sb = 0, sq = 0;  // subband mode: current subband and chunk within it
         for (int kk = 0; kk < a.nchunks; kk++) {
-            const int st = kk % NSTAGE;
-            if (!afptx::mbar_wait_bounded(full0 + 8 * st, (uint32_t)(kk / NSTAGE) & 1u, WAIT_LIMIT)) {
+            const int st = kk % NS;
+            if (!afptx::mbar_wait_bounded(full0 + 8 * st, (uint32_t)(kk / NS) & 1u, WAIT_LIMIT)) {
                 if (lane == 0) atomicExch(a.err, 1);
                 return;
             }
@@ -436,13 +437,13 @@ struct Tile {
 // Grid = tiles x DM blocks of one job, tile 0 starting at output a.tbase.
 // Consecutive blocks take all DM blocks of one time tile, so the input window
 // of a time tile stays resident in L2 while every DM block reads it.
-template <int NW, int M>
+template <int NW, int M, int NS = NSTAGE>
 __global__ void __launch_bounds__((NW + 1) * 32, 1) k_tile(const TileArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const unsigned jb = blockIdx.x % a.nblk;
-    const int64_t t0 = a.tbase + (int64_t)(blockIdx.x / a.nblk) * Tile<NW, M>::TTE;
-    Tile<NW, M>::run(a, jb, t0, smem);
+    const int64_t t0 = a.tbase + (int64_t)(blockIdx.x / a.nblk) * Tile<NW, M, false, NS>::TTE;
+    Tile<NW, M, false, NS>::run(a, jb, t0, smem);
 }
 
 // Stage 1 of the subband dedispersion: grid = tiles x row blocks, tile 0

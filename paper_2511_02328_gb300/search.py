@@ -48,6 +48,11 @@ class Plan:
     def subband_info(self):
         return _lib.af_plan_subband_info(self.handle)
 
+    def kernel(self):
+        """dict(path='simple'|'tile'|'subband', ring, spread) of the dedispersion kernel."""
+        path, ring, spread = _lib.af_plan_kernel(self.handle)
+        return dict(path=("simple", "tile", "subband")[path], ring=ring, spread=spread)
+
     def close(self):
         if self.handle:
             _lib.af_plan_destroy(self.handle)

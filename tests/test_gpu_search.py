@@ -267,9 +267,48 @@ def test_fallback_kernel_for_wide_delay_spread():
     nsamp = int(D.max()) + 3000
     x = np.random.default_rng(4).integers(0, 256, (nchan, nsamp), dtype=np.uint8)
     p = Plan(nchan, 1000.0, 1500.0, tsamp, dms)
+    assert p.kernel()["path"] == "simple"
     plane = p.dedisperse(torch.from_numpy(x).cuda())
     torch.cuda.synchronize()
     assert np.array_equal(plane.cpu().numpy(), oracle.dedisperse(x, D))
+    p.close()
+
+
+def _expected_ring(spread, nw=11, m=8):
+    """Deepest ring (4, 3, 2) whose shared memory fits the device's opt-in
+    limit: ring x (32 channel windows of rw bytes + the offset tables + 2 barriers)."""
+    optin = getattr(torch.cuda.get_device_properties(0), "shared_memory_per_block_optin", 232448)
+    rw = (15 + spread + 128 * m + 15) & ~15
+    for ns in (4, 3, 2):
+        if ns * 32 * rw + ns * nw * 48 * 4 + 16 * ns <= optin:
+            return ns
+    return 0
+
+
+@pytest.mark.parametrize("step,ring", [(1.0, 4), (4.0, 3), (5.0, 3), (6.0, 2), (10.0, 2), (12.0, 0)])
+def test_coarse_dm_grids_shallower_ring(step, ring):
+    """Coarse DM grids widen each channel's window; the tile kernel then runs
+    with a 3- or 2-deep ring before the fallback kernel takes over.  Every
+    depth gives the oracle's plane and row sums bit-exact (256 channels,
+    1000-1500 MHz, 98.304 us, 61 DMs of the given step, a ragged last tile)."""
+    from paper_2511_02328_gb300.search import Plan
+    nchan, tsamp = 256, 98.304e-6
+    dms = np.arange(0.0, 1.0 + 60 * step, step)
+    D = oracle.delay_table(nchan, 1000.0, 1500.0, tsamp, dms)
+    nsamp = int(D.max()) + 3 * 8192 + 77
+    x = np.random.default_rng(int(step * 10)).integers(0, 256, (nchan, nsamp), dtype=np.uint8)
+    p = Plan(nchan, 1000.0, 1500.0, tsamp, dms)
+    k = p.kernel()
+    assert k["ring"] == _expected_ring(k["spread"]) == ring
+    assert k["path"] == ("tile" if ring else "simple")
+    stats = torch.empty((p.ndm, 2), dtype=torch.int64, device="cuda")
+    plane = p.dedisperse(torch.from_numpy(x).cuda(), stats=stats)
+    torch.cuda.synchronize()
+    Y = oracle.dedisperse(x, D)
+    assert np.array_equal(plane.cpu().numpy(), Y)
+    S, Q = oracle.rowstats(Y)
+    st = stats.cpu().numpy()
+    assert np.array_equal(st[:, 0], S) and np.array_equal(st[:, 1], Q)
     p.close()
 
 
@@ -279,6 +318,7 @@ def test_simple_kernel_forced_matches(c1_data, monkeypatch):
     x, D, Y, _, _ = c1_data
     monkeypatch.setenv("AFGB_DEDISP_KERNEL", "simple")
     p = _plan(C1)
+    assert p.kernel() == dict(path="simple", ring=0, spread=p.kernel()["spread"])
     stats = torch.empty((p.ndm, 2), dtype=torch.int64, device="cuda")
     plane = p.dedisperse(torch.from_numpy(x).cuda(), stats=stats)
     torch.cuda.synchronize()
