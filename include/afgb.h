@@ -116,16 +116,25 @@ int af_plan_info(af_plan_t plan, int* nchan, int* ndm, int32_t* dmax, double* ts
 
 /* Which kernel af_dedisperse runs for this plan (any output may be NULL):
  *  path    AF_PATH_SIMPLE (one thread per output, every delay read from the
- *          table), AF_PATH_TILE (the shared-memory tile kernel) or
- *          AF_PATH_SUBBAND (the two stages of Sec. 2.3);
- *  ring    depth of the tile kernel's shared-memory ring (4; 3 or 2 when a
- *          coarse DM grid widens each channel's window), 0 on the simple path;
- *  spread  largest delay difference between DMs of one block of the tile
- *          kernel, in samples (what sets the window width).
+ *          table), AF_PATH_TILE (the shared-memory tile kernel over channels),
+ *          AF_PATH_SUBBAND (the two stages of Sec. 2.3) or AF_PATH_PAIRS (the
+ *          same exact sum over channel-pair rows: adjacent channels added
+ *          once per distinct relative delay, then the tile kernel over pair
+ *          rows; used when the rows of a time block fit the row budget,
+ *          AFGB_PAIR_BUDGET_MB, default min(16 GiB, 1/8 of device memory),
+ *          else the tile kernel runs);
+ *  ring    depth of the kernel's shared-memory ring (4; 3 or 2 when a coarse
+ *          DM grid widens each channel's window; 2 for pair rows), 0 on the
+ *          simple path;
+ *  spread  largest delay difference between DMs of one block of the kernel,
+ *          in samples (what sets the window width).
+ * AFGB_DEDISP_KERNEL=tile|simple in the environment at plan creation forces
+ * the channel tile kernel or the simple kernel.
  * Read-only; no device work.  Not a step of the paper's method. */
 #define AF_PATH_SIMPLE 0
 #define AF_PATH_TILE 1
 #define AF_PATH_SUBBAND 2
+#define AF_PATH_PAIRS 3
 int af_plan_kernel(af_plan_t plan, int* path, int* ring, int32_t* spread);
 
 /* Reads and clears the plan's device error flag, which a kernel of this plan

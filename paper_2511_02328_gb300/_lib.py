@@ -233,7 +233,7 @@ def af_plan_info(plan):
     return nchan.value, ndm.value, dmax.value, tsamp.value
 
 
-PATH_SIMPLE, PATH_TILE, PATH_SUBBAND = 0, 1, 2
+PATH_SIMPLE, PATH_TILE, PATH_SUBBAND, PATH_PAIRS = 0, 1, 2, 3
 
 
 def af_plan_kernel(plan):

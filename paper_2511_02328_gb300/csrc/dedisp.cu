@@ -124,7 +124,7 @@ int af_ensure_smem(const void* kernel, size_t bytes)
 // ascending (ties keep list order), padded to a multiple of nw by repeating
 // the last one; the smallest delay of each block per channel; the window.
 int af_tile_tables_build(const int32_t* delays, const double* dms, int ndm, int nchan, int nw, int m, int device,
-                         af_tile_tables* t)
+                         af_tile_tables* t, std::vector<int32_t>* h_dsort, std::vector<int32_t>* h_dmin)
 {
     af_tile_tables_free(t);
     std::vector<int> order(ndm);
@@ -162,6 +162,8 @@ int af_tile_tables_build(const int32_t* delays, const double* dms, int ndm, int 
     t->ns1 = 0;
     for (int ns = 4; ns >= 2 && t->ns1 == 0; ns--)
         if (spread < (1 << 20) && af_tile_smem(nw, t->rw, ns) <= (size_t)optin) t->ns1 = ns;
+    if (h_dsort) *h_dsort = dsort;
+    if (h_dmin) *h_dmin = dmin;
     cudaError_t e;
     if ((e = cudaMalloc(&t->d_dsort, dsort.size() * 4)) != cudaSuccess ||
         (e = cudaMemcpy(t->d_dsort, dsort.data(), dsort.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -203,6 +205,8 @@ int af_prepare_dedisp_tables(af_plan_t p)
     cudaError_t e;
     if ((e = cudaMalloc(&p->d_err, sizeof(int))) != cudaSuccess || (e = cudaMemset(p->d_err, 0, sizeof(int))) != cudaSuccess)
         return af_cuda_check(e, "af_plan: error flag");
+    if (p->sb_nsub == 0)
+        if (int rc = af_pairs_build(p)) return rc;
     if (p->tile.ns1 > 0) return af_ensure_smem(single_kernel(p->tile.ns1), af_tile_smem(kDefaultNW, p->tile.rw, p->tile.ns1));
     return AF_OK;
 }
@@ -213,6 +217,11 @@ size_t af_tile_smem(int nw, int rw, int ns)
 }
 
 int af_dedisp_tile_outputs() { return aftile::tte_of(kDefaultM); }
+
+bool af_dedisp_uses_pairs(af_plan_t p, int64_t nout)
+{
+    return p->pairs.ok && !p->force_simple && !p->force_tile && p->sb_nsub == 0 && af_pairs_block(p, nout) > 0;
+}
 
 bool af_dedisp_uses_tiles(af_plan_t p) { return p->tile.ns1 > 0 && !p->force_simple && p->sb_nsub == 0; }
 
@@ -258,6 +267,7 @@ int af_launch_dedisperse(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_
     // brute-force kernels, which compute the same plane from the effective delays
     if (p->sb_nsub > 0 && p->sb.tile.fits && !p->force_simple && !p->force_brute)
         return af_launch_subband(p, d_in, nsamp, nout, d_plane, d_stats, s);
+    if (af_dedisp_uses_pairs(p, nout)) return af_launch_pairs(p, d_in, nsamp, nout, d_plane, d_stats, s);
     if (p->tile.ns1 > 0 && !p->force_simple) {
         if (d_stats)
             if (int rc = af_cuda_check(cudaMemsetAsync(d_stats, 0, (size_t)p->ndm * sizeof(af_rowstats_t), s),
@@ -284,6 +294,10 @@ extern "C" int af_plan_kernel(af_plan_t p, int* path, int* ring, int32_t* spread
         pa = AF_PATH_SUBBAND;
         rg = aftile::NSTAGE;
         sp = p->sb.tile.spread;
+    } else if (p->pairs.ok && !p->force_simple && !p->force_tile) {
+        pa = AF_PATH_PAIRS;
+        rg = p->pairs.shape == 0 ? 2 : p->pairs.shape == 1 ? 3 : 4;
+        sp = p->pairs.tt.spread;
     } else if (p->tile.ns1 > 0 && !p->force_simple) {
         pa = AF_PATH_TILE;
         rg = p->tile.ns1;

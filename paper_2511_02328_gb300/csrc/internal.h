@@ -52,7 +52,8 @@ struct af_tile_tables {
 int af_ensure_smem(const void* kernel, size_t bytes);
 
 int af_tile_tables_build(const int32_t* delays, const double* dms, int ndm, int nchan, int nw, int m, int device,
-                         af_tile_tables* t);
+                         af_tile_tables* t, std::vector<int32_t>* h_dsort = nullptr,
+                         std::vector<int32_t>* h_dmin = nullptr);
 void af_tile_tables_free(af_tile_tables* t);
 size_t af_tile_smem(int nw, int rw, int ns = 4);
 
@@ -72,6 +73,38 @@ struct af_sb_device {
     int cps = 0;                   // 32-channel chunks per subband
 };
 
+// ---------------------------------------------------------------- pair rows
+// Single-plan dedispersion through channel-pair rows (pairs.cu): host tables
+// (built once per plan), device tables, and the row buffer of one time block.
+struct af_pair_tables {
+    bool ok = false;               // the plan uses this path
+    int np = 0, nrows = 0, rwe = 0, maxdr = 0;
+    double rows_per_pair = 0;      // rows copied per pair and DM block (mean)
+    size_t budget = 0;             // bytes the row buffer may take (AFGB_PAIR_BUDGET_MB at plan creation)
+    int shape = 0;                 // ring shape of the row kernel (pairs.cu)
+    af_tile_tables tt;             // DM order and block minima for this block shape
+    std::vector<int32_t> h_rb, h_dlo, h_dhi, h_srow, h_scpart;
+    int32_t* d_rdelta = nullptr;   // [nrows] delta of each row (sorted within a pair)
+    int4* d_pinfo = nullptr;       // [np] first row, rows, dlo, row length
+    int64_t* d_rowoff = nullptr;   // [nrows] element offset in the row buffer
+    int2* d_chunks = nullptr;      // per chunk: row slots, first slot
+    int32_t* d_chkoff = nullptr;   // [nblk + 1]
+    int* d_tabs = nullptr;         // per chunk: every consumer warp's table
+    int32_t* d_sbytes = nullptr;   // per slot: window bytes
+    int64_t* d_soff = nullptr;     // per slot: window offset for a time block's first tile
+    uint16_t* d_ps = nullptr;      // row buffer
+    size_t ps_bytes = 0;
+    int64_t L = 0, maxlen = 0;     // current time block and longest row
+};
+int af_pairs_build(af_plan_t p);
+void af_pairs_free(af_pair_tables* T);
+int64_t af_pairs_block(af_plan_t p, int64_t nout);
+int af_pairs_reserve(af_plan_t p, int64_t nout);
+int af_launch_pairs(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,
+                    af_rowstats_t* d_stats, cudaStream_t s);
+int af_pair_tile_outputs();
+bool af_dedisp_uses_pairs(af_plan_t p, int64_t nout);
+
 // ---------------------------------------------------------------- plan
 struct af_plan_s {
     int nchan = 0;
@@ -90,6 +123,9 @@ struct af_plan_s {
     bool force_simple = false;             // use the fallback kernel (AFGB_DEDISP_KERNEL=simple)
     bool force_brute = false;              // subband plans: brute-force tile kernel on the
                                            // effective delays (AFGB_DEDISP_KERNEL=brute)
+    bool force_tile = false;               // byte tile kernel even where pair rows apply
+                                           // (AFGB_DEDISP_KERNEL=tile)
+    af_pair_tables pairs;                  // pair-row path of brute-force plans
 
     // two-stage subband dedispersion (sb_nsub > 0); `delays` then holds the
     // effective table D[j(m)][c] + R[m][s(c)]

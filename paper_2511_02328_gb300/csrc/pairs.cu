@@ -1,0 +1,679 @@
+// pairs.cu -- exact brute-force dedispersion (Sec. 2.3) of single plans
+// through shared channel-pair rows.
+//
+//   Y[d][t] = sum_c X[c][t + D[d][c]]
+//           = sum_q P(q, delta_q(d))[t + D[d][2q]],
+//   P(q, delta)[u] = X[2q][u] + X[2q+1][u + delta],
+//   delta_q(d)     = D[d][2q+1] - D[d][2q].
+//
+// The same integer sum, grouped: two adjacent channels are added once per
+// distinct relative delay delta of the pair (a pair has a handful over the
+// whole DM range and one or two inside a block of neighbouring DMs), and the
+// DM sums then run over pair rows, half as many terms as channels.
+//
+// Stage 1 (k_pair_rows) writes every row P(q, delta) as uint16 for one time
+// block of L outputs (row element e is time ub + e, ub = (T0 + min_d D[d][2q])
+// rounded down to 8).
+//
+// Stage 2 (k_pair_tile) is a tile kernel over rows: a block takes NW DM rows
+// (one consumer warp each, DMs ascending) and TTE = 1016 outputs; a producer
+// warp streams the block's rows through an NS-deep shared-memory ring, up to
+// SL rows per stage (whole pairs), one bulk async copy per row window plus one
+// for the chunk's consumer tables of (stage slot, offset) per pair, which the
+// host computes once (tiles start at multiples of 8, so no offset depends on
+// the tile).  Lane L
+// of a consumer warp owns outputs 2 (L + 32 m) + k, m < 16, k < 2: one
+// aligned 32-bit shared load brings the two 16-bit samples of a group, so the
+// pairs are bucketed by the parity r of the sample offset; one IADD3 adds two
+// pairs' words into the 16-bit lanes of the bucket's accumulator (at most
+// 128 pairs of 510 between folds); a fold re-aligns bucket 1 by one sample
+// (one lane shuffle) into the 32-bit output sums.
+//
+// Every wait is bounded (the tile kernel's error flag); the host tables are
+// built once per plan and the row buffer is sized per call from a budget.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace {
+
+constexpr int kPNW = 15;            // DM rows (consumer warps) per block
+// Ring shapes (row slots per stage, at most one per producer lane; depth):
+// 0 = 32 x 2, 1 = 24 x 3, 2 = 16 x 4 (AFGB_PAIR_SHAPE at plan creation, else
+// the first that fits the shared memory; on the 4096-channel workload 32 x 2
+// measured 28.0 ms, 16 x 4 29.5 ms).
+constexpr int kShapes = 3;
+constexpr int kShapeSL[kShapes] = {32, 24, 16};
+constexpr int kShapeNS[kShapes] = {2, 3, 4};
+constexpr int kPMG = 16;            // 2-sample groups per lane
+constexpr int kPTTE = 1016;         // outputs per tile: a multiple of 8 below 64 * kPMG - 1
+constexpr int kPTABW = 40;          // ints per (stage, warp) table: 2 starts, 2 counts, <= 34 offsets
+constexpr int kPFlush = 128;        // pairs per fold: 128 * 510 < 2^16
+constexpr uint32_t kPWait = 1u << 24;
+constexpr int kET = 4096;           // stage 1: row samples per block
+constexpr int kS1T = 256;
+constexpr int kMaxDr = 32768;       // stage 1: largest delta range of a pair
+constexpr int kMinTiles = 8;        // smallest useful time block, in tiles
+
+inline int64_t r8(int64_t x) { return (x + 7) & ~(int64_t)7; }
+inline int64_t r16(int64_t x) { return (x + 15) & ~(int64_t)15; }
+
+struct PairArgs {
+    const uint16_t* PS;      // rows of the time block
+    const int2* chunks;      // per chunk: {row slots, first slot}
+    const int32_t* chkoff;   // [nblk + 1] first chunk of each block
+    const int* tabs;         // per chunk: NW x TABW ints, every consumer warp's table for its ring stage
+    const int32_t* sbytes;   // per slot: window bytes
+    const int64_t* soff;     // per slot: element offset of its window in PS for the block's first tile
+    const int32_t* perm;     // [ndm_pad] plane row, -1 = padding
+    int rwb;
+    unsigned nblk;
+    int64_t T0;              // first output of the time block (a multiple of 8)
+    int64_t tend;            // outputs t < tend are written
+    int64_t nout;
+    int32_t* Y;
+    af_rowstats_t* stats;
+    int* err;
+};
+
+// ------------------------------------------------------------------ stage 1
+// Block = (pair q, ET row samples); writes every row of the pair for them.
+// pinfo[q] = {first row, rows, dlo, row length}; rows of a pair are sorted by
+// delta, so [dmn, dmx] is the pair's delta range.
+__global__ void __launch_bounds__(kS1T)
+k_pair_rows(const uint8_t* __restrict__ X, int64_t nsamp, int nchan, const int4* __restrict__ pinfo,
+            const int32_t* __restrict__ rdelta, const int64_t* __restrict__ rowoff, int64_t T0, int etiles,
+            uint16_t* __restrict__ PS)
+{
+    extern __shared__ __align__(16) uint8_t sm[];
+    const int tid = threadIdx.x;
+    const int q = blockIdx.x / etiles;
+    const int64_t e0 = (int64_t)(blockIdx.x % etiles) * kET;
+    const int4 pi = __ldg(pinfo + q);
+    if (e0 >= pi.w) return;
+    const int c0 = 2 * q, c1 = 2 * q + 1;
+    const bool single = c1 >= nchan;
+    const int64_t u0 = ((T0 + pi.z) & ~(int64_t)7) + e0;
+    const int dmn = __ldg(rdelta + pi.x), dmx = __ldg(rdelta + pi.x + pi.y - 1);
+    uint8_t* sa = sm;
+    uint8_t* sb = sm + kET;
+    const int bw = kET + (dmx - dmn) + 4;  // + the word the last funnel shift reads past
+    const uint8_t* x0 = X + (int64_t)c0 * nsamp;
+    const uint8_t* x1 = X + (int64_t)(single ? c0 : c1) * nsamp;
+    for (int i = tid; i < kET; i += kS1T) {
+        const int64_t u = u0 + i;
+        sa[i] = (u >= 0 && u < nsamp) ? __ldg(x0 + u) : (uint8_t)0;
+    }
+    for (int i = tid; i < bw; i += kS1T) {
+        const int64_t u = u0 + dmn + i;
+        sb[i] = (!single && u >= 0 && u < nsamp) ? __ldg(x1 + u) : (uint8_t)0;
+    }
+    __syncthreads();
+    const int i0 = tid * 16;
+    if (e0 + i0 >= pi.w) return;  // row lengths are multiples of 16
+    uint32_t alo[4], ahi[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const uint32_t w = *reinterpret_cast<const uint32_t*>(sa + i0 + 4 * k);
+        alo[k] = __byte_perm(w, 0u, 0x4140);  // samples 0, 1 into 16-bit lanes
+        ahi[k] = __byte_perm(w, 0u, 0x4342);  // samples 2, 3
+    }
+    for (int k = 0; k < pi.y; k++) {
+        const int s = __ldg(rdelta + pi.x + k) - dmn + i0;
+        const int s4 = s & ~3;
+        const uint32_t sh = (uint32_t)(s & 3) * 8u;
+        uint32_t w[5];
+#pragma unroll
+        for (int j = 0; j < 5; j++) w[j] = *reinterpret_cast<const uint32_t*>(sb + s4 + 4 * j);
+        uint32_t o[8];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint32_t b = __funnelshift_r(w[j], w[j + 1], sh);
+            o[2 * j] = alo[j] + __byte_perm(b, 0u, 0x4140);
+            o[2 * j + 1] = ahi[j] + __byte_perm(b, 0u, 0x4342);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(PS + __ldg(rowoff + pi.x + k) + e0 + i0);
+        dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+        dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+    }
+}
+
+// ------------------------------------------------------------------ stage 2
+template <int NW, int SL, int NS>
+struct PairTile {
+    static __device__ __forceinline__ int2 load_cd(const PairArgs& a, int cbeg, int nchk, int kk)
+    {
+        return kk < nchk ? __ldg(a.chunks + cbeg + kk) : make_int2(0, 0);
+    }
+
+    // Chunk c (block-local kk) into stage st: its precomputed table block and
+    // one window per row slot, all completing on the stage's full barrier.
+    static __device__ __forceinline__ void produce(const PairArgs& a, uint8_t* smem, int* tab, uint32_t full_bar,
+                                                   int c, const int2& cd, uint32_t bytes, int64_t src, int st,
+                                                   int lane)
+    {
+        constexpr uint32_t TB = (uint32_t)(NW * kPTABW * 4);
+        const uint32_t tot = __reduce_add_sync(0xffffffffu, bytes) + TB;
+        __syncwarp();
+        afptx::fence_proxy_async();  // the consumers' reads of this stage come before the copies
+        if (lane == 0) {
+            afptx::mbar_arrive_expect_tx(full_bar, tot);
+            afptx::bulk_g2s(afptx::smem_addr(tab + st * NW * kPTABW), a.tabs + (int64_t)c * NW * kPTABW, TB,
+                            full_bar);
+        }
+        __syncwarp();
+        if (lane < cd.x && bytes)
+            afptx::bulk_g2s(afptx::smem_addr(smem) + (uint32_t)((st * SL + lane) * a.rwb), a.PS + src, bytes,
+                            full_bar);
+    }
+
+    // Bucket 1 holds, in lane L group m, samples 2 (L + 32 m) + 1 and + 2: output
+    // k = 0 takes its own upper half, k = 1 the lower half of the next lane's word
+    // (lane 0 of group m + 1 for L = 31).
+    static __device__ __forceinline__ void fold(uint32_t (&A)[2][kPMG], uint32_t (&Wd)[kPMG][2], int lane)
+    {
+        uint32_t carry = 0u;
+#pragma unroll
+        for (int m = kPMG - 1; m >= 0; m--) {
+            const uint32_t a0 = A[0][m], a1 = A[1][m];
+            const uint32_t lo1 = a1 & 0xFFFFu;
+            uint32_t nx = __shfl_down_sync(0xffffffffu, lo1, 1);
+            const uint32_t l0 = __shfl_sync(0xffffffffu, lo1, 0);
+            if (lane == 31) nx = carry;
+            carry = l0;
+            Wd[m][0] += (a0 & 0xFFFFu) + (a1 >> 16);
+            Wd[m][1] += (a0 >> 16) + nx;
+            A[0][m] = 0u;
+            A[1][m] = 0u;
+        }
+    }
+
+    static __device__ __forceinline__ void run(const PairArgs& a, uint8_t* smem)
+    {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const unsigned jb = blockIdx.x % a.nblk;
+        const int64_t t0 = a.T0 + (int64_t)(blockIdx.x / a.nblk) * kPTTE;
+        int* tab = (int*)(smem + (size_t)NS * SL * a.rwb);
+        uint64_t* bars = (uint64_t*)(tab + NS * NW * kPTABW);
+        const uint32_t full0 = afptx::smem_addr(bars), empty0 = full0 + 8 * NS;
+        const int cbeg = __ldg(a.chkoff + jb), nchk = __ldg(a.chkoff + jb + 1) - cbeg;
+
+        if (threadIdx.x == 0) {
+            for (int s = 0; s < NS; s++) {
+                afptx::mbar_init(full0 + 8 * s, 1);
+                afptx::mbar_init(empty0 + 8 * s, NW);
+            }
+            afptx::fence_mbar_init();
+        }
+        __syncthreads();
+
+        if (warp == NW) {
+            // ---------------- producer warp: chunk descriptors two ahead, slot records one ahead
+            const int64_t dt = t0 - a.T0;
+            int2 cda = load_cd(a, cbeg, nchk, 0), cdb = load_cd(a, cbeg, nchk, 1);
+            uint32_t bcur = 0, bnxt = 0;
+            int64_t scur = 0, snxt = 0;
+            if (lane < cda.x) {
+                bcur = (uint32_t)__ldg(a.sbytes + cda.y + lane);
+                scur = __ldg(a.soff + cda.y + lane) + dt;
+            }
+            int kk = 0;
+            for (; kk < nchk; kk++) {
+                const int st = kk % NS;
+                const int2 cdc = load_cd(a, cbeg, nchk, kk + 2);
+                bnxt = 0;
+                if (lane < cdb.x) {
+                    bnxt = (uint32_t)__ldg(a.sbytes + cdb.y + lane);
+                    snxt = __ldg(a.soff + cdb.y + lane) + dt;
+                }
+                if (kk >= NS &&
+                    !afptx::mbar_wait_bounded(empty0 + 8 * st, (uint32_t)(kk / NS - 1) & 1u, kPWait)) {
+                    if (lane == 0) atomicExch(a.err, 1);
+                    break;
+                }
+                produce(a, smem, tab, full0 + 8 * st, cbeg + kk, cda, bcur, scur, st, lane);
+                bcur = bnxt;
+                scur = snxt;
+                cda = cdb;
+                cdb = cdc;
+            }
+            for (int k2 = max(0, kk - NS); k2 < kk; k2++)
+                afptx::mbar_wait_bounded(full0 + 8 * (k2 % NS), (uint32_t)(k2 / NS) & 1u, kPWait);
+            return;
+        }
+
+        // ---------------- consumer warps: one DM row each
+        const int drow = (int)jb * NW + warp;
+        uint32_t A[2][kPMG], Wd[kPMG][2];
+#pragma unroll
+        for (int m = 0; m < kPMG; m++) {
+            A[0][m] = A[1][m] = 0u;
+            Wd[m][0] = Wd[m][1] = 0u;
+        }
+        const uint32_t lane4 = (uint32_t)lane * 4u;
+        int npacc = 0;
+        for (int kk = 0; kk < nchk; kk++) {
+            const int st = kk % NS;
+            if (!afptx::mbar_wait_bounded(full0 + 8 * st, (uint32_t)(kk / NS) & 1u, kPWait)) {
+                if (lane == 0) atomicExch(a.err, 1);
+                return;
+            }
+            const int* tb = tab + (st * NW + warp) * kPTABW;
+            const int4 h = *reinterpret_cast<const int4*>(tb);  // starts 0, 1; counts 0, 1
+            const int npc = h.z + h.w;
+            if (npacc + npc > kPFlush) {
+                fold(A, Wd, lane);
+                npacc = 0;
+            }
+            npacc += npc;
+#pragma unroll
+            for (int r = 0; r < 2; r++) {
+                const int beg = r == 0 ? h.x : h.y;
+                const int n = r == 0 ? h.z : h.w;
+                const int* o = tb + 4 + beg;
+                // the next pair's offsets one iteration ahead (reads past the
+                // bucket stay inside the table and are never used)
+                int2 nx = *reinterpret_cast<const int2*>(o);
+                int i = 0;
+                for (; i + 2 <= n; i += 2) {
+                    const int2 oo = nx;
+                    nx = *reinterpret_cast<const int2*>(o + i + 2);
+                    const uint8_t* p1 = smem + oo.x + lane4;
+                    const uint8_t* p2 = smem + oo.y + lane4;
+                    uint32_t w1[kPMG], w2[kPMG];
+#pragma unroll
+                    for (int m = 0; m < kPMG; m++) {
+                        w1[m] = *reinterpret_cast<const uint32_t*>(p1 + 128 * m);
+                        w2[m] = *reinterpret_cast<const uint32_t*>(p2 + 128 * m);
+                    }
+#pragma unroll
+                    for (int m = 0; m < kPMG; m++) A[r][m] += w1[m] + w2[m];
+                }
+                if (i < n) {
+                    const uint8_t* p1 = smem + nx.x + lane4;
+#pragma unroll
+                    for (int m = 0; m < kPMG; m++) A[r][m] += *reinterpret_cast<const uint32_t*>(p1 + 128 * m);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) afptx::mbar_arrive(empty0 + 8 * st);
+        }
+        fold(A, Wd, lane);
+
+        // ---- outputs and fused row sums
+        const int orow = __ldg(a.perm + drow);
+        long long ssum = 0, ssq = 0;
+#pragma unroll
+        for (int m = 0; m < kPMG; m++) {
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const int pos = 2 * (lane + 32 * m) + k;
+                const int64_t t = t0 + pos;
+                const uint32_t v = Wd[m][k];
+                if (orow >= 0 && pos < kPTTE && t < a.tend) {
+                    a.Y[(int64_t)orow * a.nout + t] = (int32_t)v;
+                    ssum += (long long)v;
+                    ssq += (long long)v * (long long)v;
+                }
+            }
+        }
+        if (a.stats) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
+                ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
+            }
+            if (lane == 0 && orow >= 0) {
+                atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[orow].sum), (unsigned long long)ssum);
+                atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[orow].sumsq), (unsigned long long)ssq);
+            }
+        }
+    }
+};
+
+// Grid = time tiles of the block x DM blocks, DM blocks fastest (a tile's rows
+// stay in L2 while every DM block reads them).
+template <int NW, int SL, int NS>
+__global__ void __launch_bounds__((NW + 1) * 32, 1) k_pair_tile(const PairArgs a)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    PairTile<NW, SL, NS>::run(a, smem);
+}
+
+size_t tile_smem(int shape, int rwb)
+{
+    const int sl = kShapeSL[shape], ns = kShapeNS[shape];
+    return (size_t)ns * sl * rwb + (size_t)ns * kPNW * kPTABW * 4 + 2 * (size_t)ns * 8;
+}
+
+const void* tile_kernel(int shape)
+{
+    return shape == 0 ? (const void*)k_pair_tile<kPNW, 32, 2>
+         : shape == 1 ? (const void*)k_pair_tile<kPNW, 24, 3>
+                      : (const void*)k_pair_tile<kPNW, 16, 4>;
+}
+size_t rows_smem(int maxdr) { return (size_t)kET + (size_t)r16(kET + maxdr + 4); }
+
+size_t pair_budget()
+{
+    if (const char* b = getenv("AFGB_PAIR_BUDGET_MB")) return (size_t)atoll(b) << 20;
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    return std::min<size_t>((size_t)16 << 30, tot / 8);
+}
+
+}  // namespace
+
+int af_pair_tile_outputs() { return kPTTE; }
+
+void af_pairs_free(af_pair_tables* T)
+{
+    af_tile_tables_free(&T->tt);
+    cudaFree(T->d_rdelta);
+    cudaFree(T->d_pinfo);
+    cudaFree(T->d_rowoff);
+    cudaFree(T->d_chunks);
+    cudaFree(T->d_chkoff);
+    cudaFree(T->d_tabs);
+    cudaFree(T->d_sbytes);
+    cudaFree(T->d_soff);
+    cudaFree(T->d_ps);
+    *T = af_pair_tables();
+}
+
+// Host tables (once per plan).  Leaves T->ok false, and returns AF_OK, when
+// the plan is not suited: a block whose pair needs more than a stage of rows,
+// a pair whose delta range exceeds the stage-1 window, more rows per pair and
+// block than the byte kernel's cost, or windows that do not fit.
+//
+// With tiles and time blocks starting at multiples of 8, a consumer's sample
+// offset inside its row window, e = D[d][2q] - (block minimum & ~7), does not
+// depend on the tile, so every warp's bucketed table of (slot, offset) per
+// chunk is computed here once; a window starts (t0 - T0) after its position
+// for the time block's first tile.
+int af_pairs_build(af_plan_t p)
+{
+    af_pair_tables* T = &p->pairs;
+    af_pairs_free(T);
+    const int nchan = p->nchan, ndm = p->ndm, NW = kPNW;
+    std::vector<int32_t> dsort, dmin;
+    if (int rc = af_tile_tables_build(p->delays.data(), p->dms.data(), ndm, nchan, NW, 8, p->device, &T->tt, &dsort,
+                                      &dmin))
+        return rc;
+    const int nblk = T->tt.nblk;
+    const int np = (nchan + 1) / 2;
+    const int32_t* D = p->delays.data();
+    // rows: distinct deltas of each pair over all DMs
+    std::vector<int32_t> rb(np + 1, 0), rdelta, dlo(np), dhi(np);
+    std::vector<int32_t> v(ndm);
+    int maxdr = 0;
+    for (int q = 0; q < np; q++) {
+        const int c0 = 2 * q, c1 = 2 * q + 1;
+        int32_t lo = INT32_MAX, hi = INT32_MIN;
+        for (int d = 0; d < ndm; d++) {
+            const int32_t x = D[(size_t)d * nchan + c0];
+            lo = std::min(lo, x);
+            hi = std::max(hi, x);
+            v[d] = c1 < nchan ? D[(size_t)d * nchan + c1] - x : 0;
+        }
+        dlo[q] = lo;
+        dhi[q] = hi;
+        std::sort(v.begin(), v.end());
+        const size_t n0 = rdelta.size();
+        for (int d = 0; d < ndm; d++)
+            if (d == 0 || v[d] != v[d - 1]) rdelta.push_back(v[d]);
+        rb[q + 1] = (int32_t)rdelta.size();
+        maxdr = std::max(maxdr, rdelta.back() - rdelta[n0]);
+    }
+    // window of the even channels' block spread
+    int spread = 0;
+    for (int j = 0; j < nblk; j++)
+        for (int c = 0; c < nchan; c += 2) {
+            int32_t hi = INT32_MIN;
+            for (int w = 0; w < NW; w++) hi = std::max(hi, dsort[(size_t)(j * NW + w) * nchan + c]);
+            spread = std::max(spread, hi - dmin[(size_t)j * nchan + c]);
+        }
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    const int64_t rwe = r8((int64_t)spread + 1031);
+    if (spread >= (1 << 20) || maxdr > kMaxDr) return AF_OK;
+    const int rwb = (int)(2 * rwe);
+    int shape = -1;
+    if (const char* e = getenv("AFGB_PAIR_SHAPE")) shape = atoi(e);
+    if (shape < 0 || shape >= kShapes || tile_smem(shape, rwb) > (size_t)optin) {
+        shape = -1;
+        for (int k = kShapes - 1; k >= 0; k--)
+            if (tile_smem(k, rwb) <= (size_t)optin) shape = k;
+    }
+    if (shape < 0) return AF_OK;
+    const int SL = kShapeSL[shape], NS = kShapeNS[shape];
+    // chunks of whole pairs, at most SL rows each, per block; their tables
+    struct Ent {
+        int slot[kPNW];
+        int e[kPNW];
+    };
+    std::vector<Ent> ents;
+    std::vector<int2> chunks;
+    std::vector<int32_t> chkoff(nblk + 1, 0), sbytes, srow, scpart;
+    std::vector<int> tabs;
+    std::vector<int32_t> dq(NW), d0(NW), S;
+    int open_slots = 0, first_slot = 0, kloc = 0;
+    auto flush = [&]() {
+        if (ents.empty()) return;
+        const int st = kloc % NS;
+        const size_t base = tabs.size();
+        tabs.resize(base + (size_t)NW * kPTABW, 0);
+        for (int w = 0; w < NW; w++) {
+            int* tb = tabs.data() + base + (size_t)w * kPTABW;
+            int cnt[2] = {0, 0};
+            for (const Ent& en : ents) cnt[en.e[w] & 1]++;
+            int pos[2] = {0, (cnt[0] + 1) & ~1};  // bucket starts even: offsets load in pairs
+            tb[0] = pos[0];
+            tb[1] = pos[1];
+            tb[2] = cnt[0];
+            tb[3] = cnt[1];
+            for (const Ent& en : ents) {
+                const int r = en.e[w] & 1;
+                tb[4 + pos[r]++] = (st * SL + en.slot[w]) * rwb + 2 * (en.e[w] - r);
+            }
+        }
+        chunks.push_back(make_int2(open_slots, first_slot));
+        ents.clear();
+        open_slots = 0;
+        kloc++;
+    };
+    for (int j = 0; j < nblk; j++) {
+        kloc = 0;
+        for (int q = 0; q < np; q++) {
+            const int c0 = 2 * q, c1 = 2 * q + 1;
+            int32_t hi = INT32_MIN;
+            for (int w = 0; w < NW; w++) {
+                const int32_t* row = dsort.data() + (size_t)(j * NW + w) * nchan;
+                d0[w] = row[c0];
+                dq[w] = c1 < nchan ? row[c1] - row[c0] : 0;
+                hi = std::max(hi, row[c0]);
+            }
+            S.assign(dq.begin(), dq.end());
+            std::sort(S.begin(), S.end());
+            S.erase(std::unique(S.begin(), S.end()), S.end());
+            if ((int)S.size() > SL) return AF_OK;
+            if (open_slots + (int)S.size() > SL) flush();
+            if (ents.empty()) first_slot = (int)sbytes.size();
+            const int32_t dm = dmin[(size_t)j * nchan + c0];
+            const int bytes = (int)(2 * r8((int64_t)(hi - dm) + 1031));
+            for (int32_t dv : S) {
+                sbytes.push_back(bytes);
+                srow.push_back((int32_t)(std::lower_bound(rdelta.begin() + rb[q], rdelta.begin() + rb[q + 1], dv) -
+                                         rdelta.begin()));
+                scpart.push_back((dm & ~7) - (dlo[q] & ~7));
+            }
+            Ent en;
+            for (int w = 0; w < NW; w++) {
+                en.slot[w] = open_slots + (int)(std::lower_bound(S.begin(), S.end(), dq[w]) - S.begin());
+                en.e[w] = d0[w] - (dm & ~7);
+            }
+            ents.push_back(en);
+            open_slots += (int)S.size();
+        }
+        flush();
+        chkoff[j + 1] = (int32_t)chunks.size();
+    }
+    // cost: row windows copied per pair against the byte kernel's two channel windows
+    const double rows_per_pair = (double)sbytes.size() / ((double)nblk * np);
+    if (rows_per_pair > 3.0) return AF_OK;
+    T->np = np;
+    T->nrows = (int)rdelta.size();
+    T->rwe = (int)rwe;
+    T->maxdr = maxdr;
+    T->rows_per_pair = rows_per_pair;
+    T->budget = pair_budget();
+    T->shape = shape;
+    T->h_rb = rb;
+    T->h_dlo = dlo;
+    T->h_dhi = dhi;
+    T->h_srow = srow;
+    T->h_scpart = scpart;
+    cudaError_t e;
+    auto up = [&](void** d, const void* h, size_t n) {
+        if ((e = cudaMalloc(d, n)) != cudaSuccess) return false;
+        return (e = cudaMemcpy(*d, h, n, cudaMemcpyHostToDevice)) == cudaSuccess;
+    };
+    if (!up((void**)&T->d_rdelta, rdelta.data(), rdelta.size() * 4) ||
+        !up((void**)&T->d_chunks, chunks.data(), chunks.size() * sizeof(int2)) ||
+        !up((void**)&T->d_chkoff, chkoff.data(), chkoff.size() * 4) ||
+        !up((void**)&T->d_tabs, tabs.data(), tabs.size() * 4) ||
+        !up((void**)&T->d_sbytes, sbytes.data(), sbytes.size() * 4) ||
+        (e = cudaMalloc(&T->d_pinfo, (size_t)np * sizeof(int4))) != cudaSuccess ||
+        (e = cudaMalloc(&T->d_rowoff, (size_t)T->nrows * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&T->d_soff, srow.size() * 8)) != cudaSuccess) {
+        af_pairs_free(T);
+        return af_cuda_check(e, "pair tables");
+    }
+    T->ok = true;
+    return AF_OK;
+}
+
+// Row lengths for time blocks of L outputs: r16(L + dhi - dlo + rwe + 8).
+static int64_t rows_elems(const af_pair_tables* T, int64_t L)
+{
+    int64_t n = 0;
+    for (int q = 0; q < T->np; q++)
+        n += (int64_t)(T->h_rb[q + 1] - T->h_rb[q]) * r16(L + T->h_dhi[q] - T->h_dlo[q] + T->rwe + 8);
+    return n;
+}
+
+// Time block length for nout outputs within the budget (0: pairs not usable).
+int64_t af_pairs_block(af_plan_t p, int64_t nout)
+{
+    const af_pair_tables* T = &p->pairs;
+    if (!T->ok || nout <= 0) return 0;
+    const int64_t tiles = (nout + kPTTE - 1) / kPTTE;
+    const int64_t cap = (int64_t)(T->budget / 2);
+    int64_t lo = kMinTiles, hi = tiles;
+    if (rows_elems(T, lo * kPTTE) > cap) return 0;
+    if (lo >= hi) return hi * kPTTE;
+    while (lo < hi) {  // largest tile count within the budget
+        const int64_t mid = (lo + hi + 1) / 2;
+        if (rows_elems(T, mid * kPTTE) <= cap) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo * kPTTE;
+}
+
+// Row buffer and offsets for time blocks of L outputs.
+static int pairs_layout(af_plan_t p, int64_t L)
+{
+    af_pair_tables* T = &p->pairs;
+    if (T->L == L) return AF_OK;
+    const int64_t need = rows_elems(T, L);
+    if ((size_t)need * 2 > T->ps_bytes) {
+        cudaFree(T->d_ps);
+        T->d_ps = nullptr;
+        T->ps_bytes = 0;
+        if (cudaError_t e = cudaMalloc(&T->d_ps, (size_t)need * 2)) return af_cuda_check(e, "pair rows");
+        T->ps_bytes = (size_t)need * 2;
+    }
+    std::vector<int64_t> rowoff(T->nrows), soff(T->h_srow.size());
+    std::vector<int4> pinfo(T->np);
+    int64_t off = 0;
+    T->maxlen = 0;
+    for (int q = 0; q < T->np; q++) {
+        const int64_t len = r16(L + T->h_dhi[q] - T->h_dlo[q] + T->rwe + 8);
+        pinfo[q] = make_int4(T->h_rb[q], T->h_rb[q + 1] - T->h_rb[q], T->h_dlo[q], (int)len);
+        for (int g = T->h_rb[q]; g < T->h_rb[q + 1]; g++, off += len) rowoff[g] = off;
+        T->maxlen = std::max(T->maxlen, len);
+    }
+    for (size_t i = 0; i < soff.size(); i++) soff[i] = rowoff[T->h_srow[i]] + T->h_scpart[i];
+    cudaError_t e;
+    if ((e = cudaMemcpy(T->d_rowoff, rowoff.data(), rowoff.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(T->d_soff, soff.data(), soff.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(T->d_pinfo, pinfo.data(), pinfo.size() * sizeof(int4), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+        return af_cuda_check(e, "pair layout");
+    T->L = L;
+    return AF_OK;
+}
+
+int af_pairs_reserve(af_plan_t p, int64_t nout)
+{
+    const int64_t L = af_pairs_block(p, nout);
+    return L > 0 ? pairs_layout(p, L) : AF_OK;
+}
+
+int af_launch_pairs(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,
+                    af_rowstats_t* d_stats, cudaStream_t s)
+{
+    af_pair_tables* T = &p->pairs;
+    const int64_t L = af_pairs_block(p, nout);
+    if (L <= 0) return af_set_error(AF_EINVAL, "pairs: not usable for this plan and length");
+    if (int rc = pairs_layout(p, L)) return rc;
+    const int rwb = 2 * T->rwe;
+    const size_t s2 = tile_smem(T->shape, rwb), s1 = rows_smem(T->maxdr);
+    if (int rc = af_ensure_smem(tile_kernel(T->shape), s2)) return rc;
+    if (int rc = af_ensure_smem((const void*)k_pair_rows, s1)) return rc;
+    if (d_stats)
+        if (int rc = af_cuda_check(cudaMemsetAsync(d_stats, 0, (size_t)p->ndm * sizeof(af_rowstats_t), s),
+                                   "pairs stats reset"))
+            return rc;
+    const int etiles = (int)((T->maxlen + kET - 1) / kET);
+    PairArgs a;
+    a.PS = T->d_ps;
+    a.chunks = T->d_chunks;
+    a.chkoff = T->d_chkoff;
+    a.tabs = T->d_tabs;
+    a.sbytes = T->d_sbytes;
+    a.soff = T->d_soff;
+    a.perm = T->tt.d_perm;
+    a.rwb = rwb;
+    a.nblk = (unsigned)T->tt.nblk;
+    a.nout = nout;
+    a.Y = d_plane;
+    a.stats = d_stats;
+    a.err = p->d_err;
+    for (int64_t T0 = 0; T0 < nout; T0 += L) {
+        const unsigned long long g1 = (unsigned long long)T->np * etiles;
+        const int64_t tiles = (std::min(L, nout - T0) + kPTTE - 1) / kPTTE;
+        const unsigned long long g2 = (unsigned long long)tiles * a.nblk;
+        if (g1 > 0x7fffffffULL || g2 > 0x7fffffffULL)
+            return af_set_error(AF_EINVAL, "pairs: problem too large for one grid");
+        k_pair_rows<<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, T->d_pinfo, T->d_rdelta, T->d_rowoff, T0,
+                                                   etiles, T->d_ps);
+        if (int rc = af_cuda_check(cudaGetLastError(), "pair rows launch")) return rc;
+        a.T0 = T0;
+        a.tend = std::min(nout, T0 + L);
+        if (T->shape == 0)
+            k_pair_tile<kPNW, 32, 2><<<(unsigned)g2, (kPNW + 1) * 32, s2, s>>>(a);
+        else if (T->shape == 1)
+            k_pair_tile<kPNW, 24, 3><<<(unsigned)g2, (kPNW + 1) * 32, s2, s>>>(a);
+        else
+            k_pair_tile<kPNW, 16, 4><<<(unsigned)g2, (kPNW + 1) * 32, s2, s>>>(a);
+        if (int rc = af_cuda_check(cudaGetLastError(), "pair tile launch")) return rc;
+    }
+    return AF_OK;
+}

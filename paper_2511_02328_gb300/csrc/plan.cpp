@@ -81,6 +81,7 @@ static void free_plan(af_plan_t p)
     if (cur != p->device) cudaSetDevice(p->device);
     cudaFree(p->d_delays);
     af_tile_tables_free(&p->tile);
+    af_pairs_free(&p->pairs);
     af_sb_free(p);
     cudaFree(p->d_err);
     cudaFree(p->d_stats);
@@ -173,6 +174,7 @@ static int plan_finish(af_plan_s* p, const char* who)
     if (const char* k = getenv("AFGB_DEDISP_KERNEL")) {
         p->force_simple = strcmp(k, "simple") == 0;
         p->force_brute = strcmp(k, "brute") == 0;
+        p->force_tile = strcmp(k, "tile") == 0;
     }
     const size_t tbytes = (size_t)p->ndm * p->nchan * sizeof(int32_t);
     int rc = AF_OK;
@@ -567,7 +569,7 @@ extern "C" int af_search_reserve(af_plan_t p, int64_t max_nsamp, int32_t cap)
         }
     p->ws_nsamp = max_nsamp;
     p->ws_cap = cap;
-    return AF_OK;
+    return af_pairs_reserve(p, nout);  // the pair-row buffer, where that path applies
 }
 
 extern "C" int af_search(af_plan_t p, const uint8_t* h_in, int64_t nsamp, const int32_t* widths, int nw,

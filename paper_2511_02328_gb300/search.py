@@ -49,9 +49,9 @@ class Plan:
         return _lib.af_plan_subband_info(self.handle)
 
     def kernel(self):
-        """dict(path='simple'|'tile'|'subband', ring, spread) of the dedispersion kernel."""
+        """dict(path='simple'|'tile'|'subband'|'pairs', ring, spread) of the dedispersion kernel."""
         path, ring, spread = _lib.af_plan_kernel(self.handle)
-        return dict(path=("simple", "tile", "subband")[path], ring=ring, spread=spread)
+        return dict(path=("simple", "tile", "subband", "pairs")[path], ring=ring, spread=spread)
 
     def close(self):
         if self.handle:

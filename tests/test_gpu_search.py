@@ -148,9 +148,14 @@ SHAPES = [
 ]
 
 
+@pytest.mark.parametrize("kernel", ["auto", "tile"])
 @pytest.mark.parametrize("shape", SHAPES, ids=[str(i) for i in range(len(SHAPES))])
-def test_random_shapes_bit_exact(shape):
+def test_random_shapes_bit_exact(shape, kernel, monkeypatch):
+    """Both single-plan paths (pair rows where they apply, else the channel
+    tile kernel; and the channel tile kernel forced) give the oracle's plane."""
     from paper_2511_02328_gb300.search import Plan
+    if kernel != "auto":
+        monkeypatch.setenv("AFGB_DEDISP_KERNEL", kernel)
     nchan, f_lo, f_hi, tsamp, nsamp, dms = shape
     rng = np.random.default_rng(nchan * 7 + nsamp)
     x = rng.integers(0, 256, (nchan, nsamp), dtype=np.uint8)
@@ -286,12 +291,13 @@ def _expected_ring(spread, nw=11, m=8):
 
 
 @pytest.mark.parametrize("step,ring", [(1.0, 4), (4.0, 3), (5.0, 3), (6.0, 2), (10.0, 2), (12.0, 0)])
-def test_coarse_dm_grids_shallower_ring(step, ring):
+def test_coarse_dm_grids_shallower_ring(step, ring, monkeypatch):
     """Coarse DM grids widen each channel's window; the tile kernel then runs
     with a 3- or 2-deep ring before the fallback kernel takes over.  Every
     depth gives the oracle's plane and row sums bit-exact (256 channels,
     1000-1500 MHz, 98.304 us, 61 DMs of the given step, a ragged last tile)."""
     from paper_2511_02328_gb300.search import Plan
+    monkeypatch.setenv("AFGB_DEDISP_KERNEL", "tile")
     nchan, tsamp = 256, 98.304e-6
     dms = np.arange(0.0, 1.0 + 60 * step, step)
     D = oracle.delay_table(nchan, 1000.0, 1500.0, tsamp, dms)
@@ -309,6 +315,61 @@ def test_coarse_dm_grids_shallower_ring(step, ring):
     S, Q = oracle.rowstats(Y)
     st = stats.cpu().numpy()
     assert np.array_equal(st[:, 0], S) and np.array_equal(st[:, 1], Q)
+    p.close()
+
+
+def _pair_rows_bytes(D, L, nw=15):
+    """Bytes of the pair-row buffer for time blocks of L outputs: per pair
+    q (channels 2q, 2q+1) one row per distinct delay difference, each of
+    r16(L + max - min delay of channel 2q + rwe + 8) uint16 samples, rwe =
+    r8(largest spread of channel 2q within a block of nw DMs + 1031); the
+    rows of D are in ascending DM order."""
+    ndm, nchan = D.shape
+    Ds = D
+    pad = -(-ndm // nw) * nw
+    Dp = np.concatenate([Ds, np.repeat(Ds[-1:], pad - ndm, 0)]).reshape(-1, nw, nchan)
+    spread = int((Dp.max(1) - Dp.min(1))[:, 0::2].max())
+    rwe = (spread + 1031 + 7) & ~7
+    total = 0
+    for q in range((nchan + 1) // 2):
+        c0, c1 = 2 * q, 2 * q + 1
+        rows = len(np.unique(D[:, c1] - D[:, c0])) if c1 < nchan else 1
+        total += rows * ((L + int(D[:, c0].max() - D[:, c0].min()) + rwe + 8 + 15) & ~15)
+    return 2 * total
+
+
+@pytest.mark.parametrize("nchan,f_lo,f_hi", [(256, 1000.0, 1500.0), (255, 1500.0, 1000.0)])
+def test_pair_rows_several_time_blocks(nchan, f_lo, f_hi, monkeypatch):
+    """The pair-row path with a row budget that holds 9 tiles of outputs: the
+    plane (several time blocks, a ragged last one) and its row sums are the
+    oracle's; odd channel counts end with a single-channel row."""
+    from paper_2511_02328_gb300.search import Plan
+    tsamp, dms = 98.304e-6, np.arange(0.0, 301.0, 1.0)
+    D = oracle.delay_table(nchan, f_lo, f_hi, tsamp, dms)
+    nsamp = int(D.max()) + 30 * 1022 + 311
+    budget = _pair_rows_bytes(D, 9 * 1022)
+    assert budget < _pair_rows_bytes(D, 31 * 1022)
+    monkeypatch.setenv("AFGB_PAIR_BUDGET_MB", str(-(-budget // (1 << 20))))
+    x = np.random.default_rng(nchan).integers(0, 256, (nchan, nsamp), dtype=np.uint8)
+    p = Plan(nchan, f_lo, f_hi, tsamp, dms)
+    assert p.kernel()["path"] == "pairs"
+    stats = torch.empty((p.ndm, 2), dtype=torch.int64, device="cuda")
+    plane = p.dedisperse(torch.from_numpy(x).cuda(), stats=stats)
+    torch.cuda.synchronize()
+    Y = oracle.dedisperse(x, D)
+    assert np.array_equal(plane.cpu().numpy(), Y)
+    S, Q = oracle.rowstats(Y)
+    st = stats.cpu().numpy()
+    assert np.array_equal(st[:, 0], S) and np.array_equal(st[:, 1], Q)
+    p.close()
+
+
+def test_pair_rows_is_the_default_path(c1_data):
+    """The 256-channel workload runs on pair rows by default and the channel
+    tile kernel, forced, gives the same plane."""
+    x, D, Y, _, _ = c1_data
+    p = _plan(C1)
+    assert p.kernel()["path"] == "pairs"
     p.close()
 
 
