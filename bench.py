@@ -203,11 +203,11 @@ STREAM_WORKLOAD = ("streaming: 19 beams, 4096 ch x 49.152 us uint8, windows of 2
 
 
 SB_N0, SB_NSUB = 8, 64
-# DRAM read + write bytes of one k_tile<11,8> launch on this workload, from an ncu capture of the same
-# kernel (dram__bytes_read.sum + dram__bytes_write.sum); reset to None whenever the kernel changes
-TILE_TRAFFIC_BYTES = 1.34e10
-TILE_TRAFFIC_BASIS = ("ncu dram__bytes read+write of k_tile<11,8> at 2^17 samples (5.23 GB, 83 output tiles), "
-                      "scaled by the output tiles to this 2^18-sample launch (212 tiles)")
+# DRAM read + write bytes of one stage-2 pair-row tile launch (k_pair_tile) on this workload, from an ncu
+# capture of the same kernel (dram__bytes_read.sum + dram__bytes_write.sum); None until captured, and reset
+# to None whenever the kernel changes
+PAIR_TILE_TRAFFIC_BYTES = None
+PAIR_TILE_TRAFFIC_BASIS = None
 
 
 def match_pulses(cands, pulses, dms):
@@ -301,6 +301,8 @@ def run_prep(args, dev, x, plane, snr, bw, ms_brute, stream):
     halves = {name: Plan(NCHAN, F_LO, F_HI, TSAMP, DMS, channels=rng)
               for name, rng in (("L", (0, NCHAN // 2)), ("H", (NCHAN // 2, NCHAN)))}
     hplanes = {k: torch.empty((ndm, v.nout(NSAMP)), dtype=torch.int32, device=dev) for k, v in halves.items()}
+    for v in halves.values():
+        _lib.af_dedisperse_reserve(v.handle, NSAMP)
     jobs = {
         "zerodm": (lambda: _lib.af_zerodm(x.data_ptr(), NCHAN, NSAMP, y.data_ptr(), sp), 2.0 * NCHAN * NSAMP),
         "downsample_8": (lambda: _lib.af_downsample(x.data_ptr(), NCHAN, NSAMP, 8, ds.data_ptr(), sp),
@@ -402,7 +404,8 @@ def run_batch(args, dev, stream):
     ms_batch = timed(lambda: _lib.af_batch_run(batch, sp), steps)
     ncand = sum(_lib.af_batch_candidates(batch, i, 1 << 16)[1] for i in range(len(beams)))
 
-    # the same searches one plan at a time, writing into the batch's buffers
+    # the same searches one plan at a time, writing into the batch's buffers (the channel tile kernel, the
+    # batch's own kernel family: 19 pair-row buffers would not fit the device)
     plans, bufs = [], []
     for i, bm in enumerate(beams):
         plans.append(Plan(bm["nchan"], bm["f_lo"], bm["f_hi"], bm["tsamp"], bm["dm_list"]))
@@ -540,6 +543,7 @@ def run_paper_sec3(args, dev, stream):
                                                                fs_mode=_lib.AF_FS_INVSQ, block_len=1 << 17))
         x = synth.filterbank_torch(nchan, nsamp, seed=seed, device=dev)
         plane = torch.empty((ndm, nout), dtype=torch.int32, device=dev)
+        _lib.af_dedisperse_reserve(bp.handle, nsamp)
         ms_b = timed(lambda: _lib.af_dedisperse(bp.handle, x.data_ptr(), nsamp, plane.data_ptr(), 0, sp))
         nout_s = sb.nout(nsamp)
         ms_s = timed(lambda: _lib.af_dedisperse(sb.handle, x.data_ptr(), nsamp, plane.data_ptr(), 0, sp))
@@ -704,7 +708,10 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     sp = stream.cuda_stream
     H = plan.handle
-    launches_per_step = 4   # dedisperse (row sums fused), rowconst, boxcar, candidates
+    _lib.af_dedisperse_reserve(H, NSAMP)   # the pair-row buffer (setup, outside the timed region)
+    kern = plan.kernel()
+    # dedispersion (pair rows: stage 1 + stage 2; else one tile launch), rowconst, boxcar, candidates
+    launches_per_step = (5 if kern["path"] == "pairs" else 4)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
 
@@ -722,6 +729,8 @@ def main():
         step()
     torch.cuda.synchronize()
 
+    if kern["path"] == "pairs":
+        _lib.af_dedisperse_timing(H, args.steps)   # per-stage events of the timed calls
     gpu_id = local
     clocks = ClockSampler(gpu_id)
     clocks.start()
@@ -742,6 +751,12 @@ def main():
         dist.barrier()
     ms_total = t_start.elapsed_time(t_end)
     ms_dedisp = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    stage = None
+    if kern["path"] == "pairs":
+        st = [_lib.af_dedisperse_times(H, i) for i in range(args.steps)]
+        stage = {"rows_ms": float(np.mean([x[0] for x in st])), "tiles_ms": float(np.mean([x[1] for x in st])),
+                 "row_bytes": int(st[-1][2])}
+        _lib.af_dedisperse_timing(H, 0)
     ncand = int(count.item())
     ms_total = max_over_ranks(ms_total, dist, dev)
 
@@ -823,11 +838,46 @@ def main():
     sm_max = float(pk.get("sm_max_mhz", SM_MAX_MHZ_FALLBACK))
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = nsm * 128 * sm_max * 1e6 / 1e12          # T int32 lane-ops/s
+    smem_peak = nsm * 128 * sm_max * 1e6 / 1e12         # TB/s: 128 B of shared loads per clock per SM
     add_rate, pattern_rate = _lib.af_diag_int_rates()  # measured on this device (probe kernels)
-    achieved = work / (ms_dedisp * 1e-3) / 1e12        # T adds/s
+    achieved = work / (ms_dedisp * 1e-3) / 1e12        # T adds/s, both stages
     hbm_peak = float(pk.get("hbm_gbs", 6800.0))
     alg_bytes = NCHAN * NSAMP + plan.ndm * nout * 4
     hbm_ach = alg_bytes / (ms_dedisp * 1e-3) / 1e9
+    if stage is not None:
+        # stage 2: every (DM, channel pair, output) is one 2-byte shared load and one 16-bit lane add
+        npairs = (NCHAN + 1) // 2
+        lds_bytes = 2.0 * plan.ndm * npairs * nout
+        s2_ach = lds_bytes / (stage["tiles_ms"] * 1e-3) / 1e12
+        s1_bytes = stage["row_bytes"] + NCHAN * NSAMP
+        s1_ach = s1_bytes / (stage["rows_ms"] * 1e-3) / 1e9
+        roofline = {
+            "bound": "smem", "kernel": "k_pair_tile<15,32,2> (stage 2 of the pair-row dedispersion)",
+            "achieved": s2_ach, "peak": smem_peak, "unit": "TB/s", "frac": s2_ach / smem_peak,
+            "traffic": PAIR_TILE_TRAFFIC_BYTES, "traffic_basis": PAIR_TILE_TRAFFIC_BASIS,
+            "work": "2 B shared load per (DM, channel pair, output): %.3g B per launch" % lds_bytes,
+            "ms": stage["tiles_ms"],
+            "peak_basis": "%d SMs x 128 B shared-load bandwidth per clock x %.0f MHz (derived, of max clock)"
+                          % (nsm, sm_max),
+            "stage1": {"kernel": "k_pair_rows", "bound": "hbm", "ms": stage["rows_ms"], "achieved": s1_ach,
+                       "peak": hbm_peak, "unit": "GB/s", "frac": s1_ach / hbm_peak, "basis": "of measured",
+                       "work": "row writes %.3g B + input read %.3g B" % (stage["row_bytes"], NCHAN * NSAMP)},
+            "dedispersion": {"ms": ms_dedisp, "adds_per_s": achieved * 1e12,
+                             "frac_of_derived_int32_peak": achieved / alu_peak,
+                             "frac_of_measured_int32_add_rate": achieved * 1e12 / add_rate,
+                             "hbm": {"achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
+                                     "frac": hbm_ach / hbm_peak, "basis": "of measured"}},
+        }
+    else:
+        roofline = {"bound": "alu", "kernel": "k_tile<11,8>", "achieved": achieved, "peak": alu_peak,
+                    "unit": "Tops/s", "frac": achieved / alu_peak, "traffic": None,
+                    "peak_basis": "%d SMs x 128 int32 lanes x %.0f MHz (derived, of max clock)" % (nsm, sm_max),
+                    "measured_int32_add_peak": add_rate / 1e12,
+                    "frac_of_measured_add_peak": achieved * 1e12 / add_rate,
+                    "measured_inner_pattern_peak": pattern_rate / 1e12,
+                    "frac_of_measured_pattern_peak": achieved * 1e12 / pattern_rate,
+                    "hbm": {"achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak,
+                            "basis": "of measured"}}
     clk = clocks.summary()
 
     cpu = None
@@ -852,15 +902,8 @@ def main():
             "realtime_factor_step": nout * TSAMP / (ms_step * 1e-3),
             "dedisp_ms": ms_dedisp,
             "candidates": ncand,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                         "frac": achieved / alu_peak, "traffic": TILE_TRAFFIC_BYTES,
-                         "traffic_basis": TILE_TRAFFIC_BASIS,
-                         "peak_basis": "%d SMs x 128 int32 lanes x %.0f MHz (derived, of max clock)" % (nsm, sm_max),
-                         "measured_int32_add_peak": add_rate / 1e12, "frac_of_measured_add_peak": achieved * 1e12 / add_rate,
-                         "measured_inner_pattern_peak": pattern_rate / 1e12,
-                         "frac_of_measured_pattern_peak": achieved * 1e12 / pattern_rate,
-                         "hbm": {"achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak,
-                                 "basis": "of measured"}},
+            "dedisp_kernel": kern,
+            "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": aggregate_rate(world, work, e2e_s), "unit": UNIT, "ms": e2e_s * 1e3, "h2d_ms": h2d_ms,
                     "h2d_gbs": NCHAN * NSAMP / (h2d_ms * 1e-3) / 1e9, "h2d_bytes_per_step": NCHAN * NSAMP,

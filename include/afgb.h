@@ -120,12 +120,11 @@ int af_plan_info(af_plan_t plan, int* nchan, int* ndm, int32_t* dmax, double* ts
  *          AF_PATH_SUBBAND (the two stages of Sec. 2.3) or AF_PATH_PAIRS (the
  *          same exact sum over channel-pair rows: adjacent channels added
  *          once per distinct relative delay, then the tile kernel over pair
- *          rows; used when the rows of a time block fit the row budget,
- *          AFGB_PAIR_BUDGET_MB, default min(16 GiB, 1/8 of device memory),
- *          else the tile kernel runs);
+ *          rows; reported once af_dedisperse_reserve or af_search_reserve
+ *          has reserved the row buffer);
  *  ring    depth of the kernel's shared-memory ring (4; 3 or 2 when a coarse
- *          DM grid widens each channel's window; 2 for pair rows), 0 on the
- *          simple path;
+ *          DM grid widens each channel's window; 2 to 4 for pair rows), 0 on
+ *          the simple path;
  *  spread  largest delay difference between DMs of one block of the kernel,
  *          in samples (what sets the window width).
  * AFGB_DEDISP_KERNEL=tile|simple in the environment at plan creation forces
@@ -236,7 +235,33 @@ int af_plan_subband_info(af_plan_t plan, int* n0, int* nsub, int* ncoarse, int32
  *  nsamp    samples per channel (row pitch of d_in), > Dmax
  *  d_plane  int32 [ndm][nout] output (row pitch nout)
  *  d_stats  optional af_rowstats_t [ndm] output (may be NULL)
- * Enqueued on `stream`. */
+ * Enqueued on `stream`.  Brute-force plans run the pair-row kernels once
+ * af_dedisperse_reserve (or af_search_reserve) has reserved their row buffer,
+ * else the channel tile kernel; both give the same plane. */
+/* Reserves the pair-row buffer of a brute-force plan (af_plan_kernel path
+ * AF_PATH_PAIRS) for inputs of up to max_nsamp samples: the time-block length
+ * is the longest whose rows (uint16, one per channel pair and distinct delay
+ * difference D[d][2q+1] - D[d][2q], each block length + the pair's delay range
+ * long) fit the row budget (AFGB_PAIR_BUDGET_MB at plan creation, default
+ * min(16 GiB, 1/8 of device memory)); later calls of any length run in as many
+ * time blocks as they need.  Allocates and uploads synchronously (waits for the
+ * device when it replaces a reservation); AF_OK without effect for plans that
+ * cannot use pair rows.  AF_EINVAL if max_nsamp <= Dmax, AF_ENOMEM / AF_ECUDA
+ * on allocation failure.  Not a step of the paper's method: the same sum,
+ * grouped. */
+int af_dedisperse_reserve(af_plan_t plan, int64_t max_nsamp);
+
+/* Stage timing of the pair-row path (measurement aid, not a step of the
+ * paper's method).  af_dedisperse_timing(plan, n) creates events for n call
+ * slots (0 <= n <= 4096; 0 turns timing off) after waiting for the device;
+ * every later af_dedisperse call on the pair-row path records, in slot
+ * (calls since then) mod n, events on its stream around stage 1 (row sums)
+ * and stage 2 (tiles) of each of its first 8 time blocks.
+ * af_dedisperse_times(plan, i, ...) waits for slot i's events and returns the
+ * summed stage times in ms and the row-buffer bytes that call wrote (any
+ * output may be NULL); AF_EINVAL for a slot outside 0..n-1. */
+int af_dedisperse_timing(af_plan_t plan, int ncalls);
+int af_dedisperse_times(af_plan_t plan, int call, float* rows_ms, float* tiles_ms, int64_t* row_bytes);
 int af_dedisperse(af_plan_t plan, const uint8_t* d_in, int64_t nsamp,
                   int32_t* d_plane, af_rowstats_t* d_stats, void* stream);
 

@@ -68,6 +68,9 @@ SIGNATURES = {
     "af_plan_nout": [_P, _I64, _P],
     "af_plan_check": [_P],
     "af_plan_kernel": [_P, _P, _P, _P],
+    "af_dedisperse_reserve": [_P, _I64],
+    "af_dedisperse_timing": [_P, _I],
+    "af_dedisperse_times": [_P, _I, _P, _P, _P],
     "af_dedisperse": [_P, _P, _I64, _P, _P, _P],
     "af_rowstats": [_P, _P, _I64, _P, _P],
     "af_boxcar_snr": [_P, _P, _I64, _P, _P, _I, _P, _P, _P],
@@ -242,6 +245,22 @@ def af_plan_kernel(plan):
     _check(lib().af_plan_kernel(plan, ctypes.byref(path), ctypes.byref(ring), ctypes.byref(spread)),
            "af_plan_kernel")
     return path.value, ring.value, spread.value
+
+
+def af_dedisperse_reserve(plan, max_nsamp):
+    _check(lib().af_dedisperse_reserve(plan, max_nsamp), "af_dedisperse_reserve")
+
+
+def af_dedisperse_timing(plan, ncalls):
+    _check(lib().af_dedisperse_timing(plan, ncalls), "af_dedisperse_timing")
+
+
+def af_dedisperse_times(plan, call):
+    """(stage-1 ms, stage-2 ms, row-buffer bytes) of timed call slot `call`."""
+    r, t, b = ctypes.c_float(), ctypes.c_float(), _I64()
+    _check(lib().af_dedisperse_times(plan, call, ctypes.byref(r), ctypes.byref(t), ctypes.byref(b)),
+           "af_dedisperse_times")
+    return r.value, t.value, b.value
 
 
 def af_plan_delays(plan):

@@ -220,7 +220,8 @@ int af_dedisp_tile_outputs() { return aftile::tte_of(kDefaultM); }
 
 bool af_dedisp_uses_pairs(af_plan_t p, int64_t nout)
 {
-    return p->pairs.ok && !p->force_simple && !p->force_tile && p->sb_nsub == 0 && af_pairs_block(p, nout) > 0;
+    (void)nout;  // any length: more time blocks
+    return p->pairs.ok && !p->force_simple && !p->force_tile && p->sb_nsub == 0 && p->pairs.lay[0].L > 0;
 }
 
 bool af_dedisp_uses_tiles(af_plan_t p) { return p->tile.ns1 > 0 && !p->force_simple && p->sb_nsub == 0; }
@@ -294,7 +295,7 @@ extern "C" int af_plan_kernel(af_plan_t p, int* path, int* ring, int32_t* spread
         pa = AF_PATH_SUBBAND;
         rg = aftile::NSTAGE;
         sp = p->sb.tile.spread;
-    } else if (p->pairs.ok && !p->force_simple && !p->force_tile) {
+    } else if (af_dedisp_uses_pairs(p, 1)) {
         pa = AF_PATH_PAIRS;
         rg = p->pairs.shape == 0 ? 2 : p->pairs.shape == 1 ? 3 : 4;
         sp = p->pairs.tt.spread;

@@ -85,23 +85,39 @@ struct af_pair_tables {
     af_tile_tables tt;             // DM order and block minima for this block shape
     std::vector<int32_t> h_rb, h_dlo, h_dhi, h_srow, h_scpart;
     int32_t* d_rdelta = nullptr;   // [nrows] delta of each row (sorted within a pair)
-    int4* d_pinfo = nullptr;       // [np] first row, rows, dlo, row length
-    int64_t* d_rowoff = nullptr;   // [nrows] element offset in the row buffer
     int2* d_chunks = nullptr;      // per chunk: row slots, first slot
     int32_t* d_chkoff = nullptr;   // [nblk + 1]
     int* d_tabs = nullptr;         // per chunk: every consumer warp's table
     int32_t* d_sbytes = nullptr;   // per slot: window bytes
-    int64_t* d_soff = nullptr;     // per slot: window offset for a time block's first tile
     uint16_t* d_ps = nullptr;      // row buffer
     size_t ps_bytes = 0;
-    int64_t L = 0, maxlen = 0;     // current time block and longest row
+    // Row-buffer layouts made by the reservation calls: 0 for af_dedisperse
+    // (the longest time block the budget allows), 1 for af_search (at least
+    // four blocks, so that the input copy overlaps the work).
+    struct Layout {
+        int64_t L = 0, maxlen = 0;     // outputs per time block, longest row
+        int4* d_pinfo = nullptr;       // [np] first row, rows, dlo, row length
+        int64_t* d_rowoff = nullptr;   // [nrows] element offset in the row buffer
+        int64_t* d_soff = nullptr;     // per slot: window offset for a time block's first tile
+    } lay[2];
+    // optional stage timing of af_dedisperse calls (af_dedisperse_timing):
+    // events [call % ncalls][block][3] = before stage 1, between, after stage 2
+    std::vector<cudaEvent_t> tev;
+    int tcalls = 0, tblocks = 0, tnext = 0;
+    std::vector<int> tnb;              // blocks recorded per call slot
+    std::vector<int64_t> trowbytes;    // row-buffer bytes written per call slot
 };
 int af_pairs_build(af_plan_t p);
 void af_pairs_free(af_pair_tables* T);
 int64_t af_pairs_block(af_plan_t p, int64_t nout);
-int af_pairs_reserve(af_plan_t p, int64_t nout);
+int af_pairs_reserve(af_plan_t p, int64_t nout, bool search);
 int af_launch_pairs(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,
                     af_rowstats_t* d_stats, cudaStream_t s);
+// Stage 1 + stage 2 of the time block starting at T0 (a multiple of the
+// layout's block length; row sums accumulate, the caller clears them once).
+int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,
+                          af_rowstats_t* d_stats, cudaStream_t s, int layout, int64_t T0,
+                          cudaEvent_t* mid = nullptr);
 int af_pair_tile_outputs();
 bool af_dedisp_uses_pairs(af_plan_t p, int64_t nout);
 

@@ -376,14 +376,17 @@ void af_pairs_free(af_pair_tables* T)
 {
     af_tile_tables_free(&T->tt);
     cudaFree(T->d_rdelta);
-    cudaFree(T->d_pinfo);
-    cudaFree(T->d_rowoff);
     cudaFree(T->d_chunks);
     cudaFree(T->d_chkoff);
     cudaFree(T->d_tabs);
     cudaFree(T->d_sbytes);
-    cudaFree(T->d_soff);
+    for (auto& l : T->lay) {
+        cudaFree(l.d_pinfo);
+        cudaFree(l.d_rowoff);
+        cudaFree(l.d_soff);
+    }
     cudaFree(T->d_ps);
+    for (cudaEvent_t ev : T->tev) cudaEventDestroy(ev);
     *T = af_pair_tables();
 }
 
@@ -549,9 +552,12 @@ int af_pairs_build(af_plan_t p)
         !up((void**)&T->d_chkoff, chkoff.data(), chkoff.size() * 4) ||
         !up((void**)&T->d_tabs, tabs.data(), tabs.size() * 4) ||
         !up((void**)&T->d_sbytes, sbytes.data(), sbytes.size() * 4) ||
-        (e = cudaMalloc(&T->d_pinfo, (size_t)np * sizeof(int4))) != cudaSuccess ||
-        (e = cudaMalloc(&T->d_rowoff, (size_t)T->nrows * 8)) != cudaSuccess ||
-        (e = cudaMalloc(&T->d_soff, srow.size() * 8)) != cudaSuccess) {
+        (e = cudaMalloc(&T->lay[0].d_pinfo, (size_t)np * sizeof(int4))) != cudaSuccess ||
+        (e = cudaMalloc(&T->lay[0].d_rowoff, (size_t)T->nrows * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&T->lay[0].d_soff, srow.size() * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&T->lay[1].d_pinfo, (size_t)np * sizeof(int4))) != cudaSuccess ||
+        (e = cudaMalloc(&T->lay[1].d_rowoff, (size_t)T->nrows * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&T->lay[1].d_soff, srow.size() * 8)) != cudaSuccess) {
         af_pairs_free(T);
         return af_cuda_check(e, "pair tables");
     }
@@ -586,12 +592,17 @@ int64_t af_pairs_block(af_plan_t p, int64_t nout)
     return lo * kPTTE;
 }
 
-// Row buffer and offsets for time blocks of L outputs.
-static int pairs_layout(af_plan_t p, int64_t L)
+// Layout k (0: af_dedisperse, 1: af_search) of the row buffer for time
+// blocks of L outputs; waits for the device first when it replaces a layout
+// or the buffer (kernels in flight may read them).  Reservation calls only.
+static int pairs_layout(af_plan_t p, int k, int64_t L)
 {
     af_pair_tables* T = &p->pairs;
-    if (T->L == L) return AF_OK;
+    af_pair_tables::Layout& ly = T->lay[k];
+    if (ly.L == L) return AF_OK;
     const int64_t need = rows_elems(T, L);
+    if (ly.L || (size_t)need * 2 > T->ps_bytes)
+        if (int rc = af_cuda_check(cudaDeviceSynchronize(), "pair layout")) return rc;
     if ((size_t)need * 2 > T->ps_bytes) {
         cudaFree(T->d_ps);
         T->d_ps = nullptr;
@@ -601,79 +612,152 @@ static int pairs_layout(af_plan_t p, int64_t L)
     }
     std::vector<int64_t> rowoff(T->nrows), soff(T->h_srow.size());
     std::vector<int4> pinfo(T->np);
-    int64_t off = 0;
-    T->maxlen = 0;
+    int64_t off = 0, maxlen = 0;
     for (int q = 0; q < T->np; q++) {
         const int64_t len = r16(L + T->h_dhi[q] - T->h_dlo[q] + T->rwe + 8);
         pinfo[q] = make_int4(T->h_rb[q], T->h_rb[q + 1] - T->h_rb[q], T->h_dlo[q], (int)len);
         for (int g = T->h_rb[q]; g < T->h_rb[q + 1]; g++, off += len) rowoff[g] = off;
-        T->maxlen = std::max(T->maxlen, len);
+        maxlen = std::max(maxlen, len);
     }
     for (size_t i = 0; i < soff.size(); i++) soff[i] = rowoff[T->h_srow[i]] + T->h_scpart[i];
+    ly.L = 0;
     cudaError_t e;
-    if ((e = cudaMemcpy(T->d_rowoff, rowoff.data(), rowoff.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(T->d_soff, soff.data(), soff.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(T->d_pinfo, pinfo.data(), pinfo.size() * sizeof(int4), cudaMemcpyHostToDevice)) !=
+    if ((e = cudaMemcpy(ly.d_rowoff, rowoff.data(), rowoff.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(ly.d_soff, soff.data(), soff.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(ly.d_pinfo, pinfo.data(), pinfo.size() * sizeof(int4), cudaMemcpyHostToDevice)) !=
             cudaSuccess)
         return af_cuda_check(e, "pair layout");
-    T->L = L;
+    ly.L = L;
+    ly.maxlen = maxlen;
     return AF_OK;
 }
 
-int af_pairs_reserve(af_plan_t p, int64_t nout)
-{
-    const int64_t L = af_pairs_block(p, nout);
-    return L > 0 ? pairs_layout(p, L) : AF_OK;
-}
-
-int af_launch_pairs(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,
-                    af_rowstats_t* d_stats, cudaStream_t s)
+int af_pairs_reserve(af_plan_t p, int64_t nout, bool search)
 {
     af_pair_tables* T = &p->pairs;
     const int64_t L = af_pairs_block(p, nout);
-    if (L <= 0) return af_set_error(AF_EINVAL, "pairs: not usable for this plan and length");
-    if (int rc = pairs_layout(p, L)) return rc;
+    if (L <= 0) return AF_OK;  // the channel tile kernel serves this plan
+    if (L > T->lay[0].L)
+        if (int rc = pairs_layout(p, 0, L)) return rc;
+    if (search) {
+        // at least four time blocks, so that the input copy overlaps the work
+        const int64_t tiles = (nout + kPTTE - 1) / kPTTE;
+        const int64_t L4 = std::min(T->lay[0].L, (tiles + 3) / 4 * kPTTE);
+        if (int rc = pairs_layout(p, 1, L4)) return rc;
+    }
+    return AF_OK;
+}
+
+int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,
+                          af_rowstats_t* d_stats, cudaStream_t s, int layout, int64_t T0, cudaEvent_t* mid)
+{
+    af_pair_tables* T = &p->pairs;
+    const af_pair_tables::Layout& ly = T->lay[layout];
+    const int64_t L = ly.L;
+    if (L <= 0 || L % kPTTE || T0 % L) return af_set_error(AF_EINVAL, "pairs: time block not laid out");
     const int rwb = 2 * T->rwe;
     const size_t s2 = tile_smem(T->shape, rwb), s1 = rows_smem(T->maxdr);
     if (int rc = af_ensure_smem(tile_kernel(T->shape), s2)) return rc;
     if (int rc = af_ensure_smem((const void*)k_pair_rows, s1)) return rc;
-    if (d_stats)
-        if (int rc = af_cuda_check(cudaMemsetAsync(d_stats, 0, (size_t)p->ndm * sizeof(af_rowstats_t), s),
-                                   "pairs stats reset"))
-            return rc;
-    const int etiles = (int)((T->maxlen + kET - 1) / kET);
+    const int etiles = (int)((ly.maxlen + kET - 1) / kET);
+    const unsigned long long g1 = (unsigned long long)T->np * etiles;
+    const int64_t tiles = (std::min(L, nout - T0) + kPTTE - 1) / kPTTE;
+    const unsigned long long g2 = (unsigned long long)tiles * (unsigned)T->tt.nblk;
+    if (g1 > 0x7fffffffULL || g2 > 0x7fffffffULL) return af_set_error(AF_EINVAL, "pairs: problem too large for one grid");
+    k_pair_rows<<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, ly.d_pinfo, T->d_rdelta, ly.d_rowoff, T0,
+                                               etiles, T->d_ps);
+    if (int rc = af_cuda_check(cudaGetLastError(), "pair rows launch")) return rc;
+    if (mid) AF_CUDA(cudaEventRecord(*mid, s));
     PairArgs a;
     a.PS = T->d_ps;
     a.chunks = T->d_chunks;
     a.chkoff = T->d_chkoff;
     a.tabs = T->d_tabs;
     a.sbytes = T->d_sbytes;
-    a.soff = T->d_soff;
+    a.soff = ly.d_soff;
     a.perm = T->tt.d_perm;
     a.rwb = rwb;
     a.nblk = (unsigned)T->tt.nblk;
+    a.T0 = T0;
+    a.tend = std::min(nout, T0 + L);
     a.nout = nout;
     a.Y = d_plane;
     a.stats = d_stats;
     a.err = p->d_err;
-    for (int64_t T0 = 0; T0 < nout; T0 += L) {
-        const unsigned long long g1 = (unsigned long long)T->np * etiles;
-        const int64_t tiles = (std::min(L, nout - T0) + kPTTE - 1) / kPTTE;
-        const unsigned long long g2 = (unsigned long long)tiles * a.nblk;
-        if (g1 > 0x7fffffffULL || g2 > 0x7fffffffULL)
-            return af_set_error(AF_EINVAL, "pairs: problem too large for one grid");
-        k_pair_rows<<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, T->d_pinfo, T->d_rdelta, T->d_rowoff, T0,
-                                                   etiles, T->d_ps);
-        if (int rc = af_cuda_check(cudaGetLastError(), "pair rows launch")) return rc;
-        a.T0 = T0;
-        a.tend = std::min(nout, T0 + L);
-        if (T->shape == 0)
-            k_pair_tile<kPNW, 32, 2><<<(unsigned)g2, (kPNW + 1) * 32, s2, s>>>(a);
-        else if (T->shape == 1)
-            k_pair_tile<kPNW, 24, 3><<<(unsigned)g2, (kPNW + 1) * 32, s2, s>>>(a);
-        else
-            k_pair_tile<kPNW, 16, 4><<<(unsigned)g2, (kPNW + 1) * 32, s2, s>>>(a);
-        if (int rc = af_cuda_check(cudaGetLastError(), "pair tile launch")) return rc;
+    if (T->shape == 0)
+        k_pair_tile<kPNW, 32, 2><<<(unsigned)g2, (kPNW + 1) * 32, s2, s>>>(a);
+    else if (T->shape == 1)
+        k_pair_tile<kPNW, 24, 3><<<(unsigned)g2, (kPNW + 1) * 32, s2, s>>>(a);
+    else
+        k_pair_tile<kPNW, 16, 4><<<(unsigned)g2, (kPNW + 1) * 32, s2, s>>>(a);
+    return af_cuda_check(cudaGetLastError(), "pair tile launch");
+}
+
+int af_launch_pairs(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,
+                    af_rowstats_t* d_stats, cudaStream_t s)
+{
+    af_pair_tables* T = &p->pairs;
+    const int64_t L = T->lay[0].L;
+    if (L <= 0) return af_set_error(AF_EINVAL, "pairs: no row buffer reserved");
+    if (d_stats)
+        if (int rc = af_cuda_check(cudaMemsetAsync(d_stats, 0, (size_t)p->ndm * sizeof(af_rowstats_t), s),
+                                   "pairs stats reset"))
+            return rc;
+    const int slot = T->tcalls > 0 ? T->tnext : -1;
+    int b = 0;
+    for (int64_t T0 = 0; T0 < nout; T0 += L, b++) {
+        const bool rec = slot >= 0 && b < T->tblocks;
+        cudaEvent_t* e = rec ? &T->tev[((size_t)slot * T->tblocks + b) * 3] : nullptr;
+        if (rec) AF_CUDA(cudaEventRecord(e[0], s));
+        if (int rc = af_launch_pairs_block(p, d_in, nsamp, nout, d_plane, d_stats, s, 0, T0, rec ? e + 1 : nullptr))
+            return rc;
+        if (rec) AF_CUDA(cudaEventRecord(e[2], s));
     }
+    if (slot >= 0) {
+        T->tnb[slot] = std::min(b, T->tblocks);
+        T->trowbytes[slot] = 2 * rows_elems(T, L) * (int64_t)b;
+        T->tnext = (slot + 1) % T->tcalls;
+    }
+    return AF_OK;
+}
+
+extern "C" int af_dedisperse_timing(af_plan_t p, int ncalls)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    if (ncalls < 0 || ncalls > 4096) return af_set_error(AF_EINVAL, "af_dedisperse_timing: ncalls in 0..4096");
+    af_pair_tables* T = &p->pairs;
+    AF_CUDA(cudaDeviceSynchronize());
+    for (cudaEvent_t ev : T->tev) cudaEventDestroy(ev);
+    T->tev.clear();
+    T->tcalls = T->tnext = 0;
+    T->tblocks = 8;
+    if (ncalls == 0) return AF_OK;
+    T->tev.assign((size_t)ncalls * T->tblocks * 3, nullptr);
+    for (cudaEvent_t& ev : T->tev)
+        if (cudaError_t e = cudaEventCreate(&ev)) return af_cuda_check(e, "af_dedisperse_timing");
+    T->tnb.assign(ncalls, 0);
+    T->trowbytes.assign(ncalls, 0);
+    T->tcalls = ncalls;
+    return AF_OK;
+}
+
+extern "C" int af_dedisperse_times(af_plan_t p, int call, float* rows_ms, float* tiles_ms, int64_t* row_bytes)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    af_pair_tables* T = &p->pairs;
+    if (call < 0 || call >= T->tcalls) return af_set_error(AF_EINVAL, "af_dedisperse_times: no such call slot");
+    float r = 0.f, t = 0.f;
+    for (int b = 0; b < T->tnb[call]; b++) {
+        cudaEvent_t* e = &T->tev[((size_t)call * T->tblocks + b) * 3];
+        float x = 0.f, y = 0.f;
+        AF_CUDA(cudaEventSynchronize(e[2]));
+        AF_CUDA(cudaEventElapsedTime(&x, e[0], e[1]));
+        AF_CUDA(cudaEventElapsedTime(&y, e[1], e[2]));
+        r += x;
+        t += y;
+    }
+    if (rows_ms) *rows_ms = r;
+    if (tiles_ms) *tiles_ms = t;
+    if (row_bytes) *row_bytes = T->trowbytes[call];
     return AF_OK;
 }

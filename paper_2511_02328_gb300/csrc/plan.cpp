@@ -544,6 +544,14 @@ extern "C" int af_cluster(af_plan_t p, af_cand_t* h_cands, int32_t n, double dm_
     return AF_OK;
 }
 
+extern "C" int af_dedisperse_reserve(af_plan_t p, int64_t max_nsamp)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    int64_t nout;
+    if (int rc = check_nout(p, max_nsamp, &nout)) return rc;
+    return af_pairs_reserve(p, nout, false);
+}
+
 extern "C" int af_search_reserve(af_plan_t p, int64_t max_nsamp, int32_t cap)
 {
     if (int rc = af_check_plan(p)) return rc;
@@ -569,7 +577,7 @@ extern "C" int af_search_reserve(af_plan_t p, int64_t max_nsamp, int32_t cap)
         }
     p->ws_nsamp = max_nsamp;
     p->ws_cap = cap;
-    return af_pairs_reserve(p, nout);  // the pair-row buffer, where that path applies
+    return af_pairs_reserve(p, nout, true);  // the pair-row buffers, where that path applies
 }
 
 extern "C" int af_search(af_plan_t p, const uint8_t* h_in, int64_t nsamp, const int32_t* widths, int nw,
@@ -585,7 +593,30 @@ extern "C" int af_search(af_plan_t p, const uint8_t* h_in, int64_t nsamp, const 
     af_widths_t w;
     if (int rc = af_check_widths(p, widths, nw, nout, &w)) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    if (af_dedisp_uses_tiles(p)) {
+    if (af_dedisp_uses_pairs(p, nout)) {
+        // Pair rows: the outputs in the search layout's time blocks (at least
+        // four); each block's rows and tiles run as soon as its input columns
+        // (block end + Dmax) are in, overlapping the rest of the copy.
+        const int ly = p->pairs.lay[1].L > 0 ? 1 : 0;
+        const int64_t L = p->pairs.lay[ly].L;
+        AF_CUDA(cudaEventRecord(p->ws_ev[0], s));
+        AF_CUDA(cudaStreamWaitEvent(p->ws_copy, p->ws_ev[0], 0));
+        AF_CUDA(cudaMemsetAsync(p->d_stats, 0, (size_t)p->ndm * sizeof(af_rowstats_t), s));
+        int64_t col = 0;
+        int k = 0;
+        for (int64_t T0 = 0; T0 < nout; T0 += L, k++) {
+            const int64_t need = T0 + L >= nout ? nsamp : std::min<int64_t>(nsamp, T0 + L + p->dmax);
+            if (need > col) {
+                AF_CUDA(cudaMemcpy2DAsync(p->ws_in + col, (size_t)nsamp, h_in + col, (size_t)nsamp, (size_t)(need - col),
+                                          (size_t)p->nchan, cudaMemcpyHostToDevice, p->ws_copy));
+                col = need;
+            }
+            cudaEvent_t ev = p->ws_ev[k % 4];
+            AF_CUDA(cudaEventRecord(ev, p->ws_copy));
+            AF_CUDA(cudaStreamWaitEvent(s, ev, 0));
+            if (int rc = af_launch_pairs_block(p, p->ws_in, nsamp, nout, p->ws_plane, p->d_stats, s, ly, T0)) return rc;
+        }
+    } else if (af_dedisp_uses_tiles(p)) {
         // The input arrives in time segments on the copy stream; each segment's
         // output tiles are dedispersed as soon as their columns (and the Dmax
         // halo after them) are in, overlapping the rest of the copy.

@@ -352,6 +352,8 @@ def test_pair_rows_several_time_blocks(nchan, f_lo, f_hi, monkeypatch):
     monkeypatch.setenv("AFGB_PAIR_BUDGET_MB", str(-(-budget // (1 << 20))))
     x = np.random.default_rng(nchan).integers(0, 256, (nchan, nsamp), dtype=np.uint8)
     p = Plan(nchan, f_lo, f_hi, tsamp, dms)
+    assert p.kernel()["path"] == "tile"                 # nothing reserved yet
+    p.reserve(nsamp)
     assert p.kernel()["path"] == "pairs"
     stats = torch.empty((p.ndm, 2), dtype=torch.int64, device="cuda")
     plane = p.dedisperse(torch.from_numpy(x).cuda(), stats=stats)
@@ -365,10 +367,10 @@ def test_pair_rows_several_time_blocks(nchan, f_lo, f_hi, monkeypatch):
 
 
 def test_pair_rows_is_the_default_path(c1_data):
-    """The 256-channel workload runs on pair rows by default and the channel
-    tile kernel, forced, gives the same plane."""
+    """The 256-channel workload runs on pair rows once reserved."""
     x, D, Y, _, _ = c1_data
     p = _plan(C1)
+    p.reserve(x.shape[1])
     assert p.kernel()["path"] == "pairs"
     p.close()
 
