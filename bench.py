@@ -435,8 +435,10 @@ def run_batch(args, dev, stream):
         "speedup_vs_one_plan_at_a_time": ms_sep / ms_batch, "tile_shape": [nw, m], "autotune_ms": tuned_ms,
         "autotune_cached": bool(cached), "build_s": build_s, "candidates": int(ncand), "steps": steps,
         "alu_frac_whole_batch": work / (ms_batch * 1e-3) / alu_peak,
-        "note": "ms_per_batch covers dedispersion of all beams in one persistent launch plus every beam's S/N and "
-                "candidates (CUDA graph replay); alu_frac is the batch's adds over 152 x 128 x max clock",
+        "note": "ms_per_batch covers the dedispersion of all beams (tile_shape [nw, m]: one persistent "
+                "channel-tile launch; [15, 0]: beam after beam, pair rows sharing one row buffer where a beam's plan "
+                "uses them) plus every beam's S/N and candidates, one CUDA graph replay; one_plan_at_a_time runs the "
+                "channel tile kernel per beam; alu_frac is the batch's adds over 152 x 128 x max clock",
     }
 
 

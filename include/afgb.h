@@ -394,11 +394,14 @@ int af_search(af_plan_t plan, const uint8_t* h_in, int64_t nsamp,
 /* ---- many beams in one persistent launch, replayed as a CUDA graph ------ *
  * The paper runs several antenna streams on one GPU (Sec. 4.3); here each
  * beam is an independent search (its own band, sampling, DM list, length,
- * widths and threshold) and all beams' dedispersion runs as ONE persistent
- * kernel that takes (beam, DM block, time tile) items from a work counter,
- * followed by every beam's boxcar S/N and candidate compaction.  Results are
- * identical to af_dedisperse / af_boxcar_snr / af_candidates on each beam
- * alone. */
+ * widths and threshold).  All beams' dedispersion runs either as ONE
+ * persistent channel-tile kernel that takes (beam, DM block, time tile) items
+ * from a work counter, or beam after beam, each on its single-plan path (pair
+ * rows, see af_dedisperse_reserve, sharing one row buffer where the beam's
+ * plan uses them), whichever the build-time
+ * autotuner measures faster; then every beam's boxcar S/N and candidate
+ * compaction; all of it one CUDA graph.  Results are identical to
+ * af_dedisperse / af_boxcar_snr / af_candidates on each beam alone. */
 typedef struct af_batch_s* af_batch_t;
 
 typedef struct {
@@ -418,11 +421,14 @@ typedef struct {
 
 /* Builds the batch: one plan per beam, each beam's plane / S/N / candidate
  * buffers on the current device (AF_ENOBUFS if they need more than
- * hbm_budget bytes; 0 = no budget), and picks the tile shape of the
- * dedispersion kernel by timing every compiled shape on these beams (the
- * beams' inputs must be valid device memory; their contents do not matter).
+ * hbm_budget bytes; 0 = no budget), and picks the dedispersion strategy by
+ * timing every compiled tile shape and the pair-row strategy on these beams
+ * (the beams' inputs must be valid device memory; their contents do not
+ * matter).  The pair-row strategy takes a row buffer of at most 16 GiB
+ * (outside hbm_budget), freed again when another strategy wins.
  * With the environment variable AFGB_AUTOTUNE_CACHE naming a file, the
- * choice is cached there as JSON keyed by GPU name and beam shapes. */
+ * choice is cached there as JSON keyed by GPU name and beam shapes;
+ * AFGB_BATCH_STRATEGY=tile or =pairs limits the choice to those strategies. */
 int af_batch_build(af_batch_t* out, const af_beam_desc_t* beams, int nbeams, size_t hbm_budget);
 
 /* Enqueues the whole batch on `stream`: the first call captures a CUDA graph,
@@ -439,8 +445,9 @@ int af_batch_candidates(af_batch_t batch, int beam, af_cand_t* h_out, int32_t ca
 int af_batch_buffers(af_batch_t batch, int beam, int32_t** d_plane, float** d_snr, uint8_t** d_best_w,
                      int64_t* nout);
 
-/* The tile shape chosen by the autotuner: DM rows per block, 128-output
- * groups per lane, its measured time (ms, 0 if read from the cache). */
+/* The strategy chosen by the autotuner: the persistent tile kernel's DM rows
+ * per block and 128-output groups per lane, or nw = 15, m = 0 for beam after
+ * beam; its measured time (ms, 0 if read from the cache). */
 int af_batch_shape(af_batch_t batch, int* nw, int* m, float* tuned_ms, int* from_cache);
 
 int af_batch_destroy(af_batch_t batch);

@@ -1,15 +1,17 @@
-// batch.cu -- many beams of uneven shape in one persistent dedispersion
-// launch, replayed as a CUDA graph, with the block shape picked by timing.
+// batch.cu -- many beams of uneven shape dedispersed by one CUDA graph, the
+// execution strategy picked by timing.
 //
 // af_batch_build makes one plan per beam, allocates every beam's plane, S/N
-// and candidate buffers (within an HBM budget), then autotunes: for each
-// compiled tile shape (DM rows per block x outputs per lane) it builds the
-// beams' tile tables and times the persistent kernel on the batch itself;
-// the fastest shape is kept and cached in a JSON file (AFGB_AUTOTUNE_CACHE)
-// keyed by the GPU name and the beams' shapes.  af_batch_run replays a graph
-// of: counter and row-sum resets, the persistent dedispersion kernel over all
-// (beam, DM block, time tile) items, then per beam the boxcar S/N and the
-// candidate compaction.
+// and candidate buffers (within an HBM budget), then autotunes over the
+// strategies: one persistent channel-tile launch over all (beam, DM block,
+// time tile) items for each compiled tile shape (DM rows per block x outputs
+// per lane), and the beams one after another, each on its single-plan path
+// (pair rows, pairs.cu, sharing one row buffer, where the plan uses them);
+// each is timed on the batch itself, the fastest is kept and
+// cached in a JSON file (AFGB_AUTOTUNE_CACHE) keyed by the GPU name and the
+// beams' shapes.  af_batch_run replays a graph of: the dedispersion (with its
+// counter and row-sum resets), then per beam the boxcar S/N and the candidate
+// compaction.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -59,6 +61,8 @@ const Shape kShapes[] = {
     {15, 6, launch_persistent<15, 6>, set_attr<15, 6>},
 };
 constexpr int kNShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+constexpr int kPairs = kNShapes;       // strategy index of beam after beam (pair rows where they apply)
+constexpr size_t kPairsMax = (size_t)16 << 30;  // largest shared row buffer
 
 struct Beam {
     af_plan_t plan = nullptr;
@@ -92,6 +96,8 @@ struct af_batch_s {
     long long total = 0;
     int grid = 0;
     size_t smem = 0;
+    uint16_t* d_rows = nullptr;          // row buffer shared by the beams' plans (pair-row strategy)
+    size_t rows_bytes = 0;
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
 };
@@ -115,7 +121,37 @@ static void free_batch(af_batch_t b)
     cudaFree(b->d_first);
     cudaFree(b->d_counter);
     cudaFree(b->d_err);
+    cudaFree(b->d_rows);
     delete b;
+}
+
+// The beam-after-beam strategy: every beam on its single-plan path, pair rows
+// for the beams whose plans use them, all on one shared row buffer sized for
+// the largest such beam's full length (at most kPairsMax; the other beams, or
+// all of them past the cap, run in time blocks); the rest on the channel tile
+// kernel.  AF_EINVAL: no beam can use pair rows (the persistent strategies
+// cover that case).
+static int setup_pairs(af_batch_t b)
+{
+    size_t need = 0;
+    for (Beam& x : b->beams)
+        if (x.plan->pairs.ok) need = std::max(need, af_pairs_bytes(x.plan, x.nout));
+    if (need == 0) return af_set_error(AF_EINVAL, "batch: no beam can use pair rows");
+    need = std::min(need, kPairsMax);
+    if (!b->d_rows) {
+        if (cudaMalloc(&b->d_rows, need) != cudaSuccess) {
+            cudaGetLastError();
+            b->d_rows = nullptr;
+            return af_set_error(AF_EINVAL, "batch: no room for the shared row buffer");
+        }
+        b->rows_bytes = need;
+    }
+    for (Beam& x : b->beams)
+        if (x.plan->pairs.ok)
+            if (int rc = af_pairs_attach(x.plan, b->d_rows, b->rows_bytes, x.nout))
+                return rc == AF_ENOBUFS ? af_set_error(AF_EINVAL, "batch: shared row buffer too small") : rc;
+    b->shape = kPairs;
+    return AF_OK;
 }
 
 // Builds the per-beam tile tables for shape si and uploads the job list.
@@ -175,6 +211,13 @@ static int setup_shape(af_batch_t b, int si)
 
 static int enqueue_dedisp(af_batch_t b, cudaStream_t s)
 {
+    if (b->shape == kPairs) {
+        for (int k : b->order) {
+            Beam& x = b->beams[k];
+            if (int rc = af_launch_dedisperse(x.plan, x.d_in, x.nsamp, x.nout, x.d_plane, x.d_stats, s)) return rc;
+        }
+        return AF_OK;
+    }
     const Shape& sh = kShapes[b->shape];
     AF_CUDA(sh.attr(b->smem));
     AF_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s));
@@ -270,13 +313,19 @@ static int autotune(af_batch_t b)
     }();
     if (path) {
         int nw = 0, m = 0;
-        if (cache_lookup(path, key, &nw, &m))
+        if (cache_lookup(path, key, &nw, &m)) {
+            if (m == 0) {
+                if (int rc = setup_pairs(b)) return rc;
+                b->from_cache = true;
+                return AF_OK;
+            }
             for (int si = 0; si < kNShapes; si++)
                 if (kShapes[si].nw == nw && kShapes[si].m == m) {
                     if (int rc = setup_shape(b, si)) return rc;
                     b->from_cache = true;
                     return AF_OK;
                 }
+        }
     }
     cudaStream_t s;
     AF_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
@@ -286,8 +335,12 @@ static int autotune(af_batch_t b)
     int best = -1;
     float best_ms = 0.0f;
     int rc = AF_OK;
-    for (int si = 0; si < kNShapes && rc == AF_OK; si++) {
-        int r = setup_shape(b, si);
+    // AFGB_BATCH_STRATEGY=tile|pairs restricts the candidates
+    const char* only = getenv("AFGB_BATCH_STRATEGY");
+    for (int si = 0; si <= kNShapes && rc == AF_OK; si++) {
+        if (only && !strcmp(only, "tile") && si == kPairs) continue;
+        if (only && !strcmp(only, "pairs") && si != kPairs) continue;
+        int r = si == kPairs ? setup_pairs(b) : setup_shape(b, si);
         if (r == AF_EINVAL) continue;  // this shape's window does not fit: skip it
         if (r) {
             rc = r;
@@ -314,9 +367,19 @@ static int autotune(af_batch_t b)
     cudaStreamDestroy(s);
     if (rc) return rc;
     if (best < 0) return af_set_error(AF_EINVAL, "batch: no compiled tile shape fits these beams");
-    if (int r = setup_shape(b, best)) return r;
+    if (best != kPairs && b->d_rows) {
+        // the row buffer is not needed: detach nothing (the plans keep their
+        // layouts but never launch pair rows in this batch), free it
+        if (int r = af_cuda_check(cudaDeviceSynchronize(), "batch")) return r;
+        for (Beam& x : b->beams) x.plan->pairs.lay[0].L = x.plan->pairs.lay[1].L = 0;
+        cudaFree(b->d_rows);
+        b->d_rows = nullptr;
+        b->rows_bytes = 0;
+    }
+    if (int r = best == kPairs ? setup_pairs(b) : setup_shape(b, best)) return r;
     b->tuned_ms = best_ms;
-    if (path) cache_store(path, key, kShapes[best].nw, kShapes[best].m, best_ms);
+    if (path) cache_store(path, key, best == kPairs ? 15 : kShapes[best].nw, best == kPairs ? 0 : kShapes[best].m,
+                          best_ms);
     return AF_OK;
 }
 
@@ -426,6 +489,8 @@ extern "C" int af_batch_candidates(af_batch_t b, int beam, af_cand_t* h_out, int
         cudaMemset(b->d_err, 0, sizeof(int));
         return af_set_error(AF_ETIMEOUT, "af_batch: a kernel's bounded wait for an asynchronous copy ran out");
     }
+    if (b->shape == kPairs)
+        if (int rc = af_plan_check(x.plan)) return rc;  // the pair kernels flag on the beam's plan
     int32_t n = std::min(std::min(total, cap), x.cap);
     if (n > 0) {
         AF_CUDA(cudaMemcpy(h_out, x.d_cands, (size_t)n * sizeof(af_cand_t), cudaMemcpyDeviceToHost));
@@ -453,8 +518,8 @@ extern "C" int af_batch_buffers(af_batch_t b, int beam, int32_t** d_plane, float
 extern "C" int af_batch_shape(af_batch_t b, int* nw, int* m, float* tuned_ms, int* from_cache)
 {
     if (!b) return af_set_error(AF_EINVAL, "af_batch_shape: NULL batch");
-    if (nw) *nw = kShapes[b->shape].nw;
-    if (m) *m = kShapes[b->shape].m;
+    if (nw) *nw = b->shape == kPairs ? 15 : kShapes[b->shape].nw;
+    if (m) *m = b->shape == kPairs ? 0 : kShapes[b->shape].m;
     if (tuned_ms) *tuned_ms = b->tuned_ms;
     if (from_cache) *from_cache = b->from_cache ? 1 : 0;
     return AF_OK;

@@ -91,6 +91,7 @@ struct af_pair_tables {
     int32_t* d_sbytes = nullptr;   // per slot: window bytes
     uint16_t* d_ps = nullptr;      // row buffer
     size_t ps_bytes = 0;
+    bool ps_owned = true;          // false: a buffer shared by a batch's plans
     // Row-buffer layouts made by the reservation calls: 0 for af_dedisperse
     // (the longest time block the budget allows), 1 for af_search (at least
     // four blocks, so that the input copy overlaps the work).
@@ -119,6 +120,10 @@ int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64
                           af_rowstats_t* d_stats, cudaStream_t s, int layout, int64_t T0,
                           cudaEvent_t* mid = nullptr);
 int af_pair_tile_outputs();
+// Row-buffer bytes of a full-length single time block, and the use of a row
+// buffer owned by someone else (a batch's plans run one after another on one).
+size_t af_pairs_bytes(af_plan_t p, int64_t nout);
+int af_pairs_attach(af_plan_t p, uint16_t* buf, size_t bytes, int64_t nout);
 bool af_dedisp_uses_pairs(af_plan_t p, int64_t nout);
 
 // ---------------------------------------------------------------- plan

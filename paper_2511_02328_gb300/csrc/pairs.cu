@@ -385,7 +385,7 @@ void af_pairs_free(af_pair_tables* T)
         cudaFree(l.d_rowoff);
         cudaFree(l.d_soff);
     }
-    cudaFree(T->d_ps);
+    if (T->ps_owned) cudaFree(T->d_ps);
     for (cudaEvent_t ev : T->tev) cudaEventDestroy(ev);
     *T = af_pair_tables();
 }
@@ -604,6 +604,7 @@ static int pairs_layout(af_plan_t p, int k, int64_t L)
     if (ly.L || (size_t)need * 2 > T->ps_bytes)
         if (int rc = af_cuda_check(cudaDeviceSynchronize(), "pair layout")) return rc;
     if ((size_t)need * 2 > T->ps_bytes) {
+        if (!T->ps_owned) return af_set_error(AF_ENOBUFS, "pairs: the shared row buffer is too small");
         cudaFree(T->d_ps);
         T->d_ps = nullptr;
         T->ps_bytes = 0;
@@ -646,6 +647,35 @@ int af_pairs_reserve(af_plan_t p, int64_t nout, bool search)
         if (int rc = pairs_layout(p, 1, L4)) return rc;
     }
     return AF_OK;
+}
+
+size_t af_pairs_bytes(af_plan_t p, int64_t nout)
+{
+    const af_pair_tables* T = &p->pairs;
+    if (!T->ok || nout <= 0) return 0;
+    return 2 * (size_t)rows_elems(T, (nout + kPTTE - 1) / kPTTE * kPTTE);
+}
+
+int af_pairs_attach(af_plan_t p, uint16_t* buf, size_t bytes, int64_t nout)
+{
+    af_pair_tables* T = &p->pairs;
+    if (!T->ok) return af_set_error(AF_EINVAL, "pairs: plan cannot use pair rows");
+    const int64_t tiles = (nout + kPTTE - 1) / kPTTE;
+    const int64_t cap = (int64_t)(bytes / 2);
+    int64_t lo = std::min<int64_t>(kMinTiles, tiles), hi = tiles;
+    if (rows_elems(T, lo * kPTTE) > cap) return af_set_error(AF_ENOBUFS, "pairs: shared row buffer too small");
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) / 2;
+        if (rows_elems(T, mid * kPTTE) <= cap) lo = mid;
+        else hi = mid - 1;
+    }
+    if (int rc = af_cuda_check(cudaDeviceSynchronize(), "pairs attach")) return rc;
+    if (T->ps_owned) cudaFree(T->d_ps);
+    T->d_ps = buf;
+    T->ps_bytes = bytes;
+    T->ps_owned = false;
+    T->lay[0].L = T->lay[1].L = 0;
+    return pairs_layout(p, 0, lo * kPTTE);
 }
 
 int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,

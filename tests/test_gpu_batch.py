@@ -71,14 +71,21 @@ def _check_against_oracle(batch, xs):
         assert float(err.max()) <= TOL, (i, float(err.max()))
 
 
-def test_batch_matches_oracle_and_single_beam():
+@pytest.mark.parametrize("strategy", ["auto", "tile", "pairs"])
+def test_batch_matches_oracle_and_single_beam(strategy, monkeypatch):
+    """Every dedispersion strategy of the batch (the autotuner's pick, the
+    persistent tile kernel, pair rows beam after beam) gives each beam's
+    oracle plane and S/N and the single-beam host search's candidates."""
     from paper_2511_02328_gb300 import _lib
     from paper_2511_02328_gb300.search import Plan
+    if strategy != "auto":
+        monkeypatch.setenv("AFGB_BATCH_STRATEGY", strategy)
     xs = _make(1)
     xs_dev = [torch.from_numpy(x).cuda() for x in xs]
     batch = _build(xs_dev)
     nw, m, ms, cached = _lib.af_batch_shape(batch)
-    assert (nw, m) in [(11, 8), (7, 8), (15, 6)]
+    assert (nw, m) in {"auto": [(11, 8), (7, 8), (15, 6), (15, 0)], "tile": [(11, 8), (7, 8), (15, 6)],
+                       "pairs": [(15, 0)]}[strategy]
     _lib.af_batch_run(batch, torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     _check_against_oracle(batch, xs)
