@@ -459,9 +459,12 @@ int af_batch_destroy(af_batch_t batch);
  * exactly (the paper's time blocking with a halo of the maximum shift, Eq. L1
  * of Sec. 2.3, applied across chunks).  The overlap of each beam stays on the
  * device.  Requests are admitted into slots whose number the HBM budget sets;
- * a dispatcher thread runs every admitted window together (one persistent
- * dedispersion launch, then each window's S/N and candidates), so requests
- * that arrive while others run join the next launch. */
+ * a dispatcher thread runs every admitted window together (their
+ * dedispersion -- window after window on pair rows, see
+ * af_dedisperse_reserve, when the plan uses them and the budget holds the
+ * row buffer next to one slot; else one persistent channel-tile launch --
+ * then each window's S/N and candidates), so requests that arrive while
+ * others run join the next dispatch. */
 typedef struct af_stream_s* af_stream_t;
 
 typedef struct {
@@ -475,7 +478,8 @@ typedef struct {
     int nw;
     float thresh;
     int32_t cap;            /* candidates kept per window                       */
-    size_t hbm_budget;      /* bytes for slots + beam state; 0 = no limit       */
+    size_t hbm_budget;      /* bytes for slots + beam state (+ the pair-row buffer
+                               when used); 0 = no limit                          */
     int max_slots;          /* upper bound on slots (0 = 4)                     */
     int timeout_ms;         /* af_stream_push: longest wait for a free slot;
                                0 = return AF_EAGAIN at once                     */
@@ -495,7 +499,7 @@ typedef struct {
 
 typedef struct {
     int64_t windows;        /* windows completed and polled                     */
-    int64_t launches;       /* persistent dedispersion launches                 */
+    int64_t launches;       /* dispatches (one dedispersion pass over the ready windows each) */
     int max_inflight;       /* most windows admitted at once                    */
     int slots;
     double p50_ms, p99_ms, max_ms;  /* chunk-to-candidate latency               */

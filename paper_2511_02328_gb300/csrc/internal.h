@@ -123,6 +123,7 @@ int af_pair_tile_outputs();
 // Row-buffer bytes of a full-length single time block, and the use of a row
 // buffer owned by someone else (a batch's plans run one after another on one).
 size_t af_pairs_bytes(af_plan_t p, int64_t nout);
+size_t af_pairs_reserved_bytes(af_plan_t p, int64_t nout);  // what af_pairs_reserve would allocate
 int af_pairs_attach(af_plan_t p, uint16_t* buf, size_t bytes, int64_t nout);
 bool af_dedisp_uses_pairs(af_plan_t p, int64_t nout);
 

@@ -649,6 +649,12 @@ int af_pairs_reserve(af_plan_t p, int64_t nout, bool search)
     return AF_OK;
 }
 
+size_t af_pairs_reserved_bytes(af_plan_t p, int64_t nout)
+{
+    const int64_t L = af_pairs_block(p, nout);
+    return L > 0 ? 2 * (size_t)rows_elems(&p->pairs, L) : 0;
+}
+
 size_t af_pairs_bytes(af_plan_t p, int64_t nout)
 {
     const af_pair_tables* T = &p->pairs;

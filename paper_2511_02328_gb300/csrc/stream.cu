@@ -9,8 +9,10 @@
 //
 // Requests (one window of one beam) are admitted into slots; the number of
 // slots is set by an HBM budget.  A dispatcher thread takes every window whose
-// input is on the device and runs them together -- one persistent
-// dedispersion launch over all their (DM block, time tile) items, then each
+// input is on the device and runs them together -- their dedispersion (on
+// pair rows, pairs.cu, window after window on the plan's row buffer where the
+// plan uses them and the budget holds the buffer; else one persistent
+// channel-tile launch over all their (DM block, time tile) items), then each
 // window's boxcar S/N and candidate compaction, then the candidates' copy to
 // pinned host memory.  Windows that arrive while others run are admitted as
 // slots free up and join the next launch, so copies and computation of
@@ -106,6 +108,7 @@ struct af_stream_s {
     int* d_err = nullptr;
     int grid = 0;
     size_t smem = 0;
+    bool pairs = false;                  // windows dedispersed on pair rows
     int max_batch = 0;
     // inline classification of held windows
     cudaStream_t cstream = nullptr;
@@ -166,6 +169,14 @@ static int dispatch(af_stream_s* s, const std::vector<int>& batch)
         first[i + 1] = first[i] + (long long)tiles * a.nblk;
     }
     cudaStream_t d = s->dstream;
+    if (s->pairs) {
+        // window after window on the plan's row buffer (one stream: no overlap between them)
+        for (int k : batch) {
+            Slot& sl = s->slots[k];
+            AF_CUDA(cudaStreamWaitEvent(d, sl.input_ready, 0));
+            if (int rc = af_launch_pairs(p, sl.d_in, s->window, s->hop, sl.d_plane, sl.d_stats, d)) return rc;
+        }
+    } else {
     AF_CUDA(cudaMemcpyAsync(s->d_jobs[r], jobs, batch.size() * sizeof(aftile::TileArgs), cudaMemcpyHostToDevice, d));
     AF_CUDA(cudaMemcpyAsync(s->d_first[r], first, (batch.size() + 1) * sizeof(long long), cudaMemcpyHostToDevice, d));
     for (int k : batch) AF_CUDA(cudaStreamWaitEvent(d, s->slots[k].input_ready, 0));
@@ -175,6 +186,7 @@ static int dispatch(af_stream_s* s, const std::vector<int>& batch)
     aftile::k_tile_persistent<kNW, kM><<<s->grid, (kNW + 1) * 32, s->smem, d>>>(
         s->d_jobs[r], s->d_first[r], (int)batch.size(), first[batch.size()], s->d_counter);
     AF_CUDA(cudaGetLastError());
+    }
     AF_CUDA(cudaEventRecord(s->ring_free[r], d));
     for (int k : batch) {
         Slot& sl = s->slots[k];
@@ -291,7 +303,6 @@ extern "C" int af_stream_open(af_stream_t* out, const af_stream_cfg_t* cfg)
     s->timeout_ms = cfg->timeout_ms;
     if (s->hop < 1 || s->hop > INT32_MAX) rc = af_set_error(AF_EINVAL, "af_stream_open: window must exceed Dmax %d", p->dmax);
     if (!rc) rc = af_check_widths(p, cfg->widths, cfg->nw, s->hop, &s->widths);
-    if (!rc && !p->tile.fits) rc = af_set_error(AF_EINVAL, "af_stream_open: DM grid too coarse for the tile kernel");
     if (rc) {
         free_stream(s);
         return rc;
@@ -300,14 +311,31 @@ extern "C" int af_stream_open(af_stream_t* out, const af_stream_cfg_t* cfg)
                               (size_t)s->ndm * sizeof(af_rowstats_t) + (size_t)s->cap * sizeof(af_cand_t) + 64;
     const size_t beam_bytes = (size_t)s->nchan * (size_t)std::max<int64_t>(s->dmax, 1);
     size_t budget = cfg->hbm_budget;
+    // the pair-row buffer, where the plan uses pair rows and the budget holds it with one slot
+    size_t rows = 0;
+    if (p->pairs.ok && !p->force_tile && !p->force_simple) {
+        rows = af_pairs_reserved_bytes(p, s->hop);
+        if (budget && budget < beam_bytes * s->nbeams + slot_bytes + rows) rows = 0;
+    }
+    if (!rows && !p->tile.fits) {
+        free_stream(s);
+        return af_set_error(AF_EINVAL, "af_stream_open: DM grid too coarse for the tile kernel");
+    }
     int nslots = cfg->max_slots > 0 ? cfg->max_slots : 4;
     if (budget) {
-        if (budget < beam_bytes * s->nbeams + slot_bytes) {
+        if (budget < beam_bytes * s->nbeams + slot_bytes + rows) {
             free_stream(s);
             return af_set_error(AF_ENOBUFS, "af_stream_open: budget %zu below one slot (%zu) + beam state (%zu)",
                                 budget, slot_bytes, beam_bytes * s->nbeams);
         }
-        nslots = std::min<int64_t>(nslots, (budget - beam_bytes * s->nbeams) / slot_bytes);
+        nslots = std::min<int64_t>(nslots, (budget - beam_bytes * s->nbeams - rows) / slot_bytes);
+    }
+    if (rows) {
+        if ((rc = af_pairs_reserve(p, s->hop, false))) {
+            free_stream(s);
+            return rc;
+        }
+        s->pairs = af_dedisp_uses_pairs(p, s->hop);
     }
     s->max_batch = nslots;
     s->slots.resize(nslots);
@@ -349,7 +377,7 @@ extern "C" int af_stream_open(af_stream_t* out, const af_stream_cfg_t* cfg)
         (e = cudaMalloc(&s->d_cprob, (size_t)s->cap * sizeof(float))) == cudaSuccess &&
         (e = cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking)) == cudaSuccess)
         e = cudaStreamCreateWithFlags(&s->dstream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && !s->pairs) {
         s->smem = af_tile_smem(kNW, p->tile.rw);
         if (af_ensure_smem((const void*)aftile::k_tile_persistent<kNW, kM>, s->smem) != AF_OK)
             e = cudaErrorInvalidValue;

@@ -74,9 +74,14 @@ def _drain(s, n, keep_planes=False):
     return out
 
 
-def test_concatenated_windows_equal_one_shot():
+@pytest.mark.parametrize("kernel", ["auto", "tile"])
+def test_concatenated_windows_equal_one_shot(kernel, monkeypatch):
+    """On both dedispersion paths of the engine (pair rows, and the persistent
+    channel-tile kernel forced)."""
     from paper_2511_02328_gb300 import _lib
     from paper_2511_02328_gb300.search import Plan
+    if kernel != "auto":
+        monkeypatch.setenv("AFGB_DEDISP_KERNEL", kernel)
     x, hop = _stream_data(1)
     s = _open(1)
     h, dmax, nslots = _lib.af_stream_info(s)
