@@ -85,7 +85,12 @@ struct PairArgs {
 // ------------------------------------------------------------------ stage 1
 // Block = (pair q, ET row samples); writes every row of the pair for them.
 // pinfo[q] = {first row, rows, dlo, row length}; rows of a pair are sorted by
-// delta, so [dmn, dmx] is the pair's delta range.
+// delta, so [dmn, dmx] is the pair's delta range.  Channel 2q's window goes to
+// A, channel 2q+1's (shifted by dmn, dmx - dmn + 4 bytes longer) to B: blocks
+// whose windows lie inside the input row copy them with aligned 16-byte loads
+// (the window then starts aoff / boff bytes into A / B), edge blocks byte by
+// byte with zeros outside the row.  Words at any byte offset are read with a
+// funnel shift (one shift amount per block and row).
 __global__ void __launch_bounds__(kS1T)
 k_pair_rows(const uint8_t* __restrict__ X, int64_t nsamp, int nchan, const int4* __restrict__ pinfo,
             const int32_t* __restrict__ rdelta, const int64_t* __restrict__ rowoff, int64_t T0, int etiles,
@@ -101,36 +106,56 @@ k_pair_rows(const uint8_t* __restrict__ X, int64_t nsamp, int nchan, const int4*
     const bool single = c1 >= nchan;
     const int64_t u0 = ((T0 + pi.z) & ~(int64_t)7) + e0;
     const int dmn = __ldg(rdelta + pi.x), dmx = __ldg(rdelta + pi.x + pi.y - 1);
-    uint8_t* sa = sm;
-    uint8_t* sb = sm + kET;
     const int bw = kET + (dmx - dmn) + 4;  // + the word the last funnel shift reads past
-    const uint8_t* x0 = X + (int64_t)c0 * nsamp;
-    const uint8_t* x1 = X + (int64_t)(single ? c0 : c1) * nsamp;
-    for (int i = tid; i < kET; i += kS1T) {
-        const int64_t u = u0 + i;
-        sa[i] = (u >= 0 && u < nsamp) ? __ldg(x0 + u) : (uint8_t)0;
-    }
-    for (int i = tid; i < bw; i += kS1T) {
-        const int64_t u = u0 + dmn + i;
-        sb[i] = (!single && u >= 0 && u < nsamp) ? __ldg(x1 + u) : (uint8_t)0;
+    uint8_t* A = sm;
+    uint8_t* B = sm + kET + 48;
+    const uint8_t* x0 = X + (int64_t)c0 * nsamp + u0;
+    const uint8_t* x1 = X + (int64_t)(single ? c0 : c1) * nsamp + u0 + dmn;
+    const bool fast = !single && u0 >= 0 && u0 + kET + 48 <= nsamp && u0 + dmn >= 0 && u0 + dmn + bw + 48 <= nsamp;
+    int aoff = 0, boff = 0;
+    if (fast) {
+        aoff = (int)((uintptr_t)x0 & 15);
+        boff = (int)((uintptr_t)x1 & 15);
+        const uint4* ga = reinterpret_cast<const uint4*>(x0 - aoff);
+        const uint4* gb = reinterpret_cast<const uint4*>(x1 - boff);
+        const int na = (aoff + kET + 4 + 15) >> 4, nb = (boff + bw + 4 + 15) >> 4;
+        for (int k = tid; k < na; k += kS1T) reinterpret_cast<uint4*>(A)[k] = __ldg(ga + k);
+        for (int k = tid; k < nb; k += kS1T) reinterpret_cast<uint4*>(B)[k] = __ldg(gb + k);
+    } else {
+        for (int i = tid; i < kET + 4; i += kS1T) {
+            const int64_t u = u0 + i;
+            A[i] = (u >= 0 && u < nsamp) ? __ldg(x0 + i) : (uint8_t)0;
+        }
+        for (int i = tid; i < bw + 4; i += kS1T) {
+            const int64_t u = u0 + dmn + i;
+            B[i] = (!single && u >= 0 && u < nsamp) ? __ldg(x1 + i) : (uint8_t)0;
+        }
     }
     __syncthreads();
     const int i0 = tid * 16;
     if (e0 + i0 >= pi.w) return;  // row lengths are multiples of 16
+    const uint32_t* A32 = reinterpret_cast<const uint32_t*>(A);
+    const uint32_t* B32 = reinterpret_cast<const uint32_t*>(B);
     uint32_t alo[4], ahi[4];
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const uint32_t w = *reinterpret_cast<const uint32_t*>(sa + i0 + 4 * k);
-        alo[k] = __byte_perm(w, 0u, 0x4140);  // samples 0, 1 into 16-bit lanes
-        ahi[k] = __byte_perm(w, 0u, 0x4342);  // samples 2, 3
-    }
-    for (int k = 0; k < pi.y; k++) {
-        const int s = __ldg(rdelta + pi.x + k) - dmn + i0;
-        const int s4 = s & ~3;
-        const uint32_t sh = (uint32_t)(s & 3) * 8u;
+    {
+        const int pa = aoff + i0;
+        const uint32_t sh = (uint32_t)(pa & 3) * 8u;
         uint32_t w[5];
 #pragma unroll
-        for (int j = 0; j < 5; j++) w[j] = *reinterpret_cast<const uint32_t*>(sb + s4 + 4 * j);
+        for (int j = 0; j < 5; j++) w[j] = A32[(pa >> 2) + j];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const uint32_t a = __funnelshift_r(w[k], w[k + 1], sh);
+            alo[k] = __byte_perm(a, 0u, 0x4140);  // samples 0, 1 into 16-bit lanes
+            ahi[k] = __byte_perm(a, 0u, 0x4342);  // samples 2, 3
+        }
+    }
+    for (int k = 0; k < pi.y; k++) {
+        const int pb = boff + __ldg(rdelta + pi.x + k) - dmn + i0;
+        const uint32_t sh = (uint32_t)(pb & 3) * 8u;
+        uint32_t w[5];
+#pragma unroll
+        for (int j = 0; j < 5; j++) w[j] = B32[(pb >> 2) + j];
         uint32_t o[8];
 #pragma unroll
         for (int j = 0; j < 4; j++) {
@@ -358,7 +383,7 @@ const void* tile_kernel(int shape)
          : shape == 1 ? (const void*)k_pair_tile<kPNW, 24, 3>
                       : (const void*)k_pair_tile<kPNW, 16, 4>;
 }
-size_t rows_smem(int maxdr) { return (size_t)kET + (size_t)r16(kET + maxdr + 4); }
+size_t rows_smem(int maxdr) { return (size_t)kET + 48 + (size_t)r16(kET + maxdr + 4 + 4 + 48); }
 
 size_t pair_budget()
 {
