@@ -147,7 +147,7 @@ static int setup_pairs(af_batch_t b)
         b->rows_bytes = need;
     }
     for (Beam& x : b->beams)
-        if (x.plan->pairs.ok)
+        if (x.plan->pairs.ok)  // attaches where pair rows are expected to beat the channel kernel
             if (int rc = af_pairs_attach(x.plan, b->d_rows, b->rows_bytes, x.nout))
                 return rc == AF_ENOBUFS ? af_set_error(AF_EINVAL, "batch: shared row buffer too small") : rc;
     b->shape = kPairs;

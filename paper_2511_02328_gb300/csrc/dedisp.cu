@@ -297,7 +297,7 @@ extern "C" int af_plan_kernel(af_plan_t p, int* path, int* ring, int32_t* spread
         sp = p->sb.tile.spread;
     } else if (af_dedisp_uses_pairs(p, 1)) {
         pa = AF_PATH_PAIRS;
-        rg = p->pairs.shape == 0 ? 2 : p->pairs.shape == 1 ? 3 : 4;
+        rg = af_pair_ring_depth(p->pairs.shape);
         sp = p->pairs.tt.spread;
     } else if (p->tile.ns1 > 0 && !p->force_simple) {
         pa = AF_PATH_TILE;

@@ -83,7 +83,8 @@ struct af_pair_tables {
     size_t budget = 0;             // bytes the row buffer may take (AFGB_PAIR_BUDGET_MB at plan creation)
     int shape = 0;                 // ring shape of the row kernel (pairs.cu)
     af_tile_tables tt;             // DM order and block minima for this block shape
-    std::vector<int32_t> h_rb, h_dlo, h_dhi, h_srow, h_scpart;
+    double copy_per_tile = 0;      // bytes of row windows copied per time tile (all DM blocks)
+    std::vector<int32_t> h_rb, h_ub, h_rB, h_rspan, h_srow, h_scpart;
     int32_t* d_rdelta = nullptr;   // [nrows] delta of each row (sorted within a pair)
     int2* d_chunks = nullptr;      // per chunk: row slots, first slot
     int32_t* d_chkoff = nullptr;   // [nblk + 1]
@@ -97,7 +98,8 @@ struct af_pair_tables {
     // four blocks, so that the input copy overlaps the work).
     struct Layout {
         int64_t L = 0, maxlen = 0;     // outputs per time block, longest row
-        int4* d_pinfo = nullptr;       // [np] first row, rows, dlo, row length
+        int4* d_pinfo = nullptr;       // [np] first row, rows, range start ub, range length
+        int2* d_rinfo = nullptr;       // [nrows] row start - ub, row length
         int64_t* d_rowoff = nullptr;   // [nrows] element offset in the row buffer
         int64_t* d_soff = nullptr;     // per slot: window offset for a time block's first tile
     } lay[2];
@@ -120,6 +122,7 @@ int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64
                           af_rowstats_t* d_stats, cudaStream_t s, int layout, int64_t T0,
                           cudaEvent_t* mid = nullptr);
 int af_pair_tile_outputs();
+int af_pair_ring_depth(int shape);
 // Row-buffer bytes of a full-length single time block, and the use of a row
 // buffer owned by someone else (a batch's plans run one after another on one).
 size_t af_pairs_bytes(af_plan_t p, int64_t nout);
@@ -147,6 +150,8 @@ struct af_plan_s {
                                            // effective delays (AFGB_DEDISP_KERNEL=brute)
     bool force_tile = false;               // byte tile kernel even where pair rows apply
                                            // (AFGB_DEDISP_KERNEL=tile)
+    bool force_pairs = false;              // pair rows wherever they apply, without the cost
+                                           // comparison (AFGB_DEDISP_KERNEL=pairs)
     af_pair_tables pairs;                  // pair-row path of brute-force plans
 
     // two-stage subband dedispersion (sb_nsub > 0); `delays` then holds the

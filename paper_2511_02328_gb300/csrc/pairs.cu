@@ -45,12 +45,13 @@ namespace {
 
 constexpr int kPNW = 15;            // DM rows (consumer warps) per block
 // Ring shapes (row slots per stage, at most one per producer lane; depth):
-// 0 = 32 x 2, 1 = 24 x 3, 2 = 16 x 4 (AFGB_PAIR_SHAPE at plan creation, else
-// the first that fits the shared memory; on the 4096-channel workload 32 x 2
-// measured 28.0 ms, 16 x 4 29.5 ms).
-constexpr int kShapes = 3;
-constexpr int kShapeSL[kShapes] = {32, 24, 16};
-constexpr int kShapeNS[kShapes] = {2, 3, 4};
+// 0 = 32 x 2, 1 = 24 x 3, 2 = 16 x 4, 3 = 24 x 2, 4 = 16 x 2 (AFGB_PAIR_SHAPE
+// at plan creation, else the first that fits the shared memory; on the
+// 4096-channel workload 32 x 2 measured 28.0 ms, 16 x 4 29.5 ms; the last two
+// serve windows too wide for the others).
+constexpr int kShapes = 5;
+constexpr int kShapeSL[kShapes] = {32, 24, 16, 24, 16};
+constexpr int kShapeNS[kShapes] = {2, 3, 4, 2, 2};
 constexpr int kPMG = 16;            // 2-sample groups per lane
 constexpr int kPTTE = 1016;         // outputs per tile: a multiple of 8 below 64 * kPMG - 1
 constexpr int kPTABW = 40;          // ints per (stage, warp) table: 2 starts, 2 counts, <= 34 offsets
@@ -83,9 +84,12 @@ struct PairArgs {
 };
 
 // ------------------------------------------------------------------ stage 1
-// Block = (pair q, ET row samples); writes every row of the pair for them.
-// pinfo[q] = {first row, rows, dlo, row length}; rows of a pair are sorted by
-// delta, so [dmn, dmx] is the pair's delta range.  Channel 2q's window goes to
+// Block = (pair q, ET samples of the pair's range); writes, for every row of
+// the pair, the part of those samples inside the row's own range.
+// pinfo[q] = {first row, rows, ub (the pair's first delay rounded down to 16),
+// length of the pair's range}; rinfo[g] = {row start - ub (a multiple of 16),
+// row length}; rows of a pair are sorted by delta, so [dmn, dmx] is the pair's
+// delta range.  Channel 2q's window goes to
 // A, channel 2q+1's (shifted by dmn, dmx - dmn + 4 bytes longer) to B: blocks
 // whose windows lie inside the input row copy them with aligned 16-byte loads
 // (the window then starts aoff / boff bytes into A / B), edge blocks byte by
@@ -93,8 +97,8 @@ struct PairArgs {
 // funnel shift (one shift amount per block and row).
 __global__ void __launch_bounds__(kS1T)
 k_pair_rows(const uint8_t* __restrict__ X, int64_t nsamp, int nchan, const int4* __restrict__ pinfo,
-            const int32_t* __restrict__ rdelta, const int64_t* __restrict__ rowoff, int64_t T0, int etiles,
-            uint16_t* __restrict__ PS)
+            const int32_t* __restrict__ rdelta, const int2* __restrict__ rinfo, const int64_t* __restrict__ rowoff,
+            int64_t T0, int etiles, uint16_t* __restrict__ PS)
 {
     extern __shared__ __align__(16) uint8_t sm[];
     const int tid = threadIdx.x;
@@ -104,7 +108,7 @@ k_pair_rows(const uint8_t* __restrict__ X, int64_t nsamp, int nchan, const int4*
     if (e0 >= pi.w) return;
     const int c0 = 2 * q, c1 = 2 * q + 1;
     const bool single = c1 >= nchan;
-    const int64_t u0 = ((T0 + pi.z) & ~(int64_t)7) + e0;
+    const int64_t u0 = T0 + pi.z + e0;
     const int dmn = __ldg(rdelta + pi.x), dmx = __ldg(rdelta + pi.x + pi.y - 1);
     const int bw = kET + (dmx - dmn) + 4;  // + the word the last funnel shift reads past
     uint8_t* A = sm;
@@ -133,7 +137,7 @@ k_pair_rows(const uint8_t* __restrict__ X, int64_t nsamp, int nchan, const int4*
     }
     __syncthreads();
     const int i0 = tid * 16;
-    if (e0 + i0 >= pi.w) return;  // row lengths are multiples of 16
+    if (e0 + i0 >= pi.w) return;  // range and row lengths are multiples of 16
     const uint32_t* A32 = reinterpret_cast<const uint32_t*>(A);
     const uint32_t* B32 = reinterpret_cast<const uint32_t*>(B);
     uint32_t alo[4], ahi[4];
@@ -151,6 +155,9 @@ k_pair_rows(const uint8_t* __restrict__ X, int64_t nsamp, int nchan, const int4*
         }
     }
     for (int k = 0; k < pi.y; k++) {
+        const int2 ri = __ldg(rinfo + pi.x + k);
+        const int64_t rel = e0 + i0 - ri.x;  // sample index within the row
+        if (rel < 0 || rel >= ri.y) continue;
         const int pb = boff + __ldg(rdelta + pi.x + k) - dmn + i0;
         const uint32_t sh = (uint32_t)(pb & 3) * 8u;
         uint32_t w[5];
@@ -163,7 +170,7 @@ k_pair_rows(const uint8_t* __restrict__ X, int64_t nsamp, int nchan, const int4*
             o[2 * j] = alo[j] + __byte_perm(b, 0u, 0x4140);
             o[2 * j + 1] = ahi[j] + __byte_perm(b, 0u, 0x4342);
         }
-        uint4* dst = reinterpret_cast<uint4*>(PS + __ldg(rowoff + pi.x + k) + e0 + i0);
+        uint4* dst = reinterpret_cast<uint4*>(PS + __ldg(rowoff + pi.x + k) + rel);
         dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
         dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
     }
@@ -379,9 +386,13 @@ size_t tile_smem(int shape, int rwb)
 
 const void* tile_kernel(int shape)
 {
-    return shape == 0 ? (const void*)k_pair_tile<kPNW, 32, 2>
-         : shape == 1 ? (const void*)k_pair_tile<kPNW, 24, 3>
-                      : (const void*)k_pair_tile<kPNW, 16, 4>;
+    switch (shape) {
+    case 0: return (const void*)k_pair_tile<kPNW, 32, 2>;
+    case 1: return (const void*)k_pair_tile<kPNW, 24, 3>;
+    case 2: return (const void*)k_pair_tile<kPNW, 16, 4>;
+    case 3: return (const void*)k_pair_tile<kPNW, 24, 2>;
+    default: return (const void*)k_pair_tile<kPNW, 16, 2>;
+    }
 }
 size_t rows_smem(int maxdr) { return (size_t)kET + 48 + (size_t)r16(kET + maxdr + 4 + 4 + 48); }
 
@@ -390,12 +401,19 @@ size_t pair_budget()
     if (const char* b = getenv("AFGB_PAIR_BUDGET_MB")) return (size_t)atoll(b) << 20;
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
-    return std::min<size_t>((size_t)16 << 30, tot / 8);
+    return std::min<size_t>((size_t)48 << 30, tot / 5);
 }
+
+// Rates measured on GB300 at 2070 MHz: stage 2 moves shared-memory bytes
+// (consumer loads + row-window copies) at about 41 TB/s, stage 1 writes row
+// bytes at about 4.6 TB/s of HBM, the channel tile kernel adds about 17.7 T
+// samples/s.
+constexpr double kPairSmemBps = 41e12, kPairRowBps = 4.6e12, kTileAddps = 17.7e12;
 
 }  // namespace
 
 int af_pair_tile_outputs() { return kPTTE; }
+int af_pair_ring_depth(int shape) { return kShapeNS[shape]; }
 
 void af_pairs_free(af_pair_tables* T)
 {
@@ -407,6 +425,7 @@ void af_pairs_free(af_pair_tables* T)
     cudaFree(T->d_sbytes);
     for (auto& l : T->lay) {
         cudaFree(l.d_pinfo);
+        cudaFree(l.d_rinfo);
         cudaFree(l.d_rowoff);
         cudaFree(l.d_soff);
     }
@@ -437,26 +456,31 @@ int af_pairs_build(af_plan_t p)
     const int nblk = T->tt.nblk;
     const int np = (nchan + 1) / 2;
     const int32_t* D = p->delays.data();
-    // rows: distinct deltas of each pair over all DMs
-    std::vector<int32_t> rb(np + 1, 0), rdelta, dlo(np), dhi(np);
-    std::vector<int32_t> v(ndm);
+    // rows: distinct deltas of each pair over all DMs; row g spans the delays
+    // D[d][2q] of the DMs that use it, from B_g (its smallest, rounded down to
+    // 16) over span_g samples; the pair's range starts at ub_q = min_g B_g
+    std::vector<int32_t> rb(np + 1, 0), rdelta, rB, rspan, ub(np);
+    std::vector<std::pair<int32_t, int32_t>> v(ndm);  // (delta, D[d][2q])
     int maxdr = 0;
     for (int q = 0; q < np; q++) {
         const int c0 = 2 * q, c1 = 2 * q + 1;
-        int32_t lo = INT32_MAX, hi = INT32_MIN;
         for (int d = 0; d < ndm; d++) {
             const int32_t x = D[(size_t)d * nchan + c0];
-            lo = std::min(lo, x);
-            hi = std::max(hi, x);
-            v[d] = c1 < nchan ? D[(size_t)d * nchan + c1] - x : 0;
+            v[d] = std::make_pair(c1 < nchan ? D[(size_t)d * nchan + c1] - x : 0, x);
         }
-        dlo[q] = lo;
-        dhi[q] = hi;
         std::sort(v.begin(), v.end());
         const size_t n0 = rdelta.size();
-        for (int d = 0; d < ndm; d++)
-            if (d == 0 || v[d] != v[d - 1]) rdelta.push_back(v[d]);
+        for (int d = 0; d < ndm;) {
+            int e = d;
+            while (e < ndm && v[e].first == v[d].first) e++;
+            const int32_t B = v[d].second & ~15;  // the run is sorted by delay
+            rdelta.push_back(v[d].first);
+            rB.push_back(B);
+            rspan.push_back(v[e - 1].second - B);
+            d = e;
+        }
         rb[q + 1] = (int32_t)rdelta.size();
+        ub[q] = *std::min_element(rB.begin() + n0, rB.end());
         maxdr = std::max(maxdr, rdelta.back() - rdelta[n0]);
     }
     // window of the even channels' block spread
@@ -490,7 +514,7 @@ int af_pairs_build(af_plan_t p)
     std::vector<int2> chunks;
     std::vector<int32_t> chkoff(nblk + 1, 0), sbytes, srow, scpart;
     std::vector<int> tabs;
-    std::vector<int32_t> dq(NW), d0(NW), S;
+    std::vector<int32_t> dq(NW), d0(NW), S, sdm;
     int open_slots = 0, first_slot = 0, kloc = 0;
     auto flush = [&]() {
         if (ents.empty()) return;
@@ -520,12 +544,10 @@ int af_pairs_build(af_plan_t p)
         kloc = 0;
         for (int q = 0; q < np; q++) {
             const int c0 = 2 * q, c1 = 2 * q + 1;
-            int32_t hi = INT32_MIN;
             for (int w = 0; w < NW; w++) {
                 const int32_t* row = dsort.data() + (size_t)(j * NW + w) * nchan;
                 d0[w] = row[c0];
                 dq[w] = c1 < nchan ? row[c1] - row[c0] : 0;
-                hi = std::max(hi, row[c0]);
             }
             S.assign(dq.begin(), dq.end());
             std::sort(S.begin(), S.end());
@@ -533,18 +555,27 @@ int af_pairs_build(af_plan_t p)
             if ((int)S.size() > SL) return AF_OK;
             if (open_slots + (int)S.size() > SL) flush();
             if (ents.empty()) first_slot = (int)sbytes.size();
-            const int32_t dm = dmin[(size_t)j * nchan + c0];
-            const int bytes = (int)(2 * r8((int64_t)(hi - dm) + 1031));
-            for (int32_t dv : S) {
-                sbytes.push_back(bytes);
-                srow.push_back((int32_t)(std::lower_bound(rdelta.begin() + rb[q], rdelta.begin() + rb[q + 1], dv) -
-                                         rdelta.begin()));
-                scpart.push_back((dm & ~7) - (dlo[q] & ~7));
+            // one window per (block, row): from the smallest delay of the block's DMs on that row
+            sdm.assign(S.size(), 0);
+            for (size_t k = 0; k < S.size(); k++) {
+                int32_t lo = INT32_MAX, hi = INT32_MIN;
+                for (int w = 0; w < NW; w++)
+                    if (dq[w] == S[k]) {
+                        lo = std::min(lo, d0[w]);
+                        hi = std::max(hi, d0[w]);
+                    }
+                const int g = (int)(std::lower_bound(rdelta.begin() + rb[q], rdelta.begin() + rb[q + 1], S[k]) -
+                                    rdelta.begin());
+                sdm[k] = lo;
+                sbytes.push_back((int)(2 * r8((int64_t)(hi - lo) + 1031)));
+                srow.push_back(g);
+                scpart.push_back((lo & ~7) - rB[g]);
             }
             Ent en;
             for (int w = 0; w < NW; w++) {
-                en.slot[w] = open_slots + (int)(std::lower_bound(S.begin(), S.end(), dq[w]) - S.begin());
-                en.e[w] = d0[w] - (dm & ~7);
+                const int k = (int)(std::lower_bound(S.begin(), S.end(), dq[w]) - S.begin());
+                en.slot[w] = open_slots + k;
+                en.e[w] = d0[w] - (sdm[k] & ~7);
             }
             ents.push_back(en);
             open_slots += (int)S.size();
@@ -552,9 +583,12 @@ int af_pairs_build(af_plan_t p)
         flush();
         chkoff[j + 1] = (int32_t)chunks.size();
     }
-    // cost: row windows copied per pair against the byte kernel's two channel windows
+    // rows copied per pair and block: beyond 8 the copies alone exceed the
+    // channel kernel's loads (the reservation weighs the rest)
     const double rows_per_pair = (double)sbytes.size() / ((double)nblk * np);
-    if (rows_per_pair > 3.0) return AF_OK;
+    if (rows_per_pair > 8.0) return AF_OK;
+    double copy = 0;
+    for (int32_t b : sbytes) copy += b;
     T->np = np;
     T->nrows = (int)rdelta.size();
     T->rwe = (int)rwe;
@@ -562,9 +596,11 @@ int af_pairs_build(af_plan_t p)
     T->rows_per_pair = rows_per_pair;
     T->budget = pair_budget();
     T->shape = shape;
+    T->copy_per_tile = copy;
     T->h_rb = rb;
-    T->h_dlo = dlo;
-    T->h_dhi = dhi;
+    T->h_ub = ub;
+    T->h_rB = rB;
+    T->h_rspan = rspan;
     T->h_srow = srow;
     T->h_scpart = scpart;
     cudaError_t e;
@@ -578,6 +614,8 @@ int af_pairs_build(af_plan_t p)
         !up((void**)&T->d_tabs, tabs.data(), tabs.size() * 4) ||
         !up((void**)&T->d_sbytes, sbytes.data(), sbytes.size() * 4) ||
         (e = cudaMalloc(&T->lay[0].d_pinfo, (size_t)np * sizeof(int4))) != cudaSuccess ||
+        (e = cudaMalloc(&T->lay[0].d_rinfo, (size_t)T->nrows * sizeof(int2))) != cudaSuccess ||
+        (e = cudaMalloc(&T->lay[1].d_rinfo, (size_t)T->nrows * sizeof(int2))) != cudaSuccess ||
         (e = cudaMalloc(&T->lay[0].d_rowoff, (size_t)T->nrows * 8)) != cudaSuccess ||
         (e = cudaMalloc(&T->lay[0].d_soff, srow.size() * 8)) != cudaSuccess ||
         (e = cudaMalloc(&T->lay[1].d_pinfo, (size_t)np * sizeof(int4))) != cudaSuccess ||
@@ -590,12 +628,14 @@ int af_pairs_build(af_plan_t p)
     return AF_OK;
 }
 
-// Row lengths for time blocks of L outputs: r16(L + dhi - dlo + rwe + 8).
+// Row g's length for time blocks of L outputs: its delay span, a window and
+// slack past the block, r16(L + span_g + 1047).
+static int64_t row_len(const af_pair_tables* T, int g, int64_t L) { return r16(L + T->h_rspan[g] + 1047); }
+
 static int64_t rows_elems(const af_pair_tables* T, int64_t L)
 {
     int64_t n = 0;
-    for (int q = 0; q < T->np; q++)
-        n += (int64_t)(T->h_rb[q + 1] - T->h_rb[q]) * r16(L + T->h_dhi[q] - T->h_dlo[q] + T->rwe + 8);
+    for (int g = 0; g < T->nrows; g++) n += row_len(T, g, L);
     return n;
 }
 
@@ -638,12 +678,19 @@ static int pairs_layout(af_plan_t p, int k, int64_t L)
     }
     std::vector<int64_t> rowoff(T->nrows), soff(T->h_srow.size());
     std::vector<int4> pinfo(T->np);
+    std::vector<int2> rinfo(T->nrows);
     int64_t off = 0, maxlen = 0;
     for (int q = 0; q < T->np; q++) {
-        const int64_t len = r16(L + T->h_dhi[q] - T->h_dlo[q] + T->rwe + 8);
-        pinfo[q] = make_int4(T->h_rb[q], T->h_rb[q + 1] - T->h_rb[q], T->h_dlo[q], (int)len);
-        for (int g = T->h_rb[q]; g < T->h_rb[q + 1]; g++, off += len) rowoff[g] = off;
-        maxlen = std::max(maxlen, len);
+        int64_t end = 0;
+        for (int g = T->h_rb[q]; g < T->h_rb[q + 1]; g++) {
+            const int64_t len = row_len(T, g, L);
+            rowoff[g] = off;
+            off += len;
+            rinfo[g] = make_int2(T->h_rB[g] - T->h_ub[q], (int)len);
+            end = std::max(end, (int64_t)rinfo[g].x + len);
+        }
+        pinfo[q] = make_int4(T->h_rb[q], T->h_rb[q + 1] - T->h_rb[q], T->h_ub[q], (int)end);
+        maxlen = std::max(maxlen, end);
     }
     for (size_t i = 0; i < soff.size(); i++) soff[i] = rowoff[T->h_srow[i]] + T->h_scpart[i];
     ly.L = 0;
@@ -651,18 +698,32 @@ static int pairs_layout(af_plan_t p, int k, int64_t L)
     if ((e = cudaMemcpy(ly.d_rowoff, rowoff.data(), rowoff.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(ly.d_soff, soff.data(), soff.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(ly.d_pinfo, pinfo.data(), pinfo.size() * sizeof(int4), cudaMemcpyHostToDevice)) !=
-            cudaSuccess)
+            cudaSuccess ||
+        (e = cudaMemcpy(ly.d_rinfo, rinfo.data(), rinfo.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess)
         return af_cuda_check(e, "pair layout");
     ly.L = L;
     ly.maxlen = maxlen;
     return AF_OK;
 }
 
+// Whether pair rows in time blocks of L outputs are expected to beat the
+// channel tile kernel on nout outputs (AFGB_DEDISP_KERNEL=pairs skips the test).
+static bool pairs_pay(af_plan_t p, int64_t nout, int64_t L)
+{
+    const af_pair_tables* T = &p->pairs;
+    if (p->force_pairs || p->tile.ns1 == 0) return true;  // no tile kernel: the one-thread-per-output kernel
+    const double tiles = (double)((nout + kPTTE - 1) / kPTTE), blocks = (double)((nout + L - 1) / L);
+    const double s2 = (2.0 * T->tt.ndm_pad * T->np * (double)nout + tiles * T->copy_per_tile) / kPairSmemBps;
+    const double s1 = (blocks * 2.0 * (double)rows_elems(T, L) + (double)p->nchan * (double)(nout + p->dmax)) /
+                      kPairRowBps;
+    return s1 + s2 < (double)p->ndm * p->nchan * (double)nout / kTileAddps;
+}
+
 int af_pairs_reserve(af_plan_t p, int64_t nout, bool search)
 {
     af_pair_tables* T = &p->pairs;
     const int64_t L = af_pairs_block(p, nout);
-    if (L <= 0) return AF_OK;  // the channel tile kernel serves this plan
+    if (L <= 0 || !pairs_pay(p, nout, L)) return AF_OK;  // the channel tile kernel serves this plan
     if (L > T->lay[0].L)
         if (int rc = pairs_layout(p, 0, L)) return rc;
     if (search) {
@@ -691,6 +752,7 @@ int af_pairs_attach(af_plan_t p, uint16_t* buf, size_t bytes, int64_t nout)
 {
     af_pair_tables* T = &p->pairs;
     if (!T->ok) return af_set_error(AF_EINVAL, "pairs: plan cannot use pair rows");
+    T->lay[0].L = T->lay[1].L = 0;  // until attached: the channel tile kernel
     const int64_t tiles = (nout + kPTTE - 1) / kPTTE;
     const int64_t cap = (int64_t)(bytes / 2);
     int64_t lo = std::min<int64_t>(kMinTiles, tiles), hi = tiles;
@@ -700,12 +762,12 @@ int af_pairs_attach(af_plan_t p, uint16_t* buf, size_t bytes, int64_t nout)
         if (rows_elems(T, mid * kPTTE) <= cap) lo = mid;
         else hi = mid - 1;
     }
+    if (!pairs_pay(p, nout, lo * kPTTE)) return AF_OK;  // this beam stays on the channel tile kernel
     if (int rc = af_cuda_check(cudaDeviceSynchronize(), "pairs attach")) return rc;
     if (T->ps_owned) cudaFree(T->d_ps);
     T->d_ps = buf;
     T->ps_bytes = bytes;
     T->ps_owned = false;
-    T->lay[0].L = T->lay[1].L = 0;
     return pairs_layout(p, 0, lo * kPTTE);
 }
 
@@ -725,8 +787,8 @@ int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64
     const int64_t tiles = (std::min(L, nout - T0) + kPTTE - 1) / kPTTE;
     const unsigned long long g2 = (unsigned long long)tiles * (unsigned)T->tt.nblk;
     if (g1 > 0x7fffffffULL || g2 > 0x7fffffffULL) return af_set_error(AF_EINVAL, "pairs: problem too large for one grid");
-    k_pair_rows<<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, ly.d_pinfo, T->d_rdelta, ly.d_rowoff, T0,
-                                               etiles, T->d_ps);
+    k_pair_rows<<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, ly.d_pinfo, T->d_rdelta, ly.d_rinfo,
+                                               ly.d_rowoff, T0, etiles, T->d_ps);
     if (int rc = af_cuda_check(cudaGetLastError(), "pair rows launch")) return rc;
     if (mid) AF_CUDA(cudaEventRecord(*mid, s));
     PairArgs a;
@@ -745,12 +807,14 @@ int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64
     a.Y = d_plane;
     a.stats = d_stats;
     a.err = p->d_err;
-    if (T->shape == 0)
-        k_pair_tile<kPNW, 32, 2><<<(unsigned)g2, (kPNW + 1) * 32, s2, s>>>(a);
-    else if (T->shape == 1)
-        k_pair_tile<kPNW, 24, 3><<<(unsigned)g2, (kPNW + 1) * 32, s2, s>>>(a);
-    else
-        k_pair_tile<kPNW, 16, 4><<<(unsigned)g2, (kPNW + 1) * 32, s2, s>>>(a);
+    const dim3 grid2((unsigned)g2), blk2((kPNW + 1) * 32);
+    switch (T->shape) {
+    case 0: k_pair_tile<kPNW, 32, 2><<<grid2, blk2, s2, s>>>(a); break;
+    case 1: k_pair_tile<kPNW, 24, 3><<<grid2, blk2, s2, s>>>(a); break;
+    case 2: k_pair_tile<kPNW, 16, 4><<<grid2, blk2, s2, s>>>(a); break;
+    case 3: k_pair_tile<kPNW, 24, 2><<<grid2, blk2, s2, s>>>(a); break;
+    default: k_pair_tile<kPNW, 16, 2><<<grid2, blk2, s2, s>>>(a); break;
+    }
     return af_cuda_check(cudaGetLastError(), "pair tile launch");
 }
 

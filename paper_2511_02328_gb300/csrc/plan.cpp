@@ -175,6 +175,7 @@ static int plan_finish(af_plan_s* p, const char* who)
         p->force_simple = strcmp(k, "simple") == 0;
         p->force_brute = strcmp(k, "brute") == 0;
         p->force_tile = strcmp(k, "tile") == 0;
+        p->force_pairs = strcmp(k, "pairs") == 0;
     }
     const size_t tbytes = (size_t)p->ndm * p->nchan * sizeof(int32_t);
     int rc = AF_OK;

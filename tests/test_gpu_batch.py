@@ -80,6 +80,8 @@ def test_batch_matches_oracle_and_single_beam(strategy, monkeypatch):
     from paper_2511_02328_gb300.search import Plan
     if strategy != "auto":
         monkeypatch.setenv("AFGB_BATCH_STRATEGY", strategy)
+    if strategy == "pairs":
+        monkeypatch.setenv("AFGB_DEDISP_KERNEL", "pairs")   # every beam that can, on pair rows
     xs = _make(1)
     xs_dev = [torch.from_numpy(x).cuda() for x in xs]
     batch = _build(xs_dev)

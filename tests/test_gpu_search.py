@@ -148,11 +148,11 @@ SHAPES = [
 ]
 
 
-@pytest.mark.parametrize("kernel", ["auto", "tile"])
+@pytest.mark.parametrize("kernel", ["auto", "pairs", "tile"])
 @pytest.mark.parametrize("shape", SHAPES, ids=[str(i) for i in range(len(SHAPES))])
 def test_random_shapes_bit_exact(shape, kernel, monkeypatch):
-    """Both single-plan paths (pair rows where they apply, else the channel
-    tile kernel; and the channel tile kernel forced) give the oracle's plane."""
+    """Every single-plan path (the default choice; pair rows wherever they
+    apply; the channel tile kernel) gives the oracle's plane."""
     from paper_2511_02328_gb300.search import Plan
     if kernel != "auto":
         monkeypatch.setenv("AFGB_DEDISP_KERNEL", kernel)
@@ -249,6 +249,8 @@ def test_c2_sampled_rows():
         pulses.append(synth.Pulse(offs, 20, synth.pulse_amplitude(20.0, cfg["nchan"], 20)))
     x = synth.filterbank(cfg["nchan"], cfg["nsamp"], seed=2, pulses=pulses)
     p = _plan(cfg)
+    p.reserve(cfg["nsamp"])
+    assert p.kernel()["path"] == "pairs"        # the benchmark's path on this workload
     stats = torch.empty((p.ndm, 2), dtype=torch.int64, device="cuda")
     plane = p.dedisperse(torch.from_numpy(x).cuda(), stats=stats)
     snr, bw = p.boxcar_snr(plane, cfg["widths"], stats=stats)
@@ -318,23 +320,21 @@ def test_coarse_dm_grids_shallower_ring(step, ring, monkeypatch):
     p.close()
 
 
-def _pair_rows_bytes(D, L, nw=15):
+def _pair_rows_bytes(D, L):
     """Bytes of the pair-row buffer for time blocks of L outputs: per pair
-    q (channels 2q, 2q+1) one row per distinct delay difference, each of
-    r16(L + max - min delay of channel 2q + rwe + 8) uint16 samples, rwe =
-    r8(largest spread of channel 2q within a block of nw DMs + 1031); the
-    rows of D are in ascending DM order."""
+    q (channels 2q, 2q+1) one row per distinct delay difference
+    d = D[.][2q+1] - D[.][2q], each of r16(L + span + 1047) uint16 samples,
+    span = the largest D[.][2q] of the DMs with that difference minus their
+    smallest rounded down to 16."""
     ndm, nchan = D.shape
-    Ds = D
-    pad = -(-ndm // nw) * nw
-    Dp = np.concatenate([Ds, np.repeat(Ds[-1:], pad - ndm, 0)]).reshape(-1, nw, nchan)
-    spread = int((Dp.max(1) - Dp.min(1))[:, 0::2].max())
-    rwe = (spread + 1031 + 7) & ~7
     total = 0
     for q in range((nchan + 1) // 2):
         c0, c1 = 2 * q, 2 * q + 1
-        rows = len(np.unique(D[:, c1] - D[:, c0])) if c1 < nchan else 1
-        total += rows * ((L + int(D[:, c0].max() - D[:, c0].min()) + rwe + 8 + 15) & ~15)
+        dd = D[:, c1] - D[:, c0] if c1 < nchan else np.zeros(ndm, dtype=D.dtype)
+        for v in np.unique(dd):
+            d0 = D[dd == v, c0]
+            span = int(d0.max()) - (int(d0.min()) & ~15)
+            total += (L + span + 1047 + 15) & ~15
     return 2 * total
 
 
@@ -350,6 +350,7 @@ def test_pair_rows_several_time_blocks(nchan, f_lo, f_hi, monkeypatch):
     budget = _pair_rows_bytes(D, 9 * 1022)
     assert budget < _pair_rows_bytes(D, 31 * 1022)
     monkeypatch.setenv("AFGB_PAIR_BUDGET_MB", str(-(-budget // (1 << 20))))
+    monkeypatch.setenv("AFGB_DEDISP_KERNEL", "pairs")
     x = np.random.default_rng(nchan).integers(0, 256, (nchan, nsamp), dtype=np.uint8)
     p = Plan(nchan, f_lo, f_hi, tsamp, dms)
     assert p.kernel()["path"] == "tile"                 # nothing reserved yet
@@ -366,13 +367,24 @@ def test_pair_rows_several_time_blocks(nchan, f_lo, f_hi, monkeypatch):
     p.close()
 
 
-def test_pair_rows_is_the_default_path(c1_data):
-    """The 256-channel workload runs on pair rows once reserved."""
+def test_pair_rows_forced_and_default_choice(c1_data, monkeypatch):
+    """AFGB_DEDISP_KERNEL=pairs puts the 256-channel workload on pair rows;
+    without it the reservation keeps whichever path its cost model prefers,
+    and both give the oracle's plane."""
     x, D, Y, _, _ = c1_data
-    p = _plan(C1)
-    p.reserve(x.shape[1])
-    assert p.kernel()["path"] == "pairs"
-    p.close()
+    for k in ("pairs", None):
+        if k:
+            monkeypatch.setenv("AFGB_DEDISP_KERNEL", k)
+        else:
+            monkeypatch.delenv("AFGB_DEDISP_KERNEL", raising=False)
+        p = _plan(C1)
+        p.reserve(x.shape[1])
+        path = p.kernel()["path"]
+        assert path == "pairs" if k else path in ("pairs", "tile")
+        plane = p.dedisperse(torch.from_numpy(x).cuda())
+        torch.cuda.synchronize()
+        assert np.array_equal(plane.cpu().numpy(), Y)
+        p.close()
 
 
 def test_simple_kernel_forced_matches(c1_data, monkeypatch):

@@ -74,10 +74,10 @@ def _drain(s, n, keep_planes=False):
     return out
 
 
-@pytest.mark.parametrize("kernel", ["auto", "tile"])
+@pytest.mark.parametrize("kernel", ["auto", "pairs", "tile"])
 def test_concatenated_windows_equal_one_shot(kernel, monkeypatch):
-    """On both dedispersion paths of the engine (pair rows, and the persistent
-    channel-tile kernel forced)."""
+    """On every dedispersion path of the engine (its default choice, pair rows
+    forced, the persistent channel-tile kernel forced)."""
     from paper_2511_02328_gb300 import _lib
     from paper_2511_02328_gb300.search import Plan
     if kernel != "auto":
