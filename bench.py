@@ -206,8 +206,9 @@ SB_N0, SB_NSUB = 8, 64
 # DRAM read + write bytes of one stage-2 pair-row tile launch (k_pair_tile) on this workload, from an ncu
 # capture of the same kernel (dram__bytes_read.sum + dram__bytes_write.sum); None until captured, and reset
 # to None whenever the kernel changes
-PAIR_TILE_TRAFFIC_BYTES = None
-PAIR_TILE_TRAFFIC_BASIS = None
+PAIR_TILE_TRAFFIC_BYTES = 2.76e10
+PAIR_TILE_TRAFFIC_BASIS = ("ncu dram__bytes read+write of k_pair_tile<15,32,2> at 2^16 samples (2.47 GB, 19 output "
+                           "tiles), scaled by the output tiles to this 2^18-sample launch (212 tiles)")
 
 
 def match_pulses(cands, pulses, dms):
