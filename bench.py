@@ -206,9 +206,9 @@ SB_N0, SB_NSUB = 8, 64
 # DRAM read + write bytes of one stage-2 pair-row tile launch (k_pair_tile) on this workload, from an ncu
 # capture of the same kernel (dram__bytes_read.sum + dram__bytes_write.sum); None until captured, and reset
 # to None whenever the kernel changes
-PAIR_TILE_TRAFFIC_BYTES = 2.76e10
-PAIR_TILE_TRAFFIC_BASIS = ("ncu dram__bytes read+write of k_pair_tile<15,32,2> at 2^16 samples (2.47 GB, 19 output "
-                           "tiles), scaled by the output tiles to this 2^18-sample launch (212 tiles)")
+PAIR_TILE_TRAFFIC = {2: (2.76e10, "ncu dram__bytes read+write of k_pair_tile<15,32,2> on pair rows at 2^16 samples "
+                             "(2.47 GB, 19 output tiles), scaled by the output tiles to this 2^18-sample launch "
+                             "(212 tiles)")}   # keyed by channels per row
 
 
 def match_pulses(cands, pulses, dms):
@@ -553,7 +553,8 @@ def run_paper_sec3(args, dev, stream):
         _lib.af_plan_check(bp.handle)
         _lib.af_plan_check(sb.handle)
         kb = bp.kernel()
-        out = {"nchan": nchan, "ndm": ndm, "nout": nout, "brute_kernel": f'{kb["path"]}/ring {kb["ring"]}',
+        out = {"nchan": nchan, "ndm": ndm, "nout": nout,
+               "brute_kernel": f'{kb["path"]}/ring {kb["ring"]}/group {kb["group"]}',
                "brute_ms": ms_b, "brute_R": span_s / (ms_b * 1e-3),
                "brute_rate": float(ndm) * nchan * nout / (ms_b * 1e-3), "subband_ms": ms_s,
                "subband_R": nout_s * tsamp / (ms_s * 1e-3)}
@@ -848,21 +849,24 @@ def main():
     alg_bytes = NCHAN * NSAMP + plan.ndm * nout * 4
     hbm_ach = alg_bytes / (ms_dedisp * 1e-3) / 1e9
     if stage is not None:
-        # stage 2: every (DM, channel pair, output) is one 2-byte shared load and one 16-bit lane add
-        npairs = (NCHAN + 1) // 2
-        lds_bytes = 2.0 * plan.ndm * npairs * nout
+        # stage 2: every (DM, channel group, output) is one 2-byte shared load and one 16-bit lane add
+        G = kern["group"]
+        ngroups = (NCHAN + G - 1) // G
+        lds_bytes = 2.0 * plan.ndm * ngroups * nout
+        traffic, traffic_basis = PAIR_TILE_TRAFFIC.get(G, (None, None))
         s2_ach = lds_bytes / (stage["tiles_ms"] * 1e-3) / 1e12
         s1_bytes = stage["row_bytes"] + NCHAN * NSAMP
         s1_ach = s1_bytes / (stage["rows_ms"] * 1e-3) / 1e9
         roofline = {
-            "bound": "smem", "kernel": "k_pair_tile<15,32,2> (stage 2 of the pair-row dedispersion)",
+            "bound": "smem", "kernel": "k_pair_tile<15,32,2> (stage 2 of the group-row dedispersion, %d channels "
+                                       "per row)" % G,
             "achieved": s2_ach, "peak": smem_peak, "unit": "TB/s", "frac": s2_ach / smem_peak,
-            "traffic": PAIR_TILE_TRAFFIC_BYTES, "traffic_basis": PAIR_TILE_TRAFFIC_BASIS,
-            "work": "2 B shared load per (DM, channel pair, output): %.3g B per launch" % lds_bytes,
+            "traffic": traffic, "traffic_basis": traffic_basis,
+            "work": "2 B shared load per (DM, channel group, output): %.3g B per launch" % lds_bytes,
             "ms": stage["tiles_ms"],
             "peak_basis": "%d SMs x 128 B shared-load bandwidth per clock x %.0f MHz (derived, of max clock)"
                           % (nsm, sm_max),
-            "stage1": {"kernel": "k_pair_rows", "bound": "hbm", "ms": stage["rows_ms"], "achieved": s1_ach,
+            "stage1": {"kernel": "k_group_rows<%d>" % G, "bound": "hbm", "ms": stage["rows_ms"], "achieved": s1_ach,
                        "peak": hbm_peak, "unit": "GB/s", "frac": s1_ach / hbm_peak, "basis": "of measured",
                        "work": "row writes %.3g B + input read %.3g B" % (stage["row_bytes"], NCHAN * NSAMP)},
             "dedispersion": {"ms": ms_dedisp, "adds_per_s": achieved * 1e12,

@@ -118,23 +118,26 @@ int af_plan_info(af_plan_t plan, int* nchan, int* ndm, int32_t* dmax, double* ts
  *  path    AF_PATH_SIMPLE (one thread per output, every delay read from the
  *          table), AF_PATH_TILE (the shared-memory tile kernel over channels),
  *          AF_PATH_SUBBAND (the two stages of Sec. 2.3) or AF_PATH_PAIRS (the
- *          same exact sum over channel-pair rows: adjacent channels added
- *          once per distinct relative delay, then the tile kernel over pair
- *          rows; reported once af_dedisperse_reserve or af_search_reserve
- *          has reserved the row buffer);
+ *          same exact sum over channel-group rows: the channels of a group
+ *          (2 or 4 adjacent channels) added once per distinct tuple of
+ *          relative delays, then a tile kernel over group rows; reported once
+ *          af_dedisperse_reserve or af_search_reserve has reserved the row
+ *          buffer);
  *  ring    depth of the kernel's shared-memory ring (4; 3 or 2 when a coarse
- *          DM grid widens each channel's window; 2 to 4 for pair rows), 0 on
+ *          DM grid widens each channel's window; 2 to 4 for group rows), 0 on
  *          the simple path;
  *  spread  largest delay difference between DMs of one block of the kernel,
- *          in samples (what sets the window width).
- * AFGB_DEDISP_KERNEL=tile|simple in the environment at plan creation forces
- * the channel tile kernel or the simple kernel.
- * Read-only; no device work.  Not a step of the paper's method. */
+ *          in samples (what sets the window width);
+ *  group   channels per row: 2 or 4 on the group-row path, else 1.
+ * AFGB_DEDISP_KERNEL=tile|simple|pairs in the environment at plan creation
+ * forces the channel tile kernel, the simple kernel, or group rows wherever
+ * they apply (without the cost comparison); AFGB_PAIR_GROUP=2|4 fixes the
+ * group size.  Read-only; no device work.  Not a step of the paper's method. */
 #define AF_PATH_SIMPLE 0
 #define AF_PATH_TILE 1
 #define AF_PATH_SUBBAND 2
 #define AF_PATH_PAIRS 3
-int af_plan_kernel(af_plan_t plan, int* path, int* ring, int32_t* spread);
+int af_plan_kernel(af_plan_t plan, int* path, int* ring, int32_t* spread, int* group);
 
 /* Reads and clears the plan's device error flag, which a kernel of this plan
  * sets when one of its bounded waits (for an asynchronous copy) ran out and it
@@ -238,13 +241,15 @@ int af_plan_subband_info(af_plan_t plan, int* n0, int* nsub, int* ncoarse, int32
  * Enqueued on `stream`.  Brute-force plans run the pair-row kernels once
  * af_dedisperse_reserve (or af_search_reserve) has reserved their row buffer,
  * else the channel tile kernel; both give the same plane. */
-/* Reserves the pair-row buffer of a brute-force plan (af_plan_kernel path
- * AF_PATH_PAIRS) for inputs of up to max_nsamp samples: the time-block length
- * is the longest whose rows (uint16, one per channel pair and distinct delay
- * difference D[d][2q+1] - D[d][2q], each block length + the pair's delay range
- * long) fit the row budget (AFGB_PAIR_BUDGET_MB at plan creation, default
- * min(16 GiB, 1/8 of device memory)); later calls of any length run in as many
- * time blocks as they need.  Allocates and uploads synchronously (waits for the
+/* Reserves the group-row buffer of a brute-force plan (af_plan_kernel path
+ * AF_PATH_PAIRS) for inputs of up to max_nsamp samples, if a cost model
+ * (rates measured on GB300) predicts group rows faster than the channel tile
+ * kernel; of channel pairs and channel quads it takes the faster.  The
+ * time-block length is the longest whose rows (uint16, one per group and
+ * distinct tuple of relative delays, each the block length + the delay span of
+ * its DMs long) fit the row budget (AFGB_PAIR_BUDGET_MB at plan creation,
+ * default min(48 GiB, 1/5 of device memory)); later calls of any length run in
+ * as many time blocks as they need.  Allocates and uploads synchronously (waits for the
  * device when it replaces a reservation); AF_OK without effect for plans that
  * cannot use pair rows.  AF_EINVAL if max_nsamp <= Dmax, AF_ENOMEM / AF_ECUDA
  * on allocation failure.  Not a step of the paper's method: the same sum,

@@ -67,7 +67,7 @@ SIGNATURES = {
     "af_plan_info": [_P, _P, _P, _P, _P],
     "af_plan_nout": [_P, _I64, _P],
     "af_plan_check": [_P],
-    "af_plan_kernel": [_P, _P, _P, _P],
+    "af_plan_kernel": [_P, _P, _P, _P, _P],
     "af_dedisperse_reserve": [_P, _I64],
     "af_dedisperse_timing": [_P, _I],
     "af_dedisperse_times": [_P, _I, _P, _P, _P],
@@ -240,11 +240,11 @@ PATH_SIMPLE, PATH_TILE, PATH_SUBBAND, PATH_PAIRS = 0, 1, 2, 3
 
 
 def af_plan_kernel(plan):
-    """(path, ring, spread) of the kernel that dedisperses this plan."""
-    path, ring, spread = _I(), _I(), _I32()
-    _check(lib().af_plan_kernel(plan, ctypes.byref(path), ctypes.byref(ring), ctypes.byref(spread)),
-           "af_plan_kernel")
-    return path.value, ring.value, spread.value
+    """(path, ring, spread, group) of the kernel that dedisperses this plan."""
+    path, ring, spread, group = _I(), _I(), _I32(), _I()
+    _check(lib().af_plan_kernel(plan, ctypes.byref(path), ctypes.byref(ring), ctypes.byref(spread),
+                                ctypes.byref(group)), "af_plan_kernel")
+    return path.value, ring.value, spread.value, group.value
 
 
 def af_dedisperse_reserve(plan, max_nsamp):

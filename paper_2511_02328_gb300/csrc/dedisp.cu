@@ -287,10 +287,10 @@ int af_launch_dedisperse(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_
     return AF_OK;
 }
 
-extern "C" int af_plan_kernel(af_plan_t p, int* path, int* ring, int32_t* spread)
+extern "C" int af_plan_kernel(af_plan_t p, int* path, int* ring, int32_t* spread, int* group)
 {
     if (int rc = af_check_plan(p)) return rc;
-    int pa = AF_PATH_SIMPLE, rg = 0, sp = p->tile.spread;
+    int pa = AF_PATH_SIMPLE, rg = 0, sp = p->tile.spread, gr = 1;
     if (p->sb_nsub > 0 && p->sb.tile.fits && !p->force_simple && !p->force_brute) {
         pa = AF_PATH_SUBBAND;
         rg = aftile::NSTAGE;
@@ -299,6 +299,7 @@ extern "C" int af_plan_kernel(af_plan_t p, int* path, int* ring, int32_t* spread
         pa = AF_PATH_PAIRS;
         rg = af_pair_ring_depth(p->pairs.shape);
         sp = p->pairs.tt.spread;
+        gr = p->pairs.G;
     } else if (p->tile.ns1 > 0 && !p->force_simple) {
         pa = AF_PATH_TILE;
         rg = p->tile.ns1;
@@ -306,6 +307,7 @@ extern "C" int af_plan_kernel(af_plan_t p, int* path, int* ring, int32_t* spread
     if (path) *path = pa;
     if (ring) *ring = rg;
     if (spread) *spread = sp;
+    if (group) *group = gr;
     return AF_OK;
 }
 

@@ -77,15 +77,17 @@ struct af_sb_device {
 // Single-plan dedispersion through channel-pair rows (pairs.cu): host tables
 // (built once per plan), device tables, and the row buffer of one time block.
 struct af_pair_tables {
-    bool ok = false;               // the plan uses this path
-    int np = 0, nrows = 0, rwe = 0, maxdr = 0;
+    bool ok = false;               // the plan can use this path
+    int G = 2;                     // channels per group (2: pairs, 4: quads)
+    int np = 0, nrows = 0, rwe = 0, maxdr = 0;   // np = groups
     double rows_per_pair = 0;      // rows copied per pair and DM block (mean)
     size_t budget = 0;             // bytes the row buffer may take (AFGB_PAIR_BUDGET_MB at plan creation)
     int shape = 0;                 // ring shape of the row kernel (pairs.cu)
     af_tile_tables tt;             // DM order and block minima for this block shape
     double copy_per_tile = 0;      // bytes of row windows copied per time tile (all DM blocks)
     std::vector<int32_t> h_rb, h_ub, h_rB, h_rspan, h_srow, h_scpart;
-    int32_t* d_rdelta = nullptr;   // [nrows] delta of each row (sorted within a pair)
+    int32_t* d_rdelta = nullptr;   // [nrows][G-1] relative delays of each row
+    int2* d_gdr = nullptr;         // [groups][G-1] smallest and largest relative delay
     int2* d_chunks = nullptr;      // per chunk: row slots, first slot
     int32_t* d_chkoff = nullptr;   // [nblk + 1]
     int* d_tabs = nullptr;         // per chunk: every consumer warp's table
@@ -113,7 +115,7 @@ struct af_pair_tables {
 int af_pairs_build(af_plan_t p);
 void af_pairs_free(af_pair_tables* T);
 int64_t af_pairs_block(af_plan_t p, int64_t nout);
-int af_pairs_reserve(af_plan_t p, int64_t nout, bool search);
+int af_pairs_reserve(af_plan_t p, int64_t nout, bool search, bool allow_quads = true);
 int af_launch_pairs(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,
                     af_rowstats_t* d_stats, cudaStream_t s);
 // Stage 1 + stage 2 of the time block starting at T0 (a multiple of the
@@ -150,9 +152,11 @@ struct af_plan_s {
                                            // effective delays (AFGB_DEDISP_KERNEL=brute)
     bool force_tile = false;               // byte tile kernel even where pair rows apply
                                            // (AFGB_DEDISP_KERNEL=tile)
-    bool force_pairs = false;              // pair rows wherever they apply, without the cost
+    bool force_pairs = false;              // group rows wherever they apply, without the cost
                                            // comparison (AFGB_DEDISP_KERNEL=pairs)
-    af_pair_tables pairs;                  // pair-row path of brute-force plans
+    int force_group = 0;                   // 2 or 4: only that group size (AFGB_PAIR_GROUP)
+    af_pair_tables pairs;                  // group-row path of brute-force plans (the one in use)
+    af_pair_tables quads;                  // the other group size, until a reservation picks
 
     // two-stage subband dedispersion (sb_nsub > 0); `delays` then holds the
     // effective table D[j(m)][c] + R[m][s(c)]

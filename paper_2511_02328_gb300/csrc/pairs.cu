@@ -36,6 +36,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <array>
 #include <vector>
 
 #include "internal.h"
@@ -55,7 +56,6 @@ constexpr int kShapeNS[kShapes] = {2, 3, 4, 2, 2};
 constexpr int kPMG = 16;            // 2-sample groups per lane
 constexpr int kPTTE = 1016;         // outputs per tile: a multiple of 8 below 64 * kPMG - 1
 constexpr int kPTABW = 40;          // ints per (stage, warp) table: 2 starts, 2 counts, <= 34 offsets
-constexpr int kPFlush = 128;        // pairs per fold: 128 * 510 < 2^16
 constexpr uint32_t kPWait = 1u << 24;
 constexpr int kET = 4096;           // stage 1: row samples per block
 constexpr int kS1T = 256;
@@ -74,6 +74,7 @@ struct PairArgs {
     const int64_t* soff;     // per slot: element offset of its window in PS for the block's first tile
     const int32_t* perm;     // [ndm_pad] plane row, -1 = padding
     int rwb;
+    int flush;               // rows between folds: flush * 255 * G < 2^16
     unsigned nblk;
     int64_t T0;              // first output of the time block (a multiple of 8)
     int64_t tend;            // outputs t < tend are written
@@ -84,65 +85,82 @@ struct PairArgs {
 };
 
 // ------------------------------------------------------------------ stage 1
-// Block = (pair q, ET samples of the pair's range); writes, for every row of
-// the pair, the part of those samples inside the row's own range.
-// pinfo[q] = {first row, rows, ub (the pair's first delay rounded down to 16),
-// length of the pair's range}; rinfo[g] = {row start - ub (a multiple of 16),
-// row length}; rows of a pair are sorted by delta, so [dmn, dmx] is the pair's
-// delta range.  Channel 2q's window goes to
-// A, channel 2q+1's (shifted by dmn, dmx - dmn + 4 bytes longer) to B: blocks
-// whose windows lie inside the input row copy them with aligned 16-byte loads
-// (the window then starts aoff / boff bytes into A / B), edge blocks byte by
-// byte with zeros outside the row.  Words at any byte offset are read with a
-// funnel shift (one shift amount per block and row).
+// Block = (group q of G channels, ET samples of the group's range); writes,
+// for every row of the group, the part of those samples inside the row's own
+// range.  pinfo[q] = {first row, rows, ub (the group's first delay rounded down
+// to 16), length of the group's range}; rinfo[g] = {row start - ub (a multiple
+// of 16), row length}; rdelta[g][i-1] = row g's delay of channel Gq+i relative
+// to channel Gq; gdr[q][i-1] = the smallest and largest of those over the
+// group's rows.  Channel Gq's window goes to W0, channel Gq+i's (shifted by
+// the smallest delta, longer by the delta range + 4 bytes) to Wi: blocks whose
+// windows lie inside the input rows copy them with aligned 16-byte loads (a
+// window then starts off_i bytes into its buffer), edge blocks byte by byte
+// with zeros outside the rows and for missing channels.  Words at any byte
+// offset are read with a funnel shift (one shift per block and row).
+template <int G>
 __global__ void __launch_bounds__(kS1T)
-k_pair_rows(const uint8_t* __restrict__ X, int64_t nsamp, int nchan, const int4* __restrict__ pinfo,
-            const int32_t* __restrict__ rdelta, const int2* __restrict__ rinfo, const int64_t* __restrict__ rowoff,
-            int64_t T0, int etiles, uint16_t* __restrict__ PS)
+k_group_rows(const uint8_t* __restrict__ X, int64_t nsamp, int nchan, const int4* __restrict__ pinfo,
+             const int2* __restrict__ gdr, const int32_t* __restrict__ rdelta, const int2* __restrict__ rinfo,
+             const int64_t* __restrict__ rowoff, int64_t T0, int etiles, int wstride, uint16_t* __restrict__ PS)
 {
+    constexpr int K = G - 1;
     extern __shared__ __align__(16) uint8_t sm[];
     const int tid = threadIdx.x;
     const int q = blockIdx.x / etiles;
     const int64_t e0 = (int64_t)(blockIdx.x % etiles) * kET;
     const int4 pi = __ldg(pinfo + q);
     if (e0 >= pi.w) return;
-    const int c0 = 2 * q, c1 = 2 * q + 1;
-    const bool single = c1 >= nchan;
+    const int c0 = G * q;
     const int64_t u0 = T0 + pi.z + e0;
-    const int dmn = __ldg(rdelta + pi.x), dmx = __ldg(rdelta + pi.x + pi.y - 1);
-    const int bw = kET + (dmx - dmn) + 4;  // + the word the last funnel shift reads past
-    uint8_t* A = sm;
-    uint8_t* B = sm + kET + 48;
+    int dmn[K], bw[K], off[K + 1];
+    bool fast = u0 >= 0 && u0 + kET + 48 <= nsamp;
+#pragma unroll
+    for (int i = 0; i < K; i++) {
+        const int2 r = __ldg(gdr + (int64_t)q * K + i);
+        dmn[i] = r.x;
+        bw[i] = kET + (r.y - r.x) + 4;  // + the word the last funnel shift reads past
+        fast = fast && c0 + 1 + i < nchan && u0 + r.x >= 0 && u0 + r.x + bw[i] + 48 <= nsamp;
+    }
     const uint8_t* x0 = X + (int64_t)c0 * nsamp + u0;
-    const uint8_t* x1 = X + (int64_t)(single ? c0 : c1) * nsamp + u0 + dmn;
-    const bool fast = !single && u0 >= 0 && u0 + kET + 48 <= nsamp && u0 + dmn >= 0 && u0 + dmn + bw + 48 <= nsamp;
-    int aoff = 0, boff = 0;
     if (fast) {
-        aoff = (int)((uintptr_t)x0 & 15);
-        boff = (int)((uintptr_t)x1 & 15);
-        const uint4* ga = reinterpret_cast<const uint4*>(x0 - aoff);
-        const uint4* gb = reinterpret_cast<const uint4*>(x1 - boff);
-        const int na = (aoff + kET + 4 + 15) >> 4, nb = (boff + bw + 4 + 15) >> 4;
-        for (int k = tid; k < na; k += kS1T) reinterpret_cast<uint4*>(A)[k] = __ldg(ga + k);
-        for (int k = tid; k < nb; k += kS1T) reinterpret_cast<uint4*>(B)[k] = __ldg(gb + k);
-    } else {
-        for (int i = tid; i < kET + 4; i += kS1T) {
-            const int64_t u = u0 + i;
-            A[i] = (u >= 0 && u < nsamp) ? __ldg(x0 + i) : (uint8_t)0;
+        off[0] = (int)((uintptr_t)x0 & 15);
+        const uint4* g0 = reinterpret_cast<const uint4*>(x0 - off[0]);
+        const int n0 = (off[0] + kET + 4 + 15) >> 4;
+        for (int k = tid; k < n0; k += kS1T) reinterpret_cast<uint4*>(sm)[k] = __ldg(g0 + k);
+#pragma unroll
+        for (int i = 0; i < K; i++) {
+            const uint8_t* xi = X + (int64_t)(c0 + 1 + i) * nsamp + u0 + dmn[i];
+            off[i + 1] = (int)((uintptr_t)xi & 15);
+            const uint4* gi = reinterpret_cast<const uint4*>(xi - off[i + 1]);
+            uint4* wi = reinterpret_cast<uint4*>(sm + kET + 48 + i * wstride);
+            const int ni = (off[i + 1] + bw[i] + 4 + 15) >> 4;
+            for (int k = tid; k < ni; k += kS1T) wi[k] = __ldg(gi + k);
         }
-        for (int i = tid; i < bw + 4; i += kS1T) {
-            const int64_t u = u0 + dmn + i;
-            B[i] = (!single && u >= 0 && u < nsamp) ? __ldg(x1 + i) : (uint8_t)0;
+    } else {
+        off[0] = 0;
+        for (int k = tid; k < kET + 4; k += kS1T) {
+            const int64_t u = u0 + k;
+            sm[k] = (u >= 0 && u < nsamp) ? __ldg(x0 + k) : (uint8_t)0;
+        }
+#pragma unroll
+        for (int i = 0; i < K; i++) {
+            off[i + 1] = 0;
+            const bool have = c0 + 1 + i < nchan;
+            const uint8_t* xi = X + (int64_t)(have ? c0 + 1 + i : c0) * nsamp + u0 + dmn[i];
+            uint8_t* wi = sm + kET + 48 + i * wstride;
+            for (int k = tid; k < bw[i] + 4; k += kS1T) {
+                const int64_t u = u0 + dmn[i] + k;
+                wi[k] = (have && u >= 0 && u < nsamp) ? __ldg(xi + k) : (uint8_t)0;
+            }
         }
     }
     __syncthreads();
     const int i0 = tid * 16;
     if (e0 + i0 >= pi.w) return;  // range and row lengths are multiples of 16
-    const uint32_t* A32 = reinterpret_cast<const uint32_t*>(A);
-    const uint32_t* B32 = reinterpret_cast<const uint32_t*>(B);
     uint32_t alo[4], ahi[4];
     {
-        const int pa = aoff + i0;
+        const uint32_t* A32 = reinterpret_cast<const uint32_t*>(sm);
+        const int pa = off[0] + i0;
         const uint32_t sh = (uint32_t)(pa & 3) * 8u;
         uint32_t w[5];
 #pragma unroll
@@ -158,17 +176,26 @@ k_pair_rows(const uint8_t* __restrict__ X, int64_t nsamp, int nchan, const int4*
         const int2 ri = __ldg(rinfo + pi.x + k);
         const int64_t rel = e0 + i0 - ri.x;  // sample index within the row
         if (rel < 0 || rel >= ri.y) continue;
-        const int pb = boff + __ldg(rdelta + pi.x + k) - dmn + i0;
-        const uint32_t sh = (uint32_t)(pb & 3) * 8u;
-        uint32_t w[5];
-#pragma unroll
-        for (int j = 0; j < 5; j++) w[j] = B32[(pb >> 2) + j];
         uint32_t o[8];
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            const uint32_t b = __funnelshift_r(w[j], w[j + 1], sh);
-            o[2 * j] = alo[j] + __byte_perm(b, 0u, 0x4140);
-            o[2 * j + 1] = ahi[j] + __byte_perm(b, 0u, 0x4342);
+            o[2 * j] = alo[j];
+            o[2 * j + 1] = ahi[j];
+        }
+#pragma unroll
+        for (int i = 0; i < K; i++) {
+            const uint32_t* W32 = reinterpret_cast<const uint32_t*>(sm + kET + 48 + i * wstride);
+            const int pb = off[i + 1] + __ldg(rdelta + (int64_t)(pi.x + k) * K + i) - dmn[i] + i0;
+            const uint32_t sh = (uint32_t)(pb & 3) * 8u;
+            uint32_t w[5];
+#pragma unroll
+            for (int j = 0; j < 5; j++) w[j] = W32[(pb >> 2) + j];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint32_t b = __funnelshift_r(w[j], w[j + 1], sh);
+                o[2 * j] += __byte_perm(b, 0u, 0x4140);
+                o[2 * j + 1] += __byte_perm(b, 0u, 0x4342);
+            }
         }
         uint4* dst = reinterpret_cast<uint4*>(PS + __ldg(rowoff + pi.x + k) + rel);
         dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
@@ -299,7 +326,7 @@ struct PairTile {
             const int* tb = tab + (st * NW + warp) * kPTABW;
             const int4 h = *reinterpret_cast<const int4*>(tb);  // starts 0, 1; counts 0, 1
             const int npc = h.z + h.w;
-            if (npacc + npc > kPFlush) {
+            if (npacc + npc > a.flush) {
                 fold(A, Wd, lane);
                 npacc = 0;
             }
@@ -394,7 +421,8 @@ const void* tile_kernel(int shape)
     default: return (const void*)k_pair_tile<kPNW, 16, 2>;
     }
 }
-size_t rows_smem(int maxdr) { return (size_t)kET + 48 + (size_t)r16(kET + maxdr + 4 + 4 + 48); }
+int rows_wstride(int maxdr) { return (int)r16(kET + maxdr + 4 + 4 + 48); }
+size_t rows_smem(int maxdr, int G) { return (size_t)kET + 48 + (size_t)(G - 1) * rows_wstride(maxdr); }
 
 size_t pair_budget()
 {
@@ -404,11 +432,14 @@ size_t pair_budget()
     return std::min<size_t>((size_t)48 << 30, tot / 5);
 }
 
-// Rates measured on GB300 at 2070 MHz: stage 2 moves shared-memory bytes
-// (consumer loads + row-window copies) at about 41 TB/s, stage 1 writes row
-// bytes at about 4.6 TB/s of HBM, the channel tile kernel adds about 17.7 T
-// samples/s.
-constexpr double kPairSmemBps = 41e12, kPairRowBps = 4.6e12, kTileAddps = 17.7e12;
+// Rates measured on GB300 at 2070 MHz (4096-channel workload, 1001 DMs):
+// stage 2 moves shared-memory bytes (consumer loads + row-window copies) at
+// about 41 TB/s on pair rows and 29 TB/s on quad rows (smaller chunks, twice
+// the folds); stage 1 writes row bytes at about 5.0 TB/s of HBM for pairs and
+// 3.4 TB/s for quads; the channel tile kernel adds about 17.7 T samples/s.
+constexpr double kTileAddps = 17.7e12;
+inline double smem_rate(int G) { return G == 4 ? 29e12 : 41e12; }
+inline double row_rate(int G) { return G == 4 ? 3.4e12 : 5.0e12; }
 
 }  // namespace
 
@@ -419,6 +450,7 @@ void af_pairs_free(af_pair_tables* T)
 {
     af_tile_tables_free(&T->tt);
     cudaFree(T->d_rdelta);
+    cudaFree(T->d_gdr);
     cudaFree(T->d_chunks);
     cudaFree(T->d_chkoff);
     cudaFree(T->d_tabs);
@@ -434,59 +466,82 @@ void af_pairs_free(af_pair_tables* T)
     *T = af_pair_tables();
 }
 
-// Host tables (once per plan).  Leaves T->ok false, and returns AF_OK, when
-// the plan is not suited: a block whose pair needs more than a stage of rows,
-// a pair whose delta range exceeds the stage-1 window, more rows per pair and
-// block than the byte kernel's cost, or windows that do not fit.
+// Host tables of channel groups of G (2 or 4) channels (once per plan).
+// Leaves T->ok false, and returns AF_OK, when the plan is not suited: a block
+// whose group needs more than a stage of rows, a delta range beyond the
+// stage-1 window, more than 8 rows per group and block, or windows that fit
+// no ring shape.
+//
+// Group q holds channels G q .. G q + G - 1 (fewer in the last group); a row
+// is one tuple of delays relative to the group's first channel,
+// (D[d][Gq+i] - D[d][Gq])_{i=1..G-1} (0 for a missing channel), and holds the
+// sum over the group's channels at those shifts.  Row g spans the delays
+// D[d][Gq] of the DMs with its tuple, from B_g (the smallest, rounded down to
+// 16) over span_g samples; the group's range starts at ub_q = min_g B_g.
 //
 // With tiles and time blocks starting at multiples of 8, a consumer's sample
-// offset inside its row window, e = D[d][2q] - (block minimum & ~7), does not
+// offset inside its row window, e = D[d][Gq] - (window start & ~7), does not
 // depend on the tile, so every warp's bucketed table of (slot, offset) per
 // chunk is computed here once; a window starts (t0 - T0) after its position
 // for the time block's first tile.
-int af_pairs_build(af_plan_t p)
+typedef std::array<int32_t, 3> Key;
+
+static int build_groups(af_plan_t p, int G, af_pair_tables* T)
 {
-    af_pair_tables* T = &p->pairs;
     af_pairs_free(T);
-    const int nchan = p->nchan, ndm = p->ndm, NW = kPNW;
+    const int nchan = p->nchan, ndm = p->ndm, NW = kPNW, K = G - 1;
     std::vector<int32_t> dsort, dmin;
     if (int rc = af_tile_tables_build(p->delays.data(), p->dms.data(), ndm, nchan, NW, 8, p->device, &T->tt, &dsort,
                                       &dmin))
         return rc;
     const int nblk = T->tt.nblk;
-    const int np = (nchan + 1) / 2;
+    const int ng = (nchan + G - 1) / G;
     const int32_t* D = p->delays.data();
-    // rows: distinct deltas of each pair over all DMs; row g spans the delays
-    // D[d][2q] of the DMs that use it, from B_g (its smallest, rounded down to
-    // 16) over span_g samples; the pair's range starts at ub_q = min_g B_g
-    std::vector<int32_t> rb(np + 1, 0), rdelta, rB, rspan, ub(np);
-    std::vector<std::pair<int32_t, int32_t>> v(ndm);  // (delta, D[d][2q])
+    auto key_of = [&](const int32_t* row, int c0) {
+        Key k = {0, 0, 0};
+        for (int i = 1; i < G; i++)
+            if (c0 + i < nchan) k[i - 1] = row[c0 + i] - row[c0];
+        return k;
+    };
+    std::vector<int32_t> rb(ng + 1, 0), rdelta, rB, rspan, ub(ng);
+    std::vector<Key> rkey;
+    std::vector<int2> gdr((size_t)ng * K);
+    std::vector<std::pair<Key, int32_t>> v(ndm);  // (tuple, D[d][Gq])
     int maxdr = 0;
-    for (int q = 0; q < np; q++) {
-        const int c0 = 2 * q, c1 = 2 * q + 1;
+    for (int q = 0; q < ng; q++) {
+        const int c0 = G * q;
         for (int d = 0; d < ndm; d++) {
-            const int32_t x = D[(size_t)d * nchan + c0];
-            v[d] = std::make_pair(c1 < nchan ? D[(size_t)d * nchan + c1] - x : 0, x);
+            const int32_t* row = D + (size_t)d * nchan;
+            v[d] = std::make_pair(key_of(row, c0), row[c0]);
         }
         std::sort(v.begin(), v.end());
-        const size_t n0 = rdelta.size();
+        const size_t n0 = rB.size();
         for (int d = 0; d < ndm;) {
             int e = d;
             while (e < ndm && v[e].first == v[d].first) e++;
             const int32_t B = v[d].second & ~15;  // the run is sorted by delay
-            rdelta.push_back(v[d].first);
+            rkey.push_back(v[d].first);
+            for (int i = 0; i < K; i++) rdelta.push_back(v[d].first[i]);
             rB.push_back(B);
             rspan.push_back(v[e - 1].second - B);
             d = e;
         }
-        rb[q + 1] = (int32_t)rdelta.size();
+        rb[q + 1] = (int32_t)rB.size();
         ub[q] = *std::min_element(rB.begin() + n0, rB.end());
-        maxdr = std::max(maxdr, rdelta.back() - rdelta[n0]);
+        for (int i = 0; i < K; i++) {
+            int32_t lo = INT32_MAX, hi = INT32_MIN;
+            for (size_t g = n0; g < rB.size(); g++) {
+                lo = std::min(lo, rkey[g][i]);
+                hi = std::max(hi, rkey[g][i]);
+            }
+            gdr[(size_t)q * K + i] = make_int2(lo, hi);
+            maxdr = std::max(maxdr, hi - lo);
+        }
     }
-    // window of the even channels' block spread
+    // window of the groups' first channels' block spread
     int spread = 0;
     for (int j = 0; j < nblk; j++)
-        for (int c = 0; c < nchan; c += 2) {
+        for (int c = 0; c < nchan; c += G) {
             int32_t hi = INT32_MIN;
             for (int w = 0; w < NW; w++) hi = std::max(hi, dsort[(size_t)(j * NW + w) * nchan + c]);
             spread = std::max(spread, hi - dmin[(size_t)j * nchan + c]);
@@ -505,7 +560,7 @@ int af_pairs_build(af_plan_t p)
     }
     if (shape < 0) return AF_OK;
     const int SL = kShapeSL[shape], NS = kShapeNS[shape];
-    // chunks of whole pairs, at most SL rows each, per block; their tables
+    // chunks of whole groups, at most SL rows each, per block; their tables
     struct Ent {
         int slot[kPNW];
         int e[kPNW];
@@ -514,7 +569,8 @@ int af_pairs_build(af_plan_t p)
     std::vector<int2> chunks;
     std::vector<int32_t> chkoff(nblk + 1, 0), sbytes, srow, scpart;
     std::vector<int> tabs;
-    std::vector<int32_t> dq(NW), d0(NW), S, sdm;
+    std::vector<Key> dq(NW), S;
+    std::vector<int32_t> d0(NW), sdm;
     int open_slots = 0, first_slot = 0, kloc = 0;
     auto flush = [&]() {
         if (ents.empty()) return;
@@ -542,12 +598,12 @@ int af_pairs_build(af_plan_t p)
     };
     for (int j = 0; j < nblk; j++) {
         kloc = 0;
-        for (int q = 0; q < np; q++) {
-            const int c0 = 2 * q, c1 = 2 * q + 1;
+        for (int q = 0; q < ng; q++) {
+            const int c0 = G * q;
             for (int w = 0; w < NW; w++) {
                 const int32_t* row = dsort.data() + (size_t)(j * NW + w) * nchan;
                 d0[w] = row[c0];
-                dq[w] = c1 < nchan ? row[c1] - row[c0] : 0;
+                dq[w] = key_of(row, c0);
             }
             S.assign(dq.begin(), dq.end());
             std::sort(S.begin(), S.end());
@@ -564,8 +620,8 @@ int af_pairs_build(af_plan_t p)
                         lo = std::min(lo, d0[w]);
                         hi = std::max(hi, d0[w]);
                     }
-                const int g = (int)(std::lower_bound(rdelta.begin() + rb[q], rdelta.begin() + rb[q + 1], S[k]) -
-                                    rdelta.begin());
+                const int g = (int)(std::lower_bound(rkey.begin() + rb[q], rkey.begin() + rb[q + 1], S[k]) -
+                                    rkey.begin());
                 sdm[k] = lo;
                 sbytes.push_back((int)(2 * r8((int64_t)(hi - lo) + 1031)));
                 srow.push_back(g);
@@ -583,17 +639,18 @@ int af_pairs_build(af_plan_t p)
         flush();
         chkoff[j + 1] = (int32_t)chunks.size();
     }
-    // rows copied per pair and block: beyond 8 the copies alone exceed the
-    // channel kernel's loads (the reservation weighs the rest)
-    const double rows_per_pair = (double)sbytes.size() / ((double)nblk * np);
-    if (rows_per_pair > 8.0) return AF_OK;
+    // rows copied per group and block: beyond 8 the copies alone outweigh the
+    // loads they save (the reservation weighs the rest)
+    const double rows_per_group = (double)sbytes.size() / ((double)nblk * ng);
+    if (rows_per_group > 8.0) return AF_OK;
     double copy = 0;
     for (int32_t b : sbytes) copy += b;
-    T->np = np;
-    T->nrows = (int)rdelta.size();
+    T->G = G;
+    T->np = ng;
+    T->nrows = (int)rB.size();
     T->rwe = (int)rwe;
     T->maxdr = maxdr;
-    T->rows_per_pair = rows_per_pair;
+    T->rows_per_pair = rows_per_group;
     T->budget = pair_budget();
     T->shape = shape;
     T->copy_per_tile = copy;
@@ -609,22 +666,32 @@ int af_pairs_build(af_plan_t p)
         return (e = cudaMemcpy(*d, h, n, cudaMemcpyHostToDevice)) == cudaSuccess;
     };
     if (!up((void**)&T->d_rdelta, rdelta.data(), rdelta.size() * 4) ||
+        !up((void**)&T->d_gdr, gdr.data(), gdr.size() * sizeof(int2)) ||
         !up((void**)&T->d_chunks, chunks.data(), chunks.size() * sizeof(int2)) ||
         !up((void**)&T->d_chkoff, chkoff.data(), chkoff.size() * 4) ||
         !up((void**)&T->d_tabs, tabs.data(), tabs.size() * 4) ||
-        !up((void**)&T->d_sbytes, sbytes.data(), sbytes.size() * 4) ||
-        (e = cudaMalloc(&T->lay[0].d_pinfo, (size_t)np * sizeof(int4))) != cudaSuccess ||
-        (e = cudaMalloc(&T->lay[0].d_rinfo, (size_t)T->nrows * sizeof(int2))) != cudaSuccess ||
-        (e = cudaMalloc(&T->lay[1].d_rinfo, (size_t)T->nrows * sizeof(int2))) != cudaSuccess ||
-        (e = cudaMalloc(&T->lay[0].d_rowoff, (size_t)T->nrows * 8)) != cudaSuccess ||
-        (e = cudaMalloc(&T->lay[0].d_soff, srow.size() * 8)) != cudaSuccess ||
-        (e = cudaMalloc(&T->lay[1].d_pinfo, (size_t)np * sizeof(int4))) != cudaSuccess ||
-        (e = cudaMalloc(&T->lay[1].d_rowoff, (size_t)T->nrows * 8)) != cudaSuccess ||
-        (e = cudaMalloc(&T->lay[1].d_soff, srow.size() * 8)) != cudaSuccess) {
+        !up((void**)&T->d_sbytes, sbytes.data(), sbytes.size() * 4)) {
         af_pairs_free(T);
-        return af_cuda_check(e, "pair tables");
+        return af_cuda_check(e, "group tables");
     }
+    for (auto& l : T->lay)
+        if ((e = cudaMalloc(&l.d_pinfo, (size_t)ng * sizeof(int4))) != cudaSuccess ||
+            (e = cudaMalloc(&l.d_rinfo, (size_t)T->nrows * sizeof(int2))) != cudaSuccess ||
+            (e = cudaMalloc(&l.d_rowoff, (size_t)T->nrows * 8)) != cudaSuccess ||
+            (e = cudaMalloc(&l.d_soff, srow.size() * 8)) != cudaSuccess) {
+            af_pairs_free(T);
+            return af_cuda_check(e, "group tables");
+        }
     T->ok = true;
+    return AF_OK;
+}
+
+// Channel pairs and channel quads, both kept until a reservation picks one.
+int af_pairs_build(af_plan_t p)
+{
+    if (int rc = build_groups(p, 2, &p->pairs)) return rc;
+    if (p->nchan >= 8)
+        if (int rc = build_groups(p, 4, &p->quads)) return rc;
     return AF_OK;
 }
 
@@ -640,9 +707,8 @@ static int64_t rows_elems(const af_pair_tables* T, int64_t L)
 }
 
 // Time block length for nout outputs within the budget (0: pairs not usable).
-int64_t af_pairs_block(af_plan_t p, int64_t nout)
+static int64_t block_len(const af_pair_tables* T, int64_t nout)
 {
-    const af_pair_tables* T = &p->pairs;
     if (!T->ok || nout <= 0) return 0;
     const int64_t tiles = (nout + kPTTE - 1) / kPTTE;
     const int64_t cap = (int64_t)(T->budget / 2);
@@ -656,6 +722,8 @@ int64_t af_pairs_block(af_plan_t p, int64_t nout)
     }
     return lo * kPTTE;
 }
+
+int64_t af_pairs_block(af_plan_t p, int64_t nout) { return block_len(&p->pairs, nout); }
 
 // Layout k (0: af_dedisperse, 1: af_search) of the row buffer for time
 // blocks of L outputs; waits for the device first when it replaces a layout
@@ -706,26 +774,61 @@ static int pairs_layout(af_plan_t p, int k, int64_t L)
     return AF_OK;
 }
 
-// Whether pair rows in time blocks of L outputs are expected to beat the
-// channel tile kernel on nout outputs (AFGB_DEDISP_KERNEL=pairs skips the test).
-static bool pairs_pay(af_plan_t p, int64_t nout, int64_t L)
+// Predicted time (s) of group rows T in time blocks of L outputs on nout outputs.
+static double rows_cost(af_plan_t p, const af_pair_tables* T, int64_t nout, int64_t L)
 {
-    const af_pair_tables* T = &p->pairs;
-    if (p->force_pairs || p->tile.ns1 == 0) return true;  // no tile kernel: the one-thread-per-output kernel
     const double tiles = (double)((nout + kPTTE - 1) / kPTTE), blocks = (double)((nout + L - 1) / L);
-    const double s2 = (2.0 * T->tt.ndm_pad * T->np * (double)nout + tiles * T->copy_per_tile) / kPairSmemBps;
+    const double s2 = (2.0 * T->tt.ndm_pad * T->np * (double)nout + tiles * T->copy_per_tile) / smem_rate(T->G);
     const double s1 = (blocks * 2.0 * (double)rows_elems(T, L) + (double)p->nchan * (double)(nout + p->dmax)) /
-                      kPairRowBps;
-    return s1 + s2 < (double)p->ndm * p->nchan * (double)nout / kTileAddps;
+                      row_rate(T->G);
+    return s1 + s2;
 }
 
-int af_pairs_reserve(af_plan_t p, int64_t nout, bool search)
+// Gives up a table set's row buffer and layouts (after the device is idle).
+static int pairs_release(af_pair_tables* T)
 {
+    if (!T->d_ps && !T->lay[0].L && !T->lay[1].L) return AF_OK;
+    if (int rc = af_cuda_check(cudaDeviceSynchronize(), "group rows release")) return rc;
+    if (T->ps_owned) cudaFree(T->d_ps);
+    T->d_ps = nullptr;
+    T->ps_bytes = 0;
+    T->ps_owned = true;
+    T->lay[0].L = T->lay[1].L = 0;
+    return AF_OK;
+}
+
+// Reserves the group rows for nout outputs: of pairs and quads (quads only
+// if allowed, AFGB_PAIR_GROUP=2|4 restricts), the one predicted fastest, if
+// it beats the channel tile kernel (AFGB_DEDISP_KERNEL=pairs skips that
+// comparison); it becomes p->pairs.  Otherwise nothing is reserved.
+int af_pairs_reserve(af_plan_t p, int64_t nout, bool search, bool allow_quads)
+{
+    af_pair_tables* cand[2] = {&p->pairs, &p->quads};
+    int best = -1;
+    double best_t = 0;
+    int64_t best_L = 0;
+    for (int k = 0; k < 2; k++) {
+        const af_pair_tables* T = cand[k];
+        if (!T->ok || (T->G == 4 && !allow_quads) || (p->force_group && T->G != p->force_group)) continue;
+        const int64_t L = block_len(T, nout);
+        if (L <= 0) continue;
+        const double t = rows_cost(p, T, nout, L);
+        if (best < 0 || t < best_t) {
+            best = k;
+            best_t = t;
+            best_L = L;
+        }
+    }
+    if (best < 0) return AF_OK;
+    const bool tile = p->tile.ns1 > 0;  // else the one-thread-per-output kernel
+    if (!p->force_pairs && tile && best_t >= (double)p->ndm * p->nchan * (double)nout / kTileAddps) return AF_OK;
+    if (best == 1) {
+        if (int rc = pairs_release(&p->pairs)) return rc;
+        std::swap(p->pairs, p->quads);
+    }
     af_pair_tables* T = &p->pairs;
-    const int64_t L = af_pairs_block(p, nout);
-    if (L <= 0 || !pairs_pay(p, nout, L)) return AF_OK;  // the channel tile kernel serves this plan
-    if (L > T->lay[0].L)
-        if (int rc = pairs_layout(p, 0, L)) return rc;
+    if (best_L > T->lay[0].L)
+        if (int rc = pairs_layout(p, 0, best_L)) return rc;
     if (search) {
         // at least four time blocks, so that the input copy overlaps the work
         const int64_t tiles = (nout + kPTTE - 1) / kPTTE;
@@ -762,7 +865,9 @@ int af_pairs_attach(af_plan_t p, uint16_t* buf, size_t bytes, int64_t nout)
         if (rows_elems(T, mid * kPTTE) <= cap) lo = mid;
         else hi = mid - 1;
     }
-    if (!pairs_pay(p, nout, lo * kPTTE)) return AF_OK;  // this beam stays on the channel tile kernel
+    if (!p->force_pairs && p->tile.ns1 > 0 &&
+        rows_cost(p, T, nout, lo * kPTTE) >= (double)p->ndm * p->nchan * (double)nout / kTileAddps)
+        return AF_OK;  // this beam stays on the channel tile kernel
     if (int rc = af_cuda_check(cudaDeviceSynchronize(), "pairs attach")) return rc;
     if (T->ps_owned) cudaFree(T->d_ps);
     T->d_ps = buf;
@@ -779,16 +884,23 @@ int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64
     const int64_t L = ly.L;
     if (L <= 0 || L % kPTTE || T0 % L) return af_set_error(AF_EINVAL, "pairs: time block not laid out");
     const int rwb = 2 * T->rwe;
-    const size_t s2 = tile_smem(T->shape, rwb), s1 = rows_smem(T->maxdr);
+    const size_t s2 = tile_smem(T->shape, rwb), s1 = rows_smem(T->maxdr, T->G);
+    const void* k1 = T->G == 4 ? (const void*)k_group_rows<4> : (const void*)k_group_rows<2>;
     if (int rc = af_ensure_smem(tile_kernel(T->shape), s2)) return rc;
-    if (int rc = af_ensure_smem((const void*)k_pair_rows, s1)) return rc;
+    if (int rc = af_ensure_smem(k1, s1)) return rc;
     const int etiles = (int)((ly.maxlen + kET - 1) / kET);
     const unsigned long long g1 = (unsigned long long)T->np * etiles;
     const int64_t tiles = (std::min(L, nout - T0) + kPTTE - 1) / kPTTE;
     const unsigned long long g2 = (unsigned long long)tiles * (unsigned)T->tt.nblk;
     if (g1 > 0x7fffffffULL || g2 > 0x7fffffffULL) return af_set_error(AF_EINVAL, "pairs: problem too large for one grid");
-    k_pair_rows<<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, ly.d_pinfo, T->d_rdelta, ly.d_rinfo,
-                                               ly.d_rowoff, T0, etiles, T->d_ps);
+    if (T->G == 4)
+        k_group_rows<4><<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, ly.d_pinfo, T->d_gdr, T->d_rdelta,
+                                                      ly.d_rinfo, ly.d_rowoff, T0, etiles, rows_wstride(T->maxdr),
+                                                      T->d_ps);
+    else
+        k_group_rows<2><<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, ly.d_pinfo, T->d_gdr, T->d_rdelta,
+                                                      ly.d_rinfo, ly.d_rowoff, T0, etiles, rows_wstride(T->maxdr),
+                                                      T->d_ps);
     if (int rc = af_cuda_check(cudaGetLastError(), "pair rows launch")) return rc;
     if (mid) AF_CUDA(cudaEventRecord(*mid, s));
     PairArgs a;
@@ -800,6 +912,7 @@ int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64
     a.soff = ly.d_soff;
     a.perm = T->tt.d_perm;
     a.rwb = rwb;
+    a.flush = 65535 / (255 * T->G);
     a.nblk = (unsigned)T->tt.nblk;
     a.T0 = T0;
     a.tend = std::min(nout, T0 + L);

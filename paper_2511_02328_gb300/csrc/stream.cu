@@ -331,7 +331,7 @@ extern "C" int af_stream_open(af_stream_t* out, const af_stream_cfg_t* cfg)
         nslots = std::min<int64_t>(nslots, (budget - beam_bytes * s->nbeams - rows) / slot_bytes);
     }
     if (rows) {
-        if ((rc = af_pairs_reserve(p, s->hop, false))) {
+        if ((rc = af_pairs_reserve(p, s->hop, false, false))) {
             free_stream(s);
             return rc;
         }

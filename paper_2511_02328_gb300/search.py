@@ -49,9 +49,9 @@ class Plan:
         return _lib.af_plan_subband_info(self.handle)
 
     def kernel(self):
-        """dict(path='simple'|'tile'|'subband'|'pairs', ring, spread) of the dedispersion kernel."""
-        path, ring, spread = _lib.af_plan_kernel(self.handle)
-        return dict(path=("simple", "tile", "subband", "pairs")[path], ring=ring, spread=spread)
+        """dict(path='simple'|'tile'|'subband'|'pairs', ring, spread, group) of the dedispersion kernel."""
+        path, ring, spread, group = _lib.af_plan_kernel(self.handle)
+        return dict(path=("simple", "tile", "subband", "pairs")[path], ring=ring, spread=spread, group=group)
 
     def close(self):
         if self.handle:

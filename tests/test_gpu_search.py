@@ -148,13 +148,17 @@ SHAPES = [
 ]
 
 
-@pytest.mark.parametrize("kernel", ["auto", "pairs", "tile"])
+@pytest.mark.parametrize("kernel", ["auto", "pairs", "quads", "tile"])
 @pytest.mark.parametrize("shape", SHAPES, ids=[str(i) for i in range(len(SHAPES))])
 def test_random_shapes_bit_exact(shape, kernel, monkeypatch):
-    """Every single-plan path (the default choice; pair rows wherever they
-    apply; the channel tile kernel) gives the oracle's plane."""
+    """Every single-plan path (the default choice; rows of channel pairs or of
+    channel quads wherever they apply; the channel tile kernel) gives the
+    oracle's plane."""
     from paper_2511_02328_gb300.search import Plan
-    if kernel != "auto":
+    if kernel in ("pairs", "quads"):
+        monkeypatch.setenv("AFGB_DEDISP_KERNEL", "pairs")
+        monkeypatch.setenv("AFGB_PAIR_GROUP", "2" if kernel == "pairs" else "4")
+    elif kernel != "auto":
         monkeypatch.setenv("AFGB_DEDISP_KERNEL", kernel)
     nchan, f_lo, f_hi, tsamp, nsamp, dms = shape
     rng = np.random.default_rng(nchan * 7 + nsamp)
@@ -320,42 +324,45 @@ def test_coarse_dm_grids_shallower_ring(step, ring, monkeypatch):
     p.close()
 
 
-def _pair_rows_bytes(D, L):
-    """Bytes of the pair-row buffer for time blocks of L outputs: per pair
-    q (channels 2q, 2q+1) one row per distinct delay difference
-    d = D[.][2q+1] - D[.][2q], each of r16(L + span + 1047) uint16 samples,
-    span = the largest D[.][2q] of the DMs with that difference minus their
-    smallest rounded down to 16."""
+def _pair_rows_bytes(D, L, G=2):
+    """Bytes of the group-row buffer for time blocks of L outputs: per group
+    q (channels Gq .. Gq+G-1) one row per distinct tuple of delays relative
+    to channel Gq (0 for a missing channel), each of r16(L + span + 1047)
+    uint16 samples, span = the largest D[.][Gq] of the DMs with that tuple
+    minus their smallest rounded down to 16."""
     ndm, nchan = D.shape
     total = 0
-    for q in range((nchan + 1) // 2):
-        c0, c1 = 2 * q, 2 * q + 1
-        dd = D[:, c1] - D[:, c0] if c1 < nchan else np.zeros(ndm, dtype=D.dtype)
-        for v in np.unique(dd):
-            d0 = D[dd == v, c0]
+    for q in range((nchan + G - 1) // G):
+        c0 = G * q
+        rel = np.stack([D[:, c0 + i] - D[:, c0] if c0 + i < nchan else np.zeros(ndm, dtype=D.dtype)
+                        for i in range(1, G)], axis=1)
+        for v in np.unique(rel, axis=0):
+            d0 = D[np.all(rel == v, axis=1), c0]
             span = int(d0.max()) - (int(d0.min()) & ~15)
             total += (L + span + 1047 + 15) & ~15
     return 2 * total
 
 
+@pytest.mark.parametrize("G", [2, 4])
 @pytest.mark.parametrize("nchan,f_lo,f_hi", [(256, 1000.0, 1500.0), (255, 1500.0, 1000.0)])
-def test_pair_rows_several_time_blocks(nchan, f_lo, f_hi, monkeypatch):
-    """The pair-row path with a row budget that holds 9 tiles of outputs: the
-    plane (several time blocks, a ragged last one) and its row sums are the
-    oracle's; odd channel counts end with a single-channel row."""
+def test_pair_rows_several_time_blocks(nchan, f_lo, f_hi, G, monkeypatch):
+    """The group-row path (pairs, quads) with a row budget that holds 9 tiles
+    of outputs: the plane (several time blocks, a ragged last one) and its row
+    sums are the oracle's; 255 channels end with a short group."""
     from paper_2511_02328_gb300.search import Plan
     tsamp, dms = 98.304e-6, np.arange(0.0, 301.0, 1.0)
     D = oracle.delay_table(nchan, f_lo, f_hi, tsamp, dms)
-    nsamp = int(D.max()) + 30 * 1022 + 311
-    budget = _pair_rows_bytes(D, 9 * 1022)
-    assert budget < _pair_rows_bytes(D, 31 * 1022)
+    nsamp = int(D.max()) + 30 * 1016 + 311
+    budget = _pair_rows_bytes(D, 9 * 1016, G)
+    assert budget < _pair_rows_bytes(D, 31 * 1016, G)
     monkeypatch.setenv("AFGB_PAIR_BUDGET_MB", str(-(-budget // (1 << 20))))
     monkeypatch.setenv("AFGB_DEDISP_KERNEL", "pairs")
+    monkeypatch.setenv("AFGB_PAIR_GROUP", str(G))
     x = np.random.default_rng(nchan).integers(0, 256, (nchan, nsamp), dtype=np.uint8)
     p = Plan(nchan, f_lo, f_hi, tsamp, dms)
     assert p.kernel()["path"] == "tile"                 # nothing reserved yet
     p.reserve(nsamp)
-    assert p.kernel()["path"] == "pairs"
+    assert (p.kernel()["path"], p.kernel()["group"]) == ("pairs", G)
     stats = torch.empty((p.ndm, 2), dtype=torch.int64, device="cuda")
     plane = p.dedisperse(torch.from_numpy(x).cuda(), stats=stats)
     torch.cuda.synchronize()
@@ -393,7 +400,8 @@ def test_simple_kernel_forced_matches(c1_data, monkeypatch):
     x, D, Y, _, _ = c1_data
     monkeypatch.setenv("AFGB_DEDISP_KERNEL", "simple")
     p = _plan(C1)
-    assert p.kernel() == dict(path="simple", ring=0, spread=p.kernel()["spread"])
+    k = p.kernel()
+    assert (k["path"], k["ring"], k["group"]) == ("simple", 0, 1)
     stats = torch.empty((p.ndm, 2), dtype=torch.int64, device="cuda")
     plane = p.dedisperse(torch.from_numpy(x).cuda(), stats=stats)
     torch.cuda.synchronize()
