@@ -119,7 +119,7 @@ int af_plan_info(af_plan_t plan, int* nchan, int* ndm, int32_t* dmax, double* ts
  *          table), AF_PATH_TILE (the shared-memory tile kernel over channels),
  *          AF_PATH_SUBBAND (the two stages of Sec. 2.3) or AF_PATH_PAIRS (the
  *          same exact sum over channel-group rows: the channels of a group
- *          (2 or 4 adjacent channels) added once per distinct tuple of
+ *          (2, 3 or 4 adjacent channels) added once per distinct tuple of
  *          relative delays, then a tile kernel over group rows; reported once
  *          af_dedisperse_reserve or af_search_reserve has reserved the row
  *          buffer);
@@ -128,10 +128,10 @@ int af_plan_info(af_plan_t plan, int* nchan, int* ndm, int32_t* dmax, double* ts
  *          the simple path;
  *  spread  largest delay difference between DMs of one block of the kernel,
  *          in samples (what sets the window width);
- *  group   channels per row: 2 or 4 on the group-row path, else 1.
+ *  group   channels per row: 2, 3 or 4 on the group-row path, else 1.
  * AFGB_DEDISP_KERNEL=tile|simple|pairs in the environment at plan creation
  * forces the channel tile kernel, the simple kernel, or group rows wherever
- * they apply (without the cost comparison); AFGB_PAIR_GROUP=2|4 fixes the
+ * they apply (without the cost comparison); AFGB_PAIR_GROUP=2|3|4 fixes the
  * group size.  Read-only; no device work.  Not a step of the paper's method. */
 #define AF_PATH_SIMPLE 0
 #define AF_PATH_TILE 1
@@ -244,7 +244,7 @@ int af_plan_subband_info(af_plan_t plan, int* n0, int* nsub, int* ncoarse, int32
 /* Reserves the group-row buffer of a brute-force plan (af_plan_kernel path
  * AF_PATH_PAIRS) for inputs of up to max_nsamp samples, if a cost model
  * (rates measured on GB300) predicts group rows faster than the channel tile
- * kernel; of channel pairs and channel quads it takes the faster.  The
+ * kernel; of groups of 2, 3 and 4 channels it takes the fastest.  The
  * time-block length is the longest whose rows (uint16, one per group and
  * distinct tuple of relative delays, each the block length + the delay span of
  * its DMs long) fit the row budget (AFGB_PAIR_BUDGET_MB at plan creation,

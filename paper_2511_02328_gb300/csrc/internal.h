@@ -78,7 +78,7 @@ struct af_sb_device {
 // (built once per plan), device tables, and the row buffer of one time block.
 struct af_pair_tables {
     bool ok = false;               // the plan can use this path
-    int G = 2;                     // channels per group (2: pairs, 4: quads)
+    int G = 2;                     // channels per group (2, 3 or 4)
     int np = 0, nrows = 0, rwe = 0, maxdr = 0;   // np = groups
     double rows_per_pair = 0;      // rows copied per pair and DM block (mean)
     size_t budget = 0;             // bytes the row buffer may take (AFGB_PAIR_BUDGET_MB at plan creation)
@@ -115,7 +115,7 @@ struct af_pair_tables {
 int af_pairs_build(af_plan_t p);
 void af_pairs_free(af_pair_tables* T);
 int64_t af_pairs_block(af_plan_t p, int64_t nout);
-int af_pairs_reserve(af_plan_t p, int64_t nout, bool search, bool allow_quads = true);
+int af_pairs_reserve(af_plan_t p, int64_t nout, bool search, bool allow_larger = true);
 int af_launch_pairs(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,
                     af_rowstats_t* d_stats, cudaStream_t s);
 // Stage 1 + stage 2 of the time block starting at T0 (a multiple of the
@@ -154,9 +154,9 @@ struct af_plan_s {
                                            // (AFGB_DEDISP_KERNEL=tile)
     bool force_pairs = false;              // group rows wherever they apply, without the cost
                                            // comparison (AFGB_DEDISP_KERNEL=pairs)
-    int force_group = 0;                   // 2 or 4: only that group size (AFGB_PAIR_GROUP)
+    int force_group = 0;                   // 2, 3 or 4: only that group size (AFGB_PAIR_GROUP)
     af_pair_tables pairs;                  // group-row path of brute-force plans (the one in use)
-    af_pair_tables quads;                  // the other group size, until a reservation picks
+    af_pair_tables alt[2];                 // the other group sizes (3, 4), until a reservation picks
 
     // two-stage subband dedispersion (sb_nsub > 0); `delays` then holds the
     // effective table D[j(m)][c] + R[m][s(c)]

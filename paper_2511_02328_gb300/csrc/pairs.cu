@@ -438,8 +438,8 @@ size_t pair_budget()
 // the folds); stage 1 writes row bytes at about 5.0 TB/s of HBM for pairs and
 // 3.4 TB/s for quads; the channel tile kernel adds about 17.7 T samples/s.
 constexpr double kTileAddps = 17.7e12;
-inline double smem_rate(int G) { return G == 4 ? 29e12 : 41e12; }
-inline double row_rate(int G) { return G == 4 ? 3.4e12 : 5.0e12; }
+inline double smem_rate(int G) { return G == 4 ? 29e12 : G == 3 ? 35e12 : 41e12; }
+inline double row_rate(int G) { return G == 4 ? 3.4e12 : G == 3 ? 4.4e12 : 5.0e12; }
 
 }  // namespace
 
@@ -686,12 +686,14 @@ static int build_groups(af_plan_t p, int G, af_pair_tables* T)
     return AF_OK;
 }
 
-// Channel pairs and channel quads, both kept until a reservation picks one.
+// Groups of 2, 3 and 4 channels, all kept until a reservation picks one.
 int af_pairs_build(af_plan_t p)
 {
     if (int rc = build_groups(p, 2, &p->pairs)) return rc;
-    if (p->nchan >= 8)
-        if (int rc = build_groups(p, 4, &p->quads)) return rc;
+    if (p->nchan >= 8) {
+        if (int rc = build_groups(p, 3, &p->alt[0])) return rc;
+        if (int rc = build_groups(p, 4, &p->alt[1])) return rc;
+    }
     return AF_OK;
 }
 
@@ -797,19 +799,20 @@ static int pairs_release(af_pair_tables* T)
     return AF_OK;
 }
 
-// Reserves the group rows for nout outputs: of pairs and quads (quads only
-// if allowed, AFGB_PAIR_GROUP=2|4 restricts), the one predicted fastest, if
-// it beats the channel tile kernel (AFGB_DEDISP_KERNEL=pairs skips that
-// comparison); it becomes p->pairs.  Otherwise nothing is reserved.
-int af_pairs_reserve(af_plan_t p, int64_t nout, bool search, bool allow_quads)
+// Reserves the group rows for nout outputs: of the group sizes (2 only
+// unless larger groups are allowed; AFGB_PAIR_GROUP=2|3|4 restricts), the one
+// predicted fastest, if it beats the channel tile kernel
+// (AFGB_DEDISP_KERNEL=pairs skips that comparison); it becomes p->pairs.
+// Otherwise nothing is reserved.
+int af_pairs_reserve(af_plan_t p, int64_t nout, bool search, bool allow_larger)
 {
-    af_pair_tables* cand[2] = {&p->pairs, &p->quads};
+    af_pair_tables* cand[3] = {&p->pairs, &p->alt[0], &p->alt[1]};
     int best = -1;
     double best_t = 0;
     int64_t best_L = 0;
-    for (int k = 0; k < 2; k++) {
+    for (int k = 0; k < 3; k++) {
         const af_pair_tables* T = cand[k];
-        if (!T->ok || (T->G == 4 && !allow_quads) || (p->force_group && T->G != p->force_group)) continue;
+        if (!T->ok || (T->G != 2 && !allow_larger) || (p->force_group && T->G != p->force_group)) continue;
         const int64_t L = block_len(T, nout);
         if (L <= 0) continue;
         const double t = rows_cost(p, T, nout, L);
@@ -822,9 +825,9 @@ int af_pairs_reserve(af_plan_t p, int64_t nout, bool search, bool allow_quads)
     if (best < 0) return AF_OK;
     const bool tile = p->tile.ns1 > 0;  // else the one-thread-per-output kernel
     if (!p->force_pairs && tile && best_t >= (double)p->ndm * p->nchan * (double)nout / kTileAddps) return AF_OK;
-    if (best == 1) {
+    if (best > 0) {
         if (int rc = pairs_release(&p->pairs)) return rc;
-        std::swap(p->pairs, p->quads);
+        std::swap(p->pairs, *cand[best]);
     }
     af_pair_tables* T = &p->pairs;
     if (best_L > T->lay[0].L)
@@ -885,7 +888,9 @@ int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64
     if (L <= 0 || L % kPTTE || T0 % L) return af_set_error(AF_EINVAL, "pairs: time block not laid out");
     const int rwb = 2 * T->rwe;
     const size_t s2 = tile_smem(T->shape, rwb), s1 = rows_smem(T->maxdr, T->G);
-    const void* k1 = T->G == 4 ? (const void*)k_group_rows<4> : (const void*)k_group_rows<2>;
+    const void* k1 = T->G == 4   ? (const void*)k_group_rows<4>
+                     : T->G == 3 ? (const void*)k_group_rows<3>
+                                 : (const void*)k_group_rows<2>;
     if (int rc = af_ensure_smem(tile_kernel(T->shape), s2)) return rc;
     if (int rc = af_ensure_smem(k1, s1)) return rc;
     const int etiles = (int)((ly.maxlen + kET - 1) / kET);
@@ -895,6 +900,10 @@ int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64
     if (g1 > 0x7fffffffULL || g2 > 0x7fffffffULL) return af_set_error(AF_EINVAL, "pairs: problem too large for one grid");
     if (T->G == 4)
         k_group_rows<4><<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, ly.d_pinfo, T->d_gdr, T->d_rdelta,
+                                                      ly.d_rinfo, ly.d_rowoff, T0, etiles, rows_wstride(T->maxdr),
+                                                      T->d_ps);
+    else if (T->G == 3)
+        k_group_rows<3><<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, ly.d_pinfo, T->d_gdr, T->d_rdelta,
                                                       ly.d_rinfo, ly.d_rowoff, T0, etiles, rows_wstride(T->maxdr),
                                                       T->d_ps);
     else

@@ -82,7 +82,8 @@ static void free_plan(af_plan_t p)
     cudaFree(p->d_delays);
     af_tile_tables_free(&p->tile);
     af_pairs_free(&p->pairs);
-    af_pairs_free(&p->quads);
+    af_pairs_free(&p->alt[0]);
+    af_pairs_free(&p->alt[1]);
     af_sb_free(p);
     cudaFree(p->d_err);
     cudaFree(p->d_stats);
@@ -178,7 +179,10 @@ static int plan_finish(af_plan_s* p, const char* who)
         p->force_tile = strcmp(k, "tile") == 0;
         p->force_pairs = strcmp(k, "pairs") == 0;
     }
-    if (const char* g = getenv("AFGB_PAIR_GROUP")) p->force_group = atoi(g) == 4 ? 4 : atoi(g) == 2 ? 2 : 0;
+    if (const char* g = getenv("AFGB_PAIR_GROUP")) {
+        const int v = atoi(g);
+        p->force_group = v >= 2 && v <= 4 ? v : 0;
+    }
     const size_t tbytes = (size_t)p->ndm * p->nchan * sizeof(int32_t);
     int rc = AF_OK;
     if ((e = cudaMalloc(&p->d_delays, tbytes)) != cudaSuccess ||

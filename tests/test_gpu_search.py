@@ -148,16 +148,16 @@ SHAPES = [
 ]
 
 
-@pytest.mark.parametrize("kernel", ["auto", "pairs", "quads", "tile"])
+@pytest.mark.parametrize("kernel", ["auto", "pairs", "triples", "quads", "tile"])
 @pytest.mark.parametrize("shape", SHAPES, ids=[str(i) for i in range(len(SHAPES))])
 def test_random_shapes_bit_exact(shape, kernel, monkeypatch):
     """Every single-plan path (the default choice; rows of channel pairs or of
     channel quads wherever they apply; the channel tile kernel) gives the
     oracle's plane."""
     from paper_2511_02328_gb300.search import Plan
-    if kernel in ("pairs", "quads"):
+    if kernel in ("pairs", "triples", "quads"):
         monkeypatch.setenv("AFGB_DEDISP_KERNEL", "pairs")
-        monkeypatch.setenv("AFGB_PAIR_GROUP", "2" if kernel == "pairs" else "4")
+        monkeypatch.setenv("AFGB_PAIR_GROUP", {"pairs": "2", "triples": "3", "quads": "4"}[kernel])
     elif kernel != "auto":
         monkeypatch.setenv("AFGB_DEDISP_KERNEL", kernel)
     nchan, f_lo, f_hi, tsamp, nsamp, dms = shape
@@ -343,10 +343,10 @@ def _pair_rows_bytes(D, L, G=2):
     return 2 * total
 
 
-@pytest.mark.parametrize("G", [2, 4])
+@pytest.mark.parametrize("G", [2, 3, 4])
 @pytest.mark.parametrize("nchan,f_lo,f_hi", [(256, 1000.0, 1500.0), (255, 1500.0, 1000.0)])
 def test_pair_rows_several_time_blocks(nchan, f_lo, f_hi, G, monkeypatch):
-    """The group-row path (pairs, quads) with a row budget that holds 9 tiles
+    """The group-row path (2, 3, 4 channels) with a row budget that holds 9 tiles
     of outputs: the plane (several time blocks, a ragged last one) and its row
     sums are the oracle's; 255 channels end with a short group."""
     from paper_2511_02328_gb300.search import Plan
