@@ -206,9 +206,7 @@ SB_N0, SB_NSUB = 8, 64
 # DRAM read + write bytes of one stage-2 pair-row tile launch (k_pair_tile) on this workload, from an ncu
 # capture of the same kernel (dram__bytes_read.sum + dram__bytes_write.sum); None until captured, and reset
 # to None whenever the kernel changes
-PAIR_TILE_TRAFFIC = {2: (2.76e10, "ncu dram__bytes read+write of k_pair_tile<15,32,2> on pair rows at 2^16 samples "
-                             "(2.47 GB, 19 output tiles), scaled by the output tiles to this 2^18-sample launch "
-                             "(212 tiles)")}   # keyed by channels per row
+PAIR_TILE_TRAFFIC = {}   # keyed by channels per row: (bytes per launch, basis); filled from a capture of the current kernel
 
 
 def match_pulses(cands, pulses, dms):
@@ -759,7 +757,7 @@ def main():
     if kern["path"] == "pairs":
         st = [_lib.af_dedisperse_times(H, i) for i in range(args.steps)]
         stage = {"rows_ms": float(np.mean([x[0] for x in st])), "tiles_ms": float(np.mean([x[1] for x in st])),
-                 "row_bytes": int(st[-1][2])}
+                 "row_bytes": int(st[-1][2]), "copy_bytes": int(st[-1][3])}
         _lib.af_dedisperse_timing(H, 0)
     ncand = int(count.item())
     ms_total = max_over_ranks(ms_total, dist, dev)
@@ -858,12 +856,17 @@ def main():
         s1_bytes = stage["row_bytes"] + NCHAN * NSAMP
         s1_ach = s1_bytes / (stage["rows_ms"] * 1e-3) / 1e9
         roofline = {
-            "bound": "smem", "kernel": "k_pair_tile<15,32,2> (stage 2 of the group-row dedispersion, %d channels "
-                                       "per row)" % G,
+            "bound": "smem", "kernel": "k_pair_tile<15,%d> (stage 2 of the group-row dedispersion, %d channels "
+                                       "per row)" % (kern["ring"], G),
             "achieved": s2_ach, "peak": smem_peak, "unit": "TB/s", "frac": s2_ach / smem_peak,
             "traffic": traffic, "traffic_basis": traffic_basis,
             "work": "2 B shared load per (DM, channel group, output): %.3g B per launch" % lds_bytes,
             "ms": stage["tiles_ms"],
+            "with_copies": {"achieved": (lds_bytes + stage["copy_bytes"]) / (stage["tiles_ms"] * 1e-3) / 1e12,
+                            "frac": (lds_bytes + stage["copy_bytes"]) / (stage["tiles_ms"] * 1e-3) / 1e12 / smem_peak,
+                            "copy_bytes": stage["copy_bytes"],
+                            "note": "shared-memory bytes including the row windows the producer copies in (the "
+                                    "kernel's whole shared-memory traffic but its small tables)"},
             "peak_basis": "%d SMs x 128 B shared-load bandwidth per clock x %.0f MHz (derived, of max clock)"
                           % (nsm, sm_max),
             "stage1": {"kernel": "k_group_rows<%d>" % G, "bound": "hbm", "ms": stage["rows_ms"], "achieved": s1_ach,

@@ -263,10 +263,12 @@ int af_dedisperse_reserve(af_plan_t plan, int64_t max_nsamp);
  * (calls since then) mod n, events on its stream around stage 1 (row sums)
  * and stage 2 (tiles) of each of its first 8 time blocks.
  * af_dedisperse_times(plan, i, ...) waits for slot i's events and returns the
- * summed stage times in ms and the row-buffer bytes that call wrote (any
- * output may be NULL); AF_EINVAL for a slot outside 0..n-1. */
+ * summed stage times in ms, the row-buffer bytes that call wrote and the
+ * row-window bytes its stage 2 copied into shared memory (any output may be
+ * NULL); AF_EINVAL for a slot outside 0..n-1. */
 int af_dedisperse_timing(af_plan_t plan, int ncalls);
-int af_dedisperse_times(af_plan_t plan, int call, float* rows_ms, float* tiles_ms, int64_t* row_bytes);
+int af_dedisperse_times(af_plan_t plan, int call, float* rows_ms, float* tiles_ms, int64_t* row_bytes,
+                        int64_t* copy_bytes);
 int af_dedisperse(af_plan_t plan, const uint8_t* d_in, int64_t nsamp,
                   int32_t* d_plane, af_rowstats_t* d_stats, void* stream);
 

@@ -70,7 +70,7 @@ SIGNATURES = {
     "af_plan_kernel": [_P, _P, _P, _P, _P],
     "af_dedisperse_reserve": [_P, _I64],
     "af_dedisperse_timing": [_P, _I],
-    "af_dedisperse_times": [_P, _I, _P, _P, _P],
+    "af_dedisperse_times": [_P, _I, _P, _P, _P, _P],
     "af_dedisperse": [_P, _P, _I64, _P, _P, _P],
     "af_rowstats": [_P, _P, _I64, _P, _P],
     "af_boxcar_snr": [_P, _P, _I64, _P, _P, _I, _P, _P, _P],
@@ -256,11 +256,11 @@ def af_dedisperse_timing(plan, ncalls):
 
 
 def af_dedisperse_times(plan, call):
-    """(stage-1 ms, stage-2 ms, row-buffer bytes) of timed call slot `call`."""
-    r, t, b = ctypes.c_float(), ctypes.c_float(), _I64()
-    _check(lib().af_dedisperse_times(plan, call, ctypes.byref(r), ctypes.byref(t), ctypes.byref(b)),
-           "af_dedisperse_times")
-    return r.value, t.value, b.value
+    """(stage-1 ms, stage-2 ms, row-buffer bytes, row-window bytes copied) of timed call slot `call`."""
+    r, t, b, c = ctypes.c_float(), ctypes.c_float(), _I64(), _I64()
+    _check(lib().af_dedisperse_times(plan, call, ctypes.byref(r), ctypes.byref(t), ctypes.byref(b),
+                                     ctypes.byref(c)), "af_dedisperse_times")
+    return r.value, t.value, b.value, c.value
 
 
 def af_plan_delays(plan):

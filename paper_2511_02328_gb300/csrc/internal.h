@@ -82,7 +82,8 @@ struct af_pair_tables {
     int np = 0, nrows = 0, rwe = 0, maxdr = 0;   // np = groups
     double rows_per_pair = 0;      // rows copied per pair and DM block (mean)
     size_t budget = 0;             // bytes the row buffer may take (AFGB_PAIR_BUDGET_MB at plan creation)
-    int shape = 0;                 // ring shape of the row kernel (pairs.cu)
+    int shape = 0;                 // ring depth of the row kernel (2 to 4 stages)
+    int stage_bytes = 0;           // bytes of one ring stage (windows packed back to back)
     af_tile_tables tt;             // DM order and block minima for this block shape
     double copy_per_tile = 0;      // bytes of row windows copied per time tile (all DM blocks)
     std::vector<int32_t> h_rb, h_ub, h_rB, h_rspan, h_srow, h_scpart;
@@ -91,7 +92,7 @@ struct af_pair_tables {
     int2* d_chunks = nullptr;      // per chunk: row slots, first slot
     int32_t* d_chkoff = nullptr;   // [nblk + 1]
     int* d_tabs = nullptr;         // per chunk: every consumer warp's table
-    int32_t* d_sbytes = nullptr;   // per slot: window bytes
+    int2* d_srec = nullptr;        // per slot: window bytes, byte offset inside its ring stage
     uint16_t* d_ps = nullptr;      // row buffer
     size_t ps_bytes = 0;
     bool ps_owned = true;          // false: a buffer shared by a batch's plans
@@ -111,6 +112,7 @@ struct af_pair_tables {
     int tcalls = 0, tblocks = 0, tnext = 0;
     std::vector<int> tnb;              // blocks recorded per call slot
     std::vector<int64_t> trowbytes;    // row-buffer bytes written per call slot
+    std::vector<int64_t> tcopybytes;   // row-window bytes copied into shared memory per call slot
 };
 int af_pairs_build(af_plan_t p);
 void af_pairs_free(af_pair_tables* T);

@@ -45,14 +45,11 @@
 namespace {
 
 constexpr int kPNW = 15;            // DM rows (consumer warps) per block
-// Ring shapes (row slots per stage, at most one per producer lane; depth):
-// 0 = 32 x 2, 1 = 24 x 3, 2 = 16 x 4, 3 = 24 x 2, 4 = 16 x 2 (AFGB_PAIR_SHAPE
-// at plan creation, else the first that fits the shared memory; on the
-// 4096-channel workload 32 x 2 measured 28.0 ms, 16 x 4 29.5 ms; the last two
-// serve windows too wide for the others).
-constexpr int kShapes = 5;
-constexpr int kShapeSL[kShapes] = {32, 24, 16, 24, 16};
-constexpr int kShapeNS[kShapes] = {2, 3, 4, 2, 2};
+// Ring: up to kPSL row windows per stage (one per producer lane), packed back
+// to back (a stage holds as many whole groups as fit its bytes); the depth is
+// 2, 3 or 4 stages (AFGB_PAIR_STAGES at plan creation, default 3: on the
+// 4096-channel workload with groups of 3, stage 2 took 19.8 / 19.2 / 21.5 ms).
+constexpr int kPSL = 32;
 constexpr int kPMG = 16;            // 2-sample groups per lane
 constexpr int kPTTE = 1016;         // outputs per tile: a multiple of 8 below 64 * kPMG - 1
 constexpr int kPTABW = 40;          // ints per (stage, warp) table: 2 starts, 2 counts, <= 34 offsets
@@ -70,10 +67,10 @@ struct PairArgs {
     const int2* chunks;      // per chunk: {row slots, first slot}
     const int32_t* chkoff;   // [nblk + 1] first chunk of each block
     const int* tabs;         // per chunk: NW x TABW ints, every consumer warp's table for its ring stage
-    const int32_t* sbytes;   // per slot: window bytes
+    const int2* srec;        // per slot: {window bytes, byte offset inside its stage}
     const int64_t* soff;     // per slot: element offset of its window in PS for the block's first tile
     const int32_t* perm;     // [ndm_pad] plane row, -1 = padding
-    int rwb;
+    int stage_bytes;         // bytes of one ring stage's windows
     int flush;               // rows between folds: flush * 255 * G < 2^16
     unsigned nblk;
     int64_t T0;              // first output of the time block (a multiple of 8)
@@ -155,56 +152,56 @@ k_group_rows(const uint8_t* __restrict__ X, int64_t nsamp, int nchan, const int4
         }
     }
     __syncthreads();
-    const int i0 = tid * 16;
-    if (e0 + i0 >= pi.w) return;  // range and row lengths are multiples of 16
+    // thread tid takes the 4-sample words w = tid + 256 j (j < 4) of the block:
+    // consecutive lanes read consecutive shared words (no bank conflicts) and
+    // store consecutive 8-byte pieces of a row
     uint32_t alo[4], ahi[4];
+    bool live[4];
     {
         const uint32_t* A32 = reinterpret_cast<const uint32_t*>(sm);
-        const int pa = off[0] + i0;
-        const uint32_t sh = (uint32_t)(pa & 3) * 8u;
-        uint32_t w[5];
+        const uint32_t sh = (uint32_t)(off[0] & 3) * 8u;
 #pragma unroll
-        for (int j = 0; j < 5; j++) w[j] = A32[(pa >> 2) + j];
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const uint32_t a = __funnelshift_r(w[k], w[k + 1], sh);
-            alo[k] = __byte_perm(a, 0u, 0x4140);  // samples 0, 1 into 16-bit lanes
-            ahi[k] = __byte_perm(a, 0u, 0x4342);  // samples 2, 3
+        for (int j = 0; j < 4; j++) {
+            const int w = tid + kS1T * j;
+            live[j] = e0 + 4 * w < pi.w;
+            const int p = (off[0] >> 2) + w;
+            const uint32_t a = __funnelshift_r(A32[p], A32[p + 1], sh);
+            alo[j] = __byte_perm(a, 0u, 0x4140);  // samples 0, 1 into 16-bit lanes
+            ahi[j] = __byte_perm(a, 0u, 0x4342);  // samples 2, 3
         }
     }
     for (int k = 0; k < pi.y; k++) {
         const int2 ri = __ldg(rinfo + pi.x + k);
-        const int64_t rel = e0 + i0 - ri.x;  // sample index within the row
-        if (rel < 0 || rel >= ri.y) continue;
-        uint32_t o[8];
+        uint32_t lo[4], hi[4];
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            o[2 * j] = alo[j];
-            o[2 * j + 1] = ahi[j];
+            lo[j] = alo[j];
+            hi[j] = ahi[j];
         }
 #pragma unroll
         for (int i = 0; i < K; i++) {
             const uint32_t* W32 = reinterpret_cast<const uint32_t*>(sm + kET + 48 + i * wstride);
-            const int pb = off[i + 1] + __ldg(rdelta + (int64_t)(pi.x + k) * K + i) - dmn[i] + i0;
+            const int pb = off[i + 1] + __ldg(rdelta + (int64_t)(pi.x + k) * K + i) - dmn[i];
             const uint32_t sh = (uint32_t)(pb & 3) * 8u;
-            uint32_t w[5];
-#pragma unroll
-            for (int j = 0; j < 5; j++) w[j] = W32[(pb >> 2) + j];
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                const uint32_t b = __funnelshift_r(w[j], w[j + 1], sh);
-                o[2 * j] += __byte_perm(b, 0u, 0x4140);
-                o[2 * j + 1] += __byte_perm(b, 0u, 0x4342);
+                const int p = (pb >> 2) + tid + kS1T * j;
+                const uint32_t b = __funnelshift_r(W32[p], W32[p + 1], sh);
+                lo[j] += __byte_perm(b, 0u, 0x4140);
+                hi[j] += __byte_perm(b, 0u, 0x4342);
             }
         }
-        uint4* dst = reinterpret_cast<uint4*>(PS + __ldg(rowoff + pi.x + k) + rel);
-        dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
-        dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+        uint16_t* row = PS + __ldg(rowoff + pi.x + k);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int64_t rel = e0 + 4 * (tid + kS1T * j) - ri.x;  // sample index within the row
+            if (live[j] && rel >= 0 && rel < ri.y) *reinterpret_cast<uint2*>(row + rel) = make_uint2(lo[j], hi[j]);
+        }
     }
 }
 
 // ------------------------------------------------------------------ stage 2
-template <int NW, int SL, int NS>
+template <int NW, int NS>
 struct PairTile {
     static __device__ __forceinline__ int2 load_cd(const PairArgs& a, int cbeg, int nchk, int kk)
     {
@@ -214,8 +211,8 @@ struct PairTile {
     // Chunk c (block-local kk) into stage st: its precomputed table block and
     // one window per row slot, all completing on the stage's full barrier.
     static __device__ __forceinline__ void produce(const PairArgs& a, uint8_t* smem, int* tab, uint32_t full_bar,
-                                                   int c, const int2& cd, uint32_t bytes, int64_t src, int st,
-                                                   int lane)
+                                                   int c, const int2& cd, uint32_t bytes, uint32_t soff,
+                                                   int64_t src, int st, int lane)
     {
         constexpr uint32_t TB = (uint32_t)(NW * kPTABW * 4);
         const uint32_t tot = __reduce_add_sync(0xffffffffu, bytes) + TB;
@@ -228,7 +225,7 @@ struct PairTile {
         }
         __syncwarp();
         if (lane < cd.x && bytes)
-            afptx::bulk_g2s(afptx::smem_addr(smem) + (uint32_t)((st * SL + lane) * a.rwb), a.PS + src, bytes,
+            afptx::bulk_g2s(afptx::smem_addr(smem) + (uint32_t)(st * a.stage_bytes + soff), a.PS + src, bytes,
                             full_bar);
     }
 
@@ -258,7 +255,7 @@ struct PairTile {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const unsigned jb = blockIdx.x % a.nblk;
         const int64_t t0 = a.T0 + (int64_t)(blockIdx.x / a.nblk) * kPTTE;
-        int* tab = (int*)(smem + (size_t)NS * SL * a.rwb);
+        int* tab = (int*)(smem + (size_t)NS * a.stage_bytes);
         uint64_t* bars = (uint64_t*)(tab + NS * NW * kPTABW);
         const uint32_t full0 = afptx::smem_addr(bars), empty0 = full0 + 8 * NS;
         const int cbeg = __ldg(a.chkoff + jb), nchk = __ldg(a.chkoff + jb + 1) - cbeg;
@@ -276,19 +273,19 @@ struct PairTile {
             // ---------------- producer warp: chunk descriptors two ahead, slot records one ahead
             const int64_t dt = t0 - a.T0;
             int2 cda = load_cd(a, cbeg, nchk, 0), cdb = load_cd(a, cbeg, nchk, 1);
-            uint32_t bcur = 0, bnxt = 0;
+            int2 rcur = make_int2(0, 0), rnxt = make_int2(0, 0);
             int64_t scur = 0, snxt = 0;
             if (lane < cda.x) {
-                bcur = (uint32_t)__ldg(a.sbytes + cda.y + lane);
+                rcur = __ldg(a.srec + cda.y + lane);
                 scur = __ldg(a.soff + cda.y + lane) + dt;
             }
             int kk = 0;
             for (; kk < nchk; kk++) {
                 const int st = kk % NS;
                 const int2 cdc = load_cd(a, cbeg, nchk, kk + 2);
-                bnxt = 0;
+                rnxt = make_int2(0, 0);
                 if (lane < cdb.x) {
-                    bnxt = (uint32_t)__ldg(a.sbytes + cdb.y + lane);
+                    rnxt = __ldg(a.srec + cdb.y + lane);
                     snxt = __ldg(a.soff + cdb.y + lane) + dt;
                 }
                 if (kk >= NS &&
@@ -296,8 +293,9 @@ struct PairTile {
                     if (lane == 0) atomicExch(a.err, 1);
                     break;
                 }
-                produce(a, smem, tab, full0 + 8 * st, cbeg + kk, cda, bcur, scur, st, lane);
-                bcur = bnxt;
+                produce(a, smem, tab, full0 + 8 * st, cbeg + kk, cda, (uint32_t)rcur.x, (uint32_t)rcur.y, scur, st,
+                        lane);
+                rcur = rnxt;
                 scur = snxt;
                 cda = cdb;
                 cdb = cdc;
@@ -398,31 +396,23 @@ struct PairTile {
 
 // Grid = time tiles of the block x DM blocks, DM blocks fastest (a tile's rows
 // stay in L2 while every DM block reads them).
-template <int NW, int SL, int NS>
+template <int NW, int NS>
 __global__ void __launch_bounds__((NW + 1) * 32, 1) k_pair_tile(const PairArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem[];
-    PairTile<NW, SL, NS>::run(a, smem);
+    PairTile<NW, NS>::run(a, smem);
 }
 
-size_t tile_smem(int shape, int rwb)
-{
-    const int sl = kShapeSL[shape], ns = kShapeNS[shape];
-    return (size_t)ns * sl * rwb + (size_t)ns * kPNW * kPTABW * 4 + 2 * (size_t)ns * 8;
-}
-
-const void* tile_kernel(int shape)
-{
-    switch (shape) {
-    case 0: return (const void*)k_pair_tile<kPNW, 32, 2>;
-    case 1: return (const void*)k_pair_tile<kPNW, 24, 3>;
-    case 2: return (const void*)k_pair_tile<kPNW, 16, 4>;
-    case 3: return (const void*)k_pair_tile<kPNW, 24, 2>;
-    default: return (const void*)k_pair_tile<kPNW, 16, 2>;
-    }
-}
+size_t tables_smem(int ns) { return (size_t)ns * kPNW * kPTABW * 4 + 2 * (size_t)ns * 8; }
 int rows_wstride(int maxdr) { return (int)r16(kET + maxdr + 4 + 4 + 48); }
 size_t rows_smem(int maxdr, int G) { return (size_t)kET + 48 + (size_t)(G - 1) * rows_wstride(maxdr); }
+
+const void* tile_kernel(int ns)
+{
+    return ns == 4 ? (const void*)k_pair_tile<kPNW, 4>
+         : ns == 3 ? (const void*)k_pair_tile<kPNW, 3>
+                   : (const void*)k_pair_tile<kPNW, 2>;
+}
 
 size_t pair_budget()
 {
@@ -432,19 +422,20 @@ size_t pair_budget()
     return std::min<size_t>((size_t)48 << 30, tot / 5);
 }
 
-// Rates measured on GB300 at 2070 MHz (4096-channel workload, 1001 DMs):
-// stage 2 moves shared-memory bytes (consumer loads + row-window copies) at
-// about 41 TB/s on pair rows and 29 TB/s on quad rows (smaller chunks, twice
-// the folds); stage 1 writes row bytes at about 5.0 TB/s of HBM for pairs and
-// 3.4 TB/s for quads; the channel tile kernel adds about 17.7 T samples/s.
+// Rates measured on GB300 at 2070 MHz (4096-channel workload, 1001 DMs, 3-deep
+// ring): stage 2 moves shared-memory bytes (consumer loads + row-window
+// copies) at about 40 / 37 / 31 TB/s for groups of 2 / 3 / 4 channels (fewer
+// groups per chunk and more frequent folds as groups grow); stage 1 moves row
+// bytes + input at about 6.9 / 6.5 / 5.4 TB/s of HBM; the channel tile kernel
+// adds about 17.7 T samples/s.
 constexpr double kTileAddps = 17.7e12;
-inline double smem_rate(int G) { return G == 4 ? 29e12 : G == 3 ? 35e12 : 41e12; }
-inline double row_rate(int G) { return G == 4 ? 3.4e12 : G == 3 ? 4.4e12 : 5.0e12; }
+inline double smem_rate(int G) { return G == 4 ? 31e12 : G == 3 ? 37e12 : 40e12; }
+inline double row_rate(int G) { return G == 4 ? 5.2e12 : G == 3 ? 6.2e12 : 6.5e12; }
 
 }  // namespace
 
 int af_pair_tile_outputs() { return kPTTE; }
-int af_pair_ring_depth(int shape) { return kShapeNS[shape]; }
+int af_pair_ring_depth(int ns) { return ns; }
 
 void af_pairs_free(af_pair_tables* T)
 {
@@ -454,7 +445,7 @@ void af_pairs_free(af_pair_tables* T)
     cudaFree(T->d_chunks);
     cudaFree(T->d_chkoff);
     cudaFree(T->d_tabs);
-    cudaFree(T->d_sbytes);
+    cudaFree(T->d_srec);
     for (auto& l : T->lay) {
         cudaFree(l.d_pinfo);
         cudaFree(l.d_rinfo);
@@ -550,28 +541,25 @@ static int build_groups(af_plan_t p, int G, af_pair_tables* T)
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
     const int64_t rwe = r8((int64_t)spread + 1031);
     if (spread >= (1 << 20) || maxdr > kMaxDr) return AF_OK;
-    const int rwb = (int)(2 * rwe);
-    int shape = -1;
-    if (const char* e = getenv("AFGB_PAIR_SHAPE")) shape = atoi(e);
-    if (shape < 0 || shape >= kShapes || tile_smem(shape, rwb) > (size_t)optin) {
-        shape = -1;
-        for (int k = kShapes - 1; k >= 0; k--)
-            if (tile_smem(k, rwb) <= (size_t)optin) shape = k;
-    }
-    if (shape < 0) return AF_OK;
-    const int SL = kShapeSL[shape], NS = kShapeNS[shape];
-    // chunks of whole groups, at most SL rows each, per block; their tables
+    int NS = 3;
+    if (const char* e = getenv("AFGB_PAIR_STAGES")) NS = std::min(4, std::max(2, atoi(e)));
+    // one stage: up to kPSL windows back to back; the widest window must fit
+    const int stage_bytes = (int)(((size_t)optin - tables_smem(NS)) / NS) & ~15;
+    if (2 * rwe > stage_bytes) return AF_OK;
+    // chunks of whole groups, at most kPSL windows and stage_bytes each, per block; their tables
     struct Ent {
         int slot[kPNW];
         int e[kPNW];
     };
     std::vector<Ent> ents;
     std::vector<int2> chunks;
-    std::vector<int32_t> chkoff(nblk + 1, 0), sbytes, srow, scpart;
+    std::vector<int32_t> chkoff(nblk + 1, 0), srow, scpart;
+    std::vector<int2> srec;  // per slot: window bytes, offset inside its stage
     std::vector<int> tabs;
     std::vector<Key> dq(NW), S;
     std::vector<int32_t> d0(NW), sdm;
-    int open_slots = 0, first_slot = 0, kloc = 0;
+    int open_slots = 0, open_bytes = 0, first_slot = 0, kloc = 0;
+    std::vector<int> sbyt, soffs;  // slot bytes and stage offsets of the open group
     auto flush = [&]() {
         if (ents.empty()) return;
         const int st = kloc % NS;
@@ -588,12 +576,13 @@ static int build_groups(af_plan_t p, int G, af_pair_tables* T)
             tb[3] = cnt[1];
             for (const Ent& en : ents) {
                 const int r = en.e[w] & 1;
-                tb[4 + pos[r]++] = (st * SL + en.slot[w]) * rwb + 2 * (en.e[w] - r);
+                tb[4 + pos[r]++] = st * stage_bytes + srec[first_slot + en.slot[w]].y + 2 * (en.e[w] - r);
             }
         }
         chunks.push_back(make_int2(open_slots, first_slot));
         ents.clear();
         open_slots = 0;
+        open_bytes = 0;
         kloc++;
     };
     for (int j = 0; j < nblk; j++) {
@@ -608,11 +597,11 @@ static int build_groups(af_plan_t p, int G, af_pair_tables* T)
             S.assign(dq.begin(), dq.end());
             std::sort(S.begin(), S.end());
             S.erase(std::unique(S.begin(), S.end()), S.end());
-            if ((int)S.size() > SL) return AF_OK;
-            if (open_slots + (int)S.size() > SL) flush();
-            if (ents.empty()) first_slot = (int)sbytes.size();
+            if ((int)S.size() > kPSL) return AF_OK;
             // one window per (block, row): from the smallest delay of the block's DMs on that row
             sdm.assign(S.size(), 0);
+            sbyt.assign(S.size(), 0);
+            int gbytes = 0;
             for (size_t k = 0; k < S.size(); k++) {
                 int32_t lo = INT32_MAX, hi = INT32_MIN;
                 for (int w = 0; w < NW; w++)
@@ -620,12 +609,20 @@ static int build_groups(af_plan_t p, int G, af_pair_tables* T)
                         lo = std::min(lo, d0[w]);
                         hi = std::max(hi, d0[w]);
                     }
+                sdm[k] = lo;
+                sbyt[k] = (int)(2 * r8((int64_t)(hi - lo) + 1031));
+                gbytes += sbyt[k];
+            }
+            if (gbytes > stage_bytes) return AF_OK;
+            if (open_slots + (int)S.size() > kPSL || open_bytes + gbytes > stage_bytes) flush();
+            if (ents.empty()) first_slot = (int)srec.size();
+            for (size_t k = 0; k < S.size(); k++) {
                 const int g = (int)(std::lower_bound(rkey.begin() + rb[q], rkey.begin() + rb[q + 1], S[k]) -
                                     rkey.begin());
-                sdm[k] = lo;
-                sbytes.push_back((int)(2 * r8((int64_t)(hi - lo) + 1031)));
+                srec.push_back(make_int2(sbyt[k], open_bytes));
+                open_bytes += sbyt[k];
                 srow.push_back(g);
-                scpart.push_back((lo & ~7) - rB[g]);
+                scpart.push_back((sdm[k] & ~7) - rB[g]);
             }
             Ent en;
             for (int w = 0; w < NW; w++) {
@@ -641,10 +638,10 @@ static int build_groups(af_plan_t p, int G, af_pair_tables* T)
     }
     // rows copied per group and block: beyond 8 the copies alone outweigh the
     // loads they save (the reservation weighs the rest)
-    const double rows_per_group = (double)sbytes.size() / ((double)nblk * ng);
+    const double rows_per_group = (double)srec.size() / ((double)nblk * ng);
     if (rows_per_group > 8.0) return AF_OK;
     double copy = 0;
-    for (int32_t b : sbytes) copy += b;
+    for (const int2& r : srec) copy += r.x;
     T->G = G;
     T->np = ng;
     T->nrows = (int)rB.size();
@@ -652,7 +649,8 @@ static int build_groups(af_plan_t p, int G, af_pair_tables* T)
     T->maxdr = maxdr;
     T->rows_per_pair = rows_per_group;
     T->budget = pair_budget();
-    T->shape = shape;
+    T->shape = NS;
+    T->stage_bytes = stage_bytes;
     T->copy_per_tile = copy;
     T->h_rb = rb;
     T->h_ub = ub;
@@ -670,7 +668,7 @@ static int build_groups(af_plan_t p, int G, af_pair_tables* T)
         !up((void**)&T->d_chunks, chunks.data(), chunks.size() * sizeof(int2)) ||
         !up((void**)&T->d_chkoff, chkoff.data(), chkoff.size() * 4) ||
         !up((void**)&T->d_tabs, tabs.data(), tabs.size() * 4) ||
-        !up((void**)&T->d_sbytes, sbytes.data(), sbytes.size() * 4)) {
+        !up((void**)&T->d_srec, srec.data(), srec.size() * sizeof(int2))) {
         af_pairs_free(T);
         return af_cuda_check(e, "group tables");
     }
@@ -886,8 +884,7 @@ int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64
     const af_pair_tables::Layout& ly = T->lay[layout];
     const int64_t L = ly.L;
     if (L <= 0 || L % kPTTE || T0 % L) return af_set_error(AF_EINVAL, "pairs: time block not laid out");
-    const int rwb = 2 * T->rwe;
-    const size_t s2 = tile_smem(T->shape, rwb), s1 = rows_smem(T->maxdr, T->G);
+    const size_t s2 = (size_t)T->shape * T->stage_bytes + tables_smem(T->shape), s1 = rows_smem(T->maxdr, T->G);
     const void* k1 = T->G == 4   ? (const void*)k_group_rows<4>
                      : T->G == 3 ? (const void*)k_group_rows<3>
                                  : (const void*)k_group_rows<2>;
@@ -917,10 +914,10 @@ int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64
     a.chunks = T->d_chunks;
     a.chkoff = T->d_chkoff;
     a.tabs = T->d_tabs;
-    a.sbytes = T->d_sbytes;
+    a.srec = T->d_srec;
     a.soff = ly.d_soff;
     a.perm = T->tt.d_perm;
-    a.rwb = rwb;
+    a.stage_bytes = T->stage_bytes;
     a.flush = 65535 / (255 * T->G);
     a.nblk = (unsigned)T->tt.nblk;
     a.T0 = T0;
@@ -930,13 +927,12 @@ int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64
     a.stats = d_stats;
     a.err = p->d_err;
     const dim3 grid2((unsigned)g2), blk2((kPNW + 1) * 32);
-    switch (T->shape) {
-    case 0: k_pair_tile<kPNW, 32, 2><<<grid2, blk2, s2, s>>>(a); break;
-    case 1: k_pair_tile<kPNW, 24, 3><<<grid2, blk2, s2, s>>>(a); break;
-    case 2: k_pair_tile<kPNW, 16, 4><<<grid2, blk2, s2, s>>>(a); break;
-    case 3: k_pair_tile<kPNW, 24, 2><<<grid2, blk2, s2, s>>>(a); break;
-    default: k_pair_tile<kPNW, 16, 2><<<grid2, blk2, s2, s>>>(a); break;
-    }
+    if (T->shape == 4)
+        k_pair_tile<kPNW, 4><<<grid2, blk2, s2, s>>>(a);
+    else if (T->shape == 3)
+        k_pair_tile<kPNW, 3><<<grid2, blk2, s2, s>>>(a);
+    else
+        k_pair_tile<kPNW, 2><<<grid2, blk2, s2, s>>>(a);
     return af_cuda_check(cudaGetLastError(), "pair tile launch");
 }
 
@@ -963,6 +959,7 @@ int af_launch_pairs(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nou
     if (slot >= 0) {
         T->tnb[slot] = std::min(b, T->tblocks);
         T->trowbytes[slot] = 2 * rows_elems(T, L) * (int64_t)b;
+        T->tcopybytes[slot] = (int64_t)((double)((nout + kPTTE - 1) / kPTTE) * T->copy_per_tile);
         T->tnext = (slot + 1) % T->tcalls;
     }
     return AF_OK;
@@ -984,11 +981,13 @@ extern "C" int af_dedisperse_timing(af_plan_t p, int ncalls)
         if (cudaError_t e = cudaEventCreate(&ev)) return af_cuda_check(e, "af_dedisperse_timing");
     T->tnb.assign(ncalls, 0);
     T->trowbytes.assign(ncalls, 0);
+    T->tcopybytes.assign(ncalls, 0);
     T->tcalls = ncalls;
     return AF_OK;
 }
 
-extern "C" int af_dedisperse_times(af_plan_t p, int call, float* rows_ms, float* tiles_ms, int64_t* row_bytes)
+extern "C" int af_dedisperse_times(af_plan_t p, int call, float* rows_ms, float* tiles_ms, int64_t* row_bytes,
+                                   int64_t* copy_bytes)
 {
     if (int rc = af_check_plan(p)) return rc;
     af_pair_tables* T = &p->pairs;
@@ -1006,5 +1005,6 @@ extern "C" int af_dedisperse_times(af_plan_t p, int call, float* rows_ms, float*
     if (rows_ms) *rows_ms = r;
     if (tiles_ms) *tiles_ms = t;
     if (row_bytes) *row_bytes = T->trowbytes[call];
+    if (copy_bytes) *copy_bytes = T->tcopybytes[call];
     return AF_OK;
 }
