@@ -206,7 +206,10 @@ SB_N0, SB_NSUB = 8, 64
 # DRAM read + write bytes of one stage-2 pair-row tile launch (k_pair_tile) on this workload, from an ncu
 # capture of the same kernel (dram__bytes_read.sum + dram__bytes_write.sum); None until captured, and reset
 # to None whenever the kernel changes
-PAIR_TILE_TRAFFIC = {}   # keyed by channels per row: (bytes per launch, basis); filled from a capture of the current kernel
+PAIR_TILE_TRAFFIC = {   # keyed by channels per row: (bytes per launch, basis), from a capture of the current kernel
+    3: (3.64e10, "ncu dram__bytes read+write of k_pair_tile<15,3> on rows of 3 channels at 2^16 samples (3.26 GB, "
+                 "19 output tiles), scaled by the output tiles to this 2^18-sample launch (212 tiles)"),
+}
 
 
 def match_pulses(cands, pulses, dms):
