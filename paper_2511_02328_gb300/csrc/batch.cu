@@ -134,10 +134,17 @@ static void free_batch(af_batch_t b)
 static int setup_pairs(af_batch_t b)
 {
     size_t need = 0;
-    for (Beam& x : b->beams)
-        if (x.plan->pairs.ok) need = std::max(need, af_pairs_bytes(x.plan, x.nout));
-    if (need == 0) return af_set_error(AF_EINVAL, "batch: no beam can use pair rows");
-    need = std::min(need, kPairsMax);
+    std::vector<bool> use(b->beams.size(), false);
+    for (size_t i = 0; i < b->beams.size(); i++) {
+        Beam& x = b->beams[i];
+        if (!x.plan->pairs.ok) continue;
+        int64_t L = 0;  // the beam's fastest group size within the largest buffer
+        if (int rc = af_pairs_pick(x.plan, x.nout, true, kPairsMax, &L)) return rc;
+        if (L <= 0) continue;
+        use[i] = true;
+        need = std::max(need, std::min(af_pairs_bytes(x.plan, x.nout), kPairsMax));
+    }
+    if (need == 0) return af_set_error(AF_EINVAL, "batch: no beam gains from group rows");
     if (!b->d_rows) {
         if (cudaMalloc(&b->d_rows, need) != cudaSuccess) {
             cudaGetLastError();
@@ -146,9 +153,9 @@ static int setup_pairs(af_batch_t b)
         }
         b->rows_bytes = need;
     }
-    for (Beam& x : b->beams)
-        if (x.plan->pairs.ok)  // attaches where pair rows are expected to beat the channel kernel
-            if (int rc = af_pairs_attach(x.plan, b->d_rows, b->rows_bytes, x.nout))
+    for (size_t i = 0; i < b->beams.size(); i++)
+        if (use[i])
+            if (int rc = af_pairs_attach(b->beams[i].plan, b->d_rows, b->rows_bytes, b->beams[i].nout))
                 return rc == AF_ENOBUFS ? af_set_error(AF_EINVAL, "batch: shared row buffer too small") : rc;
     b->shape = kPairs;
     return AF_OK;

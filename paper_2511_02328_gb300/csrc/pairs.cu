@@ -707,11 +707,11 @@ static int64_t rows_elems(const af_pair_tables* T, int64_t L)
 }
 
 // Time block length for nout outputs within the budget (0: pairs not usable).
-static int64_t block_len(const af_pair_tables* T, int64_t nout)
+static int64_t block_len(const af_pair_tables* T, int64_t nout, size_t max_bytes = SIZE_MAX)
 {
     if (!T->ok || nout <= 0) return 0;
     const int64_t tiles = (nout + kPTTE - 1) / kPTTE;
-    const int64_t cap = (int64_t)(T->budget / 2);
+    const int64_t cap = (int64_t)(std::min(T->budget, max_bytes) / 2);
     int64_t lo = kMinTiles, hi = tiles;
     if (rows_elems(T, lo * kPTTE) > cap) return 0;
     if (lo >= hi) return hi * kPTTE;
@@ -797,13 +797,15 @@ static int pairs_release(af_pair_tables* T)
     return AF_OK;
 }
 
-// Reserves the group rows for nout outputs: of the group sizes (2 only
-// unless larger groups are allowed; AFGB_PAIR_GROUP=2|3|4 restricts), the one
-// predicted fastest, if it beats the channel tile kernel
-// (AFGB_DEDISP_KERNEL=pairs skips that comparison); it becomes p->pairs.
-// Otherwise nothing is reserved.
-int af_pairs_reserve(af_plan_t p, int64_t nout, bool search, bool allow_larger)
+// Picks the group rows for nout outputs: of the group sizes (2 only unless
+// larger groups are allowed; AFGB_PAIR_GROUP=2|3|4 restricts), the one
+// predicted fastest within max_bytes of rows, if it beats the channel tile
+// kernel (AFGB_DEDISP_KERNEL=pairs skips that comparison); it becomes
+// p->pairs (a previously picked set gives up its buffer).  *L gets its time
+// block; 0 when nothing suits.
+int af_pairs_pick(af_plan_t p, int64_t nout, bool allow_larger, size_t max_bytes, int64_t* L)
 {
+    *L = 0;
     af_pair_tables* cand[3] = {&p->pairs, &p->alt[0], &p->alt[1]};
     int best = -1;
     double best_t = 0;
@@ -811,13 +813,13 @@ int af_pairs_reserve(af_plan_t p, int64_t nout, bool search, bool allow_larger)
     for (int k = 0; k < 3; k++) {
         const af_pair_tables* T = cand[k];
         if (!T->ok || (T->G != 2 && !allow_larger) || (p->force_group && T->G != p->force_group)) continue;
-        const int64_t L = block_len(T, nout);
-        if (L <= 0) continue;
-        const double t = rows_cost(p, T, nout, L);
+        const int64_t Lk = block_len(T, nout, max_bytes);
+        if (Lk <= 0) continue;
+        const double t = rows_cost(p, T, nout, Lk);
         if (best < 0 || t < best_t) {
             best = k;
             best_t = t;
-            best_L = L;
+            best_L = Lk;
         }
     }
     if (best < 0) return AF_OK;
@@ -827,6 +829,17 @@ int af_pairs_reserve(af_plan_t p, int64_t nout, bool search, bool allow_larger)
         if (int rc = pairs_release(&p->pairs)) return rc;
         std::swap(p->pairs, *cand[best]);
     }
+    *L = best_L;
+    return AF_OK;
+}
+
+// Reserves the picked group rows: the row buffer and the layouts of
+// af_dedisperse and (with `search`) af_search.  Nothing when none suits.
+int af_pairs_reserve(af_plan_t p, int64_t nout, bool search, bool allow_larger, size_t max_bytes)
+{
+    int64_t best_L = 0;
+    if (int rc = af_pairs_pick(p, nout, allow_larger, max_bytes, &best_L)) return rc;
+    if (best_L <= 0) return AF_OK;
     af_pair_tables* T = &p->pairs;
     if (best_L > T->lay[0].L)
         if (int rc = pairs_layout(p, 0, best_L)) return rc;

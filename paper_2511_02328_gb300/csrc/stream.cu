@@ -311,13 +311,21 @@ extern "C" int af_stream_open(af_stream_t* out, const af_stream_cfg_t* cfg)
                               (size_t)s->ndm * sizeof(af_rowstats_t) + (size_t)s->cap * sizeof(af_cand_t) + 64;
     const size_t beam_bytes = (size_t)s->nchan * (size_t)std::max<int64_t>(s->dmax, 1);
     size_t budget = cfg->hbm_budget;
-    // the pair-row buffer, where the plan uses pair rows and the budget holds it with one slot
+    // the group-row buffer, where the plan uses group rows: the fastest group
+    // size whose buffer the budget holds next to the beam state and one slot
     size_t rows = 0;
     if (p->pairs.ok && !p->force_tile && !p->force_simple) {
-        rows = af_pairs_reserved_bytes(p, s->hop);
-        if (budget && budget < beam_bytes * s->nbeams + slot_bytes + rows) rows = 0;
+        const size_t fixed = beam_bytes * s->nbeams + slot_bytes;
+        if (!budget || budget > fixed) {
+            if ((rc = af_pairs_reserve(p, s->hop, false, true, budget ? budget - fixed : SIZE_MAX))) {
+                free_stream(s);
+                return rc;
+            }
+            s->pairs = af_dedisp_uses_pairs(p, s->hop);
+            if (s->pairs) rows = p->pairs.ps_bytes;
+        }
     }
-    if (!rows && !p->tile.fits) {
+    if (!s->pairs && !p->tile.fits) {
         free_stream(s);
         return af_set_error(AF_EINVAL, "af_stream_open: DM grid too coarse for the tile kernel");
     }
@@ -329,13 +337,6 @@ extern "C" int af_stream_open(af_stream_t* out, const af_stream_cfg_t* cfg)
                                 budget, slot_bytes, beam_bytes * s->nbeams);
         }
         nslots = std::min<int64_t>(nslots, (budget - beam_bytes * s->nbeams - rows) / slot_bytes);
-    }
-    if (rows) {
-        if ((rc = af_pairs_reserve(p, s->hop, false, false))) {
-            free_stream(s);
-            return rc;
-        }
-        s->pairs = af_dedisp_uses_pairs(p, s->hop);
     }
     s->max_batch = nslots;
     s->slots.resize(nslots);
