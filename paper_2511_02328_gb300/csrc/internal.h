@@ -98,7 +98,7 @@ struct af_pair_tables {
     bool ps_owned = true;          // false: a buffer shared by a batch's plans
     // Row-buffer layouts made by the reservation calls: 0 for af_dedisperse
     // (the longest time block the budget allows), 1 for af_search (at least
-    // four blocks, so that the input copy overlaps the work).
+    // eight blocks, so that the input copy overlaps the work).
     struct Layout {
         int64_t L = 0, maxlen = 0;     // outputs per time block, longest row
         int4* d_pinfo = nullptr;       // [np] first row, rows, range start ub, range length

@@ -844,10 +844,11 @@ int af_pairs_reserve(af_plan_t p, int64_t nout, bool search, bool allow_larger, 
     if (best_L > T->lay[0].L)
         if (int rc = pairs_layout(p, 0, best_L)) return rc;
     if (search) {
-        // at least four time blocks, so that the input copy overlaps the work
+        // at least eight time blocks, so that the input copy overlaps the work
+        // (the first block waits for its outputs + Dmax of input)
         const int64_t tiles = (nout + kPTTE - 1) / kPTTE;
-        const int64_t L4 = std::min(T->lay[0].L, (tiles + 3) / 4 * kPTTE);
-        if (int rc = pairs_layout(p, 1, L4)) return rc;
+        const int64_t L8 = std::min(T->lay[0].L, (tiles + 7) / 8 * kPTTE);
+        if (int rc = pairs_layout(p, 1, L8)) return rc;
     }
     return AF_OK;
 }

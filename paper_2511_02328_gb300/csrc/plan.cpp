@@ -601,8 +601,8 @@ extern "C" int af_search(af_plan_t p, const uint8_t* h_in, int64_t nsamp, const 
     if (int rc = af_check_widths(p, widths, nw, nout, &w)) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if (af_dedisp_uses_pairs(p, nout)) {
-        // Pair rows: the outputs in the search layout's time blocks (at least
-        // four); each block's rows and tiles run as soon as its input columns
+        // Group rows: the outputs in the search layout's time blocks (at least
+        // eight); each block's rows and tiles run as soon as its input columns
         // (block end + Dmax) are in, overlapping the rest of the copy.
         const int ly = p->pairs.lay[1].L > 0 ? 1 : 0;
         const int64_t L = p->pairs.lay[ly].L;
@@ -618,7 +618,7 @@ extern "C" int af_search(af_plan_t p, const uint8_t* h_in, int64_t nsamp, const 
                                           (size_t)p->nchan, cudaMemcpyHostToDevice, p->ws_copy));
                 col = need;
             }
-            cudaEvent_t ev = p->ws_ev[k % 4];
+            cudaEvent_t ev = p->ws_ev[k % 4];  // an event is reused once the stream has waited on it
             AF_CUDA(cudaEventRecord(ev, p->ws_copy));
             AF_CUDA(cudaStreamWaitEvent(s, ev, 0));
             if (int rc = af_launch_pairs_block(p, p->ws_in, nsamp, nout, p->ws_plane, p->d_stats, s, ly, T0)) return rc;
