@@ -203,7 +203,7 @@ STREAM_WORKLOAD = ("streaming: 19 beams, 4096 ch x 49.152 us uint8, windows of 2
 
 
 SB_N0, SB_NSUB = 8, 64
-# DRAM read + write bytes of one stage-2 pair-row tile launch (k_pair_tile) on this workload, from an ncu
+# DRAM read + write bytes of one stage-2 group-row tile launch (k_pair_tile) on this workload, from an ncu
 # capture of the same kernel (dram__bytes_read.sum + dram__bytes_write.sum); None until captured, and reset
 # to None whenever the kernel changes
 PAIR_TILE_TRAFFIC = {   # keyed by channels per row: (bytes per launch, basis), from a capture of the current kernel
@@ -407,7 +407,7 @@ def run_batch(args, dev, stream):
     ncand = sum(_lib.af_batch_candidates(batch, i, 1 << 16)[1] for i in range(len(beams)))
 
     # the same searches one plan at a time, writing into the batch's buffers (the channel tile kernel, the
-    # batch's own kernel family: 19 pair-row buffers would not fit the device)
+    # batch's own kernel family: 19 group-row buffers would not fit the device)
     plans, bufs = [], []
     for i, bm in enumerate(beams):
         plans.append(Plan(bm["nchan"], bm["f_lo"], bm["f_hi"], bm["tsamp"], bm["dm_list"]))
@@ -438,7 +438,7 @@ def run_batch(args, dev, stream):
         "autotune_cached": bool(cached), "build_s": build_s, "candidates": int(ncand), "steps": steps,
         "alu_frac_whole_batch": work / (ms_batch * 1e-3) / alu_peak,
         "note": "ms_per_batch covers the dedispersion of all beams (tile_shape [nw, m]: one persistent "
-                "channel-tile launch; [15, 0]: beam after beam, pair rows sharing one row buffer where a beam's plan "
+                "channel-tile launch; [15, 0]: beam after beam, group rows sharing one row buffer where a beam's plan "
                 "uses them) plus every beam's S/N and candidates, one CUDA graph replay; one_plan_at_a_time runs the "
                 "channel tile kernel per beam; alu_frac is the batch's adds over 152 x 128 x max clock",
     }
@@ -713,9 +713,9 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     sp = stream.cuda_stream
     H = plan.handle
-    _lib.af_dedisperse_reserve(H, NSAMP)   # the pair-row buffer (setup, outside the timed region)
+    _lib.af_dedisperse_reserve(H, NSAMP)   # the group-row buffer (setup, outside the timed region)
     kern = plan.kernel()
-    # dedispersion (pair rows: stage 1 + stage 2; else one tile launch), rowconst, boxcar, candidates
+    # dedispersion (group rows: stage 1 + stage 2; else one tile launch), rowconst, boxcar, candidates
     launches_per_step = (5 if kern["path"] == "pairs" else 4)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]

@@ -238,7 +238,7 @@ int af_plan_subband_info(af_plan_t plan, int* n0, int* nsub, int* ncoarse, int32
  *  nsamp    samples per channel (row pitch of d_in), > Dmax
  *  d_plane  int32 [ndm][nout] output (row pitch nout)
  *  d_stats  optional af_rowstats_t [ndm] output (may be NULL)
- * Enqueued on `stream`.  Brute-force plans run the pair-row kernels once
+ * Enqueued on `stream`.  Brute-force plans run the group-row kernels once
  * af_dedisperse_reserve (or af_search_reserve) has reserved their row buffer,
  * else the channel tile kernel; both give the same plane. */
 /* Reserves the group-row buffer of a brute-force plan (af_plan_kernel path
@@ -251,15 +251,15 @@ int af_plan_subband_info(af_plan_t plan, int* n0, int* nsub, int* ncoarse, int32
  * default min(48 GiB, 1/5 of device memory)); later calls of any length run in
  * as many time blocks as they need.  Allocates and uploads synchronously (waits for the
  * device when it replaces a reservation); AF_OK without effect for plans that
- * cannot use pair rows.  AF_EINVAL if max_nsamp <= Dmax, AF_ENOMEM / AF_ECUDA
+ * cannot use group rows.  AF_EINVAL if max_nsamp <= Dmax, AF_ENOMEM / AF_ECUDA
  * on allocation failure.  Not a step of the paper's method: the same sum,
  * grouped. */
 int af_dedisperse_reserve(af_plan_t plan, int64_t max_nsamp);
 
-/* Stage timing of the pair-row path (measurement aid, not a step of the
+/* Stage timing of the group-row path (measurement aid, not a step of the
  * paper's method).  af_dedisperse_timing(plan, n) creates events for n call
  * slots (0 <= n <= 4096; 0 turns timing off) after waiting for the device;
- * every later af_dedisperse call on the pair-row path records, in slot
+ * every later af_dedisperse call on the group-row path records, in slot
  * (calls since then) mod n, events on its stream around stage 1 (row sums)
  * and stage 2 (tiles) of each of its first 8 time blocks.
  * af_dedisperse_times(plan, i, ...) waits for slot i's events and returns the
@@ -429,9 +429,9 @@ typedef struct {
 /* Builds the batch: one plan per beam, each beam's plane / S/N / candidate
  * buffers on the current device (AF_ENOBUFS if they need more than
  * hbm_budget bytes; 0 = no budget), and picks the dedispersion strategy by
- * timing every compiled tile shape and the pair-row strategy on these beams
+ * timing every compiled tile shape and the group-row strategy on these beams
  * (the beams' inputs must be valid device memory; their contents do not
- * matter).  The pair-row strategy takes a row buffer of at most 16 GiB
+ * matter).  The group-row strategy takes a row buffer of at most 16 GiB
  * (outside hbm_budget), freed again when another strategy wins.
  * With the environment variable AFGB_AUTOTUNE_CACHE naming a file, the
  * choice is cached there as JSON keyed by GPU name and beam shapes;
@@ -467,7 +467,7 @@ int af_batch_destroy(af_batch_t batch);
  * of Sec. 2.3, applied across chunks).  The overlap of each beam stays on the
  * device.  Requests are admitted into slots whose number the HBM budget sets;
  * a dispatcher thread runs every admitted window together (their
- * dedispersion -- window after window on pair rows, see
+ * dedispersion -- window after window on group rows, see
  * af_dedisperse_reserve, when the plan uses them and the budget holds the
  * row buffer next to one slot; else one persistent channel-tile launch --
  * then each window's S/N and candidates), so requests that arrive while
@@ -485,7 +485,7 @@ typedef struct {
     int nw;
     float thresh;
     int32_t cap;            /* candidates kept per window                       */
-    size_t hbm_budget;      /* bytes for slots + beam state (+ the pair-row buffer
+    size_t hbm_budget;      /* bytes for slots + beam state (+ the group-row buffer
                                when used); 0 = no limit                          */
     int max_slots;          /* upper bound on slots (0 = 4)                     */
     int timeout_ms;         /* af_stream_push: longest wait for a free slot;

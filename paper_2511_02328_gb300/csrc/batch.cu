@@ -6,7 +6,7 @@
 // strategies: one persistent channel-tile launch over all (beam, DM block,
 // time tile) items for each compiled tile shape (DM rows per block x outputs
 // per lane), and the beams one after another, each on its single-plan path
-// (pair rows, pairs.cu, sharing one row buffer, where the plan uses them);
+// (group rows, pairs.cu, sharing one row buffer, where the plan uses them);
 // each is timed on the batch itself, the fastest is kept and
 // cached in a JSON file (AFGB_AUTOTUNE_CACHE) keyed by the GPU name and the
 // beams' shapes.  af_batch_run replays a graph of: the dedispersion (with its
@@ -61,7 +61,7 @@ const Shape kShapes[] = {
     {15, 6, launch_persistent<15, 6>, set_attr<15, 6>},
 };
 constexpr int kNShapes = sizeof(kShapes) / sizeof(kShapes[0]);
-constexpr int kPairs = kNShapes;       // strategy index of beam after beam (pair rows where they apply)
+constexpr int kPairs = kNShapes;       // strategy index of beam after beam (group rows where they apply)
 constexpr size_t kPairsMax = (size_t)16 << 30;  // largest shared row buffer
 
 struct Beam {
@@ -96,7 +96,7 @@ struct af_batch_s {
     long long total = 0;
     int grid = 0;
     size_t smem = 0;
-    uint16_t* d_rows = nullptr;          // row buffer shared by the beams' plans (pair-row strategy)
+    uint16_t* d_rows = nullptr;          // row buffer shared by the beams' plans (group-row strategy)
     size_t rows_bytes = 0;
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
@@ -125,11 +125,11 @@ static void free_batch(af_batch_t b)
     delete b;
 }
 
-// The beam-after-beam strategy: every beam on its single-plan path, pair rows
+// The beam-after-beam strategy: every beam on its single-plan path, group rows
 // for the beams whose plans use them, all on one shared row buffer sized for
 // the largest such beam's full length (at most kPairsMax; the other beams, or
 // all of them past the cap, run in time blocks); the rest on the channel tile
-// kernel.  AF_EINVAL: no beam can use pair rows (the persistent strategies
+// kernel.  AF_EINVAL: no beam can use group rows (the persistent strategies
 // cover that case).
 static int setup_pairs(af_batch_t b)
 {
@@ -376,7 +376,7 @@ static int autotune(af_batch_t b)
     if (best < 0) return af_set_error(AF_EINVAL, "batch: no compiled tile shape fits these beams");
     if (best != kPairs && b->d_rows) {
         // the row buffer is not needed: detach nothing (the plans keep their
-        // layouts but never launch pair rows in this batch), free it
+        // layouts but never launch group rows in this batch), free it
         if (int r = af_cuda_check(cudaDeviceSynchronize(), "batch")) return r;
         for (Beam& x : b->beams) x.plan->pairs.lay[0].L = x.plan->pairs.lay[1].L = 0;
         cudaFree(b->d_rows);

@@ -73,8 +73,8 @@ struct af_sb_device {
     int cps = 0;                   // 32-channel chunks per subband
 };
 
-// ---------------------------------------------------------------- pair rows
-// Single-plan dedispersion through channel-pair rows (pairs.cu): host tables
+// ---------------------------------------------------------------- group rows
+// Single-plan dedispersion through channel-group rows (pairs.cu): host tables
 // (built once per plan), device tables, and the row buffer of one time block.
 struct af_pair_tables {
     bool ok = false;               // the plan can use this path
@@ -154,7 +154,7 @@ struct af_plan_s {
     bool force_simple = false;             // use the fallback kernel (AFGB_DEDISP_KERNEL=simple)
     bool force_brute = false;              // subband plans: brute-force tile kernel on the
                                            // effective delays (AFGB_DEDISP_KERNEL=brute)
-    bool force_tile = false;               // byte tile kernel even where pair rows apply
+    bool force_tile = false;               // byte tile kernel even where group rows apply
                                            // (AFGB_DEDISP_KERNEL=tile)
     bool force_pairs = false;              // group rows wherever they apply, without the cost
                                            // comparison (AFGB_DEDISP_KERNEL=pairs)

@@ -1,36 +1,39 @@
 // pairs.cu -- exact brute-force dedispersion (Sec. 2.3) of single plans
-// through shared channel-pair rows.
+// through shared channel-group rows.
 //
 //   Y[d][t] = sum_c X[c][t + D[d][c]]
-//           = sum_q P(q, delta_q(d))[t + D[d][2q]],
-//   P(q, delta)[u] = X[2q][u] + X[2q+1][u + delta],
-//   delta_q(d)     = D[d][2q+1] - D[d][2q].
+//           = sum_q P(q, delta_q(d))[t + D[d][Gq]],
+//   P(q, delta)[u]   = sum_{i<G} X[Gq+i][u + delta_i],  delta_0 = 0,
+//   delta_q(d)_i     = D[d][Gq+i] - D[d][Gq],
 //
-// The same integer sum, grouped: two adjacent channels are added once per
-// distinct relative delay delta of the pair (a pair has a handful over the
-// whole DM range and one or two inside a block of neighbouring DMs), and the
-// DM sums then run over pair rows, half as many terms as channels.
+// for groups of G = 2, 3 or 4 adjacent channels (a short last group has zeros
+// for its missing channels).  The same integer sum, grouped: the channels of
+// a group are added once per distinct tuple of relative delays (a group has a
+// few dozen over the whole DM range and a few inside a block of neighbouring
+// DMs), and the DM sums then run over group rows, nchan / G terms.
 //
-// Stage 1 (k_pair_rows) writes every row P(q, delta) as uint16 for one time
-// block of L outputs (row element e is time ub + e, ub = (T0 + min_d D[d][2q])
-// rounded down to 8).
+// Stage 1 (k_group_rows<G>) writes every row P(q, delta) as uint16 for one
+// time block of L outputs; row g covers only the delays D[d][Gq] of the DMs
+// that use it (element e is time T0 + B_g + e, B_g their smallest delay
+// rounded down to 16).
 //
 // Stage 2 (k_pair_tile) is a tile kernel over rows: a block takes NW DM rows
 // (one consumer warp each, DMs ascending) and TTE = 1016 outputs; a producer
-// warp streams the block's rows through an NS-deep shared-memory ring, up to
-// SL rows per stage (whole pairs), one bulk async copy per row window plus one
-// for the chunk's consumer tables of (stage slot, offset) per pair, which the
-// host computes once (tiles start at multiples of 8, so no offset depends on
-// the tile).  Lane L
+// warp streams the block's row windows (one per block and row) through an
+// NS-deep shared-memory ring, up to 32 windows of whole groups packed back to
+// back per stage, one bulk async copy per window plus one for the chunk's
+// consumer tables of (window, offset) per group, which the host computes once
+// (tiles start at multiples of 8, so no offset depends on the tile).  Lane L
 // of a consumer warp owns outputs 2 (L + 32 m) + k, m < 16, k < 2: one
 // aligned 32-bit shared load brings the two 16-bit samples of a group, so the
-// pairs are bucketed by the parity r of the sample offset; one IADD3 adds two
-// pairs' words into the 16-bit lanes of the bucket's accumulator (at most
-// 128 pairs of 510 between folds); a fold re-aligns bucket 1 by one sample
-// (one lane shuffle) into the 32-bit output sums.
+// groups are bucketed by the parity r of the sample offset; one IADD3 adds two
+// rows' words into the 16-bit lanes of the bucket's accumulator (at most
+// 65535 / (255 G) rows between folds); a fold re-aligns bucket 1 by one
+// sample (one lane shuffle) into the 32-bit output sums.
 //
-// Every wait is bounded (the tile kernel's error flag); the host tables are
-// built once per plan and the row buffer is sized per call from a budget.
+// Every wait is bounded (the tile kernel's error flag).  The host tables of
+// every group size are built once per plan; a reservation picks the group size
+// by a cost model and sizes the row buffer from a budget.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -56,7 +59,7 @@ constexpr int kPTABW = 40;          // ints per (stage, warp) table: 2 starts, 2
 constexpr uint32_t kPWait = 1u << 24;
 constexpr int kET = 4096;           // stage 1: row samples per block
 constexpr int kS1T = 256;
-constexpr int kMaxDr = 32768;       // stage 1: largest delta range of a pair
+constexpr int kMaxDr = 32768;       // stage 1: largest range of one relative delay over a group's rows
 constexpr int kMinTiles = 8;        // smallest useful time block, in tiles
 
 inline int64_t r8(int64_t x) { return (x + 7) & ~(int64_t)7; }
@@ -334,7 +337,7 @@ struct PairTile {
                 const int beg = r == 0 ? h.x : h.y;
                 const int n = r == 0 ? h.z : h.w;
                 const int* o = tb + 4 + beg;
-                // the next pair's offsets one iteration ahead (reads past the
+                // the next two rows' offsets one iteration ahead (reads past the
                 // bucket stay inside the table and are never used)
                 int2 nx = *reinterpret_cast<const int2*>(o);
                 int i = 0;
@@ -706,7 +709,7 @@ static int64_t rows_elems(const af_pair_tables* T, int64_t L)
     return n;
 }
 
-// Time block length for nout outputs within the budget (0: pairs not usable).
+// Time block length for nout outputs within the budget (0: the rows do not fit).
 static int64_t block_len(const af_pair_tables* T, int64_t nout, size_t max_bytes = SIZE_MAX)
 {
     if (!T->ok || nout <= 0) return 0;
@@ -741,7 +744,7 @@ static int pairs_layout(af_plan_t p, int k, int64_t L)
         cudaFree(T->d_ps);
         T->d_ps = nullptr;
         T->ps_bytes = 0;
-        if (cudaError_t e = cudaMalloc(&T->d_ps, (size_t)need * 2)) return af_cuda_check(e, "pair rows");
+        if (cudaError_t e = cudaMalloc(&T->d_ps, (size_t)need * 2)) return af_cuda_check(e, "group rows");
         T->ps_bytes = (size_t)need * 2;
     }
     std::vector<int64_t> rowoff(T->nrows), soff(T->h_srow.size());
@@ -869,7 +872,7 @@ size_t af_pairs_bytes(af_plan_t p, int64_t nout)
 int af_pairs_attach(af_plan_t p, uint16_t* buf, size_t bytes, int64_t nout)
 {
     af_pair_tables* T = &p->pairs;
-    if (!T->ok) return af_set_error(AF_EINVAL, "pairs: plan cannot use pair rows");
+    if (!T->ok) return af_set_error(AF_EINVAL, "pairs: plan cannot use group rows");
     T->lay[0].L = T->lay[1].L = 0;  // until attached: the channel tile kernel
     const int64_t tiles = (nout + kPTTE - 1) / kPTTE;
     const int64_t cap = (int64_t)(bytes / 2);
@@ -921,7 +924,7 @@ int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64
         k_group_rows<2><<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, ly.d_pinfo, T->d_gdr, T->d_rdelta,
                                                       ly.d_rinfo, ly.d_rowoff, T0, etiles, rows_wstride(T->maxdr),
                                                       T->d_ps);
-    if (int rc = af_cuda_check(cudaGetLastError(), "pair rows launch")) return rc;
+    if (int rc = af_cuda_check(cudaGetLastError(), "group rows launch")) return rc;
     if (mid) AF_CUDA(cudaEventRecord(*mid, s));
     PairArgs a;
     a.PS = T->d_ps;

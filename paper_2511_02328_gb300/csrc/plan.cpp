@@ -584,7 +584,7 @@ extern "C" int af_search_reserve(af_plan_t p, int64_t max_nsamp, int32_t cap)
         }
     p->ws_nsamp = max_nsamp;
     p->ws_cap = cap;
-    return af_pairs_reserve(p, nout, true);  // the pair-row buffers, where that path applies
+    return af_pairs_reserve(p, nout, true);  // the group-row buffers, where that path applies
 }
 
 extern "C" int af_search(af_plan_t p, const uint8_t* h_in, int64_t nsamp, const int32_t* widths, int nw,

@@ -10,7 +10,7 @@
 // Requests (one window of one beam) are admitted into slots; the number of
 // slots is set by an HBM budget.  A dispatcher thread takes every window whose
 // input is on the device and runs them together -- their dedispersion (on
-// pair rows, pairs.cu, window after window on the plan's row buffer where the
+// group rows, pairs.cu, window after window on the plan's row buffer where the
 // plan uses them and the budget holds the buffer; else one persistent
 // channel-tile launch over all their (DM block, time tile) items), then each
 // window's boxcar S/N and candidate compaction, then the candidates' copy to
@@ -108,7 +108,7 @@ struct af_stream_s {
     int* d_err = nullptr;
     int grid = 0;
     size_t smem = 0;
-    bool pairs = false;                  // windows dedispersed on pair rows
+    bool pairs = false;                  // windows dedispersed on group rows
     int max_batch = 0;
     // inline classification of held windows
     cudaStream_t cstream = nullptr;

@@ -71,15 +71,15 @@ class Plan:
         return _lib.af_plan_nout(self.handle, nsamp)
 
     def reserve(self, nsamp):
-        """Reserve the pair-row buffer for inputs of up to nsamp samples (no-op for
-        plans that cannot use pair rows, or when already reserved that far)."""
+        """Reserve the group-row buffer for inputs of up to nsamp samples (no-op for
+        plans that cannot use group rows, or when already reserved that far)."""
         if nsamp > getattr(self, "_reserved", 0):
             _lib.af_dedisperse_reserve(self.handle, nsamp)
             self._reserved = nsamp
 
     def dedisperse(self, x, plane=None, stats=None, stream=None):
         """x: uint8 cuda tensor [nchan][nsamp] -> int32 plane [ndm][nout].  Reserves
-        the pair-row buffer first when nsamp exceeds the reservation (a
+        the group-row buffer first when nsamp exceeds the reservation (a
         synchronous allocation; the C call itself never allocates)."""
         assert x.dtype == torch.uint8 and x.is_cuda and x.is_contiguous() and x.shape[0] == self.nchan
         nsamp = x.shape[1]

@@ -74,14 +74,14 @@ def _check_against_oracle(batch, xs):
 @pytest.mark.parametrize("strategy", ["auto", "tile", "pairs"])
 def test_batch_matches_oracle_and_single_beam(strategy, monkeypatch):
     """Every dedispersion strategy of the batch (the autotuner's pick, the
-    persistent tile kernel, pair rows beam after beam) gives each beam's
+    persistent tile kernel, group rows beam after beam) gives each beam's
     oracle plane and S/N and the single-beam host search's candidates."""
     from paper_2511_02328_gb300 import _lib
     from paper_2511_02328_gb300.search import Plan
     if strategy != "auto":
         monkeypatch.setenv("AFGB_BATCH_STRATEGY", strategy)
     if strategy == "pairs":
-        monkeypatch.setenv("AFGB_DEDISP_KERNEL", "pairs")   # every beam that can, on pair rows
+        monkeypatch.setenv("AFGB_DEDISP_KERNEL", "pairs")   # every beam that can, on group rows
     xs = _make(1)
     xs_dev = [torch.from_numpy(x).cuda() for x in xs]
     batch = _build(xs_dev)

@@ -375,7 +375,7 @@ def test_pair_rows_several_time_blocks(nchan, f_lo, f_hi, G, monkeypatch):
 
 
 def test_pair_rows_forced_and_default_choice(c1_data, monkeypatch):
-    """AFGB_DEDISP_KERNEL=pairs puts the 256-channel workload on pair rows;
+    """AFGB_DEDISP_KERNEL=pairs puts the 256-channel workload on group rows;
     without it the reservation keeps whichever path its cost model prefers,
     and both give the oracle's plane."""
     x, D, Y, _, _ = c1_data

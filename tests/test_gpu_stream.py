@@ -76,7 +76,7 @@ def _drain(s, n, keep_planes=False):
 
 @pytest.mark.parametrize("kernel", ["auto", "pairs", "tile"])
 def test_concatenated_windows_equal_one_shot(kernel, monkeypatch):
-    """On every dedispersion path of the engine (its default choice, pair rows
+    """On every dedispersion path of the engine (its default choice, group rows
     forced, the persistent channel-tile kernel forced)."""
     from paper_2511_02328_gb300 import _lib
     from paper_2511_02328_gb300.search import Plan
