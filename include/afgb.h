@@ -255,6 +255,11 @@ int af_plan_subband_info(af_plan_t plan, int* n0, int* nsub, int* ncoarse, int32
  * on allocation failure.  Not a step of the paper's method: the same sum,
  * grouped. */
 int af_dedisperse_reserve(af_plan_t plan, int64_t max_nsamp);
+/* Device bytes af_dedisperse_reserve(plan, max_nsamp) would allocate (the
+ * group-row buffer; 0 where the channel tile kernel serves the plan), without
+ * allocating or changing anything.  AF_EINVAL if max_nsamp <= Dmax or bytes
+ * is NULL. */
+int af_dedisperse_workspace_size(af_plan_t plan, int64_t max_nsamp, size_t* bytes);
 
 /* Stage timing of the group-row path (measurement aid, not a step of the
  * paper's method).  af_dedisperse_timing(plan, n) creates events for n call
@@ -394,6 +399,10 @@ int af_cluster(af_plan_t plan, af_cand_t* h_cands, int32_t n, double dm_tol,
  * cap.  Requires af_search_reserve(plan, >= nsamp, >= cap) first (AF_ENOBUFS
  * otherwise). */
 int af_search_reserve(af_plan_t plan, int64_t max_nsamp, int32_t cap);
+/* Device bytes af_search_reserve(plan, max_nsamp, cap) would allocate: the
+ * input, plane, S/N, best-width and candidate buffers and the group-row
+ * buffer; allocates nothing.  AF_EINVAL as af_search_reserve, or bytes NULL. */
+int af_search_workspace_size(af_plan_t plan, int64_t max_nsamp, int32_t cap, size_t* bytes);
 int af_search(af_plan_t plan, const uint8_t* h_in, int64_t nsamp,
               const int32_t* widths, int nw, float thresh,
               af_cand_t* h_out, int32_t cap, int32_t* h_count, void* stream);

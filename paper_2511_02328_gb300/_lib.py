@@ -69,6 +69,8 @@ SIGNATURES = {
     "af_plan_check": [_P],
     "af_plan_kernel": [_P, _P, _P, _P, _P],
     "af_dedisperse_reserve": [_P, _I64],
+    "af_dedisperse_workspace_size": [_P, _I64, _P],
+    "af_search_workspace_size": [_P, _I64, _I32, _P],
     "af_dedisperse_timing": [_P, _I],
     "af_dedisperse_times": [_P, _I, _P, _P, _P, _P],
     "af_dedisperse": [_P, _P, _I64, _P, _P, _P],
@@ -249,6 +251,18 @@ def af_plan_kernel(plan):
 
 def af_dedisperse_reserve(plan, max_nsamp):
     _check(lib().af_dedisperse_reserve(plan, max_nsamp), "af_dedisperse_reserve")
+
+
+def af_dedisperse_workspace_size(plan, max_nsamp):
+    b = ctypes.c_size_t()
+    _check(lib().af_dedisperse_workspace_size(plan, max_nsamp, ctypes.byref(b)), "af_dedisperse_workspace_size")
+    return b.value
+
+
+def af_search_workspace_size(plan, max_nsamp, cap):
+    b = ctypes.c_size_t()
+    _check(lib().af_search_workspace_size(plan, max_nsamp, cap, ctypes.byref(b)), "af_search_workspace_size")
+    return b.value
 
 
 def af_dedisperse_timing(plan, ncalls):

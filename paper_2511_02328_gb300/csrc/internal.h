@@ -120,6 +120,7 @@ int64_t af_pairs_block(af_plan_t p, int64_t nout);
 int af_pairs_reserve(af_plan_t p, int64_t nout, bool search, bool allow_larger = true,
                      size_t max_bytes = SIZE_MAX);
 int af_pairs_pick(af_plan_t p, int64_t nout, bool allow_larger, size_t max_bytes, int64_t* L);
+size_t af_pairs_workspace(af_plan_t p, int64_t nout);  // row-buffer bytes a reservation would allocate
 int af_launch_pairs(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,
                     af_rowstats_t* d_stats, cudaStream_t s);
 // Stage 1 + stage 2 of the time block starting at T0 (a multiple of the

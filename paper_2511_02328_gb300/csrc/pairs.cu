@@ -806,10 +806,12 @@ static int pairs_release(af_pair_tables* T)
 // kernel (AFGB_DEDISP_KERNEL=pairs skips that comparison); it becomes
 // p->pairs (a previously picked set gives up its buffer).  *L gets its time
 // block; 0 when nothing suits.
-int af_pairs_pick(af_plan_t p, int64_t nout, bool allow_larger, size_t max_bytes, int64_t* L)
+// The candidate (0: p->pairs, 1, 2: p->alt) and time block the pick would
+// take, or -1; changes nothing.
+static int pairs_choose(af_plan_t p, int64_t nout, bool allow_larger, size_t max_bytes, int64_t* L)
 {
     *L = 0;
-    af_pair_tables* cand[3] = {&p->pairs, &p->alt[0], &p->alt[1]};
+    const af_pair_tables* cand[3] = {&p->pairs, &p->alt[0], &p->alt[1]};
     int best = -1;
     double best_t = 0;
     int64_t best_L = 0;
@@ -825,15 +827,32 @@ int af_pairs_pick(af_plan_t p, int64_t nout, bool allow_larger, size_t max_bytes
             best_L = Lk;
         }
     }
-    if (best < 0) return AF_OK;
+    if (best < 0) return -1;
     const bool tile = p->tile.ns1 > 0;  // else the one-thread-per-output kernel
-    if (!p->force_pairs && tile && best_t >= (double)p->ndm * p->nchan * (double)nout / kTileAddps) return AF_OK;
+    if (!p->force_pairs && tile && best_t >= (double)p->ndm * p->nchan * (double)nout / kTileAddps) return -1;
+    *L = best_L;
+    return best;
+}
+
+int af_pairs_pick(af_plan_t p, int64_t nout, bool allow_larger, size_t max_bytes, int64_t* L)
+{
+    const int best = pairs_choose(p, nout, allow_larger, max_bytes, L);
+    if (best < 0) return AF_OK;
     if (best > 0) {
+        af_pair_tables* cand[3] = {&p->pairs, &p->alt[0], &p->alt[1]};
         if (int rc = pairs_release(&p->pairs)) return rc;
         std::swap(p->pairs, *cand[best]);
     }
-    *L = best_L;
     return AF_OK;
+}
+
+size_t af_pairs_workspace(af_plan_t p, int64_t nout)
+{
+    int64_t L = 0;
+    const int best = pairs_choose(p, nout, true, SIZE_MAX, &L);
+    if (best < 0) return 0;
+    const af_pair_tables* cand[3] = {&p->pairs, &p->alt[0], &p->alt[1]};
+    return 2 * (size_t)rows_elems(cand[best], L);
 }
 
 // Reserves the picked group rows: the row buffer and the layouts of

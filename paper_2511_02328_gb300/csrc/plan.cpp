@@ -551,6 +551,28 @@ extern "C" int af_cluster(af_plan_t p, af_cand_t* h_cands, int32_t n, double dm_
     return AF_OK;
 }
 
+extern "C" int af_dedisperse_workspace_size(af_plan_t p, int64_t max_nsamp, size_t* bytes)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    if (!bytes) return af_set_error(AF_EINVAL, "af_dedisperse_workspace_size: NULL output");
+    int64_t nout;
+    if (int rc = check_nout(p, max_nsamp, &nout)) return rc;
+    *bytes = p->sb_nsub == 0 ? af_pairs_workspace(p, nout) : 0;
+    return AF_OK;
+}
+
+extern "C" int af_search_workspace_size(af_plan_t p, int64_t max_nsamp, int32_t cap, size_t* bytes)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    if (!bytes || cap < 1) return af_set_error(AF_EINVAL, "af_search_workspace_size: NULL output or cap < 1");
+    int64_t nout;
+    if (int rc = check_nout(p, max_nsamp, &nout)) return rc;
+    const size_t npl = (size_t)p->ndm * (size_t)nout;
+    *bytes = (size_t)p->nchan * (size_t)max_nsamp + npl * 9 + (size_t)cap * sizeof(af_cand_t) + 16 +
+             (p->sb_nsub == 0 ? af_pairs_workspace(p, nout) : 0);
+    return AF_OK;
+}
+
 extern "C" int af_dedisperse_reserve(af_plan_t p, int64_t max_nsamp)
 {
     if (int rc = af_check_plan(p)) return rc;

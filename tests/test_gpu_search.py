@@ -449,3 +449,31 @@ def test_diag_int_rates_plausible():
     nominal = nsm * 128 * 2.07e9
     assert 0.1 * nominal < add <= 1.05 * nominal
     assert 0.05 * nominal < pattern <= 1.05 * add
+
+
+def test_workspace_sizes_match_reservations(c1_data):
+    """af_dedisperse_workspace_size / af_search_workspace_size report what the
+    reservations then take from the device (allocation granularity aside),
+    without allocating themselves."""
+    from paper_2511_02328_gb300 import _lib
+    x, D, Y, _, _ = c1_data
+    nsamp = x.shape[1]
+    p = _plan(C1)
+    torch.cuda.synchronize()
+    f0 = torch.cuda.mem_get_info()[0]
+    want = _lib.af_dedisperse_workspace_size(p.handle, nsamp)
+    assert torch.cuda.mem_get_info()[0] == f0
+    _lib.af_dedisperse_reserve(p.handle, nsamp)
+    used = f0 - torch.cuda.mem_get_info()[0]
+    assert want <= used <= want + (64 << 20)
+    assert (want > 0) == (p.kernel()["path"] == "pairs")
+    q = _plan(C1)
+    s_want = _lib.af_search_workspace_size(q.handle, nsamp, 1024)
+    f1 = torch.cuda.mem_get_info()[0]
+    _lib.af_search_reserve(q.handle, nsamp, 1024)
+    s_used = f1 - torch.cuda.mem_get_info()[0]
+    assert s_want <= s_used <= s_want + (128 << 20)
+    with pytest.raises(_lib.AFError):
+        _lib.af_dedisperse_workspace_size(p.handle, int(D.max()))     # nsamp <= Dmax
+    p.close()
+    q.close()
