@@ -403,6 +403,15 @@ int af_search_reserve(af_plan_t plan, int64_t max_nsamp, int32_t cap);
  * input, plane, S/N, best-width and candidate buffers and the group-row
  * buffer; allocates nothing.  AF_EINVAL as af_search_reserve, or bytes NULL. */
 int af_search_workspace_size(af_plan_t plan, int64_t max_nsamp, int32_t cap, size_t* bytes);
+/* Phase timing of af_search (measurement aid, not a step of the paper's
+ * method): with af_search_timing(plan, 1), every af_search call records
+ * events on its stream; af_search_times returns, for the last call, the time
+ * until the first time block's input was in (the wait of the copy), the
+ * dedispersion from there (with the rest of the copy overlapped) and the
+ * S/N + candidate kernels, in ms (outputs may be NULL).  AF_EINVAL if timing
+ * was never enabled. */
+int af_search_timing(af_plan_t plan, int enable);
+int af_search_times(af_plan_t plan, float* wait_ms, float* dedisp_ms, float* snr_ms);
 int af_search(af_plan_t plan, const uint8_t* h_in, int64_t nsamp,
               const int32_t* widths, int nw, float thresh,
               af_cand_t* h_out, int32_t cap, int32_t* h_count, void* stream);

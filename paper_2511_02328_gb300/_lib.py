@@ -72,6 +72,8 @@ SIGNATURES = {
     "af_dedisperse_workspace_size": [_P, _I64, _P],
     "af_search_workspace_size": [_P, _I64, _I32, _P],
     "af_dedisperse_timing": [_P, _I],
+    "af_search_timing": [_P, _I],
+    "af_search_times": [_P, _P, _P, _P],
     "af_dedisperse_times": [_P, _I, _P, _P, _P, _P],
     "af_dedisperse": [_P, _P, _I64, _P, _P, _P],
     "af_rowstats": [_P, _P, _I64, _P, _P],
@@ -263,6 +265,17 @@ def af_search_workspace_size(plan, max_nsamp, cap):
     b = ctypes.c_size_t()
     _check(lib().af_search_workspace_size(plan, max_nsamp, cap, ctypes.byref(b)), "af_search_workspace_size")
     return b.value
+
+
+def af_search_timing(plan, enable):
+    _check(lib().af_search_timing(plan, int(bool(enable))), "af_search_timing")
+
+
+def af_search_times(plan):
+    """(copy wait, dedispersion, S/N + candidates) of the last timed af_search call, ms."""
+    a, b, c = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+    _check(lib().af_search_times(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "af_search_times")
+    return a.value, b.value, c.value
 
 
 def af_dedisperse_timing(plan, ncalls):

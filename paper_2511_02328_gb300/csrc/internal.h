@@ -102,7 +102,8 @@ struct af_pair_tables {
     struct Layout {
         int64_t L = 0, maxlen = 0;     // outputs per time block, longest row
         int4* d_pinfo = nullptr;       // [np] first row, rows, range start ub, range length
-        int2* d_rinfo = nullptr;       // [nrows] row start - ub, row length
+        int2* d_rinfo = nullptr;       // [nrows] row start - ub, row length (rows of a group by start)
+        int* d_gmax = nullptr;         // [np] longest row of each group
         int64_t* d_rowoff = nullptr;   // [nrows] element offset in the row buffer
         int64_t* d_soff = nullptr;     // per slot: window offset for a time block's first tile
     } lay[2];
@@ -188,6 +189,11 @@ struct af_plan_s {
     int32_t* ws_count = nullptr;
     cudaStream_t ws_copy = nullptr;        // input copies of af_search, overlapped with dedispersion
     cudaEvent_t ws_ev[4] = {};             // one per copied time segment
+    // optional phase timing of af_search (af_search_timing): events on the
+    // caller's stream at the start, when the first block may run (its input
+    // is in), after the dedispersion, after S/N + candidates
+    bool ws_timing = false;
+    cudaEvent_t ws_tev[4] = {};
 };
 
 int af_check_plan(af_plan_t p);

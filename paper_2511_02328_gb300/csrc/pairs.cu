@@ -100,8 +100,9 @@ struct PairArgs {
 template <int G>
 __global__ void __launch_bounds__(kS1T)
 k_group_rows(const uint8_t* __restrict__ X, int64_t nsamp, int nchan, const int4* __restrict__ pinfo,
-             const int2* __restrict__ gdr, const int32_t* __restrict__ rdelta, const int2* __restrict__ rinfo,
-             const int64_t* __restrict__ rowoff, int64_t T0, int etiles, int wstride, uint16_t* __restrict__ PS)
+             const int* __restrict__ gmax, const int2* __restrict__ gdr, const int32_t* __restrict__ rdelta,
+             const int2* __restrict__ rinfo, const int64_t* __restrict__ rowoff, int64_t T0, int etiles, int wstride,
+             uint16_t* __restrict__ PS)
 {
     constexpr int K = G - 1;
     extern __shared__ __align__(16) uint8_t sm[];
@@ -110,6 +111,28 @@ k_group_rows(const uint8_t* __restrict__ X, int64_t nsamp, int nchan, const int4
     const int64_t e0 = (int64_t)(blockIdx.x % etiles) * kET;
     const int4 pi = __ldg(pinfo + q);
     if (e0 >= pi.w) return;
+    // the rows overlapping [e0, e0 + ET): rows are ordered by start, so they are
+    // those from the first starting after e0 - (longest row) to the first
+    // starting at or after e0 + ET (each still checked below)
+    int kbeg, kend;
+    {
+        const int lo_start = (int)(e0 - __ldg(gmax + q)), hi_start = (int)(e0 + kET);
+        int a = 0, b = pi.y;
+        while (a < b) {
+            const int m = (a + b) >> 1;
+            if (__ldg(rinfo + pi.x + m).x <= lo_start) a = m + 1;
+            else b = m;
+        }
+        kbeg = a;
+        b = pi.y;
+        while (a < b) {
+            const int m = (a + b) >> 1;
+            if (__ldg(rinfo + pi.x + m).x < hi_start) a = m + 1;
+            else b = m;
+        }
+        kend = a;
+    }
+    if (kbeg >= kend) return;
     const int c0 = G * q;
     const int64_t u0 = T0 + pi.z + e0;
     int dmn[K], bw[K], off[K + 1];
@@ -173,7 +196,7 @@ k_group_rows(const uint8_t* __restrict__ X, int64_t nsamp, int nchan, const int4
             ahi[j] = __byte_perm(a, 0u, 0x4342);  // samples 2, 3
         }
     }
-    for (int k = 0; k < pi.y; k++) {
+    for (int k = kbeg; k < kend; k++) {
         const int2 ri = __ldg(rinfo + pi.x + k);
         uint32_t lo[4], hi[4];
 #pragma unroll
@@ -451,6 +474,7 @@ void af_pairs_free(af_pair_tables* T)
     cudaFree(T->d_srec);
     for (auto& l : T->lay) {
         cudaFree(l.d_pinfo);
+        cudaFree(l.d_gmax);
         cudaFree(l.d_rinfo);
         cudaFree(l.d_rowoff);
         cudaFree(l.d_soff);
@@ -497,10 +521,18 @@ static int build_groups(af_plan_t p, int G, af_pair_tables* T)
             if (c0 + i < nchan) k[i - 1] = row[c0 + i] - row[c0];
         return k;
     };
+    // rows of a group are stored in order of their start B_g (so that the rows
+    // a stretch of samples overlaps are contiguous); rlook maps a tuple to its
+    // row (per group, sorted by tuple)
     std::vector<int32_t> rb(ng + 1, 0), rdelta, rB, rspan, ub(ng);
-    std::vector<Key> rkey;
+    std::vector<std::pair<Key, int32_t>> rlook;
     std::vector<int2> gdr((size_t)ng * K);
     std::vector<std::pair<Key, int32_t>> v(ndm);  // (tuple, D[d][Gq])
+    struct Row {
+        Key key;
+        int32_t B, span;
+    };
+    std::vector<Row> rows;
     int maxdr = 0;
     for (int q = 0; q < ng; q++) {
         const int c0 = G * q;
@@ -509,24 +541,30 @@ static int build_groups(af_plan_t p, int G, af_pair_tables* T)
             v[d] = std::make_pair(key_of(row, c0), row[c0]);
         }
         std::sort(v.begin(), v.end());
-        const size_t n0 = rB.size();
+        rows.clear();
         for (int d = 0; d < ndm;) {
             int e = d;
             while (e < ndm && v[e].first == v[d].first) e++;
             const int32_t B = v[d].second & ~15;  // the run is sorted by delay
-            rkey.push_back(v[d].first);
-            for (int i = 0; i < K; i++) rdelta.push_back(v[d].first[i]);
-            rB.push_back(B);
-            rspan.push_back(v[e - 1].second - B);
+            rows.push_back(Row{v[d].first, B, v[e - 1].second - B});
             d = e;
         }
+        std::stable_sort(rows.begin(), rows.end(), [](const Row& a, const Row& b) { return a.B < b.B; });
+        const size_t n0 = rB.size();
+        for (const Row& r : rows) {
+            rlook.push_back(std::make_pair(r.key, (int32_t)rB.size()));
+            for (int i = 0; i < K; i++) rdelta.push_back(r.key[i]);
+            rB.push_back(r.B);
+            rspan.push_back(r.span);
+        }
+        std::sort(rlook.begin() + n0, rlook.end());
         rb[q + 1] = (int32_t)rB.size();
-        ub[q] = *std::min_element(rB.begin() + n0, rB.end());
+        ub[q] = rB[n0];
         for (int i = 0; i < K; i++) {
             int32_t lo = INT32_MAX, hi = INT32_MIN;
-            for (size_t g = n0; g < rB.size(); g++) {
-                lo = std::min(lo, rkey[g][i]);
-                hi = std::max(hi, rkey[g][i]);
+            for (const Row& r : rows) {
+                lo = std::min(lo, r.key[i]);
+                hi = std::max(hi, r.key[i]);
             }
             gdr[(size_t)q * K + i] = make_int2(lo, hi);
             maxdr = std::max(maxdr, hi - lo);
@@ -620,8 +658,8 @@ static int build_groups(af_plan_t p, int G, af_pair_tables* T)
             if (open_slots + (int)S.size() > kPSL || open_bytes + gbytes > stage_bytes) flush();
             if (ents.empty()) first_slot = (int)srec.size();
             for (size_t k = 0; k < S.size(); k++) {
-                const int g = (int)(std::lower_bound(rkey.begin() + rb[q], rkey.begin() + rb[q + 1], S[k]) -
-                                    rkey.begin());
+                const int g = std::lower_bound(rlook.begin() + rb[q], rlook.begin() + rb[q + 1],
+                                               std::make_pair(S[k], INT32_MIN))->second;
                 srec.push_back(make_int2(sbyt[k], open_bytes));
                 open_bytes += sbyt[k];
                 srow.push_back(g);
@@ -677,6 +715,7 @@ static int build_groups(af_plan_t p, int G, af_pair_tables* T)
     }
     for (auto& l : T->lay)
         if ((e = cudaMalloc(&l.d_pinfo, (size_t)ng * sizeof(int4))) != cudaSuccess ||
+            (e = cudaMalloc(&l.d_gmax, (size_t)ng * sizeof(int))) != cudaSuccess ||
             (e = cudaMalloc(&l.d_rinfo, (size_t)T->nrows * sizeof(int2))) != cudaSuccess ||
             (e = cudaMalloc(&l.d_rowoff, (size_t)T->nrows * 8)) != cudaSuccess ||
             (e = cudaMalloc(&l.d_soff, srow.size() * 8)) != cudaSuccess) {
@@ -698,9 +737,10 @@ int af_pairs_build(af_plan_t p)
     return AF_OK;
 }
 
-// Row g's length for time blocks of L outputs: its delay span, a window and
-// slack past the block, r16(L + span_g + 1047).
-static int64_t row_len(const af_pair_tables* T, int g, int64_t L) { return r16(L + T->h_rspan[g] + 1047); }
+// Row g's length for time blocks of L outputs: the last tile of a block
+// starts at most L - TTE + span_g into the row, and its window (at most
+// span_g + 1031 samples, rounded to 8) must fit: r16(L + 2 span_g + 32).
+static int64_t row_len(const af_pair_tables* T, int g, int64_t L) { return r16(L + 2 * (int64_t)T->h_rspan[g] + 32); }
 
 static int64_t rows_elems(const af_pair_tables* T, int64_t L)
 {
@@ -749,18 +789,21 @@ static int pairs_layout(af_plan_t p, int k, int64_t L)
     }
     std::vector<int64_t> rowoff(T->nrows), soff(T->h_srow.size());
     std::vector<int4> pinfo(T->np);
+    std::vector<int> gmax(T->np);
     std::vector<int2> rinfo(T->nrows);
     int64_t off = 0, maxlen = 0;
     for (int q = 0; q < T->np; q++) {
-        int64_t end = 0;
+        int64_t end = 0, longest = 0;
         for (int g = T->h_rb[q]; g < T->h_rb[q + 1]; g++) {
             const int64_t len = row_len(T, g, L);
             rowoff[g] = off;
             off += len;
             rinfo[g] = make_int2(T->h_rB[g] - T->h_ub[q], (int)len);
             end = std::max(end, (int64_t)rinfo[g].x + len);
+            longest = std::max(longest, len);
         }
         pinfo[q] = make_int4(T->h_rb[q], T->h_rb[q + 1] - T->h_rb[q], T->h_ub[q], (int)end);
+        gmax[q] = (int)longest;
         maxlen = std::max(maxlen, end);
     }
     for (size_t i = 0; i < soff.size(); i++) soff[i] = rowoff[T->h_srow[i]] + T->h_scpart[i];
@@ -770,7 +813,8 @@ static int pairs_layout(af_plan_t p, int k, int64_t L)
         (e = cudaMemcpy(ly.d_soff, soff.data(), soff.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(ly.d_pinfo, pinfo.data(), pinfo.size() * sizeof(int4), cudaMemcpyHostToDevice)) !=
             cudaSuccess ||
-        (e = cudaMemcpy(ly.d_rinfo, rinfo.data(), rinfo.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess)
+        (e = cudaMemcpy(ly.d_rinfo, rinfo.data(), rinfo.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(ly.d_gmax, gmax.data(), gmax.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
         return af_cuda_check(e, "pair layout");
     ly.L = L;
     ly.maxlen = maxlen;
@@ -932,15 +976,15 @@ int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64
     const unsigned long long g2 = (unsigned long long)tiles * (unsigned)T->tt.nblk;
     if (g1 > 0x7fffffffULL || g2 > 0x7fffffffULL) return af_set_error(AF_EINVAL, "pairs: problem too large for one grid");
     if (T->G == 4)
-        k_group_rows<4><<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, ly.d_pinfo, T->d_gdr, T->d_rdelta,
+        k_group_rows<4><<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, ly.d_pinfo, ly.d_gmax, T->d_gdr, T->d_rdelta,
                                                       ly.d_rinfo, ly.d_rowoff, T0, etiles, rows_wstride(T->maxdr),
                                                       T->d_ps);
     else if (T->G == 3)
-        k_group_rows<3><<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, ly.d_pinfo, T->d_gdr, T->d_rdelta,
+        k_group_rows<3><<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, ly.d_pinfo, ly.d_gmax, T->d_gdr, T->d_rdelta,
                                                       ly.d_rinfo, ly.d_rowoff, T0, etiles, rows_wstride(T->maxdr),
                                                       T->d_ps);
     else
-        k_group_rows<2><<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, ly.d_pinfo, T->d_gdr, T->d_rdelta,
+        k_group_rows<2><<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, ly.d_pinfo, ly.d_gmax, T->d_gdr, T->d_rdelta,
                                                       ly.d_rinfo, ly.d_rowoff, T0, etiles, rows_wstride(T->maxdr),
                                                       T->d_ps);
     if (int rc = af_cuda_check(cudaGetLastError(), "group rows launch")) return rc;

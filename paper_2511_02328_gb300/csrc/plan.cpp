@@ -62,6 +62,9 @@ static void free_search_ws(af_plan_t p)
     if (p->ws_copy) cudaStreamDestroy(p->ws_copy);
     for (cudaEvent_t& e : p->ws_ev)
         if (e) cudaEventDestroy(e), e = nullptr;
+    for (cudaEvent_t& e : p->ws_tev)
+        if (e) cudaEventDestroy(e), e = nullptr;
+    p->ws_timing = false;
     p->ws_copy = nullptr;
     p->ws_in = nullptr;
     p->ws_plane = nullptr;
@@ -609,6 +612,31 @@ extern "C" int af_search_reserve(af_plan_t p, int64_t max_nsamp, int32_t cap)
     return af_pairs_reserve(p, nout, true);  // the group-row buffers, where that path applies
 }
 
+extern "C" int af_search_timing(af_plan_t p, int enable)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    if (enable && !p->ws_tev[0])
+        for (cudaEvent_t& e : p->ws_tev)
+            if (cudaError_t ce = cudaEventCreate(&e)) return af_cuda_check(ce, "af_search_timing");
+    p->ws_timing = enable != 0;
+    return AF_OK;
+}
+
+extern "C" int af_search_times(af_plan_t p, float* wait_ms, float* dedisp_ms, float* snr_ms)
+{
+    if (int rc = af_check_plan(p)) return rc;
+    if (!p->ws_tev[0]) return af_set_error(AF_EINVAL, "af_search_times: timing was never enabled");
+    float a = 0.f, b = 0.f, c = 0.f;
+    AF_CUDA(cudaEventSynchronize(p->ws_tev[3]));
+    AF_CUDA(cudaEventElapsedTime(&a, p->ws_tev[0], p->ws_tev[1]));
+    AF_CUDA(cudaEventElapsedTime(&b, p->ws_tev[1], p->ws_tev[2]));
+    AF_CUDA(cudaEventElapsedTime(&c, p->ws_tev[2], p->ws_tev[3]));
+    if (wait_ms) *wait_ms = a;
+    if (dedisp_ms) *dedisp_ms = b;
+    if (snr_ms) *snr_ms = c;
+    return AF_OK;
+}
+
 extern "C" int af_search(af_plan_t p, const uint8_t* h_in, int64_t nsamp, const int32_t* widths, int nw,
                          float thresh, af_cand_t* h_out, int32_t cap, int32_t* h_count, void* stream)
 {
@@ -622,6 +650,8 @@ extern "C" int af_search(af_plan_t p, const uint8_t* h_in, int64_t nsamp, const 
     af_widths_t w;
     if (int rc = af_check_widths(p, widths, nw, nout, &w)) return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    const bool tm = p->ws_timing;
+    if (tm) AF_CUDA(cudaEventRecord(p->ws_tev[0], s));
     if (af_dedisp_uses_pairs(p, nout)) {
         // Group rows: the outputs in the search layout's time blocks (at least
         // eight); each block's rows and tiles run as soon as its input columns
@@ -643,6 +673,7 @@ extern "C" int af_search(af_plan_t p, const uint8_t* h_in, int64_t nsamp, const 
             cudaEvent_t ev = p->ws_ev[k % 4];  // an event is reused once the stream has waited on it
             AF_CUDA(cudaEventRecord(ev, p->ws_copy));
             AF_CUDA(cudaStreamWaitEvent(s, ev, 0));
+            if (tm && k == 0) AF_CUDA(cudaEventRecord(p->ws_tev[1], s));
             if (int rc = af_launch_pairs_block(p, p->ws_in, nsamp, nout, p->ws_plane, p->d_stats, s, ly, T0)) return rc;
         }
     } else if (af_dedisp_uses_tiles(p)) {
@@ -666,18 +697,22 @@ extern "C" int af_search(af_plan_t p, const uint8_t* h_in, int64_t nsamp, const 
             }
             AF_CUDA(cudaEventRecord(p->ws_ev[k], p->ws_copy));
             AF_CUDA(cudaStreamWaitEvent(s, p->ws_ev[k], 0));
+            if (tm && k == 0) AF_CUDA(cudaEventRecord(p->ws_tev[1], s));
             if (int rc = af_launch_dedisperse_tiles(p, p->ws_in, nsamp, nout, p->ws_plane, p->d_stats, s, tb, te))
                 return rc;
         }
     } else {
         AF_CUDA(cudaMemcpyAsync(p->ws_in, h_in, (size_t)p->nchan * nsamp, cudaMemcpyHostToDevice, s));
+        if (tm) AF_CUDA(cudaEventRecord(p->ws_tev[1], s));
         if (int rc = af_launch_dedisperse(p, p->ws_in, nsamp, nout, p->ws_plane, p->d_stats, s)) return rc;
     }
+    if (tm) AF_CUDA(cudaEventRecord(p->ws_tev[2], s));
     if (int rc = af_launch_boxcar(p->ws_plane, p->ndm, nout, p->d_stats, w, p->d_rowconst, p->ws_snr, p->ws_bw, s))
         return rc;
     if (int rc = af_launch_candidates(p->ws_snr, p->ws_bw, p->ndm, nout, w, thresh, 0, p->ws_cands, cap,
                                       p->ws_count, s))
         return rc;
+    if (tm) AF_CUDA(cudaEventRecord(p->ws_tev[3], s));
     int32_t total = 0;
     AF_CUDA(cudaMemcpyAsync(&total, p->ws_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     AF_CUDA(cudaStreamSynchronize(s));

@@ -327,7 +327,7 @@ def test_coarse_dm_grids_shallower_ring(step, ring, monkeypatch):
 def _pair_rows_bytes(D, L, G=2):
     """Bytes of the group-row buffer for time blocks of L outputs: per group
     q (channels Gq .. Gq+G-1) one row per distinct tuple of delays relative
-    to channel Gq (0 for a missing channel), each of r16(L + span + 1047)
+    to channel Gq (0 for a missing channel), each of r16(L + 2 span + 32)
     uint16 samples, span = the largest D[.][Gq] of the DMs with that tuple
     minus their smallest rounded down to 16."""
     ndm, nchan = D.shape
@@ -339,7 +339,7 @@ def _pair_rows_bytes(D, L, G=2):
         for v in np.unique(rel, axis=0):
             d0 = D[np.all(rel == v, axis=1), c0]
             span = int(d0.max()) - (int(d0.min()) & ~15)
-            total += (L + span + 1047 + 15) & ~15
+            total += (L + 2 * span + 32 + 15) & ~15
     return 2 * total
 
 
