@@ -779,6 +779,15 @@ def main():
         c, nc = _lib.af_search(H, x_pin.data_ptr(), NSAMP, WIDTHS, THRESH, CAP, sp, out=out)
         plan.cluster(c)
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    # one more call with phase events (outside the timed region): where the e2e time goes
+    _lib.af_search_timing(H, 1)
+    _lib.af_search(H, x_pin.data_ptr(), NSAMP, WIDTHS, THRESH, CAP, sp, out=out)
+    ph = _lib.af_search_times(H)
+    _lib.af_search_timing(H, 0)
+    e2e_phases = {"copy_wait_ms": ph[0], "dedisp_ms": ph[1], "snr_candidates_ms": ph[2],
+                  "note": "first time block's input copy (its outputs + Dmax), dedispersion with the rest of the "
+                          "copy overlapped, S/N + candidate kernels; the remainder of e2e ms is host work and the "
+                          "candidate copy back"}
     # the input copy alone (pinned host -> device), for the e2e breakdown
     h2d = torch.empty_like(x)
     for _ in range(2):
@@ -919,6 +928,7 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": aggregate_rate(world, work, e2e_s), "unit": UNIT, "ms": e2e_s * 1e3, "h2d_ms": h2d_ms,
+                    "phases": e2e_phases,
                     "h2d_gbs": NCHAN * NSAMP / (h2d_ms * 1e-3) / 1e9, "h2d_bytes_per_step": NCHAN * NSAMP,
                     "d2h_bytes_per_step": 4 + 24 * min(nc, CAP)},
             "gpu_launches": launches_per_step * args.steps,
