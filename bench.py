@@ -775,9 +775,12 @@ def main():
         dist.barrier()
     t0 = time.perf_counter()
     nc = 0
+    walls = []
     for _ in range(args.e2e_steps):
+        ta = time.perf_counter()
         c, nc = _lib.af_search(H, x_pin.data_ptr(), NSAMP, WIDTHS, THRESH, CAP, sp, out=out)
         plan.cluster(c)
+        walls.append((time.perf_counter() - ta) * 1e3)
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
     # one more call with phase events (outside the timed region): where the e2e time goes
     _lib.af_search_timing(H, 1)
@@ -785,9 +788,10 @@ def main():
     ph = _lib.af_search_times(H)
     _lib.af_search_timing(H, 0)
     e2e_phases = {"copy_wait_ms": ph[0], "dedisp_ms": ph[1], "snr_candidates_ms": ph[2],
+                  "call_ms": {"min": min(walls), "median": float(np.median(walls)), "max": max(walls)},
                   "note": "first time block's input copy (its outputs + Dmax), dedispersion with the rest of the "
                           "copy overlapped, S/N + candidate kernels; the remainder of e2e ms is host work and the "
-                          "candidate copy back"}
+                          "candidate copy back; call_ms = each timed call's wall time (search + clustering)"}
     # the input copy alone (pinned host -> device), for the e2e breakdown
     h2d = torch.empty_like(x)
     for _ in range(2):

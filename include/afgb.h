@@ -397,7 +397,9 @@ int af_cluster(af_plan_t plan, af_cand_t* h_cands, int32_t n, double dm_tol,
  * and returns after the stream has been synchronised.  *h_count = total
  * found; AF_EOVERFLOW (with the first cap candidates in h_out) if it exceeds
  * cap.  Requires af_search_reserve(plan, >= nsamp, >= cap) first (AF_ENOBUFS
- * otherwise). */
+ * otherwise); the reservation also holds a small pinned host buffer into
+ * which the count, the error flag and up to 4096 candidates come back
+ * together (one wait per call; longer lists take a second copy). */
 int af_search_reserve(af_plan_t plan, int64_t max_nsamp, int32_t cap);
 /* Device bytes af_search_reserve(plan, max_nsamp, cap) would allocate: the
  * input, plane, S/N, best-width and candidate buffers and the group-row

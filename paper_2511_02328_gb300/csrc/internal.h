@@ -187,6 +187,8 @@ struct af_plan_s {
     uint8_t* ws_bw = nullptr;
     af_cand_t* ws_cands = nullptr;
     int32_t* ws_count = nullptr;
+    int32_t* ws_host = nullptr;            // pinned: count, error flag, 2 pad words, then ws_stage candidates
+    int32_t ws_stage = 0;                  // candidates copied back with the count (one wait per search)
     cudaStream_t ws_copy = nullptr;        // input copies of af_search, overlapped with dedispersion
     cudaEvent_t ws_ev[4] = {};             // one per copied time segment
     // optional phase timing of af_search (af_search_timing): events on the

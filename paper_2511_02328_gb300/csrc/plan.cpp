@@ -51,6 +51,9 @@ int af_check_plan(af_plan_t p)
 // Dispersion constant, Eq. (KDM): seconds when frequencies are in MHz.
 static const double kKDM = 4.148808e3;
 
+// Candidates af_search copies back together with their count.
+static const int32_t kSearchStage = 4096;
+
 static void free_search_ws(af_plan_t p)
 {
     cudaFree(p->ws_in);
@@ -59,6 +62,7 @@ static void free_search_ws(af_plan_t p)
     cudaFree(p->ws_bw);
     cudaFree(p->ws_cands);
     cudaFree(p->ws_count);
+    cudaFreeHost(p->ws_host);
     if (p->ws_copy) cudaStreamDestroy(p->ws_copy);
     for (cudaEvent_t& e : p->ws_ev)
         if (e) cudaEventDestroy(e), e = nullptr;
@@ -72,6 +76,8 @@ static void free_search_ws(af_plan_t p)
     p->ws_bw = nullptr;
     p->ws_cands = nullptr;
     p->ws_count = nullptr;
+    p->ws_host = nullptr;
+    p->ws_stage = 0;
     p->ws_nsamp = 0;
     p->ws_cap = 0;
 }
@@ -598,6 +604,8 @@ extern "C" int af_search_reserve(af_plan_t p, int64_t max_nsamp, int32_t cap)
         (e = cudaMalloc(&p->ws_snr, npl * 4)) != cudaSuccess || (e = cudaMalloc(&p->ws_bw, npl)) != cudaSuccess ||
         (e = cudaMalloc(&p->ws_cands, (size_t)cap * sizeof(af_cand_t))) != cudaSuccess ||
         (e = cudaMalloc(&p->ws_count, 16)) != cudaSuccess ||
+        (e = cudaHostAlloc(&p->ws_host, 16 + (size_t)std::min(cap, kSearchStage) * sizeof(af_cand_t),
+                           cudaHostAllocDefault)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&p->ws_copy, cudaStreamNonBlocking)) != cudaSuccess) {
         free_search_ws(p);
         return af_cuda_check(e, "af_search_reserve");
@@ -609,6 +617,7 @@ extern "C" int af_search_reserve(af_plan_t p, int64_t max_nsamp, int32_t cap)
         }
     p->ws_nsamp = max_nsamp;
     p->ws_cap = cap;
+    p->ws_stage = std::min(cap, kSearchStage);
     return af_pairs_reserve(p, nout, true);  // the group-row buffers, where that path applies
 }
 
@@ -713,20 +722,31 @@ extern "C" int af_search(af_plan_t p, const uint8_t* h_in, int64_t nsamp, const 
                                       p->ws_count, s))
         return rc;
     if (tm) AF_CUDA(cudaEventRecord(p->ws_tev[3], s));
-    int32_t total = 0;
-    AF_CUDA(cudaMemcpyAsync(&total, p->ws_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    // One wait in the usual case: the count, the error flag and the first
+    // ws_stage candidates come back together into pinned memory; only a
+    // larger candidate list takes a second copy.
+    int32_t* hs = p->ws_host;
+    af_cand_t* hc = reinterpret_cast<af_cand_t*>(hs + 4);
+    const int32_t stage = std::min(cap, p->ws_stage);
+    AF_CUDA(cudaMemcpyAsync(hs, p->ws_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AF_CUDA(cudaMemcpyAsync(hs + 1, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (stage > 0)
+        AF_CUDA(cudaMemcpyAsync(hc, p->ws_cands, (size_t)stage * sizeof(af_cand_t), cudaMemcpyDeviceToHost, s));
     AF_CUDA(cudaStreamSynchronize(s));
-    int flag = 0;
-    AF_CUDA(cudaMemcpyAsync(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    AF_CUDA(cudaStreamSynchronize(s));
-    if (flag) {
+    const int32_t total = hs[0];
+    if (hs[1]) {
         AF_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int), s));
         return af_set_error(AF_ETIMEOUT, "af_search: a kernel's bounded wait for an asynchronous copy ran out");
     }
     int32_t ncopy = total < cap ? total : cap;
     if (ncopy > 0) {
-        AF_CUDA(cudaMemcpyAsync(h_out, p->ws_cands, (size_t)ncopy * sizeof(af_cand_t), cudaMemcpyDeviceToHost, s));
-        AF_CUDA(cudaStreamSynchronize(s));
+        if (ncopy <= stage) {
+            memcpy(h_out, hc, (size_t)ncopy * sizeof(af_cand_t));
+        } else {
+            AF_CUDA(cudaMemcpyAsync(h_out, p->ws_cands, (size_t)ncopy * sizeof(af_cand_t), cudaMemcpyDeviceToHost,
+                                    s));
+            AF_CUDA(cudaStreamSynchronize(s));
+        }
         std::sort(h_out, h_out + ncopy, cand_less_dt);
     }
     *h_count = total;

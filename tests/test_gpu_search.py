@@ -136,6 +136,23 @@ def test_host_search_equals_device_path(c1_data):
     p.close()
 
 
+def test_host_search_long_candidate_lists(c1_data):
+    """Candidate lists shorter and longer than the 4096 af_search returns with
+    its count (one copy back, or a second copy), and a capacity below both."""
+    x, D, Y, ref_snr, ref_bw = c1_data
+    p = _plan(C1)
+    for thresh, cap in ((4.0, 1 << 16), (3.5, 1 << 16), (3.5, 5000)):
+        cands, n = p.search_host(x, C1["widths"], thresh, cap=cap)
+        ref, nref = oracle.peaks(ref_snr, ref_bw, C1["widths"], thresh)
+        assert abs(n - nref) <= 8
+        assert len(cands) == min(n, cap)
+        if cap >= n:
+            _cands_agree(cands, ref, ref_snr, thresh)
+        k = list(zip(cands["dm_idx"].tolist(), cands["t"].tolist()))
+        assert k == sorted(k)
+    p.close()
+
+
 SHAPES = [
     # nchan, f_lo, f_hi, tsamp, nsamp, dms
     (1, 1400.0, 1500.0, 1e-3, 100, [0.0]),
@@ -187,6 +204,40 @@ def test_extreme_values_bit_exact():
     plane = p.dedisperse(x)
     torch.cuda.synchronize()
     assert int(plane.min()) == int(plane.max()) == 255 * nchan
+    p.close()
+
+
+def test_boxcar_and_candidates_on_wide_range_planes():
+    """Planes whose window deviations |B - q| pass 2^22 in some tiles and not
+    in others (the boxcar kernel's two conversion paths), with full-range
+    spikes; candidates from a 16-byte aligned and from a misaligned S/N plane."""
+    from paper_2511_02328_gb300.search import Plan
+    nchan = 4096
+    p = Plan(nchan, 1000.0, 1500.0, 4.9152e-5, [0.0, 1.0, 2.0, 3.0, 4.0])
+    rng = np.random.default_rng(11)
+    ndm, nout = 5, 3 * 4096 + 777
+    Y = rng.integers(500_000, 501_000, (ndm, nout)).astype(np.int32)
+    Y[1, 5000:5040] = 255 * nchan                      # full-range block: generic path there
+    Y[2, 100:103] = 0
+    Y[3, ::997] = 255 * nchan                           # isolated spikes in every tile
+    Y[4, 9000:9300] += 4_000                            # a broad pulse, fast path
+    widths = [1, 2, 4, 8, 16, 32, 64, 128, 256]
+    plane = torch.from_numpy(Y).cuda()
+    snr, bw = p.boxcar_snr(plane, widths)
+    torch.cuda.synchronize()
+    ref_snr, ref_bw = oracle.boxcar_snr(Y, widths)
+    _snr_close(snr.cpu().numpy(), ref_snr)
+    _widths_agree(bw.cpu().numpy(), ref_bw, Y, widths)
+    ref, nref = oracle.peaks(ref_snr, ref_bw, widths, 4.0)
+    assert nref > 10
+    got, n = p.cands_to_numpy(*p.candidates(snr, bw, widths, 4.0))
+    _cands_agree(got, ref, ref_snr, 4.0)
+    buf = torch.empty(ndm * nout + 1, dtype=torch.float32, device="cuda")
+    snr_off = buf[1:].view(ndm, nout)                   # 4-byte offset: scalar loads
+    snr_off.copy_(snr)
+    assert snr_off.data_ptr() % 16 != 0
+    got2, n2 = p.cands_to_numpy(*p.candidates(snr_off, bw, widths, 4.0))
+    assert n2 == n and np.array_equal(got2, got)
     p.close()
 
 
