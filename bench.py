@@ -18,6 +18,7 @@ For N > 1 launch with torch.distributed.run; every rank searches its own beam
 (same workload shape, different seed): weak scaling, no data-path collective.
 """
 import argparse
+import gc
 import json
 import os
 import subprocess
@@ -670,7 +671,7 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="afgb", choices=["afgb", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--no-subband", action="store_true")
@@ -773,6 +774,8 @@ def main():
         _lib.af_search(H, x_pin.data_ptr(), NSAMP, WIDTHS, THRESH, CAP, sp, out=out)
     if dist is not None:
         dist.barrier()
+    gc_was = gc.isenabled()
+    gc.disable()          # no collector pause inside the timed calls
     t0 = time.perf_counter()
     nc = 0
     walls = []
@@ -782,13 +785,16 @@ def main():
         plan.cluster(c)
         walls.append((time.perf_counter() - ta) * 1e3)
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if gc_was:
+        gc.enable()
     # one more call with phase events (outside the timed region): where the e2e time goes
     _lib.af_search_timing(H, 1)
     _lib.af_search(H, x_pin.data_ptr(), NSAMP, WIDTHS, THRESH, CAP, sp, out=out)
     ph = _lib.af_search_times(H)
     _lib.af_search_timing(H, 0)
     e2e_phases = {"copy_wait_ms": ph[0], "dedisp_ms": ph[1], "snr_candidates_ms": ph[2],
-                  "call_ms": {"min": min(walls), "median": float(np.median(walls)), "max": max(walls)},
+                  "call_ms": {"min": min(walls), "median": float(np.median(walls)), "max": max(walls),
+                              "each": [round(v, 2) for v in walls]},
                   "note": "first time block's input copy (its outputs + Dmax), dedispersion with the rest of the "
                           "copy overlapped, S/N + candidate kernels; the remainder of e2e ms is host work and the "
                           "candidate copy back; call_ms = each timed call's wall time (search + clustering)"}
@@ -856,7 +862,8 @@ def main():
     sm_max = float(pk.get("sm_max_mhz", SM_MAX_MHZ_FALLBACK))
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = nsm * 128 * sm_max * 1e6 / 1e12          # T int32 lane-ops/s
-    smem_peak = nsm * 128 * sm_max * 1e6 / 1e12         # TB/s: 128 B of shared loads per clock per SM
+    smem_derived = nsm * 128 * sm_max * 1e6 / 1e12      # TB/s: 128 B of shared loads per clock per SM
+    smem_peak = _lib.af_diag_smem_rate() / 1e12         # TB/s, measured on this device (probe kernel)
     add_rate, pattern_rate = _lib.af_diag_int_rates()  # measured on this device (probe kernels)
     achieved = work / (ms_dedisp * 1e-3) / 1e12        # T adds/s, both stages
     hbm_peak = float(pk.get("hbm_gbs", 6800.0))
@@ -883,8 +890,10 @@ def main():
                             "copy_bytes": stage["copy_bytes"],
                             "note": "shared-memory bytes including the row windows the producer copies in (the "
                                     "kernel's whole shared-memory traffic but its small tables)"},
-            "peak_basis": "%d SMs x 128 B shared-load bandwidth per clock x %.0f MHz (derived, of max clock)"
-                          % (nsm, sm_max),
+            "peak_basis": "of measured: shared-load bandwidth of a conflict-free 32-bit load probe on this "
+                          "device (af_diag_smem_rate)",
+            "derived_peak": {"value": smem_derived, "frac": s2_ach / smem_derived,
+                             "basis": "%d SMs x 128 B per clock x %.0f MHz (max clock)" % (nsm, sm_max)},
             "stage1": {"kernel": "k_group_rows<%d>" % G, "bound": "hbm", "ms": stage["rows_ms"], "achieved": s1_ach,
                        "peak": hbm_peak, "unit": "GB/s", "frac": s1_ach / hbm_peak, "basis": "of measured",
                        "work": "row writes %.3g B + input read %.3g B" % (stage["row_bytes"], NCHAN * NSAMP)},

@@ -592,6 +592,13 @@ int af_stream_close(af_stream_t s);
  *                       paired adds, i.e. 8 sample additions per step.
  * Allocates nothing (a static device array receives the probes' results). */
 int af_diag_int_rates(double* add_per_s, double* pattern_adds_per_s);
+/* Shared-memory load bandwidth of the current device in bytes per second, the
+ * denominator of the group-row tile kernel's roofline: one block of 1024
+ * threads per SM, 8 independent lane-consecutive (bank-conflict-free) 32-bit
+ * shared loads per thread and step, each added into an accumulator.  A few
+ * milliseconds, synchronous; allocates nothing.  AF_EINVAL if bytes_per_s is
+ * NULL. */
+int af_diag_smem_rate(double* bytes_per_s);
 
 /* ---- candidate classifier ----------------------------------------------- *
  * The paper detects pulses with a YOLOv11n network on DM-time images

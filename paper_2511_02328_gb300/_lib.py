@@ -62,6 +62,7 @@ SIGNATURES = {
     "af_boxcar_snr_robust": [_P, _P, _I64, _P, _P, _I, _P, _P, _P],
     "af_grid": [_P, _I, _I64, _I64, _I, _P, _P, _P],
     "af_diag_int_rates": [_P, _P],
+    "af_diag_smem_rate": [_P],
     "af_plan_destroy": [_P],
     "af_plan_delays": [_P, _P, _P],
     "af_plan_info": [_P, _P, _P, _P, _P],
@@ -198,6 +199,13 @@ def af_diag_int_rates():
     a, b = _D(), _D()
     _check(lib().af_diag_int_rates(ctypes.byref(a), ctypes.byref(b)), "af_diag_int_rates")
     return a.value, b.value
+
+
+def af_diag_smem_rate():
+    """Measured shared-memory load bandwidth of the current device (bytes/s)."""
+    a = ctypes.c_double()
+    _check(lib().af_diag_smem_rate(ctypes.byref(a)), "af_diag_smem_rate")
+    return a.value
 
 
 AF_FS_MEDIAN = 0

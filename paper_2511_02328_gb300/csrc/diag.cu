@@ -1,13 +1,17 @@
 // diag.cu -- measured integer issue rates of the device, the denominator of
 // the dedispersion roofline (no counterpart in the paper).
 //
-// Two probe kernels, one block of 1024 threads per SM (120 KB of dynamic
+// Three probe kernels, one block of 1024 threads per SM (120 KB of dynamic
 // shared memory keeps it to one), a fixed number of iterations each:
 //   ADD:     8 independent chains of 2-input 32-bit additions per thread;
 //   PATTERN: the tile kernel's inner step -- two 32-bit shared loads (two
 //            channels, 4 samples each), widening into 16-bit lanes
 //            (w & 0x00FF00FF, prmt(w, 0x4341)) and the paired adds -- counted
-//            as 8 sample additions per iteration.
+//            as 8 sample additions per iteration;
+//   SHARED:  8 independent 32-bit shared loads per iteration at immediate
+//            offsets from one moving base (lane-consecutive words: no bank
+//            conflicts), each folded into an accumulator -- the shared-memory
+//            load bandwidth the group-row tile kernel is bound by.
 // Results go to a static device array (no allocation); every shared address is
 // inside the block's own array.
 #include <cuda_runtime.h>
@@ -46,6 +50,26 @@ __global__ void __launch_bounds__(kDT, 1) k_diag(uint32_t seed, uint32_t mask)
             asm volatile("add.u32 %0, %0, %1;" : "+r"(a5) : "r"(a6));
             asm volatile("add.u32 %0, %0, %1;" : "+r"(a6) : "r"(a7));
             asm volatile("add.u32 %0, %0, %1;" : "+r"(a7) : "r"(a0));
+        } else if (OP == 2) {
+            // base + 7 * 256 + 4 stays under (31 * 2048 + mask + 1796) bytes < kDSmem
+            const uint32_t b = sbase + (((uint32_t)it * 128u) & mask);
+            uint32_t w0, w1, w2, w3, w4, w5, w6, w7;
+            asm volatile("ld.shared.u32 %0, [%1];" : "=r"(w0) : "r"(b));
+            asm volatile("ld.shared.u32 %0, [%1+256];" : "=r"(w1) : "r"(b));
+            asm volatile("ld.shared.u32 %0, [%1+512];" : "=r"(w2) : "r"(b));
+            asm volatile("ld.shared.u32 %0, [%1+768];" : "=r"(w3) : "r"(b));
+            asm volatile("ld.shared.u32 %0, [%1+1024];" : "=r"(w4) : "r"(b));
+            asm volatile("ld.shared.u32 %0, [%1+1280];" : "=r"(w5) : "r"(b));
+            asm volatile("ld.shared.u32 %0, [%1+1536];" : "=r"(w6) : "r"(b));
+            asm volatile("ld.shared.u32 %0, [%1+1792];" : "=r"(w7) : "r"(b));
+            a0 += w0;
+            a1 += w1;
+            a2 += w2;
+            a3 += w3;
+            a4 += w4;
+            a5 += w5;
+            a6 += w6;
+            a7 += w7;
         } else {
             // two independent accumulator pairs, one per parity of the iteration
             uint32_t w1, w2;
@@ -84,6 +108,19 @@ int time_probe(int nblk, float* ms)
 }
 
 }  // namespace
+
+extern "C" int af_diag_smem_rate(double* bytes_per_s)
+{
+    if (!bytes_per_s) return af_set_error(AF_EINVAL, "af_diag_smem_rate: NULL output");
+    int dev = 0, nsm = 0;
+    AF_CUDA(cudaGetDevice(&dev));
+    AF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int nblk = nsm < kDMaxBlocks ? nsm : kDMaxBlocks;
+    float ms = 0.f;
+    if (int rc = time_probe<2>(nblk, &ms)) return rc;
+    *bytes_per_s = (double)nblk * kDT * kDIters * 8.0 * 4.0 / (ms * 1e-3);
+    return AF_OK;
+}
 
 extern "C" int af_diag_int_rates(double* add_per_s, double* pattern_adds_per_s)
 {

@@ -502,6 +502,17 @@ def test_diag_int_rates_plausible():
     assert 0.05 * nominal < pattern <= 1.05 * add
 
 
+def test_diag_smem_rate_plausible():
+    # the measured shared-memory load bandwidth (the group-row tile kernel's
+    # roofline denominator): positive and at most 128 B per SM per clock at
+    # the 2.07 GHz maximum clock
+    from paper_2511_02328_gb300 import _lib
+    bw = _lib.af_diag_smem_rate()
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    nominal = nsm * 128 * 2.07e9
+    assert 0.2 * nominal < bw <= 1.05 * nominal
+
+
 def test_workspace_sizes_match_reservations(c1_data):
     """af_dedisperse_workspace_size / af_search_workspace_size report what the
     reservations then take from the device (allocation granularity aside),
