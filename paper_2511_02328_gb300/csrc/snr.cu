@@ -234,44 +234,103 @@ int launch_boxcar_tiles(const int32_t* d_plane, int ndm, int64_t nout, const af_
 
 // ---------------------------------------------------------------- robust S/N
 // Per-row median and MAD (lower medians, exact) by radix selection: one block
-// per row; each pass histograms the remaining value range into at most 2048
-// bins in shared memory and keeps the bin holding the wanted rank, so a range
-// of R values takes ceil(log2(R) / 11) passes (two for 20-bit rows).
+// per row; each pass histograms a window of the value range into at most 2048
+// bins in shared memory and keeps the bin holding the wanted rank, so a window
+// of R values takes ceil(log2(R) / 11) passes.
+//
+// Windows.  A first pass takes the row's minimum, maximum, mean mu and a bound
+// s >= sigma on its standard deviation.  Any median m of a distribution lies
+// within sigma of its mean (Cantelli), so the median is searched in
+// [mu - s - 1, mu + s + 1]; and since E|X - m| <= E|X - mu| <= sigma, Markov's
+// inequality leaves at most half of the values at |X - m| >= 2 sigma, so the
+// lower median of |X - m| (the MAD) is below 2 sigma and is searched in
+// [0, 2 s + 1].  For noise-like rows both windows are under 2048 wide: one
+// pass each, three passes in all (five over the full ranges).  The first
+// histogram pass of each search also counts the values below its window and
+// in it; the selection goes on only if the wanted rank falls inside, which
+// makes the result exact whatever the floating-point bound -- otherwise (never
+// expected) the same selection runs on the full range.
 constexpr int kRT = 512;
 constexpr int kRB = 2048;
-constexpr int kRU = 8;   // loads per thread per iteration
 
-template <int MODE>  // 0: u = v - base;  1: u = |v - base|
+template <int MODE>  // 0: u = v - base;  1: u = |v - base|   (mod 2^32, no signed overflow)
 __device__ __forceinline__ uint32_t robust_key(int32_t v, int32_t base)
 {
-    if (MODE == 0) return (uint32_t)(v - base);
-    return v >= base ? (uint32_t)(v - base) : (uint32_t)(base - v);
+    if (MODE == 0) return (uint32_t)v - (uint32_t)base;
+    return v >= base ? (uint32_t)v - (uint32_t)base : (uint32_t)base - (uint32_t)v;
 }
 
-// rank-th smallest key among the row's values (0-based), keys in [0, range].
+// Calls f(v) for every value of the row y[0 .. n), spread over the block: a
+// scalar head up to the first 16-byte boundary, then kRU4 16-byte loads per
+// thread in flight per step, then the scalar tail.
+constexpr int kRU4 = 4;
+template <typename F>
+__device__ __forceinline__ void for_row(const int32_t* __restrict__ y, int64_t n, F&& f)
+{
+    const int tid = threadIdx.x;
+    int64_t head = (int64_t)(((16u - ((uint32_t)reinterpret_cast<uintptr_t>(y) & 15u)) & 15u) >> 2);
+    if (head > n) head = n;
+    if (tid < head) f(__ldg(y + tid));
+    const int4* y4 = reinterpret_cast<const int4*>(y + head);
+    const int64_t n4 = (n - head) >> 2;
+    for (int64_t i = tid; i < n4; i += (int64_t)kRT * kRU4) {
+        int4 v[kRU4];
+#pragma unroll
+        for (int u = 0; u < kRU4; u++)
+            if (i + u * kRT < n4) v[u] = __ldg(y4 + i + u * kRT);
+#pragma unroll
+        for (int u = 0; u < kRU4; u++)
+            if (i + u * kRT < n4) {
+                f(v[u].x);
+                f(v[u].y);
+                f(v[u].z);
+                f(v[u].w);
+            }
+    }
+    const int64_t t0 = head + 4 * n4;
+    if (t0 + tid < n) f(__ldg(y + t0 + tid));  // at most 3 values
+}
+
+// Block sum of one int64 per thread, returned to every thread (sred: kRT/32 slots).
+__device__ __forceinline__ long long block_sum(long long x, long long* sred)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    __syncthreads();  // earlier readers of sred are done
+    if (lane == 0) sred[warp] = x;
+    __syncthreads();
+    long long t = 0;
+    for (int i = 0; i < kRT / 32; i++) t += sred[i];
+    return t;
+}
+
+// The rank-th smallest key (0-based) among the row's keys in [0, width).  For
+// MODE 0, rank counts from the row's smallest value: the first pass counts
+// the values under `base` (none when base is the row minimum).  Returns false,
+// with every thread agreeing, when the first pass shows the rank outside the
+// window.
 template <int MODE>
-__device__ uint32_t robust_select(const int32_t* __restrict__ y, int64_t n, int32_t base, uint32_t range,
-                                  int64_t rank, uint32_t* hist, long long* sel)
+__device__ bool robust_select(const int32_t* __restrict__ y, int64_t n, int32_t base, uint64_t width, int64_t rank,
+                              uint32_t* hist, long long* sel, long long* sred, uint32_t* out)
 {
     uint32_t start = 0;
-    uint64_t width = (uint64_t)range + 1;
     const int tid = threadIdx.x, lane = tid & 31;
-    while (width > 1) {
-        const int bits = 64 - __clzll((long long)(width - 1));
+    bool first = true;
+    while (first || width > 1) {
+        const int bits = width > 1 ? 64 - __clzll((long long)(width - 1)) : 0;
         const int s = bits > 11 ? bits - 11 : 0;
         for (int i = tid; i < kRB; i += kRT) hist[i] = 0u;
         __syncthreads();
-        for (int64_t t = tid; t < n; t += (int64_t)kRT * kRU) {
-            int32_t v[kRU];  // kRU independent loads in flight per thread
-#pragma unroll
-            for (int u = 0; u < kRU; u++) v[u] = t + u * kRT < n ? __ldg(y + t + u * kRT) : 0;
-#pragma unroll
-            for (int u = 0; u < kRU; u++) {
-                const uint32_t k = robust_key<MODE>(v[u], base);
-                if (t + u * kRT < n && k >= start && (uint64_t)(k - start) < width) atomicAdd(&hist[(k - start) >> s], 1u);
-            }
-        }
-        __syncthreads();
+        long long below = 0;
+        const bool count_below = MODE == 0 && first;
+        for_row(y, n, [&](int32_t v) {
+            const uint32_t k = robust_key<MODE>(v, base);
+            if (k >= start && (uint64_t)(k - start) < width) atomicAdd(&hist[(k - start) >> s], 1u);
+            else if (count_below && v < base) below++;
+        });
+        if (MODE == 0 && first) rank -= block_sum(below, sred);  // syncs the block
+        else __syncthreads();
         if (tid < 32) {
             // lane l owns bins [64 l, 64 l + 64): find the bin where the count passes rank
             uint32_t own = 0;
@@ -283,6 +342,8 @@ __device__ uint32_t robust_select(const int32_t* __restrict__ y, int64_t n, int3
                 const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += v;
             }
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            if (lane == 0) sel[2] = (rank >= 0 && rank < (int64_t)total) ? 1 : 0;
             const uint32_t excl = incl - own;
             if ((int64_t)excl <= rank && rank < (int64_t)incl) {
                 int64_t cum = excl;
@@ -299,56 +360,88 @@ __device__ uint32_t robust_select(const int32_t* __restrict__ y, int64_t n, int3
             }
         }
         __syncthreads();
+        if (!sel[2]) return false;  // only on a first pass: later windows hold the rank by construction
         const uint32_t b = (uint32_t)sel[0];
         rank -= sel[1];
         start += b << s;
         const uint64_t left = width - ((uint64_t)b << s);
         width = left < ((uint64_t)1 << s) ? left : ((uint64_t)1 << s);
+        first = false;
         __syncthreads();
     }
-    return start;
+    *out = start;
+    return true;
 }
 
 __global__ void __launch_bounds__(kRT, 2) k_row_robust(const int32_t* __restrict__ Y, int64_t nout,
                                                     af_robust_t* __restrict__ out)
 {
     __shared__ uint32_t hist[kRB];
-    __shared__ long long sel[2];
+    __shared__ long long sel[3];
+    __shared__ long long sred[kRT / 32];
     __shared__ int32_t smin[kRT / 32], smax[kRT / 32];
+    __shared__ float ssq[kRT / 32];
     const int d = blockIdx.x;
     const int32_t* y = Y + (int64_t)d * nout;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // pass 1: range, and sums of u = v - y[0] (exact) and of u^2 (fp32 per thread; only the window depends on it)
+    const int32_t y0 = __ldg(y);
     int32_t lo = INT32_MAX, hi = INT32_MIN;
-    for (int64_t t = tid; t < nout; t += (int64_t)kRT * kRU) {
-        int32_t v[kRU];
-#pragma unroll
-        for (int u = 0; u < kRU; u++) v[u] = t + u * kRT < nout ? __ldg(y + t + u * kRT) : __ldg(y + t);
-#pragma unroll
-        for (int u = 0; u < kRU; u++) {
-            lo = min(lo, v[u]);
-            hi = max(hi, v[u]);
-        }
-    }
+    long long su = 0;
+    float sq = 0.0f;
+    for_row(y, nout, [&](int32_t v) {
+        lo = min(lo, v);
+        hi = max(hi, v);
+        su += (long long)v - y0;
+        // v - y0 mod 2^32 as a signed value: exact unless the row spans more
+        // than 2^31, where only the window estimate (never the result) suffers
+        const float f = (float)(int32_t)((uint32_t)v - (uint32_t)y0);
+        sq = fmaf(f, f, sq);
+    });
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
         hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        sq += __shfl_xor_sync(0xffffffffu, sq, o);
     }
     if (lane == 0) {
         smin[warp] = lo;
         smax[warp] = hi;
+        ssq[warp] = sq;
     }
-    __syncthreads();
+    su = block_sum(su, sred);  // syncs: smin, smax, ssq are visible
     lo = smin[0];
     hi = smax[0];
-    for (int i = 1; i < kRT / 32; i++) {
+    double m2 = 0.0;
+    for (int i = 0; i < kRT / 32; i++) {
         lo = min(lo, smin[i]);
         hi = max(hi, smax[i]);
+        m2 += (double)ssq[i];
     }
+    const double nn = (double)nout, mean_u = (double)su / nn;
+    m2 /= nn;
+    // s >= sigma: the fp32 sums of u^2 (about nout / 512 terms per thread, then 32
+    // per warp) carry a relative error below (terms) * 2^-24; the margin is 4x that
+    const double rel = 1e-4 + ((double)nout / kRT + 64.0) * 2.4e-7;
+    const double sb = sqrt(fmax(m2 - mean_u * mean_u, 0.0) + rel * m2 + 1.0);
+    const double mu = (double)y0 + mean_u;
     const int64_t k = (nout - 1) / 2;
-    const int32_t med = lo + (int32_t)robust_select<0>(y, nout, lo, (uint32_t)(hi - lo), k, hist, sel);
-    const uint32_t r2 = (uint32_t)max(hi - med, med - lo);
-    const uint32_t mad = robust_select<1>(y, nout, med, r2, k, hist, sel);
+
+    const int64_t wl = max((int64_t)lo, (int64_t)floor(mu - sb) - 1);
+    const int64_t wh = min((int64_t)hi, (int64_t)ceil(mu + sb) + 1);
+    uint32_t key = 0;
+    int32_t med;
+    if (wl <= wh && robust_select<0>(y, nout, (int32_t)wl, (uint64_t)(wh - wl) + 1, k, hist, sel, sred, &key))
+        med = (int32_t)((uint32_t)(int32_t)wl + key);  // a row value: no overflow in the sum
+    else {  // the same selection over the whole range [lo, hi]
+        robust_select<0>(y, nout, lo, (uint64_t)((int64_t)hi - lo) + 1, k, hist, sel, sred, &key);
+        med = (int32_t)((uint32_t)lo + key);
+    }
+    const int64_t r2 = max((int64_t)hi - med, (int64_t)med - lo);
+    const int64_t wm = min(r2, (int64_t)ceil(2.0 * sb) + 1);
+    uint32_t mad = 0;
+    if (!robust_select<1>(y, nout, med, (uint64_t)wm + 1, k, hist, sel, sred, &mad))
+        robust_select<1>(y, nout, med, (uint64_t)r2 + 1, k, hist, sel, sred, &mad);
     if (tid == 0) {
         out[d].median = med;
         out[d].mad = mad;

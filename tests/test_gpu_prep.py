@@ -124,17 +124,23 @@ def _robust_plane(seed, ndm, nout):
     Y[2, :] = 123456                            # constant row (MAD 0)
     if nout > 5:
         Y[3, :5] = [0, 10 ** 6, 3, 3, 3]        # wide range
+    Y[4, :] = np.where(np.arange(nout) % 2 == 0, 0, 10 ** 6)      # two values: median at the mean - sigma bound
+    Y[5, 0] = 2 * 10 ** 9                       # the first value (the kernel's pivot) an outlier
+    Y[6, :] = rng.choice(np.array([-2 ** 31, 2 ** 31 - 1]), nout)  # the whole int32 range
+    Y[7, :] = rng.exponential(1000.0, nout).round().astype(np.int32)  # skewed
     return Y
 
 
 @pytest.mark.parametrize("nout", [1, 2, 3, 1000, 20001, 215261])
 def test_robust_rowstats_exact(nout):
-    Y = _robust_plane(nout, 6, nout)
+    """Median and MAD exact on noise, outliers, a constant row, two-valued and
+    full-int32-range rows, an outlier first value and a skewed row."""
+    Y = _robust_plane(nout, 8, nout)
     med, mad = oracle.row_robust(Y)
     L = _lib()
-    p = L.af_plan(16, 1000.0, 1500.0, 1e-4, np.zeros(6))
+    p = L.af_plan(16, 1000.0, 1500.0, 1e-4, np.zeros(8))
     y = torch.from_numpy(Y).cuda()
-    r = torch.empty((6, 2), dtype=torch.int64, device="cuda")
+    r = torch.empty((8, 2), dtype=torch.int64, device="cuda")
     L.af_rowstats_robust(p, y.data_ptr(), nout, r.data_ptr())
     torch.cuda.synchronize()
     got = r.cpu().numpy()
