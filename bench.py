@@ -341,8 +341,9 @@ def run_prep(args, dev, x, plane, snr, bw, ms_brute, stream):
         res[name] = r
     res["multiband_FLH_vs_F"] = (ms_brute + res["dedisperse_L"]["ms"] + res["dedisperse_H"]["ms"]) / ms_brute
     res["note"] = ("algorithmic bytes: zero-DM reads and writes the input once; downsampling reads it once and "
-                   "writes 1/8; median/MAD reads the plane once (the kernel makes 3 passes on noise-like rows); the robust boxcar "
-                   "reads the plane and writes S/N + width (4 + 4 + 1 bytes per output); gridding reads the plane "
+                   "writes 1/8; median/MAD reads the plane once (the kernel makes 3 passes on noise-like rows); "
+                   "the robust boxcar reads the plane and writes S/N + width (4 + 4 + 1 bytes per output); gridding "
+                   "reads the plane "
                    "once (the kernel makes 2 passes) into 0.5 s slices of 512 x 512 (area path); HBM peak of "
                    "measured")
     for v in halves.values():
