@@ -30,6 +30,17 @@ __device__ __forceinline__ uint32_t sqlaw_value(uint64_t T, uint32_t N, float rc
     return v < 255u ? v : 255u;
 }
 
+// The same for D <= 16384, in 32 bits: T = 4 V S <= 4 * 255 * 255 * D < 2^32 and
+// r <= 510, so r^2 N <= 260100 D < 2^32 as well.
+__device__ __forceinline__ uint32_t sqlaw_value32(uint32_t T, uint32_t N, float rcpN)
+{
+    uint32_t r = (uint32_t)sqrtf((float)T * rcpN);
+    if (r * r * N > T) r--;
+    if ((r + 1) * (r + 1) * N <= T) r++;
+    const uint32_t v = (r + 1) / 2;
+    return v < 255u ? v : 255u;
+}
+
 __global__ void __launch_bounds__(kDsThreads)
 k_downsample(const uint8_t* __restrict__ X, int64_t nsamp, int D, int64_t nout, int tb, unsigned runs,
              uint8_t* __restrict__ out)
@@ -68,7 +79,8 @@ k_downsample(const uint8_t* __restrict__ X, int64_t nsamp, int D, int64_t nout, 
         for (; i < b; i++) S += sx[i];
         const uint32_t N = (uint32_t)(b - a);
         const float rcpN = N == (uint32_t)D ? rcpD : 1.0f / (float)N;  // only the last bin is short
-        out[(int64_t)c * nout + k0 + k] = (uint8_t)sqlaw_value(4ull * 255ull * S, N, rcpN);
+        out[(int64_t)c * nout + k0 + k] = D <= 16384 ? (uint8_t)sqlaw_value32(1020u * S, N, rcpN)
+                                                     : (uint8_t)sqlaw_value(4ull * 255ull * S, N, rcpN);
     }
 }
 

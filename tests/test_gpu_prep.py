@@ -27,12 +27,14 @@ def _lib():
     return _lib
 
 
+# D <= 16384 takes the kernel's 32-bit arithmetic, larger D the 64-bit one
 @pytest.mark.parametrize("shape,D", [((3, 1000), 1), ((5, 1001), 3), ((64, 4096), 8), ((7, 100003), 64),
-                                     ((2, 70000), 32768), ((1, 17), 16), ((4096, 1 << 14), 4)])
+                                     ((2, 40000), 16384), ((2, 70000), 32768), ((1, 17), 16), ((4096, 1 << 14), 4)])
 def test_downsample_bit_exact(shape, D):
     rng = np.random.default_rng(shape[0] * 7 + D)
     X = rng.integers(0, 256, size=shape, dtype=np.uint8)
     X[0, :min(shape[1], 50)] = 255          # saturating bins
+    X[-1, :min(shape[1], D)] = 255          # a whole bin at 255: the largest sums
     ref = oracle.downsample_sqlaw(X, D)
     x = torch.from_numpy(X).cuda()
     out = torch.empty(ref.shape, dtype=torch.uint8, device="cuda")
@@ -49,7 +51,9 @@ def test_downsample_argument_errors():
             L.af_downsample(x.data_ptr(), 2, 10, D, x.data_ptr())
 
 
-@pytest.mark.parametrize("shape", [(1, 7), (2, 9), (64, 4096), (37, 10001), (4096, 8192), (255, 1 << 12)])
+# the 512-sample path (nsamp % 512 == 0, 16-byte aligned rows) and the generic kernel
+@pytest.mark.parametrize("shape", [(1, 7), (2, 9), (31, 32), (64, 4096), (37, 10001), (4096, 8192), (4097, 96),
+                                   (6144, 64), (255, 1 << 12), (8192, 1024)])
 @pytest.mark.parametrize("inplace", [False, True])
 def test_zerodm_bit_exact(shape, inplace):
     rfi = synth.RFI(bursts=[(shape[1] // 3, 5, 60.0)], narrow_channels=[0])
