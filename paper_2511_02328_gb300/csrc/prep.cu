@@ -103,7 +103,7 @@ extern "C" int af_downsample(const uint8_t* d_in, int nchan, int64_t nsamp, int 
 // ---------------------------------------------------------------- zero-DM
 // Zero-DM filter: q[t] = round_half_up(sum_c X[c][t] / nchan), out = clip(X - q + 128).
 // Fast path (rows 16-byte aligned, nsamp % 16 == 0): a block owns a tile of
-// 512 samples; its 8 warps split the channels, lane l holding samples
+// 512 samples; its 16 warps split the channels, lane l holding samples
 // [16 l, 16 l + 16) of the tile as one 16-byte load per channel.
 //   pass 1: per-warp channel sums in 16-bit lanes (bytes 0,2 / 1,3 of each
 //           word, folded into 32-bit sums every 256 channels), reduced across
