@@ -74,7 +74,7 @@ constexpr int kBOut = kBT * kPer;    // outputs per block
 // With SMALL (every window sum < 2^31) the difference B - q is formed and
 // converted in 32 bits.
 template <bool SMALL>
-__global__ void __launch_bounds__(kBT, 3)
+__global__ void __launch_bounds__(kBT, 4)
 k_boxcar(const int32_t* __restrict__ Y, int64_t nout, unsigned tiles, af_widths_t w,
          const af_rowconst_t* __restrict__ rc, float* __restrict__ snr, uint8_t* __restrict__ bw)
 {
