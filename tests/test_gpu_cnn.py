@@ -110,6 +110,37 @@ def test_cutouts_bit_exact(pulse_data):
     p.close()
 
 
+@pytest.mark.parametrize("nsamp", [1 << 13, (1 << 13) + 5])
+def test_cutouts_wide_band_and_foreign_rows(nsamp):
+    """1024 channels (16 per frequency-time row, 128 per CTA of the cluster),
+    wide and narrow bins at both ends of the plane, and candidates whose DM
+    index is not a row of the plan (zero cut-outs, the rest unaffected); input
+    rows of whole 16-byte blocks (16-byte loads) and not (byte loads)."""
+    from paper_2511_02328_gb300 import _lib
+    from paper_2511_02328_gb300.search import Plan
+    nchan, f_lo, f_hi, tsamp = 1024, 1200.0, 1500.0, 1e-4
+    dms = np.arange(0.0, 40.0, 1.0)
+    X = synth.filterbank(nchan, nsamp, seed=21)
+    D = oracle.delay_table(nchan, f_lo, f_hi, tsamp, dms)
+    Y = oracle.dedisperse(X, D)
+    nout = Y.shape[1]
+    good = [(20, nout // 2, 64), (0, 3, 1), (39, nout - 1, 16), (5, 900, 128)]
+    cands = good[:2] + [(-1, 100, 4)] + good[2:] + [(len(dms), 50, 8)]
+    p = Plan(nchan, f_lo, f_hi, tsamp, dms)
+    xd = torch.from_numpy(X).cuda()
+    plane = p.dedisperse(xd)
+    cd = _cand_array(cands)
+    out = torch.empty((len(cands), 64, 64, 2), dtype=torch.bfloat16, device="cuda")
+    _lib.af_cutouts(p.handle, xd.data_ptr(), nsamp, plane.data_ptr(), nout, cd.data_ptr(), len(cands),
+                    out.data_ptr())
+    torch.cuda.synchronize()
+    got = out.float().cpu().numpy().transpose(0, 3, 1, 2)
+    ref = cutout.cutouts(X, D, Y, good)
+    assert np.array_equal(got[[0, 1, 3, 4]], ref)
+    assert not got[2].any() and not got[5].any()
+    p.close()
+
+
 def test_forward_and_gradients_match_oracle():
     from paper_2511_02328_gb300 import _lib
     rng = np.random.default_rng(7)
