@@ -51,9 +51,10 @@ def test_downsample_argument_errors():
             L.af_downsample(x.data_ptr(), 2, 10, D, x.data_ptr())
 
 
-# the 512-sample path (nsamp % 512 == 0, 16-byte aligned rows) and the generic kernel
-@pytest.mark.parametrize("shape", [(1, 7), (2, 9), (31, 32), (64, 4096), (37, 10001), (4096, 8192), (4097, 96),
-                                   (6144, 64), (255, 1 << 12), (8192, 1024)])
+# the 512-sample tile path (nsamp % 512 == 0, 16-byte aligned rows, at least 16 channels) and the generic kernel
+@pytest.mark.parametrize("shape", [(1, 7), (2, 9), (31, 32), (1, 128), (5, 256), (64, 4096), (37, 10001),
+                                   (4096, 8192), (4097, 96), (6144, 64), (255, 1 << 12), (8192, 1024),
+                                   (16, 1 << 16), (1025, 1 << 15)])
 @pytest.mark.parametrize("inplace", [False, True])
 def test_zerodm_bit_exact(shape, inplace):
     rfi = synth.RFI(bursts=[(shape[1] // 3, 5, 60.0)], narrow_channels=[0])
