@@ -85,3 +85,23 @@ def test_nout_bounds_checked():
     D = np.full((1, 4), 10, dtype=np.int32)
     with pytest.raises(ValueError):
         oracle.dedisperse(X, D)
+
+
+@pytest.mark.parametrize("nchan,hop,nwin", [(16, 120, 4), (7, 37, 3), (33, 1, 5)])
+def test_windows_with_hop_nout_tile_the_one_shot_plane(nchan, hop, nwin):
+    # Streaming reading of Sec. 2.3 with nout = nsamp - Dmax: windows of Dmax + hop
+    # samples that start every hop samples (consecutive windows overlap by Dmax)
+    # give planes of hop columns each, and their concatenation is the plane of the
+    # whole input, column for column.
+    rng = np.random.default_rng(nchan)
+    D = oracle.delay_table(nchan, 1000.0, 1500.0, 1e-3, np.arange(0.0, 30.0, 3.0))
+    dmax = int(D.max())
+    assert dmax > 0
+    window = dmax + hop
+    total = (nwin - 1) * hop + window
+    X = rng.integers(0, 256, (nchan, total), dtype=np.uint8)
+    Y = oracle.dedisperse(X, D)
+    assert Y.shape[1] == nwin * hop
+    parts = [oracle.dedisperse(X[:, k * hop:k * hop + window], D) for k in range(nwin)]
+    assert all(p.shape[1] == hop for p in parts)
+    assert np.array_equal(np.concatenate(parts, axis=1), Y)
