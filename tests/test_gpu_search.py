@@ -539,3 +539,28 @@ def test_workspace_sizes_match_reservations(c1_data):
         _lib.af_dedisperse_workspace_size(p.handle, int(D.max()))     # nsamp <= Dmax
     p.close()
     q.close()
+
+
+def test_cluster_equals_the_oracle_rule():
+    """af_cluster against the oracle's greedy rule (Sec. 4.2 tolerances: |dDM| < 20,
+    |dTOA| < 0.2 s) on random candidate lists with many equal S/N values: the same
+    clusters are kept, in the same order."""
+    from oracle import nms
+    from paper_2511_02328_gb300 import _lib
+    dms = dm_list(C1)
+    p = _plan(C1)
+    rng = np.random.default_rng(11)
+    span = 30000
+    for n in (0, 1, 2, 50, 400, 2000):
+        key = rng.choice(len(dms) * span, size=n, replace=False)   # distinct (dm_idx, t)
+        a = np.zeros(n, dtype=_lib.CAND_DTYPE)
+        a["dm_idx"] = key // span
+        a["t"] = key % span
+        a["abs_sample"] = a["t"]
+        a["width"] = 1 << rng.integers(0, 6, n)
+        a["snr"] = rng.choice(np.arange(6.0, 30.0, 0.5), n)
+        kept = p.cluster(a.copy())
+        ref = nms.cluster([(int(c["dm_idx"]), int(c["t"]), int(c["width"]), float(c["snr"])) for c in a],
+                          dms, C1["tsamp"])
+        assert [(int(c["dm_idx"]), int(c["t"])) for c in kept] == [(c[0], c[1]) for c in ref], n
+    p.close()
