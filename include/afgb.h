@@ -599,6 +599,19 @@ int af_diag_int_rates(double* add_per_s, double* pattern_adds_per_s);
  * milliseconds, synchronous; allocates nothing.  AF_EINVAL if bytes_per_s is
  * NULL. */
 int af_diag_smem_rate(double* bytes_per_s);
+/* Failure path of the bounded device waits, made to happen.  The ring kernels
+ * (tile, group-row and subband stage-2 kernels) wait on mbarriers with at most
+ * 2^18 polls; a wait that runs out raises the plan's (batch's, engine's) error
+ * flag and the kernel returns, so a lost arrival surfaces as AF_ETIMEOUT and
+ * never as a hang.  This probe runs the same bounded poll loop in one block of
+ * 128 threads on the legacy default stream: arrive = 0 waits on a barrier that
+ * nothing arrives at, so every wait gives up after `polls` polls and the call
+ * returns AF_ETIMEOUT; arrive != 0 lets one thread arrive first and returns
+ * AF_OK.  *ms (nullable) receives the kernel's duration, i.e. how long `polls`
+ * polls of a wait that never completes take on this device.  Synchronous;
+ * allocates nothing; AF_EINVAL unless 1 <= polls <= 2^24.  Not a step of the
+ * paper's method. */
+int af_diag_bounded_wait(int arrive, int64_t polls, float* ms);
 
 /* ---- candidate classifier ----------------------------------------------- *
  * The paper detects pulses with a YOLOv11n network on DM-time images

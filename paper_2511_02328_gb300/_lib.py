@@ -63,6 +63,7 @@ SIGNATURES = {
     "af_grid": [_P, _I, _I64, _I64, _I, _P, _P, _P],
     "af_diag_int_rates": [_P, _P],
     "af_diag_smem_rate": [_P],
+    "af_diag_bounded_wait": [_I, _I64, _P],
     "af_plan_destroy": [_P],
     "af_plan_delays": [_P, _P, _P],
     "af_plan_info": [_P, _P, _P, _P, _P],
@@ -206,6 +207,15 @@ def af_diag_smem_rate():
     a = ctypes.c_double()
     _check(lib().af_diag_smem_rate(ctypes.byref(a)), "af_diag_smem_rate")
     return a.value
+
+
+def af_diag_bounded_wait(arrive, polls):
+    """Bounded-wait probe: (status, ms).  AF_ETIMEOUT when nothing arrived and
+    the wait gave up after `polls` polls, AF_OK when the arrival came."""
+    ms = ctypes.c_float()
+    rc = _check(lib().af_diag_bounded_wait(int(arrive), int(polls), ctypes.byref(ms)), "af_diag_bounded_wait",
+                allow=(AF_ETIMEOUT,))
+    return rc, ms.value
 
 
 AF_FS_MEDIAN = 0

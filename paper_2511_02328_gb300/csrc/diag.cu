@@ -14,10 +14,17 @@
 //            load bandwidth the group-row tile kernel is bound by.
 // Results go to a static device array (no allocation); every shared address is
 // inside the block's own array.
+//
+// A fourth probe exercises the failure path of the bounded mbarrier waits that
+// the ring kernels (tile, group-row and subband stage-2 kernels) use: one block
+// waits on a barrier that nothing arrives at, with the same poll loop
+// (afptx::mbar_wait_bounded), raises the error flag the way those kernels do
+// and returns, so that the host reads AF_ETIMEOUT and the context stays usable.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "internal.h"
+#include "ptx.cuh"
 
 namespace {
 
@@ -107,6 +114,29 @@ int time_probe(int nblk, float* ms)
     return af_cuda_check(e, "af_diag_int_rates probe");
 }
 
+// Error flag of the bounded-wait probe (a static device variable: no allocation).
+__device__ int g_diag_wait_err;
+
+// One block of 128 threads waits on an mbarrier of one arrival.  arrive = 1:
+// thread 0 arrives, the phase completes and every wait succeeds.  arrive = 0:
+// nothing arrives, every thread's wait gives up after `polls` polls, lane 0 of
+// each warp raises the flag (as the ring kernels' warps do) and the block
+// returns.  No copy is in flight, so nothing else has to drain.
+__global__ void __launch_bounds__(128) k_diag_wait(int arrive, uint32_t polls)
+{
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t b = afptx::smem_addr(&bar);
+    if (threadIdx.x == 0) {
+        afptx::mbar_init(b, 1);
+        afptx::fence_mbar_init();
+    }
+    __syncthreads();
+    if (arrive && threadIdx.x == 0) afptx::mbar_arrive(b);
+    if (!afptx::mbar_wait_bounded(b, 0u, polls) && (threadIdx.x & 31) == 0) atomicExch(&g_diag_wait_err, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) afptx::mbar_inval(b);
+}
+
 }  // namespace
 
 extern "C" int af_diag_smem_rate(double* bytes_per_s)
@@ -135,5 +165,33 @@ extern "C" int af_diag_int_rates(double* add_per_s, double* pattern_adds_per_s)
     const double threads = (double)nblk * kDT * kDIters;
     *add_per_s = threads * 8.0 / (ms0 * 1e-3);
     *pattern_adds_per_s = threads * 8.0 / (ms1 * 1e-3);
+    return AF_OK;
+}
+
+extern "C" int af_diag_bounded_wait(int arrive, int64_t polls, float* ms)
+{
+    if (polls < 1 || polls > (int64_t)1 << 24)
+        return af_set_error(AF_EINVAL, "af_diag_bounded_wait: polls %lld outside 1..2^24", (long long)polls);
+    const int zero = 0;
+    AF_CUDA(cudaMemcpyToSymbol(g_diag_wait_err, &zero, sizeof zero));
+    cudaEvent_t a, b;
+    AF_CUDA(cudaEventCreate(&a));
+    AF_CUDA(cudaEventCreate(&b));
+    cudaEventRecord(a);
+    k_diag_wait<<<1, 128>>>(arrive ? 1 : 0, (uint32_t)polls);
+    cudaEventRecord(b);
+    cudaError_t e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+    int err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&err, g_diag_wait_err, sizeof err);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (int rc = af_cuda_check(e, "af_diag_bounded_wait")) return rc;
+    if (ms) *ms = t;
+    if (err)
+        return af_set_error(AF_ETIMEOUT, "af_diag_bounded_wait: the wait ran out after %lld polls (%.3f ms)",
+                            (long long)polls, (double)t);
     return AF_OK;
 }

@@ -56,7 +56,7 @@ constexpr int kPSL = 32;
 constexpr int kPMG = 16;            // 2-sample groups per lane
 constexpr int kPTTE = 1016;         // outputs per tile: a multiple of 8 below 64 * kPMG - 1
 constexpr int kPTABW = 40;          // ints per (stage, warp) table: 2 starts, 2 counts, <= 34 offsets
-constexpr uint32_t kPWait = 1u << 24;
+constexpr uint32_t kPWait = afptx::kMbarWaitPolls;
 constexpr int kET = 4096;           // stage 1: row samples per block
 constexpr int kS1T = 256;
 constexpr int kMaxDr = 32768;       // stage 1: largest range of one relative delay over a group's rows

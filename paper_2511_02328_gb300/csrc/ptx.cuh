@@ -64,6 +64,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
+// Poll limit of the ring kernels' mbarrier waits.  A poll of a phase that does
+// not complete returns after the hardware's suspend window (measured on GB300
+// by af_diag_bounded_wait: 3.8 us per poll), so 2^18 polls give up after about
+// one second; a wait that succeeds lasts one ring stage, microseconds.
+constexpr uint32_t kMbarWaitPolls = 1u << 18;
+
 // Bounded wait: returns false if the phase did not complete within `limit` polls.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint32_t limit)
 {

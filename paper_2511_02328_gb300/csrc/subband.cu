@@ -39,7 +39,7 @@ constexpr int kS2Threads = 256;
 constexpr int kS2BufBytes = 24576;       // target bytes per stage-2 buffer
 constexpr int64_t kScratchBudget = (int64_t)1 << 30;  // default stage-1 scratch
 constexpr int64_t kMaxDefaultL = (int64_t)1 << 18;
-constexpr uint32_t kS2WaitLimit = 1u << 24;
+constexpr uint32_t kS2WaitLimit = afptx::kMbarWaitPolls;
 constexpr int kS2RBytes = 16384;          // residual-shift table kept in shared memory up to this size
 
 template <typename T, int NM>

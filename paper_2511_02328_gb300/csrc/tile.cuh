@@ -50,7 +50,7 @@ constexpr int NSTAGE = 4;              // default depth of the shared-memory rin
 constexpr int TABW = 48;               // ints per (stage, warp) table: 4 starts, 4 counts,
                                        // 40 offsets (at most 35 used; the slack absorbs
                                        // one-pair-ahead reads)
-constexpr uint32_t WAIT_LIMIT = 1u << 24;
+constexpr uint32_t WAIT_LIMIT = afptx::kMbarWaitPolls;
 constexpr int FLUSH_CHUNKS = 256 / CC;
 
 // One beam's dedispersion job (also the argument block of the kernels).

@@ -64,3 +64,9 @@ def test_host_only_calls_without_gpu(libpath):
         _lib.af_plan(16, 1000.0, 1500.0, 1e-3, [-5.0])
     assert e.value.code == _lib.AF_EINVAL
     assert "dm_list" in _lib.af_last_error()
+    with pytest.raises(_lib.AFError) as e:
+        _lib.af_diag_bounded_wait(0, 0)
+    assert e.value.code == _lib.AF_EINVAL
+    with pytest.raises(_lib.AFError) as e:
+        _lib.af_diag_bounded_wait(0, (1 << 24) + 1)
+    assert e.value.code == _lib.AF_EINVAL
