@@ -240,7 +240,13 @@ int af_plan_subband_info(af_plan_t plan, int* n0, int* nsub, int* ncoarse, int32
  *  d_stats  optional af_rowstats_t [ndm] output (may be NULL)
  * Enqueued on `stream`.  Brute-force plans run the group-row kernels once
  * af_dedisperse_reserve (or af_search_reserve) has reserved their row buffer,
- * else the channel tile kernel; both give the same plane. */
+ * else the channel tile kernel; both give the same plane.  Never allocates.
+ * AF_EINVAL for a NULL buffer, a d_in not 16-byte aligned, nsamp <= Dmax or
+ * nout > 2^31 - 1; AF_ECUDA if the launch fails.  A device wait that ran out
+ * (AF_ETIMEOUT) is reported by af_plan_check, which waits for the device. */
+int af_dedisperse(af_plan_t plan, const uint8_t* d_in, int64_t nsamp,
+                  int32_t* d_plane, af_rowstats_t* d_stats, void* stream);
+
 /* Reserves the group-row buffer of a brute-force plan (af_plan_kernel path
  * AF_PATH_PAIRS) for inputs of up to max_nsamp samples, if a cost model
  * (rates measured on GB300) predicts group rows faster than the channel tile
@@ -274,8 +280,6 @@ int af_dedisperse_workspace_size(af_plan_t plan, int64_t max_nsamp, size_t* byte
 int af_dedisperse_timing(af_plan_t plan, int ncalls);
 int af_dedisperse_times(af_plan_t plan, int call, float* rows_ms, float* tiles_ms, int64_t* row_bytes,
                         int64_t* copy_bytes);
-int af_dedisperse(af_plan_t plan, const uint8_t* d_in, int64_t nsamp,
-                  int32_t* d_plane, af_rowstats_t* d_stats, void* stream);
 
 /* Row sums of a plane [ndm][nout] into d_stats [ndm] (see af_rowstats_t). */
 int af_rowstats(af_plan_t plan, const int32_t* d_plane, int64_t nout,
