@@ -281,7 +281,9 @@ int af_dedisperse_timing(af_plan_t plan, int ncalls);
 int af_dedisperse_times(af_plan_t plan, int call, float* rows_ms, float* tiles_ms, int64_t* row_bytes,
                         int64_t* copy_bytes);
 
-/* Row sums of a plane [ndm][nout] into d_stats [ndm] (see af_rowstats_t). */
+/* Row sums of a plane [ndm][nout] into d_stats [ndm] (see af_rowstats_t).
+ * Enqueued on `stream`.  AF_EINVAL for a NULL buffer or nout outside
+ * 1..2^31-1. */
 int af_rowstats(af_plan_t plan, const int32_t* d_plane, int64_t nout,
                 af_rowstats_t* d_stats, void* stream);
 
@@ -298,10 +300,12 @@ int af_rowstats(af_plan_t plan, const int32_t* d_plane, int64_t nout,
  *  d_stats     row sums from af_dedisperse/af_rowstats, or NULL: then the
  *              library computes them into the plan's scratch first
  *  widths      HOST array of nw strictly ascending widths, 1 <= w <= nout,
- *              nw <= AF_MAX_WIDTHS, and w * 255 * nchan < 2^32
+ *              w <= 8192, nw <= AF_MAX_WIDTHS, and w * 255 * nchan < 2^32
  *  d_best_snr  float [ndm][nout] output
  *  d_best_w    uint8 [ndm][nout] output (may be NULL)
- * Uses the plan's scratch (per-row normalisation constants). */
+ * Uses the plan's scratch (per-row normalisation constants); never allocates.
+ * Enqueued on `stream`.  AF_EINVAL for a NULL plane or S/N buffer, nout
+ * outside 1..2^31-1 or a width list outside these rules. */
 int af_boxcar_snr(af_plan_t plan, const int32_t* d_plane, int64_t nout,
                   const af_rowstats_t* d_stats, const int32_t* widths, int nw,
                   float* d_best_snr, uint8_t* d_best_w, void* stream);
@@ -378,7 +382,10 @@ int af_grid(const int32_t* d_plane, int ndm, int64_t nout, int64_t ns, int M, ui
  *  d_best_snr, d_best_w  outputs of af_boxcar_snr ([ndm][nout])
  *  widths, nw            the same host width list
  *  sample0               added to t to form abs_sample
- *  d_out                 af_cand_t [cap] output; d_count int32 [1] output */
+ *  d_out                 af_cand_t [cap] output; d_count int32 [1] output
+ * Enqueued on `stream`.  AF_EINVAL for a NULL buffer (d_out may be NULL only
+ * with cap = 0), a negative cap, nout outside 1..2^31-1, a non-finite
+ * threshold or a width list af_boxcar_snr would reject. */
 int af_candidates(af_plan_t plan, const float* d_best_snr, const uint8_t* d_best_w,
                   int64_t nout, const int32_t* widths, int nw, float thresh,
                   int64_t sample0, af_cand_t* d_out, int32_t cap, int32_t* d_count,
