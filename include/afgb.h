@@ -11,6 +11,13 @@
  * Conventions shared by every call:
  *  - Every call returns an int status: AF_OK (0) or one of the AF_E* codes.
  *    af_last_error() returns a thread-local message for the last failure.
+ *  - Errors, unless a call's own comment adds to them: AF_EINVAL for a NULL
+ *    handle, a NULL required pointer or a size outside its stated range
+ *    (checked before any work is enqueued); AF_ECUDA when a CUDA call or a
+ *    launch fails; AF_ENOMEM when an allocation fails (only the calls that
+ *    create, reserve, build or open allocate device or pinned memory; the
+ *    *_timing calls create CUDA events).  A call rejected for its arguments
+ *    has enqueued nothing and changed nothing.
  *  - Pointers named d_* are DEVICE pointers owned by the caller (for example
  *    torch tensors); pointers named h_* or host_* are host pointers owned by
  *    the caller.  The library never frees caller memory.
