@@ -64,6 +64,25 @@ def test_constant_row_is_zero_snr():
     assert np.all(bw[:, :61] == 0)
 
 
+def test_best_width_exact_tie_goes_to_the_smaller_width():
+    # With widths 1 and 4 (sqrt(4) = 2 exactly) a row can tie exactly: at t = 0
+    # nout*B_4 - 4*S = 2*(nout*B_1 - S), so snr_4 = (2 num)/(2 den) = snr_1 in IEEE
+    # arithmetic.  Row: 16 samples, S = 160 (mean 10), Q = 2400, sigma = sqrt(50);
+    # B_1 = 30, B_4 = 80: both S/N are 20 / sqrt(50) = 2 sqrt(2).
+    Y = np.array([[30, 20, 20, 10] + [5] * 8 + [10] * 4], dtype=np.int32)
+    snr, bw = oracle.boxcar_snr(Y, [1, 4])
+    assert snr[0, 0] == pytest.approx(2.0 * math.sqrt(2.0), rel=1e-15)
+    assert bw[0, 0] == 0
+    bs, bb = brute.boxcar_snr(Y.tolist(), [1, 4])
+    assert bb[0][0] == 0 and bs[0][0] == pytest.approx(2.0 * math.sqrt(2.0), rel=1e-15)
+    # one count more in the 4-sample window breaks the tie towards width 4
+    Y2 = Y.copy()
+    Y2[0, 3] += 1
+    Y2[0, 15] -= 1
+    _, bw2 = oracle.boxcar_snr(Y2, [1, 4])
+    assert bw2[0, 0] == 1
+
+
 @pytest.mark.parametrize("seed", range(8))
 def test_snr_matches_brute_force(seed):
     rng = np.random.default_rng(100 + seed)
