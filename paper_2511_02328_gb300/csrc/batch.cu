@@ -391,7 +391,7 @@ static int autotune(af_batch_t b)
 }
 
 extern "C" int af_batch_build(af_batch_t* out, const af_beam_desc_t* beams, int nbeams, size_t hbm_budget)
-{
+try {
     if (!out || !beams || nbeams < 1 || nbeams > 4096) return af_set_error(AF_EINVAL, "af_batch_build: bad arguments");
     *out = nullptr;
     af_batch_s* b = new (std::nothrow) af_batch_s();
@@ -456,10 +456,12 @@ extern "C" int af_batch_build(af_batch_t* out, const af_beam_desc_t* beams, int 
     }
     *out = b;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_batch_build");
 }
 
 extern "C" int af_batch_run(af_batch_t b, void* stream)
-{
+try {
     if (!b) return af_set_error(AF_EINVAL, "af_batch_run: NULL batch");
     cudaStream_t s = (cudaStream_t)stream;
     if (!b->exec) {
@@ -481,10 +483,12 @@ extern "C" int af_batch_run(af_batch_t b, void* stream)
     }
     AF_CUDA(cudaGraphLaunch(b->exec, s));
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_batch_run");
 }
 
 extern "C" int af_batch_candidates(af_batch_t b, int beam, af_cand_t* h_out, int32_t cap, int32_t* h_count)
-{
+try {
     if (!b || beam < 0 || beam >= (int)b->beams.size() || !h_count || (cap > 0 && !h_out))
         return af_set_error(AF_EINVAL, "af_batch_candidates: bad arguments");
     Beam& x = b->beams[beam];
@@ -508,11 +512,13 @@ extern "C" int af_batch_candidates(af_batch_t b, int beam, af_cand_t* h_out, int
     *h_count = total;
     if (total > std::min(cap, x.cap)) return af_set_error(AF_EOVERFLOW, "af_batch_candidates: %d found", total);
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_batch_candidates");
 }
 
 extern "C" int af_batch_buffers(af_batch_t b, int beam, int32_t** d_plane, float** d_snr, uint8_t** d_bw,
                                 int64_t* nout)
-{
+try {
     if (!b || beam < 0 || beam >= (int)b->beams.size()) return af_set_error(AF_EINVAL, "af_batch_buffers: bad beam");
     Beam& x = b->beams[beam];
     if (d_plane) *d_plane = x.d_plane;
@@ -520,20 +526,26 @@ extern "C" int af_batch_buffers(af_batch_t b, int beam, int32_t** d_plane, float
     if (d_bw) *d_bw = x.d_bw;
     if (nout) *nout = x.nout;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_batch_buffers");
 }
 
 extern "C" int af_batch_shape(af_batch_t b, int* nw, int* m, float* tuned_ms, int* from_cache)
-{
+try {
     if (!b) return af_set_error(AF_EINVAL, "af_batch_shape: NULL batch");
     if (nw) *nw = b->shape == kPairs ? 15 : kShapes[b->shape].nw;
     if (m) *m = b->shape == kPairs ? 0 : kShapes[b->shape].m;
     if (tuned_ms) *tuned_ms = b->tuned_ms;
     if (from_cache) *from_cache = b->from_cache ? 1 : 0;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_batch_shape");
 }
 
 extern "C" int af_batch_destroy(af_batch_t b)
-{
+try {
     free_batch(b);
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_batch_destroy");
 }

@@ -288,7 +288,7 @@ int af_launch_dedisperse(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_
 }
 
 extern "C" int af_plan_kernel(af_plan_t p, int* path, int* ring, int32_t* spread, int* group)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     int pa = AF_PATH_SIMPLE, rg = 0, sp = p->tile.spread, gr = 1;
     if (p->sb_nsub > 0 && p->sb.tile.fits && !p->force_simple && !p->force_brute) {
@@ -309,6 +309,8 @@ extern "C" int af_plan_kernel(af_plan_t p, int* path, int* ring, int32_t* spread
     if (spread) *spread = sp;
     if (group) *group = gr;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_plan_kernel");
 }
 
 int af_launch_rowstats(const int32_t* d_plane, int ndm, int64_t nout, af_rowstats_t* d_stats, cudaStream_t s)

@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(128) k_diag_wait(int arrive, uint32_t polls)
 }  // namespace
 
 extern "C" int af_diag_smem_rate(double* bytes_per_s)
-{
+try {
     if (!bytes_per_s) return af_set_error(AF_EINVAL, "af_diag_smem_rate: NULL output");
     int dev = 0, nsm = 0;
     AF_CUDA(cudaGetDevice(&dev));
@@ -150,10 +150,12 @@ extern "C" int af_diag_smem_rate(double* bytes_per_s)
     if (int rc = time_probe<2>(nblk, &ms)) return rc;
     *bytes_per_s = (double)nblk * kDT * kDIters * 8.0 * 4.0 / (ms * 1e-3);
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_diag_smem_rate");
 }
 
 extern "C" int af_diag_int_rates(double* add_per_s, double* pattern_adds_per_s)
-{
+try {
     if (!add_per_s || !pattern_adds_per_s) return af_set_error(AF_EINVAL, "af_diag_int_rates: NULL output");
     int dev = 0, nsm = 0;
     AF_CUDA(cudaGetDevice(&dev));
@@ -166,10 +168,12 @@ extern "C" int af_diag_int_rates(double* add_per_s, double* pattern_adds_per_s)
     *add_per_s = threads * 8.0 / (ms0 * 1e-3);
     *pattern_adds_per_s = threads * 8.0 / (ms1 * 1e-3);
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_diag_int_rates");
 }
 
 extern "C" int af_diag_bounded_wait(int arrive, int64_t polls, float* ms)
-{
+try {
     if (polls < 1 || polls > (int64_t)1 << 24)
         return af_set_error(AF_EINVAL, "af_diag_bounded_wait: polls %lld outside 1..2^24", (long long)polls);
     const int zero = 0;
@@ -194,4 +198,6 @@ extern "C" int af_diag_bounded_wait(int arrive, int64_t polls, float* ms)
         return af_set_error(AF_ETIMEOUT, "af_diag_bounded_wait: the wait ran out after %lld polls (%.3f ms)",
                             (long long)polls, (double)t);
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_diag_bounded_wait");
 }

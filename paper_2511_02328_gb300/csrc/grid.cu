@@ -186,7 +186,7 @@ void launch_pass(bool area, unsigned blocks, cudaStream_t st, const int32_t* X, 
 
 extern "C" int af_grid(const int32_t* d_plane, int ndm, int64_t nout, int64_t ns, int M, uint8_t* d_out,
                        int64_t* d_work, void* stream)
-{
+try {
     if (!d_plane || !d_out || !d_work) return af_set_error(AF_EINVAL, "af_grid: NULL buffer");
     if (ndm < 1 || nout < 1 || ns < 1) return af_set_error(AF_EINVAL, "af_grid: empty plane or slice");
     if (M < 2 || M > 4096) return af_set_error(AF_EINVAL, "af_grid: M %d not in 2..4096", M);
@@ -222,4 +222,6 @@ extern "C" int af_grid(const int32_t* d_plane, int ndm, int64_t nout, int64_t ns
         if (int rc = af_cuda_check(cudaGetLastError(), "af_grid launch")) return rc;
     }
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_grid");
 }

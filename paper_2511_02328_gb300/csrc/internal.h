@@ -12,6 +12,11 @@
 // ---------------------------------------------------------------- errors
 int af_set_error(int code, const char* fmt, ...);
 int af_cuda_check(cudaError_t e, const char* what);
+// Status for a C++ exception that reached an entry point (call it only inside a
+// catch handler): AF_ENOMEM for std::bad_alloc, else AF_EINVAL, with a message.
+// Every extern "C" int entry point is a function-try-block ending in it, so no
+// exception crosses the C ABI.
+int af_host_exception(const char* who);
 #define AF_CUDA(call)                                                  \
     do {                                                               \
         cudaError_t _e = (call);                                       \

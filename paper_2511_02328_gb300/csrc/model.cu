@@ -111,7 +111,7 @@ static void init_weights(af_model_t m, uint64_t seed, std::vector<float>& p)
 }
 
 extern "C" int af_model_create(af_model_t* out, int max_batch, uint64_t seed)
-{
+try {
     if (!out || max_batch < 1 || max_batch > 65536) return af_set_error(AF_EINVAL, "af_model_create: bad arguments");
     *out = nullptr;
     af_model_s* m = new (std::nothrow) af_model_s();
@@ -182,19 +182,25 @@ extern "C" int af_model_create(af_model_t* out, int max_batch, uint64_t seed)
     }
     *out = m;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_model_create");
 }
 
 extern "C" int af_model_destroy(af_model_t m)
-{
+try {
     free_model(m);
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_model_destroy");
 }
 
 extern "C" int af_model_nparams(af_model_t m, int64_t* n)
-{
+try {
     if (!m || !n) return af_set_error(AF_EINVAL, "af_model_nparams: NULL argument");
     *n = m->nparams;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_model_nparams");
 }
 
 static int copy_params(af_model_t m, float* dst, const float* src, int64_t n, cudaMemcpyKind kind, const char* what)
@@ -207,21 +213,27 @@ static int copy_params(af_model_t m, float* dst, const float* src, int64_t n, cu
 }
 
 extern "C" int af_model_set_params(af_model_t m, const float* h, int64_t n)
-{
+try {
     if (!m || !h) return af_set_error(AF_EINVAL, "af_model_set_params: NULL argument");
     return copy_params(m, m->d_params, h, n, cudaMemcpyHostToDevice, "af_model_set_params");
+} catch (...) {
+    return af_host_exception("af_model_set_params");
 }
 
 extern "C" int af_model_get_params(af_model_t m, float* h, int64_t n)
-{
+try {
     if (!m || !h) return af_set_error(AF_EINVAL, "af_model_get_params: NULL argument");
     return copy_params(m, h, m->d_params, n, cudaMemcpyDeviceToHost, "af_model_get_params");
+} catch (...) {
+    return af_host_exception("af_model_get_params");
 }
 
 extern "C" int af_model_get_grads(af_model_t m, float* h, int64_t n)
-{
+try {
     if (!m || !h) return af_set_error(AF_EINVAL, "af_model_get_grads: NULL argument");
     return copy_params(m, h, m->d_grads, n, cudaMemcpyDeviceToHost, "af_model_get_grads");
+} catch (...) {
+    return af_host_exception("af_model_get_grads");
 }
 
 static int forward(af_model_t m, const __nv_bfloat16* x, int n, const int32_t* y, float* prob, cudaStream_t s)
@@ -286,17 +298,19 @@ static int check_batch(af_model_t m, const void* x, int n)
 
 extern "C" int af_model_forward(af_model_t m, const uint16_t* d_x, int32_t n, float* d_logits, float* d_prob,
                                 void* stream)
-{
+try {
     if (int rc = check_batch(m, d_x, n)) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if (int rc = forward(m, (const __nv_bfloat16*)d_x, n, nullptr, d_prob, s)) return rc;
     if (d_logits) AF_CUDA(cudaMemcpyAsync(d_logits, m->d_logits, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_model_forward");
 }
 
 extern "C" int af_model_backward(af_model_t m, const uint16_t* d_x, const int32_t* d_y, int32_t n, float* d_loss,
                                  void* stream)
-{
+try {
     if (int rc = check_batch(m, d_x, n)) return rc;
     if (!d_y) return af_set_error(AF_EINVAL, "af_model_backward: labels NULL");
     cudaStream_t s = (cudaStream_t)stream;
@@ -304,29 +318,35 @@ extern "C" int af_model_backward(af_model_t m, const uint16_t* d_x, const int32_
     if (int rc = backward(m, n, s)) return rc;
     if (d_loss) AF_CUDA(cudaMemcpyAsync(d_loss, m->d_loss, 4, cudaMemcpyDeviceToDevice, s));
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_model_backward");
 }
 
 extern "C" int af_train_step(af_model_t m, const uint16_t* d_x, const int32_t* d_y, int32_t n, float lr,
                              float* d_loss, void* stream)
-{
+try {
     if (!(lr > 0.0f) || !isfinite(lr)) return af_set_error(AF_EINVAL, "af_train_step: bad learning rate");
     if (int rc = af_model_backward(m, d_x, d_y, n, d_loss, stream)) return rc;
     m->step++;
     return nn_adam(m->d_params, m->d_grads, m->d_m, m->d_v, m->nparams, lr, m->step, (cudaStream_t)stream);
+} catch (...) {
+    return af_host_exception("af_train_step");
 }
 
 extern "C" int af_nn_gemm(int layout, int epi, const uint16_t* d_a, int lda, const uint16_t* d_b, int ldb, int M,
                           int N, int K, int splits, float* d_c, int ldc, const float* d_bias, void* stream)
-{
+try {
     if (!d_a || !d_b || !d_c || (epi == NN_EPI_BIAS_RELU && !d_bias) || epi < 0 || epi > 2 || ldc < N)
         return af_set_error(AF_EINVAL, "af_nn_gemm: bad arguments");
     return nn_gemm(layout, epi, (const __nv_bfloat16*)d_a, lda, (const __nv_bfloat16*)d_b, ldb, M, N, K, splits, d_c,
                    ldc, d_bias, (cudaStream_t)stream);
+} catch (...) {
+    return af_host_exception("af_nn_gemm");
 }
 
 extern "C" int af_cutouts(af_plan_t p, const uint8_t* d_in, int64_t nsamp, const int32_t* d_plane, int64_t nout,
                           const af_cand_t* d_cands, int32_t n, uint16_t* d_out, void* stream)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     if (!d_in || !d_plane || (n > 0 && (!d_cands || !d_out)) || n < 0)
         return af_set_error(AF_EINVAL, "af_cutouts: NULL buffer");
@@ -334,11 +354,13 @@ extern "C" int af_cutouts(af_plan_t p, const uint8_t* d_in, int64_t nsamp, const
     if (nout != nsamp - p->dmax) return af_set_error(AF_EINVAL, "af_cutouts: nout must be nsamp - Dmax");
     return nn_cutouts(d_in, nsamp, p->nchan, p->d_delays, p->ndm, d_plane, nout, d_cands, n, (__nv_bfloat16*)d_out,
                       (cudaStream_t)stream);
+} catch (...) {
+    return af_host_exception("af_cutouts");
 }
 
 extern "C" int af_classify(af_model_t m, af_plan_t p, const uint8_t* d_in, int64_t nsamp, const int32_t* d_plane,
                            int64_t nout, const af_cand_t* d_cands, int32_t n, float* d_prob, void* stream)
-{
+try {
     if (!m || !d_prob) return af_set_error(AF_EINVAL, "af_classify: NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
     for (int32_t i0 = 0; i0 < n; i0 += m->max_batch) {
@@ -348,12 +370,14 @@ extern "C" int af_classify(af_model_t m, af_plan_t p, const uint8_t* d_in, int64
         if (int rc = forward(m, m->d_cut, k, nullptr, d_prob + i0, s)) return rc;
     }
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_classify");
 }
 
 // Checkpoint: a JSON header line, then raw little-endian fp32 parameters and
 // Adam moments.
 extern "C" int af_model_save(af_model_t m, const char* path)
-{
+try {
     if (!m || !path) return af_set_error(AF_EINVAL, "af_model_save: NULL argument");
     std::vector<float> buf(3 * m->nparams);
     AF_CUDA(cudaMemcpy(buf.data(), m->d_params, m->nparams * 4, cudaMemcpyDeviceToHost));
@@ -367,10 +391,12 @@ extern "C" int af_model_save(af_model_t m, const char* path)
     fclose(f);
     if (wrote != buf.size()) return af_set_error(AF_EINVAL, "af_model_save: short write");
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_model_save");
 }
 
 extern "C" int af_model_load(af_model_t m, const char* path)
-{
+try {
     if (!m || !path) return af_set_error(AF_EINVAL, "af_model_load: NULL argument");
     FILE* f = fopen(path, "rb");
     if (!f) return af_set_error(AF_EINVAL, "af_model_load: cannot open %s", path);
@@ -398,4 +424,6 @@ extern "C" int af_model_load(af_model_t m, const char* path)
     AF_CUDA(cudaMemcpy(m->d_v, buf.data() + 2 * m->nparams, m->nparams * 4, cudaMemcpyHostToDevice));
     m->step = step;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_model_load");
 }

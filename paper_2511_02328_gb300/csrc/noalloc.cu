@@ -61,7 +61,7 @@ int scratch_address(void** out)
 extern "C" int af_boxcar_snr_noalloc(const int32_t* d_plane, int ndm, int64_t nout, int nchan,
                                      const int32_t* widths, int nw, float* d_best_snr, uint8_t* d_best_w,
                                      void* stream)
-{
+try {
     if (!d_plane || !d_best_snr) return af_set_error(AF_EINVAL, "af_boxcar_snr_noalloc: NULL buffer");
     if (ndm < 1 || ndm > AF_NOALLOC_MAX_ROWS)
         return af_set_error(AF_EINVAL, "af_boxcar_snr_noalloc: ndm %d outside 1..%d (the static scratch holds %d rows)",
@@ -90,4 +90,6 @@ extern "C" int af_boxcar_snr_noalloc(const int32_t* d_plane, int ndm, int64_t no
     cudaStream_t s = (cudaStream_t)stream;
     if (int rc = af_launch_rowstats(d_plane, ndm, nout, stats, s)) return rc;
     return af_launch_boxcar(d_plane, ndm, nout, stats, w, rconst, d_best_snr, d_best_w, s);
+} catch (...) {
+    return af_host_exception("af_boxcar_snr_noalloc");
 }

@@ -1046,7 +1046,7 @@ int af_launch_pairs(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nou
 }
 
 extern "C" int af_dedisperse_timing(af_plan_t p, int ncalls)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     if (ncalls < 0 || ncalls > 4096) return af_set_error(AF_EINVAL, "af_dedisperse_timing: ncalls in 0..4096");
     af_pair_tables* T = &p->pairs;
@@ -1064,11 +1064,13 @@ extern "C" int af_dedisperse_timing(af_plan_t p, int ncalls)
     T->tcopybytes.assign(ncalls, 0);
     T->tcalls = ncalls;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_dedisperse_timing");
 }
 
 extern "C" int af_dedisperse_times(af_plan_t p, int call, float* rows_ms, float* tiles_ms, int64_t* row_bytes,
                                    int64_t* copy_bytes)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     af_pair_tables* T = &p->pairs;
     if (call < 0 || call >= T->tcalls) return af_set_error(AF_EINVAL, "af_dedisperse_times: no such call slot");
@@ -1087,4 +1089,6 @@ extern "C" int af_dedisperse_times(af_plan_t p, int call, float* rows_ms, float*
     if (row_bytes) *row_bytes = T->trowbytes[call];
     if (copy_bytes) *copy_bytes = T->tcopybytes[call];
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_dedisperse_times");
 }

@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <exception>
 #include <new>
 #include <string>
 #include <vector>
@@ -36,6 +37,23 @@ int af_cuda_check(cudaError_t e, const char* what)
     if (e == cudaSuccess) return AF_OK;
     return af_set_error(e == cudaErrorMemoryAllocation ? AF_ENOMEM : AF_ECUDA, "%s: %s (%s)", what,
                         cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+int af_host_exception(const char* who)
+{
+    try {
+        try {
+            throw;
+        } catch (const std::bad_alloc&) {
+            return af_set_error(AF_ENOMEM, "%s: host allocation failed", who);
+        } catch (const std::exception& e) {
+            return af_set_error(AF_EINVAL, "%s: %s", who, e.what());
+        } catch (...) {
+            return af_set_error(AF_EINVAL, "%s: unexpected host exception", who);
+        }
+    } catch (...) {
+        return AF_ENOMEM;  // recording the message failed as well
+    }
 }
 
 extern "C" const char* af_last_error(void) { return g_last_error.c_str(); }
@@ -208,7 +226,7 @@ static int plan_finish(af_plan_s* p, const char* who)
 
 extern "C" int af_plan(af_plan_t* out, int nchan, double f_lo, double f_hi, double tsamp,
                        const double* dm_list, int ndm)
-{
+try {
     if (!out) return af_set_error(AF_EINVAL, "af_plan: out is NULL");
     *out = nullptr;
     if (int rc = check_plan_args("af_plan", nchan, f_lo, f_hi, tsamp, dm_list, ndm)) return rc;
@@ -221,11 +239,13 @@ extern "C" int af_plan(af_plan_t* out, int nchan, double f_lo, double f_hi, doub
     if (int rc = plan_finish(p, "af_plan")) return rc;
     *out = p;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_plan");
 }
 
 extern "C" int af_plan_channels(af_plan_t* out, int nchan, double f_lo, double f_hi, double tsamp,
                                 const double* dm_list, int ndm, int c0, int c1)
-{
+try {
     static const char* who = "af_plan_channels";
     if (!out) return af_set_error(AF_EINVAL, "%s: out is NULL", who);
     *out = nullptr;
@@ -242,6 +262,8 @@ extern "C" int af_plan_channels(af_plan_t* out, int nchan, double f_lo, double f
     if (int rc = plan_finish(p, who)) return rc;
     *out = p;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_plan_channels");
 }
 
 // Representative frequency of channels [c0, c1), Sec. 2.3: the median of the
@@ -266,7 +288,7 @@ static double subband_freq(int nchan, double f_lo, double f_hi, int c0, int c1, 
 
 extern "C" int af_plan_subband(af_plan_t* out, int nchan, double f_lo, double f_hi, double tsamp,
                                const double* dm_list, int ndm, int n0, int nsub, int fs_mode, int64_t block_len)
-{
+try {
     static const char* who = "af_plan_subband";
     if (!out) return af_set_error(AF_EINVAL, "%s: out is NULL", who);
     *out = nullptr;
@@ -345,11 +367,13 @@ extern "C" int af_plan_subband(af_plan_t* out, int nchan, double f_lo, double f_
     if (int rc = plan_finish(p, who)) return rc;
     *out = p;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_plan_subband");
 }
 
 extern "C" int af_plan_subband_info(af_plan_t p, int* n0, int* nsub, int* ncoarse, int32_t* first, double* fs,
                                     int32_t* coarse_delays, int32_t* residuals, int64_t* block_len)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     if (p->sb_nsub == 0) return af_set_error(AF_EINVAL, "af_plan_subband_info: not a subband plan");
     if (n0) *n0 = p->sb_n0;
@@ -361,34 +385,42 @@ extern "C" int af_plan_subband_info(af_plan_t p, int* n0, int* nsub, int* ncoars
     if (residuals) memcpy(residuals, p->sb_r.data(), p->sb_r.size() * sizeof(int32_t));
     if (block_len) *block_len = p->sb_L;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_plan_subband_info");
 }
 
 extern "C" int af_plan_destroy(af_plan_t plan)
-{
+try {
     free_plan(plan);
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_plan_destroy");
 }
 
 extern "C" int af_plan_delays(af_plan_t p, int32_t* host_out, int32_t* dmax)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     if (host_out) memcpy(host_out, p->delays.data(), p->delays.size() * sizeof(int32_t));
     if (dmax) *dmax = p->dmax;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_plan_delays");
 }
 
 extern "C" int af_plan_info(af_plan_t p, int* nchan, int* ndm, int32_t* dmax, double* tsamp)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     if (nchan) *nchan = p->nchan;
     if (ndm) *ndm = p->ndm;
     if (dmax) *dmax = p->dmax;
     if (tsamp) *tsamp = p->tsamp;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_plan_info");
 }
 
 extern "C" int af_plan_check(af_plan_t p)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     int flag = 0;
     AF_CUDA(cudaDeviceSynchronize());
@@ -398,10 +430,12 @@ extern "C" int af_plan_check(af_plan_t p)
         return af_set_error(AF_ETIMEOUT, "a kernel's bounded wait for an asynchronous copy ran out");
     }
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_plan_check");
 }
 
 extern "C" int af_plan_nout(af_plan_t p, int64_t nsamp, int64_t* nout)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     if (!nout) return af_set_error(AF_EINVAL, "af_plan_nout: nout is NULL");
     int64_t n = nsamp - (int64_t)p->dmax;
@@ -409,6 +443,8 @@ extern "C" int af_plan_nout(af_plan_t p, int64_t nsamp, int64_t* nout)
         return af_set_error(AF_EINVAL, "af_plan_nout: nsamp %lld <= Dmax %d", (long long)nsamp, p->dmax);
     *nout = n;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_plan_nout");
 }
 
 int af_check_widths(af_plan_t p, const int32_t* widths, int nw, int64_t nout, af_widths_t* out)
@@ -443,7 +479,7 @@ static int check_nout(af_plan_t p, int64_t nsamp, int64_t* nout)
 
 extern "C" int af_dedisperse(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int32_t* d_plane,
                              af_rowstats_t* d_stats, void* stream)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     if (!d_in || !d_plane) return af_set_error(AF_EINVAL, "af_dedisperse: NULL buffer");
     if (((uintptr_t)d_in & 15) != 0) return af_set_error(AF_EINVAL, "af_dedisperse: d_in not 16-byte aligned");
@@ -452,20 +488,24 @@ extern "C" int af_dedisperse(af_plan_t p, const uint8_t* d_in, int64_t nsamp, in
     if (int rc = check_nout(p, nsamp, &nout)) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     return af_launch_dedisperse(p, d_in, nsamp, nout, d_plane, d_stats, s);
+} catch (...) {
+    return af_host_exception("af_dedisperse");
 }
 
 extern "C" int af_rowstats(af_plan_t p, const int32_t* d_plane, int64_t nout, af_rowstats_t* d_stats,
                            void* stream)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     if (!d_plane || !d_stats) return af_set_error(AF_EINVAL, "af_rowstats: NULL buffer");
     if (nout < 1 || nout > INT32_MAX) return af_set_error(AF_EINVAL, "af_rowstats: bad nout");
     return af_launch_rowstats(d_plane, p->ndm, nout, d_stats, (cudaStream_t)stream);
+} catch (...) {
+    return af_host_exception("af_rowstats");
 }
 
 extern "C" int af_boxcar_snr(af_plan_t p, const int32_t* d_plane, int64_t nout, const af_rowstats_t* d_stats,
                              const int32_t* widths, int nw, float* d_best_snr, uint8_t* d_best_w, void* stream)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     if (!d_plane || !d_best_snr) return af_set_error(AF_EINVAL, "af_boxcar_snr: NULL buffer");
     if (nout < 1 || nout > INT32_MAX) return af_set_error(AF_EINVAL, "af_boxcar_snr: bad nout");
@@ -477,21 +517,25 @@ extern "C" int af_boxcar_snr(af_plan_t p, const int32_t* d_plane, int64_t nout, 
         d_stats = p->d_stats;
     }
     return af_launch_boxcar(d_plane, p->ndm, nout, d_stats, w, p->d_rowconst, d_best_snr, d_best_w, s);
+} catch (...) {
+    return af_host_exception("af_boxcar_snr");
 }
 
 extern "C" int af_rowstats_robust(af_plan_t p, const int32_t* d_plane, int64_t nout, af_robust_t* d_robust,
                                   void* stream)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     if (!d_plane || !d_robust) return af_set_error(AF_EINVAL, "af_rowstats_robust: NULL buffer");
     if (nout < 1 || nout > INT32_MAX) return af_set_error(AF_EINVAL, "af_rowstats_robust: bad nout");
     return af_launch_row_robust(d_plane, p->ndm, nout, d_robust, (cudaStream_t)stream);
+} catch (...) {
+    return af_host_exception("af_rowstats_robust");
 }
 
 extern "C" int af_boxcar_snr_robust(af_plan_t p, const int32_t* d_plane, int64_t nout, const af_robust_t* d_robust,
                                     const int32_t* widths, int nw, float* d_best_snr, uint8_t* d_best_w,
                                     void* stream)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     if (!d_plane || !d_best_snr) return af_set_error(AF_EINVAL, "af_boxcar_snr_robust: NULL buffer");
     if (nout < 1 || nout > INT32_MAX) return af_set_error(AF_EINVAL, "af_boxcar_snr_robust: bad nout");
@@ -505,12 +549,14 @@ extern "C" int af_boxcar_snr_robust(af_plan_t p, const int32_t* d_plane, int64_t
         d_robust = scratch;
     }
     return af_launch_boxcar_robust(d_plane, p->ndm, nout, d_robust, w, p->d_rowconst, d_best_snr, d_best_w, s);
+} catch (...) {
+    return af_host_exception("af_boxcar_snr_robust");
 }
 
 extern "C" int af_candidates(af_plan_t p, const float* d_best_snr, const uint8_t* d_best_w, int64_t nout,
                              const int32_t* widths, int nw, float thresh, int64_t sample0, af_cand_t* d_out,
                              int32_t cap, int32_t* d_count, void* stream)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     if (!d_best_snr || !d_best_w || !d_count || (cap > 0 && !d_out))
         return af_set_error(AF_EINVAL, "af_candidates: NULL buffer");
@@ -521,6 +567,8 @@ extern "C" int af_candidates(af_plan_t p, const float* d_best_snr, const uint8_t
     if (int rc = af_check_widths(p, widths, nw, nout, &w)) return rc;
     return af_launch_candidates(d_best_snr, d_best_w, p->ndm, nout, w, thresh, sample0, d_out, cap, d_count,
                                 (cudaStream_t)stream);
+} catch (...) {
+    return af_host_exception("af_candidates");
 }
 
 static bool cand_less_dt(const af_cand_t& a, const af_cand_t& b)
@@ -532,7 +580,7 @@ static bool cand_less_dt(const af_cand_t& a, const af_cand_t& b)
 
 extern "C" int af_cluster(af_plan_t p, af_cand_t* h_cands, int32_t n, double dm_tol, double toa_tol,
                           af_cand_t* h_out, int32_t* n_out)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     if (n < 0 || (n > 0 && (!h_cands || !h_out)) || !n_out) return af_set_error(AF_EINVAL, "af_cluster: bad args");
     for (int32_t i = 0; i < n; i++)
@@ -558,20 +606,24 @@ extern "C" int af_cluster(af_plan_t p, af_cand_t* h_cands, int32_t n, double dm_
     }
     *n_out = k;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_cluster");
 }
 
 extern "C" int af_dedisperse_workspace_size(af_plan_t p, int64_t max_nsamp, size_t* bytes)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     if (!bytes) return af_set_error(AF_EINVAL, "af_dedisperse_workspace_size: NULL output");
     int64_t nout;
     if (int rc = check_nout(p, max_nsamp, &nout)) return rc;
     *bytes = p->sb_nsub == 0 ? af_pairs_workspace(p, nout) : 0;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_dedisperse_workspace_size");
 }
 
 extern "C" int af_search_workspace_size(af_plan_t p, int64_t max_nsamp, int32_t cap, size_t* bytes)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     if (!bytes || cap < 1) return af_set_error(AF_EINVAL, "af_search_workspace_size: NULL output or cap < 1");
     int64_t nout;
@@ -580,18 +632,22 @@ extern "C" int af_search_workspace_size(af_plan_t p, int64_t max_nsamp, int32_t 
     *bytes = (size_t)p->nchan * (size_t)max_nsamp + npl * 9 + (size_t)cap * sizeof(af_cand_t) + 16 +
              (p->sb_nsub == 0 ? af_pairs_workspace(p, nout) : 0);
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_search_workspace_size");
 }
 
 extern "C" int af_dedisperse_reserve(af_plan_t p, int64_t max_nsamp)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     int64_t nout;
     if (int rc = check_nout(p, max_nsamp, &nout)) return rc;
     return af_pairs_reserve(p, nout, false);
+} catch (...) {
+    return af_host_exception("af_dedisperse_reserve");
 }
 
 extern "C" int af_search_reserve(af_plan_t p, int64_t max_nsamp, int32_t cap)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     int64_t nout;
     if (int rc = check_nout(p, max_nsamp, &nout)) return rc;
@@ -619,20 +675,24 @@ extern "C" int af_search_reserve(af_plan_t p, int64_t max_nsamp, int32_t cap)
     p->ws_cap = cap;
     p->ws_stage = std::min(cap, kSearchStage);
     return af_pairs_reserve(p, nout, true);  // the group-row buffers, where that path applies
+} catch (...) {
+    return af_host_exception("af_search_reserve");
 }
 
 extern "C" int af_search_timing(af_plan_t p, int enable)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     if (enable && !p->ws_tev[0])
         for (cudaEvent_t& e : p->ws_tev)
             if (cudaError_t ce = cudaEventCreate(&e)) return af_cuda_check(ce, "af_search_timing");
     p->ws_timing = enable != 0;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_search_timing");
 }
 
 extern "C" int af_search_times(af_plan_t p, float* wait_ms, float* dedisp_ms, float* snr_ms)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     if (!p->ws_tev[0]) return af_set_error(AF_EINVAL, "af_search_times: timing was never enabled");
     float a = 0.f, b = 0.f, c = 0.f;
@@ -644,11 +704,13 @@ extern "C" int af_search_times(af_plan_t p, float* wait_ms, float* dedisp_ms, fl
     if (dedisp_ms) *dedisp_ms = b;
     if (snr_ms) *snr_ms = c;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_search_times");
 }
 
 extern "C" int af_search(af_plan_t p, const uint8_t* h_in, int64_t nsamp, const int32_t* widths, int nw,
                          float thresh, af_cand_t* h_out, int32_t cap, int32_t* h_count, void* stream)
-{
+try {
     if (int rc = af_check_plan(p)) return rc;
     if (!h_in || !h_count || (cap > 0 && !h_out)) return af_set_error(AF_EINVAL, "af_search: NULL buffer");
     int64_t nout;
@@ -752,4 +814,6 @@ extern "C" int af_search(af_plan_t p, const uint8_t* h_in, int64_t nsamp, const 
     *h_count = total;
     if (total > cap) return af_set_error(AF_EOVERFLOW, "af_search: %d candidates, capacity %d", total, cap);
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_search");
 }

@@ -87,7 +87,7 @@ k_downsample(const uint8_t* __restrict__ X, int64_t nsamp, int D, int64_t nout, 
 }  // namespace
 
 extern "C" int af_downsample(const uint8_t* d_in, int nchan, int64_t nsamp, int D, uint8_t* d_out, void* stream)
-{
+try {
     if (!d_in || !d_out) return af_set_error(AF_EINVAL, "af_downsample: NULL buffer");
     if (nchan < 1 || nsamp < 1) return af_set_error(AF_EINVAL, "af_downsample: empty input");
     if (D < 1 || D > kDsSpan) return af_set_error(AF_EINVAL, "af_downsample: D %d not in 1..%d", D, kDsSpan);
@@ -98,6 +98,8 @@ extern "C" int af_downsample(const uint8_t* d_in, int nchan, int64_t nsamp, int 
     k_downsample<<<(unsigned)(runs * nchan), kDsThreads, 0, (cudaStream_t)stream>>>(d_in, nsamp, D, nout, tb,
                                                                                     (unsigned)runs, d_out);
     return af_cuda_check(cudaGetLastError(), "af_downsample launch");
+} catch (...) {
+    return af_host_exception("af_downsample");
 }
 
 // ---------------------------------------------------------------- zero-DM
@@ -205,7 +207,7 @@ k_zerodm(const uint8_t* X, int nchan, int64_t nsamp, uint8_t* out)
 }  // namespace
 
 extern "C" int af_zerodm(const uint8_t* d_in, int nchan, int64_t nsamp, uint8_t* d_out, void* stream)
-{
+try {
     if (!d_in || !d_out) return af_set_error(AF_EINVAL, "af_zerodm: NULL buffer");
     if (nchan < 1 || nchan > 65536 || nsamp < 1) return af_set_error(AF_EINVAL, "af_zerodm: bad shape");
     cudaStream_t s = (cudaStream_t)stream;
@@ -221,4 +223,6 @@ extern "C" int af_zerodm(const uint8_t* d_in, int nchan, int64_t nsamp, uint8_t*
         k_zerodm<<<(unsigned)blocks, kZT, 0, s>>>(d_in, nchan, nsamp, d_out);
     }
     return af_cuda_check(cudaGetLastError(), "af_zerodm launch");
+} catch (...) {
+    return af_host_exception("af_zerodm");
 }

@@ -279,7 +279,7 @@ static void free_stream(af_stream_s* s)
 }
 
 extern "C" int af_stream_open(af_stream_t* out, const af_stream_cfg_t* cfg)
-{
+try {
     if (!out || !cfg) return af_set_error(AF_EINVAL, "af_stream_open: NULL argument");
     *out = nullptr;
     if (cfg->nbeams < 1 || cfg->nbeams > 4096) return af_set_error(AF_EINVAL, "af_stream_open: nbeams");
@@ -392,11 +392,13 @@ extern "C" int af_stream_open(af_stream_t* out, const af_stream_cfg_t* cfg)
     s->thr = std::thread(dispatcher, s);
     *out = s;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_stream_open");
 }
 
 extern "C" int af_stream_push(af_stream_t s, int beam, const uint8_t* h_data, int64_t nsamp, int64_t pitch,
                                int64_t seq)
-{
+try {
     if (!s || !h_data || beam < 0 || beam >= s->nbeams) return af_set_error(AF_EINVAL, "af_stream_push: bad arguments");
     if (pitch == 0) pitch = nsamp;
     if (pitch < nsamp) return af_set_error(AF_EINVAL, "af_stream_push: pitch %lld < nsamp %lld", (long long)pitch, (long long)nsamp);
@@ -486,10 +488,12 @@ extern "C" int af_stream_push(af_stream_t s, int beam, const uint8_t* h_data, in
     }
     s->cv_ready.notify_one();
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_stream_push");
 }
 
 extern "C" int af_stream_poll(af_stream_t s, af_stream_result_t* out, int timeout_ms)
-{
+try {
     if (!s || !out) return af_set_error(AF_EINVAL, "af_stream_poll: NULL argument");
     std::unique_lock<std::mutex> lk(s->mu);
     if (s->done.empty() && !s->error) {
@@ -529,10 +533,12 @@ extern "C" int af_stream_poll(af_stream_t s, af_stream_result_t* out, int timeou
         out->status = AF_ETIMEOUT;
     }
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_stream_poll");
 }
 
 extern "C" int af_stream_release(af_stream_t s, int32_t slot)
-{
+try {
     if (!s || slot < 0 || slot >= (int)s->slots.size()) return af_set_error(AF_EINVAL, "af_stream_release: bad slot");
     {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -541,10 +547,12 @@ extern "C" int af_stream_release(af_stream_t s, int32_t slot)
     }
     s->cv_free.notify_all();
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_stream_release");
 }
 
 extern "C" int af_stream_result_plane(af_stream_t s, int32_t slot, int32_t** d_plane, float** d_snr, int64_t* nout)
-{
+try {
     if (!s || slot < 0 || slot >= (int)s->slots.size()) return af_set_error(AF_EINVAL, "af_stream_result_plane: bad slot");
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->slots[slot].state != HELD) return af_set_error(AF_EINVAL, "af_stream_result_plane: slot not held");
@@ -552,11 +560,13 @@ extern "C" int af_stream_result_plane(af_stream_t s, int32_t slot, int32_t** d_p
     if (d_snr) *d_snr = s->slots[slot].d_snr;
     if (nout) *nout = s->hop;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_stream_result_plane");
 }
 
 extern "C" int af_stream_classify(af_stream_t s, int32_t slot, af_model_t model, const af_cand_t* h_cands, int32_t n,
                                   float* h_prob)
-{
+try {
     if (!s || !model || slot < 0 || slot >= (int)s->slots.size() || n < 0 || n > s->cap ||
         (n > 0 && (!h_cands || !h_prob)))
         return af_set_error(AF_EINVAL, "af_stream_classify: bad arguments (n must be <= the engine's cap)");
@@ -573,25 +583,31 @@ extern "C" int af_stream_classify(af_stream_t s, int32_t slot, af_model_t model,
     AF_CUDA(cudaMemcpyAsync(h_prob, s->d_cprob, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, cs));
     AF_CUDA(cudaStreamSynchronize(cs));
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_stream_classify");
 }
 
 extern "C" int af_stream_cluster(af_stream_t s, af_cand_t* h_cands, int32_t n, af_cand_t* h_out, int32_t* n_out)
-{
+try {
     if (!s) return af_set_error(AF_EINVAL, "af_stream_cluster: NULL stream");
     return af_cluster(s->plan, h_cands, n, 20.0, 0.2, h_out, n_out);
+} catch (...) {
+    return af_host_exception("af_stream_cluster");
 }
 
 extern "C" int af_stream_info(af_stream_t s, int64_t* hop, int64_t* dmax, int* nslots)
-{
+try {
     if (!s) return af_set_error(AF_EINVAL, "af_stream_info: NULL stream");
     if (hop) *hop = s->hop;
     if (dmax) *dmax = s->dmax;
     if (nslots) *nslots = (int)s->slots.size();
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_stream_info");
 }
 
 extern "C" int af_stream_stats(af_stream_t s, af_stream_stats_t* st)
-{
+try {
     if (!s || !st) return af_set_error(AF_EINVAL, "af_stream_stats: NULL argument");
     std::lock_guard<std::mutex> lk(s->mu);
     memset(st, 0, sizeof *st);
@@ -614,11 +630,13 @@ extern "C" int af_stream_stats(af_stream_t s, af_stream_stats_t* st)
         st->rate = st->wall_s > 0 ? work / st->wall_s : 0.0;
     }
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_stream_stats");
 }
 
 extern "C" int af_stream_snapshot(af_stream_t s, int beam, uint8_t* h_overlap, int64_t* next_seq,
                                   int64_t* next_sample)
-{
+try {
     if (!s || beam < 0 || beam >= s->nbeams) return af_set_error(AF_EINVAL, "af_stream_snapshot: bad beam");
     BeamState& b = s->beams[beam];
     AF_CUDA(cudaEventSynchronize(b.overlap_ready));
@@ -628,11 +646,13 @@ extern "C" int af_stream_snapshot(af_stream_t s, int beam, uint8_t* h_overlap, i
     if (next_seq) *next_seq = b.next_seq;
     if (next_sample) *next_sample = b.next_sample;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_stream_snapshot");
 }
 
 extern "C" int af_stream_restore(af_stream_t s, int beam, const uint8_t* h_overlap, int64_t next_seq,
                                  int64_t next_sample)
-{
+try {
     if (!s || beam < 0 || beam >= s->nbeams || (!h_overlap && s->dmax > 0) || next_seq < 1 || next_sample < 0)
         return af_set_error(AF_EINVAL, "af_stream_restore: bad arguments");
     BeamState& b = s->beams[beam];
@@ -649,10 +669,14 @@ extern "C" int af_stream_restore(af_stream_t s, int beam, const uint8_t* h_overl
     b.next_seq = next_seq;
     b.next_sample = next_sample;
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_stream_restore");
 }
 
 extern "C" int af_stream_close(af_stream_t s)
-{
+try {
     free_stream(s);
     return AF_OK;
+} catch (...) {
+    return af_host_exception("af_stream_close");
 }
