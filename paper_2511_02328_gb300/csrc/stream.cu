@@ -133,7 +133,11 @@ static void CUDART_CB on_done(void* p)
     Slot& sl = s->slots[a->slot];
     sl.t_done = Clock::now();
     sl.state = DONE;
-    s->done.push_back(a->slot);
+    try {  // runs on a CUDA callback thread: nothing may throw out of it
+        s->done.push_back(a->slot);
+    } catch (...) {
+        s->error = AF_ENOMEM;
+    }
     s->cv_done.notify_all();
 }
 
@@ -208,18 +212,23 @@ static void dispatcher(af_stream_s* s)
 {
     cudaSetDevice(s->plan->device);
     for (;;) {
-        std::vector<int> batch;
-        {
-            std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_ready.wait(lk, [&] { return s->stop || !s->ready.empty(); });
-            if (s->ready.empty() && s->stop) return;
-            while (!s->ready.empty() && (int)batch.size() < s->max_batch) {
-                batch.push_back(s->ready.front());
-                s->ready.pop_front();
+        int rc = AF_OK;
+        try {  // a host exception becomes the engine's error status, as a failed dispatch does
+            std::vector<int> batch;
+            {
+                std::unique_lock<std::mutex> lk(s->mu);
+                s->cv_ready.wait(lk, [&] { return s->stop || !s->ready.empty(); });
+                if (s->ready.empty() && s->stop) return;
+                while (!s->ready.empty() && (int)batch.size() < s->max_batch) {
+                    batch.push_back(s->ready.front());
+                    s->ready.pop_front();
+                }
+                for (int k : batch) s->slots[k].state = RUNNING;
             }
-            for (int k : batch) s->slots[k].state = RUNNING;
+            rc = dispatch(s, batch);
+        } catch (...) {
+            rc = af_host_exception("af_stream dispatcher");
         }
-        int rc = dispatch(s, batch);
         if (rc != AF_OK) {
             std::lock_guard<std::mutex> lk(s->mu);
             s->error = rc;
