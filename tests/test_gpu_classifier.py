@@ -3,7 +3,6 @@ clustering, cut-outs, training on the GPU with the library's kernels, and the
 comparison with the plain S/N threshold at equal recall of injected pulses
 with S/N >= 8: the network must keep the recall (within 1 %) while raising
 fewer false positives."""
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
