@@ -484,7 +484,7 @@ try {
     if (!d_in || !d_plane) return af_set_error(AF_EINVAL, "af_dedisperse: NULL buffer");
     if (((uintptr_t)d_in & 15) != 0) return af_set_error(AF_EINVAL, "af_dedisperse: d_in not 16-byte aligned");
     if (255.0 * p->nchan >= 2147483648.0) return af_set_error(AF_EINVAL, "af_dedisperse: too many channels");
-    int64_t nout;
+    int64_t nout = 0;
     if (int rc = check_nout(p, nsamp, &nout)) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     return af_launch_dedisperse(p, d_in, nsamp, nout, d_plane, d_stats, s);
@@ -614,7 +614,7 @@ extern "C" int af_dedisperse_workspace_size(af_plan_t p, int64_t max_nsamp, size
 try {
     if (int rc = af_check_plan(p)) return rc;
     if (!bytes) return af_set_error(AF_EINVAL, "af_dedisperse_workspace_size: NULL output");
-    int64_t nout;
+    int64_t nout = 0;
     if (int rc = check_nout(p, max_nsamp, &nout)) return rc;
     *bytes = p->sb_nsub == 0 ? af_pairs_workspace(p, nout) : 0;
     return AF_OK;
@@ -626,7 +626,7 @@ extern "C" int af_search_workspace_size(af_plan_t p, int64_t max_nsamp, int32_t 
 try {
     if (int rc = af_check_plan(p)) return rc;
     if (!bytes || cap < 1) return af_set_error(AF_EINVAL, "af_search_workspace_size: NULL output or cap < 1");
-    int64_t nout;
+    int64_t nout = 0;
     if (int rc = check_nout(p, max_nsamp, &nout)) return rc;
     const size_t npl = (size_t)p->ndm * (size_t)nout;
     *bytes = (size_t)p->nchan * (size_t)max_nsamp + npl * 9 + (size_t)cap * sizeof(af_cand_t) + 16 +
@@ -639,7 +639,7 @@ try {
 extern "C" int af_dedisperse_reserve(af_plan_t p, int64_t max_nsamp)
 try {
     if (int rc = af_check_plan(p)) return rc;
-    int64_t nout;
+    int64_t nout = 0;
     if (int rc = check_nout(p, max_nsamp, &nout)) return rc;
     return af_pairs_reserve(p, nout, false);
 } catch (...) {
@@ -649,7 +649,7 @@ try {
 extern "C" int af_search_reserve(af_plan_t p, int64_t max_nsamp, int32_t cap)
 try {
     if (int rc = af_check_plan(p)) return rc;
-    int64_t nout;
+    int64_t nout = 0;
     if (int rc = check_nout(p, max_nsamp, &nout)) return rc;
     if (cap < 1) return af_set_error(AF_EINVAL, "af_search_reserve: cap must be >= 1");
     if (max_nsamp <= p->ws_nsamp && cap <= p->ws_cap) return AF_OK;
@@ -713,7 +713,7 @@ extern "C" int af_search(af_plan_t p, const uint8_t* h_in, int64_t nsamp, const 
 try {
     if (int rc = af_check_plan(p)) return rc;
     if (!h_in || !h_count || (cap > 0 && !h_out)) return af_set_error(AF_EINVAL, "af_search: NULL buffer");
-    int64_t nout;
+    int64_t nout = 0;
     if (int rc = check_nout(p, nsamp, &nout)) return rc;
     if (nsamp > p->ws_nsamp || cap > p->ws_cap)
         return af_set_error(AF_ENOBUFS, "af_search: call af_search_reserve(nsamp >= %lld, cap >= %d) first",
