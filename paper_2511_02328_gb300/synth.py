@@ -92,8 +92,10 @@ def filterbank(nchan, nsamp, seed, pulses=(), rfi=None, rows_per_chunk=64,
 
 def pulse_params(n, seed, dm_range, width_range_s, snr_range, t_range_s, min_sep_s, tsamp):
     """Draw n pulses: DM ~ U(dm_range), width ~ log-U(width_range_s) rounded to
-    >= 1 sample, S/N ~ U(snr_range), arrival times at least min_sep_s apart in
-    t_range_s.  Returns a list of dicts (dm, width_samples, snr, t0_sample)."""
+    >= 1 sample, S/N ~ U(snr_range), arrival times in distinct slots of
+    min_sep_s within t_range_s, each jittered by up to a quarter slot (so
+    neighbours are at least 0.75 * min_sep_s apart).  Returns a list of dicts
+    (dm, width_samples, snr, t0_sample)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     t_lo, t_hi = t_range_s
     slots = int((t_hi - t_lo) // min_sep_s)
