@@ -1,10 +1,15 @@
 """Pins for the oracle's delay table (Eq. KDM, Eq. coarse_delay, Sec. 2.3)."""
+import json
+import os
+
 import numpy as np
 import pytest
 
 import oracle
 from oracle import brute
 from conftest import C1, C2, dm_list
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 def test_physical_delay_dm1000():
@@ -42,6 +47,26 @@ def test_delays_match_exact_rational(cfg):
         # a tie within double rounding would make the comparison ambiguous
         assert abs(abs(x - int(x)) - 0.5) > 1e-9
         assert D[d, c] == n, (d, c, D[d, c], n, float(x))
+
+
+@pytest.mark.parametrize("cfg", [C1, C2, dict(C2, dm_hi=2000.0)], ids=["c1", "c2", "stream"])
+def test_no_rounding_ties_in_the_workload_tables(cfg):
+    # Rounding reading: half away from zero.  On the workloads' whole tables no
+    # product a*b (Eq. coarse_delay, same operation order in IEEE double) lies
+    # within 1e-9 of a .5 tie, so round-half-to-even gives the same table and
+    # the tie rule never decides a delay here.
+    dms = dm_list(cfg)
+    D = oracle.delay_table(cfg["nchan"], cfg["f_lo"], cfg["f_hi"], cfg["tsamp"], dms)
+    K = float(json.load(open(os.path.join(GOLDEN, "paper_constants.json")))["K_DM"]["value"])
+    df = (cfg["f_hi"] - cfg["f_lo"]) / cfg["nchan"]
+    fc = cfg["f_lo"] + (np.arange(cfg["nchan"], dtype=np.float64) + 0.5) * df
+    fr = max(cfg["f_lo"], cfg["f_hi"])
+    a = (K * dms) / cfg["tsamp"]
+    b = 1.0 / (fc * fc) - 1.0 / (fr * fr)
+    x = a[:, None] * b[None, :]
+    frac = x - np.floor(x)
+    assert int(np.count_nonzero(np.abs(frac - 0.5) < 1e-9)) == 0
+    assert np.array_equal(np.rint(x).astype(np.int64), D.astype(np.int64))
 
 
 def test_dmax_closed_form():
