@@ -152,6 +152,11 @@ def aggregate_rate(world, work_per_rank, seconds):
     return world * work_per_rank / seconds
 
 
+def oracle_cflags():
+    from oracle.build import CFLAGS
+    return [f for f in CFLAGS if f not in ("-fPIC", "-shared")]
+
+
 def cpu_oracle_sample(x, D, rows, nout):
     """Time the oracle (as it stands) on a bounded sample: the listed DM rows of
     the same workload, dedispersion + S/N + candidates."""
@@ -161,7 +166,7 @@ def cpu_oracle_sample(x, D, rows, nout):
     snr, bw = oracle.boxcar_snr(Y, WIDTHS)
     oracle.peaks(snr, bw, WIDTHS, THRESH)
     dt = time.perf_counter() - t0
-    work = len(rows) * NCHAN * nout
+    work = len(rows) * NCHAN * int(nout)
     return work / dt, dt
 
 
@@ -174,7 +179,7 @@ def run_reference(args):
     x, _ = make_input(12345, lambda dms: oracle.delay_table(NCHAN, F_LO, F_HI, TSAMP, dms))
     D = oracle.delay_table(NCHAN, F_LO, F_HI, TSAMP, DMS)
     nout = NSAMP - int(D.max())
-    rows_per_step = 8
+    rows_per_step = 4 * cores          # the oracle runs one DM row per thread at a time
     rng = np.random.default_rng(5)
     for _ in range(args.warmup):
         cpu_oracle_sample(x, D, rng.choice(len(DMS), 2, replace=False), nout)
@@ -185,8 +190,8 @@ def run_reference(args):
         times.append(dt)
     total = sum(times)
     value = args.steps * rows_per_step * NCHAN * nout / total
-    sample = "%d random DM rows of 1001 per step (full nout=%d, all 4096 channels): dedispersion + S/N + peaks" % (
-        rows_per_step, nout)
+    sample = ("%d random DM rows of 1001 per step (full nout=%d, all 4096 channels): dedispersion + S/N + peaks; "
+              "%d OpenMP threads, gcc %s" % (rows_per_step, nout, cores, " ".join(oracle_cflags())))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
@@ -920,11 +925,13 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         D = plan.delays()
-        rows = np.array([0, 250, 500, 750, 1000, 123, 377, 888])
+        nthr = oracle.threads()
+        rows = np.unique(np.linspace(0, len(DMS) - 1, 4 * nthr).round().astype(np.int64))
         v, dt = cpu_oracle_sample(x_host, D, rows, nout)
-        cpu = {"value": v, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-               "sample": "8 DM rows of 1001 (full nout=%d, 4096 channels): dedispersion + S/N + peaks, %.1f s"
-                         % (nout, dt)}
+        cpu = {"value": v, "unit": UNIT, "cores": nthr, "kind": "oracle",
+               "sample": "%d evenly spaced DM rows of 1001 (full nout=%d, 4096 channels): dedispersion + S/N + "
+                         "peaks, %.2f s on %d OpenMP threads; gcc %s"
+                         % (len(rows), nout, dt, nthr, " ".join(oracle_cflags()))}
 
     if rank == 0:
         line = {

@@ -40,6 +40,8 @@ def lib():
         L.oracle_dmax.restype = ctypes.c_int32
         L.oracle_dmax.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
         L.oracle_dedisperse.restype = None
+        L.oracle_threads.restype = ctypes.c_int
+        L.oracle_threads.argtypes = []
         L.oracle_dedisperse.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
                                         ctypes.c_int, ctypes.c_int64, ctypes.c_void_p]
         L.oracle_rowstats.restype = None
@@ -300,4 +302,5 @@ def boxcar_snr_robust(Y, widths):
 
 
 def threads():
-    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    """Threads of the oracle's OpenMP team (what its parallel loops use)."""
+    return int(lib().oracle_threads())

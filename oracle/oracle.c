@@ -16,6 +16,7 @@
  * something other than itself (exact rational arithmetic, brute force in pure
  * Python, closed forms, invariants, injected-pulse recovery).
  */
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -88,6 +89,19 @@ int32_t oracle_dmax(const int32_t* D, int ndm, int nchan)
  * the data and no zero padding is needed (the paper truncates by the DM delay,
  * Sec. 3).  The caller passes nout; every delay must satisfy D + nout <= nsamp.
  * Loop order d, c, t; OpenMP over DM rows only.                            */
+/* Threads of the OpenMP team that the parallel loops below run on (not part
+ * of the method: reported beside the oracle's timings). */
+int oracle_threads(void)
+{
+    int n = 1;
+    #pragma omp parallel
+    {
+        #pragma omp single
+        n = omp_get_num_threads();
+    }
+    return n;
+}
+
 void oracle_dedisperse(const uint8_t* X, int nchan, int64_t nsamp,
                        const int32_t* D, int ndm, int64_t nout, int32_t* Y)
 {

@@ -205,6 +205,9 @@ struct af_plan_s {
 
 int af_check_plan(af_plan_t p);
 int af_check_widths(af_plan_t p, const int32_t* widths, int nw, int64_t nout, af_widths_t* out);
+// The same checks for planes summed over `nchan` channels of 8-bit data (no
+// plan needed); sets .small when every window sum is below 2^31.
+int af_check_widths_nchan(int nchan, const int32_t* widths, int nw, int64_t nout, af_widths_t* out);
 
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `s` and return AF_OK or AF_ECUDA (launch error).

@@ -20,7 +20,6 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
-#include <string.h>
 
 #include <mutex>
 
@@ -68,21 +67,9 @@ try {
                             ndm, AF_NOALLOC_MAX_ROWS, AF_NOALLOC_MAX_ROWS);
     if (nout < 1 || nout > INT32_MAX) return af_set_error(AF_EINVAL, "af_boxcar_snr_noalloc: bad nout");
     if (nchan < 1 || nchan > 65536) return af_set_error(AF_EINVAL, "af_boxcar_snr_noalloc: bad nchan %d", nchan);
-    if (!widths || nw < 1 || nw > AF_MAX_WIDTHS)
-        return af_set_error(AF_EINVAL, "af_boxcar_snr_noalloc: nw %d not in 1..%d", nw, AF_MAX_WIDTHS);
+    // the same width checks (and the same choice of the 32-bit boxcar kernel) as af_boxcar_snr
     af_widths_t w;
-    memset(&w, 0, sizeof w);
-    for (int i = 0; i < nw; i++) {
-        if (widths[i] < 1 || (i > 0 && widths[i] <= widths[i - 1]))
-            return af_set_error(AF_EINVAL, "af_boxcar_snr_noalloc: widths must be strictly ascending and >= 1");
-        if ((int64_t)widths[i] > nout || widths[i] > 8192)
-            return af_set_error(AF_EINVAL, "af_boxcar_snr_noalloc: width %d too large", widths[i]);
-        if ((double)widths[i] * 255.0 * (double)nchan >= 4294967296.0)
-            return af_set_error(AF_EINVAL, "af_boxcar_snr_noalloc: width %d too large for exact window sums",
-                                widths[i]);
-        w.w[i] = widths[i];
-    }
-    w.n = nw;
+    if (int rc = af_check_widths_nchan(nchan, widths, nw, nout, &w)) return rc;
     void* base = nullptr;
     if (int rc = scratch_address(&base)) return rc;
     af_rowstats_t* stats = (af_rowstats_t*)base;

@@ -326,8 +326,10 @@ struct PairTile {
                 cda = cdb;
                 cdb = cdc;
             }
+            // (a drain wait that runs out raises the error flag like any other)
             for (int k2 = max(0, kk - NS); k2 < kk; k2++)
-                afptx::mbar_wait_bounded(full0 + 8 * (k2 % NS), (uint32_t)(k2 / NS) & 1u, kPWait);
+                if (!afptx::mbar_wait_bounded(full0 + 8 * (k2 % NS), (uint32_t)(k2 / NS) & 1u, kPWait) && lane == 0)
+                    atomicExch(a.err, 1);
             return;
         }
 

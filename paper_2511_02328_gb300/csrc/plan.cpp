@@ -449,6 +449,11 @@ try {
 
 int af_check_widths(af_plan_t p, const int32_t* widths, int nw, int64_t nout, af_widths_t* out)
 {
+    return af_check_widths_nchan(p->nchan, widths, nw, nout, out);
+}
+
+int af_check_widths_nchan(int nchan, const int32_t* widths, int nw, int64_t nout, af_widths_t* out)
+{
     if (!widths) return af_set_error(AF_EINVAL, "widths is NULL");
     if (nw < 1 || nw > AF_MAX_WIDTHS) return af_set_error(AF_EINVAL, "nw %d not in 1..%d", nw, AF_MAX_WIDTHS);
     memset(out, 0, sizeof *out);
@@ -457,13 +462,13 @@ int af_check_widths(af_plan_t p, const int32_t* widths, int nw, int64_t nout, af
             return af_set_error(AF_EINVAL, "widths must be strictly ascending and >= 1");
         if ((int64_t)widths[i] > nout)
             return af_set_error(AF_EINVAL, "width %d exceeds nout %lld", widths[i], (long long)nout);
-        if ((double)widths[i] * 255.0 * (double)p->nchan >= 4294967296.0)
+        if ((double)widths[i] * 255.0 * (double)nchan >= 4294967296.0)
             return af_set_error(AF_EINVAL, "width %d too large for exact 32-bit window sums", widths[i]);
         if (widths[i] > 8192) return af_set_error(AF_EINVAL, "width %d > 8192 not supported", widths[i]);
         out->w[i] = widths[i];
     }
     out->n = nw;
-    out->small = (double)widths[nw - 1] * 255.0 * (double)p->nchan < 2147483648.0 ? 1 : 0;
+    out->small = (double)widths[nw - 1] * 255.0 * (double)nchan < 2147483648.0 ? 1 : 0;
     return AF_OK;
 }
 

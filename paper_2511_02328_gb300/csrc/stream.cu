@@ -27,6 +27,7 @@
 #include <condition_variable>
 #include <deque>
 #include <mutex>
+#include <string>
 #include <new>
 #include <thread>
 #include <vector>
@@ -95,6 +96,7 @@ struct af_stream_s {
     std::thread thr;
     bool stop = false;
     int error = AF_OK;
+    std::string error_msg;               // the cause, recorded by the thread that set `error`
     cudaStream_t dstream = nullptr;
     // job buffers for the persistent launches (ring)
     static constexpr int kRing = 8;
@@ -137,6 +139,11 @@ static void CUDART_CB on_done(void* p)
         s->done.push_back(a->slot);
     } catch (...) {
         s->error = AF_ENOMEM;
+        s->error_msg.clear();
+        try {
+            s->error_msg = "host allocation failed in the completion callback";
+        } catch (...) {
+        }
     }
     s->cv_done.notify_all();
 }
@@ -232,6 +239,10 @@ static void dispatcher(af_stream_s* s)
         if (rc != AF_OK) {
             std::lock_guard<std::mutex> lk(s->mu);
             s->error = rc;
+            try {  // this thread's af_last_error() holds the cause; keep it for push / poll
+                s->error_msg = af_last_error();
+            } catch (...) {
+            }
             s->cv_done.notify_all();
             s->cv_free.notify_all();
         }
@@ -417,7 +428,7 @@ try {
     bool first = false;
     {
         std::unique_lock<std::mutex> lk(s->mu);
-        if (s->error) return af_set_error(s->error, "af_stream_push: the engine failed earlier");
+        if (s->error) return af_set_error(s->error, "af_stream_push: the engine failed earlier: %s", s->error_msg.c_str());
         BeamState& b = s->beams[beam];
         if (seq != b.next_seq)
             return af_set_error(AF_EINVAL, "af_stream_push: beam %d expects chunk %lld, got %lld (dropped or repeated)",
@@ -437,7 +448,7 @@ try {
             if (!s->cv_free.wait_for(lk, std::chrono::milliseconds(s->timeout_ms),
                                      [&] { return has_free() || s->error; }))
                 return af_set_error(AF_ETIMEOUT, "af_stream_push: no slot freed within %d ms", s->timeout_ms);
-            if (s->error) return af_set_error(s->error, "af_stream_push: the engine failed");
+            if (s->error) return af_set_error(s->error, "af_stream_push: the engine failed: %s", s->error_msg.c_str());
         }
         for (size_t i = 0; i < s->slots.size(); i++)
             if (s->slots[i].state == FREE) {
@@ -490,6 +501,7 @@ try {
             sl.state = FREE;
             s->inflight--;
             s->error = rc;
+            s->error_msg = af_last_error();
             return rc;
         }
         sl.state = READY;
@@ -510,7 +522,7 @@ try {
         s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return !s->done.empty() || s->error; });
     }
     if (s->done.empty()) {
-        if (s->error) return af_set_error(s->error, "af_stream_poll: the engine failed");
+        if (s->error) return af_set_error(s->error, "af_stream_poll: the engine failed: %s", s->error_msg.c_str());
         return AF_EAGAIN;
     }
     const int k = s->done.front();

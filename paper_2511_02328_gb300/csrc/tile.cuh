@@ -322,8 +322,10 @@ struct Tile {
                 cur = nxt;
             }
             // leave no copy in flight behind (the consumers normally wait for all of them)
+            // (a drain wait that runs out raises the error flag like any other)
             for (int k2 = max(0, kk - NS); k2 < kk; k2++)
-                afptx::mbar_wait_bounded(full0 + 8 * (k2 % NS), (uint32_t)(k2 / NS) & 1u, WAIT_LIMIT);
+                if (!afptx::mbar_wait_bounded(full0 + 8 * (k2 % NS), (uint32_t)(k2 / NS) & 1u, WAIT_LIMIT) && lane == 0)
+                    atomicExch(a.err, 1);
             return;
         }
 

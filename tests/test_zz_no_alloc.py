@@ -9,6 +9,8 @@ failure has already run every other test."""
 import numpy as np
 import pytest
 
+import oracle
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -52,6 +54,48 @@ def test_noalloc_matches_boxcar_snr_two_calls_in_a_row():
         err = np.abs(got[fin] - ref_snr[fin]) / np.maximum(1.0, np.abs(ref_snr[fin]))
         assert float(err.max()) <= TOL
         assert np.array_equal(bw.cpu().numpy(), ref_bw)
+        # and, independently of the plan path, the oracle's S/N of the same plane
+        o_snr, _ = oracle.boxcar_snr(plane.cpu().numpy(), widths)
+        ofin = np.isfinite(o_snr)
+        assert np.array_equal(np.isfinite(got), ofin)
+        oerr = np.abs(got[ofin] - o_snr[ofin]) / np.maximum(1.0, np.abs(o_snr[ofin]))
+        assert float(oerr.max()) <= TOL
+
+
+def test_noalloc_at_its_row_limit_without_width_output():
+    """AF_NOALLOC_MAX_ROWS rows (the last row's constants at the end of the
+    static array), no best-width output, against the oracle and against
+    af_boxcar_snr; then a one-row call behind it on the same scratch."""
+    from paper_2511_02328_gb300 import _lib
+    from paper_2511_02328_gb300.search import Plan
+    ndm, nout, nchan = _lib.AF_NOALLOC_MAX_ROWS, 300, 16
+    widths = [1, 2, 4, 8, 16, 32]
+    rng = np.random.default_rng(21)
+    Y = rng.integers(0, 255 * nchan + 1, (ndm, nout)).astype(np.int32)
+    Y[-1, 100:110] = 255 * nchan                       # a pulse in the last row
+    plane = torch.from_numpy(Y).cuda()
+    snr = torch.full((ndm, nout), np.nan, dtype=torch.float32, device="cuda")
+    _lib.af_boxcar_snr_noalloc(plane.data_ptr(), ndm, nout, nchan, widths, snr.data_ptr(), 0,
+                               torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = snr.cpu().numpy().astype(np.float64)
+    o_snr, _ = oracle.boxcar_snr(Y, widths)
+    fin = np.isfinite(o_snr)
+    assert np.array_equal(np.isfinite(got), fin)
+    err = np.abs(got[fin] - o_snr[fin]) / np.maximum(1.0, np.abs(o_snr[fin]))
+    assert float(err.max()) <= TOL
+    p = Plan(nchan, 1000.0, 1500.0, 1e-4, np.linspace(0.0, 1.0, ndm))
+    ref, _ = p.boxcar_snr(plane, widths)
+    torch.cuda.synchronize()
+    assert np.array_equal(np.isfinite(ref.cpu().numpy()), fin)
+    assert float(np.max(np.abs(ref.cpu().numpy()[fin] - got[fin]) / np.maximum(1.0, np.abs(got[fin])))) <= TOL
+    p.close()
+    one = torch.full((1, nout), np.nan, dtype=torch.float32, device="cuda")
+    _lib.af_boxcar_snr_noalloc(plane[-1:].data_ptr(), 1, nout, nchan, widths, one.data_ptr(), 0,
+                               torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    g1, r1 = one.cpu().numpy()[0].astype(np.float64)[fin[-1]], o_snr[-1][fin[-1]]
+    assert float(np.max(np.abs(g1 - r1) / np.maximum(1.0, np.abs(r1)))) <= TOL
 
 
 def test_noalloc_rejects_more_rows_than_its_scratch():
