@@ -654,14 +654,17 @@ int af_diag_bounded_wait(int arrive, int64_t polls, float* ms);
 int af_cutouts(af_plan_t plan, const uint8_t* d_in, int64_t nsamp, const int32_t* d_plane, int64_t nout,
                const af_cand_t* d_cands, int32_t n, uint16_t* d_out, void* stream);
 
-/* The classifier's tensor-core GEMM (bf16 operands, fp32 accumulation), for
- * tests and tools:  C[m][n] (op)= sum_k A(m,k) B(k,n)  with
+/* The classifier's tensor-core GEMM (tcgen05.mma, bf16 operands, fp32
+ * accumulation in tensor memory), for tests and tools; no counterpart in the
+ * paper.  C[m][n] (op)= sum_k A(m,k) B(k,n)  with
  *  layout 0: A [M][K], B given as [N][K];   1: A [M][K], B [K][N];
  *         2: A given as [K][M], B [K][N];   3: A given as [K][M], B as [N][K]
  *  epi    0: C = acc;  1: C = max(acc + bias[n], 0);  2: C += acc (atomic, fp32)
  * lda / ldb = row pitch of the stored arrays in elements (multiples of 8),
- * ldc of C (fp32 [M][ldc]); operands 16-byte aligned; splits > 1 splits K
- * across blocks (epi 2 only). */
+ * ldc of C (fp32 [M][ldc]); K a multiple of 8; operands 16-byte aligned;
+ * splits > 1 splits K across blocks (epi 2 only).  Unlike the other calls it
+ * allocates a 4-byte flag and waits for the stream: AF_ETIMEOUT if one of the
+ * kernel's bounded waits for its tensor-core operations ran out. */
 int af_nn_gemm(int layout, int epi, const uint16_t* d_a, int lda, const uint16_t* d_b, int ldb, int M, int N, int K,
                int splits, float* d_c, int ldc, const float* d_bias, void* stream);
 
@@ -670,7 +673,10 @@ int af_nn_gemm(int layout, int epi, const uint16_t* d_a, int lda, const uint16_t
 int af_model_create(af_model_t* out, int max_batch, uint64_t seed);
 int af_model_destroy(af_model_t model);
 int af_model_nparams(af_model_t model, int64_t* n);
-/* Host fp32 parameter / gradient vectors in the flat order above (synchronous). */
+/* Host fp32 parameter / gradient vectors in the flat order above (synchronous).
+ * The classifier's convolutions run on the tcgen05 tensor cores with bounded
+ * waits for their MMAs; a wait that ran out in an earlier forward / backward /
+ * training call is reported here (and by af_model_save) as AF_ETIMEOUT. */
 int af_model_set_params(af_model_t model, const float* h_params, int64_t n);
 int af_model_get_params(af_model_t model, float* h_params, int64_t n);
 int af_model_get_grads(af_model_t model, float* h_grads, int64_t n);

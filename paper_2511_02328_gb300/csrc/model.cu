@@ -1,9 +1,13 @@
 // model.cu -- the candidate classifier: parameters, workspace, forward,
-// backward and Adam, built from the kernels of nn.cu (the paper's detector is
-// YOLOv11n on DM-time images, Sec. 2.5; this small CNN replaces it).
+// backward and Adam, built from the kernels of conv_umma.cu and nn.cu (the
+// paper's detector is YOLOv11n on DM-time images, Sec. 2.5; this small CNN
+// replaces it).
 //
-// Inference (no labels) runs the fused kernel of nn_fused.cu; the layered
-// kernels below keep the activations that the backward pass needs.
+// The convolutions run on the tcgen05 tensor cores as implicit GEMMs (forward
+// with bias, ReLU and max pool fused; data and weight gradients), keeping the
+// pooled activations and argmax bytes the backward pass needs.  Inference of
+// batches below a measured size runs the one-kernel mma.sync network of
+// nn_fused.cu instead, which needs no intermediate activations in memory.
 // Network: input NHWC bf16 [n][64][64][2]; three blocks conv3x3 (+bias) ->
 // ReLU -> 2x2 max pool with 2 -> 16 -> 32 -> 64 channels; global average pool;
 // fully connected 64 -> 2; softmax cross-entropy (label 1 = pulse).
@@ -39,6 +43,11 @@ struct Layer {
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// Inference batches of at least this many images run the layered tensor-core
+// network; smaller ones the fused one-kernel network (AFGB_CNN_UMMA_MIN
+// overrides at model creation).
+constexpr int kUmmaInferMin = 64;
+
 }  // namespace
 
 struct af_model_s {
@@ -48,18 +57,17 @@ struct af_model_s {
     Layer L[NL];
     int64_t fw_off = 0, fb_off = 0;
     float *d_params = nullptr, *d_grads = nullptr, *d_m = nullptr, *d_v = nullptr;
-    __nv_bfloat16* d_wt[NL] = {};
-    float* d_dw[NL] = {};
-    __nv_bfloat16* d_col[NL] = {};
-    float* d_r[NL] = {};
-    __nv_bfloat16* d_a[NL + 1] = {};   // d_a[0] unused (the input is the caller's)
-    uint8_t* d_idx[NL] = {};
+    __nv_bfloat16* d_wt[NL] = {};      // forward weights, bf16 [cout][kp]
+    __nv_bfloat16* d_wd[NL] = {};      // data-gradient weights, bf16 [cin][9 cout] (l >= 1)
+    __nv_bfloat16* d_a[NL + 1] = {};   // pooled activations; d_a[0] unused (the input is the caller's)
+    uint8_t* d_idx[NL] = {};           // argmax of each pool window | 4 if its maximum > 0
     __nv_bfloat16* d_da[NL + 1] = {};  // gradients w.r.t. d_a[l] (l >= 1)
-    __nv_bfloat16* d_dz[NL] = {};
-    float* d_dcol = nullptr;
+    __nv_bfloat16* d_dz[NL] = {};      // gradients w.r.t. the pre-pool ReLU outputs
     float* d_logits = nullptr;
     float* d_loss = nullptr;
+    int* d_err = nullptr;              // raised by a bounded tensor-core wait that ran out
     __nv_bfloat16* d_cut = nullptr;    // cut-outs for af_classify
+    int umma_min = 0;                  // inference batches of at least this size use the tensor-core layers
 };
 
 static void free_model(af_model_t m)
@@ -71,9 +79,7 @@ static void free_model(af_model_t m)
     cudaFree(m->d_v);
     for (int l = 0; l < NL; l++) {
         cudaFree(m->d_wt[l]);
-        cudaFree(m->d_dw[l]);
-        cudaFree(m->d_col[l]);
-        cudaFree(m->d_r[l]);
+        cudaFree(m->d_wd[l]);
         cudaFree(m->d_idx[l]);
         cudaFree(m->d_dz[l]);
     }
@@ -81,7 +87,7 @@ static void free_model(af_model_t m)
         cudaFree(m->d_a[l]);
         cudaFree(m->d_da[l]);
     }
-    cudaFree(m->d_dcol);
+    cudaFree(m->d_err);
     cudaFree(m->d_logits);
     cudaFree(m->d_loss);
     cudaFree(m->d_cut);
@@ -147,24 +153,21 @@ try {
     A(&m->d_grads, off * 4);
     A(&m->d_m, off * 4);
     A(&m->d_v, off * 4);
-    size_t dcol = 0;
     for (int l = 0; l < NL; l++) {
         const Layer& y = m->L[l];
         const int64_t P = n * y.H * y.W;
         A(&m->d_wt[l], (size_t)y.cout * y.kp * 2);
-        A(&m->d_dw[l], (size_t)y.cout * y.kp * 4);
-        A(&m->d_col[l], (size_t)P * y.kp * 2);
-        A(&m->d_r[l], (size_t)P * y.cout * 4);
+        if (l > 0) A(&m->d_wd[l], (size_t)y.cin * 9 * y.cout * 2);
         A(&m->d_idx[l], (size_t)P * y.cout / 4);
         A(&m->d_dz[l], (size_t)P * y.cout * 2);
         A(&m->d_a[l + 1], (size_t)P * y.cout / 4 * 2);
         A(&m->d_da[l + 1], (size_t)P * y.cout / 4 * 2);
-        dcol = std::max(dcol, (size_t)P * y.kp * 4);
     }
-    A(&m->d_dcol, dcol);
+    A(&m->d_err, 16);
     A(&m->d_logits, (size_t)n * 2 * 4);
     A(&m->d_loss, 16);
     A(&m->d_cut, (size_t)n * 64 * 64 * 2 * 2);
+    if (e == cudaSuccess) e = cudaMemset(m->d_err, 0, 16);
     if (e == cudaSuccess) e = cudaMemset(m->d_m, 0, off * 4);
     if (e == cudaSuccess) e = cudaMemset(m->d_v, 0, off * 4);
     if (e != cudaSuccess) {
@@ -180,6 +183,8 @@ try {
         free_model(m);
         return rc;
     }
+    m->umma_min = kUmmaInferMin;
+    if (const char* v = getenv("AFGB_CNN_UMMA_MIN")) m->umma_min = atoi(v);
     *out = m;
     return AF_OK;
 } catch (...) {
@@ -203,9 +208,23 @@ try {
     return af_host_exception("af_model_nparams");
 }
 
+// Reads (and clears) the flag a bounded tensor-core wait raises when it runs
+// out; synchronises the device.
+static int check_err(af_model_t m, const char* what)
+{
+    int h = 0;
+    AF_CUDA(cudaMemcpy(&h, m->d_err, sizeof h, cudaMemcpyDeviceToHost));
+    if (h) {
+        AF_CUDA(cudaMemset(m->d_err, 0, sizeof h));
+        return af_set_error(AF_ETIMEOUT, "%s: a tensor-core kernel's bounded wait ran out", what);
+    }
+    return AF_OK;
+}
+
 static int copy_params(af_model_t m, float* dst, const float* src, int64_t n, cudaMemcpyKind kind, const char* what)
 {
     if (!m || (!dst && !src)) return af_set_error(AF_EINVAL, "%s: NULL argument", what);
+    if (int rc = check_err(m, what)) return rc;
     if (n != m->nparams) return af_set_error(AF_EINVAL, "%s: %lld values, the model has %lld", what, (long long)n,
                                              (long long)m->nparams);
     AF_CUDA(cudaMemcpy(dst, src, n * 4, kind));
@@ -238,51 +257,40 @@ try {
 
 static int forward(af_model_t m, const __nv_bfloat16* x, int n, const int32_t* y, float* prob, cudaStream_t s)
 {
-    if (!y) {  // inference: one fused kernel, activations never leave shared memory
-        const float* P = m->d_params;
+    const float* P = m->d_params;
+    if (!y && n < m->umma_min)  // small inference batch: one fused kernel
         return nn_forward_fused(x, n, P + m->L[0].woff, P + m->L[0].boff, P + m->L[1].woff, P + m->L[1].boff,
                                 P + m->L[2].woff, P + m->L[2].boff, P + m->fw_off, P + m->fb_off, m->d_logits, prob,
                                 s);
-    }
     const __nv_bfloat16* a = x;
     for (int l = 0; l < NL; l++) {
         const Layer& L = m->L[l];
-        const int64_t P = (int64_t)n * L.H * L.W;
-        if (int rc = nn_pack_w(m->d_params + L.woff, L.cout, L.k9, L.kp, m->d_wt[l], s)) return rc;
-        if (int rc = nn_im2col(a, n, L.H, L.W, L.cin, L.kp, m->d_col[l], s)) return rc;
-        if (int rc = nn_gemm(NN_A_K_B_K, NN_EPI_BIAS_RELU, m->d_col[l], L.kp, m->d_wt[l], L.kp, (int)P, L.cout, L.kp,
-                             1, m->d_r[l], L.cout, m->d_params + L.boff, s))
+        if (int rc = nn_pack_w(P + L.woff, L.cout, L.k9, L.kp, m->d_wt[l], s)) return rc;
+        if (int rc = nn_conv_fwd(l, a, n, L.H, L.W, m->d_wt[l], P + L.boff, m->d_a[l + 1], y ? m->d_idx[l] : nullptr,
+                                 m->d_err, s))
             return rc;
-        if (int rc = nn_pool(m->d_r[l], n, L.H, L.W, L.cout, m->d_a[l + 1], m->d_idx[l], s)) return rc;
         a = m->d_a[l + 1];
     }
     if (y) {
         AF_CUDA(cudaMemsetAsync(m->d_loss, 0, 4, s));
         AF_CUDA(cudaMemsetAsync(m->d_grads, 0, m->nparams * 4, s));
     }
-    return nn_head(m->d_a[NL], n, m->d_params + m->fw_off, m->d_params + m->fb_off, m->d_logits, prob, y, m->d_loss,
+    return nn_head(m->d_a[NL], n, P + m->fw_off, P + m->fb_off, m->d_logits, prob, y, m->d_loss,
                    m->d_grads + m->fw_off, m->d_grads + m->fb_off, m->d_da[NL], s);
 }
 
-static int backward(af_model_t m, int n, cudaStream_t s)
+static int backward(af_model_t m, const __nv_bfloat16* x, int n, cudaStream_t s)
 {
     for (int l = NL - 1; l >= 0; l--) {
         const Layer& L = m->L[l];
         const int64_t P = (int64_t)n * L.H * L.W;
-        if (int rc = nn_pool_back(m->d_da[l + 1], m->d_idx[l], m->d_r[l], n, L.H, L.W, L.cout, m->d_dz[l], s))
-            return rc;
-        AF_CUDA(cudaMemsetAsync(m->d_dw[l], 0, (size_t)L.cout * L.kp * 4, s));
-        const int splits = (int)std::min<int64_t>(std::max<int64_t>(1, P / 2048), 256);
-        if (int rc = nn_gemm(NN_A_M_B_N, NN_EPI_ATOMIC, m->d_dz[l], L.cout, m->d_col[l], L.kp, L.cout, L.kp, (int)P,
-                             splits, m->d_dw[l], L.kp, nullptr, s))
-            return rc;
-        if (int rc = nn_unpack_dw(m->d_dw[l], L.cout, L.k9, L.kp, m->d_grads + L.woff, s)) return rc;
+        if (int rc = nn_pool_back(m->d_da[l + 1], m->d_idx[l], n, L.H, L.W, L.cout, m->d_dz[l], s)) return rc;
         if (int rc = nn_colsum(m->d_dz[l], P, L.cout, m->d_grads + L.boff, s)) return rc;
+        const __nv_bfloat16* a = l ? m->d_a[l] : x;
+        if (int rc = nn_conv_wgrad(l, m->d_dz[l], a, n, L.H, L.W, m->d_grads + L.woff, m->d_err, s)) return rc;
         if (l > 0) {
-            if (int rc = nn_gemm(NN_A_K_B_N, NN_EPI_STORE, m->d_dz[l], L.cout, m->d_wt[l], L.kp, (int)P, L.kp, L.cout,
-                                 1, m->d_dcol, L.kp, nullptr, s))
-                return rc;
-            if (int rc = nn_col2im(m->d_dcol, n, L.H, L.W, L.cin, L.kp, m->d_da[l], s)) return rc;
+            if (int rc = nn_pack_wd(m->d_params + L.woff, L.cin, L.cout, m->d_wd[l], s)) return rc;
+            if (int rc = nn_conv_dgrad(l, m->d_dz[l], n, L.H, L.W, m->d_wd[l], m->d_da[l], m->d_err, s)) return rc;
         }
     }
     return AF_OK;
@@ -315,7 +323,7 @@ try {
     if (!d_y) return af_set_error(AF_EINVAL, "af_model_backward: labels NULL");
     cudaStream_t s = (cudaStream_t)stream;
     if (int rc = forward(m, (const __nv_bfloat16*)d_x, n, d_y, nullptr, s)) return rc;
-    if (int rc = backward(m, n, s)) return rc;
+    if (int rc = backward(m, (const __nv_bfloat16*)d_x, n, s)) return rc;
     if (d_loss) AF_CUDA(cudaMemcpyAsync(d_loss, m->d_loss, 4, cudaMemcpyDeviceToDevice, s));
     return AF_OK;
 } catch (...) {
@@ -338,8 +346,21 @@ extern "C" int af_nn_gemm(int layout, int epi, const uint16_t* d_a, int lda, con
 try {
     if (!d_a || !d_b || !d_c || (epi == NN_EPI_BIAS_RELU && !d_bias) || epi < 0 || epi > 2 || ldc < N)
         return af_set_error(AF_EINVAL, "af_nn_gemm: bad arguments");
-    return nn_gemm(layout, epi, (const __nv_bfloat16*)d_a, lda, (const __nv_bfloat16*)d_b, ldb, M, N, K, splits, d_c,
-                   ldc, d_bias, (cudaStream_t)stream);
+    // a test entry point: it allocates its bounded-wait flag, waits for the
+    // stream and reports a wait that ran out
+    int* d_err = nullptr;
+    AF_CUDA(cudaMalloc(&d_err, sizeof(int)));
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = af_cuda_check(cudaMemsetAsync(d_err, 0, sizeof(int), s), "af_nn_gemm");
+    if (!rc)
+        rc = nn_gemm(layout, epi, (const __nv_bfloat16*)d_a, lda, (const __nv_bfloat16*)d_b, ldb, M, N, K, splits, d_c,
+                     ldc, d_bias, d_err, s);
+    int h = 0;
+    if (!rc) rc = af_cuda_check(cudaMemcpyAsync(&h, d_err, sizeof h, cudaMemcpyDeviceToHost, s), "af_nn_gemm");
+    if (!rc) rc = af_cuda_check(cudaStreamSynchronize(s), "af_nn_gemm");
+    cudaFree(d_err);
+    if (!rc && h) rc = af_set_error(AF_ETIMEOUT, "af_nn_gemm: a bounded wait ran out");
+    return rc;
 } catch (...) {
     return af_host_exception("af_nn_gemm");
 }
@@ -379,6 +400,7 @@ try {
 extern "C" int af_model_save(af_model_t m, const char* path)
 try {
     if (!m || !path) return af_set_error(AF_EINVAL, "af_model_save: NULL argument");
+    if (int rc = check_err(m, "af_model_save")) return rc;
     std::vector<float> buf(3 * m->nparams);
     AF_CUDA(cudaMemcpy(buf.data(), m->d_params, m->nparams * 4, cudaMemcpyDeviceToHost));
     AF_CUDA(cudaMemcpy(buf.data() + m->nparams, m->d_m, m->nparams * 4, cudaMemcpyDeviceToHost));

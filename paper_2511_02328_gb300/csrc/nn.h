@@ -12,19 +12,30 @@ enum { NN_A_K_B_K = 0, NN_A_K_B_N = 1, NN_A_M_B_N = 2, NN_A_M_B_K = 3 };
 // Epilogues: store fp32; add bias[n] then ReLU, store fp32; atomic add fp32 (split-K).
 enum { NN_EPI_STORE = 0, NN_EPI_BIAS_RELU = 1, NN_EPI_ATOMIC = 2 };
 
+// Plain GEMM on the tensor cores (conv_umma.cu); a bounded wait that runs out
+// raises *err.
 int nn_gemm(int layout, int epi, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
-            int splits, float* C, int ldc, const float* bias, cudaStream_t s);
-int nn_im2col(const __nv_bfloat16* a, int n, int H, int W, int cin, int kp, __nv_bfloat16* col, cudaStream_t s);
-int nn_col2im(const float* dcol, int n, int H, int W, int cin, int kp, __nv_bfloat16* da, cudaStream_t s);
-int nn_pool(const float* r, int n, int H, int W, int c, __nv_bfloat16* out, uint8_t* idx, cudaStream_t s);
-int nn_pool_back(const __nv_bfloat16* dp, const uint8_t* idx, const float* r, int n, int H, int W, int c,
-                 __nv_bfloat16* dz, cudaStream_t s);
+            int splits, float* C, int ldc, const float* bias, int* err, cudaStream_t s);
+// 3x3 convolutions (pad 1) of classifier layer 0, 1, 2 (2 -> 16 -> 32 -> 64
+// channels) as implicit GEMMs on the tensor cores (conv_umma.cu):
+//   forward: x [n][H][W][cin] -> bias, ReLU, 2x2 max pool -> out [n][H/2][W/2][cout]
+//            and idx (argmax 0..3 | 4 if positive; nullable), weights wp [cout][kp]
+//   dgrad:   dz [n][H][W][cout] -> dx [n][H][W][cin], weights wd [cin][9 cout] (layers 1, 2)
+//   wgrad:   grad [cout][9 cin] += sum_p dz[p] (x) x[p + tap]
+int nn_conv_fwd(int layer, const __nv_bfloat16* x, int n, int H, int W, const __nv_bfloat16* wp, const float* bias,
+                __nv_bfloat16* out, uint8_t* idx, int* err, cudaStream_t s);
+int nn_conv_dgrad(int layer, const __nv_bfloat16* dz, int n, int H, int W, const __nv_bfloat16* wd,
+                  __nv_bfloat16* dx, int* err, cudaStream_t s);
+int nn_conv_wgrad(int layer, const __nv_bfloat16* dz, const __nv_bfloat16* x, int n, int H, int W, float* grad,
+                  int* err, cudaStream_t s);
+int nn_pack_wd(const float* w, int cin, int cout, __nv_bfloat16* wd, cudaStream_t s);
+int nn_pool_back(const __nv_bfloat16* dp, const uint8_t* idx, int n, int H, int W, int c, __nv_bfloat16* dz,
+                 cudaStream_t s);
 int nn_colsum(const __nv_bfloat16* dz, int64_t P, int c, float* db, cudaStream_t s);
 int nn_head(const __nv_bfloat16* a3, int n, const float* fw, const float* fb, float* logits, float* prob,
             const int32_t* y, float* loss, float* dfw, float* dfb, __nv_bfloat16* da3, cudaStream_t s);
 int nn_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, int step, cudaStream_t s);
 int nn_pack_w(const float* w, int cout, int k9, int kp, __nv_bfloat16* wt, cudaStream_t s);
-int nn_unpack_dw(const float* dw, int cout, int k9, int kp, float* g, cudaStream_t s);
 int nn_f32_to_bf16(const float* x, int64_t n, __nv_bfloat16* y, cudaStream_t s);
 int nn_cutouts(const uint8_t* X, int64_t nsamp, int nchan, const int32_t* D, int ndm, const int32_t* plane,
                int64_t nout, const af_cand_t* cands, int n, __nv_bfloat16* out, cudaStream_t s);

@@ -1,7 +1,10 @@
-"""The classifier on the GPU against the oracle: the tensor-core GEMM in all
-four operand layouts, cut-outs (bit-exact bf16), forward logits (rel 1e-2),
-gradients (cosine >= 0.999 and rel-L2 <= 2e-2 per tensor), Adam, training
-that lowers the loss, checkpoint round trip, and af_classify."""
+"""The classifier on the GPU against the oracle: the tcgen05 tensor-core GEMM
+in all four operand layouts, cut-outs (bit-exact bf16), forward logits (rel
+1e-2) on both inference paths (the fused mma.sync kernel for small batches,
+the tcgen05 implicit-GEMM layers for large ones), gradients of the tcgen05
+training path (cosine >= 0.999 and rel-L2 <= 2e-2 per tensor) at two batch
+sizes, Adam, training that lowers the loss, checkpoint round trip, and
+af_classify."""
 import numpy as np
 import pytest
 
@@ -166,6 +169,69 @@ def test_forward_and_gradients_match_oracle():
     assert np.max(np.abs(lg - ref_logits)) <= 1e-2 * max(1.0, np.abs(ref_logits).max())
     e = np.exp(ref_logits - ref_logits.max(1, keepdims=True))
     assert np.allclose(prob.cpu().numpy(), e[:, 1] / e.sum(1), atol=5e-3)
+    assert abs(float(loss.item()) - ref_loss) <= 1e-2 * max(1.0, ref_loss)
+    g = _unflat(_lib.af_model_get_grads(m))
+    for k in ["w0", "b0", "w1", "b1", "w2", "b2", "fw", "fb"]:
+        a, b = g[k].astype(np.float64).ravel(), np.asarray(ref_g[k], dtype=np.float64).ravel()
+        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30)
+        rel = np.linalg.norm(a - b) / (np.linalg.norm(b) + 1e-30)
+        assert cos >= 0.999 and rel <= 2e-2, (k, cos, rel)
+    _lib.af_model_destroy(m)
+
+
+def _model_with(params, max_batch, umma_min, monkeypatch):
+    from paper_2511_02328_gb300 import _lib
+    monkeypatch.setenv("AFGB_CNN_UMMA_MIN", str(umma_min))
+    m = _lib.af_model_create(max_batch, 1)
+    _lib.af_model_set_params(m, _flat(params))
+    return m
+
+
+def test_inference_paths_match_oracle_and_each_other(monkeypatch):
+    """A batch of 96 through the tcgen05 layers (conv + bias + ReLU + pool in
+    one kernel per layer) and through the fused mma.sync kernel: both within
+    the logit tolerance of the oracle, P(pulse) of the two within 5e-3."""
+    from paper_2511_02328_gb300 import _lib
+    rng = np.random.default_rng(17)
+    p = cnn.init_params(5)
+    for l in range(3):
+        p["b%d" % l] = rng.normal(0, 0.05, p["b%d" % l].shape).astype(np.float32)
+    n = 96
+    x = cutout.bf16_round(rng.uniform(0, 1, (n, 64, 64, 2)).astype(np.float32))
+    x[:8] = 0.0                                         # all-zero images: ReLU ties in every pool window
+    ref_logits = cnn.forward(p, x, bf16=True)[0]
+    xd = _bf16_dev(x)
+    out = {}
+    for name, umma_min in (("tcgen05", 1), ("fused", 1 << 20)):
+        m = _model_with(p, n, umma_min, monkeypatch)
+        logits = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+        prob = torch.empty(n, dtype=torch.float32, device="cuda")
+        _lib.af_model_forward(m, xd.data_ptr(), n, logits.data_ptr(), prob.data_ptr())
+        torch.cuda.synchronize()
+        lg = logits.cpu().numpy()
+        assert np.max(np.abs(lg - ref_logits)) <= 1e-2 * max(1.0, np.abs(ref_logits).max()), name
+        out[name] = prob.cpu().numpy()
+        _lib.af_model_get_params(m)                      # reports a bounded wait that ran out
+        _lib.af_model_destroy(m)
+    assert np.max(np.abs(out["tcgen05"] - out["fused"])) <= 5e-3
+
+
+def test_gradients_match_oracle_larger_batch(monkeypatch):
+    """Gradients of the tcgen05 training path on 72 images (several weight-
+    gradient pixel runs per layer, the split-K atomics), against the oracle."""
+    from paper_2511_02328_gb300 import _lib
+    rng = np.random.default_rng(29)
+    p = cnn.init_params(9)
+    for l in range(3):
+        p["b%d" % l] = rng.normal(0, 0.05, p["b%d" % l].shape).astype(np.float32)
+    n = 72
+    x = cutout.bf16_round(rng.uniform(0, 1, (n, 64, 64, 2)).astype(np.float32))
+    y = rng.integers(0, 2, n).astype(np.int32)
+    m = _model_with(p, n, 1, monkeypatch)
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    _lib.af_model_backward(m, _bf16_dev(x).data_ptr(), torch.from_numpy(y).cuda().data_ptr(), n, loss.data_ptr())
+    torch.cuda.synchronize()
+    ref_loss, _, ref_g = cnn.loss_and_grads(p, x, y, bf16=True)
     assert abs(float(loss.item()) - ref_loss) <= 1e-2 * max(1.0, ref_loss)
     g = _unflat(_lib.af_model_get_grads(m))
     for k in ["w0", "b0", "w1", "b1", "w2", "b2", "fw", "fb"]:
