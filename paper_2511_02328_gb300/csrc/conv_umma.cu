@@ -34,8 +34,9 @@
 
 namespace {
 
-constexpr int kThreads = 128;  // warp w owns tensor-memory lanes 32w .. 32w + 31
 constexpr uint32_t kWait = afptx::kMbarWaitPolls;
+// producer warps 0-3, MMA warp 4, epilogue warps 5-8
+constexpr int kProd = 128, kEpi = 128, kBlock = kProd + 32 + kEpi;
 
 // cp.async of 16 (4) bytes; `bytes` < size zero-fills the rest (0: no read)
 __device__ __forceinline__ void cp16(uint32_t dst, const void* src, uint32_t bytes)
@@ -76,85 +77,132 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 constexpr int pow2_cols(int n) { return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : n <= 256 ? 256 : 512; }
 
 // ------------------------------------------------------------ the pipeline
-// Op provides: NS (stages, >= 3), SA / SB (bytes of a stage's A / B tile),
-// RB (resident bytes), TCOLS (tensor-memory columns), ntiles(), nkb(),
-// resident(), stage(), mma(), epilogue().
+// Warp-specialised: warps 0-3 produce (stage operand tiles with cp.async),
+// warp 4 issues the MMAs (one elected thread), warps 5-8 run the epilogue
+// (warp w reads tensor-memory lanes 32 (w % 4) ..).  Stages pass between them
+// through mbarriers:
+//   full[s]   128 producer arrivals: the stage's copies have landed and were
+//             made visible to the tensor cores (each producer thread waits for
+//             its own copies of a stage L steps later, fences, arrives)
+//   empty[s]  one tcgen05.commit: the MMAs reading the stage are done
+//   tfull[b]  one tcgen05.commit: accumulator b holds a finished tile
+//   tempty[b] 128 epilogue arrivals: accumulator b has been read
+// NACC accumulators of Op::NCOL columns each alternate between tiles, so the
+// epilogue of one tile overlaps the MMAs of the next.
+// Op provides: NS (stages), NACC, NCOL, SA / SB (bytes of a stage's A / B
+// tile), RB (resident bytes), ntiles(), nkb(), resident(), stage(), mma(),
+// epilogue().
+constexpr int kLag = 3;  // a producer arrives for a stage kLag steps after issuing it
+
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort)
+{
+    for (uint32_t i = 0; i < kWait; i++) {
+        if (afptx::mbar_try_wait(bar, parity)) return true;
+        if ((i & 63) == 63 && *abort) return false;
+    }
+    *abort = 1;
+    return false;
+}
+
 template <class Op>
-__global__ void __launch_bounds__(kThreads) k_umma(const typename Op::Args args)
+__global__ void __launch_bounds__(kBlock) k_umma(const typename Op::Args args)
 {
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ __align__(8) uint64_t bars[Op::NS];
+    __shared__ __align__(8) uint64_t bars[2 * Op::NS + 2 * Op::NACC];
     __shared__ uint32_t tslot;
-    constexpr int NS = Op::NS, D = NS - 2;
+    __shared__ int abort_flag;
+    constexpr int NS = Op::NS, NACC = Op::NACC;
     constexpr uint32_t SSTAGE = Op::SA + Op::SB;
+    constexpr uint32_t TCOLS = pow2_cols(NACC * Op::NCOL);
+    static_assert(kLag < NS, "the producer must be able to run kLag stages ahead");
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const Op op(args);
     const int ntiles = op.ntiles(), nkb = op.nkb();
     const int mytiles = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
     const int G = mytiles * nkb;
-    uint8_t* res = smem;
     uint8_t* stages = smem + Op::RB;
-    const uint32_t bar0 = afptx::smem_addr(bars);
+    const uint32_t full0 = afptx::smem_addr(bars), empty0 = full0 + 8 * NS, tfull0 = empty0 + 8 * NS,
+                   tempty0 = tfull0 + 8 * NACC;
+    volatile int* abort = &abort_flag;
 
     if (tid == 0) {
-        for (int s = 0; s < NS; s++) afptx::mbar_init(bar0 + 8 * s, 1);
+        for (int s = 0; s < NS; s++) {
+            afptx::mbar_init(full0 + 8 * s, kProd);
+            afptx::mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int b = 0; b < NACC; b++) {
+            afptx::mbar_init(tfull0 + 8 * b, 1);
+            afptx::mbar_init(tempty0 + 8 * b, kEpi);
+        }
+        abort_flag = 0;
         afptx::fence_mbar_init();
     }
-    if (warp == 0) {
-        afumma::tmem_alloc(afptx::smem_addr(&tslot), Op::TCOLS);
+    if (warp == 4) {
+        afumma::tmem_alloc(afptx::smem_addr(&tslot), TCOLS);
         afumma::tmem_relinquish();
-    }
-    op.resident(res, tid);  // joins the first copy group
-    auto tile_of = [&](int g) { return (int)blockIdx.x + (g / nkb) * (int)gridDim.x; };
-    for (int g = 0; g < D; g++) {
-        if (g < G) op.stage(stages + (g % NS) * SSTAGE, stages + (g % NS) * SSTAGE + Op::SA, tile_of(g), g % nkb, tid);
-        cp_commit();
     }
     afumma::fence_before_sync();
     __syncthreads();
     afumma::fence_after_sync();
     const uint32_t tmem = tslot;
+    auto tile_of = [&](int g) { return (int)blockIdx.x + (g / nkb) * (int)gridDim.x; };
 
-    bool ok = true;
-    for (int g = 0; g < G; g++) {
-        const int gp = g + D;
-        if (gp < G) {
-            const int sp = gp % NS;
-            // the stage was last read by the MMAs of step gp - NS
-            if (gp >= NS && !afptx::mbar_wait_bounded(bar0 + 8 * sp, (uint32_t)((gp - NS) / NS) & 1u, kWait))
-                ok = false;
-            op.stage(stages + sp * SSTAGE, stages + sp * SSTAGE + Op::SA, tile_of(gp), gp % nkb, tid);
-        }
-        cp_commit();
-        cp_wait<D>();                 // this thread's copies of step g are in
-        afptx::fence_proxy_async();   // ... and visible to the tensor cores
-        if (!__syncthreads_and(ok)) {
-            ok = false;
-            break;
-        }
-        const int s = g % NS, kb = g % nkb;
-        if (tid == 0) {
-            afumma::fence_after_sync();
-            op.mma(afptx::smem_addr(stages + s * SSTAGE), afptx::smem_addr(stages + s * SSTAGE + Op::SA),
-                   afptx::smem_addr(res), kb, tmem);
-            afumma::commit(bar0 + 8 * s);
-        }
-        if (kb == nkb - 1) {
-            if (!afptx::mbar_wait_bounded(bar0 + 8 * s, (uint32_t)(g / NS) & 1u, kWait)) ok = false;
-            if (!__syncthreads_and(ok)) {
-                ok = false;
-                break;
+    if (warp < 4) {
+        // ---------------- producers
+        op.resident(smem, tid);  // joins the copies of step 0
+        int g = 0;
+        for (; g < G; g++) {
+            const int s = g % NS;
+            if (g >= NS && !wait_or_abort(empty0 + 8 * s, (uint32_t)(g / NS - 1) & 1u, abort)) break;
+            op.stage(stages + s * SSTAGE, stages + s * SSTAGE + Op::SA, tile_of(g), g % nkb, tid);
+            cp_commit();
+            if (g >= kLag) {
+                cp_wait<kLag>();             // this thread's copies of step g - kLag are in
+                afptx::fence_proxy_async();  // ... and visible to the tensor cores
+                afptx::mbar_arrive(full0 + 8 * ((g - kLag) % NS));
             }
+        }
+        cp_wait<0>();
+        afptx::fence_proxy_async();
+        for (int h = g - kLag < 0 ? 0 : g - kLag; h < g; h++) afptx::mbar_arrive(full0 + 8 * (h % NS));
+    } else if (warp == 4) {
+        // ---------------- MMA issuer
+        for (int g = 0; g < G; g++) {
+            const int s = g % NS, kb = g % nkb, i = g / nkb, b = i % NACC;
+            const uint32_t acc = tmem + (uint32_t)(b * Op::NCOL);
+            bool ok = true;
+            if (kb == 0 && i >= NACC)  // the epilogue has read this accumulator's previous tile
+                ok = wait_or_abort(tempty0 + 8 * b, (uint32_t)((i - NACC) / NACC) & 1u, abort);
+            ok = ok && wait_or_abort(full0 + 8 * s, (uint32_t)(g / NS) & 1u, abort);
+            if (!__all_sync(0xffffffffu, ok)) break;
             afumma::fence_after_sync();
-            op.epilogue(tile_of(g), tmem, warp, lane);
-            afumma::fence_before_sync();  // tensor-memory reads before the next tile's MMAs
+            if (lane == 0) {
+                op.mma(afptx::smem_addr(stages + s * SSTAGE), afptx::smem_addr(stages + s * SSTAGE + Op::SA),
+                       afptx::smem_addr(smem), kb, acc);
+                afumma::commit(empty0 + 8 * s);
+                if (kb == nkb - 1) afumma::commit(tfull0 + 8 * b);
+            }
+            __syncwarp();
+        }
+        // every stage's release has arrived before the block's shared memory goes away
+        for (int g = G - NS < 0 ? 0 : G - NS; g < G && !*abort; g++)
+            wait_or_abort(empty0 + 8 * (g % NS), (uint32_t)(g / NS) & 1u, abort);
+    } else {
+        // ---------------- epilogue
+        const int quarter = warp & 3;
+        for (int i = 0; i < mytiles; i++) {
+            const int b = i % NACC;
+            if (!wait_or_abort(tfull0 + 8 * b, (uint32_t)(i / NACC) & 1u, abort)) break;
+            afumma::fence_after_sync();
+            op.epilogue((int)blockIdx.x + i * (int)gridDim.x, tmem + (uint32_t)(b * Op::NCOL), quarter, lane);
+            afumma::fence_before_sync();
+            afptx::mbar_arrive(tempty0 + 8 * b);
         }
     }
-    cp_wait<0>();
-    if (!ok && tid == 0) atomicExch(args.err, 1);
-    afumma::fence_before_sync();
     __syncthreads();
-    if (warp == 0) afumma::tmem_dealloc(tmem, Op::TCOLS);
+    if (tid == 0 && *abort) atomicExch(args.err, 1);
+    afumma::fence_after_sync();
+    if (warp == 4) afumma::tmem_dealloc(tmem, TCOLS);
 }
 
 // One MMA step of K = 16 per pair of k groups: A and B descriptors advance by
@@ -174,7 +222,7 @@ struct FwdOp {
     static_assert(CIN == 2 || CIN % 8 == 0, "input channels: 2 or a multiple of 8");
     static_assert(COUT % 16 == 0 && COUT <= 256, "output channels");
     static constexpr int KP = (9 * CIN + 31) / 32 * 32;
-    static constexpr int NS = 6, TCOLS = pow2_cols(COUT);
+    static constexpr int NS = 6, NACC = 2, NCOL = COUT;
     static constexpr uint32_t SA = 128 * 32 * 2, SB = 0, RB = COUT * KP * 2;
     struct Args {
         const __nv_bfloat16* x;   // [n][H][W][CIN]
@@ -193,26 +241,31 @@ struct FwdOp {
     __device__ void resident(uint8_t* res, int tid) const
     {
         const uint32_t base = afptx::smem_addr(res);
-        for (int e = tid; e < COUT * KP / 8; e += kThreads) {
+        for (int e = tid; e < COUT * KP / 8; e += kProd) {
             const int o = e / (KP / 8), kg = e % (KP / 8);
             cp16(base + kmaj_off(o, kg, COUT), a.wp + o * KP + 8 * kg, 16);
         }
     }
-    __device__ void pixel(int tile, int tid, int& img, int& y, int& x, bool& valid) const
+    // Row `tid` of a tile: its pixel's centre element and the 3x3 taps that lie
+    // inside the image (bit t = dy * 3 + dx), none for rows past the end.
+    __device__ const __nv_bfloat16* pixel(int tile, int tid, uint32_t& taps) const
     {
         const int pp = tile * 32 + (tid >> 2), q = tid & 3;
-        valid = pp < npool;
-        const int ppc = valid ? pp : 0;
-        img = ppc / (Ho * Wo);
-        const int rem = ppc - img * Ho * Wo;
-        y = 2 * (rem / Wo) + (q >> 1);
-        x = 2 * (rem % Wo) + (q & 1);
+        taps = 0u;
+        if (pp >= npool) return a.x;
+        const int img = pp / (Ho * Wo), rem = pp - img * Ho * Wo;
+        const int y = 2 * (rem / Wo) + (q >> 1), x = 2 * (rem % Wo) + (q & 1);
+        const uint32_t rows = (y > 0 ? 1u : 0u) | 2u | (y + 1 < a.H ? 4u : 0u);
+        const uint32_t cols = (x > 0 ? 1u : 0u) | 2u | (x + 1 < a.W ? 4u : 0u);
+#pragma unroll
+        for (int t = 0; t < 9; t++) taps |= ((rows >> (t / 3)) & (cols >> (t % 3)) & 1u) << t;
+        return a.x + (((int64_t)img * a.H + y) * a.W + x) * CIN;
     }
-    __device__ void stage(uint8_t* sa, uint8_t*, int tile, int kb, int tid) const
+    __device__ void stage(uint8_t* sa, uint8_t*, int tile, int kb_rt, int tid) const
     {
-        int img, y, x;
-        bool valid;
-        pixel(tile, tid, img, y, x, valid);
+        const int kb = KP == 32 ? 0 : kb_rt;  // one K block: taps known at compile time
+        uint32_t taps;
+        const __nv_bfloat16* ctr = pixel(tile, tid, taps);
         const uint32_t base = afptx::smem_addr(sa);
 #pragma unroll
         for (int c = 0; c < 4; c++) {
@@ -221,15 +274,15 @@ struct FwdOp {
             if constexpr (CIN == 2) {
 #pragma unroll
                 for (int i = 0; i < 4; i++) {
-                    const int t = (k0 >> 1) + i, yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-                    const bool in = valid && t < 9 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-                    const __nv_bfloat16* src = in ? a.x + (((int64_t)img * a.H + yy) * a.W + xx) * 2 : a.x;
+                    const int t = (k0 >> 1) + i;
+                    const bool in = t < 9 && ((taps >> t) & 1u);
+                    const __nv_bfloat16* src = in ? ctr + ((t / 3 - 1) * a.W + (t % 3 - 1)) * 2 : a.x;
                     cp4(dst + 4 * i, src, in ? 4u : 0u);
                 }
             } else {
-                const int t = k0 / CIN, i0 = k0 % CIN, yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-                const bool in = valid && t < 9 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-                const __nv_bfloat16* src = in ? a.x + (((int64_t)img * a.H + yy) * a.W + xx) * CIN + i0 : a.x;
+                const int t = k0 / CIN, i0 = k0 % CIN;
+                const bool in = t < 9 && ((taps >> t) & 1u);
+                const __nv_bfloat16* src = in ? ctr + ((t / 3 - 1) * a.W + (t % 3 - 1)) * CIN + i0 : a.x;
                 cp16(dst, src, in ? 16u : 0u);
             }
         }
@@ -252,22 +305,36 @@ struct FwdOp {
             afumma::ld_32x32b_x16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
             afumma::wait_ld();
             float m[16];
-            int qi[16];
+            const float4* bv = reinterpret_cast<const float4*>(a.bias + c0);
 #pragma unroll
-            for (int i = 0; i < 16; i++) {
-                m[i] = fmaxf(__uint_as_float(v[i]) + __ldg(a.bias + c0 + i), 0.f);
-                qi[i] = q;
+            for (int k = 0; k < 4; k++) {
+                const float4 b4 = __ldg(bv + k);
+                m[4 * k] = fmaxf(__uint_as_float(v[4 * k]) + b4.x, 0.f);
+                m[4 * k + 1] = fmaxf(__uint_as_float(v[4 * k + 1]) + b4.y, 0.f);
+                m[4 * k + 2] = fmaxf(__uint_as_float(v[4 * k + 2]) + b4.z, 0.f);
+                m[4 * k + 3] = fmaxf(__uint_as_float(v[4 * k + 3]) + b4.w, 0.f);
             }
+            int qi[16];
+            if (a.idx) {  // training: the argmax travels with the maximum
 #pragma unroll
-            for (int sh = 1; sh <= 2; sh <<= 1) {
+                for (int i = 0; i < 16; i++) qi[i] = q;
 #pragma unroll
-                for (int i = 0; i < 16; i++) {
-                    const float om = __shfl_xor_sync(0xffffffffu, m[i], sh);
-                    const int oq = __shfl_xor_sync(0xffffffffu, qi[i], sh);
-                    if (om > m[i] || (om == m[i] && oq < qi[i])) {  // the first maximum in raster order
-                        m[i] = om;
-                        qi[i] = oq;
+                for (int sh = 1; sh <= 2; sh <<= 1) {
+#pragma unroll
+                    for (int i = 0; i < 16; i++) {
+                        const float om = __shfl_xor_sync(0xffffffffu, m[i], sh);
+                        const int oq = __shfl_xor_sync(0xffffffffu, qi[i], sh);
+                        if (om > m[i] || (om == m[i] && oq < qi[i])) {  // the first maximum in raster order
+                            m[i] = om;
+                            qi[i] = oq;
+                        }
                     }
+                }
+            } else {
+#pragma unroll
+                for (int sh = 1; sh <= 2; sh <<= 1) {
+#pragma unroll
+                    for (int i = 0; i < 16; i++) m[i] = fmaxf(m[i], __shfl_xor_sync(0xffffffffu, m[i], sh));
                 }
             }
             if (q == 0 && pp < npool) {
@@ -306,7 +373,7 @@ template <int CIN, int COUT>
 struct DgradOp {
     static_assert(CIN % 16 == 0 && CIN <= 256 && COUT % 8 == 0 && (9 * COUT) % 32 == 0, "channels");
     static constexpr int K = 9 * COUT;
-    static constexpr int NS = 6, TCOLS = pow2_cols(CIN);
+    static constexpr int NS = 6, NACC = 2, NCOL = CIN;
     static constexpr uint32_t SA = 128 * 32 * 2, SB = 0, RB = CIN * K * 2;
     struct Args {
         const __nv_bfloat16* dz;  // [n][H][W][COUT]
@@ -323,24 +390,31 @@ struct DgradOp {
     __device__ void resident(uint8_t* res, int tid) const
     {
         const uint32_t base = afptx::smem_addr(res);
-        for (int e = tid; e < CIN * K / 8; e += kThreads) {
+        for (int e = tid; e < CIN * K / 8; e += kProd) {
             const int i = e / (K / 8), kg = e % (K / 8);
             cp16(base + kmaj_off(i, kg, CIN), a.wd + i * K + 8 * kg, 16);
         }
     }
     __device__ void stage(uint8_t* sa, uint8_t*, int tile, int kb, int tid) const
     {
+        // tap t = dy * 3 + dx reads dZ at (y + 1 - dy, x + 1 - dx): bit t set when inside
         const int p = tile * 128 + tid;
-        const bool valid = p < P;
-        const int pc = valid ? p : 0, img = pc / (a.H * a.W), rem = pc - img * a.H * a.W;
-        const int y = rem / a.W, x = rem % a.W;
+        uint32_t taps = 0u;
+        const __nv_bfloat16* ctr = a.dz;
+        if (p < P) {
+            const int img = p / (a.H * a.W), rem = p - img * a.H * a.W, y = rem / a.W, x = rem % a.W;
+            const uint32_t rows = (y + 1 < a.H ? 1u : 0u) | 2u | (y > 0 ? 4u : 0u);
+            const uint32_t cols = (x + 1 < a.W ? 1u : 0u) | 2u | (x > 0 ? 4u : 0u);
+#pragma unroll
+            for (int t = 0; t < 9; t++) taps |= ((rows >> (t / 3)) & (cols >> (t % 3)) & 1u) << t;
+            ctr = a.dz + (int64_t)p * COUT;
+        }
         const uint32_t base = afptx::smem_addr(sa);
 #pragma unroll
         for (int c = 0; c < 4; c++) {
             const int k0 = kb * 32 + 8 * c, t = k0 / COUT, o0 = k0 % COUT;
-            const int yy = y - (t / 3 - 1), xx = x - (t % 3 - 1);
-            const bool in = valid && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-            const __nv_bfloat16* src = in ? a.dz + (((int64_t)img * a.H + yy) * a.W + xx) * COUT + o0 : a.dz;
+            const bool in = (taps >> t) & 1u;
+            const __nv_bfloat16* src = in ? ctr + ((1 - t / 3) * a.W + (1 - t % 3)) * COUT + o0 : a.dz;
             cp16(base + kmaj_off(tid, c, 128), src, in ? 16u : 0u);
         }
     }
@@ -379,61 +453,75 @@ struct DgradOp {
 };
 
 // ------------------------------------------------------------ weight gradient
-// Tile = a run of `kchunk` pixels (K, split across the grid); A = dZ^T (rows
-// o < COUT of 128; the other rows' results are never read), B = the gathered
-// input (rows n = t * CIN + i); both MN-major: a 16-byte chunk is 8 channels
-// of one pixel.  Partial sums go to the fp32 gradient with atomics.
-template <int CIN, int COUT>
+// Tile = a run of `kchunk` pixels (K, split across the grid); stages of BKW
+// pixels.  A = dZ^T and B = the gathered input (rows n = t * CIN + i), both
+// MN-major: a 16-byte chunk is 8 channels of one pixel.  A holds only the
+// COUT real rows (K-direction stride COUT/8 core matrices); the MMA's other
+// rows (M = 128) read whatever follows in the stage, and their results are
+// never read.  Partial sums go to the fp32 gradient with atomics.
+template <int CIN, int COUT, int BKW>
 struct WgradOp {
-    static_assert((CIN == 2 || CIN % 8 == 0) && COUT % 16 == 0 && COUT <= 128, "channels");
+    static_assert((CIN == 2 || CIN % 8 == 0) && COUT % 16 == 0 && COUT <= 128 && BKW % 64 == 0, "shapes");
     static constexpr int K9 = 9 * CIN, NP = (K9 + 15) / 16 * 16;
     static_assert(NP <= 256 || (NP % 32 == 0 && NP <= 512), "columns");
-    static constexpr int NS = NP > 256 ? 3 : 4, TCOLS = pow2_cols(NP);
-    static constexpr uint32_t SA = 128 * 64 * 2, SB = NP * 64 * 2, RB = 0;
+    static constexpr int NS = 4, NACC = 1, NCOL = NP;
+    static constexpr uint32_t SA = COUT * BKW * 2, SB = NP * BKW * 2, RB = 0;
+    static_assert(SB >= 16 * 128, "the padding rows of A must read inside the stage");
     struct Args {
         const __nv_bfloat16* dz;  // [n][H][W][COUT]
         const __nv_bfloat16* x;   // [n][H][W][CIN]
         float* grad;              // [COUT][9 CIN], accumulated
-        int n, H, W, kchunk;      // kchunk: pixels per tile, a multiple of 64
+        int n, H, W, kchunk;      // kchunk: pixels per tile, a multiple of BKW
         int* err;
     };
     const Args a;
     int P;
     __device__ WgradOp(const Args& a_) : a(a_), P(a_.n * a_.H * a_.W) {}
     __device__ int ntiles() const { return (P + a.kchunk - 1) / a.kchunk; }
-    __device__ int nkb() const { return a.kchunk / 64; }
+    __device__ int nkb() const { return a.kchunk / BKW; }
     __device__ void resident(uint8_t*, int) const {}
     __device__ void stage(uint8_t* sa, uint8_t* sb, int tile, int kb, int tid) const
     {
-        // every chunk of this thread is pixel k = tid % 64 of the stage
-        const int k = tid & 63, p = tile * a.kchunk + kb * 64 + k;
-        const bool valid = p < P;
-        const int pc = valid ? p : 0, img = pc / (a.H * a.W), rem = pc - img * a.H * a.W;
-        const int y = rem / a.W, x = rem % a.W;
         const uint32_t ba = afptx::smem_addr(sa), bb = afptx::smem_addr(sb);
-        for (int g = tid >> 6; g < COUT / 8; g += 2)
-            cp16(ba + mnmaj_off(g, k, 128), valid ? a.dz + (int64_t)pc * COUT + 8 * g : a.dz, valid ? 16u : 0u);
-        for (int g = tid >> 6; g < NP / 8; g += 2) {
-            const uint32_t dst = bb + mnmaj_off(g, k, NP);
-            if constexpr (CIN == 2) {
+#pragma unroll 1
+        for (int r = 0; r < BKW / 64; r++) {
+            // every chunk of this thread in this pass is pixel k of the stage
+            const int k = 64 * r + (tid & 63), p = tile * a.kchunk + kb * BKW + k;
+            uint32_t taps = 0u;  // bit t = dy * 3 + dx: tap (y + dy - 1, x + dx - 1) inside the image
+            const __nv_bfloat16* ctr = a.x;
+            const bool valid = p < P;
+            if (valid) {
+                const int img = p / (a.H * a.W), rem = p - img * a.H * a.W, y = rem / a.W, x = rem % a.W;
+                const uint32_t rows = (y > 0 ? 1u : 0u) | 2u | (y + 1 < a.H ? 4u : 0u);
+                const uint32_t cols = (x > 0 ? 1u : 0u) | 2u | (x + 1 < a.W ? 4u : 0u);
 #pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    const int t = 4 * g + i, yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-                    const bool in = valid && t < 9 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-                    cp4(dst + 4 * i, in ? a.x + (((int64_t)img * a.H + yy) * a.W + xx) * 2 : a.x, in ? 4u : 0u);
+                for (int t = 0; t < 9; t++) taps |= ((rows >> (t / 3)) & (cols >> (t % 3)) & 1u) << t;
+                ctr = a.x + (int64_t)p * CIN;
+            }
+            for (int g = tid >> 6; g < COUT / 8; g += 2)
+                cp16(ba + mnmaj_off(g, k, COUT), valid ? a.dz + (int64_t)p * COUT + 8 * g : a.dz, valid ? 16u : 0u);
+            for (int g = tid >> 6; g < NP / 8; g += 2) {
+                const uint32_t dst = bb + mnmaj_off(g, k, NP);
+                if constexpr (CIN == 2) {
+#pragma unroll
+                    for (int i = 0; i < 4; i++) {
+                        const int t = 4 * g + i;
+                        const bool in = t < 9 && ((taps >> t) & 1u);
+                        cp4(dst + 4 * i, in ? ctr + ((t / 3 - 1) * a.W + (t % 3 - 1)) * 2 : a.x, in ? 4u : 0u);
+                    }
+                } else {
+                    const int n0 = 8 * g, t = n0 / CIN, i0 = n0 % CIN;
+                    const bool in = t < 9 && ((taps >> t) & 1u);
+                    cp16(dst, in ? ctr + ((t / 3 - 1) * a.W + (t % 3 - 1)) * CIN + i0 : a.x, in ? 16u : 0u);
                 }
-            } else {
-                const int n0 = 8 * g, t = n0 / CIN, i0 = n0 % CIN, yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-                const bool in = valid && t < 9 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-                cp16(dst, in ? a.x + (((int64_t)img * a.H + yy) * a.W + xx) * CIN + i0 : a.x, in ? 16u : 0u);
             }
         }
     }
     __device__ void mma(uint32_t sa, uint32_t sb, uint32_t, int kb, uint32_t tmem) const
     {
-        constexpr uint32_t lbo_a = 16 * 128, lbo_b = NP / 8 * 128;
+        constexpr uint32_t lbo_a = COUT / 8 * 128, lbo_b = NP / 8 * 128;
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
+        for (int j = 0; j < BKW / 16; j++) {
             const uint32_t acc = (kb | j) != 0;
             if constexpr (NP <= 256) {
                 mma_k16(tmem, sa + 2 * j * lbo_a, lbo_a, sb + 2 * j * lbo_b, lbo_b, afumma::idesc_bf16(128, NP, 1, 1),
@@ -470,7 +558,7 @@ struct WgradOp {
 // K split into `kchunk` runs (atomic epilogue only).
 template <bool AK, bool BK, int EPI>
 struct GemmOp {
-    static constexpr int NS = 4, TCOLS = 64;
+    static constexpr int NS = 4, NACC = 2, NCOL = 64;
     static constexpr uint32_t SA = 128 * 32 * 2, SB = 64 * 32 * 2, RB = 0;
     struct Args {
         const __nv_bfloat16* A;
@@ -510,7 +598,7 @@ struct GemmOp {
         } else {
 #pragma unroll
             for (int i = 0; i < 4; i++) {
-                const int e = tid + kThreads * i, mg = e & 15, k = e >> 4, m = m0 + 8 * mg;
+                const int e = tid + kProd * i, mg = e & 15, k = e >> 4, m = m0 + 8 * mg;
                 const bool in = m < a.M && k0 + k < kend;
                 const uint32_t bytes = in ? (uint32_t)min(16, 2 * (a.M - m)) : 0u;
                 cp16(ba + mnmaj_off(mg, k, 128), in ? a.A + (int64_t)(k0 + k) * a.lda + m : a.A, bytes);
@@ -519,14 +607,14 @@ struct GemmOp {
         if constexpr (BK) {
 #pragma unroll
             for (int i = 0; i < 2; i++) {
-                const int e = tid + kThreads * i, r = e >> 2, c = e & 3, n = n0 + r, k = k0 + 8 * c;
+                const int e = tid + kProd * i, r = e >> 2, c = e & 3, n = n0 + r, k = k0 + 8 * c;
                 const bool in = n < a.N && k < kend;
                 cp16(bb + kmaj_off(r, c, 64), in ? a.B + (int64_t)n * a.ldb + k : a.B, in ? 16u : 0u);
             }
         } else {
 #pragma unroll
             for (int i = 0; i < 2; i++) {
-                const int e = tid + kThreads * i, ng = e & 7, k = e >> 3, n = n0 + 8 * ng;
+                const int e = tid + kProd * i, ng = e & 7, k = e >> 3, n = n0 + 8 * ng;
                 const bool in = n < a.N && k0 + k < kend;
                 const uint32_t bytes = in ? (uint32_t)min(16, 2 * (a.N - n)) : 0u;
                 cp16(bb + mnmaj_off(ng, k, 64), in ? a.B + (int64_t)(k0 + k) * a.ldb + n : a.B, bytes);
@@ -586,16 +674,24 @@ int launch(const typename Op::Args& a, int ntiles, cudaStream_t s, const char* w
     AF_CUDA(cudaGetDevice(&dev));
     if (cached_dev != dev) {
         AF_CUDA(cudaFuncSetAttribute(k_umma<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int per_sm = 0, nsm = 0;
-        AF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_umma<Op>, kThreads, smem));
+        AF_CUDA(cudaFuncSetAttribute(k_umma<Op>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared));
+        int nsm = 0, smem_sm = 0, per_sm = 0;
         AF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        // every resident block holds Op::TCOLS of the 512 tensor-memory columns
-        per_sm = per_sm < 512 / Op::TCOLS ? per_sm : 512 / Op::TCOLS;
-        cached_blocks = (per_sm < 1 ? 1 : per_sm) * nsm;
+        AF_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        AF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_umma<Op>, kBlock, smem));
+        // resident blocks: by shared memory (1 KB reserved per block), warps, and
+        // the 512 tensor-memory columns each block takes its share of
+        const int by_smem = smem_sm / (int)(smem + 1024 + 256);
+        int b = by_smem < 64 / (kBlock / 32) ? by_smem : 64 / (kBlock / 32);
+        if (per_sm > b) b = per_sm;
+        const int by_tmem = 512 / pow2_cols(Op::NACC * Op::NCOL);
+        if (b > by_tmem) b = by_tmem;
+        cached_blocks = (b < 1 ? 1 : b) * nsm;
         cached_dev = dev;
     }
     const int grid = ntiles < cached_blocks ? ntiles : cached_blocks;
-    k_umma<Op><<<grid, kThreads, smem, s>>>(a);
+    k_umma<Op><<<grid, kBlock, smem, s>>>(a);
     return af_cuda_check(cudaGetLastError(), what);
 }
 
@@ -643,20 +739,19 @@ int nn_conv_dgrad(int layer, const __nv_bfloat16* dz, int n, int H, int W, const
 int nn_conv_wgrad(int layer, const __nv_bfloat16* dz, const __nv_bfloat16* x, int n, int H, int W, float* grad,
                   int* err, cudaStream_t s)
 {
-    // about two tiles of pixels per SM, each a multiple of 64 pixels
+    // about two tiles of pixels per SM, each a multiple of 256 pixels
     const int64_t P = (int64_t)n * H * W;
     int64_t kc = (P + 2 * sm_count() - 1) / (2 * sm_count());
-    kc = (kc + 63) / 64 * 64;
-    if (kc < 256) kc = 256;
+    kc = (kc + 255) / 256 * 256;
     const int tiles = (int)((P + kc - 1) / kc);
-#define AF_WG(L, CI, CO)                                                                    \
-    if (layer == L) {                                                                       \
-        typename WgradOp<CI, CO>::Args a{dz, x, grad, n, H, W, (int)kc, err};               \
-        return launch<WgradOp<CI, CO>>(a, tiles, s, "conv weight gradient (tcgen05)");      \
+#define AF_WG(L, CI, CO, BKW)                                                                      \
+    if (layer == L) {                                                                              \
+        typename WgradOp<CI, CO, BKW>::Args a{dz, x, grad, n, H, W, (int)kc, err};                 \
+        return launch<WgradOp<CI, CO, BKW>>(a, tiles, s, "conv weight gradient (tcgen05)");        \
     }
-    AF_WG(0, 2, 16)
-    AF_WG(1, 16, 32)
-    AF_WG(2, 32, 64)
+    AF_WG(0, 2, 16, 256)
+    AF_WG(1, 16, 32, 128)
+    AF_WG(2, 32, 64, 64)
 #undef AF_WG
     return af_set_error(AF_EINVAL, "conv weight gradient: layer %d", layer);
 }

@@ -46,7 +46,7 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 // Inference batches of at least this many images run the layered tensor-core
 // network; smaller ones the fused one-kernel network (AFGB_CNN_UMMA_MIN
 // overrides at model creation).
-constexpr int kUmmaInferMin = 64;
+constexpr int kUmmaInferMin = 2048;
 
 }  // namespace
 
@@ -283,9 +283,8 @@ static int backward(af_model_t m, const __nv_bfloat16* x, int n, cudaStream_t s)
 {
     for (int l = NL - 1; l >= 0; l--) {
         const Layer& L = m->L[l];
-        const int64_t P = (int64_t)n * L.H * L.W;
-        if (int rc = nn_pool_back(m->d_da[l + 1], m->d_idx[l], n, L.H, L.W, L.cout, m->d_dz[l], s)) return rc;
-        if (int rc = nn_colsum(m->d_dz[l], P, L.cout, m->d_grads + L.boff, s)) return rc;
+        if (int rc = nn_pool_back(m->d_da[l + 1], m->d_idx[l], n, L.H, L.W, L.cout, m->d_dz[l], m->d_grads + L.boff, s))
+            return rc;
         const __nv_bfloat16* a = l ? m->d_a[l] : x;
         if (int rc = nn_conv_wgrad(l, m->d_dz[l], a, n, L.H, L.W, m->d_grads + L.woff, m->d_err, s)) return rc;
         if (l > 0) {

@@ -14,39 +14,55 @@ namespace {
 
 // dz [n][H][W][c] (bf16) = the pooled gradient routed to the argmax of each
 // 2x2 window where that maximum (a ReLU output) was positive: idx holds the
-// argmax (0..3, raster order) | 4 when the maximum was > 0
-__global__ void k_pool_back(const __nv_bfloat16* __restrict__ dp, const uint8_t* __restrict__ idx, int n, int H,
-                            int W, int c, __nv_bfloat16* __restrict__ dz)
+// argmax (0..3, raster order) | 4 when the maximum was > 0.  Thread = (pooled
+// pixel, 8 channels): one 16-byte load of the pooled gradient, one 8-byte load
+// of the argmax bytes, four 16-byte stores.  The bias gradient (the sum of dz
+// over all pixels, i.e. of the routed values) is accumulated on the way:
+// per-thread sums, reduced per block in shared memory, one atomic per channel
+// and block.
+__global__ void __launch_bounds__(256) k_pool_back(const __nv_bfloat16* __restrict__ dp, const uint8_t* __restrict__ idx,
+                                                   int n, int H, int W, int c, __nv_bfloat16* __restrict__ dz,
+                                                   float* __restrict__ db)
 {
-    const int64_t total = (int64_t)n * H * W * c;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int ch = (int)(e % c);
-        const int64_t p = e / c;
-        const int x = (int)(p % W), y = (int)((p / W) % H);
-        const int64_t b = p / ((int64_t)W * H);
-        const int64_t o = ((b * (H / 2) + y / 2) * (W / 2) + x / 2) * c + ch;
-        float v = 0.f;
-        if (idx[o] == (uint8_t)(4 | ((y & 1) * 2 + (x & 1)))) v = __bfloat162float(dp[o]);
-        dz[e] = __float2bfloat16(v);
+    __shared__ float part[256][8];
+    const int Ho = H / 2, Wo = W / 2, cg = c / 8;
+    const int64_t total = (int64_t)n * Ho * Wo * cg;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;  // a multiple of cg: each thread keeps its group
+    const int g = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) % cg);
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+        const int64_t pp = e / cg;
+        const int xo = (int)(pp % Wo);
+        const int64_t r = pp / Wo;  // img * Ho + yo
+        const uint4 v = *reinterpret_cast<const uint4*>(dp + pp * c + 8 * g);
+        const uint2 ix = *reinterpret_cast<const uint2*>(idx + pp * c + 8 * g);
+        const uint16_t* vv = reinterpret_cast<const uint16_t*>(&v);
+        const uint8_t* ii = reinterpret_cast<const uint8_t*>(&ix);
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            if (ii[j] & 4) acc[j] += __bfloat162float(__ushort_as_bfloat16(vv[j]));
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            uint32_t w[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint32_t lo = ii[2 * j] == (uint8_t)(4 | q) ? vv[2 * j] : 0u;
+                const uint32_t hi = ii[2 * j + 1] == (uint8_t)(4 | q) ? vv[2 * j + 1] : 0u;
+                w[j] = lo | (hi << 16);
+            }
+            const int64_t p = (2 * r + (q >> 1)) * W + 2 * xo + (q & 1);  // (img * H + y) * W + x
+            *reinterpret_cast<uint4*>(dz + p * c + 8 * g) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
     }
-}
-
-// db[o] += sum over pixels of dz[p][o]   (dz bf16 [P][c]); block partial sums
-// are reduced in shared memory, then one atomic per channel and block
-__global__ void k_colsum(const __nv_bfloat16* __restrict__ dz, int64_t P, int c, float* __restrict__ db)
-{
-    __shared__ float part[256];
-    const int ch = threadIdx.x % c;
-    const int lanes = blockDim.x / c;
-    float s = 0.f;
-    for (int64_t p = (int64_t)blockIdx.x * lanes + threadIdx.x / c; p < P; p += (int64_t)gridDim.x * lanes)
-        s += __bfloat162float(dz[p * c + ch]);
-    part[threadIdx.x] = s;
+#pragma unroll
+    for (int j = 0; j < 8; j++) part[threadIdx.x][j] = acc[j];
     __syncthreads();
-    if (threadIdx.x < c) {
-        float t = 0.f;
-        for (int l = 0; l < lanes; l++) t += part[l * c + threadIdx.x];
-        atomicAdd(db + threadIdx.x, t);
+    if ((int)threadIdx.x < c) {
+        // channel ch = 8 gg + j is summed by the threads t with t % cg == gg
+        const int gg = threadIdx.x / 8, j = threadIdx.x % 8;
+        float sum = 0.f;
+        for (int t = gg; t < (int)blockDim.x; t += cg) sum += part[t][j];  // 256 % cg == 0: thread t has group t % cg
+        atomicAdd(db + threadIdx.x, sum);
     }
 }
 
@@ -135,19 +151,13 @@ unsigned grid_for(int64_t n, int threads)
 }  // namespace
 
 int nn_pool_back(const __nv_bfloat16* dp, const uint8_t* idx, int n, int H, int W, int c, __nv_bfloat16* dz,
-                 cudaStream_t s)
+                 float* db, cudaStream_t s)
 {
-    k_pool_back<<<grid_for((int64_t)n * H * W * c, 256), 256, 0, s>>>(dp, idx, n, H, W, c, dz);
+    if (c % 8 || c > 256 || ((uintptr_t)dp & 15) || ((uintptr_t)dz & 15) || ((uintptr_t)idx & 7))
+        return af_set_error(AF_EINVAL, "pool backward: channels / alignment");
+    const int64_t total = (int64_t)n * (H / 2) * (W / 2) * (c / 8);
+    k_pool_back<<<grid_for(total, 256), 256, 0, s>>>(dp, idx, n, H, W, c, dz, db);
     return af_cuda_check(cudaGetLastError(), "pool backward");
-}
-
-int nn_colsum(const __nv_bfloat16* dz, int64_t P, int c, float* db, cudaStream_t s)
-{
-    const int threads = (256 / c) * c;
-    unsigned blocks = grid_for(P, threads / c);
-    if (blocks > 304) blocks = 304;
-    k_colsum<<<blocks, threads, 0, s>>>(dz, P, c, db);
-    return af_cuda_check(cudaGetLastError(), "bias gradient");
 }
 
 int nn_head(const __nv_bfloat16* a3, int n, const float* fw, const float* fb, float* logits, float* prob,

@@ -29,9 +29,10 @@ int nn_conv_dgrad(int layer, const __nv_bfloat16* dz, int n, int H, int W, const
 int nn_conv_wgrad(int layer, const __nv_bfloat16* dz, const __nv_bfloat16* x, int n, int H, int W, float* grad,
                   int* err, cudaStream_t s);
 int nn_pack_wd(const float* w, int cin, int cout, __nv_bfloat16* wd, cudaStream_t s);
+// 2x2 max-pool backward (dz from the pooled gradient and the argmax bytes);
+// adds the bias gradient (sum of dz over pixels) into db.
 int nn_pool_back(const __nv_bfloat16* dp, const uint8_t* idx, int n, int H, int W, int c, __nv_bfloat16* dz,
-                 cudaStream_t s);
-int nn_colsum(const __nv_bfloat16* dz, int64_t P, int c, float* db, cudaStream_t s);
+                 float* db, cudaStream_t s);
 int nn_head(const __nv_bfloat16* a3, int n, const float* fw, const float* fb, float* logits, float* prob,
             const int32_t* y, float* loss, float* dfw, float* dfb, __nv_bfloat16* da3, cudaStream_t s);
 int nn_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, int step, cudaStream_t s);
