@@ -467,13 +467,20 @@ typedef struct {
 /* Builds the batch: one plan per beam, each beam's plane / S/N / candidate
  * buffers on the current device (AF_ENOBUFS if they need more than
  * hbm_budget bytes; 0 = no budget), and picks the dedispersion strategy by
- * timing every compiled tile shape and the group-row strategy on these beams
- * (the beams' inputs must be valid device memory; their contents do not
- * matter).  The group-row strategy takes a row buffer of at most 16 GiB
- * (outside hbm_budget), freed again when another strategy wins.
+ * timing, on these beams (their inputs must be valid device memory; their
+ * contents do not matter): one persistent channel-tile launch for every
+ * compiled tile shape; the beams one after another on their single-plan
+ * paths (group rows sharing one row buffer of at most 16 GiB); and persistent
+ * group rows -- the time axis in waves, per wave the group rows of every
+ * beam's block side by side in one buffer of at most 64 GiB, then one
+ * persistent launch over all beams' (DM block, tile) items -- for ring depths
+ * 3 and 2 and two wave lengths.  Row buffers lie outside hbm_budget and are
+ * freed again when another strategy wins.  This is the multi-beam processing
+ * of Sec. 4.3 on one GPU.
  * With the environment variable AFGB_AUTOTUNE_CACHE naming a file, the
  * choice is cached there as JSON keyed by GPU name and beam shapes;
- * AFGB_BATCH_STRATEGY=tile or =pairs limits the choice to those strategies. */
+ * AFGB_BATCH_STRATEGY=tile, =pairs or =persistent limits the choice to those
+ * strategies. */
 int af_batch_build(af_batch_t* out, const af_beam_desc_t* beams, int nbeams, size_t hbm_budget);
 
 /* Enqueues the whole batch on `stream`: the first call captures a CUDA graph,
@@ -491,9 +498,18 @@ int af_batch_buffers(af_batch_t batch, int beam, int32_t** d_plane, float** d_sn
                      int64_t* nout);
 
 /* The strategy chosen by the autotuner: the persistent tile kernel's DM rows
- * per block and 128-output groups per lane, or nw = 15, m = 0 for beam after
- * beam; its measured time (ms, 0 if read from the cache). */
+ * per block and 128-output groups per lane; nw = 15, m = 0 for beam after
+ * beam; nw = ring depth, m = -(tiles per wave) for persistent group rows; its
+ * measured time (ms, 0 if read from the cache). */
 int af_batch_shape(af_batch_t batch, int* nw, int* m, float* tuned_ms, int* from_cache);
+
+/* Candidate i (0, 1, ...) the autotuner timed at build: kind 0 = persistent
+ * channel tiles (p1, p2 = the shape), 1 = beam after beam (p1 = 15, p2 = 0;
+ * the fair baseline of a batch on group rows: the same kernels one plan at a
+ * time, no graph), 2 = persistent group rows (p1 = ring depth, p2 = tiles per
+ * wave); its time in ms.  AF_EINVAL past the last candidate (none when the
+ * choice came from the cache).  No counterpart in the paper. */
+int af_batch_tuning(af_batch_t batch, int i, int* kind, int* p1, int* p2, float* ms);
 
 int af_batch_destroy(af_batch_t batch);
 

@@ -90,6 +90,7 @@ SIGNATURES = {
     "af_batch_candidates": [_P, _I, _P, _I32, _P],
     "af_batch_buffers": [_P, _I, _P, _P, _P, _P],
     "af_batch_shape": [_P, _P, _P, _P, _P],
+    "af_batch_tuning": [_P, _I, _P, _P, _P, _P],
     "af_batch_destroy": [_P],
     "af_stream_open": [_P, _P],
     "af_stream_push": [_P, _I, _P, _I64, _I64, _I64],
@@ -430,6 +431,18 @@ def af_batch_shape(batch):
     _check(lib().af_batch_shape(batch, ctypes.byref(nw), ctypes.byref(m), ctypes.byref(ms), ctypes.byref(fc)),
            "af_batch_shape")
     return nw.value, m.value, ms.value, bool(fc.value)
+
+
+def af_batch_tuning(batch):
+    """Every candidate the autotuner timed: list of dict(kind, p1, p2, ms)."""
+    out = []
+    kind, p1, p2, ms = _I(), _I(), _I(), _F()
+    for i in range(64):
+        rc = lib().af_batch_tuning(batch, i, ctypes.byref(kind), ctypes.byref(p1), ctypes.byref(p2), ctypes.byref(ms))
+        if rc != AF_OK:
+            break
+        out.append(dict(kind=kind.value, p1=p1.value, p2=p2.value, ms=ms.value))
+    return out
 
 
 def af_batch_destroy(batch):

@@ -3,17 +3,22 @@
 The paper trains its detector on pulses injected into real spectrograms
 (Sec. 4.1) and names the RFI that triggers its search (Sec. 4.4): impulsive
 broadband (zero-DM) bursts, narrowband interference and burst-like
-fluctuations.  Here every chunk is the 256-channel workload (1000-1500 MHz,
-98.304 us, 2^15 samples of N(128,12)) with injected dispersed pulses and the
-three RFI shapes; the search runs on the GPU, its candidates are clustered
-with the true-positive rule of Sec. 4.2, and each cluster's strongest
-candidate becomes one sample (two 64 x 64 cut-outs), labelled 1 when it
-matches an injected pulse.  The per-channel start samples of the pulses come
-from the library's own delay table (a plan over the pulses' DMs).
+fluctuations.  Here every chunk is synthetic noise of one workload's band and
+sampling (CHUNK: the 256-channel search; STREAM_CHUNK: the streaming
+workload's 4096 channels and DM 0-2000 grid, in chunks of 2^15 outputs) with
+injected dispersed pulses and the three RFI shapes; the search runs on the
+GPU, its candidates are clustered with the true-positive rule of Sec. 4.2,
+and each cluster's strongest candidate becomes one sample (two 64 x 64
+cut-outs), labelled 1 when it matches an injected pulse.
 
-evaluate() compares, on held-out chunks, the plain boxcar-S/N threshold (the
-method without the network) with threshold-then-network at equal recall of
-injected pulses with S/N >= 8, and reports both false-positive rates.
+Where a pulse lands in each channel comes from the caller's `offsets_fn(dm,
+t0)` (per-channel start samples of a pulse arriving at the top of the band at
+sample t0): the test-suite and the checkpoint script pass the CPU oracle's
+injector; without one, the library's own delay table is used.
+
+equal_recall() compares the plain boxcar-S/N threshold (the method without
+the network) with threshold-then-network at equal recall of injected pulses
+with S/N >= 8, and reports both false-positive rates.
 """
 import numpy as np
 import torch
@@ -21,41 +26,55 @@ import torch
 from . import _lib, synth
 from .search import Plan
 
+WIDTHS = [1, 2, 4, 8, 16, 32, 64, 128, 256]
 CHUNK = dict(nchan=256, f_lo=1000.0, f_hi=1500.0, tsamp=98.304e-6, nsamp=1 << 15,
-             dm_list=np.arange(0.0, 501.0, 1.0), widths=[1, 2, 4, 8, 16, 32])
+             dm_list=np.arange(0.0, 501.0, 1.0), widths=[1, 2, 4, 8, 16, 32], inj_dm=(20.0, 480.0), n_pulses=4)
+# 4096 channels, 49.152 us, DMs 0..2000: the DM-2000 delay (93,766 samples) + 2^15 outputs
+STREAM_CHUNK = dict(nchan=4096, f_lo=1000.0, f_hi=1500.0, tsamp=49.152e-6, nsamp=93766 + (1 << 15),
+                    dm_list=np.arange(0.0, 2001.0, 1.0), widths=WIDTHS, inj_dm=(50.0, 1950.0), n_pulses=3)
 DM_TOL, TOA_TOL = 20.0, 0.2
 
 
-class Generator:
-    """Chunks with injected pulses and RFI; pulse delays from the library."""
+def library_offsets(cfg, pool=4096, seed=0):
+    """offsets_fn from the library's delay table: a plan over `pool` random
+    DMs in cfg's injection range, each pulse snapped to the nearest of them."""
+    rng = np.random.default_rng(seed)
+    dms = np.sort(rng.uniform(cfg["inj_dm"][0], cfg["inj_dm"][1], pool))
+    p = Plan(cfg["nchan"], cfg["f_lo"], cfg["f_hi"], cfg["tsamp"], dms)
+    D = p.delays().astype(np.int64)
+    p.close()
 
-    def __init__(self, cfg=CHUNK, n_pulses=4, seed=0, device="cuda"):
-        self.cfg, self.n_pulses, self.device = cfg, n_pulses, device
+    def fn(dm, t0):
+        j = int(np.clip(np.searchsorted(dms, dm), 0, pool - 1))
+        return int(t0) + D[j], float(dms[j])
+    return fn
+
+
+class Generator:
+    """Chunks of cfg's shape with n_pulses injected pulses and RFI."""
+
+    def __init__(self, cfg=CHUNK, nout=None, offsets_fn=None, seed=0, device="cuda"):
+        self.cfg, self.device, self.seed = cfg, device, seed
+        self.n_pulses = cfg.get("n_pulses", 4)
         self.rng = np.random.default_rng(seed)
-        self.seed = seed
-        # one plan over a pool of random injection DMs
-        self.pool_dm = self.rng.uniform(20.0, 480.0, 4096)
-        p = Plan(cfg["nchan"], cfg["f_lo"], cfg["f_hi"], cfg["tsamp"], self.pool_dm)
-        self.pool_delays = p.delays().astype(np.int64)
-        self.dmax_search = None
-        p.close()
+        self.nout = nout if nout is not None else cfg["nsamp"] - 11682
+        self.offsets_fn = offsets_fn or library_offsets(cfg, seed=seed)
         self.count = 0
 
     def chunk(self, rfi=True):
         cfg, rng = self.cfg, self.rng
         nchan, nsamp, tsamp = cfg["nchan"], cfg["nsamp"], cfg["tsamp"]
-        nout_guess = nsamp - 11682            # output span of the 0..500 DM search at this sampling
-        slots = rng.choice(np.arange(1, 5), size=self.n_pulses, replace=False) if self.n_pulses <= 4 else \
-            np.arange(1, self.n_pulses + 1)
+        span = self.nout // (self.n_pulses + 1)
         pulses, inj = [], []
-        span = nout_guess // 5
-        for k, s in enumerate(slots):
-            j = int(rng.integers(len(self.pool_dm)))
-            dm = float(self.pool_dm[j])
+        for s in range(1, self.n_pulses + 1):
+            dm = float(rng.uniform(*cfg["inj_dm"]))
             w = max(1, int(round(np.exp(rng.uniform(np.log(0.2e-3), np.log(10e-3))) / tsamp)))
             snr = float(rng.uniform(6.0, 30.0))
             t0 = int(s * span + rng.integers(-span // 4, span // 4))
-            pulses.append(synth.Pulse(t0 + self.pool_delays[j], w, synth.pulse_amplitude(snr, nchan, w)))
+            offs = self.offsets_fn(dm, t0)
+            if isinstance(offs, tuple):      # (offsets, the DM actually injected)
+                offs, dm = offs
+            pulses.append(synth.Pulse(np.asarray(offs, dtype=np.int64), w, synth.pulse_amplitude(snr, nchan, w)))
             inj.append((dm, t0 * tsamp, w, snr))
         r = None
         if rfi:
@@ -63,7 +82,8 @@ class Generator:
             bursts = []
             for _ in range(2):
                 ln = int(rng.integers(1, 21))
-                bursts.append((int(rng.integers(0, nout_guess)), ln, synth.pulse_amplitude(rng.uniform(10, 50), nchan, ln)))
+                bursts.append((int(rng.integers(0, self.nout)), ln,
+                               synth.pulse_amplitude(rng.uniform(10, 50), nchan, ln)))
             tones = [(float(rng.integers(0, nchan)), int(rng.integers(0, nsamp - 3000)), 2000,
                       float(rng.choice([-1, 1]) * 0.005), float(rng.uniform(2, 5)) * synth.NOISE_SIGMA)]
             r = synth.RFI(narrow_channels=narrow, bursts=bursts, tones=tones)
@@ -111,23 +131,29 @@ class Searcher:
 
 
 def match(reps, inj, dm_list, tsamp):
-    """For each cluster: index of the injection it matches (Sec. 4.2 rule) or -1."""
+    """For each cluster: index of the first injection it matches (Sec. 4.2
+    rule: |dDM| < 20 and |dTOA| < 0.2 s) or -1."""
     res = np.full(len(reps), -1, dtype=np.int64)
-    for i, c in enumerate(reps):
-        dm, toa = dm_list[int(c["dm_idx"])], int(c["abs_sample"]) * tsamp
-        for j, (idm, itoa, _, _) in enumerate(inj):
-            if abs(dm - idm) < DM_TOL and abs(toa - itoa) < TOA_TOL:
-                res[i] = j
-                break
+    if len(reps) == 0 or len(inj) == 0:
+        return res
+    dm = np.asarray(dm_list, dtype=np.float64)[np.asarray(reps["dm_idx"], dtype=np.int64)]
+    toa = np.asarray(reps["abs_sample"], dtype=np.int64) * tsamp
+    idm = np.array([v[0] for v in inj], dtype=np.float64)
+    itoa = np.array([v[1] for v in inj], dtype=np.float64)
+    for i0 in range(0, len(dm), 4096):      # blocks of clusters x all injections
+        ok = (np.abs(dm[i0:i0 + 4096, None] - idm[None, :]) < DM_TOL) & \
+             (np.abs(toa[i0:i0 + 4096, None] - itoa[None, :]) < TOA_TOL)
+        hit = ok.any(axis=1)
+        res[i0:i0 + 4096][hit] = ok.argmax(axis=1)[hit]
     return res
 
 
-def build_dataset(n_chunks, seed, searcher=None, gen=None):
+def build_dataset(n_chunks, seed, searcher=None, gen=None, offsets_fn=None):
     """Returns (cut-outs bf16 [N][64][64][2] on the GPU, labels int32 [N] on the
     GPU, per-sample cluster S/N, per-chunk records for evaluation)."""
     own = searcher is None
     searcher = searcher or Searcher()
-    gen = gen or Generator(seed=seed)
+    gen = gen or Generator(searcher.cfg, nout=searcher.nout, offsets_fn=offsets_fn, seed=seed)
     xs, ys, snrs, records = [], [], [], []
     for _ in range(n_chunks):
         x, inj = gen.chunk()
@@ -178,36 +204,53 @@ def predict(model, X, batch=256):
     return prob[:n].cpu().numpy()
 
 
-def evaluate(snr, prob, records, thresh=8.0, min_inj_snr=8.0, tsamp=CHUNK["tsamp"], nout=None):
-    """Recall of injected pulses with S/N >= min_inj_snr and false positives
-    (clusters matching no injection), for the plain threshold and for the
-    network at the probability cut that gives equal recall (within 1 %)."""
+def equal_recall(snr, prob, match, inj_snr, hours, thresh=8.0, min_inj_snr=8.0, low=6.0):
+    """The plain threshold against threshold-then-network at equal recall.
+
+    snr, prob: per cluster representative; match: index of the injection it
+    matches (Sec. 4.2 rule) or -1; inj_snr: per injection.  Recall = the
+    fraction of injections with S/N >= min_inj_snr matched by a selected
+    cluster; false positives = selected clusters matching none.  The network
+    keeps clusters with S/N >= low and P(pulse) >= p, p the largest cut whose
+    recall is within 1 % of the plain threshold's."""
+    snr, prob, match = np.asarray(snr), np.asarray(prob), np.asarray(match, dtype=np.int64)
+    inj_snr = np.asarray(inj_snr, dtype=np.float64)
+    want = inj_snr >= min_inj_snr
+    tot = int(want.sum())
+
     def score(sel):
-        hit, tot, fp = 0, 0, 0
-        for r in records:
-            idx = np.arange(r["start"], r["start"] + r["n"])
-            chosen = idx[sel[idx]] if r["n"] else idx
-            m = r["match"][chosen - r["start"]] if r["n"] else np.zeros(0, dtype=np.int64)
-            fp += int((m < 0).sum())
-            found = set(int(j) for j in m if j >= 0)
-            for j, (_, _, _, s) in enumerate(r["inj"]):
-                if s >= min_inj_snr:
-                    tot += 1
-                    hit += j in found
-        return hit / max(tot, 1), fp, tot
-    base_rec, base_fp, tot = score(snr >= thresh)
+        m = match[sel]
+        found = np.zeros(len(inj_snr), dtype=bool)
+        found[m[m >= 0]] = True
+        return float((found & want).sum()) / max(tot, 1), int((m < 0).sum())
+
+    base_rec, base_fp = score(snr >= thresh)
+    cand = snr >= low
     best = None
-    for p in np.unique(np.concatenate([[0.0], prob]))[::-1]:
-        rec, fp, _ = score((snr >= 6.0) & (prob >= p))
+    for p in np.unique(np.concatenate([[0.0], prob[cand]]))[::-1]:
+        rec, fp = score(cand & (prob >= p))
         if rec >= base_rec - 0.01:
             best = (float(p), rec, fp)
             break
     if best is None:
-        best = (0.0,) + score(snr >= 6.0)[:2]
-    span_s = len(records) * (nout or (CHUNK["nsamp"] - 11682)) * tsamp
+        best = (0.0,) + score(cand)
     return dict(injected=tot, threshold=thresh, recall_threshold=base_rec, fp_threshold=base_fp,
-                p_cut=best[0], recall_cnn=best[1], fp_cnn=best[2], hours=span_s / 3600.0,
-                fp_per_hour_threshold=base_fp / (span_s / 3600.0), fp_per_hour_cnn=best[2] / (span_s / 3600.0))
+                p_cut=best[0], recall_cnn=best[1], fp_cnn=best[2], hours=hours,
+                fp_per_hour_threshold=base_fp / hours, fp_per_hour_cnn=best[2] / hours)
+
+
+def evaluate(snr, prob, records, thresh=8.0, min_inj_snr=8.0, tsamp=CHUNK["tsamp"], nout=None):
+    """equal_recall() over build_dataset()'s per-chunk records."""
+    match, inj_snr = [], []
+    for r in records:
+        idx = np.arange(r["start"], r["start"] + r["n"])
+        off = len(inj_snr)
+        m = r["match"] if r["n"] else np.zeros(0, dtype=np.int64)
+        match.append(np.where(m >= 0, m + off, -1) if len(idx) else np.zeros(0, dtype=np.int64))
+        inj_snr.extend(s for (_, _, _, s) in r["inj"])
+    match = np.concatenate(match) if match else np.zeros(0, dtype=np.int64)
+    span_s = len(records) * (nout or (CHUNK["nsamp"] - 11682)) * tsamp
+    return equal_recall(snr, prob, match, inj_snr, span_s / 3600.0, thresh=thresh, min_inj_snr=min_inj_snr)
 
 
 def main(argv=None):

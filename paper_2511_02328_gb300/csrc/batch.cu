@@ -3,13 +3,20 @@
 //
 // af_batch_build makes one plan per beam, allocates every beam's plane, S/N
 // and candidate buffers (within an HBM budget), then autotunes over the
-// strategies: one persistent channel-tile launch over all (beam, DM block,
-// time tile) items for each compiled tile shape (DM rows per block x outputs
-// per lane), and the beams one after another, each on its single-plan path
-// (group rows, pairs.cu, sharing one row buffer, where the plan uses them);
-// each is timed on the batch itself, the fastest is kept and
-// cached in a JSON file (AFGB_AUTOTUNE_CACHE) keyed by the GPU name and the
-// beams' shapes.  af_batch_run replays a graph of: the dedispersion (with its
+// strategies:
+//   - one persistent channel-tile launch over all (beam, DM block, time tile)
+//     items, for each compiled tile shape (DM rows per block x outputs per
+//     lane);
+//   - the beams one after another, each on its single-plan path (group rows,
+//     pairs.cu, sharing one row buffer, where the plan uses them);
+//   - persistent group rows: the time axis in waves of W tiles; per wave the
+//     rows of every beam's block are built (one stage-1 launch per beam, all
+//     beams' rows side by side in one buffer), then ONE persistent stage-2
+//     launch takes (beam, DM block, tile) items of all beams from an atomic
+//     counter; tuned over W.
+// Each candidate is timed on the batch itself, the fastest is kept and cached
+// in a JSON file (AFGB_AUTOTUNE_CACHE) keyed by the GPU name and the beams'
+// shapes.  af_batch_run replays a graph of: the dedispersion (with its
 // counter and row-sum resets), then per beam the boxcar S/N and the candidate
 // compaction.
 #include <cuda_runtime.h>
@@ -19,6 +26,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <new>
 #include <numeric>
 #include <string>
@@ -62,7 +70,14 @@ const Shape kShapes[] = {
 };
 constexpr int kNShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 constexpr int kPairs = kNShapes;       // strategy index of beam after beam (group rows where they apply)
+constexpr int kPersist = kNShapes + 1; // strategy index of persistent group rows
 constexpr size_t kPairsMax = (size_t)16 << 30;  // largest shared row buffer
+constexpr size_t kPersistMax = (size_t)64 << 30;  // largest row buffer of the persistent group rows
+// tiles-per-wave choices of the persistent group rows: 0 = the most the row
+// buffer holds, -k = that divided by 2^k.  (The ring depth is not a choice:
+// the plans' consumer tables hold shared-memory offsets of the ring stages
+// they were built for, so the launch uses the plans' own depth.)
+constexpr int kPersistChoices[] = {0, -1, -2};
 
 struct Beam {
     af_plan_t plan = nullptr;
@@ -98,6 +113,20 @@ struct af_batch_s {
     size_t smem = 0;
     uint16_t* d_rows = nullptr;          // row buffer shared by the beams' plans (group-row strategy)
     size_t rows_bytes = 0;
+    // persistent group rows
+    int pp_ns = 0, pp_tiles = 0;         // ring depth, tiles per wave
+    std::vector<int> pp_beam;            // per beam: 1 if on group rows
+    std::vector<std::vector<int>> pp_wave_beams;  // beams with a block in each wave
+    std::vector<int> pp_wave_job0;       // first job of each wave
+    std::vector<long long> pp_wave_total;
+    af_pair_args* d_pjobs = nullptr;
+    long long* d_pfirst = nullptr;       // per wave: its jobs' item prefix (njobs + 1 entries), concatenated
+    unsigned long long* d_pcounters = nullptr;
+    size_t pp_smem = 0;
+    uint16_t* d_prows = nullptr;
+    size_t prows_bytes = 0;
+    // every candidate the autotuner timed: {kind (0 tile shape, 1 beam after beam, 2 persistent rows), p1, p2, ms}
+    std::vector<std::array<float, 4>> tuning;
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
 };
@@ -122,6 +151,10 @@ static void free_batch(af_batch_t b)
     cudaFree(b->d_counter);
     cudaFree(b->d_err);
     cudaFree(b->d_rows);
+    cudaFree(b->d_prows);
+    cudaFree(b->d_pjobs);
+    cudaFree(b->d_pfirst);
+    cudaFree(b->d_pcounters);
     delete b;
 }
 
@@ -158,6 +191,130 @@ static int setup_pairs(af_batch_t b)
             if (int rc = af_pairs_attach(b->beams[i].plan, b->d_rows, b->rows_bytes, b->beams[i].nout))
                 return rc == AF_ENOBUFS ? af_set_error(AF_EINVAL, "batch: shared row buffer too small") : rc;
     b->shape = kPairs;
+    return AF_OK;
+}
+
+// Persistent group rows with `tiles` output tiles per wave (0: the most that
+// kPersistMax of rows holds; -k: that divided by 2^k).  The launch runs a
+// ring of the depth the plans' tables were built for; beams whose plans do
+// not gain from group rows, or were built for another depth, run on their
+// single-plan path before the waves.  AF_EINVAL: this choice does not apply
+// (no such beam, or the rows of one wave do not fit).
+static int setup_persist(af_batch_t b, int tiles)
+{
+    const int64_t tte = af_pair_tile_outputs();
+    std::vector<int> use;
+    int64_t max_tiles = 0;
+    int ns = 0;
+    for (size_t i = 0; i < b->beams.size(); i++) {
+        Beam& x = b->beams[i];
+        if (!x.plan->pairs.ok) continue;
+        int64_t L = 0;
+        if (int rc = af_pairs_pick(x.plan, x.nout, true, kPairsMax, &L)) return rc;
+        if (L <= 0) continue;
+        if (ns == 0) ns = af_pairs_ring(x.plan);
+        if (af_pairs_ring(x.plan) != ns) continue;  // tables for another ring depth
+        use.push_back((int)i);
+        max_tiles = std::max(max_tiles, (x.nout + tte - 1) / tte);
+    }
+    if (use.empty() || ns < 2) return af_set_error(AF_EINVAL, "batch: no beam for persistent group rows");
+    auto wave_bytes = [&](int64_t t, std::vector<size_t>* sizes) {
+        size_t tot = 0;
+        for (int i : use) {
+            const Beam& x = b->beams[i];
+            const size_t by = (af_pairs_bytes(x.plan, std::min(x.nout, t * tte)) + 255) & ~(size_t)255;
+            if (sizes) sizes->push_back(by);
+            tot += by;
+        }
+        return tot;
+    };
+    int64_t t = std::min<int64_t>(max_tiles, 8);
+    if (wave_bytes(t, nullptr) > kPersistMax) return af_set_error(AF_EINVAL, "batch: one wave of rows is too large");
+    if (tiles > 0) {
+        t = std::max<int64_t>(t, std::min<int64_t>(tiles, max_tiles));
+    } else {
+        int64_t lo = t, hi = max_tiles;  // the most tiles whose rows fit
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) / 2;
+            if (wave_bytes(mid, nullptr) <= kPersistMax) lo = mid;
+            else hi = mid - 1;
+        }
+        t = std::max<int64_t>(t, lo >> (tiles < 0 ? -tiles : 0));
+    }
+    std::vector<size_t> sizes;
+    const size_t need = wave_bytes(t, &sizes);
+    if (need > b->prows_bytes) {
+        if (b->d_prows) {
+            if (int rc = af_cuda_check(cudaDeviceSynchronize(), "batch")) return rc;
+            cudaFree(b->d_prows);
+        }
+        b->d_prows = nullptr;
+        b->prows_bytes = 0;
+        if (cudaMalloc(&b->d_prows, need) != cudaSuccess) {
+            cudaGetLastError();
+            b->d_prows = nullptr;
+            return af_set_error(AF_EINVAL, "batch: no room for the persistent row buffer");
+        }
+        b->prows_bytes = need;
+    }
+    b->pp_beam.assign(b->beams.size(), 0);
+    size_t off = 0;
+    int64_t nwaves = 0;
+    for (size_t k = 0; k < use.size(); k++) {
+        Beam& x = b->beams[use[k]];
+        if (int rc = af_pairs_attach(x.plan, b->d_prows + off / 2, sizes[k], x.nout))
+            return rc == AF_ENOBUFS ? af_set_error(AF_EINVAL, "batch: persistent rows do not fit") : rc;
+        off += sizes[k];
+        const int64_t L = x.plan->pairs.lay[0].L;
+        if (L <= 0) continue;  // the cost model keeps this beam on the channel tile kernel
+        b->pp_beam[use[k]] = 1;
+        nwaves = std::max(nwaves, (x.nout + L - 1) / L);
+    }
+    if (nwaves == 0) return af_set_error(AF_EINVAL, "batch: no beam on persistent group rows");
+    std::vector<af_pair_args> jobs;
+    std::vector<long long> first;
+    b->pp_wave_beams.assign(nwaves, {});
+    b->pp_wave_job0.assign(nwaves + 1, 0);
+    b->pp_wave_total.assign(nwaves, 0);
+    size_t smem = 0;
+    for (int64_t w = 0; w < nwaves; w++) {
+        b->pp_wave_job0[w] = (int)jobs.size();
+        first.push_back(0);
+        for (int k : b->order) {
+            if (!b->pp_beam[k]) continue;
+            Beam& x = b->beams[k];
+            const int64_t L = x.plan->pairs.lay[0].L, T0 = w * L;
+            if (T0 >= x.nout) continue;
+            af_pair_args a;
+            long long items = 0;
+            if (int rc = af_pairs_block_args(x.plan, x.nout, 0, T0, x.d_plane, x.d_stats, &a, &items)) return rc;
+            jobs.push_back(a);
+            first.push_back(first.back() + items);
+            b->pp_wave_beams[w].push_back(k);
+            smem = std::max(smem, af_pairs_stage2_smem(x.plan, ns));
+        }
+        b->pp_wave_total[w] = first.back();
+    }
+    b->pp_wave_job0[nwaves] = (int)jobs.size();
+    cudaFree(b->d_pjobs);
+    cudaFree(b->d_pfirst);
+    cudaFree(b->d_pcounters);
+    b->d_pjobs = nullptr;
+    b->d_pfirst = nullptr;
+    b->d_pcounters = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&b->d_pjobs, jobs.size() * sizeof(af_pair_args))) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_pjobs, jobs.data(), jobs.size() * sizeof(af_pair_args), cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaMalloc(&b->d_pfirst, first.size() * sizeof(long long))) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_pfirst, first.data(), first.size() * sizeof(long long), cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaMalloc(&b->d_pcounters, (size_t)nwaves * sizeof(unsigned long long))) != cudaSuccess)
+        return af_cuda_check(e, "batch: persistent job upload");
+    b->pp_ns = ns;
+    b->pp_tiles = (int)t;
+    b->pp_smem = smem;
+    b->shape = kPersist;
     return AF_OK;
 }
 
@@ -218,6 +375,30 @@ static int setup_shape(af_batch_t b, int si)
 
 static int enqueue_dedisp(af_batch_t b, cudaStream_t s)
 {
+    if (b->shape == kPersist) {
+        const int nwaves = (int)b->pp_wave_beams.size();
+        AF_CUDA(cudaMemsetAsync(b->d_pcounters, 0, (size_t)nwaves * sizeof(unsigned long long), s));
+        for (int k : b->order) {
+            Beam& x = b->beams[k];
+            if (!b->pp_beam[k]) {  // its single-plan path
+                if (int rc = af_launch_dedisperse(x.plan, x.d_in, x.nsamp, x.nout, x.d_plane, x.d_stats, s)) return rc;
+            } else {
+                AF_CUDA(cudaMemsetAsync(x.d_stats, 0, (size_t)x.plan->ndm * sizeof(af_rowstats_t), s));
+            }
+        }
+        for (int w = 0; w < nwaves; w++) {
+            for (int k : b->pp_wave_beams[w]) {
+                Beam& x = b->beams[k];
+                if (int rc = af_launch_pairs_rows(x.plan, x.d_in, x.nsamp, 0, (int64_t)w * x.plan->pairs.lay[0].L, s))
+                    return rc;
+            }
+            const int j0 = b->pp_wave_job0[w], nj = b->pp_wave_job0[w + 1] - j0;
+            if (int rc = af_launch_pairs_persistent(b->pp_ns, b->pp_smem, b->grid, b->d_pjobs + j0, b->d_pfirst + j0 + w,
+                                                    nj, b->pp_wave_total[w], b->d_pcounters + w, s))
+                return rc;
+        }
+        return AF_OK;
+    }
     if (b->shape == kPairs) {
         for (int k : b->order) {
             Beam& x = b->beams[k];
@@ -310,6 +491,36 @@ static void cache_store(const std::string& path, const std::string& key, int nw,
     }
 }
 
+// One candidate strategy: kind 0 = persistent channel tiles (shape p1),
+// 1 = beam after beam, 2 = persistent group rows (ring p1, tiles per wave p2).
+struct Cand {
+    int kind, p1, p2;
+};
+
+static int setup_cand(af_batch_t b, const Cand& c)
+{
+    return c.kind == 0 ? setup_shape(b, c.p1) : c.kind == 1 ? setup_pairs(b) : setup_persist(b, c.p2);
+}
+
+// Back to no group-row layout on any plan, and free the row buffers the
+// candidate `keep` (kind) does not use.
+static int release_rows(af_batch_t b, int keep)
+{
+    if (int r = af_cuda_check(cudaDeviceSynchronize(), "batch")) return r;
+    for (Beam& x : b->beams) x.plan->pairs.lay[0].L = x.plan->pairs.lay[1].L = 0;
+    if (keep != 1 && b->d_rows) {
+        cudaFree(b->d_rows);
+        b->d_rows = nullptr;
+        b->rows_bytes = 0;
+    }
+    if (keep != 2 && b->d_prows) {
+        cudaFree(b->d_prows);
+        b->d_prows = nullptr;
+        b->prows_bytes = 0;
+    }
+    return AF_OK;
+}
+
 static int autotune(af_batch_t b)
 {
     const char* path = getenv("AFGB_AUTOTUNE_CACHE");
@@ -321,38 +532,47 @@ static int autotune(af_batch_t b)
     if (path) {
         int nw = 0, m = 0;
         if (cache_lookup(path, key, &nw, &m)) {
-            if (m == 0) {
-                if (int rc = setup_pairs(b)) return rc;
+            // m > 0: tile shape (nw, m); m == 0: beam after beam; m < 0: persistent rows (ring nw, -m tiles)
+            Cand c{-1, 0, 0};
+            if (m == 0) c = Cand{1, 0, 0};
+            else if (m < 0) c = Cand{2, nw, -m};  // the tiles per wave it resolved to
+            else
+                for (int si = 0; si < kNShapes; si++)
+                    if (kShapes[si].nw == nw && kShapes[si].m == m) c = Cand{0, si, 0};
+            if (c.kind >= 0) {
+                if (int rc = setup_cand(b, c)) return rc;
                 b->from_cache = true;
                 return AF_OK;
             }
-            for (int si = 0; si < kNShapes; si++)
-                if (kShapes[si].nw == nw && kShapes[si].m == m) {
-                    if (int rc = setup_shape(b, si)) return rc;
-                    b->from_cache = true;
-                    return AF_OK;
-                }
         }
     }
+    // AFGB_BATCH_STRATEGY=tile|pairs|persistent restricts the candidates
+    const char* only = getenv("AFGB_BATCH_STRATEGY");
+    std::vector<Cand> cands;
+    if (!only || !strcmp(only, "tile"))
+        for (int si = 0; si < kNShapes; si++) cands.push_back(Cand{0, si, 0});
+    if (!only || !strcmp(only, "pairs")) cands.push_back(Cand{1, 0, 0});
+    if (!only || !strcmp(only, "persistent"))
+        for (int tc : kPersistChoices) cands.push_back(Cand{2, 0, tc});
     cudaStream_t s;
     AF_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int best = -1;
+    Cand best_c{0, 0, 0};
     float best_ms = 0.0f;
     int rc = AF_OK;
-    // AFGB_BATCH_STRATEGY=tile|pairs restricts the candidates
-    const char* only = getenv("AFGB_BATCH_STRATEGY");
-    for (int si = 0; si <= kNShapes && rc == AF_OK; si++) {
-        if (only && !strcmp(only, "tile") && si == kPairs) continue;
-        if (only && !strcmp(only, "pairs") && si != kPairs) continue;
-        int r = si == kPairs ? setup_pairs(b) : setup_shape(b, si);
-        if (r == AF_EINVAL) continue;  // this shape's window does not fit: skip it
+    b->tuning.clear();
+    for (size_t ci = 0; ci < cands.size() && rc == AF_OK; ci++) {
+        Cand c = cands[ci];
+        int r = setup_cand(b, c);
+        if (r == AF_EINVAL) continue;  // this candidate does not apply to these beams: skip it
         if (r) {
             rc = r;
             break;
         }
+        if (c.kind == 2) c.p1 = b->pp_ns, c.p2 = b->pp_tiles;  // what it resolved to
         float ms = 0.0f;
         for (int rep = 0; rep < 3 && rc == AF_OK; rep++) {
             cudaEventRecord(e0, s);
@@ -364,8 +584,12 @@ static int autotune(af_batch_t b)
             cudaEventElapsedTime(&t, e0, e1);
             if (rep > 0) ms += t / 2.0f;  // first run warms up
         }
-        if (rc == AF_OK && (best < 0 || ms < best_ms)) {
-            best = si;
+        if (rc != AF_OK) break;
+        b->tuning.push_back({(float)c.kind, (float)(c.kind == 0 ? kShapes[c.p1].nw : c.p1),
+                             (float)(c.kind == 0 ? kShapes[c.p1].m : c.p2), ms});
+        if (best < 0 || ms < best_ms) {
+            best = (int)ci;
+            best_c = c;
             best_ms = ms;
         }
     }
@@ -373,20 +597,15 @@ static int autotune(af_batch_t b)
     cudaEventDestroy(e1);
     cudaStreamDestroy(s);
     if (rc) return rc;
-    if (best < 0) return af_set_error(AF_EINVAL, "batch: no compiled tile shape fits these beams");
-    if (best != kPairs && b->d_rows) {
-        // the row buffer is not needed: detach nothing (the plans keep their
-        // layouts but never launch group rows in this batch), free it
-        if (int r = af_cuda_check(cudaDeviceSynchronize(), "batch")) return r;
-        for (Beam& x : b->beams) x.plan->pairs.lay[0].L = x.plan->pairs.lay[1].L = 0;
-        cudaFree(b->d_rows);
-        b->d_rows = nullptr;
-        b->rows_bytes = 0;
-    }
-    if (int r = best == kPairs ? setup_pairs(b) : setup_shape(b, best)) return r;
+    if (best < 0) return af_set_error(AF_EINVAL, "batch: no strategy fits these beams");
+    if (int r = release_rows(b, best_c.kind)) return r;
+    if (int r = setup_cand(b, best_c)) return r;
     b->tuned_ms = best_ms;
-    if (path) cache_store(path, key, best == kPairs ? 15 : kShapes[best].nw, best == kPairs ? 0 : kShapes[best].m,
-                          best_ms);
+    if (path) {
+        const int nw = best_c.kind == 0 ? kShapes[best_c.p1].nw : best_c.kind == 1 ? 15 : best_c.p1;
+        const int m = best_c.kind == 0 ? kShapes[best_c.p1].m : best_c.kind == 1 ? 0 : -best_c.p2;
+        cache_store(path, key, nw, m, best_ms);
+    }
     return AF_OK;
 }
 
@@ -500,7 +719,7 @@ try {
         cudaMemset(b->d_err, 0, sizeof(int));
         return af_set_error(AF_ETIMEOUT, "af_batch: a kernel's bounded wait for an asynchronous copy ran out");
     }
-    if (b->shape == kPairs)
+    if (b->shape == kPairs || b->shape == kPersist)
         if (int rc = af_plan_check(x.plan)) return rc;  // the pair kernels flag on the beam's plan
     int32_t n = std::min(std::min(total, cap), x.cap);
     if (n > 0) {
@@ -533,13 +752,29 @@ try {
 extern "C" int af_batch_shape(af_batch_t b, int* nw, int* m, float* tuned_ms, int* from_cache)
 try {
     if (!b) return af_set_error(AF_EINVAL, "af_batch_shape: NULL batch");
-    if (nw) *nw = b->shape == kPairs ? 15 : kShapes[b->shape].nw;
-    if (m) *m = b->shape == kPairs ? 0 : kShapes[b->shape].m;
+    // persistent channel tiles: the shape; beam after beam: (15, 0); persistent
+    // group rows: (ring depth, -tiles per wave)
+    if (nw) *nw = b->shape == kPairs ? 15 : b->shape == kPersist ? b->pp_ns : kShapes[b->shape].nw;
+    if (m) *m = b->shape == kPairs ? 0 : b->shape == kPersist ? -b->pp_tiles : kShapes[b->shape].m;
     if (tuned_ms) *tuned_ms = b->tuned_ms;
     if (from_cache) *from_cache = b->from_cache ? 1 : 0;
     return AF_OK;
 } catch (...) {
     return af_host_exception("af_batch_shape");
+}
+
+extern "C" int af_batch_tuning(af_batch_t b, int i, int* kind, int* p1, int* p2, float* ms)
+try {
+    if (!b || i < 0 || i >= (int)b->tuning.size() || !kind || !p1 || !p2 || !ms)
+        return af_set_error(AF_EINVAL, "af_batch_tuning: bad arguments or no candidate %d", i);
+    const auto& t = b->tuning[i];
+    *kind = (int)t[0];
+    *p1 = (int)t[1];
+    *p2 = (int)t[2];
+    *ms = t[3];
+    return AF_OK;
+} catch (...) {
+    return af_host_exception("af_batch_tuning");
 }
 
 extern "C" int af_batch_destroy(af_batch_t b)

@@ -79,6 +79,26 @@ struct af_sb_device {
 };
 
 // ---------------------------------------------------------------- group rows
+// Arguments of one group-row stage-2 launch (a plan's time block).
+struct af_pair_args {
+    const uint16_t* PS;      // rows of the time block
+    const int2* chunks;      // per chunk: {row slots, first slot}
+    const int32_t* chkoff;   // [nblk + 1] first chunk of each block
+    const int* tabs;         // per chunk: NW x TABW ints, every consumer warp's table for its ring stage
+    const int2* srec;        // per slot: {window bytes, byte offset inside its stage}
+    const int64_t* soff;     // per slot: element offset of its window in PS for the block's first tile
+    const int32_t* perm;     // [ndm_pad] plane row, -1 = padding
+    int stage_bytes;         // bytes of one ring stage's windows
+    int flush;               // rows between folds: flush * 255 * G < 2^16
+    unsigned nblk;
+    int64_t T0;              // first output of the time block (a multiple of 8)
+    int64_t tend;            // outputs t < tend are written
+    int64_t nout;
+    int32_t* Y;
+    af_rowstats_t* stats;
+    int* err;
+};
+
 // Single-plan dedispersion through channel-group rows (pairs.cu): host tables
 // (built once per plan), device tables, and the row buffer of one time block.
 struct af_pair_tables {
@@ -127,6 +147,18 @@ int af_pairs_reserve(af_plan_t p, int64_t nout, bool search, bool allow_larger =
                      size_t max_bytes = SIZE_MAX);
 int af_pairs_pick(af_plan_t p, int64_t nout, bool allow_larger, size_t max_bytes, int64_t* L);
 size_t af_pairs_workspace(af_plan_t p, int64_t nout);  // row-buffer bytes a reservation would allocate
+// Stage 1 alone (the rows of time block T0 of layout `layout`), the stage-2
+// arguments of that block (and its item count: tiles x DM blocks), the
+// stage-2 shared memory of a ring of ns stages, the plan's ring depth, and
+// one persistent stage-2 launch over many plans' blocks (jobs in device
+// memory, first[j] = items before job j, first[njobs] = total).
+int af_launch_pairs_rows(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int layout, int64_t T0, cudaStream_t s);
+int af_pairs_block_args(af_plan_t p, int64_t nout, int layout, int64_t T0, int32_t* d_plane, af_rowstats_t* d_stats,
+                        af_pair_args* out, long long* items);
+size_t af_pairs_stage2_smem(af_plan_t p, int ns);
+int af_pairs_ring(af_plan_t p);
+int af_launch_pairs_persistent(int ns, size_t smem, int grid, const af_pair_args* d_jobs, const long long* d_first,
+                               int njobs, long long total, unsigned long long* d_counter, cudaStream_t s);
 int af_launch_pairs(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,
                     af_rowstats_t* d_stats, cudaStream_t s);
 // Stage 1 + stage 2 of the time block starting at T0 (a multiple of the

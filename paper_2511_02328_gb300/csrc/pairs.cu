@@ -65,24 +65,7 @@ constexpr int kMinTiles = 8;        // smallest useful time block, in tiles
 inline int64_t r8(int64_t x) { return (x + 7) & ~(int64_t)7; }
 inline int64_t r16(int64_t x) { return (x + 15) & ~(int64_t)15; }
 
-struct PairArgs {
-    const uint16_t* PS;      // rows of the time block
-    const int2* chunks;      // per chunk: {row slots, first slot}
-    const int32_t* chkoff;   // [nblk + 1] first chunk of each block
-    const int* tabs;         // per chunk: NW x TABW ints, every consumer warp's table for its ring stage
-    const int2* srec;        // per slot: {window bytes, byte offset inside its stage}
-    const int64_t* soff;     // per slot: element offset of its window in PS for the block's first tile
-    const int32_t* perm;     // [ndm_pad] plane row, -1 = padding
-    int stage_bytes;         // bytes of one ring stage's windows
-    int flush;               // rows between folds: flush * 255 * G < 2^16
-    unsigned nblk;
-    int64_t T0;              // first output of the time block (a multiple of 8)
-    int64_t tend;            // outputs t < tend are written
-    int64_t nout;
-    int32_t* Y;
-    af_rowstats_t* stats;
-    int* err;
-};
+typedef af_pair_args PairArgs;
 
 // ------------------------------------------------------------------ stage 1
 // Block = (group q of G channels, ET samples of the group's range); writes,
@@ -276,11 +259,10 @@ struct PairTile {
         }
     }
 
-    static __device__ __forceinline__ void run(const PairArgs& a, uint8_t* smem)
+    // DM block jb, outputs t0 .. t0 + TTE - 1 of the time block a.T0.
+    static __device__ __forceinline__ void run(const PairArgs& a, uint8_t* smem, unsigned jb, int64_t t0)
     {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const unsigned jb = blockIdx.x % a.nblk;
-        const int64_t t0 = a.T0 + (int64_t)(blockIdx.x / a.nblk) * kPTTE;
         int* tab = (int*)(smem + (size_t)NS * a.stage_bytes);
         uint64_t* bars = (uint64_t*)(tab + NS * NW * kPTABW);
         const uint32_t full0 = afptx::smem_addr(bars), empty0 = full0 + 8 * NS;
@@ -428,7 +410,41 @@ template <int NW, int NS>
 __global__ void __launch_bounds__((NW + 1) * 32, 1) k_pair_tile(const PairArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem[];
-    PairTile<NW, NS>::run(a, smem);
+    PairTile<NW, NS>::run(a, smem, blockIdx.x % a.nblk, a.T0 + (int64_t)(blockIdx.x / a.nblk) * kPTTE);
+}
+
+// Persistent form over many plans' time blocks (a batch of beams): items
+// (job, DM block, tile) in job order, DM blocks fastest, handed out by an
+// atomic counter; every job carries its own tables and ring-stage size (the
+// shared memory is sized for the largest).  The ring barriers are
+// invalidated and initialised again between items.
+template <int NW, int NS>
+__global__ void __launch_bounds__((NW + 1) * 32, 1)
+k_pair_persistent(const PairArgs* __restrict__ jobs, const long long* __restrict__ first, int njobs,
+                  long long total, unsigned long long* counter)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ long long item_s;
+    for (;;) {
+        if (threadIdx.x == 0) item_s = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long item = item_s;
+        if (item >= total) return;
+        int lo = 0, hi = njobs - 1;  // the job holding the item: first[j] <= item < first[j + 1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (__ldg(first + mid) <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const PairArgs& a = jobs[lo];
+        const long long local = item - __ldg(first + lo);
+        PairTile<NW, NS>::run(a, smem, (unsigned)(local % a.nblk), a.T0 + (local / a.nblk) * kPTTE);
+        __syncthreads();  // every warp is done with the ring before its barriers are reset
+        if (threadIdx.x == 0) {
+            const uint32_t bar0 = afptx::smem_addr(smem + (size_t)NS * a.stage_bytes + (size_t)NS * NW * kPTABW * 4);
+            for (int s = 0; s < 2 * NS; s++) afptx::mbar_inval(bar0 + 8 * s);
+        }
+    }
 }
 
 size_t tables_smem(int ns) { return (size_t)ns * kPNW * kPTABW * 4 + 2 * (size_t)ns * 8; }
@@ -587,7 +603,8 @@ static int build_groups(af_plan_t p, int G, af_pair_tables* T)
     int NS = 3;
     if (const char* e = getenv("AFGB_PAIR_STAGES")) NS = std::min(4, std::max(2, atoi(e)));
     // one stage: up to kPSL windows back to back; the widest window must fit
-    const int stage_bytes = (int)(((size_t)optin - tables_smem(NS)) / NS) & ~15;
+    // (16 bytes stay free for the static shared memory of the persistent form)
+    const int stage_bytes = (int)(((size_t)optin - tables_smem(NS) - 16) / NS) & ~15;
     if (2 * rwe > stage_bytes) return AF_OK;
     // chunks of whole groups, at most kPSL windows and stage_bytes each, per block; their tables
     struct Ent {
@@ -959,24 +976,20 @@ int af_pairs_attach(af_plan_t p, uint16_t* buf, size_t bytes, int64_t nout)
     return pairs_layout(p, 0, lo * kPTTE);
 }
 
-int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,
-                          af_rowstats_t* d_stats, cudaStream_t s, int layout, int64_t T0, cudaEvent_t* mid)
+int af_launch_pairs_rows(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int layout, int64_t T0, cudaStream_t s)
 {
     af_pair_tables* T = &p->pairs;
     const af_pair_tables::Layout& ly = T->lay[layout];
     const int64_t L = ly.L;
     if (L <= 0 || L % kPTTE || T0 % L) return af_set_error(AF_EINVAL, "pairs: time block not laid out");
-    const size_t s2 = (size_t)T->shape * T->stage_bytes + tables_smem(T->shape), s1 = rows_smem(T->maxdr, T->G);
+    const size_t s1 = rows_smem(T->maxdr, T->G);
     const void* k1 = T->G == 4   ? (const void*)k_group_rows<4>
                      : T->G == 3 ? (const void*)k_group_rows<3>
                                  : (const void*)k_group_rows<2>;
-    if (int rc = af_ensure_smem(tile_kernel(T->shape), s2)) return rc;
     if (int rc = af_ensure_smem(k1, s1)) return rc;
     const int etiles = (int)((ly.maxlen + kET - 1) / kET);
     const unsigned long long g1 = (unsigned long long)T->np * etiles;
-    const int64_t tiles = (std::min(L, nout - T0) + kPTTE - 1) / kPTTE;
-    const unsigned long long g2 = (unsigned long long)tiles * (unsigned)T->tt.nblk;
-    if (g1 > 0x7fffffffULL || g2 > 0x7fffffffULL) return af_set_error(AF_EINVAL, "pairs: problem too large for one grid");
+    if (g1 > 0x7fffffffULL) return af_set_error(AF_EINVAL, "pairs: problem too large for one grid");
     if (T->G == 4)
         k_group_rows<4><<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, ly.d_pinfo, ly.d_gmax, T->d_gdr, T->d_rdelta,
                                                       ly.d_rinfo, ly.d_rowoff, T0, etiles, rows_wstride(T->maxdr),
@@ -989,9 +1002,17 @@ int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64
         k_group_rows<2><<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, ly.d_pinfo, ly.d_gmax, T->d_gdr, T->d_rdelta,
                                                       ly.d_rinfo, ly.d_rowoff, T0, etiles, rows_wstride(T->maxdr),
                                                       T->d_ps);
-    if (int rc = af_cuda_check(cudaGetLastError(), "group rows launch")) return rc;
-    if (mid) AF_CUDA(cudaEventRecord(*mid, s));
-    PairArgs a;
+    return af_cuda_check(cudaGetLastError(), "group rows launch");
+}
+
+int af_pairs_block_args(af_plan_t p, int64_t nout, int layout, int64_t T0, int32_t* d_plane, af_rowstats_t* d_stats,
+                        af_pair_args* out, long long* items)
+{
+    af_pair_tables* T = &p->pairs;
+    const af_pair_tables::Layout& ly = T->lay[layout];
+    const int64_t L = ly.L;
+    if (L <= 0 || L % kPTTE || T0 % L || T0 >= nout) return af_set_error(AF_EINVAL, "pairs: time block not laid out");
+    af_pair_args& a = *out;
     a.PS = T->d_ps;
     a.chunks = T->d_chunks;
     a.chkoff = T->d_chkoff;
@@ -1008,7 +1029,44 @@ int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64
     a.Y = d_plane;
     a.stats = d_stats;
     a.err = p->d_err;
-    const dim3 grid2((unsigned)g2), blk2((kPNW + 1) * 32);
+    *items = (long long)((std::min(L, nout - T0) + kPTTE - 1) / kPTTE) * (long long)T->tt.nblk;
+    return AF_OK;
+}
+
+size_t af_pairs_stage2_smem(af_plan_t p, int ns) { return (size_t)ns * p->pairs.stage_bytes + tables_smem(ns); }
+
+int af_launch_pairs_persistent(int ns, size_t smem, int grid, const af_pair_args* d_jobs, const long long* d_first,
+                               int njobs, long long total, unsigned long long* d_counter, cudaStream_t s)
+{
+    const void* fn = ns == 4   ? (const void*)k_pair_persistent<kPNW, 4>
+                     : ns == 3 ? (const void*)k_pair_persistent<kPNW, 3>
+                               : (const void*)k_pair_persistent<kPNW, 2>;
+    if (int rc = af_ensure_smem(fn, smem)) return rc;
+    const dim3 blk((kPNW + 1) * 32);
+    if (ns == 4)
+        k_pair_persistent<kPNW, 4><<<grid, blk, smem, s>>>(d_jobs, d_first, njobs, total, d_counter);
+    else if (ns == 3)
+        k_pair_persistent<kPNW, 3><<<grid, blk, smem, s>>>(d_jobs, d_first, njobs, total, d_counter);
+    else
+        k_pair_persistent<kPNW, 2><<<grid, blk, smem, s>>>(d_jobs, d_first, njobs, total, d_counter);
+    return af_cuda_check(cudaGetLastError(), "persistent pair tile launch");
+}
+
+int af_pairs_ring(af_plan_t p) { return p->pairs.shape; }
+
+int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,
+                          af_rowstats_t* d_stats, cudaStream_t s, int layout, int64_t T0, cudaEvent_t* mid)
+{
+    af_pair_tables* T = &p->pairs;
+    if (int rc = af_launch_pairs_rows(p, d_in, nsamp, layout, T0, s)) return rc;
+    if (mid) AF_CUDA(cudaEventRecord(*mid, s));
+    PairArgs a;
+    long long items = 0;
+    if (int rc = af_pairs_block_args(p, nout, layout, T0, d_plane, d_stats, &a, &items)) return rc;
+    const size_t s2 = af_pairs_stage2_smem(p, T->shape);
+    if (int rc = af_ensure_smem(tile_kernel(T->shape), s2)) return rc;
+    if ((unsigned long long)items > 0x7fffffffULL) return af_set_error(AF_EINVAL, "pairs: problem too large for one grid");
+    const dim3 grid2((unsigned)items), blk2((kPNW + 1) * 32);
     if (T->shape == 4)
         k_pair_tile<kPNW, 4><<<grid2, blk2, s2, s>>>(a);
     else if (T->shape == 3)

@@ -71,23 +71,31 @@ def _check_against_oracle(batch, xs):
         assert float(err.max()) <= TOL, (i, float(err.max()))
 
 
-@pytest.mark.parametrize("strategy", ["auto", "tile", "pairs"])
+@pytest.mark.parametrize("strategy", ["auto", "tile", "pairs", "persistent"])
 def test_batch_matches_oracle_and_single_beam(strategy, monkeypatch):
     """Every dedispersion strategy of the batch (the autotuner's pick, the
-    persistent tile kernel, group rows beam after beam) gives each beam's
-    oracle plane and S/N and the single-beam host search's candidates."""
+    persistent tile kernel, group rows beam after beam, persistent group rows
+    over all beams in waves) gives each beam's oracle plane and S/N and the
+    single-beam host search's candidates."""
     from paper_2511_02328_gb300 import _lib
     from paper_2511_02328_gb300.search import Plan
     if strategy != "auto":
         monkeypatch.setenv("AFGB_BATCH_STRATEGY", strategy)
-    if strategy == "pairs":
+    if strategy in ("pairs", "persistent"):
         monkeypatch.setenv("AFGB_DEDISP_KERNEL", "pairs")   # every beam that can, on group rows
     xs = _make(1)
     xs_dev = [torch.from_numpy(x).cuda() for x in xs]
     batch = _build(xs_dev)
     nw, m, ms, cached = _lib.af_batch_shape(batch)
-    assert (nw, m) in {"auto": [(11, 8), (7, 8), (15, 6), (15, 0)], "tile": [(11, 8), (7, 8), (15, 6)],
-                       "pairs": [(15, 0)]}[strategy]
+    if strategy == "persistent" or (strategy == "auto" and m < 0):
+        assert nw in (2, 3, 4) and m < 0           # ring depth, -(tiles per wave)
+    else:
+        assert (nw, m) in {"auto": [(11, 8), (7, 8), (15, 6), (15, 0)], "tile": [(11, 8), (7, 8), (15, 6)],
+                           "pairs": [(15, 0)]}[strategy]
+    tuning = _lib.af_batch_tuning(batch)
+    assert len(tuning) >= 1 and all(t["ms"] > 0 for t in tuning)
+    if strategy == "auto":                          # every kind of strategy was timed
+        assert {t["kind"] for t in tuning} == {0, 1, 2}
     _lib.af_batch_run(batch, torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     _check_against_oracle(batch, xs)

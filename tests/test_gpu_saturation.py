@@ -205,13 +205,14 @@ BATCH_BEAMS = [
 ]
 
 
-@pytest.mark.parametrize("strategy", ["tile", "pairs"])
+@pytest.mark.parametrize("strategy", ["tile", "pairs", "persistent"])
 def test_batch_strategies_saturated(strategy, monkeypatch):
-    """The batch's persistent channel-tile kernel and its group-row strategy on
-    saturated and mixed beams: every beam's plane is the oracle's."""
+    """The batch's persistent channel-tile kernel, its beam-after-beam group
+    rows and its persistent group rows on saturated and mixed beams: every
+    beam's plane is the oracle's."""
     from paper_2511_02328_gb300 import _lib
     from paper_2511_02328_gb300.search import device_view
-    _env(monkeypatch, "pairs" if strategy == "pairs" else None)
+    _env(monkeypatch, "pairs" if strategy != "tile" else None)
     monkeypatch.setenv("AFGB_BATCH_STRATEGY", strategy)
     xs = [pattern(b[8], b[0], b[4], seed=i) for i, b in enumerate(BATCH_BEAMS)]
     xs_dev = [torch.from_numpy(x).cuda() for x in xs]
