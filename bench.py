@@ -1058,7 +1058,8 @@ def main():
                        "l2": "inputs larger than L2 (1.07 GB input, 0.86 GB plane per step)"},
             "roofline": rl,
             "cpu_baseline": cpu,
-            "e2e": {"value": aggregate_rate(world, work, e2e_s), "unit": UNIT, "ms": e2e_s * 1e3, "h2d_ms": h2d_ms,
+            "e2e": {"value": aggregate_rate(world, work, e2e_s), "unit": UNIT, "ms": e2e_s * 1e3,
+                    "ms_median": e2e_phases["call_ms"]["median"], "h2d_ms": h2d_ms,
                     "h2d_bytes_per_step": NCHAN * NSAMP, "d2h_bytes_per_step": 4 + 24 * min(nc, CAP)},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,

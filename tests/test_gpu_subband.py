@@ -17,6 +17,9 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
+C2_LIKE = dict(nchan=4096, f_lo=1000.0, f_hi=1500.0, tsamp=49.152e-6, nsamp=1 << 18)
+
+
 @pytest.fixture(scope="module", autouse=True)
 def _built():
     import __graft_entry__
@@ -208,3 +211,67 @@ def test_full_size_sampled_rows():
     S, Q = oracle.rowstats(Yref)
     assert np.array_equal(st[rows, 0], S) and np.array_equal(st[rows, 1], Q)
     p.close()
+
+
+@pytest.mark.slow
+def test_snr_loss_of_twenty_pulses_within_the_smearing_bound():
+    """The benchmark's subband setting (n0 = 8, 64 subbands of 64 channels,
+    1/f^2 centres) on the 4096-channel workload with its 20 injected pulses
+    (DM U(50, 1000), width log-U(0.2, 10) ms, S/N U(6, 30), placed by the
+    oracle's injector): every pulse the brute-force plane finds keeps the
+    fraction of its brute-force S/N that the smearing of Eq. (sb_smear) allows.
+    A pulse of W samples whose subband delays spread it over d more samples
+    (d = the largest 2 K |dDM| df_s / F_s^3 of its subbands, in samples, plus
+    two samples of rounding) keeps at least sqrt(W / (W + d)) of its matched-
+    filter S/N; the S/N measurements carry unit noise, allowed for as 3 /
+    S/N_brute.  Best S/N per pulse = the largest boxcar S/N within |dDM| < 20
+    and |dTOA| < 0.2 s (Sec. 4.2)."""
+    from paper_2511_02328_gb300 import _lib, synth
+    from paper_2511_02328_gb300.search import Plan
+    cfg = dict(C2_LIKE)
+    nchan, f_lo, f_hi, tsamp, nsamp = cfg["nchan"], cfg["f_lo"], cfg["f_hi"], cfg["tsamp"], cfg["nsamp"]
+    dms = np.arange(0.0, 1001.0, 1.0)
+    widths = [1, 2, 4, 8, 16, 32, 64, 128, 256]
+    pp = synth.pulse_params(20, 13012, (50.0, 1000.0), (0.2e-3, 10e-3), (6.0, 30.0),
+                            (0.5, (nsamp - 50000) * tsamp - 0.5), 0.45, tsamp)
+    pulses = [synth.Pulse(oracle.injection_offsets(nchan, f_lo, f_hi, tsamp, p["dm"], p["t0"]), p["width"],
+                          synth.pulse_amplitude(p["snr"], nchan, p["width"])) for p in pp]
+    x = torch.from_numpy(synth.filterbank(nchan, nsamp, seed=12012, pulses=pulses)).cuda()
+    n0, nsub = 8, 64
+    tab = oracle.subband_tables(nchan, f_lo, f_hi, tsamp, dms, n0, nsub, oracle.FS_INVSQ)
+    best = {}
+    for name, plan in (("brute", Plan(nchan, f_lo, f_hi, tsamp, dms)),
+                       ("subband", Plan(nchan, f_lo, f_hi, tsamp, dms,
+                                        subband=dict(n0=n0, nsub=nsub, fs_mode=_lib.AF_FS_INVSQ, block_len=nsamp)))):
+        plane = plan.dedisperse(x)
+        snr, _ = plan.boxcar_snr(plane, widths)
+        torch.cuda.synchronize()
+        if name == "subband":
+            _lib.af_plan_check(plan.handle)
+        vals = []
+        for p in pp:
+            rows = np.nonzero(np.abs(dms - p["dm"]) < 20.0)[0]
+            half = int(0.2 / tsamp)
+            t0, t1 = max(0, p["t0"] - half), min(plane.shape[1], p["t0"] + half + 1)
+            vals.append(float(snr[rows[0]:rows[-1] + 1, t0:t1].max().item()))
+        best[name] = np.array(vals)
+        del plane, snr
+        plan.close()
+    # the smearing of Eq. (sb_smear) at each pulse's nearest fine DM, in samples
+    f = f_lo + (np.arange(nchan) + 0.5) * (f_hi - f_lo) / nchan
+    width = (f_hi - f_lo) / nchan * np.diff(tab["first"])
+    ratios, checked = [], 0
+    for i, p in enumerate(pp):
+        m = int(np.argmin(np.abs(dms - p["dm"])))
+        ddm = abs(dms[m] - dms[(m // n0) * n0])
+        d = float(np.max(2.0 * 4.148808e3 * ddm * width / tab["F"] ** 3)) / tsamp + 2.0
+        sb, ss = best["brute"][i], best["subband"][i]
+        if sb < 8.0:                      # not a detection of the brute-force plane
+            continue
+        checked += 1
+        ratios.append(ss / sb)
+        bound = np.sqrt(p["width"] / (p["width"] + d)) - 3.0 / sb
+        assert ss / sb >= bound, (i, p, ss, sb, d, bound)
+    print("subband / brute-force S/N on %d pulses: mean %.4f min %.4f" % (checked, np.mean(ratios), np.min(ratios)))
+    assert checked >= 10                  # of 20 injected at S/N U(6, 30)
+    assert np.mean(ratios) >= 0.95
