@@ -27,6 +27,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+
 #include "internal.h"
 #include "nn.h"
 #include "ptx.cuh"
@@ -34,7 +37,6 @@
 
 namespace {
 
-constexpr uint32_t kWait = afptx::kMbarWaitPolls;
 // producer warps 0-3, MMA warp 4, epilogue warps 5-8
 constexpr int kProd = 128, kEpi = 128, kBlock = kProd + 32 + kEpi;
 
@@ -94,11 +96,42 @@ constexpr int pow2_cols(int n) { return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ?
 // epilogue().
 constexpr int kLag = 3;  // a producer arrives for a stage kLag steps after issuing it
 
+// One poll of an mbarrier phase that suspends the thread for at most
+// `hint_ns` (the hardware returns earlier when the phase completes).
+__device__ __forceinline__ bool mbar_try_wait_hint(uint32_t bar, uint32_t parity, uint32_t hint_ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for a phase with short suspensions (a pipeline step is microseconds),
+// giving up after kWaitNs of wall time or when another thread gave up; a wait
+// that gives up raises the block's abort flag.
+constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s
 __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort)
 {
-    for (uint32_t i = 0; i < kWait; i++) {
-        if (afptx::mbar_try_wait(bar, parity)) return true;
-        if ((i & 63) == 63 && *abort) return false;
+    if (mbar_try_wait_hint(bar, parity, 200u)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t i = 1;; i++) {
+        if (mbar_try_wait_hint(bar, parity, 200u)) return true;
+        if ((i & 15) == 0) {
+            if (*abort) return false;
+            if (globaltimer_ns() - t0 > kWaitNs) break;
+        }
     }
     *abort = 1;
     return false;
@@ -664,33 +697,46 @@ __global__ void k_pack_wd(const float* __restrict__ w, int cin, int cout, __nv_b
     wd[e] = __float2bfloat16(w[(o * 9 + t) * cin + i]);
 }
 
+// Resident blocks per device for Op (computed once per device, under a lock:
+// model calls may come from several host threads).
+template <class Op>
+int resident_blocks(int dev, size_t smem, int* out)
+{
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) {
+        *out = it->second;
+        return AF_OK;
+    }
+    AF_CUDA(cudaFuncSetAttribute(k_umma<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    AF_CUDA(cudaFuncSetAttribute(k_umma<Op>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
+    int nsm = 0, smem_sm = 0, per_sm = 0;
+    AF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    AF_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    AF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_umma<Op>, kBlock, smem));
+    // resident blocks: by shared memory (1 KB reserved per block), warps, and
+    // the 512 tensor-memory columns each block takes its share of
+    const int by_smem = smem_sm / (int)(smem + 1024 + 256);
+    int b = by_smem < 64 / (kBlock / 32) ? by_smem : 64 / (kBlock / 32);
+    if (per_sm > b) b = per_sm;
+    const int by_tmem = 512 / pow2_cols(Op::NACC * Op::NCOL);
+    if (b > by_tmem) b = by_tmem;
+    *out = cache[dev] = (b < 1 ? 1 : b) * nsm;
+    return AF_OK;
+}
+
 template <class Op>
 int launch(const typename Op::Args& a, int ntiles, cudaStream_t s, const char* what)
 {
     if (ntiles <= 0) return AF_OK;
     const size_t smem = Op::RB + (size_t)Op::NS * (Op::SA + Op::SB);
-    static int cached_dev = -1, cached_blocks = 0;
-    int dev = 0;
+    int dev = 0, blocks = 0;
     AF_CUDA(cudaGetDevice(&dev));
-    if (cached_dev != dev) {
-        AF_CUDA(cudaFuncSetAttribute(k_umma<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        AF_CUDA(cudaFuncSetAttribute(k_umma<Op>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     (int)cudaSharedmemCarveoutMaxShared));
-        int nsm = 0, smem_sm = 0, per_sm = 0;
-        AF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        AF_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-        AF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_umma<Op>, kBlock, smem));
-        // resident blocks: by shared memory (1 KB reserved per block), warps, and
-        // the 512 tensor-memory columns each block takes its share of
-        const int by_smem = smem_sm / (int)(smem + 1024 + 256);
-        int b = by_smem < 64 / (kBlock / 32) ? by_smem : 64 / (kBlock / 32);
-        if (per_sm > b) b = per_sm;
-        const int by_tmem = 512 / pow2_cols(Op::NACC * Op::NCOL);
-        if (b > by_tmem) b = by_tmem;
-        cached_blocks = (b < 1 ? 1 : b) * nsm;
-        cached_dev = dev;
-    }
-    const int grid = ntiles < cached_blocks ? ntiles : cached_blocks;
+    if (int rc = resident_blocks<Op>(dev, smem, &blocks)) return rc;
+    const int grid = ntiles < blocks ? ntiles : blocks;
     k_umma<Op><<<grid, kBlock, smem, s>>>(a);
     return af_cuda_check(cudaGetLastError(), what);
 }

@@ -152,9 +152,11 @@ size_t af_pairs_workspace(af_plan_t p, int64_t nout);  // row-buffer bytes a res
 // stage-2 shared memory of a ring of ns stages, the plan's ring depth, and
 // one persistent stage-2 launch over many plans' blocks (jobs in device
 // memory, first[j] = items before job j, first[njobs] = total).
-int af_launch_pairs_rows(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int layout, int64_t T0, cudaStream_t s);
+// Lb = the block's length (a multiple of the tile, at most the layout's; 0 = the layout's); T0 a multiple of the tile.
+int af_launch_pairs_rows(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int layout, int64_t T0, cudaStream_t s,
+                         int64_t Lb = 0);
 int af_pairs_block_args(af_plan_t p, int64_t nout, int layout, int64_t T0, int32_t* d_plane, af_rowstats_t* d_stats,
-                        af_pair_args* out, long long* items);
+                        af_pair_args* out, long long* items, int64_t Lb = 0);
 size_t af_pairs_stage2_smem(af_plan_t p, int ns);
 int af_pairs_ring(af_plan_t p);
 int af_launch_pairs_persistent(int ns, size_t smem, int grid, const af_pair_args* d_jobs, const long long* d_first,
@@ -165,7 +167,12 @@ int af_launch_pairs(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nou
 // layout's block length; row sums accumulate, the caller clears them once).
 int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,
                           af_rowstats_t* d_stats, cudaStream_t s, int layout, int64_t T0,
-                          cudaEvent_t* mid = nullptr);
+                          cudaEvent_t* mid = nullptr, int64_t Lb = 0);
+// The time blocks af_search runs on nout outputs, in tiles: the first small
+// (its input, outputs + Dmax, is copied before any work), each next one four
+// times the previous (its input arrives while the previous one runs), at most
+// cap_tiles each.
+std::vector<int64_t> af_search_block_tiles(int64_t nout, int64_t cap_tiles);
 int af_pair_tile_outputs();
 int af_pair_ring_depth(int shape);
 // Row-buffer bytes of a full-length single time block, and the use of a row

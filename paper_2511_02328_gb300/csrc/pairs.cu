@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kS1T)
 k_group_rows(const uint8_t* __restrict__ X, int64_t nsamp, int nchan, const int4* __restrict__ pinfo,
              const int* __restrict__ gmax, const int2* __restrict__ gdr, const int32_t* __restrict__ rdelta,
              const int2* __restrict__ rinfo, const int64_t* __restrict__ rowoff, int64_t T0, int etiles, int wstride,
-             uint16_t* __restrict__ PS)
+             int dshort, uint16_t* __restrict__ PS)
 {
     constexpr int K = G - 1;
     extern __shared__ __align__(16) uint8_t sm[];
@@ -93,7 +93,9 @@ k_group_rows(const uint8_t* __restrict__ X, int64_t nsamp, int nchan, const int4
     const int q = blockIdx.x / etiles;
     const int64_t e0 = (int64_t)(blockIdx.x % etiles) * kET;
     const int4 pi = __ldg(pinfo + q);
-    if (e0 >= pi.w) return;
+    // a time block dshort outputs shorter than the layout's needs every row
+    // (and the group's range) dshort samples shorter (dshort a multiple of 16)
+    if (e0 >= pi.w - dshort) return;
     // the rows overlapping [e0, e0 + ET): rows are ordered by start, so they are
     // those from the first starting after e0 - (longest row) to the first
     // starting at or after e0 + ET (each still checked below)
@@ -172,7 +174,7 @@ k_group_rows(const uint8_t* __restrict__ X, int64_t nsamp, int nchan, const int4
 #pragma unroll
         for (int j = 0; j < 4; j++) {
             const int w = tid + kS1T * j;
-            live[j] = e0 + 4 * w < pi.w;
+            live[j] = e0 + 4 * w < pi.w - dshort;
             const int p = (off[0] >> 2) + w;
             const uint32_t a = __funnelshift_r(A32[p], A32[p + 1], sh);
             alo[j] = __byte_perm(a, 0u, 0x4140);  // samples 0, 1 into 16-bit lanes
@@ -204,7 +206,8 @@ k_group_rows(const uint8_t* __restrict__ X, int64_t nsamp, int nchan, const int4
 #pragma unroll
         for (int j = 0; j < 4; j++) {
             const int64_t rel = e0 + 4 * (tid + kS1T * j) - ri.x;  // sample index within the row
-            if (live[j] && rel >= 0 && rel < ri.y) *reinterpret_cast<uint2*>(row + rel) = make_uint2(lo[j], hi[j]);
+            if (live[j] && rel >= 0 && rel < ri.y - dshort)
+                *reinterpret_cast<uint2*>(row + rel) = make_uint2(lo[j], hi[j]);
         }
     }
 }
@@ -929,13 +932,31 @@ int af_pairs_reserve(af_plan_t p, int64_t nout, bool search, bool allow_larger, 
     if (best_L > T->lay[0].L)
         if (int rc = pairs_layout(p, 0, best_L)) return rc;
     if (search) {
-        // at least eight time blocks, so that the input copy overlaps the work
-        // (the first block waits for its outputs + Dmax of input)
-        const int64_t tiles = (nout + kPTTE - 1) / kPTTE;
-        const int64_t L8 = std::min(T->lay[0].L, (tiles + 7) / 8 * kPTTE);
-        if (int rc = pairs_layout(p, 1, L8)) return rc;
+        // af_search's growing time blocks, so that the input copy overlaps the
+        // work: the layout holds the longest of them
+        const std::vector<int64_t> blocks = af_search_block_tiles(nout, T->lay[0].L / kPTTE);
+        const int64_t Lmax = *std::max_element(blocks.begin(), blocks.end()) * kPTTE;
+        if (int rc = pairs_layout(p, 1, Lmax)) return rc;
     }
     return AF_OK;
+}
+
+std::vector<int64_t> af_search_block_tiles(int64_t nout, int64_t cap_tiles)
+{
+    // the dedispersion consumes input ~5 times slower than a pinned host copy
+    // delivers it, so each block can be 4 times the previous one and still
+    // find its input in place when the previous one ends
+    const int64_t tiles = (nout + kPTTE - 1) / kPTTE;
+    cap_tiles = std::max<int64_t>(1, cap_tiles);
+    std::vector<int64_t> out;
+    int64_t b = std::max<int64_t>(1, tiles / 32), done = 0;
+    while (done < tiles) {
+        const int64_t t = std::min(std::min(b, cap_tiles), tiles - done);
+        out.push_back(t);
+        done += t;
+        b *= 4;
+    }
+    return out;
 }
 
 size_t af_pairs_reserved_bytes(af_plan_t p, int64_t nout)
@@ -976,12 +997,16 @@ int af_pairs_attach(af_plan_t p, uint16_t* buf, size_t bytes, int64_t nout)
     return pairs_layout(p, 0, lo * kPTTE);
 }
 
-int af_launch_pairs_rows(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int layout, int64_t T0, cudaStream_t s)
+int af_launch_pairs_rows(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int layout, int64_t T0, cudaStream_t s,
+                         int64_t Lb)
 {
     af_pair_tables* T = &p->pairs;
     const af_pair_tables::Layout& ly = T->lay[layout];
     const int64_t L = ly.L;
-    if (L <= 0 || L % kPTTE || T0 % L) return af_set_error(AF_EINVAL, "pairs: time block not laid out");
+    if (Lb <= 0) Lb = L;
+    if (L <= 0 || L % kPTTE || T0 % kPTTE || Lb > L || Lb % kPTTE)
+        return af_set_error(AF_EINVAL, "pairs: time block not laid out");
+    const int dshort = (int)((L - Lb) & ~(int64_t)15);
     const size_t s1 = rows_smem(T->maxdr, T->G);
     const void* k1 = T->G == 4   ? (const void*)k_group_rows<4>
                      : T->G == 3 ? (const void*)k_group_rows<3>
@@ -993,25 +1018,28 @@ int af_launch_pairs_rows(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int la
     if (T->G == 4)
         k_group_rows<4><<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, ly.d_pinfo, ly.d_gmax, T->d_gdr, T->d_rdelta,
                                                       ly.d_rinfo, ly.d_rowoff, T0, etiles, rows_wstride(T->maxdr),
-                                                      T->d_ps);
+                                                      dshort, T->d_ps);
     else if (T->G == 3)
         k_group_rows<3><<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, ly.d_pinfo, ly.d_gmax, T->d_gdr, T->d_rdelta,
                                                       ly.d_rinfo, ly.d_rowoff, T0, etiles, rows_wstride(T->maxdr),
-                                                      T->d_ps);
+                                                      dshort, T->d_ps);
     else
         k_group_rows<2><<<(unsigned)g1, kS1T, s1, s>>>(d_in, nsamp, p->nchan, ly.d_pinfo, ly.d_gmax, T->d_gdr, T->d_rdelta,
                                                       ly.d_rinfo, ly.d_rowoff, T0, etiles, rows_wstride(T->maxdr),
-                                                      T->d_ps);
+                                                      dshort, T->d_ps);
     return af_cuda_check(cudaGetLastError(), "group rows launch");
 }
 
 int af_pairs_block_args(af_plan_t p, int64_t nout, int layout, int64_t T0, int32_t* d_plane, af_rowstats_t* d_stats,
-                        af_pair_args* out, long long* items)
+                        af_pair_args* out, long long* items, int64_t Lb)
 {
     af_pair_tables* T = &p->pairs;
     const af_pair_tables::Layout& ly = T->lay[layout];
-    const int64_t L = ly.L;
-    if (L <= 0 || L % kPTTE || T0 % L || T0 >= nout) return af_set_error(AF_EINVAL, "pairs: time block not laid out");
+    int64_t L = ly.L;
+    if (Lb <= 0) Lb = L;
+    if (L <= 0 || L % kPTTE || T0 % kPTTE || T0 >= nout || Lb > L || Lb % kPTTE)
+        return af_set_error(AF_EINVAL, "pairs: time block not laid out");
+    L = Lb;
     af_pair_args& a = *out;
     a.PS = T->d_ps;
     a.chunks = T->d_chunks;
@@ -1055,14 +1083,14 @@ int af_launch_pairs_persistent(int ns, size_t smem, int grid, const af_pair_args
 int af_pairs_ring(af_plan_t p) { return p->pairs.shape; }
 
 int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64_t nout, int32_t* d_plane,
-                          af_rowstats_t* d_stats, cudaStream_t s, int layout, int64_t T0, cudaEvent_t* mid)
+                          af_rowstats_t* d_stats, cudaStream_t s, int layout, int64_t T0, cudaEvent_t* mid, int64_t Lb)
 {
     af_pair_tables* T = &p->pairs;
-    if (int rc = af_launch_pairs_rows(p, d_in, nsamp, layout, T0, s)) return rc;
+    if (int rc = af_launch_pairs_rows(p, d_in, nsamp, layout, T0, s, Lb)) return rc;
     if (mid) AF_CUDA(cudaEventRecord(*mid, s));
     PairArgs a;
     long long items = 0;
-    if (int rc = af_pairs_block_args(p, nout, layout, T0, d_plane, d_stats, &a, &items)) return rc;
+    if (int rc = af_pairs_block_args(p, nout, layout, T0, d_plane, d_stats, &a, &items, Lb)) return rc;
     const size_t s2 = af_pairs_stage2_smem(p, T->shape);
     if (int rc = af_ensure_smem(tile_kernel(T->shape), s2)) return rc;
     if ((unsigned long long)items > 0x7fffffffULL) return af_set_error(AF_EINVAL, "pairs: problem too large for one grid");

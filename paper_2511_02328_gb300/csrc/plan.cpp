@@ -729,17 +729,19 @@ try {
     const bool tm = p->ws_timing;
     if (tm) AF_CUDA(cudaEventRecord(p->ws_tev[0], s));
     if (af_dedisp_uses_pairs(p, nout)) {
-        // Group rows: the outputs in the search layout's time blocks (at least
-        // eight); each block's rows and tiles run as soon as its input columns
-        // (block end + Dmax) are in, overlapping the rest of the copy.
+        // Group rows: the outputs in growing time blocks (a small first one,
+        // each next four times longer, at most the search layout's length);
+        // each block's rows and tiles run as soon as its input columns (block
+        // end + Dmax) are in, overlapping the rest of the copy.
         const int ly = p->pairs.lay[1].L > 0 ? 1 : 0;
-        const int64_t L = p->pairs.lay[ly].L;
+        const int64_t tte = af_pair_tile_outputs();
+        const std::vector<int64_t> blocks = af_search_block_tiles(nout, p->pairs.lay[ly].L / tte);
         AF_CUDA(cudaEventRecord(p->ws_ev[0], s));
         AF_CUDA(cudaStreamWaitEvent(p->ws_copy, p->ws_ev[0], 0));
         AF_CUDA(cudaMemsetAsync(p->d_stats, 0, (size_t)p->ndm * sizeof(af_rowstats_t), s));
-        int64_t col = 0;
-        int k = 0;
-        for (int64_t T0 = 0; T0 < nout; T0 += L, k++) {
+        int64_t col = 0, T0 = 0;
+        for (size_t k = 0; k < blocks.size(); k++) {
+            const int64_t L = blocks[k] * tte;
             const int64_t need = T0 + L >= nout ? nsamp : std::min<int64_t>(nsamp, T0 + L + p->dmax);
             if (need > col) {
                 AF_CUDA(cudaMemcpy2DAsync(p->ws_in + col, (size_t)nsamp, h_in + col, (size_t)nsamp, (size_t)(need - col),
@@ -750,7 +752,9 @@ try {
             AF_CUDA(cudaEventRecord(ev, p->ws_copy));
             AF_CUDA(cudaStreamWaitEvent(s, ev, 0));
             if (tm && k == 0) AF_CUDA(cudaEventRecord(p->ws_tev[1], s));
-            if (int rc = af_launch_pairs_block(p, p->ws_in, nsamp, nout, p->ws_plane, p->d_stats, s, ly, T0)) return rc;
+            if (int rc = af_launch_pairs_block(p, p->ws_in, nsamp, nout, p->ws_plane, p->d_stats, s, ly, T0, nullptr, L))
+                return rc;
+            T0 += L;
         }
     } else if (af_dedisp_uses_tiles(p)) {
         // The input arrives in time segments on the copy stream; each segment's
