@@ -1,8 +1,14 @@
-"""Trains the streaming workload's candidate classifier and writes the
-checkpoint that the benchmark's streaming block classifies with.
+"""Trains a candidate classifier on oracle-injected pulses and writes its
+checkpoint; by default the streaming workload's, which the benchmark's
+streaming block classifies with.
 
-    python tests/classifier_checkpoint.py --chunks 8000 \
+    python tests/classifier_checkpoint.py --chunks 12000 \
         --out paper_2511_02328_gb300/data/stream_cnn_4096ch.ckpt
+    python tests/classifier_checkpoint.py --workload 256ch --chunks 28000 --eval-chunks 3000 --out cnn_256ch.ckpt
+
+The 256ch workload is the learned-classifier configuration: the 256-channel
+search's data (1000-1500 MHz, 98.304 us, 2^15 samples, DMs 0..500) with four
+pulses per chunk (DM U(20, 480)) and the same RFI classes.
 
 Training data: chunks of the streaming workload's band and DM grid (4096
 channels, 1000-1500 MHz, 49.152 us, DMs 0..2000, 2^15 outputs each) of
@@ -39,6 +45,7 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--seed", type=int, default=11)
+    ap.add_argument("--workload", choices=["stream", "256ch"], default="stream")
     ap.add_argument("--out", default=os.path.join(ROOT, "paper_2511_02328_gb300", "data", "stream_cnn_4096ch.ckpt"))
     a = ap.parse_args(argv)
     import __graft_entry__
@@ -47,7 +54,7 @@ def main(argv=None):
     import oracle
     from paper_2511_02328_gb300 import _lib, classifier
 
-    c = classifier.STREAM_CHUNK
+    c = classifier.STREAM_CHUNK if a.workload == "stream" else classifier.CHUNK
 
     def offsets(dm, t0):
         return oracle.injection_offsets(c["nchan"], c["f_lo"], c["f_hi"], c["tsamp"], dm, t0)
@@ -66,7 +73,7 @@ def main(argv=None):
     res = classifier.evaluate(snr_e, prob, rec_e, tsamp=c["tsamp"], nout=searcher.nout)
     res.update(samples=int(X.shape[0]), positives=int(Y.sum().item()), eval_samples=int(Xe.shape[0]),
                loss_per_epoch=hist, data_s=t1 - t0, train_s=t2 - t1, chunks=a.chunks, eval_chunks=a.eval_chunks,
-               injector="oracle.injection_offsets")
+               injector="oracle.injection_offsets", workload=a.workload)
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
     _lib.af_model_save(model, a.out)
     print(json.dumps(res))
