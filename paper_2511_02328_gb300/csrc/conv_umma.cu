@@ -40,10 +40,11 @@ namespace {
 // producer warps 0-3, MMA warp 4, epilogue warps 5-8
 constexpr int kProd = 128, kEpi = 128, kBlock = kProd + 32 + kEpi;
 
-// cp.async of 16 (4) bytes; `bytes` < size zero-fills the rest (0: no read)
+// cp.async of 16 (4) bytes through L1 (a 3x3 gather reads each input pixel up
+// to nine times); `bytes` < size zero-fills the rest (0: no read)
 __device__ __forceinline__ void cp16(uint32_t dst, const void* src, uint32_t bytes)
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void cp4(uint32_t dst, const void* src, uint32_t bytes)
 {
@@ -91,10 +92,11 @@ constexpr int pow2_cols(int n) { return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ?
 //   tempty[b] 128 epilogue arrivals: accumulator b has been read
 // NACC accumulators of Op::NCOL columns each alternate between tiles, so the
 // epilogue of one tile overlaps the MMAs of the next.
-// Op provides: NS (stages), NACC, NCOL, SA / SB (bytes of a stage's A / B
+// Op provides: NS (stages), LAG, NACC, NCOL, SA / SB (bytes of a stage's A / B
 // tile), RB (resident bytes), ntiles(), nkb(), resident(), stage(), mma(),
 // epilogue().
-constexpr int kLag = 3;  // a producer arrives for a stage kLag steps after issuing it
+// A producer thread arrives for a stage Op::LAG steps after issuing its
+// copies (LAG stages of its copies in flight, LAG < NS).
 
 // One poll of an mbarrier phase that suspends the thread for at most
 // `hint_ns` (the hardware returns earlier when the phase completes).
@@ -144,10 +146,10 @@ __global__ void __launch_bounds__(kBlock) k_umma(const typename Op::Args args)
     __shared__ __align__(8) uint64_t bars[2 * Op::NS + 2 * Op::NACC];
     __shared__ uint32_t tslot;
     __shared__ int abort_flag;
-    constexpr int NS = Op::NS, NACC = Op::NACC;
+    constexpr int NS = Op::NS, NACC = Op::NACC, kLag = Op::LAG;
     constexpr uint32_t SSTAGE = Op::SA + Op::SB;
     constexpr uint32_t TCOLS = pow2_cols(NACC * Op::NCOL);
-    static_assert(kLag < NS, "the producer must be able to run kLag stages ahead");
+    static_assert(kLag < NS, "the producer must be able to run LAG stages ahead");
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const Op op(args);
     const int ntiles = op.ntiles(), nkb = op.nkb();
@@ -255,7 +257,7 @@ struct FwdOp {
     static_assert(CIN == 2 || CIN % 8 == 0, "input channels: 2 or a multiple of 8");
     static_assert(COUT % 16 == 0 && COUT <= 256, "output channels");
     static constexpr int KP = (9 * CIN + 31) / 32 * 32;
-    static constexpr int NS = 6, NACC = 2, NCOL = COUT;
+    static constexpr int NS = 6, LAG = 3, NACC = 2, NCOL = COUT;
     static constexpr uint32_t SA = 128 * 32 * 2, SB = 0, RB = COUT * KP * 2;
     struct Args {
         const __nv_bfloat16* x;   // [n][H][W][CIN]
@@ -406,7 +408,7 @@ template <int CIN, int COUT>
 struct DgradOp {
     static_assert(CIN % 16 == 0 && CIN <= 256 && COUT % 8 == 0 && (9 * COUT) % 32 == 0, "channels");
     static constexpr int K = 9 * COUT;
-    static constexpr int NS = 6, NACC = 2, NCOL = CIN;
+    static constexpr int NS = 6, LAG = 3, NACC = 2, NCOL = CIN;
     static constexpr uint32_t SA = 128 * 32 * 2, SB = 0, RB = CIN * K * 2;
     struct Args {
         const __nv_bfloat16* dz;  // [n][H][W][COUT]
@@ -497,7 +499,7 @@ struct WgradOp {
     static_assert((CIN == 2 || CIN % 8 == 0) && COUT % 16 == 0 && COUT <= 128 && BKW % 64 == 0, "shapes");
     static constexpr int K9 = 9 * CIN, NP = (K9 + 15) / 16 * 16;
     static_assert(NP <= 256 || (NP % 32 == 0 && NP <= 512), "columns");
-    static constexpr int NS = 4, NACC = 1, NCOL = NP;
+    static constexpr int NS = 4, LAG = 3, NACC = 1, NCOL = NP;
     static constexpr uint32_t SA = COUT * BKW * 2, SB = NP * BKW * 2, RB = 0;
     static_assert(SB >= 16 * 128, "the padding rows of A must read inside the stage");
     struct Args {
@@ -591,7 +593,7 @@ struct WgradOp {
 // K split into `kchunk` runs (atomic epilogue only).
 template <bool AK, bool BK, int EPI>
 struct GemmOp {
-    static constexpr int NS = 4, NACC = 2, NCOL = 64;
+    static constexpr int NS = 4, LAG = 3, NACC = 2, NCOL = 64;
     static constexpr uint32_t SA = 128 * 32 * 2, SB = 64 * 32 * 2, RB = 0;
     struct Args {
         const __nv_bfloat16* A;

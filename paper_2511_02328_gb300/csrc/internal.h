@@ -239,6 +239,8 @@ struct af_plan_s {
     // caller's stream at the start, when the first block may run (its input
     // is in), after the dedispersion, after S/N + candidates
     bool ws_timing = false;
+    std::vector<int32_t> ws_band;          // af_search's input copies: channel bands [ws_band[j], ws_band[j+1])
+    std::vector<int32_t> ws_band_dmax;     // ... and each band's largest delay over every DM
     cudaEvent_t ws_tev[4] = {};
 };
 

@@ -71,6 +71,43 @@ static const double kKDM = 4.148808e3;
 
 // Candidates af_search copies back together with their count.
 static const int32_t kSearchStage = 4096;
+// af_search copies its input in channel bands: a band needs, for the outputs
+// before T, the columns before T + (its largest delay), so the low-delay bands
+// of the first time block arrive sooner than a copy of every channel up to
+// T + Dmax would (half the bytes on a 1000-1500 MHz band).
+static const int kSearchBands = 8;
+
+static void search_bands(af_plan_t p)
+{
+    const int nb = std::min(kSearchBands, p->nchan);
+    p->ws_band.assign(nb + 1, 0);
+    p->ws_band_dmax.assign(nb, 0);
+    for (int j = 0; j <= nb; j++) p->ws_band[j] = (int32_t)((int64_t)p->nchan * j / nb);
+    for (int j = 0; j < nb; j++) {
+        int32_t m = 0;
+        for (int d = 0; d < p->ndm; d++)
+            for (int c = p->ws_band[j]; c < p->ws_band[j + 1]; c++)
+                m = std::max(m, p->delays[(size_t)d * p->nchan + c]);
+        p->ws_band_dmax[j] = m;
+    }
+}
+
+// Copies, band by band on the copy stream, every input column that the
+// outputs before `end` read (all of them when `last`); col[j] = the columns
+// band j already has.
+static int search_copy_upto(af_plan_t p, const uint8_t* h_in, int64_t nsamp, int64_t end, bool last, int64_t* col)
+{
+    const int nb = (int)p->ws_band_dmax.size();
+    for (int j = 0; j < nb; j++) {
+        const int64_t need = last ? nsamp : std::min<int64_t>(nsamp, end + p->ws_band_dmax[j]);
+        if (need <= col[j]) continue;
+        const size_t c0 = (size_t)p->ws_band[j], nc = (size_t)(p->ws_band[j + 1] - p->ws_band[j]);
+        AF_CUDA(cudaMemcpy2DAsync(p->ws_in + c0 * nsamp + col[j], (size_t)nsamp, h_in + c0 * nsamp + col[j],
+                                  (size_t)nsamp, (size_t)(need - col[j]), nc, cudaMemcpyHostToDevice, p->ws_copy));
+        col[j] = need;
+    }
+    return AF_OK;
+}
 
 static void free_search_ws(af_plan_t p)
 {
@@ -679,6 +716,7 @@ try {
     p->ws_nsamp = max_nsamp;
     p->ws_cap = cap;
     p->ws_stage = std::min(cap, kSearchStage);
+    search_bands(p);
     return af_pairs_reserve(p, nout, true);  // the group-row buffers, where that path applies
 } catch (...) {
     return af_host_exception("af_search_reserve");
@@ -732,22 +770,18 @@ try {
         // Group rows: the outputs in growing time blocks (a small first one,
         // each next four times longer, at most the search layout's length);
         // each block's rows and tiles run as soon as its input columns (block
-        // end + Dmax) are in, overlapping the rest of the copy.
+        // end + each channel band's largest delay) are in, overlapping the
+        // rest of the copy.
         const int ly = p->pairs.lay[1].L > 0 ? 1 : 0;
         const int64_t tte = af_pair_tile_outputs();
         const std::vector<int64_t> blocks = af_search_block_tiles(nout, p->pairs.lay[ly].L / tte);
         AF_CUDA(cudaEventRecord(p->ws_ev[0], s));
         AF_CUDA(cudaStreamWaitEvent(p->ws_copy, p->ws_ev[0], 0));
         AF_CUDA(cudaMemsetAsync(p->d_stats, 0, (size_t)p->ndm * sizeof(af_rowstats_t), s));
-        int64_t col = 0, T0 = 0;
+        int64_t col[kSearchBands] = {}, T0 = 0;
         for (size_t k = 0; k < blocks.size(); k++) {
             const int64_t L = blocks[k] * tte;
-            const int64_t need = T0 + L >= nout ? nsamp : std::min<int64_t>(nsamp, T0 + L + p->dmax);
-            if (need > col) {
-                AF_CUDA(cudaMemcpy2DAsync(p->ws_in + col, (size_t)nsamp, h_in + col, (size_t)nsamp, (size_t)(need - col),
-                                          (size_t)p->nchan, cudaMemcpyHostToDevice, p->ws_copy));
-                col = need;
-            }
+            if (int rc = search_copy_upto(p, h_in, nsamp, T0 + L, T0 + L >= nout, col)) return rc;
             cudaEvent_t ev = p->ws_ev[k % 4];  // an event is reused once the stream has waited on it
             AF_CUDA(cudaEventRecord(ev, p->ws_copy));
             AF_CUDA(cudaStreamWaitEvent(s, ev, 0));
@@ -758,23 +792,19 @@ try {
         }
     } else if (af_dedisp_uses_tiles(p)) {
         // The input arrives in time segments on the copy stream; each segment's
-        // output tiles are dedispersed as soon as their columns (and the Dmax
-        // halo after them) are in, overlapping the rest of the copy.
+        // output tiles are dedispersed as soon as their columns (and each
+        // channel band's delay halo after them) are in, overlapping the rest
+        // of the copy.
         const int64_t tte = af_dedisp_tile_outputs();
         const unsigned tiles = (unsigned)((nout + tte - 1) / tte);
         const unsigned K = tiles < 4u ? tiles : 4u;
         AF_CUDA(cudaEventRecord(p->ws_ev[0], s));  // copies follow the caller's earlier work on s
         AF_CUDA(cudaStreamWaitEvent(p->ws_copy, p->ws_ev[0], 0));
         AF_CUDA(cudaMemsetAsync(p->d_stats, 0, (size_t)p->ndm * sizeof(af_rowstats_t), s));
-        int64_t col = 0;
+        int64_t col[kSearchBands] = {};
         for (unsigned k = 0; k < K; k++) {
             const unsigned tb = tiles * k / K, te = tiles * (k + 1) / K;
-            const int64_t need = k + 1 == K ? nsamp : std::min<int64_t>(nsamp, (int64_t)te * tte + p->dmax);
-            if (need > col) {
-                AF_CUDA(cudaMemcpy2DAsync(p->ws_in + col, (size_t)nsamp, h_in + col, (size_t)nsamp, (size_t)(need - col),
-                                          (size_t)p->nchan, cudaMemcpyHostToDevice, p->ws_copy));
-                col = need;
-            }
+            if (int rc = search_copy_upto(p, h_in, nsamp, (int64_t)te * tte, k + 1 == K, col)) return rc;
             AF_CUDA(cudaEventRecord(p->ws_ev[k], p->ws_copy));
             AF_CUDA(cudaStreamWaitEvent(s, p->ws_ev[k], 0));
             if (tm && k == 0) AF_CUDA(cudaEventRecord(p->ws_tev[1], s));
