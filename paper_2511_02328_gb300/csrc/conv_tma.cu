@@ -1,0 +1,780 @@
+// conv_tma.cu -- the classifier's 3x3 convolutions (pad 1) on the tcgen05
+// tensor cores, every operand tile staged in shared memory by bulk async
+// copies (the TMA unit).  The classifier replaces the paper's YOLO detector
+// (Sec. 2.5).
+//
+// Activations and activation gradients of this path are channel-blocked:
+// [n][C/8][H][W][8] bf16.  The eight channels of a pixel are 16 contiguous
+// bytes and eight consecutive pixels of one channel block 128 contiguous
+// bytes -- one core matrix of the tensor cores' no-swizzle layout, K-major
+// where the channels are the contraction (forward, data gradient), MN-major
+// where the pixels are (weight gradient).
+//
+// A tile is R = 128 / W whole rows y0 .. y0 + R - 1 of one image (128 output
+// pixels).  A stage holds three copies of rows y0 - 1 .. y0 + R of every
+// channel block, copy dx shifted by dx - 1 columns (pixel (r, x) of copy dx =
+// X[y0 - 1 + r][x + dx - 1]).  Each copy of a block is one contiguous run of
+// the image's rows, so one bulk copy; the shift wraps a row's first (last)
+// pixel to the previous (next) row's end, and once the copies have landed a
+// fix warp zeroes those pixels and the rows outside the image: the
+// convolution's zero padding.  Tap (dy, dx) of the filter is then copy dx
+// from its row dy on, a descriptor start address; no im2col gather is made:
+//
+//   forward  Z[p][o]     = sum_{t,i} X[p + t][i] W[o][t][i]   A = X copies (K-major), B = W
+//   dgrad    dX[p][i]    = sum_{t,o} dZ[p - t][o] W[o][t][i]  the same form on dZ, taps flipped,
+//                                                            W transposed
+//   wgrad    dW[o][t][i] = sum_p dZ[p][o] X[p + t][i]         A = dZ^T, B = X copies (MN-major)
+//
+// The first layer's two input channels are padded to one block of eight; a
+// K step of 16 then pairs two taps: the step's second core-matrix column is
+// the other tap's data, one leading-dimension offset (a row or a copy) away.
+//
+// One warp-specialised kernel serves all three: warp 0 issues a tile's bulk
+// copies (one per lane) into an NS-deep ring; warp 6 fixes a stage's padding
+// once its copies have landed and releases it; warp 1 (one elected thread)
+// issues the tile's MMAs into one of NACC tensor-memory accumulators and
+// commits them; warps 2-5 read the accumulator back (tcgen05.ld, warp w reads
+// lanes 32 (w % 4) ..) for the epilogue.  Each role waits on one barrier, so
+// the roles overlap across tiles.  Every wait is bounded in wall time; a
+// wait that runs out raises the caller's error flag and the block leaves.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+
+#include "internal.h"
+#include "nn.h"
+#include "ptx.cuh"
+#include "umma.cuh"
+
+namespace {
+
+constexpr int kThreads = 224;  // copy warp, MMA warp, four epilogue warps, fix warp
+constexpr int kFixWarp = 6;
+
+constexpr uint32_t align1k(uint32_t b) { return (b + 1023u) / 1024u * 1024u; }
+constexpr int clampi(int v, int lo, int hi) { return v < lo ? lo : v > hi ? hi : v; }
+constexpr int pow2_cols(int n) { return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : n <= 256 ? 256 : 512; }
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// The epilogue warps' own barrier (id 1, 128 threads).
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Barrier of the epilogue warps that also ORs a flag over them: every warp
+// leaves with the same answer.
+__device__ __forceinline__ bool epi_sync_any(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
+
+// Geometry of a tile of W columns over CB channel blocks: R rows of outputs,
+// a copy (one column shift) holds R + 2 rows of every block.
+template <int CB, int W>
+struct Geo {
+    static_assert(W == 16 || W == 32 || W == 64, "tile widths");
+    static constexpr int R = 128 / W;
+    static constexpr uint32_t PLANE = (uint32_t)(R + 2) * W * 16;  // one channel block of a copy
+    static constexpr uint32_t COPY = align1k(PLANE * CB);          // a copy, 1024-byte aligned
+};
+
+// The three shifted copies of a tile (image img, rows y0 - 1 .. y0 + R) of a
+// channel-blocked tensor `in` with CB blocks of H x W pixels.  Copy c (< 3 CB)
+// is block c % CB of copy dx = c / CB: the image's rows among y0 - 1 ..
+// y0 + R, one run; copy 0 lands one pixel later than it starts in memory,
+// copy 2 one pixel earlier.  Planes (one block of one copy) sit copy-major
+// (dx * COPY + cb * PLANE) or, BM, block-major ((3 cb + dx) * PLANE).
+template <int CB, int W, bool BM = false>
+struct Halo {
+    using G = Geo<CB, W>;
+    static constexpr int R = G::R, NCOPY = 3 * CB;
+    static constexpr uint32_t BYTES = BM ? align1k(3 * CB * G::PLANE) : 3 * G::COPY;
+    __host__ __device__ static constexpr uint32_t plane(int dx, int cb)
+    {
+        return BM ? (uint32_t)(3 * cb + dx) * G::PLANE : (uint32_t)dx * G::COPY + (uint32_t)cb * G::PLANE;
+    }
+    // the image's rows ylo .. ylo + nrows - 1 land at stage row rlo
+    __device__ static void rows(int y0, int H, int& ylo, int& nrows, int& rlo)
+    {
+        ylo = y0 > 0 ? y0 - 1 : 0;
+        const int yhi = y0 + R < H ? y0 + R : H - 1;
+        nrows = yhi - ylo + 1;
+        rlo = ylo - (y0 - 1);
+    }
+    __device__ static uint32_t tx(int y0, int H)
+    {
+        int ylo, nrows, rlo;
+        rows(y0, H, ylo, nrows, rlo);
+        return (uint32_t)CB * (3u * (uint32_t)nrows * W * 16 - 32u);
+    }
+    __device__ static void copy(int c, uint32_t st, const __nv_bfloat16* in, int img, int y0, int H, uint32_t bar)
+    {
+        int ylo, nrows, rlo;
+        rows(y0, H, ylo, nrows, rlo);
+        const int dx = c / CB, cb = c - dx * CB;
+        const uint8_t* src = reinterpret_cast<const uint8_t*>(in) + (((int64_t)img * CB + cb) * H + ylo) * W * 16;
+        const uint32_t dst = st + plane(dx, cb) + (uint32_t)rlo * W * 16;
+        const uint32_t len = (uint32_t)nrows * W * 16;
+        if (dx == 1) afptx::bulk_g2s(dst, src, len, bar);
+        else if (dx == 0) afptx::bulk_g2s(dst + 16, src, len - 16, bar);
+        else afptx::bulk_g2s(dst, src + 16, len - 16, bar);
+    }
+    // After the copies landed: zero the wrapped pixels (column 0 of copy 0,
+    // column W - 1 of copy 2, every row and block) and the rows outside the
+    // image, then make the writes visible to the tensor cores.
+    __device__ static void fixup(uint8_t* st, int y0, int H, int lane)
+    {
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        for (int e = lane; e < 2 * CB * (R + 2); e += 32) {
+            const int k = e / (CB * (R + 2)), rem = e - k * CB * (R + 2), cb = rem / (R + 2), r = rem - cb * (R + 2);
+            *reinterpret_cast<uint4*>(st + plane(2 * k, cb) + (r * W + (k ? W - 1 : 0)) * 16) = z;
+        }
+        if (y0 == 0 || y0 + R == H) {
+            const int r = y0 == 0 ? 0 : R + 1;  // R < H: a tile has one edge at most
+            for (int e = lane; e < 3 * CB * W; e += 32) {
+                const int c = e / W, x = e - c * W, dx = c / CB, cb = c - dx * CB;
+                *reinterpret_cast<uint4*>(st + plane(dx, cb) + (r * W + x) * 16) = z;
+            }
+        }
+        afptx::fence_proxy_async();
+    }
+};
+
+// ------------------------------------------------------------ the pipeline
+// Barriers: full[s] (the bulk copies' transaction bytes), ready[s] (the fix
+// warp fixed the stage), empty[s] (MMA commit), tfull[b] (MMA
+// commit: accumulator b holds a finished tile), tempty[b] (128 epilogue
+// arrivals: accumulator b was read).  Op provides NS, NACC, NCOL, PER_TILE (an
+// epilogue per tile, else one at the end over the block's tiles), RB
+// (resident bytes, a multiple of 1024), SSTAGE, SLACK (bytes after the ring
+// that MMAs may read), NCOPY, ntiles(), tx(), copy(), fixup(), resident(),
+// mma(), epilogue(), final().
+template <class Op>
+__global__ void __launch_bounds__(kThreads) k_tconv(const typename Op::Args args)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bars[3 * Op::NS + 2 * Op::NACC];
+    __shared__ uint32_t tslot;
+    __shared__ int abort_flag;
+    __shared__ __align__(16) float xv[32 * 16];  // pool exchange between epilogue warps
+    __shared__ uint32_t xq[32];
+    constexpr int NS = Op::NS, NACC = Op::NACC;
+    constexpr uint32_t TCOLS = pow2_cols(NACC * Op::NCOL);
+    static_assert(Op::NCOPY <= 32, "one bulk copy per producer lane");
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const Op op(args);
+    const int ntiles = op.ntiles();
+    const int mytiles = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    const uint32_t raw = afptx::smem_addr(smem_raw), base = (raw + 1023u) & ~1023u;
+    uint8_t* sm = smem_raw + (base - raw);
+    const uint32_t ring = base + Op::RB;
+    const uint32_t full0 = afptx::smem_addr(bars), ready0 = full0 + 8 * NS, empty0 = ready0 + 8 * NS,
+                   tfull0 = empty0 + 8 * NS, tempty0 = tfull0 + 8 * NACC;
+    volatile int* abort = &abort_flag;
+    auto tile_of = [&](int g) { return (int)blockIdx.x + g * (int)gridDim.x; };
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; s++) {
+            afptx::mbar_init(full0 + 8 * s, 1);
+            afptx::mbar_init(ready0 + 8 * s, 1);
+            afptx::mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int b = 0; b < NACC; b++) {
+            afptx::mbar_init(tfull0 + 8 * b, 1);
+            afptx::mbar_init(tempty0 + 8 * b, 128);
+        }
+        abort_flag = 0;
+        afptx::fence_mbar_init();
+    }
+    if (warp == 1) {
+        afumma::tmem_alloc(afptx::smem_addr(&tslot), TCOLS);
+        afumma::tmem_relinquish();
+    }
+    op.resident(sm, tid);  // resident weights (generic stores)
+    if constexpr (Op::SLACK > 0)
+        for (uint32_t i = tid; i < Op::SLACK / 16; i += kThreads)
+            reinterpret_cast<uint4*>(sm + Op::RB + NS * Op::SSTAGE)[i] = make_uint4(0u, 0u, 0u, 0u);
+    afptx::fence_proxy_async();  // ... visible to the tensor cores
+    afumma::fence_before_sync();
+    __syncthreads();
+    afumma::fence_after_sync();
+    const uint32_t tmem = tslot;
+
+    if (warp == 0) {
+        // ---------------- copies: tile g into stage g % NS once the MMAs of tile g - NS are done
+        int g = 0;
+        for (; g < mytiles; g++) {
+            const int s = g % NS;
+            if (g >= NS &&
+                !__all_sync(0xffffffffu, afumma::wait_or_abort(empty0 + 8 * s, (uint32_t)(g / NS - 1) & 1u, abort)))
+                break;
+            if (lane == 0) afptx::mbar_arrive_expect_tx(full0 + 8 * s, op.tx(tile_of(g)));
+            __syncwarp();
+            if (lane < Op::NCOPY) op.copy(lane, ring + (uint32_t)s * Op::SSTAGE, tile_of(g), full0 + 8 * s);
+        }
+        // the last copies land before the block's shared memory goes away (a
+        // bounded wait that an abort does not cut short)
+        if (lane == 0)
+            for (int h = g - NS < 0 ? 0 : g - NS; h < g; h++) {
+                const uint64_t t0 = afumma::globaltimer_ns();
+                while (!afumma::mbar_test_wait(full0 + 8 * (h % NS), (uint32_t)(h / NS) & 1u) &&
+                       afumma::globaltimer_ns() - t0 < afumma::kWaitNs) {
+                }
+            }
+    } else if (warp == kFixWarp) {
+        // ---------------- fixes: tile g's padding once its copies have landed, then the stage is ready
+        int g = 0;
+        for (; g < mytiles; g++) {
+            const int s = g % NS;
+            if (!__all_sync(0xffffffffu, afumma::wait_or_abort(full0 + 8 * s, (uint32_t)(g / NS) & 1u, abort))) break;
+            op.fixup(sm + Op::RB + (size_t)s * Op::SSTAGE, tile_of(g), lane);
+            __syncwarp();
+            if (lane == 0) afptx::mbar_arrive(ready0 + 8 * s);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        int g = 0;
+        for (; g < mytiles; g++) {
+            const int s = g % NS, b = g % NACC;
+            bool ok = true;
+            if (Op::PER_TILE && g >= NACC)  // the epilogue has read this accumulator's previous tile
+                ok = afumma::wait_or_abort(tempty0 + 8 * b, (uint32_t)(g / NACC - 1) & 1u, abort);
+            ok = ok && afumma::wait_or_abort(ready0 + 8 * s, (uint32_t)(g / NS) & 1u, abort);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            afumma::fence_after_sync();
+            if (lane == 0) {
+                op.mma(ring + (uint32_t)s * Op::SSTAGE, base, tmem + (uint32_t)(Op::PER_TILE ? b * Op::NCOL : 0), g);
+                afumma::commit(empty0 + 8 * s);
+                if (Op::PER_TILE) afumma::commit(tfull0 + 8 * b);
+                else if (g == mytiles - 1) afumma::commit(tfull0);
+            }
+            __syncwarp();
+        }
+        // every MMA reading the ring has completed before the block leaves
+        for (int h = g - NS < 0 ? 0 : g - NS; h < g && !*abort; h++)
+            afumma::wait_or_abort(empty0 + 8 * (h % NS), (uint32_t)(h / NS) & 1u, abort);
+    } else {
+        // ---------------- epilogue (warps 2-5)
+        const int quarter = warp & 3;
+        if (Op::PER_TILE) {
+            for (int i = 0; i < mytiles; i++) {
+                const int b = i % NACC;
+                const bool ok = afumma::wait_or_abort(tfull0 + 8 * b, (uint32_t)(i / NACC) & 1u, abort);
+                if (epi_sync_any(!ok || *abort)) break;  // all four warps leave together
+                afumma::fence_after_sync();
+                op.epilogue(tile_of(i), tmem + (uint32_t)(b * Op::NCOL), quarter, lane, xv, xq);
+                afumma::fence_before_sync();
+                afptx::mbar_arrive(tempty0 + 8 * b);
+            }
+        } else if (mytiles > 0) {
+            const bool ok = afumma::wait_or_abort(tfull0, 0u, abort);
+            if (!epi_sync_any(!ok || *abort)) {
+                afumma::fence_after_sync();
+                op.final(tmem, quarter, lane);
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && *abort) atomicExch(args.err, 1);
+    afumma::fence_after_sync();
+    if (warp == 1) afumma::tmem_dealloc(tmem, TCOLS);
+}
+
+// ------------------------------------------------------------ convolution
+// 2x2 max pool, one step: the maximum of this lane's 16 values and those of
+// the lane SH away; bit i of the result is set where the other lane's value
+// is strictly larger (ties keep this lane's, the earlier in raster order).
+template <int SH>
+__device__ __forceinline__ uint32_t pool_step(float (&m)[16])
+{
+    uint32_t won = 0u;
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        const float o = __shfl_xor_sync(0xffffffffu, m[i], SH);
+        won |= (o > m[i] ? 1u : 0u) << i;
+        m[i] = fmaxf(m[i], o);
+    }
+    return won;
+}
+
+// Forward (POOL: + bias, ReLU, 2x2 max pool with argmax) or data gradient
+// (plain store) of a 3x3 convolution over CB input channel blocks (1: the
+// two-channel first layer, taps paired), N output channels, W columns.
+// Packed weights (nn_tpack): step s, then its two K halves (core-matrix
+// columns), then N rows of 16 bytes.
+template <int CB, int N, int W, bool POOL>
+struct ConvOp {
+    using G = Geo<CB, W>;
+    static constexpr bool PAIR = CB == 1;
+    static_assert(PAIR || CB % 2 == 0, "input channel blocks: 1 or even");
+    static_assert(N % 16 == 0 && N <= 128, "output channels");
+    static constexpr int R = G::R, STEPS = PAIR ? 5 : 9 * CB / 2;
+    static constexpr uint32_t LBO_B = N / 8 * 128;  // K halves of a weight step
+    static constexpr uint32_t RB = align1k(STEPS * 2 * LBO_B);
+    static constexpr uint32_t SSTAGE = 3 * G::COPY, SLACK = 0;
+    static constexpr int NCOPY = Halo<CB, W>::NCOPY;
+    static constexpr int NS = clampi(49152 / (int)SSTAGE, 2, 4);  // shallow: more blocks (epilogue warps) per SM
+    static constexpr int NACC = 4, NCOL = N;
+    static constexpr bool PER_TILE = true;
+    struct Args {
+        const __nv_bfloat16* in;  // [n][CB][H][W][8]
+        const __nv_bfloat16* wp;  // packed weights, STEPS * 2 * LBO_B bytes
+        const float* bias;        // [N] (POOL)
+        __nv_bfloat16* out;       // POOL: [n][N/8][H/2][W/2][8]; else [n][N/8][H][W][8]
+        uint8_t* idx;             // POOL: argmax | 4 if the maximum > 0, laid out as out (nullable)
+        int n, H;
+        int* err;
+    };
+    const Args a;
+    __device__ ConvOp(const Args& a_) : a(a_) {}
+    __device__ int ntiles() const { return a.n * (a.H / R); }
+    __device__ void resident(uint8_t* res, int tid) const
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(a.wp);
+        for (int i = tid; i < (int)(STEPS * 2 * LBO_B / 16); i += kThreads)
+            reinterpret_cast<uint4*>(res)[i] = __ldg(src + i);
+    }
+    __device__ uint32_t tx(int tile) const { return Halo<CB, W>::tx((tile % (a.H / R)) * R, a.H); }
+    __device__ void copy(int c, uint32_t st, int tile, uint32_t bar) const
+    {
+        const int tpi = a.H / R, img = tile / tpi;
+        Halo<CB, W>::copy(c, st, a.in, img, (tile - img * tpi) * R, a.H, bar);
+    }
+    __device__ void fixup(uint8_t* st, int tile, int lane) const
+    {
+        Halo<CB, W>::fixup(st, (tile % (a.H / R)) * R, a.H, lane);
+    }
+    // Step s: A = the tap's copy from the tap's row, its K halves one LBO apart
+    // (two channel blocks, or for PAIR two taps); B = the step's weights.
+    __device__ void mma(uint32_t st, uint32_t res, uint32_t tmem, int) const
+    {
+        constexpr uint32_t idesc = afumma::idesc_bf16(128, N, 0, 0);
+#pragma unroll
+        for (int s = 0; s < STEPS; s++) {
+            uint32_t a0, lbo;
+            if constexpr (PAIR) {
+                // (0,dx)+(1,dx) for dx = 0, 1, 2; (2,0)+(2,1); (2,1)+(2,2) with zero weights in its first half
+                a0 = s < 3 ? st + s * G::COPY : st + (s - 3) * G::COPY + 2 * W * 16;
+                lbo = s < 3 ? W * 16 : G::COPY;
+            } else {
+                const int t = s / (CB / 2), j = s % (CB / 2);
+                a0 = st + (t % 3) * G::COPY + 2 * j * G::PLANE + (t / 3) * W * 16;
+                lbo = G::PLANE;
+            }
+            afumma::mma_bf16(tmem, afumma::smem_desc(a0, lbo, 128),
+                             afumma::smem_desc(res + (uint32_t)s * 2 * LBO_B, LBO_B, 128), idesc, s != 0);
+        }
+    }
+    __device__ void final(uint32_t, int, int) const {}
+    // Thread = tile row r = 32 quarter + lane, pixel (y0 + r / W, r % W).
+    __device__ void epilogue(int tile, uint32_t tmem, int quarter, int lane, float* xv, uint32_t* xq) const
+    {
+        const int tpi = a.H / R, img = tile / tpi, y0 = (tile - img * tpi) * R;
+        const int r = 32 * quarter + lane, yl = r / W, x = r % W;
+        const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16);
+        if constexpr (!POOL) {
+            const int64_t plane = (int64_t)a.H * W, pix = (int64_t)(y0 + yl) * W + x;
+#pragma unroll 1
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                uint32_t v[16];
+                afumma::ld_32x32b_x16(taddr + (uint32_t)c0, v);
+                afumma::wait_ld();
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const uint32_t* u = v + 8 * h;
+                    const uint4 o = make_uint4(pack_bf16(__uint_as_float(u[0]), __uint_as_float(u[1])),
+                                               pack_bf16(__uint_as_float(u[2]), __uint_as_float(u[3])),
+                                               pack_bf16(__uint_as_float(u[4]), __uint_as_float(u[5])),
+                                               pack_bf16(__uint_as_float(u[6]), __uint_as_float(u[7])));
+                    *reinterpret_cast<uint4*>(a.out + (((int64_t)img * (N / 8) + c0 / 8 + h) * plane + pix) * 8) = o;
+                }
+            }
+        } else {
+            const int Ho = a.H / 2, Wo = W / 2;
+            const bool top = (yl & 1) == 0, even = (x & 1) == 0, lead = top && even;
+            const int wi = (yl >> 1) * Wo + (x >> 1);  // the window's index in the tile, 0..31
+            const int64_t po = (int64_t)(y0 / 2 + (yl >> 1)) * Wo + (x >> 1), oplane = (int64_t)Ho * Wo;
+            const bool train = a.idx != nullptr;
+#pragma unroll 1
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                uint32_t v[16];
+                afumma::ld_32x32b_x16(taddr + (uint32_t)c0, v);
+                afumma::wait_ld();
+                float m[16];
+                const float4* bv = reinterpret_cast<const float4*>(a.bias + c0);
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const float4 b4 = __ldg(bv + k);
+                    m[4 * k] = fmaxf(__uint_as_float(v[4 * k]) + b4.x, 0.f);
+                    m[4 * k + 1] = fmaxf(__uint_as_float(v[4 * k + 1]) + b4.y, 0.f);
+                    m[4 * k + 2] = fmaxf(__uint_as_float(v[4 * k + 2]) + b4.z, 0.f);
+                    m[4 * k + 3] = fmaxf(__uint_as_float(v[4 * k + 3]) + b4.w, 0.f);
+                }
+                // row maxima (the right-hand pixel in the next lane); hx: where it won
+                const uint32_t hx = pool_step<1>(m);
+                uint32_t hx_low = 0u, vy = 0u;  // the lower row's hx; where the lower row won
+                if constexpr (W == 16) {
+                    hx_low = __shfl_xor_sync(0xffffffffu, hx, 16);  // the row below: 16 lanes on
+                    vy = pool_step<16>(m);
+                } else {
+                    // the row below sits in another warp: through shared memory (word i of
+                    // window wi at xv[32 i + wi], conflict-free)
+                    if (!top && even) {
+#pragma unroll
+                        for (int i = 0; i < 16; i++) xv[32 * i + wi] = m[i];
+                        xq[wi] = hx;
+                    }
+                    epi_sync();
+                    if (lead) {
+#pragma unroll
+                        for (int i = 0; i < 16; i++) {
+                            const float o = xv[32 * i + wi];
+                            vy |= (o > m[i] ? 1u : 0u) << i;
+                            m[i] = fmaxf(m[i], o);
+                        }
+                        hx_low = xq[wi];
+                    }
+                    epi_sync();
+                }
+                if (lead) {
+                    const int64_t e0 = (((int64_t)img * (N / 8) + c0 / 8) * oplane + po) * 8;
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const float* u = m + 8 * h;
+                        *reinterpret_cast<uint4*>(a.out + e0 + h * oplane * 8) =
+                            make_uint4(pack_bf16(u[0], u[1]), pack_bf16(u[2], u[3]), pack_bf16(u[4], u[5]),
+                                       pack_bf16(u[6], u[7]));
+                        if (train) {
+                            // argmax in raster order: (lower row won ? 2 + its column : this row's column)
+                            uint32_t w2[2] = {0u, 0u};
+#pragma unroll
+                            for (int k = 0; k < 8; k++) {
+                                const int i = 8 * h + k;
+                                const uint32_t q = ((vy >> i) & 1u) ? 2u | ((hx_low >> i) & 1u) : (hx >> i) & 1u;
+                                w2[k >> 2] |= (q | (u[k] > 0.f ? 4u : 0u)) << (8 * (k & 3));
+                            }
+                            *reinterpret_cast<uint2*>(a.idx + e0 + h * oplane * 8) = make_uint2(w2[0], w2[1]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+};
+
+
+// ------------------------------------------------------------ weight gradient
+// dW[o][t][i] += sum over the block's tiles of dZ[p][o] X[p + t][i], with ZB
+// output channel blocks (COUT = 8 ZB) and CB input channel blocks (1: the
+// two-channel first layer).  A stage holds the tile's dZ rows (R rows of every
+// block, one bulk copy per block) and the three shifted copies of X.  A
+// (dZ^T) has 128 rows of which COUT are real: the others read up to 16
+// channel blocks from the stage's start (past the ring's end for the last
+// stage: the zeroed slack) and their results are never read.  Per 16 pixels
+// of K:
+//   TAPN: one MMA per input block whose N columns are the taps: with the
+//     block's three copies back to back, tap (dy, dx) starts (dy + (R + 2) dx)
+//     rows after the first, so N = 8 NJ columns (NJ = 2 (R + 2) + 3 rounded up
+//     to even) at a stride of one row take every tap in one MMA (the columns
+//     of dy >= 3 are read and dropped); A is read once for all taps.
+//   else: one MMA per tap, N = the block's channels.
+template <int CB, int ZB, int W, bool TAPN>
+struct WgradOp {
+    using G = Geo<CB, W>;
+    using H3 = Halo<CB, W, TAPN>;
+    static_assert(CB == 1 || CB % 2 == 0, "input channel blocks: 1 or even");
+    static_assert(TAPN || CB >= 2, "the per-tap form needs N = 8 CB >= 16");
+    static constexpr int R = G::R, CIN = CB == 1 ? 2 : CB * 8, COUT = ZB * 8;
+    static constexpr int NJ = (2 * (R + 2) + 3 + 1) / 2 * 2;
+    static constexpr int NPM = TAPN ? 8 * NJ : CB * 8;  // N of one MMA
+    static constexpr int NMMA = TAPN ? CB : 9;          // MMAs per K step
+    static_assert(NPM % 16 == 0 && NPM <= 256, "MMA width");
+    static_assert(COUT <= 128, "output channels");
+    static constexpr uint32_t PLANE_Z = (uint32_t)R * W * 16, ZREG = align1k(PLANE_Z * ZB);
+    static constexpr uint32_t RB = 0, SSTAGE = ZREG + H3::BYTES;
+    static constexpr int NCOPY = H3::NCOPY + ZB;
+    static constexpr uint32_t SLACK = 16 * PLANE_Z > SSTAGE ? 16 * PLANE_Z - SSTAGE : 0;
+    static constexpr int NS = clampi(65536 / (int)SSTAGE, 2, 4);
+    static constexpr int NACC = 1, NCOL = NMMA * NPM;
+    static_assert(NCOL <= 512, "tensor-memory columns");
+    static constexpr bool PER_TILE = false;
+    struct Args {
+        const __nv_bfloat16* x;   // [n][CB][H][W][8]
+        const __nv_bfloat16* dz;  // [n][ZB][H][W][8]
+        float* grad;              // [COUT][9][CIN], accumulated
+        int n, H;
+        int* err;
+    };
+    const Args a;
+    __device__ WgradOp(const Args& a_) : a(a_) {}
+    __device__ int ntiles() const { return a.n * (a.H / R); }
+    __device__ void resident(uint8_t*, int) const {}
+    __device__ uint32_t tx(int tile) const { return H3::tx((tile % (a.H / R)) * R, a.H) + ZB * PLANE_Z; }
+    // copies 0 .. 3 CB - 1: the shifted copies of X; then one per dZ block
+    __device__ void copy(int c, uint32_t st, int tile, uint32_t bar) const
+    {
+        const int tpi = a.H / R, img = tile / tpi, y0 = (tile - img * tpi) * R;
+        if (c < H3::NCOPY) {
+            H3::copy(c, st + ZREG, a.x, img, y0, a.H, bar);
+        } else {
+            const int zb = c - H3::NCOPY;
+            afptx::bulk_g2s(st + zb * PLANE_Z, a.dz + (((int64_t)img * ZB + zb) * a.H + y0) * W * 8, PLANE_Z, bar);
+        }
+    }
+    __device__ void fixup(uint8_t* st, int tile, int lane) const
+    {
+        H3::fixup(st + ZREG, (tile % (a.H / R)) * R, a.H, lane);
+    }
+    // K step ks = pixels 16 ks .. 16 ks + 15 of the tile; MN-major operands:
+    // core matrices of 8 pixels (K, 128 bytes apart) by 8 channels (M / N).
+    __device__ void mma(uint32_t st, uint32_t, uint32_t tmem, int g) const
+    {
+        constexpr uint32_t idesc = afumma::idesc_bf16(128, NPM, 1, 1);
+        const uint32_t xs = st + ZREG;
+#pragma unroll 1
+        for (int ks = 0; ks < 8; ks++) {
+            const uint64_t da = afumma::smem_desc(st + ks * 256, 128, PLANE_Z);
+#pragma unroll
+            for (int k = 0; k < NMMA; k++) {
+                uint32_t b0, sbo;
+                if constexpr (TAPN) {
+                    b0 = xs + H3::plane(0, k);  // block k: its taps one row apart along N
+                    sbo = W * 16;
+                } else {
+                    b0 = xs + H3::plane(k % 3, 0) + (k / 3) * W * 16;  // tap k, N = the blocks
+                    sbo = G::PLANE;
+                }
+                afumma::mma_bf16(tmem + (uint32_t)(k * NPM), da, afumma::smem_desc(b0 + ks * 256, 128, sbo), idesc,
+                                 (g | ks) != 0);
+            }
+        }
+    }
+    __device__ void epilogue(int, uint32_t, int, int, float*, uint32_t*) const {}
+    // Row o = 32 quarter + lane of the accumulator: its columns into grad.
+    __device__ void final(uint32_t tmem, int quarter, int lane) const
+    {
+        if (32 * quarter >= COUT) return;  // warp-uniform: no real rows in this quarter
+        const int o = 32 * quarter + lane;
+        const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16);
+#pragma unroll 1
+        for (int c0 = 0; c0 < NCOL; c0 += 16) {
+            uint32_t v[16];
+            afumma::ld_32x32b_x16(taddr + (uint32_t)c0, v);
+            afumma::wait_ld();
+            if (o >= COUT) continue;
+#pragma unroll
+            for (int jj = 0; jj < 16; jj++) {
+                const int col = c0 + jj;
+                int t, i;
+                if constexpr (TAPN) {
+                    const int k = col / NPM, r = col - k * NPM, j = r >> 3, dx = j / (R + 2), dy = j - dx * (R + 2);
+                    i = 8 * k + (r & 7);
+                    if (dy >= 3 || dx >= 3 || i >= CIN) continue;
+                    t = 3 * dy + dx;
+                } else {
+                    t = col / NPM;
+                    i = col - t * NPM;
+                }
+                atomicAdd(a.grad + ((int64_t)o * 9 + t) * CIN + i, __uint_as_float(v[jj]));
+            }
+        }
+    }
+};
+
+// ------------------------------------------------------------ weights and input
+// Packed B operand of ConvOp, element e = ((s * 2 + kc) * nrows + row) * 8 + k:
+// step s, K half kc, row (an output channel of the operation), channel k of
+// the K half's block.  Forward: rows o, K = (tap t, input channel i).  Data
+// gradient: rows i, K = (tap t, o) with the taps flipped, W'[i][t][o] =
+// W[o][8 - t][i].  cbk = channel blocks of K per tap (1: the first layer's
+// tap pairs, the zero half of the last pair included).
+__global__ void k_tpack(const float* __restrict__ w, int cin, int cout, int cbk, int nrows, int dgrad, int total,
+                        __nv_bfloat16* __restrict__ out)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int k = e & 7, row = (e >> 3) % nrows, kc = (e / (8 * nrows)) & 1, s = e / (16 * nrows);
+    int t, c;
+    if (cbk == 1) {
+        t = s < 3 ? 3 * kc + s : s == 3 ? 6 + kc : (kc ? 8 : -1);
+        c = k;
+    } else {
+        t = s / (cbk / 2);
+        c = (2 * (s % (cbk / 2)) + kc) * 8 + k;
+    }
+    float v = 0.f;
+    if (t >= 0) {
+        if (!dgrad && c < cin) v = w[((int64_t)row * 9 + t) * cin + c];
+        if (dgrad && c < cout) v = w[((int64_t)c * 9 + (8 - t)) * cin + row];
+    }
+    out[e] = __float2bfloat16(v);
+}
+
+// [n][H][W][2] bf16 (the classifier's input) -> [n][1][H][W][8], channels 2..7 zero
+__global__ void k_to_cb8(const uint32_t* __restrict__ x, int64_t npix, uint4* __restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = make_uint4(__ldg(x + i), 0u, 0u, 0u);
+}
+
+// ------------------------------------------------------------ host side
+template <class Op>
+constexpr size_t smem_bytes()
+{
+    return 1024 + (size_t)Op::RB + (size_t)Op::NS * Op::SSTAGE + Op::SLACK;
+}
+
+// Resident blocks of Op per device (computed once per device, under a lock:
+// model calls may come from several host threads).
+template <class Op>
+int resident_blocks(int dev, int* out)
+{
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) {
+        *out = it->second;
+        return AF_OK;
+    }
+    const size_t smem = smem_bytes<Op>();
+    AF_CUDA(cudaFuncSetAttribute(k_tconv<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    AF_CUDA(cudaFuncSetAttribute(k_tconv<Op>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
+    int nsm = 0, per_sm = 0, smem_sm = 0;
+    cudaFuncAttributes fa;
+    AF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    AF_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    AF_CUDA(cudaFuncGetAttributes(&fa, k_tconv<Op>));
+    AF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tconv<Op>, kThreads, smem));
+    // by shared memory (1 KB reserved per block), at most the 512 tensor-memory
+    // columns' share; the occupancy query's answer when it is larger
+    const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
+    const int by_tmem = 512 / pow2_cols(Op::NACC * Op::NCOL);
+    int b = by_smem > per_sm ? by_smem : per_sm;
+    if (b > by_tmem) b = by_tmem;
+    *out = cache[dev] = (b < 1 ? 1 : b) * nsm;
+    return AF_OK;
+}
+
+template <class Op>
+int launch(const typename Op::Args& a, int ntiles, cudaStream_t s, const char* what)
+{
+    if (ntiles <= 0) return AF_OK;
+    int dev = 0, blocks = 0;
+    AF_CUDA(cudaGetDevice(&dev));
+    if (int rc = resident_blocks<Op>(dev, &blocks)) return rc;
+    const int grid = ntiles < blocks ? ntiles : blocks;
+    k_tconv<Op><<<grid, kThreads, smem_bytes<Op>(), s>>>(a);
+    return af_cuda_check(cudaGetLastError(), what);
+}
+
+// The classifier's layers: input channels, output channels, width (= height).
+constexpr int kCin[3] = {2, 16, 32}, kCout[3] = {16, 32, 64}, kW[3] = {64, 32, 16};
+
+using Fwd0 = ConvOp<1, 16, 64, true>;
+using Fwd1 = ConvOp<2, 32, 32, true>;
+using Fwd2 = ConvOp<4, 64, 16, true>;
+using Dg1 = ConvOp<4, 16, 32, false>;
+using Dg2 = ConvOp<8, 32, 16, false>;
+using Wg0 = WgradOp<1, 2, 64, true>;
+using Wg1 = WgradOp<2, 4, 32, true>;
+using Wg2 = WgradOp<4, 8, 16, false>;
+
+}  // namespace
+
+size_t nn_tpack_bytes(int layer, int dgrad)
+{
+    if (!dgrad) return layer == 0 ? Fwd0::STEPS * 2 * Fwd0::LBO_B : layer == 1 ? Fwd1::STEPS * 2 * Fwd1::LBO_B
+                                                                               : Fwd2::STEPS * 2 * Fwd2::LBO_B;
+    return layer == 1 ? Dg1::STEPS * 2 * Dg1::LBO_B : layer == 2 ? Dg2::STEPS * 2 * Dg2::LBO_B : 0;
+}
+
+int nn_tpack(int layer, int dgrad, const float* w, __nv_bfloat16* out, cudaStream_t s)
+{
+    if (layer < 0 || layer > 2 || (dgrad && layer == 0)) return af_set_error(AF_EINVAL, "conv pack: layer %d", layer);
+    const int cin = kCin[layer], cout = kCout[layer];
+    const int cbk = dgrad ? cout / 8 : (cin < 8 ? 1 : cin / 8), nrows = dgrad ? cin : cout;
+    const int total = (int)(nn_tpack_bytes(layer, dgrad) / 2);
+    k_tpack<<<(total + 255) / 256, 256, 0, s>>>(w, cin, cout, cbk, nrows, dgrad, total, out);
+    return af_cuda_check(cudaGetLastError(), "conv pack");
+}
+
+int nn_to_cb8(const __nv_bfloat16* x, int n, __nv_bfloat16* out, cudaStream_t s)
+{
+    if (((uintptr_t)x & 3) || ((uintptr_t)out & 15)) return af_set_error(AF_EINVAL, "to channel blocks: alignment");
+    const int64_t npix = (int64_t)n * 64 * 64;
+    const int64_t blocks = std::min<int64_t>((npix + 255) / 256, 152 * 32);
+    k_to_cb8<<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<const uint32_t*>(x), npix, reinterpret_cast<uint4*>(out));
+    return af_cuda_check(cudaGetLastError(), "to channel blocks");
+}
+
+int nn_tconv_fwd(int layer, const __nv_bfloat16* x, int n, const __nv_bfloat16* wp, const float* bias,
+                 __nv_bfloat16* out, uint8_t* idx, int* err, cudaStream_t s)
+{
+    if (layer < 0 || layer > 2 || n < 1 || !x || ((uintptr_t)x & 15) || ((uintptr_t)out & 15) ||
+        ((uintptr_t)idx & 15) || ((uintptr_t)bias & 15))
+        return af_set_error(AF_EINVAL, "conv forward: layer %d / alignment", layer);
+    const int W = kW[layer], tiles = n * (W / (128 / W));
+#define AF_TF(L, Op)                                                  \
+    if (layer == L) {                                                 \
+        typename Op::Args a{x, wp, bias, out, idx, n, W, err};        \
+        return launch<Op>(a, tiles, s, "conv forward (tcgen05)");     \
+    }
+    AF_TF(0, Fwd0)
+    AF_TF(1, Fwd1)
+    AF_TF(2, Fwd2)
+#undef AF_TF
+    return AF_OK;
+}
+
+int nn_tconv_dgrad(int layer, const __nv_bfloat16* dz, int n, const __nv_bfloat16* wp, __nv_bfloat16* dx, int* err,
+                   cudaStream_t s)
+{
+    if (layer < 1 || layer > 2 || n < 1 || !dz || ((uintptr_t)dz & 15) || ((uintptr_t)dx & 15))
+        return af_set_error(AF_EINVAL, "conv data gradient: layer %d / alignment", layer);
+    const int W = kW[layer], tiles = n * (W / (128 / W));
+#define AF_TD(L, Op)                                                      \
+    if (layer == L) {                                                     \
+        typename Op::Args a{dz, wp, nullptr, dx, nullptr, n, W, err};     \
+        return launch<Op>(a, tiles, s, "conv data gradient (tcgen05)");   \
+    }
+    AF_TD(1, Dg1)
+    AF_TD(2, Dg2)
+#undef AF_TD
+    return AF_OK;
+}
+
+int nn_tconv_wgrad(int layer, const __nv_bfloat16* dz, const __nv_bfloat16* x, int n, float* grad, int* err,
+                   cudaStream_t s)
+{
+    if (layer < 0 || layer > 2 || n < 1 || !x || !dz || ((uintptr_t)x & 15) || ((uintptr_t)dz & 15))
+        return af_set_error(AF_EINVAL, "conv weight gradient: layer %d / alignment", layer);
+    const int W = kW[layer], tiles = n * (W / (128 / W));
+#define AF_TW(L, Op)                                                      \
+    if (layer == L) {                                                     \
+        typename Op::Args a{x, dz, grad, n, W, err};                      \
+        return launch<Op>(a, tiles, s, "conv weight gradient (tcgen05)"); \
+    }
+    AF_TW(0, Wg0)
+    AF_TW(1, Wg1)
+    AF_TW(2, Wg2)
+#undef AF_TW
+    return AF_OK;
+}

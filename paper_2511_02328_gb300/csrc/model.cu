@@ -3,8 +3,9 @@
 // paper's detector is YOLOv11n on DM-time images, Sec. 2.5; this small CNN
 // replaces it).
 //
-// The convolutions run on the tcgen05 tensor cores as implicit GEMMs (forward
-// with bias, ReLU and max pool fused; data and weight gradients), keeping the
+// The convolutions run on the tcgen05 tensor cores with their operand tiles
+// staged by TMA from channel-blocked activations (conv_tma.cu: forward with
+// bias, ReLU and max pool fused; data and weight gradients), keeping the
 // pooled activations and argmax bytes the backward pass needs.  Inference of
 // batches below a measured size runs the one-kernel mma.sync network of
 // nn_fused.cu instead, which needs no intermediate activations in memory.
@@ -37,11 +38,10 @@ constexpr int NL = 3;
 constexpr int CH[NL + 1] = {2, 16, 32, 64};
 
 struct Layer {
-    int cin, cout, H, W, k9, kp;
+    int cin, cout, H, W, k9;
     int64_t woff, boff;
 };
 
-int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 // Inference batches of at least this many images run the layered tensor-core
 // network; smaller ones the fused one-kernel network (AFGB_CNN_UMMA_MIN
@@ -57,9 +57,10 @@ struct af_model_s {
     Layer L[NL];
     int64_t fw_off = 0, fb_off = 0;
     float *d_params = nullptr, *d_grads = nullptr, *d_m = nullptr, *d_v = nullptr;
-    __nv_bfloat16* d_wt[NL] = {};      // forward weights, bf16 [cout][kp]
-    __nv_bfloat16* d_wd[NL] = {};      // data-gradient weights, bf16 [cin][9 cout] (l >= 1)
-    __nv_bfloat16* d_a[NL + 1] = {};   // pooled activations; d_a[0] unused (the input is the caller's)
+    __nv_bfloat16* d_wt[NL] = {};      // forward weights, packed for the tensor cores (nn_tpack)
+    __nv_bfloat16* d_wd[NL] = {};      // data-gradient weights, packed (l >= 1)
+    __nv_bfloat16* d_x0 = nullptr;     // the input, channel-blocked [n][1][64][64][8]
+    __nv_bfloat16* d_a[NL + 1] = {};   // pooled activations, channel-blocked; d_a[0] unused
     uint8_t* d_idx[NL] = {};           // argmax of each pool window | 4 if its maximum > 0
     __nv_bfloat16* d_da[NL + 1] = {};  // gradients w.r.t. d_a[l] (l >= 1)
     __nv_bfloat16* d_dz[NL] = {};      // gradients w.r.t. the pre-pool ReLU outputs
@@ -88,6 +89,7 @@ static void free_model(af_model_t m)
         cudaFree(m->d_da[l]);
     }
     cudaFree(m->d_err);
+    cudaFree(m->d_x0);
     cudaFree(m->d_logits);
     cudaFree(m->d_loss);
     cudaFree(m->d_cut);
@@ -132,7 +134,6 @@ try {
         y.cout = CH[l + 1];
         y.H = y.W = H;
         y.k9 = 9 * y.cin;
-        y.kp = (int)round_up(y.k9, 32);
         y.woff = off;
         off += (int64_t)y.cout * y.k9;
         y.boff = off;
@@ -156,14 +157,15 @@ try {
     for (int l = 0; l < NL; l++) {
         const Layer& y = m->L[l];
         const int64_t P = n * y.H * y.W;
-        A(&m->d_wt[l], (size_t)y.cout * y.kp * 2);
-        if (l > 0) A(&m->d_wd[l], (size_t)y.cin * 9 * y.cout * 2);
+        A(&m->d_wt[l], nn_tpack_bytes(l, 0));
+        if (l > 0) A(&m->d_wd[l], nn_tpack_bytes(l, 1));
         A(&m->d_idx[l], (size_t)P * y.cout / 4);
         A(&m->d_dz[l], (size_t)P * y.cout * 2);
         A(&m->d_a[l + 1], (size_t)P * y.cout / 4 * 2);
         A(&m->d_da[l + 1], (size_t)P * y.cout / 4 * 2);
     }
     A(&m->d_err, 16);
+    A(&m->d_x0, (size_t)n * 64 * 64 * 8 * 2);
     A(&m->d_logits, (size_t)n * 2 * 4);
     A(&m->d_loss, 16);
     A(&m->d_cut, (size_t)n * 64 * 64 * 2 * 2);
@@ -262,12 +264,13 @@ static int forward(af_model_t m, const __nv_bfloat16* x, int n, const int32_t* y
         return nn_forward_fused(x, n, P + m->L[0].woff, P + m->L[0].boff, P + m->L[1].woff, P + m->L[1].boff,
                                 P + m->L[2].woff, P + m->L[2].boff, P + m->fw_off, P + m->fb_off, m->d_logits, prob,
                                 s);
-    const __nv_bfloat16* a = x;
+    if (int rc = nn_to_cb8(x, n, m->d_x0, s)) return rc;
+    const __nv_bfloat16* a = m->d_x0;
     for (int l = 0; l < NL; l++) {
         const Layer& L = m->L[l];
-        if (int rc = nn_pack_w(P + L.woff, L.cout, L.k9, L.kp, m->d_wt[l], s)) return rc;
-        if (int rc = nn_conv_fwd(l, a, n, L.H, L.W, m->d_wt[l], P + L.boff, m->d_a[l + 1], y ? m->d_idx[l] : nullptr,
-                                 m->d_err, s))
+        if (int rc = nn_tpack(l, 0, P + L.woff, m->d_wt[l], s)) return rc;
+        if (int rc = nn_tconv_fwd(l, a, n, m->d_wt[l], P + L.boff, m->d_a[l + 1], y ? m->d_idx[l] : nullptr, m->d_err,
+                                  s))
             return rc;
         a = m->d_a[l + 1];
     }
@@ -279,17 +282,19 @@ static int forward(af_model_t m, const __nv_bfloat16* x, int n, const int32_t* y
                    m->d_grads + m->fw_off, m->d_grads + m->fb_off, m->d_da[NL], s);
 }
 
-static int backward(af_model_t m, const __nv_bfloat16* x, int n, cudaStream_t s)
+// After forward() with labels: the channel-blocked input and activations are
+// in place.
+static int backward(af_model_t m, int n, cudaStream_t s)
 {
     for (int l = NL - 1; l >= 0; l--) {
         const Layer& L = m->L[l];
         if (int rc = nn_pool_back(m->d_da[l + 1], m->d_idx[l], n, L.H, L.W, L.cout, m->d_dz[l], m->d_grads + L.boff, s))
             return rc;
-        const __nv_bfloat16* a = l ? m->d_a[l] : x;
-        if (int rc = nn_conv_wgrad(l, m->d_dz[l], a, n, L.H, L.W, m->d_grads + L.woff, m->d_err, s)) return rc;
+        const __nv_bfloat16* a = l ? m->d_a[l] : m->d_x0;
+        if (int rc = nn_tconv_wgrad(l, m->d_dz[l], a, n, m->d_grads + L.woff, m->d_err, s)) return rc;
         if (l > 0) {
-            if (int rc = nn_pack_wd(m->d_params + L.woff, L.cin, L.cout, m->d_wd[l], s)) return rc;
-            if (int rc = nn_conv_dgrad(l, m->d_dz[l], n, L.H, L.W, m->d_wd[l], m->d_da[l], m->d_err, s)) return rc;
+            if (int rc = nn_tpack(l, 1, m->d_params + L.woff, m->d_wd[l], s)) return rc;
+            if (int rc = nn_tconv_dgrad(l, m->d_dz[l], n, m->d_wd[l], m->d_da[l], m->d_err, s)) return rc;
         }
     }
     return AF_OK;
@@ -322,7 +327,7 @@ try {
     if (!d_y) return af_set_error(AF_EINVAL, "af_model_backward: labels NULL");
     cudaStream_t s = (cudaStream_t)stream;
     if (int rc = forward(m, (const __nv_bfloat16*)d_x, n, d_y, nullptr, s)) return rc;
-    if (int rc = backward(m, (const __nv_bfloat16*)d_x, n, s)) return rc;
+    if (int rc = backward(m, n, s)) return rc;
     if (d_loss) AF_CUDA(cudaMemcpyAsync(d_loss, m->d_loss, 4, cudaMemcpyDeviceToDevice, s));
     return AF_OK;
 } catch (...) {

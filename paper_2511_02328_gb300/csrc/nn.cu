@@ -1,8 +1,8 @@
 // nn.cu -- elementwise and reduction kernels of the candidate classifier
 // (replaces the paper's YOLO detector, Sec. 2.5): the 2x2 max-pool backward
 // pass, the bias gradient, the classifier head (global average pool, fully
-// connected layer, softmax cross-entropy), Adam, and the weight packing for
-// the tensor-core convolutions of conv_umma.cu.
+// connected layer, softmax cross-entropy) and Adam, on the channel-blocked
+// activations of the tensor-core convolutions (conv_tma.cu).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -12,35 +12,37 @@
 
 namespace {
 
-// dz [n][H][W][c] (bf16) = the pooled gradient routed to the argmax of each
-// 2x2 window where that maximum (a ReLU output) was positive: idx holds the
-// argmax (0..3, raster order) | 4 when the maximum was > 0.  Thread = (pooled
-// pixel, 8 channels): one 16-byte load of the pooled gradient, one 8-byte load
-// of the argmax bytes, four 16-byte stores.  The bias gradient (the sum of dz
-// over all pixels, i.e. of the routed values) is accumulated on the way:
-// per-thread sums, reduced per block in shared memory, one atomic per channel
-// and block.
+// dz [n][C/8][H][W][8] (bf16) = the pooled gradient dp [n][C/8][H/2][W/2][8]
+// routed to the argmax of each 2x2 window where that maximum (a ReLU output)
+// was positive: idx, laid out as dp, holds the argmax (0..3, raster order) |
+// 4 when the maximum was > 0.  Thread = (pooled pixel, channel block): one
+// 16-byte load of the gradient, one 8-byte load of the argmax bytes, four
+// 16-byte stores.  Warp w of the grid keeps channel block w % CB and takes
+// 32-pixel runs of every image (CB divides a block's 8 warps), so each
+// thread's bias-gradient sums (the sums of dz) stay in registers: reduced per
+// warp, then per block in shared memory, one atomic per channel and block.
 __global__ void __launch_bounds__(256) k_pool_back(const __nv_bfloat16* __restrict__ dp, const uint8_t* __restrict__ idx,
-                                                   int n, int H, int W, int c, __nv_bfloat16* __restrict__ dz,
+                                                   int n, int H, int W, int CB, __nv_bfloat16* __restrict__ dz,
                                                    float* __restrict__ db)
 {
-    __shared__ float part[256][8];
-    const int Ho = H / 2, Wo = W / 2, cg = c / 8;
-    const int64_t total = (int64_t)n * Ho * Wo * cg;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;  // a multiple of cg: each thread keeps its group
-    const int g = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) % cg);
+    __shared__ float part[8][8];
+    const int Ho = H / 2, Wo = W / 2, P = Ho * Wo, lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * 8 + wib, nw = (int64_t)gridDim.x * 8;
+    const int cb = (int)(gw % CB);
+    const int64_t total = (int64_t)n * P;  // (image, pooled pixel) pairs
     float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
-        const int64_t pp = e / cg;
-        const int xo = (int)(pp % Wo);
-        const int64_t r = pp / Wo;  // img * Ho + yo
-        const uint4 v = *reinterpret_cast<const uint4*>(dp + pp * c + 8 * g);
-        const uint2 ix = *reinterpret_cast<const uint2*>(idx + pp * c + 8 * g);
+    for (int64_t f = (gw / CB) * 32 + lane; f < total; f += (nw / CB) * 32) {
+        const int64_t img = f / P;
+        const int p = (int)(f - img * P), yo = p / Wo, xo = p - yo * Wo;
+        const int64_t e = ((img * CB + cb) * P + p) * 8;
+        const uint4 v = *reinterpret_cast<const uint4*>(dp + e);
+        const uint2 ix = *reinterpret_cast<const uint2*>(idx + e);
         const uint16_t* vv = reinterpret_cast<const uint16_t*>(&v);
         const uint8_t* ii = reinterpret_cast<const uint8_t*>(&ix);
 #pragma unroll
         for (int j = 0; j < 8; j++)
             if (ii[j] & 4) acc[j] += __bfloat162float(__ushort_as_bfloat16(vv[j]));
+        __nv_bfloat16* zp = dz + (img * CB + cb) * (int64_t)H * W * 8;
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             uint32_t w[4];
@@ -50,23 +52,28 @@ __global__ void __launch_bounds__(256) k_pool_back(const __nv_bfloat16* __restri
                 const uint32_t hi = ii[2 * j + 1] == (uint8_t)(4 | q) ? vv[2 * j + 1] : 0u;
                 w[j] = lo | (hi << 16);
             }
-            const int64_t p = (2 * r + (q >> 1)) * W + 2 * xo + (q & 1);  // (img * H + y) * W + x
-            *reinterpret_cast<uint4*>(dz + p * c + 8 * g) = make_uint4(w[0], w[1], w[2], w[3]);
+            const int y = 2 * yo + (q >> 1), x = 2 * xo + (q & 1);
+            *reinterpret_cast<uint4*>(zp + ((int64_t)y * W + x) * 8) = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
 #pragma unroll
-    for (int j = 0; j < 8; j++) part[threadIdx.x][j] = acc[j];
+    for (int j = 0; j < 8; j++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+        if (lane == 0) part[wib][j] = acc[j];
+    }
     __syncthreads();
-    if ((int)threadIdx.x < c) {
-        // channel ch = 8 gg + j is summed by the threads t with t % cg == gg
-        const int gg = threadIdx.x / 8, j = threadIdx.x % 8;
+    if ((int)threadIdx.x < 8 * CB) {
+        // channel 8 c + j is summed by the warps whose block is c
+        const int c = threadIdx.x / 8, j = threadIdx.x % 8;
         float sum = 0.f;
-        for (int t = gg; t < (int)blockDim.x; t += cg) sum += part[t][j];  // 256 % cg == 0: thread t has group t % cg
+        for (int w = c; w < 8; w += CB) sum += part[w][j];
         atomicAdd(db + threadIdx.x, sum);
     }
 }
 
-// Head: per sample, global average pool of a3 [n][64 positions][64] (bf16),
+// Head: per sample, global average pool of a3 [n][8][64 positions][8] (bf16,
+// channel-blocked: channel c at block c / 8, lane c % 8),
 // logits = g fw^T + fb, softmax; with labels, the mean cross-entropy and its
 // gradients (dfw, dfb accumulated, da3 written as bf16).
 __global__ void k_head(const __nv_bfloat16* __restrict__ a3, int n, const float* __restrict__ fw,
@@ -77,9 +84,9 @@ __global__ void k_head(const __nv_bfloat16* __restrict__ a3, int n, const float*
     const int s = blockIdx.x;
     const int ch = threadIdx.x;  // 64 threads
     __shared__ float g[64], lg[2];
-    const __nv_bfloat16* a = a3 + (int64_t)s * 64 * 64;
+    const __nv_bfloat16* a = a3 + ((int64_t)s * 8 + ch / 8) * 64 * 8 + ch % 8;
     float acc = 0.f;
-    for (int q = 0; q < 64; q++) acc += __bfloat162float(a[q * 64 + ch]);
+    for (int q = 0; q < 64; q++) acc += __bfloat162float(a[q * 8]);
     g[ch] = acc / 64.f;
     __syncthreads();
     if (ch < 2) {
@@ -109,7 +116,8 @@ __global__ void k_head(const __nv_bfloat16* __restrict__ a3, int n, const float*
     atomicAdd(dfw + 64 + ch, d1 * g[ch]);
     const float dg = (d0 * fw[ch] + d1 * fw[64 + ch]) / 64.f;
     const __nv_bfloat16 v = __float2bfloat16(dg);
-    for (int q = 0; q < 64; q++) da3[(int64_t)s * 4096 + q * 64 + ch] = v;
+    __nv_bfloat16* d = da3 + ((int64_t)s * 8 + ch / 8) * 64 * 8 + ch % 8;
+    for (int q = 0; q < 64; q++) d[q * 8] = v;
 }
 
 // Adam on fp32 master weights (Kingma & Ba 2015, bias-corrected).
@@ -124,15 +132,6 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
         v[i] = vi;
         p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
     }
-}
-
-// fp32 master weights [cout][9*cin] -> bf16 [cout][kp] (zero padding)
-__global__ void k_pack_w(const float* __restrict__ w, int cout, int k9, int kp, __nv_bfloat16* __restrict__ wt)
-{
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= cout * kp) return;
-    const int o = e / kp, k = e % kp;
-    wt[e] = __float2bfloat16(k < k9 ? w[o * k9 + k] : 0.f);
 }
 
 __global__ void k_f32_to_bf16(const float* __restrict__ x, int64_t n, __nv_bfloat16* __restrict__ y)
@@ -153,10 +152,12 @@ unsigned grid_for(int64_t n, int threads)
 int nn_pool_back(const __nv_bfloat16* dp, const uint8_t* idx, int n, int H, int W, int c, __nv_bfloat16* dz,
                  float* db, cudaStream_t s)
 {
-    if (c % 8 || c > 256 || ((uintptr_t)dp & 15) || ((uintptr_t)dz & 15) || ((uintptr_t)idx & 7))
+    const int CB = c / 8;
+    if (c % 8 || (CB != 1 && CB != 2 && CB != 4 && CB != 8) || ((uintptr_t)dp & 15) || ((uintptr_t)dz & 15) ||
+        ((uintptr_t)idx & 7))
         return af_set_error(AF_EINVAL, "pool backward: channels / alignment");
-    const int64_t total = (int64_t)n * (H / 2) * (W / 2) * (c / 8);
-    k_pool_back<<<grid_for(total, 256), 256, 0, s>>>(dp, idx, n, H, W, c, dz, db);
+    const int64_t warps = CB * (((int64_t)n * (H / 2) * (W / 2) + 31) / 32);
+    k_pool_back<<<grid_for(warps * 32, 256), 256, 0, s>>>(dp, idx, n, H, W, CB, dz, db);
     return af_cuda_check(cudaGetLastError(), "pool backward");
 }
 
@@ -173,12 +174,6 @@ int nn_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, i
     const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
     k_adam<<<grid_for(n, 256), 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
     return af_cuda_check(cudaGetLastError(), "adam");
-}
-
-int nn_pack_w(const float* w, int cout, int k9, int kp, __nv_bfloat16* wt, cudaStream_t s)
-{
-    k_pack_w<<<(cout * kp + 255) / 256, 256, 0, s>>>(w, cout, k9, kp, wt);
-    return af_cuda_check(cudaGetLastError(), "pack weights");
 }
 
 int nn_f32_to_bf16(const float* x, int64_t n, __nv_bfloat16* y, cudaStream_t s)

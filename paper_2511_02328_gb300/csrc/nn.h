@@ -17,26 +17,34 @@ enum { NN_EPI_STORE = 0, NN_EPI_BIAS_RELU = 1, NN_EPI_ATOMIC = 2 };
 int nn_gemm(int layout, int epi, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
             int splits, float* C, int ldc, const float* bias, int* err, cudaStream_t s);
 // 3x3 convolutions (pad 1) of classifier layer 0, 1, 2 (2 -> 16 -> 32 -> 64
-// channels) as implicit GEMMs on the tensor cores (conv_umma.cu):
-//   forward: x [n][H][W][cin] -> bias, ReLU, 2x2 max pool -> out [n][H/2][W/2][cout]
-//            and idx (argmax 0..3 | 4 if positive; nullable), weights wp [cout][kp]
-//   dgrad:   dz [n][H][W][cout] -> dx [n][H][W][cin], weights wd [cin][9 cout] (layers 1, 2)
-//   wgrad:   grad [cout][9 cin] += sum_p dz[p] (x) x[p + tap]
-int nn_conv_fwd(int layer, const __nv_bfloat16* x, int n, int H, int W, const __nv_bfloat16* wp, const float* bias,
-                __nv_bfloat16* out, uint8_t* idx, int* err, cudaStream_t s);
-int nn_conv_dgrad(int layer, const __nv_bfloat16* dz, int n, int H, int W, const __nv_bfloat16* wd,
-                  __nv_bfloat16* dx, int* err, cudaStream_t s);
-int nn_conv_wgrad(int layer, const __nv_bfloat16* dz, const __nv_bfloat16* x, int n, int H, int W, float* grad,
-                  int* err, cudaStream_t s);
-int nn_pack_wd(const float* w, int cin, int cout, __nv_bfloat16* wd, cudaStream_t s);
-// 2x2 max-pool backward (dz from the pooled gradient and the argmax bytes);
-// adds the bias gradient (sum of dz over pixels) into db.
+// channels, 64 / 32 / 16 pixels square) on the tensor cores with TMA-staged
+// operands (conv_tma.cu).  Tensors are channel-blocked, [n][C/8][H][W][8]
+// bf16 (the first layer's input padded to 8 channels, nn_to_cb8):
+//   forward: x -> bias, ReLU, 2x2 max pool -> out [n][cout/8][H/2][W/2][8] and
+//            idx (argmax 0..3 | 4 if positive, laid out as out; nullable)
+//   dgrad:   dz [n][cout/8][H][W][8] -> dx [n][cin/8][H][W][8] (layers 1, 2)
+//   wgrad:   grad [cout][9][cin] += sum_p dz[p] (x) x[p + tap]
+// Weights come packed by nn_tpack (nn_tpack_bytes bytes; dgrad != 0: the
+// data gradient's transposed, flipped form).  A bounded wait that runs out
+// raises *err.
+int nn_tconv_fwd(int layer, const __nv_bfloat16* x, int n, const __nv_bfloat16* wp, const float* bias,
+                 __nv_bfloat16* out, uint8_t* idx, int* err, cudaStream_t s);
+int nn_tconv_dgrad(int layer, const __nv_bfloat16* dz, int n, const __nv_bfloat16* wp, __nv_bfloat16* dx, int* err,
+                   cudaStream_t s);
+int nn_tconv_wgrad(int layer, const __nv_bfloat16* dz, const __nv_bfloat16* x, int n, float* grad, int* err,
+                   cudaStream_t s);
+size_t nn_tpack_bytes(int layer, int dgrad);
+int nn_tpack(int layer, int dgrad, const float* w, __nv_bfloat16* out, cudaStream_t s);
+// [n][64][64][2] -> [n][1][64][64][8] (channels 2..7 zero)
+int nn_to_cb8(const __nv_bfloat16* x, int n, __nv_bfloat16* out, cudaStream_t s);
+// 2x2 max-pool backward on channel-blocked tensors (dz [n][c/8][H][W][8] from
+// the pooled gradient and the argmax bytes, both [n][c/8][H/2][W/2][8]); adds
+// the bias gradient (sum of dz over pixels) into db.
 int nn_pool_back(const __nv_bfloat16* dp, const uint8_t* idx, int n, int H, int W, int c, __nv_bfloat16* dz,
                  float* db, cudaStream_t s);
 int nn_head(const __nv_bfloat16* a3, int n, const float* fw, const float* fb, float* logits, float* prob,
             const int32_t* y, float* loss, float* dfw, float* dfb, __nv_bfloat16* da3, cudaStream_t s);
 int nn_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, int step, cudaStream_t s);
-int nn_pack_w(const float* w, int cout, int k9, int kp, __nv_bfloat16* wt, cudaStream_t s);
 int nn_f32_to_bf16(const float* x, int64_t n, __nv_bfloat16* y, cudaStream_t s);
 int nn_cutouts(const uint8_t* X, int64_t nsamp, int nchan, const int32_t* D, int ndm, const int32_t* plane,
                int64_t nout, const af_cand_t* cands, int n, __nv_bfloat16* out, cudaStream_t s);

@@ -1012,7 +1012,9 @@ int af_launch_pairs_rows(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int la
                      : T->G == 3 ? (const void*)k_group_rows<3>
                                  : (const void*)k_group_rows<2>;
     if (int rc = af_ensure_smem(k1, s1)) return rc;
-    const int etiles = (int)((ly.maxlen + kET - 1) / kET);
+    // a block dshort outputs shorter than the layout needs every group's range
+    // dshort samples shorter: the grid covers only that
+    const int etiles = (int)std::max<int64_t>(1, (ly.maxlen - dshort + kET - 1) / kET);
     const unsigned long long g1 = (unsigned long long)T->np * etiles;
     if (g1 > 0x7fffffffULL) return af_set_error(AF_EINVAL, "pairs: problem too large for one grid");
     if (T->G == 4)
