@@ -25,9 +25,10 @@
 //                                                            W transposed
 //   wgrad    dW[o][t][i] = sum_p dZ[p][o] X[p + t][i]         A = dZ^T, B = X copies (MN-major)
 //
-// The first layer's two input channels are padded to one block of eight; a
-// K step of 16 then pairs two taps: the step's second core-matrix column is
-// the other tap's data, one leading-dimension offset (a row or a copy) away.
+// The first layer's input is column-expanded (nn_to_cb8): one block of eight
+// channels holding the two channels of columns x - 1, x, x + 1, so one
+// unshifted copy serves every tap, a K step of 16 takes two rows dy, and the
+// weight gradient takes the three rows dy along N.
 //
 // One warp-specialised kernel serves all three: warp 0 issues a tile's bulk
 // copies (one per lane) into an NS-deep ring; warp 6 fixes a stage's padding
@@ -54,6 +55,7 @@ namespace {
 
 constexpr int kThreads = 224;  // copy warp, MMA warp, four epilogue warps, fix warp
 constexpr int kFixWarp = 6;
+constexpr uint32_t kBackoffNs = 64;  // the copy, fix and MMA warps' polls leave issue slots to the epilogue
 
 constexpr uint32_t align1k(uint32_t b) { return (b + 1023u) / 1024u * 1024u; }
 constexpr int clampi(int v, int lo, int hi) { return v < lo ? lo : v > hi ? hi : v; }
@@ -99,15 +101,20 @@ struct Geo {
 // is block c % CB of copy dx = c / CB: the image's rows among y0 - 1 ..
 // y0 + R, one run; copy 0 lands one pixel later than it starts in memory,
 // copy 2 one pixel earlier.  Planes (one block of one copy) sit copy-major
-// (dx * COPY + cb * PLANE) or, BM, block-major ((3 cb + dx) * PLANE).
-template <int CB, int W, bool BM = false>
+// (dx * COPY + cb * PLANE) or, BM, block-major ((3 cb + dx) * PLANE).  With
+// NSH = 1 only the unshifted copy is made (the first layer's column-expanded
+// input carries its own column neighbours).
+template <int CB, int W, bool BM = false, int NSH = 3>
 struct Halo {
     using G = Geo<CB, W>;
-    static constexpr int R = G::R, NCOPY = 3 * CB;
-    static constexpr uint32_t BYTES = BM ? align1k(3 * CB * G::PLANE) : 3 * G::COPY;
+    static_assert(NSH == 1 || NSH == 3, "copies");
+    static constexpr int R = G::R, NCOPY = NSH * CB;
+    static constexpr uint32_t BYTES = NSH == 1 ? align1k(CB * G::PLANE) : BM ? align1k(3 * CB * G::PLANE) : 3 * G::COPY;
     __host__ __device__ static constexpr uint32_t plane(int dx, int cb)
     {
-        return BM ? (uint32_t)(3 * cb + dx) * G::PLANE : (uint32_t)dx * G::COPY + (uint32_t)cb * G::PLANE;
+        return NSH == 1 ? (uint32_t)cb * G::PLANE
+               : BM     ? (uint32_t)(3 * cb + dx) * G::PLANE
+                        : (uint32_t)dx * G::COPY + (uint32_t)cb * G::PLANE;
     }
     // the image's rows ylo .. ylo + nrows - 1 land at stage row rlo
     __device__ static void rows(int y0, int H, int& ylo, int& nrows, int& rlo)
@@ -121,13 +128,13 @@ struct Halo {
     {
         int ylo, nrows, rlo;
         rows(y0, H, ylo, nrows, rlo);
-        return (uint32_t)CB * (3u * (uint32_t)nrows * W * 16 - 32u);
+        return NSH == 1 ? (uint32_t)CB * nrows * W * 16 : (uint32_t)CB * (3u * (uint32_t)nrows * W * 16 - 32u);
     }
     __device__ static void copy(int c, uint32_t st, const __nv_bfloat16* in, int img, int y0, int H, uint32_t bar)
     {
         int ylo, nrows, rlo;
         rows(y0, H, ylo, nrows, rlo);
-        const int dx = c / CB, cb = c - dx * CB;
+        const int dx = NSH == 1 ? 1 : c / CB, cb = NSH == 1 ? c : c - dx * CB;
         const uint8_t* src = reinterpret_cast<const uint8_t*>(in) + (((int64_t)img * CB + cb) * H + ylo) * W * 16;
         const uint32_t dst = st + plane(dx, cb) + (uint32_t)rlo * W * 16;
         const uint32_t len = (uint32_t)nrows * W * 16;
@@ -141,14 +148,14 @@ struct Halo {
     __device__ static void fixup(uint8_t* st, int y0, int H, int lane)
     {
         const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-        for (int e = lane; e < 2 * CB * (R + 2); e += 32) {
+        for (int e = lane; NSH == 3 && e < 2 * CB * (R + 2); e += 32) {
             const int k = e / (CB * (R + 2)), rem = e - k * CB * (R + 2), cb = rem / (R + 2), r = rem - cb * (R + 2);
             *reinterpret_cast<uint4*>(st + plane(2 * k, cb) + (r * W + (k ? W - 1 : 0)) * 16) = z;
         }
         if (y0 == 0 || y0 + R == H) {
             const int r = y0 == 0 ? 0 : R + 1;  // R < H: a tile has one edge at most
-            for (int e = lane; e < 3 * CB * W; e += 32) {
-                const int c = e / W, x = e - c * W, dx = c / CB, cb = c - dx * CB;
+            for (int e = lane; e < NSH * CB * W; e += 32) {
+                const int c = e / W, x = e - c * W, dx = NSH == 1 ? 1 : c / CB, cb = NSH == 1 ? c : c - dx * CB;
                 *reinterpret_cast<uint4*>(st + plane(dx, cb) + (r * W + x) * 16) = z;
             }
         }
@@ -221,8 +228,8 @@ __global__ void __launch_bounds__(kThreads) k_tconv(const typename Op::Args args
         int g = 0;
         for (; g < mytiles; g++) {
             const int s = g % NS;
-            if (g >= NS &&
-                !__all_sync(0xffffffffu, afumma::wait_or_abort(empty0 + 8 * s, (uint32_t)(g / NS - 1) & 1u, abort)))
+            if (g >= NS && !__all_sync(0xffffffffu, afumma::wait_or_abort(empty0 + 8 * s, (uint32_t)(g / NS - 1) & 1u,
+                                                                           abort, kBackoffNs)))
                 break;
             if (lane == 0) afptx::mbar_arrive_expect_tx(full0 + 8 * s, op.tx(tile_of(g)));
             __syncwarp();
@@ -242,7 +249,8 @@ __global__ void __launch_bounds__(kThreads) k_tconv(const typename Op::Args args
         int g = 0;
         for (; g < mytiles; g++) {
             const int s = g % NS;
-            if (!__all_sync(0xffffffffu, afumma::wait_or_abort(full0 + 8 * s, (uint32_t)(g / NS) & 1u, abort))) break;
+            if (!__all_sync(0xffffffffu, afumma::wait_or_abort(full0 + 8 * s, (uint32_t)(g / NS) & 1u, abort, kBackoffNs)))
+                break;
             op.fixup(sm + Op::RB + (size_t)s * Op::SSTAGE, tile_of(g), lane);
             __syncwarp();
             if (lane == 0) afptx::mbar_arrive(ready0 + 8 * s);
@@ -254,8 +262,8 @@ __global__ void __launch_bounds__(kThreads) k_tconv(const typename Op::Args args
             const int s = g % NS, b = g % NACC;
             bool ok = true;
             if (Op::PER_TILE && g >= NACC)  // the epilogue has read this accumulator's previous tile
-                ok = afumma::wait_or_abort(tempty0 + 8 * b, (uint32_t)(g / NACC - 1) & 1u, abort);
-            ok = ok && afumma::wait_or_abort(ready0 + 8 * s, (uint32_t)(g / NS) & 1u, abort);
+                ok = afumma::wait_or_abort(tempty0 + 8 * b, (uint32_t)(g / NACC - 1) & 1u, abort, kBackoffNs);
+            ok = ok && afumma::wait_or_abort(ready0 + 8 * s, (uint32_t)(g / NS) & 1u, abort, kBackoffNs);
             if (!__all_sync(0xffffffffu, ok)) break;
             afumma::fence_after_sync();
             if (lane == 0) {
@@ -321,14 +329,17 @@ __device__ __forceinline__ uint32_t pool_step(float (&m)[16])
 template <int CB, int N, int W, bool POOL>
 struct ConvOp {
     using G = Geo<CB, W>;
-    static constexpr bool PAIR = CB == 1;
-    static_assert(PAIR || CB % 2 == 0, "input channel blocks: 1 or even");
+    // CB == 1: the first layer's column-expanded input (one block: the 2
+    // channels of columns x - 1, x, x + 1, two zeros), one unshifted copy
+    static constexpr bool EXP = CB == 1;
+    using H3 = Halo<CB, W, false, EXP ? 1 : 3>;
+    static_assert(EXP || CB % 2 == 0, "input channel blocks: 1 or even");
     static_assert(N % 16 == 0 && N <= 128, "output channels");
-    static constexpr int R = G::R, STEPS = PAIR ? 5 : 9 * CB / 2;
+    static constexpr int R = G::R, STEPS = EXP ? 2 : 9 * CB / 2;
     static constexpr uint32_t LBO_B = N / 8 * 128;  // K halves of a weight step
     static constexpr uint32_t RB = align1k(STEPS * 2 * LBO_B);
-    static constexpr uint32_t SSTAGE = 3 * G::COPY, SLACK = 0;
-    static constexpr int NCOPY = Halo<CB, W>::NCOPY;
+    static constexpr uint32_t SSTAGE = H3::BYTES, SLACK = 0;
+    static constexpr int NCOPY = H3::NCOPY;
     static constexpr int NS = clampi(49152 / (int)SSTAGE, 2, 4);  // shallow: more blocks (epilogue warps) per SM
     static constexpr int NACC = 4, NCOL = N;
     static constexpr bool PER_TILE = true;
@@ -350,31 +361,28 @@ struct ConvOp {
         for (int i = tid; i < (int)(STEPS * 2 * LBO_B / 16); i += kThreads)
             reinterpret_cast<uint4*>(res)[i] = __ldg(src + i);
     }
-    __device__ uint32_t tx(int tile) const { return Halo<CB, W>::tx((tile % (a.H / R)) * R, a.H); }
+    __device__ uint32_t tx(int tile) const { return H3::tx((tile % (a.H / R)) * R, a.H); }
     __device__ void copy(int c, uint32_t st, int tile, uint32_t bar) const
     {
         const int tpi = a.H / R, img = tile / tpi;
-        Halo<CB, W>::copy(c, st, a.in, img, (tile - img * tpi) * R, a.H, bar);
+        H3::copy(c, st, a.in, img, (tile - img * tpi) * R, a.H, bar);
     }
-    __device__ void fixup(uint8_t* st, int tile, int lane) const
-    {
-        Halo<CB, W>::fixup(st, (tile % (a.H / R)) * R, a.H, lane);
-    }
+    __device__ void fixup(uint8_t* st, int tile, int lane) const { H3::fixup(st, (tile % (a.H / R)) * R, a.H, lane); }
     // Step s: A = the tap's copy from the tap's row, its K halves one LBO apart
-    // (two channel blocks, or for PAIR two taps); B = the step's weights.
+    // (two channel blocks; for EXP two rows dy); B = the step's weights.
     __device__ void mma(uint32_t st, uint32_t res, uint32_t tmem, int) const
     {
         constexpr uint32_t idesc = afumma::idesc_bf16(128, N, 0, 0);
 #pragma unroll
         for (int s = 0; s < STEPS; s++) {
             uint32_t a0, lbo;
-            if constexpr (PAIR) {
-                // (0,dx)+(1,dx) for dx = 0, 1, 2; (2,0)+(2,1); (2,1)+(2,2) with zero weights in its first half
-                a0 = s < 3 ? st + s * G::COPY : st + (s - 3) * G::COPY + 2 * W * 16;
-                lbo = s < 3 ? W * 16 : G::COPY;
+            if constexpr (EXP) {
+                // rows (0, 1), then (1, 2) with zero weights in the first half
+                a0 = st + s * W * 16;
+                lbo = W * 16;
             } else {
                 const int t = s / (CB / 2), j = s % (CB / 2);
-                a0 = st + (t % 3) * G::COPY + 2 * j * G::PLANE + (t / 3) * W * 16;
+                a0 = st + H3::plane(t % 3, 2 * j) + (t / 3) * W * 16;
                 lbo = G::PLANE;
             }
             afumma::mma_bf16(tmem, afumma::smem_desc(a0, lbo, 128),
@@ -421,12 +429,14 @@ struct ConvOp {
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
                     const float4 b4 = __ldg(bv + k);
-                    m[4 * k] = fmaxf(__uint_as_float(v[4 * k]) + b4.x, 0.f);
-                    m[4 * k + 1] = fmaxf(__uint_as_float(v[4 * k + 1]) + b4.y, 0.f);
-                    m[4 * k + 2] = fmaxf(__uint_as_float(v[4 * k + 2]) + b4.z, 0.f);
-                    m[4 * k + 3] = fmaxf(__uint_as_float(v[4 * k + 3]) + b4.w, 0.f);
+                    m[4 * k] = __uint_as_float(v[4 * k]) + b4.x;
+                    m[4 * k + 1] = __uint_as_float(v[4 * k + 1]) + b4.y;
+                    m[4 * k + 2] = __uint_as_float(v[4 * k + 2]) + b4.z;
+                    m[4 * k + 3] = __uint_as_float(v[4 * k + 3]) + b4.w;
                 }
-                // row maxima (the right-hand pixel in the next lane); hx: where it won
+                // pooled before the ReLU (it commutes with the maximum; where the
+                // maximum is positive the argmax is the ReLU outputs' one, elsewhere
+                // no gradient is routed); row maxima (the right-hand pixel in the next lane); hx: where it won
                 const uint32_t hx = pool_step<1>(m);
                 uint32_t hx_low = 0u, vy = 0u;  // the lower row's hx; where the lower row won
                 if constexpr (W == 16) {
@@ -454,6 +464,8 @@ struct ConvOp {
                 }
                 if (lead) {
                     const int64_t e0 = (((int64_t)img * (N / 8) + c0 / 8) * oplane + po) * 8;
+#pragma unroll
+                    for (int i = 0; i < 16; i++) m[i] = fmaxf(m[i], 0.f);
 #pragma unroll
                     for (int h = 0; h < 2; h++) {
                         const float* u = m + 8 * h;
@@ -492,16 +504,18 @@ struct ConvOp {
 //     block's three copies back to back, tap (dy, dx) starts (dy + (R + 2) dx)
 //     rows after the first, so N = 8 NJ columns (NJ = 2 (R + 2) + 3 rounded up
 //     to even) at a stride of one row take every tap in one MMA (the columns
-//     of dy >= 3 are read and dropped); A is read once for all taps.
+//     of dy >= 3 are read and dropped); A is read once for all taps.  The
+//     first layer (CB = 1) reads its column-expanded input unshifted: N = 32
+//     columns, rows dy = 0 .. 3, each 8 channels (dx, c) for dx < 3, c < 2.
 //   else: one MMA per tap, N = the block's channels.
 template <int CB, int ZB, int W, bool TAPN>
 struct WgradOp {
     using G = Geo<CB, W>;
-    using H3 = Halo<CB, W, TAPN>;
+    using H3 = Halo<CB, W, (TAPN && CB > 1), (CB == 1 ? 1 : 3)>;
     static_assert(CB == 1 || CB % 2 == 0, "input channel blocks: 1 or even");
     static_assert(TAPN || CB >= 2, "the per-tap form needs N = 8 CB >= 16");
     static constexpr int R = G::R, CIN = CB == 1 ? 2 : CB * 8, COUT = ZB * 8;
-    static constexpr int NJ = (2 * (R + 2) + 3 + 1) / 2 * 2;
+    static constexpr int NJ = CB == 1 ? 4 : (2 * (R + 2) + 3 + 1) / 2 * 2;
     static constexpr int NPM = TAPN ? 8 * NJ : CB * 8;  // N of one MMA
     static constexpr int NMMA = TAPN ? CB : 9;          // MMAs per K step
     static_assert(NPM % 16 == 0 && NPM <= 256, "MMA width");
@@ -582,7 +596,12 @@ struct WgradOp {
             for (int jj = 0; jj < 16; jj++) {
                 const int col = c0 + jj;
                 int t, i;
-                if constexpr (TAPN) {
+                if constexpr (CB == 1) {
+                    const int dy = col >> 3, dx = (col & 7) >> 1;
+                    i = col & 1;
+                    if (dy >= 3 || dx >= 3) continue;
+                    t = 3 * dy + dx;
+                } else if constexpr (TAPN) {
                     const int k = col / NPM, r = col - k * NPM, j = r >> 3, dx = j / (R + 2), dy = j - dx * (R + 2);
                     i = 8 * k + (r & 7);
                     if (dy >= 3 || dx >= 3 || i >= CIN) continue;
@@ -603,7 +622,8 @@ struct WgradOp {
 // the K half's block.  Forward: rows o, K = (tap t, input channel i).  Data
 // gradient: rows i, K = (tap t, o) with the taps flipped, W'[i][t][o] =
 // W[o][8 - t][i].  cbk = channel blocks of K per tap (1: the first layer's
-// tap pairs, the zero half of the last pair included).
+// column-expanded input, two K steps of rows (0, 1) and (1, 2), the repeated
+// row 1 with zero weights).
 __global__ void k_tpack(const float* __restrict__ w, int cin, int cout, int cbk, int nrows, int dgrad, int total,
                         __nv_bfloat16* __restrict__ out)
 {
@@ -612,8 +632,11 @@ __global__ void k_tpack(const float* __restrict__ w, int cin, int cout, int cbk,
     const int k = e & 7, row = (e >> 3) % nrows, kc = (e / (8 * nrows)) & 1, s = e / (16 * nrows);
     int t, c;
     if (cbk == 1) {
-        t = s < 3 ? 3 * kc + s : s == 3 ? 6 + kc : (kc ? 8 : -1);
-        c = k;
+        // column-expanded input: K half kc of step s is row dy = s + kc (step 1's
+        // first half repeats row 1 with zero weights), channel k = (dx, c)
+        const int dy = s + kc;
+        t = (s == 1 && kc == 0) || k >= 6 ? -1 : 3 * dy + (k >> 1);
+        c = k & 1;
     } else {
         t = s / (cbk / 2);
         c = (2 * (s % (cbk / 2)) + kc) * 8 + k;
@@ -626,11 +649,15 @@ __global__ void k_tpack(const float* __restrict__ w, int cin, int cout, int cbk,
     out[e] = __float2bfloat16(v);
 }
 
-// [n][H][W][2] bf16 (the classifier's input) -> [n][1][H][W][8], channels 2..7 zero
+// [n][64][64][2] bf16 (the classifier's input) -> column-expanded
+// [n][1][64][64][8]: pixel (y, x) holds the two channels of columns x - 1, x,
+// x + 1 (zero outside the image), then two zeros.
 __global__ void k_to_cb8(const uint32_t* __restrict__ x, int64_t npix, uint4* __restrict__ out)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = make_uint4(__ldg(x + i), 0u, 0u, 0u);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i & 63);
+        out[i] = make_uint4(c > 0 ? __ldg(x + i - 1) : 0u, __ldg(x + i), c < 63 ? __ldg(x + i + 1) : 0u, 0u);
+    }
 }
 
 // ------------------------------------------------------------ host side
@@ -710,7 +737,7 @@ int nn_tpack(int layer, int dgrad, const float* w, __nv_bfloat16* out, cudaStrea
 {
     if (layer < 0 || layer > 2 || (dgrad && layer == 0)) return af_set_error(AF_EINVAL, "conv pack: layer %d", layer);
     const int cin = kCin[layer], cout = kCout[layer];
-    const int cbk = dgrad ? cout / 8 : (cin < 8 ? 1 : cin / 8), nrows = dgrad ? cin : cout;
+    const int cbk = dgrad ? cout / 8 : (cin < 8 ? 1 : cin / 8), nrows = dgrad ? cin : cout;  // cbk 1: expanded
     const int total = (int)(nn_tpack_bytes(layer, dgrad) / 2);
     k_tpack<<<(total + 255) / 256, 256, 0, s>>>(w, cin, cout, cbk, nrows, dgrad, total, out);
     return af_cuda_check(cudaGetLastError(), "conv pack");

@@ -112,14 +112,18 @@ __device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity)
 // Waits for a phase by spinning on test_wait (a pipeline hand-off is a few
 // hundred cycles; a suspended try_wait can return much later than the phase
 // completes), giving up after kWaitNs of wall time or when another thread
-// gave up; a wait that gives up raises the block's abort flag.
+// gave up; a wait that gives up raises the block's abort flag.  backoff_ns > 0
+// sleeps that long between polls after the first few (for warps whose
+// latency matters less than the issue slots they would take from others).
 constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s
-__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort)
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort,
+                                              uint32_t backoff_ns = 0)
 {
     if (mbar_test_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     for (uint32_t i = 1;; i++) {
         if (mbar_test_wait(bar, parity)) return true;
+        if (backoff_ns && i > 4) __nanosleep(backoff_ns);
         if ((i & 255) == 0) {
             if (*abort) return false;
             if (globaltimer_ns() - t0 > kWaitNs) break;
