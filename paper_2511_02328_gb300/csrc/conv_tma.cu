@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kThreads) k_tconv(const typename Op::Args args
     __shared__ uint32_t tslot;
     __shared__ int abort_flag;
     __shared__ __align__(16) float xv[32 * 16];  // pool exchange between epilogue warps
-    __shared__ uint32_t xq[32];
+    __shared__ uint32_t xq[64];
     constexpr int NS = Op::NS, NACC = Op::NACC;
     constexpr uint32_t TCOLS = pow2_cols(NACC * Op::NCOL);
     static_assert(Op::NCOPY <= 32, "one bulk copy per producer lane");
@@ -305,22 +305,6 @@ __global__ void __launch_bounds__(kThreads) k_tconv(const typename Op::Args args
 }
 
 // ------------------------------------------------------------ convolution
-// 2x2 max pool, one step: the maximum of this lane's 16 values and those of
-// the lane SH away; bit i of the result is set where the other lane's value
-// is strictly larger (ties keep this lane's, the earlier in raster order).
-template <int SH>
-__device__ __forceinline__ uint32_t pool_step(float (&m)[16])
-{
-    uint32_t won = 0u;
-#pragma unroll
-    for (int i = 0; i < 16; i++) {
-        const float o = __shfl_xor_sync(0xffffffffu, m[i], SH);
-        won |= (o > m[i] ? 1u : 0u) << i;
-        m[i] = fmaxf(m[i], o);
-    }
-    return won;
-}
-
 // Forward (POOL: + bias, ReLU, 2x2 max pool with argmax) or data gradient
 // (plain store) of a 3x3 convolution over CB input channel blocks (1: the
 // two-channel first layer, taps paired), N output channels, W columns.
@@ -413,77 +397,100 @@ struct ConvOp {
                     *reinterpret_cast<uint4*>(a.out + (((int64_t)img * (N / 8) + c0 / 8 + h) * plane + pix) * 8) = o;
                 }
             }
+        } else if (a.idx) {
+            pool_epilogue<true>(img, y0, yl, x, quarter, lane, taddr, xv, xq);
         } else {
-            const int Ho = a.H / 2, Wo = W / 2;
-            const bool top = (yl & 1) == 0, even = (x & 1) == 0, lead = top && even;
-            const int wi = (yl >> 1) * Wo + (x >> 1);  // the window's index in the tile, 0..31
-            const int64_t po = (int64_t)(y0 / 2 + (yl >> 1)) * Wo + (x >> 1), oplane = (int64_t)Ho * Wo;
-            const bool train = a.idx != nullptr;
+            pool_epilogue<false>(img, y0, yl, x, quarter, lane, taddr, xv, xq);
+        }
+    }
+
+    // Bias, 2 x 2 max pool and ReLU (pooled before the ReLU: it commutes with
+    // the maximum; where the maximum is positive the argmax is the ReLU
+    // outputs' one, elsewhere no gradient is routed) and, in training, the
+    // argmax byte.  Per chunk of 16 channels the two lanes of a horizontal
+    // pixel pair split the chunk (the even column keeps channels 0-7, the odd
+    // one 8-15), so every later step handles 8 channels per lane; the upper
+    // row of a window finishes it, the row below coming through a lane
+    // shuffle (W = 16: 16 lanes on) or, from another warp, through shared
+    // memory (slot 32 p + lane of warp pair p, 8 floats and the row's bits).
+    template <bool TRAIN>
+    __device__ void pool_epilogue(int img, int y0, int yl, int x, int quarter, int lane, uint32_t taddr, float* xv,
+                                  uint32_t* xq) const
+    {
+        const int Ho = a.H / 2, Wo = W / 2;
+        const bool top = (yl & 1) == 0, odd = (x & 1) != 0;
+        const int64_t po = (int64_t)(y0 / 2 + (yl >> 1)) * Wo + (x >> 1), oplane = (int64_t)Ho * Wo;
+        const int slot = 32 * (W == 64 ? (quarter & 1) : (quarter >> 1)) + lane;
 #pragma unroll 1
-            for (int c0 = 0; c0 < N; c0 += 16) {
-                uint32_t v[16];
-                afumma::ld_32x32b_x16(taddr + (uint32_t)c0, v);
-                afumma::wait_ld();
-                float m[16];
-                const float4* bv = reinterpret_cast<const float4*>(a.bias + c0);
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            uint32_t v[16];
+            afumma::ld_32x32b_x16(taddr + (uint32_t)c0, v);
+            afumma::wait_ld();
+            float m[16];
+            const float4* bv = reinterpret_cast<const float4*>(a.bias + c0);
 #pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    const float4 b4 = __ldg(bv + k);
-                    m[4 * k] = __uint_as_float(v[4 * k]) + b4.x;
-                    m[4 * k + 1] = __uint_as_float(v[4 * k + 1]) + b4.y;
-                    m[4 * k + 2] = __uint_as_float(v[4 * k + 2]) + b4.z;
-                    m[4 * k + 3] = __uint_as_float(v[4 * k + 3]) + b4.w;
+            for (int k = 0; k < 4; k++) {
+                const float4 b4 = __ldg(bv + k);
+                m[4 * k] = __uint_as_float(v[4 * k]) + b4.x;
+                m[4 * k + 1] = __uint_as_float(v[4 * k + 1]) + b4.y;
+                m[4 * k + 2] = __uint_as_float(v[4 * k + 2]) + b4.z;
+                m[4 * k + 3] = __uint_as_float(v[4 * k + 3]) + b4.w;
+            }
+            // the pair's row maximum of this lane's 8 channels; hx bit i: the
+            // right pixel strictly larger (a tie keeps the left, earlier in raster order)
+            float h[8];
+            uint32_t hx = 0u;
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const float keep = odd ? m[i + 8] : m[i], give = odd ? m[i] : m[i + 8];
+                const float other = __shfl_xor_sync(0xffffffffu, give, 1);
+                if (TRAIN) hx |= ((odd ? keep > other : other > keep) ? 1u : 0u) << i;
+                h[i] = fmaxf(keep, other);
+            }
+            // the row below: vy bit i where it is strictly larger; hx_low its hx
+            uint32_t vy = 0u, hx_low = 0u;
+            if constexpr (W == 16) {
+                if (TRAIN) hx_low = __shfl_xor_sync(0xffffffffu, hx, 16);
+#pragma unroll
+                for (int i = 0; i < 8; i++) {
+                    const float o = __shfl_xor_sync(0xffffffffu, h[i], 16);
+                    if (TRAIN) vy |= (o > h[i] ? 1u : 0u) << i;
+                    h[i] = fmaxf(h[i], o);
                 }
-                // pooled before the ReLU (it commutes with the maximum; where the
-                // maximum is positive the argmax is the ReLU outputs' one, elsewhere
-                // no gradient is routed); row maxima (the right-hand pixel in the next lane); hx: where it won
-                const uint32_t hx = pool_step<1>(m);
-                uint32_t hx_low = 0u, vy = 0u;  // the lower row's hx; where the lower row won
-                if constexpr (W == 16) {
-                    hx_low = __shfl_xor_sync(0xffffffffu, hx, 16);  // the row below: 16 lanes on
-                    vy = pool_step<16>(m);
-                } else {
-                    // the row below sits in another warp: through shared memory (word i of
-                    // window wi at xv[32 i + wi], conflict-free)
-                    if (!top && even) {
-#pragma unroll
-                        for (int i = 0; i < 16; i++) xv[32 * i + wi] = m[i];
-                        xq[wi] = hx;
-                    }
-                    epi_sync();
-                    if (lead) {
-#pragma unroll
-                        for (int i = 0; i < 16; i++) {
-                            const float o = xv[32 * i + wi];
-                            vy |= (o > m[i] ? 1u : 0u) << i;
-                            m[i] = fmaxf(m[i], o);
-                        }
-                        hx_low = xq[wi];
-                    }
-                    epi_sync();
+            } else {
+                float4* sv = reinterpret_cast<float4*>(xv) + 2 * slot;
+                if (!top) {
+                    sv[0] = make_float4(h[0], h[1], h[2], h[3]);
+                    sv[1] = make_float4(h[4], h[5], h[6], h[7]);
+                    if (TRAIN) xq[slot] = hx;
                 }
-                if (lead) {
-                    const int64_t e0 = (((int64_t)img * (N / 8) + c0 / 8) * oplane + po) * 8;
+                epi_sync();
+                if (top) {
+                    const float4 l0 = sv[0], l1 = sv[1];
+                    const float lo[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
 #pragma unroll
-                    for (int i = 0; i < 16; i++) m[i] = fmaxf(m[i], 0.f);
-#pragma unroll
-                    for (int h = 0; h < 2; h++) {
-                        const float* u = m + 8 * h;
-                        *reinterpret_cast<uint4*>(a.out + e0 + h * oplane * 8) =
-                            make_uint4(pack_bf16(u[0], u[1]), pack_bf16(u[2], u[3]), pack_bf16(u[4], u[5]),
-                                       pack_bf16(u[6], u[7]));
-                        if (train) {
-                            // argmax in raster order: (lower row won ? 2 + its column : this row's column)
-                            uint32_t w2[2] = {0u, 0u};
-#pragma unroll
-                            for (int k = 0; k < 8; k++) {
-                                const int i = 8 * h + k;
-                                const uint32_t q = ((vy >> i) & 1u) ? 2u | ((hx_low >> i) & 1u) : (hx >> i) & 1u;
-                                w2[k >> 2] |= (q | (u[k] > 0.f ? 4u : 0u)) << (8 * (k & 3));
-                            }
-                            *reinterpret_cast<uint2*>(a.idx + e0 + h * oplane * 8) = make_uint2(w2[0], w2[1]);
-                        }
+                    for (int i = 0; i < 8; i++) {
+                        if (TRAIN) vy |= (lo[i] > h[i] ? 1u : 0u) << i;
+                        h[i] = fmaxf(h[i], lo[i]);
                     }
+                    if (TRAIN) hx_low = xq[slot];
+                }
+                epi_sync();
+            }
+            if (top) {
+                const int64_t e0 = (((int64_t)img * (N / 8) + c0 / 8 + (odd ? 1 : 0)) * oplane + po) * 8;
+                *reinterpret_cast<uint4*>(a.out + e0) =
+                    make_uint4(pack_bf16(fmaxf(h[0], 0.f), fmaxf(h[1], 0.f)), pack_bf16(fmaxf(h[2], 0.f), fmaxf(h[3], 0.f)),
+                               pack_bf16(fmaxf(h[4], 0.f), fmaxf(h[5], 0.f)), pack_bf16(fmaxf(h[6], 0.f), fmaxf(h[7], 0.f)));
+                if (TRAIN) {
+                    // argmax in raster order: (lower row won ? 2 + its column : this row's column), | 4 if positive
+                    uint32_t w2[2] = {0u, 0u};
+#pragma unroll
+                    for (int k = 0; k < 8; k++) {
+                        const uint32_t q = ((vy >> k) & 1u) ? 2u | ((hx_low >> k) & 1u) : (hx >> k) & 1u;
+                        w2[k >> 2] |= (q | (h[k] > 0.f ? 4u : 0u)) << (8 * (k & 3));
+                    }
+                    *reinterpret_cast<uint2*>(a.idx + e0) = make_uint2(w2[0], w2[1]);
                 }
             }
         }
