@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kThreads) k_tconv(const typename Op::Args args
 
     if (tid == 0) {
         for (int s = 0; s < NS; s++) {
-            afptx::mbar_init(full0 + 8 * s, 1);
+            afptx::mbar_init(full0 + 8 * s, Op::FULL_ARRIVALS);
             afptx::mbar_init(ready0 + 8 * s, 1);
             afptx::mbar_init(empty0 + 8 * s, 1);
         }
@@ -291,7 +291,31 @@ __global__ void __launch_bounds__(kThreads) k_tconv(const typename Op::Args args
                 afptx::mbar_arrive(tempty0 + 8 * b);
             }
         } else if (mytiles > 0) {
-            const bool ok = afumma::wait_or_abort(tfull0, 0u, abort);
+            bool ok = true;
+            if constexpr (Op::UNPOOL) {
+                // these warps build each tile's stage of the output gradient from
+                // the pooled one once the stage is free, then arrive on its full
+                // barrier: two groups of 64 threads take alternate tiles, each
+                // loading its next tile's inputs before it stores this one's
+                const int t = tid - 64, grp = t >> 6, tg = t & 63;
+                float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                typename Op::Pooled pre;
+                if (grp < mytiles) op.unpool_load(tile_of(grp), tg, pre);
+                for (int g = grp; g < mytiles; g += 2) {
+                    const int s = g % NS;
+                    if (g >= NS && !afumma::wait_or_abort(empty0 + 8 * s, (uint32_t)(g / NS - 1) & 1u, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    const typename Op::Pooled cur = pre;
+                    if (g + 2 < mytiles) op.unpool_load(tile_of(g + 2), tg, pre);
+                    op.unpool_store(sm + Op::RB + (size_t)s * Op::SSTAGE, tg, cur, acc);
+                    afptx::fence_proxy_async();
+                    afptx::mbar_arrive(full0 + 8 * s);
+                }
+                op.unpool_finish(t, lane, acc);
+            }
+            ok = afumma::wait_or_abort(tfull0, 0u, abort) && ok;
             if (!epi_sync_any(!ok || *abort)) {
                 afumma::fence_after_sync();
                 op.final(tmem, quarter, lane);
@@ -326,7 +350,8 @@ struct ConvOp {
     static constexpr int NCOPY = H3::NCOPY;
     static constexpr int NS = clampi(49152 / (int)SSTAGE, 2, 4);  // shallow: more blocks (epilogue warps) per SM
     static constexpr int NACC = 4, NCOL = N;
-    static constexpr bool PER_TILE = true;
+    static constexpr bool PER_TILE = true, UNPOOL = false;
+    static constexpr int FULL_ARRIVALS = 1;
     struct Args {
         const __nv_bfloat16* in;  // [n][CB][H][W][8]
         const __nv_bfloat16* wp;  // packed weights, STEPS * 2 * LBO_B bytes
@@ -515,7 +540,7 @@ struct ConvOp {
 //     first layer (CB = 1) reads its column-expanded input unshifted: N = 32
 //     columns, rows dy = 0 .. 3, each 8 channels (dx, c) for dx < 3, c < 2.
 //   else: one MMA per tap, N = the block's channels.
-template <int CB, int ZB, int W, bool TAPN>
+template <int CB, int ZB, int W, bool TAPN, bool UNPOOL_ = false>
 struct WgradOp {
     using G = Geo<CB, W>;
     using H3 = Halo<CB, W, (TAPN && CB > 1), (CB == 1 ? 1 : 3)>;
@@ -529,7 +554,12 @@ struct WgradOp {
     static_assert(COUT <= 128, "output channels");
     static constexpr uint32_t PLANE_Z = (uint32_t)R * W * 16, ZREG = align1k(PLANE_Z * ZB);
     static constexpr uint32_t RB = 0, SSTAGE = ZREG + H3::BYTES;
-    static constexpr int NCOPY = H3::NCOPY + ZB;
+    // UNPOOL: dZ is not read from memory but built in each stage from the
+    // pooled gradient dP and the argmax bytes (the pooling layer's backward
+    // pass), by the epilogue warps, which are otherwise idle until the end
+    static constexpr bool UNPOOL = UNPOOL_;
+    static constexpr int FULL_ARRIVALS = UNPOOL ? 1 + 64 : 1;
+    static constexpr int NCOPY = H3::NCOPY + (UNPOOL ? 0 : ZB);
     static constexpr uint32_t SLACK = 16 * PLANE_Z > SSTAGE ? 16 * PLANE_Z - SSTAGE : 0;
     static constexpr int NS = clampi(65536 / (int)SSTAGE, 2, 4);
     static constexpr int NACC = 1, NCOL = NMMA * NPM;
@@ -537,16 +567,73 @@ struct WgradOp {
     static constexpr bool PER_TILE = false;
     struct Args {
         const __nv_bfloat16* x;   // [n][CB][H][W][8]
-        const __nv_bfloat16* dz;  // [n][ZB][H][W][8]
+        const __nv_bfloat16* dz;  // [n][ZB][H][W][8] (not UNPOOL)
         float* grad;              // [COUT][9][CIN], accumulated
         int n, H;
         int* err;
+        const __nv_bfloat16* dp;  // UNPOOL: pooled gradient [n][ZB][H/2][W/2][8]
+        const uint8_t* idx;       // UNPOOL: argmax 0..3 | 4 if positive, laid out as dp
+        float* db;                // UNPOOL: [COUT] bias gradient (the sum of dZ), accumulated
     };
     const Args a;
     __device__ WgradOp(const Args& a_) : a(a_) {}
     __device__ int ntiles() const { return a.n * (a.H / R); }
     __device__ void resident(uint8_t*, int) const {}
-    __device__ uint32_t tx(int tile) const { return H3::tx((tile % (a.H / R)) * R, a.H) + ZB * PLANE_Z; }
+    __device__ uint32_t tx(int tile) const
+    {
+        return H3::tx((tile % (a.H / R)) * R, a.H) + (UNPOOL ? 0u : ZB * PLANE_Z);
+    }
+    // UNPOOL: thread tg (< 64) of a group of the epilogue warps handles item
+    // tg of a tile, (pooled pixel tg / ZB of the tile's R / 2 pooled rows,
+    // block tg % ZB): its gradient goes to the window's argmax where the
+    // maximum was positive, zeros to the other three pixels; acc sums the
+    // routed values of block tg % ZB (the bias gradient).
+    struct Pooled {
+        uint4 v;   // 8 channels of the pooled gradient
+        uint2 ix;  // their argmax bytes
+    };
+    static constexpr int ITEMS = ZB * (R / 2) * (W / 2);
+    static_assert(!UNPOOL || ITEMS == 64, "one item per thread of a 64-thread group");
+    __device__ void unpool_load(int tile, int tg, Pooled& p) const
+    {
+        const int tpi = a.H / R, img = tile / tpi, y0 = (tile - img * tpi) * R;
+        const int zb = tg % ZB, pp = tg / ZB, pr = pp / (W / 2), xo = pp - pr * (W / 2);
+        const int64_t e = ((((int64_t)img * ZB + zb) * (a.H / 2) + y0 / 2 + pr) * (W / 2) + xo) * 8;
+        p.v = __ldg(reinterpret_cast<const uint4*>(a.dp + e));
+        p.ix = __ldg(reinterpret_cast<const uint2*>(a.idx + e));
+    }
+    __device__ void unpool_store(uint8_t* st, int tg, const Pooled& p, float (&acc)[8]) const
+    {
+        const int zb = tg % ZB, pp = tg / ZB, pr = pp / (W / 2), xo = pp - pr * (W / 2);
+        const uint16_t* vv = reinterpret_cast<const uint16_t*>(&p.v);
+        const uint8_t* ii = reinterpret_cast<const uint8_t*>(&p.ix);
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            if (ii[j] & 4) acc[j] += __bfloat162float(__ushort_as_bfloat16(vv[j]));
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            uint32_t w[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint32_t lo = ii[2 * j] == (uint8_t)(4 | q) ? vv[2 * j] : 0u;
+                const uint32_t hi = ii[2 * j + 1] == (uint8_t)(4 | q) ? vv[2 * j + 1] : 0u;
+                w[j] = lo | (hi << 16);
+            }
+            const int r = 2 * pr + (q >> 1), x = 2 * xo + (q & 1);
+            *reinterpret_cast<uint4*>(st + zb * PLANE_Z + (r * W + x) * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+    // The bias gradient: the lanes of a warp with one block reduce, then one
+    // atomic per channel and warp.
+    __device__ void unpool_finish(int t, int lane, float (&acc)[8]) const
+    {
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+#pragma unroll
+            for (int o = 16; o >= ZB; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+            if (lane < ZB) atomicAdd(a.db + (t % ZB) * 8 + j, acc[j]);  // t % ZB = lane % ZB
+        }
+    }
     // copies 0 .. 3 CB - 1: the shifted copies of X; then one per dZ block
     __device__ void copy(int c, uint32_t st, int tile, uint32_t bar) const
     {
@@ -728,6 +815,7 @@ using Fwd2 = ConvOp<4, 64, 16, true>;
 using Dg1 = ConvOp<4, 16, 32, false>;
 using Dg2 = ConvOp<8, 32, 16, false>;
 using Wg0 = WgradOp<1, 2, 64, true>;
+using Wg0u = WgradOp<1, 2, 64, true, true>;  // layer 0's output gradient built from the pooled one
 using Wg1 = WgradOp<2, 4, 32, true>;
 using Wg2 = WgradOp<4, 8, 16, false>;
 
@@ -803,7 +891,7 @@ int nn_tconv_wgrad(int layer, const __nv_bfloat16* dz, const __nv_bfloat16* x, i
     const int W = kW[layer], tiles = n * (W / (128 / W));
 #define AF_TW(L, Op)                                                      \
     if (layer == L) {                                                     \
-        typename Op::Args a{x, dz, grad, n, W, err};                      \
+        typename Op::Args a{x, dz, grad, n, W, err, nullptr, nullptr, nullptr}; \
         return launch<Op>(a, tiles, s, "conv weight gradient (tcgen05)"); \
     }
     AF_TW(0, Wg0)
@@ -811,4 +899,14 @@ int nn_tconv_wgrad(int layer, const __nv_bfloat16* dz, const __nv_bfloat16* x, i
     AF_TW(2, Wg2)
 #undef AF_TW
     return AF_OK;
+}
+
+int nn_tconv_wgrad_unpool(const __nv_bfloat16* dp, const uint8_t* idx, const __nv_bfloat16* x, int n, float* grad,
+                          float* db, int* err, cudaStream_t s)
+{
+    if (n < 1 || !x || !dp || !idx || !db || ((uintptr_t)x & 15) || ((uintptr_t)dp & 15) || ((uintptr_t)idx & 7))
+        return af_set_error(AF_EINVAL, "conv weight gradient (unpool): argument / alignment");
+    const int W = kW[0], tiles = n * (W / (128 / W));
+    typename Wg0u::Args a{x, nullptr, grad, n, W, err, dp, idx, db};
+    return launch<Wg0u>(a, tiles, s, "conv weight gradient with pool backward (tcgen05)");
 }

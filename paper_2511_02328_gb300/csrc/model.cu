@@ -63,7 +63,7 @@ struct af_model_s {
     __nv_bfloat16* d_a[NL + 1] = {};   // pooled activations, channel-blocked; d_a[0] unused
     uint8_t* d_idx[NL] = {};           // argmax of each pool window | 4 if its maximum > 0
     __nv_bfloat16* d_da[NL + 1] = {};  // gradients w.r.t. d_a[l] (l >= 1)
-    __nv_bfloat16* d_dz[NL] = {};      // gradients w.r.t. the pre-pool ReLU outputs
+    __nv_bfloat16* d_dz[NL] = {};      // gradients w.r.t. the pre-pool ReLU outputs (layers 1, 2)
     float* d_logits = nullptr;
     float* d_loss = nullptr;
     int* d_err = nullptr;              // raised by a bounded tensor-core wait that ran out
@@ -160,7 +160,7 @@ try {
         A(&m->d_wt[l], nn_tpack_bytes(l, 0));
         if (l > 0) A(&m->d_wd[l], nn_tpack_bytes(l, 1));
         A(&m->d_idx[l], (size_t)P * y.cout / 4);
-        A(&m->d_dz[l], (size_t)P * y.cout * 2);
+        if (l > 0) A(&m->d_dz[l], (size_t)P * y.cout * 2);  // layer 0's is never stored
         A(&m->d_a[l + 1], (size_t)P * y.cout / 4 * 2);
         A(&m->d_da[l + 1], (size_t)P * y.cout / 4 * 2);
     }
@@ -288,6 +288,9 @@ static int backward(af_model_t m, int n, cudaStream_t s)
 {
     for (int l = NL - 1; l >= 0; l--) {
         const Layer& L = m->L[l];
+        if (l == 0)  // the first layer's output gradient feeds only its weight gradient: unpooled inside it
+            return nn_tconv_wgrad_unpool(m->d_da[1], m->d_idx[0], m->d_x0, n, m->d_grads + L.woff,
+                                         m->d_grads + L.boff, m->d_err, s);
         if (int rc = nn_pool_back(m->d_da[l + 1], m->d_idx[l], n, L.H, L.W, L.cout, m->d_dz[l], m->d_grads + L.boff, s))
             return rc;
         const __nv_bfloat16* a = l ? m->d_a[l] : m->d_x0;

@@ -33,6 +33,12 @@ int nn_tconv_dgrad(int layer, const __nv_bfloat16* dz, int n, const __nv_bfloat1
                    cudaStream_t s);
 int nn_tconv_wgrad(int layer, const __nv_bfloat16* dz, const __nv_bfloat16* x, int n, float* grad, int* err,
                    cudaStream_t s);
+// Layer 0's weight gradient straight from the pooled gradient dp [n][2][32][32][8]
+// and the argmax bytes idx (laid out as dp): the 2x2 max-pool backward pass
+// runs inside it (dz is never stored), and the bias gradient (the sum of dz)
+// is added to db [16].
+int nn_tconv_wgrad_unpool(const __nv_bfloat16* dp, const uint8_t* idx, const __nv_bfloat16* x, int n, float* grad,
+                          float* db, int* err, cudaStream_t s);
 size_t nn_tpack_bytes(int layer, int dgrad);
 int nn_tpack(int layer, int dgrad, const float* w, __nv_bfloat16* out, cudaStream_t s);
 // [n][64][64][2] -> the first layer's column-expanded input [n][1][64][64][8]:
