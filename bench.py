@@ -509,7 +509,12 @@ def run_classifier(args, dev, x, plan, stream):
     ms_fwd = timed(lambda: _lib.af_model_forward(model, xin.data_ptr(), n, 0, prob.data_ptr(), sp), k)
     ms_train = timed(lambda: _lib.af_train_step(model, xin.data_ptr(), y.data_ptr(), n, 1e-3, loss.data_ptr(), sp), k)
     _lib.af_model_destroy(model)
-    # the tcgen05 layers for inference too (the library takes them from 2048 images up), and a large batch
+    # the fused one-kernel network on the same batch (the library takes it below 256 images), forced
+    os.environ["AFGB_CNN_UMMA_MIN"] = str(1 << 30)
+    mfu = _lib.af_model_create(n, 7)
+    ms_fwd_fused = timed(lambda: _lib.af_model_forward(mfu, xin.data_ptr(), n, 0, prob.data_ptr(), sp), k)
+    _lib.af_model_destroy(mfu)
+    # the tcgen05 layers for inference, forced, and a large batch
     os.environ["AFGB_CNN_UMMA_MIN"] = "1"
     big = 4096
     mtc = _lib.af_model_create(big, 7)
@@ -533,6 +538,7 @@ def run_classifier(args, dev, x, plan, stream):
         "batch": n, "flop_per_sample_forward": CNN_FWD_FLOP,
         "ms_classify": ms_classify, "candidates_per_s": n / (ms_classify * 1e-3),
         "ms_forward": ms_fwd, "forward_tflops": tf(n, ms_fwd), "ms_forward_tcgen05": ms_fwd_tc,
+        "ms_forward_fused": ms_fwd_fused,
         "ms_train_step": ms_train, "train_tflops": tf(n, ms_train, 3),
         "large_batch": {"batch": big, "ms_forward_tcgen05": ms_fwd_big, "forward_tflops": tf(big, ms_fwd_big),
                         "ms_train_step": ms_train_big, "train_tflops": tf(big, ms_train_big, 3)},
@@ -541,8 +547,9 @@ def run_classifier(args, dev, x, plan, stream):
         "forward_frac_large_batch": tf(big, ms_fwd_big) / peak,
         "note": "training: the convolutions as implicit GEMMs on the tcgen05 tensor cores (bf16 operands, fp32 "
                 "accumulators in tensor memory; forward with bias, ReLU and max pool fused, data and weight "
-                "gradients); inference of this batch: the fused one-kernel mma.sync network (faster below 2048 "
-                "images), ms_forward_tcgen05 the tcgen05 layers on the same batch; a training step counts 3x the "
+                "gradients); inference of this batch: the library's choice (the tcgen05 layers from 256 images "
+                "up, the fused one-kernel mma.sync network below), ms_forward_tcgen05 / ms_forward_fused each "
+                "forced on the same batch; a training step counts 3x the "
                 "forward FLOP; peak = measured bf16 sustained (cuBLAS); af_classify includes the cut-out kernel",
     }
 
@@ -868,6 +875,10 @@ def main():
     ms_total = max_over_ranks(ms_total, dist, dev)
 
     # ---- e2e through the host-buffer entry point (pinned input, copies timed)
+    # a pause after the clock sampler's nvidia-smi has exited: in runs that
+    # started the timed calls right away, one call often stalled by 15-45 ms
+    # (not seen in runs with the pause, nor in loops without the sampler)
+    time.sleep(2.0)
     x_pin = torch.from_numpy(x_host).pin_memory()
     _lib.af_search_reserve(H, NSAMP, CAP)
     out = np.empty(CAP, dtype=_lib.CAND_DTYPE)

@@ -45,8 +45,9 @@ struct Layer {
 
 // Inference batches of at least this many images run the layered tensor-core
 // network; smaller ones the fused one-kernel network (AFGB_CNN_UMMA_MIN
-// overrides at model creation).
-constexpr int kUmmaInferMin = 2048;
+// overrides at model creation).  Measured on GB300, fused / layered: 0.040 /
+// 0.058 ms at 128 images, 0.074 / 0.070 ms at 256, 0.141 / 0.087 ms at 512.
+constexpr int kUmmaInferMin = 256;
 
 }  // namespace
 
