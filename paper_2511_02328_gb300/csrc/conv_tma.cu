@@ -560,9 +560,15 @@ struct WgradOp {
     static constexpr bool UNPOOL = UNPOOL_;
     static constexpr int FULL_ARRIVALS = UNPOOL ? 1 + 64 : 1;
     static constexpr int NCOPY = H3::NCOPY + (UNPOOL ? 0 : ZB);
-    static constexpr uint32_t SLACK = 16 * PLANE_Z > SSTAGE ? 16 * PLANE_Z - SSTAGE : 0;
+    // SWAP (taps along N with input blocks of 8 channels, i.e. layer 1): the
+    // roles turn around, A = the block's copies (M = 8 NJ = 128 rows: tap row
+    // shift j, channel), B = dZ^T (N = COUT), so the MMA is 128 x COUT instead
+    // of 128 x 8 NJ of which only COUT rows are real, and reads no slack
+    static constexpr bool SWAP = TAPN && CB > 1;
+    static_assert(!SWAP || (8 * NJ == 128 && COUT % 16 == 0), "swapped weight-gradient shape");
+    static constexpr uint32_t SLACK = !SWAP && 16 * PLANE_Z > SSTAGE ? 16 * PLANE_Z - SSTAGE : 0;
     static constexpr int NS = clampi(65536 / (int)SSTAGE, 2, 4);
-    static constexpr int NACC = 1, NCOL = NMMA * NPM;
+    static constexpr int NACC = 1, NCOL = NMMA * (SWAP ? COUT : NPM);
     static_assert(NCOL <= 512, "tensor-memory columns");
     static constexpr bool PER_TILE = false;
     struct Args {
@@ -653,8 +659,21 @@ struct WgradOp {
     // core matrices of 8 pixels (K, 128 bytes apart) by 8 channels (M / N).
     __device__ void mma(uint32_t st, uint32_t, uint32_t tmem, int g) const
     {
-        constexpr uint32_t idesc = afumma::idesc_bf16(128, NPM, 1, 1);
         const uint32_t xs = st + ZREG;
+        if constexpr (SWAP) {
+            constexpr uint32_t idesc = afumma::idesc_bf16(128, COUT, 1, 1);
+#pragma unroll 1
+            for (int ks = 0; ks < 8; ks++) {
+                const uint64_t db = afumma::smem_desc(st + ks * 256, 128, PLANE_Z);
+#pragma unroll
+                for (int k = 0; k < NMMA; k++)
+                    afumma::mma_bf16(tmem + (uint32_t)(k * COUT),
+                                     afumma::smem_desc(xs + H3::plane(0, k) + ks * 256, 128, W * 16), db, idesc,
+                                     (g | ks) != 0);
+            }
+            return;
+        }
+        constexpr uint32_t idesc = afumma::idesc_bf16(128, NPM, 1, 1);
 #pragma unroll 1
         for (int ks = 0; ks < 8; ks++) {
             const uint64_t da = afumma::smem_desc(st + ks * 256, 128, PLANE_Z);
@@ -677,6 +696,29 @@ struct WgradOp {
     // Row o = 32 quarter + lane of the accumulator: its columns into grad.
     __device__ void final(uint32_t tmem, int quarter, int lane) const
     {
+        if constexpr (SWAP) {
+            // row m = 32 quarter + lane: row shift j = m / 8 of a block's copies
+            // (tap dy = j % (R + 2), dx = j / (R + 2)), channel m % 8; columns:
+            // block k's COUT outputs
+            const int m = 32 * quarter + lane, j = m >> 3, dx = j / (R + 2), dy = j - dx * (R + 2);
+            const bool real = dy < 3 && dx < 3;
+            const int t = 3 * dy + dx;
+            const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16);
+#pragma unroll 1
+            for (int k = 0; k < NMMA; k++)
+#pragma unroll 1
+                for (int c0 = 0; c0 < COUT; c0 += 16) {
+                    uint32_t v[16];
+                    afumma::ld_32x32b_x16(taddr + (uint32_t)(k * COUT + c0), v);
+                    afumma::wait_ld();
+                    if (!real) continue;
+                    const int i = 8 * k + (m & 7);
+#pragma unroll
+                    for (int jj = 0; jj < 16; jj++)
+                        atomicAdd(a.grad + ((int64_t)(c0 + jj) * 9 + t) * CIN + i, __uint_as_float(v[jj]));
+                }
+            return;
+        }
         if (32 * quarter >= COUT) return;  // warp-uniform: no real rows in this quarter
         const int o = 32 * quarter + lane;
         const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16);
