@@ -25,10 +25,11 @@
 //                                                            W transposed
 //   wgrad    dW[o][t][i] = sum_p dZ[p][o] X[p + t][i]         A = dZ^T, B = X copies (MN-major)
 //
-// The first layer's input is column-expanded (nn_to_cb8): one block of eight
-// channels holding the two channels of columns x - 1, x, x + 1, so one
-// unshifted copy serves every tap, a K step of 16 takes two rows dy, and the
-// weight gradient takes the three rows dy along N.
+// The first layer's input is column-expanded in shared memory: its raw
+// two-channel rows are copied and the fix warp writes one block of eight
+// channels holding the two channels of columns x - 1, x, x + 1 (and two
+// zeros), so one plane serves every tap, a K step of 16 takes two rows dy, and
+// the weight gradient takes the three rows dy along N.
 //
 // One warp-specialised kernel serves all three: warp 0 issues a tile's bulk
 // copies (one per lane) into an NS-deep ring; warp 6 fixes a stage's padding
@@ -102,14 +103,19 @@ struct Geo {
 // y0 + R, one run; copy 0 lands one pixel later than it starts in memory,
 // copy 2 one pixel earlier.  Planes (one block of one copy) sit copy-major
 // (dx * COPY + cb * PLANE) or, BM, block-major ((3 cb + dx) * PLANE).  With
-// NSH = 1 only the unshifted copy is made (the first layer's column-expanded
-// input carries its own column neighbours).
+// NSH = 1 (the first layer) `in` is the raw input [n][H][W][2]: its rows are
+// copied after the plane and fixup() expands them into a column-expanded
+// plane, whose pixels carry their own column neighbours.
 template <int CB, int W, bool BM = false, int NSH = 3>
 struct Halo {
     using G = Geo<CB, W>;
     static_assert(NSH == 1 || NSH == 3, "copies");
+    static_assert(NSH == 3 || CB == 1, "the column-expanded form has one block");
     static constexpr int R = G::R, NCOPY = NSH * CB;
-    static constexpr uint32_t BYTES = NSH == 1 ? align1k(CB * G::PLANE) : BM ? align1k(3 * CB * G::PLANE) : 3 * G::COPY;
+    // NSH = 1: the raw two-channel rows (4 bytes a pixel) land after the plane
+    // and the fix warp expands them into it
+    static constexpr uint32_t RAW = (uint32_t)(R + 2) * W * 4;
+    static constexpr uint32_t BYTES = NSH == 1 ? align1k(G::PLANE + RAW) : BM ? align1k(3 * CB * G::PLANE) : 3 * G::COPY;
     __host__ __device__ static constexpr uint32_t plane(int dx, int cb)
     {
         return NSH == 1 ? (uint32_t)cb * G::PLANE
@@ -128,19 +134,24 @@ struct Halo {
     {
         int ylo, nrows, rlo;
         rows(y0, H, ylo, nrows, rlo);
-        return NSH == 1 ? (uint32_t)CB * nrows * W * 16 : (uint32_t)CB * (3u * (uint32_t)nrows * W * 16 - 32u);
+        return NSH == 1 ? (uint32_t)nrows * W * 4 : (uint32_t)CB * (3u * (uint32_t)nrows * W * 16 - 32u);
     }
     __device__ static void copy(int c, uint32_t st, const __nv_bfloat16* in, int img, int y0, int H, uint32_t bar)
     {
         int ylo, nrows, rlo;
         rows(y0, H, ylo, nrows, rlo);
-        const int dx = NSH == 1 ? 1 : c / CB, cb = NSH == 1 ? c : c - dx * CB;
-        const uint8_t* src = reinterpret_cast<const uint8_t*>(in) + (((int64_t)img * CB + cb) * H + ylo) * W * 16;
-        const uint32_t dst = st + plane(dx, cb) + (uint32_t)rlo * W * 16;
-        const uint32_t len = (uint32_t)nrows * W * 16;
-        if (dx == 1) afptx::bulk_g2s(dst, src, len, bar);
-        else if (dx == 0) afptx::bulk_g2s(dst + 16, src, len - 16, bar);
-        else afptx::bulk_g2s(dst, src + 16, len - 16, bar);
+        if constexpr (NSH == 1) {  // in: the raw input [n][H][W][2]
+            const uint8_t* src = reinterpret_cast<const uint8_t*>(in) + ((int64_t)img * H + ylo) * W * 4;
+            afptx::bulk_g2s(st + G::PLANE + (uint32_t)rlo * W * 4, src, (uint32_t)nrows * W * 4, bar);
+        } else {
+            const int dx = c / CB, cb = c - dx * CB;
+            const uint8_t* src = reinterpret_cast<const uint8_t*>(in) + (((int64_t)img * CB + cb) * H + ylo) * W * 16;
+            const uint32_t dst = st + plane(dx, cb) + (uint32_t)rlo * W * 16;
+            const uint32_t len = (uint32_t)nrows * W * 16;
+            if (dx == 1) afptx::bulk_g2s(dst, src, len, bar);
+            else if (dx == 0) afptx::bulk_g2s(dst + 16, src, len - 16, bar);
+            else afptx::bulk_g2s(dst, src + 16, len - 16, bar);
+        }
     }
     // After the copies landed: zero the wrapped pixels (column 0 of copy 0,
     // column W - 1 of copy 2, every row and block) and the rows outside the
@@ -148,15 +159,30 @@ struct Halo {
     __device__ static void fixup(uint8_t* st, int y0, int H, int lane)
     {
         const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-        for (int e = lane; NSH == 3 && e < 2 * CB * (R + 2); e += 32) {
-            const int k = e / (CB * (R + 2)), rem = e - k * CB * (R + 2), cb = rem / (R + 2), r = rem - cb * (R + 2);
-            *reinterpret_cast<uint4*>(st + plane(2 * k, cb) + (r * W + (k ? W - 1 : 0)) * 16) = z;
-        }
-        if (y0 == 0 || y0 + R == H) {
-            const int r = y0 == 0 ? 0 : R + 1;  // R < H: a tile has one edge at most
-            for (int e = lane; e < NSH * CB * W; e += 32) {
-                const int c = e / W, x = e - c * W, dx = NSH == 1 ? 1 : c / CB, cb = NSH == 1 ? c : c - dx * CB;
-                *reinterpret_cast<uint4*>(st + plane(dx, cb) + (r * W + x) * 16) = z;
+        if constexpr (NSH == 1) {
+            // the column-expanded plane: pixel (r, x) = the two channels of
+            // columns x - 1, x, x + 1 of raw row r (zeros outside the image), two zeros
+            const uint32_t* raw = reinterpret_cast<const uint32_t*>(st + G::PLANE);
+            for (int e = lane; e < (R + 2) * W; e += 32) {
+                const int r = e / W, x = e - r * W, y = y0 - 1 + r;
+                uint4 v = z;
+                if (y >= 0 && y < H) {
+                    const uint32_t* row = raw + r * W;
+                    v = make_uint4(x > 0 ? row[x - 1] : 0u, row[x], x < W - 1 ? row[x + 1] : 0u, 0u);
+                }
+                *reinterpret_cast<uint4*>(st + e * 16) = v;
+            }
+        } else {
+            for (int e = lane; e < 2 * CB * (R + 2); e += 32) {
+                const int k = e / (CB * (R + 2)), rem = e - k * CB * (R + 2), cb = rem / (R + 2), r = rem - cb * (R + 2);
+                *reinterpret_cast<uint4*>(st + plane(2 * k, cb) + (r * W + (k ? W - 1 : 0)) * 16) = z;
+            }
+            if (y0 == 0 || y0 + R == H) {
+                const int r = y0 == 0 ? 0 : R + 1;  // R < H: a tile has one edge at most
+                for (int e = lane; e < 3 * CB * W; e += 32) {
+                    const int c = e / W, x = e - c * W, dx = c / CB, cb = c - dx * CB;
+                    *reinterpret_cast<uint4*>(st + plane(dx, cb) + (r * W + x) * 16) = z;
+                }
             }
         }
         afptx::fence_proxy_async();
@@ -785,17 +811,6 @@ __global__ void k_tpack(const float* __restrict__ w, int cin, int cout, int cbk,
     out[e] = __float2bfloat16(v);
 }
 
-// [n][64][64][2] bf16 (the classifier's input) -> column-expanded
-// [n][1][64][64][8]: pixel (y, x) holds the two channels of columns x - 1, x,
-// x + 1 (zero outside the image), then two zeros.
-__global__ void k_to_cb8(const uint32_t* __restrict__ x, int64_t npix, uint4* __restrict__ out)
-{
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i & 63);
-        out[i] = make_uint4(c > 0 ? __ldg(x + i - 1) : 0u, __ldg(x + i), c < 63 ? __ldg(x + i + 1) : 0u, 0u);
-    }
-}
-
 // ------------------------------------------------------------ host side
 template <class Op>
 constexpr size_t smem_bytes()
@@ -878,15 +893,6 @@ int nn_tpack(int layer, int dgrad, const float* w, __nv_bfloat16* out, cudaStrea
     const int total = (int)(nn_tpack_bytes(layer, dgrad) / 2);
     k_tpack<<<(total + 255) / 256, 256, 0, s>>>(w, cin, cout, cbk, nrows, dgrad, total, out);
     return af_cuda_check(cudaGetLastError(), "conv pack");
-}
-
-int nn_to_cb8(const __nv_bfloat16* x, int n, __nv_bfloat16* out, cudaStream_t s)
-{
-    if (((uintptr_t)x & 3) || ((uintptr_t)out & 15)) return af_set_error(AF_EINVAL, "to channel blocks: alignment");
-    const int64_t npix = (int64_t)n * 64 * 64;
-    const int64_t blocks = std::min<int64_t>((npix + 255) / 256, 152 * 32);
-    k_to_cb8<<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<const uint32_t*>(x), npix, reinterpret_cast<uint4*>(out));
-    return af_cuda_check(cudaGetLastError(), "to channel blocks");
 }
 
 int nn_tconv_fwd(int layer, const __nv_bfloat16* x, int n, const __nv_bfloat16* wp, const float* bias,

@@ -60,7 +60,6 @@ struct af_model_s {
     float *d_params = nullptr, *d_grads = nullptr, *d_m = nullptr, *d_v = nullptr;
     __nv_bfloat16* d_wt[NL] = {};      // forward weights, packed for the tensor cores (nn_tpack)
     __nv_bfloat16* d_wd[NL] = {};      // data-gradient weights, packed (l >= 1)
-    __nv_bfloat16* d_x0 = nullptr;     // the input, channel-blocked [n][1][64][64][8]
     __nv_bfloat16* d_a[NL + 1] = {};   // pooled activations, channel-blocked; d_a[0] unused
     uint8_t* d_idx[NL] = {};           // argmax of each pool window | 4 if its maximum > 0
     __nv_bfloat16* d_da[NL + 1] = {};  // gradients w.r.t. d_a[l] (l >= 1)
@@ -90,7 +89,6 @@ static void free_model(af_model_t m)
         cudaFree(m->d_da[l]);
     }
     cudaFree(m->d_err);
-    cudaFree(m->d_x0);
     cudaFree(m->d_logits);
     cudaFree(m->d_loss);
     cudaFree(m->d_cut);
@@ -166,7 +164,6 @@ try {
         A(&m->d_da[l + 1], (size_t)P * y.cout / 4 * 2);
     }
     A(&m->d_err, 16);
-    A(&m->d_x0, (size_t)n * 64 * 64 * 8 * 2);
     A(&m->d_logits, (size_t)n * 2 * 4);
     A(&m->d_loss, 16);
     A(&m->d_cut, (size_t)n * 64 * 64 * 2 * 2);
@@ -265,8 +262,7 @@ static int forward(af_model_t m, const __nv_bfloat16* x, int n, const int32_t* y
         return nn_forward_fused(x, n, P + m->L[0].woff, P + m->L[0].boff, P + m->L[1].woff, P + m->L[1].boff,
                                 P + m->L[2].woff, P + m->L[2].boff, P + m->fw_off, P + m->fb_off, m->d_logits, prob,
                                 s);
-    if (int rc = nn_to_cb8(x, n, m->d_x0, s)) return rc;
-    const __nv_bfloat16* a = m->d_x0;
+    const __nv_bfloat16* a = x;  // the first layer expands its columns itself
     for (int l = 0; l < NL; l++) {
         const Layer& L = m->L[l];
         if (int rc = nn_tpack(l, 0, P + L.woff, m->d_wt[l], s)) return rc;
@@ -285,16 +281,16 @@ static int forward(af_model_t m, const __nv_bfloat16* x, int n, const int32_t* y
 
 // After forward() with labels: the channel-blocked input and activations are
 // in place.
-static int backward(af_model_t m, int n, cudaStream_t s)
+static int backward(af_model_t m, const __nv_bfloat16* x, int n, cudaStream_t s)
 {
     for (int l = NL - 1; l >= 0; l--) {
         const Layer& L = m->L[l];
         if (l == 0)  // the first layer's output gradient feeds only its weight gradient: unpooled inside it
-            return nn_tconv_wgrad_unpool(m->d_da[1], m->d_idx[0], m->d_x0, n, m->d_grads + L.woff,
+            return nn_tconv_wgrad_unpool(m->d_da[1], m->d_idx[0], x, n, m->d_grads + L.woff,
                                          m->d_grads + L.boff, m->d_err, s);
         if (int rc = nn_pool_back(m->d_da[l + 1], m->d_idx[l], n, L.H, L.W, L.cout, m->d_dz[l], m->d_grads + L.boff, s))
             return rc;
-        const __nv_bfloat16* a = l ? m->d_a[l] : m->d_x0;
+        const __nv_bfloat16* a = l ? m->d_a[l] : x;
         if (int rc = nn_tconv_wgrad(l, m->d_dz[l], a, n, m->d_grads + L.woff, m->d_err, s)) return rc;
         if (l > 0) {
             if (int rc = nn_tpack(l, 1, m->d_params + L.woff, m->d_wd[l], s)) return rc;
@@ -331,7 +327,7 @@ try {
     if (!d_y) return af_set_error(AF_EINVAL, "af_model_backward: labels NULL");
     cudaStream_t s = (cudaStream_t)stream;
     if (int rc = forward(m, (const __nv_bfloat16*)d_x, n, d_y, nullptr, s)) return rc;
-    if (int rc = backward(m, n, s)) return rc;
+    if (int rc = backward(m, (const __nv_bfloat16*)d_x, n, s)) return rc;
     if (d_loss) AF_CUDA(cudaMemcpyAsync(d_loss, m->d_loss, 4, cudaMemcpyDeviceToDevice, s));
     return AF_OK;
 } catch (...) {

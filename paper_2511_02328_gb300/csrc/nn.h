@@ -19,7 +19,9 @@ int nn_gemm(int layout, int epi, const __nv_bfloat16* A, int lda, const __nv_bfl
 // 3x3 convolutions (pad 1) of classifier layer 0, 1, 2 (2 -> 16 -> 32 -> 64
 // channels, 64 / 32 / 16 pixels square) on the tensor cores with TMA-staged
 // operands (conv_tma.cu).  Tensors are channel-blocked, [n][C/8][H][W][8]
-// bf16 (the first layer's input column-expanded to 8 channels, nn_to_cb8):
+// bf16 (the first layer's input: the raw [n][64][64][2], which the layer-0
+// kernels expand in shared memory to 8 channels, those of columns x - 1, x,
+// x + 1 and two zeros):
 //   forward: x -> bias, ReLU, 2x2 max pool -> out [n][cout/8][H/2][W/2][8] and
 //            idx (argmax 0..3 | 4 if positive, laid out as out; nullable)
 //   dgrad:   dz [n][cout/8][H][W][8] -> dx [n][cin/8][H][W][8] (layers 1, 2)
@@ -41,10 +43,6 @@ int nn_tconv_wgrad_unpool(const __nv_bfloat16* dp, const uint8_t* idx, const __n
                           float* db, int* err, cudaStream_t s);
 size_t nn_tpack_bytes(int layer, int dgrad);
 int nn_tpack(int layer, int dgrad, const float* w, __nv_bfloat16* out, cudaStream_t s);
-// [n][64][64][2] -> the first layer's column-expanded input [n][1][64][64][8]:
-// pixel (y, x) holds the two channels of columns x - 1, x, x + 1 (zero outside
-// the image), then two zeros
-int nn_to_cb8(const __nv_bfloat16* x, int n, __nv_bfloat16* out, cudaStream_t s);
 // 2x2 max-pool backward on channel-blocked tensors (dz [n][c/8][H][W][8] from
 // the pooled gradient and the argmax bytes, both [n][c/8][H/2][W/2][8]); adds
 // the bias gradient (sum of dz over pixels) into db.
