@@ -771,6 +771,11 @@ def run_stream(args, dev, clocks):
                      "same GPU between pushes" % speed)}
 
 
+def _g5(v):
+    """A secondary scalar of the bench line at 5 significant digits (the line stays short)."""
+    return None if v is None else float("%.5g" % v)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1074,28 +1079,29 @@ def main():
                     "h2d_bytes_per_step": NCHAN * NSAMP, "d2h_bytes_per_step": 4 + 24 * min(nc, CAP)},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
-            "realtime_factor": nout * TSAMP / (ms_dedisp * 1e-3),
-            "dedisp_ms": ms_dedisp,
-            "stage1_ms": stage["rows_ms"] if stage else None,
-            "stage2_ms": stage["tiles_ms"] if stage else None,
-            "batch_ms": batch_res["ms_per_batch"] if batch_res else None,
+            "realtime_factor": _g5(nout * TSAMP / (ms_dedisp * 1e-3)),
+            "dedisp_ms": _g5(ms_dedisp),
+            "stage1_ms": _g5(stage["rows_ms"] if stage else None),
+            "stage2_ms": _g5(stage["tiles_ms"] if stage else None),
+            "batch_ms": _g5(batch_res["ms_per_batch"] if batch_res else None),
             "batch_strategy": batch_res["strategy"] if batch_res else None,
-            "batch_speedup_vs_beam_by_beam": batch_res.get("speedup_vs_beam_by_beam") if batch_res else None,
-            "subband_ms": sub_res["ms"] if sub_res else None,
-            "cnn_train_ms": cls_res["ms_train_step"] if cls_res else None,
-            "cnn_train_frac": cls_res["train_frac"] if cls_res else None,
-            "cnn_forward_frac": cls_res["forward_frac"] if cls_res else None,
-            "cnn_train_frac_4096": cls_res["train_frac_large_batch"] if cls_res else None,
+            "batch_speedup_vs_beam_by_beam": _g5(batch_res.get("speedup_vs_beam_by_beam") if batch_res else None),
+            "subband_ms": _g5(sub_res["ms"] if sub_res else None),
+            "cnn_train_ms": _g5(cls_res["ms_train_step"] if cls_res else None),
+            "cnn_train_frac": _g5(cls_res["train_frac"] if cls_res else None),
+            "cnn_forward_frac": _g5(cls_res["forward_frac"] if cls_res else None),
+            "cnn_train_frac_4096": _g5(cls_res["train_frac_large_batch"] if cls_res else None),
+            "cnn_forward_frac_4096": _g5(cls_res["forward_frac_large_batch"] if cls_res else None),
             "stream_windows": sres.get("windows"),
             "stream_speed_vs_realtime": sres.get("arrival_speed_vs_realtime"),
-            "p50_chunk_latency_ms": sres.get("p50_ms_with_classifier"),
-            "p99_chunk_latency_ms": sres.get("p99_ms_with_classifier"),
-            "hop_ms": sres.get("hop_s", 0) * 1e3 if sres else None,
+            "p50_chunk_latency_ms": _g5(sres.get("p50_ms_with_classifier")),
+            "p99_chunk_latency_ms": _g5(sres.get("p99_ms_with_classifier")),
+            "hop_ms": _g5(sres.get("hop_s", 0) * 1e3 if sres else None),
             "pulses_snr8": er.get("injected"),
-            "recall_threshold": er.get("recall_threshold"),
-            "recall_cnn": er.get("recall_cnn"),
-            "fp_per_hour_threshold": er.get("fp_per_hour_threshold"),
-            "fp_per_hour_cnn": er.get("fp_per_hour_cnn"),
+            "recall_threshold": _g5(er.get("recall_threshold")),
+            "recall_cnn": _g5(er.get("recall_cnn")),
+            "fp_per_hour_threshold": _g5(er.get("fp_per_hour_threshold")),
+            "fp_per_hour_cnn": _g5(er.get("fp_per_hour_cnn")),
         }
         print(json.dumps(line))
     plan.close()
