@@ -880,10 +880,6 @@ def main():
     ms_total = max_over_ranks(ms_total, dist, dev)
 
     # ---- e2e through the host-buffer entry point (pinned input, copies timed)
-    # a pause after the clock sampler's nvidia-smi has exited: in runs that
-    # started the timed calls right away, one call often stalled by 15-45 ms
-    # (not seen in runs with the pause, nor in loops without the sampler)
-    time.sleep(2.0)
     x_pin = torch.from_numpy(x_host).pin_memory()
     _lib.af_search_reserve(H, NSAMP, CAP)
     out = np.empty(CAP, dtype=_lib.CAND_DTYPE)
@@ -893,28 +889,29 @@ def main():
         dist.barrier()
     gc_was = gc.isenabled()
     gc.disable()          # no collector pause inside the timed calls
+    _lib.af_search_timing(H, 1)   # four events per call: where each call's time goes
     t0 = time.perf_counter()
     nc = 0
-    walls = []
+    walls, phases = [], []
     for _ in range(args.e2e_steps):
         ta = time.perf_counter()
         c, nc = _lib.af_search(H, x_pin.data_ptr(), NSAMP, WIDTHS, THRESH, CAP, sp, out=out)
         plan.cluster(c)
         walls.append((time.perf_counter() - ta) * 1e3)
+        phases.append(_lib.af_search_times(H))
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    _lib.af_search_timing(H, 0)
     if gc_was:
         gc.enable()
-    # one more call with phase events (outside the timed region): where the e2e time goes
-    _lib.af_search_timing(H, 1)
-    _lib.af_search(H, x_pin.data_ptr(), NSAMP, WIDTHS, THRESH, CAP, sp, out=out)
-    ph = _lib.af_search_times(H)
-    _lib.af_search_timing(H, 0)
-    e2e_phases = {"copy_wait_ms": ph[0], "dedisp_ms": ph[1], "snr_candidates_ms": ph[2],
+    ph = np.median(np.asarray(phases), axis=0)
+    e2e_phases = {"copy_wait_ms": float(ph[0]), "dedisp_ms": float(ph[1]), "snr_candidates_ms": float(ph[2]),
                   "call_ms": {"min": min(walls), "median": float(np.median(walls)), "max": max(walls),
                               "each": [round(v, 2) for v in walls]},
-                  "note": "first time block's input copy (its outputs + Dmax), dedispersion with the rest of the "
-                          "copy overlapped, S/N + candidate kernels; the remainder of e2e ms is host work and the "
-                          "candidate copy back; call_ms = each timed call's wall time (search + clustering)"}
+                  "each_phase_ms": [[round(float(v), 2) for v in p] for p in phases],
+                  "note": "medians over the timed calls of: first time block's input copy (its outputs + Dmax), "
+                          "dedispersion with the rest of the copy overlapped, S/N + candidate kernels (device "
+                          "events); the remainder of a call's wall time is host work and the candidate copy back; "
+                          "call_ms = each timed call's wall time (search + clustering)"}
     # the input copy alone (pinned host -> device), for the e2e breakdown
     h2d = torch.empty_like(x)
     for _ in range(2):
