@@ -379,30 +379,30 @@ struct ConvOp {
     static constexpr bool PER_TILE = true, UNPOOL = false;
     static constexpr int FULL_ARRIVALS = 1;
     struct Args {
-        const __nv_bfloat16* in;  // [n][CB][H][W][8]
+        const __nv_bfloat16* in;  // [n][CB][H][W][8]; CB = 1: the raw input [n][H][W][2]
         const __nv_bfloat16* wp;  // packed weights, STEPS * 2 * LBO_B bytes
         const float* bias;        // [N] (POOL)
         __nv_bfloat16* out;       // POOL: [n][N/8][H/2][W/2][8]; else [n][N/8][H][W][8]
         uint8_t* idx;             // POOL: argmax | 4 if the maximum > 0, laid out as out (nullable)
-        int n, H;
+        int n;  // images; every feature map is square (H = W)
         int* err;
     };
     const Args a;
     __device__ ConvOp(const Args& a_) : a(a_) {}
-    __device__ int ntiles() const { return a.n * (a.H / R); }
+    __device__ int ntiles() const { return a.n * (W / R); }
     __device__ void resident(uint8_t* res, int tid) const
     {
         const uint4* src = reinterpret_cast<const uint4*>(a.wp);
         for (int i = tid; i < (int)(STEPS * 2 * LBO_B / 16); i += kThreads)
             reinterpret_cast<uint4*>(res)[i] = __ldg(src + i);
     }
-    __device__ uint32_t tx(int tile) const { return H3::tx((tile % (a.H / R)) * R, a.H); }
+    __device__ uint32_t tx(int tile) const { return H3::tx((tile % (W / R)) * R, W); }
     __device__ void copy(int c, uint32_t st, int tile, uint32_t bar) const
     {
-        const int tpi = a.H / R, img = tile / tpi;
-        H3::copy(c, st, a.in, img, (tile - img * tpi) * R, a.H, bar);
+        const int tpi = W / R, img = tile / tpi;
+        H3::copy(c, st, a.in, img, (tile - img * tpi) * R, W, bar);
     }
-    __device__ void fixup(uint8_t* st, int tile, int lane) const { H3::fixup(st, (tile % (a.H / R)) * R, a.H, lane); }
+    __device__ void fixup(uint8_t* st, int tile, int lane) const { H3::fixup(st, (tile % (W / R)) * R, W, lane); }
     // Step s: A = the tap's copy from the tap's row, its K halves one LBO apart
     // (two channel blocks; for EXP two rows dy); B = the step's weights.
     __device__ void mma(uint32_t st, uint32_t res, uint32_t tmem, int) const
@@ -428,11 +428,11 @@ struct ConvOp {
     // Thread = tile row r = 32 quarter + lane, pixel (y0 + r / W, r % W).
     __device__ void epilogue(int tile, uint32_t tmem, int quarter, int lane, float* xv, uint32_t* xq) const
     {
-        const int tpi = a.H / R, img = tile / tpi, y0 = (tile - img * tpi) * R;
+        const int tpi = W / R, img = tile / tpi, y0 = (tile - img * tpi) * R;
         const int r = 32 * quarter + lane, yl = r / W, x = r % W;
         const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16);
         if constexpr (!POOL) {
-            const int64_t plane = (int64_t)a.H * W, pix = (int64_t)(y0 + yl) * W + x;
+            const int64_t plane = (int64_t)W * W, pix = (int64_t)(y0 + yl) * W + x;
 #pragma unroll 1
             for (int c0 = 0; c0 < N; c0 += 16) {
                 uint32_t v[16];
@@ -468,7 +468,7 @@ struct ConvOp {
     __device__ void pool_epilogue(int img, int y0, int yl, int x, int quarter, int lane, uint32_t taddr, float* xv,
                                   uint32_t* xq) const
     {
-        const int Ho = a.H / 2, Wo = W / 2;
+        const int Ho = W / 2, Wo = W / 2;
         const bool top = (yl & 1) == 0, odd = (x & 1) != 0;
         const int64_t po = (int64_t)(y0 / 2 + (yl >> 1)) * Wo + (x >> 1), oplane = (int64_t)Ho * Wo;
         const int slot = 32 * (W == 64 ? (quarter & 1) : (quarter >> 1)) + lane;
@@ -598,10 +598,10 @@ struct WgradOp {
     static_assert(NCOL <= 512, "tensor-memory columns");
     static constexpr bool PER_TILE = false;
     struct Args {
-        const __nv_bfloat16* x;   // [n][CB][H][W][8]
+        const __nv_bfloat16* x;   // [n][CB][H][W][8]; CB = 1: the raw input [n][H][W][2]
         const __nv_bfloat16* dz;  // [n][ZB][H][W][8] (not UNPOOL)
         float* grad;              // [COUT][9][CIN], accumulated
-        int n, H;
+        int n;                    // images; every feature map is square (H = W)
         int* err;
         const __nv_bfloat16* dp;  // UNPOOL: pooled gradient [n][ZB][H/2][W/2][8]
         const uint8_t* idx;       // UNPOOL: argmax 0..3 | 4 if positive, laid out as dp
@@ -609,11 +609,11 @@ struct WgradOp {
     };
     const Args a;
     __device__ WgradOp(const Args& a_) : a(a_) {}
-    __device__ int ntiles() const { return a.n * (a.H / R); }
+    __device__ int ntiles() const { return a.n * (W / R); }
     __device__ void resident(uint8_t*, int) const {}
     __device__ uint32_t tx(int tile) const
     {
-        return H3::tx((tile % (a.H / R)) * R, a.H) + (UNPOOL ? 0u : ZB * PLANE_Z);
+        return H3::tx((tile % (W / R)) * R, W) + (UNPOOL ? 0u : ZB * PLANE_Z);
     }
     // UNPOOL: thread tg (< 64) of a group of the epilogue warps handles item
     // tg of a tile, (pooled pixel tg / ZB of the tile's R / 2 pooled rows,
@@ -628,9 +628,9 @@ struct WgradOp {
     static_assert(!UNPOOL || ITEMS == 64, "one item per thread of a 64-thread group");
     __device__ void unpool_load(int tile, int tg, Pooled& p) const
     {
-        const int tpi = a.H / R, img = tile / tpi, y0 = (tile - img * tpi) * R;
+        const int tpi = W / R, img = tile / tpi, y0 = (tile - img * tpi) * R;
         const int zb = tg % ZB, pp = tg / ZB, pr = pp / (W / 2), xo = pp - pr * (W / 2);
-        const int64_t e = ((((int64_t)img * ZB + zb) * (a.H / 2) + y0 / 2 + pr) * (W / 2) + xo) * 8;
+        const int64_t e = ((((int64_t)img * ZB + zb) * (W / 2) + y0 / 2 + pr) * (W / 2) + xo) * 8;
         p.v = __ldg(reinterpret_cast<const uint4*>(a.dp + e));
         p.ix = __ldg(reinterpret_cast<const uint2*>(a.idx + e));
     }
@@ -669,17 +669,17 @@ struct WgradOp {
     // copies 0 .. 3 CB - 1: the shifted copies of X; then one per dZ block
     __device__ void copy(int c, uint32_t st, int tile, uint32_t bar) const
     {
-        const int tpi = a.H / R, img = tile / tpi, y0 = (tile - img * tpi) * R;
+        const int tpi = W / R, img = tile / tpi, y0 = (tile - img * tpi) * R;
         if (c < H3::NCOPY) {
-            H3::copy(c, st + ZREG, a.x, img, y0, a.H, bar);
+            H3::copy(c, st + ZREG, a.x, img, y0, W, bar);
         } else {
             const int zb = c - H3::NCOPY;
-            afptx::bulk_g2s(st + zb * PLANE_Z, a.dz + (((int64_t)img * ZB + zb) * a.H + y0) * W * 8, PLANE_Z, bar);
+            afptx::bulk_g2s(st + zb * PLANE_Z, a.dz + (((int64_t)img * ZB + zb) * W + y0) * W * 8, PLANE_Z, bar);
         }
     }
     __device__ void fixup(uint8_t* st, int tile, int lane) const
     {
-        H3::fixup(st + ZREG, (tile % (a.H / R)) * R, a.H, lane);
+        H3::fixup(st + ZREG, (tile % (W / R)) * R, W, lane);
     }
     // K step ks = pixels 16 ks .. 16 ks + 15 of the tile; MN-major operands:
     // core matrices of 8 pixels (K, 128 bytes apart) by 8 channels (M / N).
@@ -904,7 +904,7 @@ int nn_tconv_fwd(int layer, const __nv_bfloat16* x, int n, const __nv_bfloat16* 
     const int W = kW[layer], tiles = n * (W / (128 / W));
 #define AF_TF(L, Op)                                                  \
     if (layer == L) {                                                 \
-        typename Op::Args a{x, wp, bias, out, idx, n, W, err};        \
+        typename Op::Args a{x, wp, bias, out, idx, n, err};        \
         return launch<Op>(a, tiles, s, "conv forward (tcgen05)");     \
     }
     AF_TF(0, Fwd0)
@@ -922,7 +922,7 @@ int nn_tconv_dgrad(int layer, const __nv_bfloat16* dz, int n, const __nv_bfloat1
     const int W = kW[layer], tiles = n * (W / (128 / W));
 #define AF_TD(L, Op)                                                      \
     if (layer == L) {                                                     \
-        typename Op::Args a{dz, wp, nullptr, dx, nullptr, n, W, err};     \
+        typename Op::Args a{dz, wp, nullptr, dx, nullptr, n, err};     \
         return launch<Op>(a, tiles, s, "conv data gradient (tcgen05)");   \
     }
     AF_TD(1, Dg1)
@@ -939,7 +939,7 @@ int nn_tconv_wgrad(int layer, const __nv_bfloat16* dz, const __nv_bfloat16* x, i
     const int W = kW[layer], tiles = n * (W / (128 / W));
 #define AF_TW(L, Op)                                                      \
     if (layer == L) {                                                     \
-        typename Op::Args a{x, dz, grad, n, W, err, nullptr, nullptr, nullptr}; \
+        typename Op::Args a{x, dz, grad, n, err, nullptr, nullptr, nullptr}; \
         return launch<Op>(a, tiles, s, "conv weight gradient (tcgen05)"); \
     }
     AF_TW(0, Wg0)
@@ -955,6 +955,6 @@ int nn_tconv_wgrad_unpool(const __nv_bfloat16* dp, const uint8_t* idx, const __n
     if (n < 1 || !x || !dp || !idx || !db || ((uintptr_t)x & 15) || ((uintptr_t)dp & 15) || ((uintptr_t)idx & 7))
         return af_set_error(AF_EINVAL, "conv weight gradient (unpool): argument / alignment");
     const int W = kW[0], tiles = n * (W / (128 / W));
-    typename Wg0u::Args a{x, nullptr, grad, n, W, err, dp, idx, db};
+    typename Wg0u::Args a{x, nullptr, grad, n, err, dp, idx, db};
     return launch<Wg0u>(a, tiles, s, "conv weight gradient with pool backward (tcgen05)");
 }

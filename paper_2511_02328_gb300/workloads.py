@@ -42,32 +42,38 @@ def multibeam(nbeams=19, max_delay_fn=None):
 def _run(argv=None):
     """Runs one step of a workload `repeat` times on cuda:0 (inputs resident on
     the device) -- the command the kernel profiles are taken with:
-        python -m paper_2511_02328_gb300.workloads search|subband|prep|train [--nsamp N] [--repeat R] [--batch B]
+        python -m paper_2511_02328_gb300.workloads search|subband|prep|train|infer [--nsamp N] [--repeat R] [--batch B]
     search:  brute-force dedispersion (row sums fused) + boxcar S/N + candidates
     subband: two-stage subband dedispersion (n0 = 8, 64 subbands)
     prep:    zero-DM filter, square-law downsampling by 8, median/MAD + robust S/N
     on the 4096-channel full-band shape with nsamp samples (default 2^18);
     train:   classifier training steps (forward, backward, Adam) on a batch of
-             B random 64 x 64 x 2 bf16 cut-outs (default 1024)."""
+             B random 64 x 64 x 2 bf16 cut-outs (default 1024);
+    infer:   classifier forward passes on such a batch (the library's choice of
+             kernels for that batch size)."""
     import argparse
     import torch
     from . import _lib, synth
     from .search import Plan
     ap = argparse.ArgumentParser(prog="python -m paper_2511_02328_gb300.workloads")
-    ap.add_argument("step", choices=["search", "subband", "prep", "train"])
+    ap.add_argument("step", choices=["search", "subband", "prep", "train", "infer"])
     ap.add_argument("--nsamp", type=int, default=1 << 18)
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--batch", type=int, default=1024)
     a = ap.parse_args(argv)
-    if a.step == "train":
+    if a.step in ("train", "infer"):
         g = torch.Generator(device="cuda")
         g.manual_seed(1)
         x = torch.rand((a.batch, 64, 64, 2), device="cuda", generator=g).to(torch.bfloat16)
         y = torch.randint(0, 2, (a.batch,), device="cuda", dtype=torch.int32, generator=g)
         loss = torch.empty(1, device="cuda")
         m = _lib.af_model_create(a.batch, 3)
+        prob = torch.empty(a.batch, device="cuda")
         for _ in range(a.repeat):
-            _lib.af_train_step(m, x.data_ptr(), y.data_ptr(), a.batch, 1e-4, loss.data_ptr())
+            if a.step == "train":
+                _lib.af_train_step(m, x.data_ptr(), y.data_ptr(), a.batch, 1e-4, loss.data_ptr())
+            else:
+                _lib.af_model_forward(m, x.data_ptr(), a.batch, 0, prob.data_ptr())
         torch.cuda.synchronize()
         _lib.af_model_get_params(m)      # reports a bounded wait that ran out
         _lib.af_model_destroy(m)
