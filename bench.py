@@ -523,9 +523,9 @@ def run_classifier(args, dev, x, plan, stream):
     xbig = xin.repeat(big // n, 1, 1, 1).contiguous()
     ybig = y.repeat(big // n).contiguous()
     pbig = torch.empty(big, dtype=torch.float32, device=dev)
-    ms_fwd_big = timed(lambda: _lib.af_model_forward(mtc, xbig.data_ptr(), big, 0, pbig.data_ptr(), sp), 3)
+    ms_fwd_big = timed(lambda: _lib.af_model_forward(mtc, xbig.data_ptr(), big, 0, pbig.data_ptr(), sp), 20)
     ms_train_big = timed(lambda: _lib.af_train_step(mtc, xbig.data_ptr(), ybig.data_ptr(), big, 1e-4, loss.data_ptr(),
-                                                    sp), 3)
+                                                    sp), 10)
     _lib.af_model_get_params(mtc)   # reports a bounded wait that ran out
     _lib.af_model_destroy(mtc)
     del xbig
