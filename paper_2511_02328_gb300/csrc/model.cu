@@ -69,6 +69,11 @@ struct af_model_s {
     int* d_err = nullptr;              // raised by a bounded tensor-core wait that ran out
     __nv_bfloat16* d_cut = nullptr;    // cut-outs for af_classify
     int umma_min = 0;                  // inference batches of at least this size use the tensor-core layers
+    // d_wt holds the packed form of the current d_params (set by a forward pass
+    // that packed them, on the stream where packed_ev is recorded; cleared by
+    // every call that changes the parameters)
+    bool packed = false;
+    cudaEvent_t packed_ev = nullptr;
 };
 
 static void free_model(af_model_t m)
@@ -92,6 +97,7 @@ static void free_model(af_model_t m)
     cudaFree(m->d_logits);
     cudaFree(m->d_loss);
     cudaFree(m->d_cut);
+    if (m->packed_ev) cudaEventDestroy(m->packed_ev);
     delete m;
 }
 
@@ -234,6 +240,7 @@ static int copy_params(af_model_t m, float* dst, const float* src, int64_t n, cu
 extern "C" int af_model_set_params(af_model_t m, const float* h, int64_t n)
 try {
     if (!m || !h) return af_set_error(AF_EINVAL, "af_model_set_params: NULL argument");
+    m->packed = false;
     return copy_params(m, m->d_params, h, n, cudaMemcpyHostToDevice, "af_model_set_params");
 } catch (...) {
     return af_host_exception("af_model_set_params");
@@ -262,10 +269,18 @@ static int forward(af_model_t m, const __nv_bfloat16* x, int n, const int32_t* y
         return nn_forward_fused(x, n, P + m->L[0].woff, P + m->L[0].boff, P + m->L[1].woff, P + m->L[1].boff,
                                 P + m->L[2].woff, P + m->L[2].boff, P + m->fw_off, P + m->fb_off, m->d_logits, prob,
                                 s);
+    if (!m->packed) {  // the parameters changed since the last packing
+        for (int l = 0; l < NL; l++)
+            if (int rc = nn_tpack(l, 0, P + m->L[l].woff, m->d_wt[l], s)) return rc;
+        if (!m->packed_ev) AF_CUDA(cudaEventCreateWithFlags(&m->packed_ev, cudaEventDisableTiming));
+        AF_CUDA(cudaEventRecord(m->packed_ev, s));
+        m->packed = true;
+    } else {
+        AF_CUDA(cudaStreamWaitEvent(s, m->packed_ev, 0));  // packed on this or another stream
+    }
     const __nv_bfloat16* a = x;  // the first layer expands its columns itself
     for (int l = 0; l < NL; l++) {
         const Layer& L = m->L[l];
-        if (int rc = nn_tpack(l, 0, P + L.woff, m->d_wt[l], s)) return rc;
         if (int rc = nn_tconv_fwd(l, a, n, m->d_wt[l], P + L.boff, m->d_a[l + 1], y ? m->d_idx[l] : nullptr, m->d_err,
                                   s))
             return rc;
@@ -340,6 +355,7 @@ try {
     if (!(lr > 0.0f) || !isfinite(lr)) return af_set_error(AF_EINVAL, "af_train_step: bad learning rate");
     if (int rc = af_model_backward(m, d_x, d_y, n, d_loss, stream)) return rc;
     m->step++;
+    m->packed = false;
     return nn_adam(m->d_params, m->d_grads, m->d_m, m->d_v, m->nparams, lr, m->step, (cudaStream_t)stream);
 } catch (...) {
     return af_host_exception("af_train_step");
@@ -445,6 +461,7 @@ try {
     const size_t got = fread(buf.data(), 4, buf.size(), f);
     fclose(f);
     if (got != buf.size()) return af_set_error(AF_EINVAL, "af_model_load: truncated checkpoint");
+    m->packed = false;
     AF_CUDA(cudaMemcpy(m->d_params, buf.data(), m->nparams * 4, cudaMemcpyHostToDevice));
     AF_CUDA(cudaMemcpy(m->d_m, buf.data() + m->nparams, m->nparams * 4, cudaMemcpyHostToDevice));
     AF_CUDA(cudaMemcpy(m->d_v, buf.data() + 2 * m->nparams, m->nparams * 4, cudaMemcpyHostToDevice));
