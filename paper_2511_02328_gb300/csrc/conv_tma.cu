@@ -455,6 +455,52 @@ struct ConvOp {
         }
     }
 
+    // Inference: the same pooling on the bf16-rounded values, two channels a
+    // word (rounding to nearest is monotone, so the maximum of the rounded
+    // values is the rounded maximum, and the ReLU of it likewise: the same
+    // bf16 outputs as pooling in fp32 and rounding once).  m: this lane's 16
+    // biased channels of the chunk c0.
+    __device__ void pool_infer(const float (&m)[16], int c0, int img, int64_t po, int64_t oplane, bool top, bool odd,
+                               int slot, uint4* xv4) const
+    {
+        uint32_t q[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) q[i] = pack_bf16(m[2 * i], m[2 * i + 1]);
+        // the even column keeps channel pairs 0-3, the odd one 4-7
+        __nv_bfloat162 h[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const uint32_t keep = odd ? q[i + 4] : q[i], give = odd ? q[i] : q[i + 4];
+            const uint32_t other = __shfl_xor_sync(0xffffffffu, give, 1);
+            h[i] = __hmax2(*reinterpret_cast<const __nv_bfloat162*>(&keep),
+                           *reinterpret_cast<const __nv_bfloat162*>(&other));
+        }
+        if constexpr (W == 16) {
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const uint32_t o = __shfl_xor_sync(0xffffffffu, *reinterpret_cast<const uint32_t*>(&h[i]), 16);
+                h[i] = __hmax2(h[i], *reinterpret_cast<const __nv_bfloat162*>(&o));
+            }
+        } else {
+            if (!top) xv4[2 * slot] = *reinterpret_cast<const uint4*>(h);
+            epi_sync();
+            if (top) {
+                const uint4 lo = xv4[2 * slot];
+                const __nv_bfloat162* l2 = reinterpret_cast<const __nv_bfloat162*>(&lo);
+#pragma unroll
+                for (int i = 0; i < 4; i++) h[i] = __hmax2(h[i], l2[i]);
+            }
+            epi_sync();
+        }
+        if (top) {
+            const __nv_bfloat162 z = __float2bfloat162_rn(0.f);
+#pragma unroll
+            for (int i = 0; i < 4; i++) h[i] = __hmax2(h[i], z);
+            const int64_t e0 = (((int64_t)img * (N / 8) + c0 / 8 + (odd ? 1 : 0)) * oplane + po) * 8;
+            *reinterpret_cast<uint4*>(a.out + e0) = *reinterpret_cast<const uint4*>(h);
+        }
+    }
+
     // Bias, 2 x 2 max pool and ReLU (pooled before the ReLU: it commutes with
     // the maximum; where the maximum is positive the argmax is the ReLU
     // outputs' one, elsewhere no gradient is routed) and, in training, the
@@ -486,6 +532,10 @@ struct ConvOp {
                 m[4 * k + 1] = __uint_as_float(v[4 * k + 1]) + b4.y;
                 m[4 * k + 2] = __uint_as_float(v[4 * k + 2]) + b4.z;
                 m[4 * k + 3] = __uint_as_float(v[4 * k + 3]) + b4.w;
+            }
+            if constexpr (!TRAIN) {
+                pool_infer(m, c0, img, po, oplane, top, odd, slot, reinterpret_cast<uint4*>(xv));
+                continue;
             }
             // the pair's row maximum of this lane's 8 channels; hx bit i: the
             // right pixel strictly larger (a tie keeps the left, earlier in raster order)
