@@ -23,7 +23,8 @@
 //   forward  Z[p][o]     = sum_{t,i} X[p + t][i] W[o][t][i]   A = X copies (K-major), B = W
 //   dgrad    dX[p][i]    = sum_{t,o} dZ[p - t][o] W[o][t][i]  the same form on dZ, taps flipped,
 //                                                            W transposed
-//   wgrad    dW[o][t][i] = sum_p dZ[p][o] X[p + t][i]         A = dZ^T, B = X copies (MN-major)
+//   wgrad    dW[o][t][i] = sum_p dZ[p][o] X[p + t][i]         A = dZ^T, B = X copies (MN-major);
+//                                                            layer 1: A = X copies, B = dZ^T
 //
 // The first layer's input is column-expanded in shared memory: its raw
 // two-channel rows are copied and the fix warp writes one block of eight
@@ -36,8 +37,10 @@
 // once its copies have landed and releases it; warp 1 (one elected thread)
 // issues the tile's MMAs into one of NACC tensor-memory accumulators and
 // commits them; warps 2-5 read the accumulator back (tcgen05.ld, warp w reads
-// lanes 32 (w % 4) ..) for the epilogue.  Each role waits on one barrier, so
-// the roles overlap across tiles.  Every wait is bounded in wall time; a
+// lanes 32 (w % 4) ..) for the epilogue (in the first layer's weight
+// gradient, whose accumulator is read once at the end, they first build each
+// stage's output gradient from the pooled one: the pooling's backward pass).
+// Each role waits on one barrier, so the roles overlap across tiles.  Every wait is bounded in wall time; a
 // wait that runs out raises the caller's error flag and the block leaves.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
