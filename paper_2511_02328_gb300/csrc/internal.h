@@ -169,7 +169,7 @@ int af_launch_pairs_block(af_plan_t p, const uint8_t* d_in, int64_t nsamp, int64
                           af_rowstats_t* d_stats, cudaStream_t s, int layout, int64_t T0,
                           cudaEvent_t* mid = nullptr, int64_t Lb = 0);
 // The time blocks af_search runs on nout outputs, in tiles: the first small
-// (its input, outputs + Dmax, is copied before any work), each next one four
+// (its input, outputs + Dmax, is copied before any work), each next one six
 // times the previous (its input arrives while the previous one runs), at most
 // cap_tiles each.
 std::vector<int64_t> af_search_block_tiles(int64_t nout, int64_t cap_tiles);

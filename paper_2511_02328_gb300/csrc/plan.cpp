@@ -768,7 +768,7 @@ try {
     if (tm) AF_CUDA(cudaEventRecord(p->ws_tev[0], s));
     if (af_dedisp_uses_pairs(p, nout)) {
         // Group rows: the outputs in growing time blocks (a small first one,
-        // each next four times longer, at most the search layout's length);
+        // each next six times longer, at most the search layout's length);
         // each block's rows and tiles run as soon as its input columns (block
         // end + each channel band's largest delay) are in, overlapping the
         // rest of the copy.
